@@ -1,0 +1,339 @@
+"""Benchmark of the online divergence-distance path (fields + traced paths).
+
+One step = one dd_query over a batch of the grid140 workload: KL and TV
+fields of 64 interior targets over all n = 18,174 vertices (k = 1,028
+boundary columns) and 64 x 256 paths traced on the KL fields.  The Poisson
+kernel is computed once per domain before timing (the paper's
+preprocessing) and reported separately.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one process per GPU under torch.distributed.run; every rank
+processes its own target batches (weak scaling, no data-path collective).
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the
+same workload (rank 0 only).
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "distance fields/s (KL+TV, one target over all vertices) with traced paths"
+UNIT = "fields/s"
+T_BATCH, S_PER_TARGET, MAX_PTS = 64, 256, 512
+N_BATCHES = 8
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload_batches(rank: int):
+    from synthetic import workloads
+    from synthetic.rng import SplitMix64
+    wl = workloads.grid140(T=T_BATCH, S=S_PER_TARGET)
+    batches = [(wl.targets, wl.sources)]
+    rng = SplitMix64(workloads.BASE_SEED + 1000 + rank)
+    for _ in range(N_BATCHES - 1):
+        t = workloads.draw_targets(rng, wl.mesh, T_BATCH)
+        s = workloads.draw_sources(rng, wl.mesh, t, S_PER_TARGET)
+        batches.append((t, s))
+    return wl, batches
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1708_02845_gb300.build import build
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1708_02845_gb300", "_lib", "libdd.so")):
+        build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    from paper_1708_02845_gb300 import dd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    ctx = dd.dd_create(local_rank, stream.cuda_stream)
+    wl, batches = workload_batches(rank)
+    mesh = wl.mesh
+    idx, off = mesh.loop_arrays()
+    mid = dd.dd_load_mesh(ctx, mesh.xy, mesh.tri, idx, off)
+    info = dd.dd_mesh_info(ctx, mid)
+    t0 = time.perf_counter()
+    iters, resid = dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
+    preproc_s = time.perf_counter() - t0
+    n_v, k, k_pad = info["n_v"], info["k"], info["k_pad"]
+
+    T, S = T_BATCH, S_PER_TARGET
+    fields = torch.empty((2, T, n_v), dtype=torch.float32, device=dev)
+    pxy = torch.empty((T * S, MAX_PTS, 2), dtype=torch.float32, device=dev)
+    plen = torch.empty(T * S, dtype=torch.int32, device=dev)
+    pst = torch.empty(T * S, dtype=torch.int32, device=dev)
+    l2_bytes = 256 << 20
+    flush = torch.empty(l2_bytes // 4, dtype=torch.float32, device=dev)
+
+    def step(i):
+        tg, sr = batches[i % len(batches)]
+        dd.dd_query(ctx, mid, tg, sr, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, dd.DD_F_KL, MAX_PTS,
+                    fields, pxy, plen, pst)
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        step(i)
+    dd.dd_sync(ctx)
+    torch.cuda.synchronize()
+
+    # per-kernel split on the same stream (untimed for the metric): fields vs tracing
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tg, sr = batches[0]
+    split_f, split_t = [], []
+    for r in range(3):
+        flush.fill_(1.0)
+        ev[0].record(stream)
+        dd.dd_distance(ctx, mid, tg, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, fields)
+        ev[1].record(stream)
+        dd.dd_trace_fields(ctx, mid, fields[0], tg, sr, MAX_PTS, pxy, plen, pst)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        split_f.append(ev[0].elapsed_time(ev[1]))
+        split_t.append(ev[1].elapsed_time(ev[2]))
+    field_ms, trace_ms = statistics.median(split_f), statistics.median(split_t)
+
+    # timed region: K steps, L2 flushed between steps (outside the step events)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step(args.warmup + i)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dev_ms = float(sum(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dev_ms = float(tt.item())
+        dist.barrier()
+    status = pst.cpu().numpy()
+    lens = plen.cpu().numpy()
+
+    # end to end through the same C-ABI call with host buffers
+    hf = torch.empty((2, T, n_v), dtype=torch.float32).pin_memory()
+    hxy = torch.empty((T * S, MAX_PTS, 2), dtype=torch.float32).pin_memory()
+    hl = torch.empty(T * S, dtype=torch.int32).pin_memory()
+    hs = torch.empty(T * S, dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    for i in range(2):
+        tg, sr = batches[i]
+        dd.dd_query(ctx, mid, tg, sr, 3, 0, 1, MAX_PTS, hf, hxy, hl, hs)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for i in range(e2e_steps):
+        tg, sr = batches[i % len(batches)]
+        dd.dd_query(ctx, mid, tg, sr, 3, 0, 1, MAX_PTS, hf, hxy, hl, hs)
+    e2e_s = time.perf_counter() - e0
+    h2d = T * 4 + T * S * 4
+    d2h = 2 * T * n_v * 4 + T * S * (MAX_PTS * 8 + 8)
+
+    fields_per_step = 2 * T
+    value = world * fields_per_step * args.steps / (dev_ms / 1e3)
+    pk, pk_kind = peaks()
+    # dominant kernel and its roofline
+    sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    if field_ms >= trace_ms:
+        flops = 8.0 * n_v * k * T            # KL: 2 FADD + 2 FFMA(=4 flop), TV: 2 FADD, per (x, b, t)
+        achieved = flops / (field_ms / 1e3) / 1e12
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "field_tile_kernel", "bound": "alu", "achieved": round(achieved, 3),
+                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock sampled)"}
+    else:
+        paths = T * S
+        roof = {"kernel": "trace_kernel", "bound": "latency", "achieved": round(paths / (trace_ms / 1e3), 1),
+                "peak": None, "unit": "paths/s", "frac": None, "traffic": None}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "grid140: unit square h=1/140, 8 square obstacles, n=%d, k=%d; 64 targets x "
+                               "(KL+TV) + 64x256 KL paths per step" % (n_v, k),
+                   "n_v": n_v, "k": k, "targets_per_step": T, "sources_per_target": S, "max_pts": MAX_PTS,
+                   "l2": "flushed between steps (256 MB write outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "paths_per_s": round(world * T * S * args.steps / (dev_ms / 1e3), 1),
+        "kernel_split_ms": {"fields": round(field_ms, 4), "trace": round(trace_ms, 4)},
+        "paths_ok_frac": float(np.mean(status == 0)), "max_path_pts": int(lens.max()),
+        "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(preproc_s, 3)},
+        "wall_s_timed_region": round(wall, 4),
+        "roofline": roof, "peaks": pk_kind,
+        "e2e": {"value": round(world * fields_per_step * e2e_steps / e2e_s, 1), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    dd.dd_destroy(ctx)
+    return line
+
+
+class OracleStep:
+    """The FP64 oracle on a bounded sample of the grid140 step (fields/s)."""
+
+    def __init__(self):
+        from oracle.poisson import PoissonOracle
+        from oracle.trace import Tracer
+        from synthetic import workloads
+        self.wl = workloads.grid140(T=T_BATCH, S=S_PER_TARGET)
+        po = PoissonOracle(self.wl.mesh.xy, self.wl.mesh.tri, self.wl.mesh.loops)
+        self.P = po.full()
+        self.tracer = Tracer(self.wl.mesh.xy, self.wl.mesh.tri)
+
+    def run(self, a: int, sample_paths: int):
+        """KL+TV of target a over all vertices plus `sample_paths` of its 256 paths.
+
+        Returns the seconds one real step-target (2 fields + 256 paths) would take."""
+        from oracle.divergence import kl_field_fast, tv_field
+        P = self.P
+        a = a % len(self.wl.targets)
+        t = int(self.wl.targets[a])
+        c0 = time.perf_counter()
+        kl = kl_field_fast(P, P[t])
+        tv_field(P, P[t])
+        c1 = time.perf_counter()
+        for q in self.wl.sources[a][:sample_paths]:
+            self.tracer.trace(kl, int(q), t, max_pts=MAX_PTS)
+        c2 = time.perf_counter()
+        return (c1 - c0) + (c2 - c1) / sample_paths * S_PER_TARGET
+
+
+def cpu_baseline(sample_targets: int = 2, sample_paths: int = 16):
+    t0 = time.perf_counter()
+    ob = OracleStep()
+    per_target = statistics.mean(ob.run(a, sample_paths) for a in range(sample_targets))
+    return {"value": round(2.0 / per_target, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample_targets} targets of grid140: KL+TV over all n plus {sample_paths} of "
+                      f"{S_PER_TARGET} paths each, scaled to 2 fields + {S_PER_TARGET} paths per target",
+            "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        ob = OracleStep()
+        for i in range(args.warmup):
+            ob.run(i, 2)
+        step_s = [ob.run(args.warmup + i, 4) for i in range(args.steps)]
+        v = 2.0 * args.steps / sum(step_s)
+        line = {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(1e3 * sum(step_s) / args.steps, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": "grid140 (as --impl ours); per step one target: KL+TV over all n "
+                                       "and 4 of its 256 paths, scaled to the full per-target work"},
+                "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(v, 4),
+                                 "sample": "per step 1 target: KL+TV over all n + 4 of 256 paths, scaled"},
+                "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "seconds": round(time.perf_counter() - t0, 1)}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * dd.h -- C ABI of the divergence-distance library (libdd.so).
+ *
+ * Chen, Gotsman & Hormann, "Path Planning with Divergence-Based Distance
+ * Functions".  A planar domain is a triangle mesh with n vertices, k of them
+ * on the boundary (outer loop plus one loop per obstacle) and m = n - k in the
+ * interior (Section IV).  The library
+ *   1. builds the cotangent Laplacian L^c (Section IV),
+ *   2. solves for the discrete Poisson kernel P = [-L_II^-1 L_IB ; I]
+ *      (Eq. 32-33), an n x k non-negative matrix with unit row sums,
+ *   3. evaluates the TV and KL divergence fields of a target vertex t over
+ *      every vertex x (Eq. 34-35),
+ *   4. traces gradient-descent paths through the mesh triangles from source
+ *      vertices to t (Section IV, "Gradient-descent path generation").
+ *
+ * Conventions shared by every call:
+ *  - Every function returns a dd_status; on failure a message is available
+ *    from dd_last_error(ctx).  No C++ exception or abort crosses the ABI.
+ *  - Vertex ids are 0-based int32 in the caller's numbering; rows of P and
+ *    entries of every field use that numbering.  Columns of P follow the
+ *    boundary loops concatenated in the order given to dd_load_mesh.
+ *  - The caller owns every buffer it passes.  The library copies meshes and
+ *    owns P, its solver workspace and cached fields until dd_unload_mesh or
+ *    dd_destroy.
+ *  - Output buffers marked "device or host" may be CUDA device memory on the
+ *    context's device (written asynchronously on the context stream) or host
+ *    memory (pinned or pageable; the call then stages through device memory
+ *    and returns after the copy completed).
+ *  - Calls on one context are not thread-safe; use one context per thread.
+ *  - All GPU work runs on the context stream, in call order.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_ctx dd_ctx;
+
+typedef enum {
+    DD_OK = 0,
+    DD_EINVAL = -1,    /* bad argument: size, id, pointer space, malformed mesh      */
+    DD_ENOMEM = -2,    /* device or host allocation failed                            */
+    DD_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed                 */
+    DD_ESTATE = -4,    /* call out of order (e.g. a field before the Poisson kernel)  */
+    DD_ENOTCONV = -5,  /* the Poisson-kernel solve did not reach rtol in max_iter     */
+    DD_ETIMEOUT = -6,  /* a bounded device-side wait gave up (kernel error flag set)  */
+    DD_EBUDGET = -7    /* the request exceeds the context's device-memory budget      */
+} dd_status;
+
+/* divergence selector bits (Eq. 34: TV, Eq. 35: KL) */
+enum { DD_F_KL = 1, DD_F_TV = 2 };
+
+/* arithmetic of the field evaluation:
+ *  DD_PREC_FP32   FP32 CUDA-core evaluation of Eq. 34-35 term by term
+ *  DD_PREC_BF16X3 KL cross term sum_b P[x,b] log P[t,b] as a tensor-core GEMM
+ *                 of split BF16 hi/lo operands (hi*hi + hi*lo + lo*hi, FP32
+ *                 accumulation); TV is always FP32 */
+enum { DD_PREC_FP32 = 0, DD_PREC_BF16X3 = 1 };
+
+/* per-path status written by the tracer */
+enum {
+    DD_TRACE_OK = 0,          /* reached the target                                   */
+    DD_TRACE_STUCK = 1,       /* stopped in a local minimum (no descending edge)      */
+    DD_TRACE_STEP_LIMIT = 2,  /* walked 4 * n_triangles states without arriving       */
+    DD_TRACE_TRUNCATED = 3    /* the polyline would exceed max_pts points             */
+};
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int32_t dd_version(void);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream) on which all work of the context runs.
+ * *out receives the context.  Errors: DD_EINVAL (no such device), DD_ECUDA. */
+dd_status dd_create(dd_ctx **out, int32_t device, void *cuda_stream);
+
+/* Replace the context stream; later calls enqueue on it. */
+dd_status dd_set_stream(dd_ctx *ctx, void *cuda_stream);
+
+/* Free every device and host resource of the context.  NULL is a no-op. */
+void dd_destroy(dd_ctx *ctx);
+
+/* Message of the last failing call on this context (never NULL). */
+const char *dd_last_error(const dd_ctx *ctx);
+
+/* Block until all work enqueued by the context has finished. */
+dd_status dd_sync(dd_ctx *ctx);
+
+/* Host-only mesh validation (no GPU needed).  Checks: ids in range, every
+ * triangle counter-clockwise with positive area, manifold edges (at most two
+ * triangles, consistently oriented), every vertex used, and boundary loops
+ * that cover exactly the vertices of the edges with one incident triangle,
+ * consecutive loop vertices joined by such an edge.
+ *   xy        host [n_v][2] float64 coordinates
+ *   tri       host [n_t][3] int32 vertex ids, counter-clockwise
+ *   loop_idx  host [k] int32 boundary vertex ids, loops concatenated
+ *   loop_off  host [n_loops + 1] int64 offsets into loop_idx (loop_off[0] = 0)
+ *   info      host [4] int64 out: n_v, k, m, number of edges
+ *   msg       host buffer of msg_len bytes for a failure message (may be NULL)
+ * Errors: DD_EINVAL with the reason in msg. */
+dd_status dd_check_mesh(const double *xy, int64_t n_v, const int32_t *tri, int64_t n_t,
+                        const int32_t *loop_idx, const int64_t *loop_off, int32_t n_loops,
+                        int64_t *info, char *msg, int32_t msg_len);
+
+/* Validate (as dd_check_mesh) and copy a mesh to the device; builds the
+ * triangle adjacency, the vertex-to-triangle and vertex-neighbour lists and
+ * the cotangent Laplacian (Section IV).  Arguments as in dd_check_mesh, all
+ * host memory.  *mesh_id receives the handle.  Errors: DD_EINVAL, DD_ENOMEM,
+ * DD_ECUDA. */
+dd_status dd_load_mesh(dd_ctx *ctx, const double *xy, int64_t n_v, const int32_t *tri, int64_t n_t,
+                       const int32_t *loop_idx, const int64_t *loop_off, int32_t n_loops,
+                       int32_t *mesh_id);
+
+/* Release a mesh and everything computed for it. */
+dd_status dd_unload_mesh(dd_ctx *ctx, int32_t mesh);
+
+/* Sizes of a loaded mesh: info[0..6] = n_v, n_t, k, m, k_pad (row pitch of P
+ * in floats, a multiple of 4), has_poisson_kernel (0/1), device bytes held. */
+dd_status dd_mesh_info(dd_ctx *ctx, int32_t mesh, int64_t *info);
+
+/* Solve for the Poisson kernel, Eq. (32)-(33): (-L_II) X = L_IB for all k
+ * right-hand sides at once by Jacobi-preconditioned conjugate gradients in
+ * FP64 on the device, iterating until every column's residual satisfies
+ * ||r_b|| <= rtol * ||L_IB e_b|| or max_iter iterations have run.  The result
+ * is stored as FP32 P (row pitch k_pad, boundary rows the identity, negative
+ * round-off clamped to 0, values below FLT_MIN flushed to 0).  All columns
+ * keep iterating until the slowest one meets rtol, so that small entries of
+ * P, whose logarithms enter KL, are accurate well beyond rtol.
+ *   rtol      relative residual target, > 0 (1e-15 gives KL within 1e-5)
+ *   max_iter  iteration cap, > 0
+ *   iters     host out (may be NULL): iterations run
+ *   resid     host out (may be NULL): largest relative residual at the end
+ * Synchronous.  Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA, DD_ENOTCONV (P is
+ * still stored, with the residual reported). */
+dd_status dd_poisson_kernel(dd_ctx *ctx, int32_t mesh, double rtol, int32_t max_iter,
+                            int32_t *iters, double *resid);
+
+/* Install a Poisson kernel computed elsewhere (e.g. a cached copy keyed by
+ * the mesh): P is host [n_v][k] float64 row-major in the mesh's vertex and
+ * column order.  It is stored exactly as dd_poisson_kernel stores its own
+ * result (FP32, clamp and flush).  Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA. */
+dd_status dd_set_poisson_kernel(dd_ctx *ctx, int32_t mesh, const double *P);
+
+/* Copy the stored FP32 Poisson kernel out, as [n_v][k] (pitch k, no padding).
+ * out: device or host.  Errors: DD_ESTATE if none is stored. */
+dd_status dd_get_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out);
+
+/* Divergence fields of T target vertices, Eq. (34)-(35):
+ *   TV_t(x) = sum_b |P[x,b] - P[t,b]|
+ *   KL_t(x) = sum_b P[x,b] log(P[x,b] / P[t,b])     (Eq. 17 with z = x, w = t)
+ * with 0 log 0 = 0, for every vertex x.
+ *   targets  host [T] interior vertex ids (a boundary target is DD_EINVAL:
+ *            its KL row is infinite)
+ *   f_mask   DD_F_KL | DD_F_TV (at least one bit)
+ *   prec     DD_PREC_FP32 or DD_PREC_BF16X3
+ *   out      device or host float32 [nf][T][n_v], nf = number of bits set,
+ *            KL block first when both are requested
+ * In FP32 a log argument below FLT_MIN is taken as FLT_MIN: where P[t,b] = 0
+ * but P[x,b] > 0 (a boundary row x of a column with no interior support) the
+ * exact KL is +inf and the result is finite and at least 87.
+ * Errors: DD_EINVAL, DD_ESTATE (no Poisson kernel), DD_ENOMEM, DD_ECUDA. */
+dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
+                      uint32_t f_mask, int32_t prec, float *out);
+
+/* Trace gradient-descent paths from S source vertices to `target` on the
+ * field of divergence f (DD_F_KL or DD_F_TV), evaluated in FP32 (Section IV).
+ *   sources     host [S] vertex ids
+ *   max_pts     capacity of each polyline in points (>= 2)
+ *   out_xy      device or host float32 [S][max_pts][2]; path s occupies the
+ *               first out_len[s] points, starting at the source vertex and,
+ *               when the status is DD_TRACE_OK, ending at the target vertex
+ *   out_len     device or host int32 [S]
+ *   out_status  device or host int32 [S], DD_TRACE_* codes
+ * Errors: DD_EINVAL, DD_ESTATE, DD_ENOMEM, DD_ECUDA. */
+dd_status dd_trace(dd_ctx *ctx, int32_t mesh, int32_t target, uint32_t f,
+                   const int32_t *sources, int32_t S, int32_t max_pts,
+                   float *out_xy, int32_t *out_len, int32_t *out_status);
+
+/* Trace T x S paths on caller-supplied fields (any scalar per vertex whose
+ * minimum is at the target, e.g. a field from dd_distance).
+ *   fields      device float32 [T][n_v] (row a is the field of targets[a])
+ *   targets     host [T] vertex ids
+ *   sources     host [T][S] vertex ids
+ *   outputs as dd_trace with T * S paths, path (a, s) at index a * S + s.
+ * Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA. */
+dd_status dd_trace_fields(dd_ctx *ctx, int32_t mesh, const float *fields,
+                          const int32_t *targets, int32_t T, const int32_t *sources, int32_t S,
+                          int32_t max_pts, float *out_xy, int32_t *out_len, int32_t *out_status);
+
+/* One pass of the whole online path for a batch: the fields of every target
+ * (dd_distance with f_mask, prec) and the T x S paths traced on the field of
+ * divergence trace_f (one bit of f_mask).  Outputs as dd_distance (fields)
+ * and dd_trace_fields (paths); each may be device or host memory.  Host
+ * outputs are copied back before the call returns. */
+dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
+                   const int32_t *sources, int32_t S, uint32_t f_mask, int32_t prec,
+                   uint32_t trace_f, int32_t max_pts, float *out_fields,
+                   float *out_xy, int32_t *out_len, int32_t *out_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

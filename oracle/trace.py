@@ -164,6 +164,12 @@ class Tracer:
             rb = -(self.gphi[t2, ib] @ g2)
             sa = la / -ra if ra < 0.0 else math.inf
             sb = lb / -rb if rb < 0.0 else math.inf
+            if math.isinf(min(sa, sb)):          # no exit edge found: treat as a valley edge
+                low = a if (f[a] < f[b] or (f[a] == f[b] and a < b)) else b
+                if not push(xy[low]):
+                    return np.asarray(path), TRUNCATED
+                state = ("v", low)
+                continue
             c = int(self.tri[t2, c2])
             if sa <= sb:
                 s = sa

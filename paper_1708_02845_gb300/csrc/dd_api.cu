@@ -1,0 +1,596 @@
+// C ABI of libdd: context, mesh upload, Poisson kernel, fields and paths.
+// Every entry point returns a dd_status and never lets a C++ exception out.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dd_internal.h"
+
+namespace {
+
+enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_COUNT };
+
+struct MeshSlot {
+    bool live = false;
+    DevMesh dev;
+};
+
+}  // namespace
+
+struct dd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<MeshSlot> meshes;
+    void *scratch[S_COUNT] = {};
+    size_t scratch_cap[S_COUNT] = {};
+    int *d_err = nullptr;                     // device error flag written by kernels
+    void *pinned[S_COUNT] = {};               // host staging for index uploads, one per scratch id
+    size_t pinned_cap[S_COUNT] = {};
+    cudaEvent_t pinned_free[S_COUNT] = {};    // recorded after the last upload from pinned[id]
+};
+
+namespace {
+
+dd_status set_err(dd_ctx *c, dd_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+dd_status cuda_err(dd_ctx *c, cudaError_t e, const char *what) {
+    cudaGetLastError();
+    return set_err(c, e == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, what); \
+    } while (0)
+
+dd_status select_device(dd_ctx *ctx) {
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+    return DD_OK;
+}
+
+// grow a scratch buffer (synchronises the stream first when it must reallocate)
+dd_status ensure_scratch(dd_ctx *ctx, int id, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (ctx->scratch_cap[id] >= bytes) return DD_OK;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize before scratch growth");
+    if (ctx->scratch[id]) cudaFree(ctx->scratch[id]);
+    ctx->scratch[id] = nullptr;
+    ctx->scratch_cap[id] = 0;
+    size_t cap = bytes + bytes / 4;
+    cudaError_t e = cudaMalloc(&ctx->scratch[id], cap);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "scratch allocation");
+    ctx->scratch_cap[id] = cap;
+    return DD_OK;
+}
+
+// copy a small host index array to a scratch buffer through pinned staging
+dd_status upload(dd_ctx *ctx, int id, const void *host, size_t bytes) {
+    dd_status st = ensure_scratch(ctx, id, bytes);
+    if (st != DD_OK) return st;
+    if (bytes == 0) return DD_OK;
+    // the previous upload from this staging buffer must have left it
+    CK(cudaEventSynchronize(ctx->pinned_free[id]), "wait for staging");
+    if (ctx->pinned_cap[id] < bytes) {
+        if (ctx->pinned[id]) cudaFreeHost(ctx->pinned[id]);
+        ctx->pinned[id] = nullptr;
+        ctx->pinned_cap[id] = 0;
+        size_t cap = bytes + bytes / 4 + 4096;
+        CK(cudaMallocHost(&ctx->pinned[id], cap), "pinned staging allocation");
+        ctx->pinned_cap[id] = cap;
+    }
+    std::memcpy(ctx->pinned[id], host, bytes);
+    CK(cudaMemcpyAsync(ctx->scratch[id], ctx->pinned[id], bytes, cudaMemcpyHostToDevice, ctx->stream),
+       "index upload");
+    CK(cudaEventRecord(ctx->pinned_free[id], ctx->stream), "record staging event");
+    return DD_OK;
+}
+
+// 1 = device memory of this context's device, 0 = host memory, -1 = another device
+int pointer_space(const dd_ctx *ctx, const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return a.device == ctx->device ? 1 : -1;
+    return 0;
+}
+
+dd_status get_mesh(dd_ctx *ctx, int32_t mesh, DevMesh **out) {
+    if (!ctx) return DD_EINVAL;
+    if (mesh < 0 || mesh >= (int32_t)ctx->meshes.size() || !ctx->meshes[mesh].live)
+        return set_err(ctx, DD_EINVAL, "unknown mesh id " + std::to_string(mesh));
+    *out = &ctx->meshes[mesh].dev;
+    return DD_OK;
+}
+
+template <typename T>
+dd_status dev_copy(dd_ctx *ctx, DevMesh &m, T **dst, const T *src, size_t count) {
+    size_t bytes = (count ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)dst, bytes);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "mesh allocation");
+    m.owned.push_back(*dst);
+    m.bytes += (int64_t)bytes;
+    if (count) {
+        e = cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "mesh upload");
+    }
+    return DD_OK;
+}
+
+void free_mesh(DevMesh &m) {
+    for (void *p : m.owned) cudaFree(p);
+    m = DevMesh();
+}
+
+dd_status check_targets(dd_ctx *ctx, const DevMesh &m, const int32_t *ids, int64_t count, bool interior_only,
+                        const char *what) {
+    if (count > 0 && !ids) return set_err(ctx, DD_EINVAL, std::string(what) + " pointer is null");
+    if (count > 0 && pointer_space(ctx, ids) != 0)
+        return set_err(ctx, DD_EINVAL, std::string(what) + " must be host memory");
+    for (int64_t i = 0; i < count; ++i) {
+        int32_t v = ids[i];
+        if (v < 0 || v >= m.n_v)
+            return set_err(ctx, DD_EINVAL, std::string(what) + " id out of range: " + std::to_string(v));
+        if (interior_only && m.is_boundary[v])
+            return set_err(ctx, DD_EINVAL, std::string(what) + " must be interior vertices; " + std::to_string(v) +
+                                               " is on the boundary");
+    }
+    return DD_OK;
+}
+
+dd_status check_kernel_flag(dd_ctx *ctx) {
+    int flag = 0;
+    CK(cudaMemcpy(&flag, ctx->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read kernel error flag");
+    if (flag) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return set_err(ctx, DD_ETIMEOUT, "a bounded device-side wait gave up");
+    }
+    return DD_OK;
+}
+
+// fields of T targets into dst [nf][T][n_v] (device), targets already in scratch
+dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t T, uint32_t f_mask, float *dst) {
+    dd_status st = ensure_scratch(ctx, S_STAGE, 3 * (size_t)T * m.k_pad * sizeof(float));
+    if (st != DD_OK) return st;
+    float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
+    launch_stage_targets(m.P, m.k_pad, m.k, d_targets, T, stage, ctx->stream);
+    float *kl = (f_mask & DD_F_KL) ? dst : nullptr;
+    float *tv = (f_mask & DD_F_TV) ? dst + ((f_mask & DD_F_KL) ? (int64_t)T * m.n_v : 0) : nullptr;
+    launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream);
+    CK(cudaGetLastError(), "field kernel launch");
+    return DD_OK;
+}
+
+int popcount2(uint32_t f) { return ((f & DD_F_KL) ? 1 : 0) + ((f & DD_F_TV) ? 1 : 0); }
+
+}  // namespace
+
+extern "C" {
+
+int32_t dd_version(void) { return 100; }
+
+dd_status dd_create(dd_ctx **out, int32_t device, void *cuda_stream) {
+    if (!out) return DD_EINVAL;
+    *out = nullptr;
+    try {
+        int count = 0;
+        if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+            cudaGetLastError();
+            return DD_EINVAL;
+        }
+        dd_ctx *ctx = new dd_ctx();
+        ctx->device = device;
+        ctx->stream = (cudaStream_t)cuda_stream;
+        bool ok = cudaSetDevice(device) == cudaSuccess && cudaMalloc((void **)&ctx->d_err, sizeof(int)) == cudaSuccess &&
+                  cudaMemset(ctx->d_err, 0, sizeof(int)) == cudaSuccess;
+        for (int i = 0; ok && i < S_COUNT; ++i)
+            ok = cudaEventCreateWithFlags(&ctx->pinned_free[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            dd_destroy(ctx);
+            return DD_ECUDA;
+        }
+        *out = ctx;
+        return DD_OK;
+    } catch (...) {
+        return DD_ENOMEM;
+    }
+}
+
+dd_status dd_set_stream(dd_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return DD_EINVAL;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return DD_OK;
+}
+
+void dd_destroy(dd_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &s : ctx->meshes)
+        if (s.live) free_mesh(s.dev);
+    for (int i = 0; i < S_COUNT; ++i)
+        if (ctx->scratch[i]) cudaFree(ctx->scratch[i]);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    for (int i = 0; i < S_COUNT; ++i) {
+        if (ctx->pinned[i]) cudaFreeHost(ctx->pinned[i]);
+        if (ctx->pinned_free[i]) cudaEventDestroy(ctx->pinned_free[i]);
+    }
+    delete ctx;
+}
+
+const char *dd_last_error(const dd_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dd_status dd_sync(dd_ctx *ctx) {
+    if (!ctx) return DD_EINVAL;
+    try {
+        dd_status st = select_device(ctx);
+        if (st != DD_OK) return st;
+        CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+        return check_kernel_flag(ctx);
+    } catch (...) {
+        return DD_ENOMEM;
+    }
+}
+
+dd_status dd_check_mesh(const double *xy, int64_t n_v, const int32_t *tri, int64_t n_t, const int32_t *loop_idx,
+                        const int64_t *loop_off, int32_t n_loops, int64_t *info, char *msg, int32_t msg_len) {
+    try {
+        HostMesh h;
+        std::string err;
+        dd_status st = build_host_mesh(xy, n_v, tri, n_t, loop_idx, loop_off, n_loops, h, err);
+        if (msg && msg_len > 0) {
+            std::snprintf(msg, (size_t)msg_len, "%s", st == DD_OK ? "" : err.c_str());
+        }
+        if (st == DD_OK && info) {
+            info[0] = h.n_v;
+            info[1] = h.k;
+            info[2] = h.m;
+            info[3] = h.n_edges;
+        }
+        return st;
+    } catch (const std::bad_alloc &) {
+        return DD_ENOMEM;
+    } catch (...) {
+        return DD_EINVAL;
+    }
+}
+
+dd_status dd_load_mesh(dd_ctx *ctx, const double *xy, int64_t n_v, const int32_t *tri, int64_t n_t,
+                       const int32_t *loop_idx, const int64_t *loop_off, int32_t n_loops, int32_t *mesh_id) {
+    if (!ctx || !mesh_id) return DD_EINVAL;
+    try {
+        dd_status st = select_device(ctx);
+        if (st != DD_OK) return st;
+        HostMesh h;
+        std::string err;
+        st = build_host_mesh(xy, n_v, tri, n_t, loop_idx, loop_off, n_loops, h, err);
+        if (st != DD_OK) return set_err(ctx, st, err);
+        MeshSlot slot;
+        DevMesh &m = slot.dev;
+        m.n_v = h.n_v;
+        m.n_t = h.n_t;
+        m.k = h.k;
+        m.m = h.m;
+        m.k_pad = (h.k + 3) / 4 * 4;
+        std::vector<float2> xyf(h.n_v);
+        for (int64_t v = 0; v < h.n_v; ++v) xyf[v] = make_float2((float)h.xy[2 * v], (float)h.xy[2 * v + 1]);
+        std::vector<int4> tri4(h.n_t), nbr4(h.n_t);
+        for (int64_t t = 0; t < h.n_t; ++t) {
+            tri4[t] = make_int4(h.tri[3 * t], h.tri[3 * t + 1], h.tri[3 * t + 2], 0);
+            nbr4[t] = make_int4(h.tnbr[3 * t], h.tnbr[3 * t + 1], h.tnbr[3 * t + 2], 0);
+        }
+        std::vector<float4> g4(2 * h.n_t);
+        for (int64_t t = 0; t < h.n_t; ++t) {
+            const float *g = &h.gphi[6 * t];
+            g4[2 * t] = make_float4(g[0], g[1], g[2], g[3]);
+            g4[2 * t + 1] = make_float4(g[4], g[5], 0.f, 0.f);
+        }
+        auto undo = [&](dd_status s2) {
+            free_mesh(m);
+            return s2;
+        };
+        if ((st = dev_copy(ctx, m, &m.xy, xyf.data(), xyf.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.tri, tri4.data(), tri4.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.tnbr, nbr4.data(), nbr4.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.gphi, g4.data(), g4.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.vt_off, h.vt_off.data(), h.vt_off.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.vt, h.vt.data(), h.vt.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.vn_off, h.vn_off.data(), h.vn_off.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.vn, h.vn.data(), h.vn.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.interior, h.I.data(), h.I.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.boundary, h.B.data(), h.B.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.a_off, h.a_off.data(), h.a_off.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.a_col, h.a_col.data(), h.a_col.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.a_val, h.a_val.data(), h.a_val.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.a_diag, h.a_diag.data(), h.a_diag.size())) != DD_OK) return undo(st);
+        m.n_rb = (int64_t)h.rb_row.size();
+        if ((st = dev_copy(ctx, m, &m.rb_row, h.rb_row.data(), h.rb_row.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.rb_col, h.rb_col.data(), h.rb_col.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.rb_val, h.rb_val.data(), h.rb_val.size())) != DD_OK) return undo(st);
+        m.is_boundary.assign(h.n_v, 0);
+        for (int32_t v : h.B) m.is_boundary[v] = 1;
+        slot.live = true;
+        ctx->meshes.push_back(slot);
+        *mesh_id = (int32_t)ctx->meshes.size() - 1;
+        return DD_OK;
+    } catch (const std::bad_alloc &) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    } catch (...) {
+        return set_err(ctx, DD_EINVAL, "unexpected failure in dd_load_mesh");
+    }
+}
+
+dd_status dd_unload_mesh(dd_ctx *ctx, int32_t mesh) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    select_device(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    free_mesh(*m);
+    ctx->meshes[mesh].live = false;
+    return DD_OK;
+}
+
+dd_status dd_mesh_info(dd_ctx *ctx, int32_t mesh, int64_t *info) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    if (!info) return set_err(ctx, DD_EINVAL, "info is null");
+    info[0] = m->n_v;
+    info[1] = m->n_t;
+    info[2] = m->k;
+    info[3] = m->m;
+    info[4] = m->k_pad;
+    info[5] = m->has_P ? 1 : 0;
+    info[6] = m->bytes;
+    return DD_OK;
+}
+
+dd_status dd_poisson_kernel(dd_ctx *ctx, int32_t mesh, double rtol, int32_t max_iter, int32_t *iters,
+                            double *resid) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    if (!(rtol > 0.0) || max_iter < 1) return set_err(ctx, DD_EINVAL, "rtol must be > 0 and max_iter >= 1");
+    try {
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        std::string err;
+        st = run_pcg(*m, rtol, max_iter, ctx->stream, iters, resid, err);
+        if (st != DD_OK) set_err(ctx, st, err);
+        return st;
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
+dd_status dd_set_poisson_kernel(dd_ctx *ctx, int32_t mesh, const double *P) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    if (!P || pointer_space(ctx, P) != 0) return set_err(ctx, DD_EINVAL, "P must be a host pointer");
+    if ((st = select_device(ctx)) != DD_OK) return st;
+    std::string err;
+    st = store_poisson(*m, P, ctx->stream, err);
+    if (st != DD_OK) set_err(ctx, st, err);
+    return st;
+}
+
+dd_status dd_get_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    if (!m->has_P) return set_err(ctx, DD_ESTATE, "no Poisson kernel stored");
+    if (!out) return set_err(ctx, DD_EINVAL, "out is null");
+    int sp = pointer_space(ctx, out);
+    if (sp < 0) return set_err(ctx, DD_EINVAL, "out is on another device");
+    if ((st = select_device(ctx)) != DD_OK) return st;
+    CK(cudaMemcpy2DAsync(out, (size_t)m->k * sizeof(float), m->P, (size_t)m->k_pad * sizeof(float),
+                         (size_t)m->k * sizeof(float), (size_t)m->n_v, cudaMemcpyDefault, ctx->stream),
+       "copy P");
+    if (sp == 0) CK(cudaStreamSynchronize(ctx->stream), "copy P");
+    return DD_OK;
+}
+
+dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T, uint32_t f_mask, int32_t prec,
+                      float *out) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    try {
+        if (!m->has_P) return set_err(ctx, DD_ESTATE, "dd_distance before dd_poisson_kernel");
+        if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
+        if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV)))
+            return set_err(ctx, DD_EINVAL, "f_mask must be a non-empty combination of DD_F_KL and DD_F_TV");
+        if (prec != DD_PREC_FP32) return set_err(ctx, DD_EINVAL, "unsupported precision");
+        if (!out) return set_err(ctx, DD_EINVAL, "out is null");
+        if ((st = check_targets(ctx, *m, targets, T, true, "targets")) != DD_OK) return st;
+        const int sp = pointer_space(ctx, out);
+        if (sp < 0) return set_err(ctx, DD_EINVAL, "out is on another device");
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        if ((st = upload(ctx, S_TARGETS, targets, (size_t)T * sizeof(int32_t))) != DD_OK) return st;
+        const size_t out_bytes = (size_t)popcount2(f_mask) * T * m->n_v * sizeof(float);
+        float *dst = out;
+        if (sp == 0) {
+            if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
+            dst = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
+        }
+        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, dst);
+        if (st != DD_OK) return st;
+        if (sp == 0) {
+            CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy fields to host");
+            CK(cudaStreamSynchronize(ctx->stream), "fields");
+            return check_kernel_flag(ctx);
+        }
+        return DD_OK;
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
+dd_status dd_trace_fields(dd_ctx *ctx, int32_t mesh, const float *fields, const int32_t *targets, int32_t T,
+                          const int32_t *sources, int32_t S, int32_t max_pts, float *out_xy, int32_t *out_len,
+                          int32_t *out_status);
+
+namespace {
+
+// paths of T x S (target, source) pairs on device fields [T][n_v]; ids already checked
+dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32_t *targets, int32_t T,
+                     const int32_t *sources, int32_t S, int32_t max_pts, float *out_xy, int32_t *out_len,
+                     int32_t *out_status, bool targets_uploaded) {
+    dd_status st;
+    if (!targets_uploaded && (st = upload(ctx, S_TARGETS, targets, (size_t)T * sizeof(int32_t))) != DD_OK) return st;
+    if ((st = upload(ctx, S_SOURCES, sources, (size_t)T * S * sizeof(int32_t))) != DD_OK) return st;
+    const int sx = pointer_space(ctx, out_xy), sl = pointer_space(ctx, out_len), ss = pointer_space(ctx, out_status);
+    if (sx < 0 || sl < 0 || ss < 0) return set_err(ctx, DD_EINVAL, "path outputs on another device");
+    const size_t n = (size_t)T * S;
+    float2 *dxy = reinterpret_cast<float2 *>(out_xy);
+    int32_t *dlen = out_len, *dst = out_status;
+    if (sx == 0) {
+        if ((st = ensure_scratch(ctx, S_XY, n * max_pts * sizeof(float2))) != DD_OK) return st;
+        dxy = reinterpret_cast<float2 *>(ctx->scratch[S_XY]);
+    }
+    if (sl == 0) {
+        if ((st = ensure_scratch(ctx, S_LEN, n * sizeof(int32_t))) != DD_OK) return st;
+        dlen = reinterpret_cast<int32_t *>(ctx->scratch[S_LEN]);
+    }
+    if (ss == 0) {
+        if ((st = ensure_scratch(ctx, S_STATUS, n * sizeof(int32_t))) != DD_OK) return st;
+        dst = reinterpret_cast<int32_t *>(ctx->scratch[S_STATUS]);
+    }
+    launch_trace(m, d_fields, m.n_v, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
+                 reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), T, S, max_pts, dxy, dlen, dst,
+                 ctx->stream);
+    CK(cudaGetLastError(), "trace kernel launch");
+    bool host = false;
+    if (sx == 0) {
+        CK(cudaMemcpyAsync(out_xy, dxy, n * max_pts * sizeof(float2), cudaMemcpyDeviceToHost, ctx->stream),
+           "copy paths");
+        host = true;
+    }
+    if (sl == 0) {
+        CK(cudaMemcpyAsync(out_len, dlen, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "copy lengths");
+        host = true;
+    }
+    if (ss == 0) {
+        CK(cudaMemcpyAsync(out_status, dst, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
+           "copy statuses");
+        host = true;
+    }
+    if (host) {
+        CK(cudaStreamSynchronize(ctx->stream), "paths");
+        return check_kernel_flag(ctx);
+    }
+    return DD_OK;
+}
+
+dd_status check_path_args(dd_ctx *ctx, int32_t S, int32_t max_pts, const void *a, const void *b, const void *c) {
+    if (S < 1) return set_err(ctx, DD_EINVAL, "S must be >= 1");
+    if (max_pts < 2) return set_err(ctx, DD_EINVAL, "max_pts must be >= 2");
+    if (!a || !b || !c) return set_err(ctx, DD_EINVAL, "null path output");
+    return DD_OK;
+}
+
+}  // namespace
+
+dd_status dd_trace_fields(dd_ctx *ctx, int32_t mesh, const float *fields, const int32_t *targets, int32_t T,
+                          const int32_t *sources, int32_t S, int32_t max_pts, float *out_xy, int32_t *out_len,
+                          int32_t *out_status) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    try {
+        if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
+        if ((st = check_path_args(ctx, S, max_pts, out_xy, out_len, out_status)) != DD_OK) return st;
+        if (!fields || pointer_space(ctx, fields) != 1)
+            return set_err(ctx, DD_EINVAL, "fields must be device memory of the context's device");
+        if ((st = check_targets(ctx, *m, targets, T, false, "targets")) != DD_OK) return st;
+        if ((st = check_targets(ctx, *m, sources, (int64_t)T * S, false, "sources")) != DD_OK) return st;
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        return trace_into(ctx, *m, fields, targets, T, sources, S, max_pts, out_xy, out_len, out_status, false);
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
+dd_status dd_trace(dd_ctx *ctx, int32_t mesh, int32_t target, uint32_t f, const int32_t *sources, int32_t S,
+                   int32_t max_pts, float *out_xy, int32_t *out_len, int32_t *out_status) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    try {
+        if (!m->has_P) return set_err(ctx, DD_ESTATE, "dd_trace before dd_poisson_kernel");
+        if (f != DD_F_KL && f != DD_F_TV) return set_err(ctx, DD_EINVAL, "f must be DD_F_KL or DD_F_TV");
+        if ((st = check_path_args(ctx, S, max_pts, out_xy, out_len, out_status)) != DD_OK) return st;
+        if ((st = check_targets(ctx, *m, &target, 1, true, "target")) != DD_OK) return st;
+        if ((st = check_targets(ctx, *m, sources, S, false, "sources")) != DD_OK) return st;
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        if ((st = upload(ctx, S_TARGETS, &target, sizeof(int32_t))) != DD_OK) return st;
+        if ((st = ensure_scratch(ctx, S_FIELDS, (size_t)m->n_v * sizeof(float))) != DD_OK) return st;
+        float *field = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
+        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), 1, f, field);
+        if (st != DD_OK) return st;
+        return trace_into(ctx, *m, field, &target, 1, sources, S, max_pts, out_xy, out_len, out_status, true);
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
+dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T, const int32_t *sources, int32_t S,
+                   uint32_t f_mask, int32_t prec, uint32_t trace_f, int32_t max_pts, float *out_fields,
+                   float *out_xy, int32_t *out_len, int32_t *out_status) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    try {
+        if (!m->has_P) return set_err(ctx, DD_ESTATE, "dd_query before dd_poisson_kernel");
+        if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
+        if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV)))
+            return set_err(ctx, DD_EINVAL, "bad f_mask");
+        if ((trace_f != DD_F_KL && trace_f != DD_F_TV) || !(f_mask & trace_f))
+            return set_err(ctx, DD_EINVAL, "trace_f must be one bit of f_mask");
+        if (prec != DD_PREC_FP32) return set_err(ctx, DD_EINVAL, "unsupported precision");
+        if (!out_fields) return set_err(ctx, DD_EINVAL, "out_fields is null");
+        if ((st = check_path_args(ctx, S, max_pts, out_xy, out_len, out_status)) != DD_OK) return st;
+        if ((st = check_targets(ctx, *m, targets, T, true, "targets")) != DD_OK) return st;
+        if ((st = check_targets(ctx, *m, sources, (int64_t)T * S, false, "sources")) != DD_OK) return st;
+        const int sf = pointer_space(ctx, out_fields);
+        if (sf < 0) return set_err(ctx, DD_EINVAL, "out_fields is on another device");
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        if ((st = upload(ctx, S_TARGETS, targets, (size_t)T * sizeof(int32_t))) != DD_OK) return st;
+        const size_t out_bytes = (size_t)popcount2(f_mask) * T * m->n_v * sizeof(float);
+        float *dst = out_fields;
+        if (sf == 0) {
+            if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
+            dst = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
+        }
+        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, dst);
+        if (st != DD_OK) return st;
+        const float *trace_field = dst + ((trace_f == DD_F_TV && (f_mask & DD_F_KL)) ? (int64_t)T * m->n_v : 0);
+        if (sf == 0)
+            CK(cudaMemcpyAsync(out_fields, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy fields");
+        st = trace_into(ctx, *m, trace_field, targets, T, sources, S, max_pts, out_xy, out_len, out_status, true);
+        if (st != DD_OK) return st;
+        if (sf == 0) {
+            CK(cudaStreamSynchronize(ctx->stream), "query");
+            return check_kernel_flag(ctx);
+        }
+        return DD_OK;
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// Internal declarations shared by the translation units of libdd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dd.h"
+
+// ---------------------------------------------------------------- host mesh
+// Topology and Laplacian of Section IV, built on the host once per mesh.
+struct HostMesh {
+    int64_t n_v = 0, n_t = 0, k = 0, m = 0, n_edges = 0;
+    std::vector<double> xy;          // [n_v][2]
+    std::vector<int32_t> tri;        // [n_t][3] counter-clockwise
+    std::vector<int32_t> B;          // boundary vertex ids, column order
+    std::vector<int32_t> I;          // interior vertex ids, ascending
+    std::vector<int32_t> col_of;     // vertex -> boundary column, or -1
+    std::vector<int32_t> row_of;     // vertex -> interior row, or -1
+    std::vector<int32_t> tnbr;       // [n_t][3] triangle across the edge opposite local vertex i, or -1
+    std::vector<int32_t> vt_off, vt; // vertex -> incident triangles (ascending)
+    std::vector<int32_t> vn_off, vn; // vertex -> neighbour vertices (ascending)
+    // A = -L_II (symmetric positive definite M-matrix) in CSR, interior numbering
+    std::vector<int64_t> a_off;
+    std::vector<int32_t> a_col;
+    std::vector<double> a_val;
+    std::vector<double> a_diag;
+    // right-hand sides L_IB: one entry per (interior row, boundary column) edge
+    std::vector<int32_t> rb_row, rb_col;
+    std::vector<double> rb_val;
+    std::vector<float> gphi;         // [n_t][6] gradient of the hat functions
+};
+
+// Validate and build; returns DD_OK or DD_EINVAL with a message.
+dd_status build_host_mesh(const double *xy, int64_t n_v, const int32_t *tri, int64_t n_t,
+                          const int32_t *loop_idx, const int64_t *loop_off, int32_t n_loops,
+                          HostMesh &out, std::string &err);
+
+// ---------------------------------------------------------------- device mesh
+struct DevMesh {
+    int64_t n_v = 0, n_t = 0, k = 0, m = 0, k_pad = 0;
+    float2 *xy = nullptr;      // [n_v]
+    int4 *tri = nullptr;       // [n_t] (v0, v1, v2, 0)
+    int4 *tnbr = nullptr;      // [n_t] (t0, t1, t2, 0)
+    float4 *gphi = nullptr;    // [n_t][2]: (g0x, g0y, g1x, g1y), (g2x, g2y, 0, 0)
+    int32_t *vt_off = nullptr, *vt = nullptr;
+    int32_t *vn_off = nullptr, *vn = nullptr;
+    int32_t *interior = nullptr;   // [m]
+    int32_t *boundary = nullptr;   // [k]
+    int64_t *a_off = nullptr;
+    int32_t *a_col = nullptr;
+    double *a_val = nullptr, *a_diag = nullptr;
+    int64_t n_rb = 0;
+    int32_t *rb_row = nullptr, *rb_col = nullptr;
+    double *rb_val = nullptr;
+    float *P = nullptr;        // [n_v][k_pad] FP32 Poisson kernel
+    bool has_P = false;
+    int64_t bytes = 0;
+    std::vector<void *> owned;
+    std::vector<uint8_t> is_boundary;  // host copy: vertex flags
+    std::vector<int32_t> vn_off_h, vn_h;
+};
+
+// ---------------------------------------------------------------- kernels
+// Poisson kernel: FP64 Jacobi-PCG over all columns; fills m.P.
+dd_status run_pcg(DevMesh &m, double rtol, int32_t max_iter, cudaStream_t s, int32_t *iters,
+                  double *resid, std::string &err);
+// Store a host FP64 P [n_v][k] into m.P with the same clamp/flush as the solver.
+dd_status store_poisson(DevMesh &m, const double *P, cudaStream_t s, std::string &err);
+
+// Per-target staging of P[t,:] and its split logarithm: stage[a][b] =
+// (P[t_a,b], log-mantissa, exponent, 0).
+void launch_stage_targets(const float *P, int64_t k_pad, int64_t k, const int32_t *targets, int32_t T,
+                          float4 *stage, cudaStream_t s);
+// FP32 fields.  out_kl / out_tv: [T][n_v] (either may be null).
+void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T,
+                        float *out_kl, float *out_tv, int *err_flag, cudaStream_t s);
+// Tracer: T*S paths.
+void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,
+                  const int32_t *sources, int32_t T, int32_t S, int32_t max_pts, float2 *out_xy,
+                  int32_t *out_len, int32_t *out_status, cudaStream_t s);
+
+#define DD_CUDA_TRY(expr, errstr)                                                   \
+    do {                                                                            \
+        cudaError_t e__ = (expr);                                                   \
+        if (e__ != cudaSuccess) {                                                   \
+            errstr = std::string(#expr) + ": " + cudaGetErrorString(e__);           \
+            return DD_ECUDA;                                                        \
+        }                                                                           \
+    } while (0)

@@ -1,0 +1,204 @@
+"""Thin ctypes binding of libdd.so: the C ABI of include/dd.h, same names.
+
+Argument marshalling only: every step of the path runs in the library's
+CUDA kernels.  Buffers may be torch tensors (device or host) or numpy arrays
+(host); their data pointers are passed through unchanged.  If the library is
+missing this module raises ImportError -- there is no fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdd.so")
+
+DD_OK, DD_EINVAL, DD_ENOMEM, DD_ECUDA, DD_ESTATE, DD_ENOTCONV, DD_ETIMEOUT, DD_EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7
+DD_F_KL, DD_F_TV = 1, 2
+DD_PREC_FP32, DD_PREC_BF16X3 = 0, 1
+DD_TRACE_OK, DD_TRACE_STUCK, DD_TRACE_STEP_LIMIT, DD_TRACE_TRUNCATED = 0, 1, 2, 3
+
+STATUS_NAMES = {0: "DD_OK", -1: "DD_EINVAL", -2: "DD_ENOMEM", -3: "DD_ECUDA", -4: "DD_ESTATE",
+                -5: "DD_ENOTCONV", -6: "DD_ETIMEOUT", -7: "DD_EBUDGET"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libdd.so is not built ({LIB_PATH}); run paper_1708_02845_gb300.build.build()")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u32 = ctypes.c_uint32
+_f64 = ctypes.c_double
+
+_SIGS = {
+    "dd_version": (_i32, []),
+    "dd_create": (_i32, [ctypes.POINTER(_p), _i32, _p]),
+    "dd_set_stream": (_i32, [_p, _p]),
+    "dd_destroy": (None, [_p]),
+    "dd_last_error": (ctypes.c_char_p, [_p]),
+    "dd_sync": (_i32, [_p]),
+    "dd_check_mesh": (_i32, [_p, _i64, _p, _i64, _p, _p, _i32, _p, ctypes.c_char_p, _i32]),
+    "dd_load_mesh": (_i32, [_p, _p, _i64, _p, _i64, _p, _p, _i32, ctypes.POINTER(_i32)]),
+    "dd_unload_mesh": (_i32, [_p, _i32]),
+    "dd_mesh_info": (_i32, [_p, _i32, _p]),
+    "dd_poisson_kernel": (_i32, [_p, _i32, _f64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f64)]),
+    "dd_set_poisson_kernel": (_i32, [_p, _i32, _p]),
+    "dd_get_poisson_kernel": (_i32, [_p, _i32, _p]),
+    "dd_distance": (_i32, [_p, _i32, _p, _i32, _u32, _i32, _p]),
+    "dd_trace": (_i32, [_p, _i32, _i32, _u32, _p, _i32, _i32, _p, _p, _p]),
+    "dd_trace_fields": (_i32, [_p, _i32, _p, _p, _i32, _p, _i32, _i32, _p, _p, _p]),
+    "dd_query": (_i32, [_p, _i32, _p, _i32, _p, _i32, _u32, _i32, _u32, _i32, _p, _p, _p, _p]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class DDError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def ptr(x):
+    """Data pointer of a torch tensor, numpy array or None (must be contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _check(ctx, st):
+    if st != DD_OK:
+        msg = lib.dd_last_error(ctx).decode() if ctx else ""
+        raise DDError(st, msg)
+
+
+def _host_i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+# ---- same names as the C ABI -------------------------------------------------
+
+def dd_version() -> int:
+    return lib.dd_version()
+
+
+def dd_create(device: int = 0, stream: int = 0):
+    h = _p()
+    st = lib.dd_create(ctypes.byref(h), device, stream or None)
+    if st != DD_OK:
+        raise DDError(st, f"dd_create(device={device}) failed")
+    return h
+
+
+def dd_set_stream(ctx, stream: int):
+    _check(ctx, lib.dd_set_stream(ctx, stream or None))
+
+
+def dd_destroy(ctx):
+    lib.dd_destroy(ctx)
+
+
+def dd_last_error(ctx) -> str:
+    return lib.dd_last_error(ctx).decode()
+
+
+def dd_sync(ctx):
+    _check(ctx, lib.dd_sync(ctx))
+
+
+def dd_check_mesh(xy, tri, loop_idx, loop_off):
+    """Host-only validation; returns (n_v, k, m, n_edges) or raises DDError."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = _host_i32(tri)
+    loop_idx = _host_i32(loop_idx)
+    loop_off = np.ascontiguousarray(loop_off, dtype=np.int64)
+    info = np.zeros(4, dtype=np.int64)
+    msg = ctypes.create_string_buffer(512)
+    st = lib.dd_check_mesh(ptr(xy), xy.shape[0], ptr(tri), tri.shape[0], ptr(loop_idx), ptr(loop_off),
+                           len(loop_off) - 1, ptr(info), msg, 512)
+    if st != DD_OK:
+        raise DDError(st, msg.value.decode())
+    return tuple(int(v) for v in info)
+
+
+def dd_load_mesh(ctx, xy, tri, loop_idx, loop_off) -> int:
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = _host_i32(tri)
+    loop_idx = _host_i32(loop_idx)
+    loop_off = np.ascontiguousarray(loop_off, dtype=np.int64)
+    mid = _i32()
+    _check(ctx, lib.dd_load_mesh(ctx, ptr(xy), xy.shape[0], ptr(tri), tri.shape[0], ptr(loop_idx), ptr(loop_off),
+                                 len(loop_off) - 1, ctypes.byref(mid)))
+    return mid.value
+
+
+def dd_unload_mesh(ctx, mesh: int):
+    _check(ctx, lib.dd_unload_mesh(ctx, mesh))
+
+
+def dd_mesh_info(ctx, mesh: int) -> dict:
+    info = np.zeros(7, dtype=np.int64)
+    _check(ctx, lib.dd_mesh_info(ctx, mesh, ptr(info)))
+    keys = ("n_v", "n_t", "k", "m", "k_pad", "has_poisson_kernel", "device_bytes")
+    return {k: int(v) for k, v in zip(keys, info)}
+
+
+def dd_poisson_kernel(ctx, mesh: int, rtol: float = 1e-15, max_iter: int = 20000, allow_notconv=False):
+    iters = _i32()
+    resid = _f64()
+    st = lib.dd_poisson_kernel(ctx, mesh, rtol, max_iter, ctypes.byref(iters), ctypes.byref(resid))
+    if not (allow_notconv and st == DD_ENOTCONV):
+        _check(ctx, st)
+    return iters.value, resid.value
+
+
+def dd_set_poisson_kernel(ctx, mesh: int, P):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    _check(ctx, lib.dd_set_poisson_kernel(ctx, mesh, ptr(P)))
+
+
+def dd_get_poisson_kernel(ctx, mesh: int, out):
+    _check(ctx, lib.dd_get_poisson_kernel(ctx, mesh, ptr(out)))
+    return out
+
+
+def dd_distance(ctx, mesh: int, targets, f_mask: int, prec: int, out):
+    t = _host_i32(targets)
+    _check(ctx, lib.dd_distance(ctx, mesh, ptr(t), len(t), f_mask, prec, ptr(out)))
+    return out
+
+
+def dd_trace(ctx, mesh: int, target: int, f: int, sources, max_pts: int, out_xy, out_len, out_status):
+    s = _host_i32(sources)
+    _check(ctx, lib.dd_trace(ctx, mesh, int(target), f, ptr(s), len(s), max_pts, ptr(out_xy), ptr(out_len),
+                             ptr(out_status)))
+
+
+def dd_trace_fields(ctx, mesh: int, fields, targets, sources, max_pts: int, out_xy, out_len, out_status):
+    t = _host_i32(targets)
+    s = _host_i32(sources).reshape(len(t), -1)
+    s = np.ascontiguousarray(s)
+    _check(ctx, lib.dd_trace_fields(ctx, mesh, ptr(fields), ptr(t), len(t), ptr(s), s.shape[1], max_pts,
+                                    ptr(out_xy), ptr(out_len), ptr(out_status)))
+
+
+def dd_query(ctx, mesh: int, targets, sources, f_mask: int, prec: int, trace_f: int, max_pts: int,
+             out_fields, out_xy, out_len, out_status):
+    t = _host_i32(targets)
+    s = np.ascontiguousarray(_host_i32(sources).reshape(len(t), -1))
+    _check(ctx, lib.dd_query(ctx, mesh, ptr(t), len(t), ptr(s), s.shape[1], f_mask, prec, trace_f, max_pts,
+                             ptr(out_fields), ptr(out_xy), ptr(out_len), ptr(out_status)))

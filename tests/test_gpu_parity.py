@@ -1,0 +1,195 @@
+"""GPU parity of libdd against the FP64 oracle, through the C ABI.
+
+Tolerances: Poisson kernel entries within the FP32 rounding of the oracle's
+value plus 1e-12 (solver); fields |g - r| / max(|r|, 1e-2) <= 1e-5 (FP32
+path) with D(t, t) = 0 exactly; traced paths within half a mean edge length
+(Hausdorff) of the oracle's paths with identical status codes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.divergence import kl_field_fast, tv_field
+from oracle.hausdorff import hausdorff
+from oracle.poisson import PoissonOracle
+from oracle.trace import Tracer
+from synthetic import workloads
+from synthetic.meshes import grid_obstacles
+from tests._gpu import TOL_FP32, ctx_and_lib, field_error, load, mean_edge
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dd, ctx = ctx_and_lib()
+    yield dd, ctx
+    dd.dd_destroy(ctx)
+
+
+CASES = {
+    "disk": lambda: workloads.disk(),
+    "grid24": lambda: workloads.small_grid(24, 2, T=5, S=8),
+    "grid37": lambda: workloads.small_grid(37, 3, T=70, S=4, seed=777),
+    "grid140": lambda: workloads.grid140(T=8, S=32),
+}
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        wl = CASES[name]()
+        po = PoissonOracle(wl.mesh.xy, wl.mesh.tri, wl.mesh.loops)
+        _cache[name] = (wl, po, po.full())
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_poisson_kernel_matches_oracle(env, name):
+    dd, ctx = env
+    wl, po, P = case(name)
+    mid = load(dd, ctx, wl.mesh)
+    iters, resid = dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
+    assert resid <= 1e-15
+    got = np.empty((wl.mesh.n_v, po.k), dtype=np.float32)
+    dd.dd_get_poisson_kernel(ctx, mid, got)
+    ref32 = np.where(P < np.finfo(np.float32).tiny, 0.0, P)
+    err = np.abs(got.astype(np.float64) - ref32)
+    assert np.all(err <= 1.2e-7 * np.abs(ref32) + 1e-12), float((err - 1.2e-7 * np.abs(ref32)).max())
+    assert np.abs(got.astype(np.float64).sum(axis=1) - 1.0).max() < 1e-5
+    dd.dd_unload_mesh(ctx, mid)
+
+
+def _fields(dd, ctx, mid, n_v, targets, host=False):
+    T = len(targets)
+    if host:
+        out = np.empty((2, T, n_v), dtype=np.float32)
+        dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, out)
+        return out
+    out = torch.empty((2, T, n_v), dtype=torch.float32, device="cuda")
+    dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, out)
+    dd.dd_sync(ctx)
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,T", [("disk", 1), ("grid24", 1), ("grid24", 2), ("grid24", 5),
+                                    ("grid37", 3), ("grid37", 70), ("grid140", 8)])
+def test_fields_on_oracle_kernel(env, name, T):
+    """Field kernels alone: the oracle's P installed, fields vs the oracle's fields."""
+    dd, ctx = env
+    wl, po, P = case(name)
+    targets = list(wl.targets[:T]) if len(wl.targets) >= T else [int(po.I[(i * 7919) % po.m]) for i in range(T)]
+    mid = load(dd, ctx, wl.mesh)
+    dd.dd_set_poisson_kernel(ctx, mid, P)
+    got = _fields(dd, ctx, mid, wl.mesh.n_v, targets)
+    for a, t in enumerate(targets):
+        ref_kl = kl_field_fast(P, P[t])
+        ref_tv = tv_field(P, P[t])
+        assert field_error(got[0, a], ref_kl) <= TOL_FP32
+        assert field_error(got[1, a], ref_tv) <= TOL_FP32
+        assert got[0, a, t] == 0.0 and got[1, a, t] == 0.0
+        inf = ~np.isfinite(ref_kl)
+        assert np.all(got[0, a][inf] >= 87.0)            # +inf rows: log argument clamped at FLT_MIN
+        assert np.all(np.isfinite(got[:, a]))
+    dd.dd_unload_mesh(ctx, mid)
+
+
+@pytest.mark.parametrize("name", ["disk", "grid24", "grid140"])
+def test_end_to_end_fields(env, name):
+    """Poisson kernel by the device solver, then fields, vs the oracle."""
+    dd, ctx = env
+    wl, po, P = case(name)
+    mid = load(dd, ctx, wl.mesh)
+    dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
+    targets = list(wl.targets[:4])
+    got = _fields(dd, ctx, mid, wl.mesh.n_v, targets, host=True)
+    for a, t in enumerate(targets):
+        assert field_error(got[0, a], kl_field_fast(P, P[t])) <= TOL_FP32
+        assert field_error(got[1, a], tv_field(P, P[t])) <= TOL_FP32
+    dd.dd_unload_mesh(ctx, mid)
+
+
+@pytest.mark.parametrize("name,f", [("disk", "kl"), ("disk", "tv"), ("grid140", "kl"), ("grid24", "kl")])
+def test_trace_parity(env, name, f):
+    dd, ctx = env
+    wl, po, P = case(name)
+    mesh = wl.mesh
+    mid = load(dd, ctx, mesh)
+    dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
+    tr = Tracer(mesh.xy, mesh.tri)
+    h = mean_edge(mesh)
+    fbit = dd.DD_F_KL if f == "kl" else dd.DD_F_TV
+    n_t = min(len(wl.targets), 2)
+    for a in range(n_t):
+        t = int(wl.targets[a])
+        srcs = wl.sources[a]
+        S, max_pts = len(srcs), 4096
+        xy = np.zeros((S, max_pts, 2), dtype=np.float32)
+        ln = np.zeros(S, dtype=np.int32)
+        st = np.zeros(S, dtype=np.int32)
+        dd.dd_trace(ctx, mid, t, fbit, srcs, max_pts, xy, ln, st)
+        ref = kl_field_fast(P, P[t]) if f == "kl" else tv_field(P, P[t])
+        for s, q in enumerate(srcs):
+            path, status = tr.trace(ref, int(q), t, max_pts=max_pts)
+            assert st[s] == status, (t, int(q), st[s], status)
+            assert np.allclose(xy[s, 0], mesh.xy[q], atol=1e-6)
+            if status == 0:
+                assert np.allclose(xy[s, ln[s] - 1], mesh.xy[t], atol=1e-6)
+            assert hausdorff(xy[s, :ln[s]], path, h / 10) <= 0.5 * h
+    dd.dd_unload_mesh(ctx, mid)
+
+
+def test_query_host_equals_device(env):
+    dd, ctx = env
+    wl, po, P = case("grid24")
+    mesh = wl.mesh
+    mid = load(dd, ctx, mesh)
+    dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
+    T, S, mp = len(wl.targets), wl.sources.shape[1], 512
+    hf = np.zeros((2, T, mesh.n_v), np.float32)
+    hxy = np.zeros((T * S, mp, 2), np.float32)
+    hl = np.zeros(T * S, np.int32)
+    hs = np.zeros(T * S, np.int32)
+    dd.dd_query(ctx, mid, wl.targets, wl.sources, 3, 0, dd.DD_F_KL, mp, hf, hxy, hl, hs)
+    df = torch.zeros((2, T, mesh.n_v), dtype=torch.float32, device="cuda")
+    dxy = torch.zeros((T * S, mp, 2), dtype=torch.float32, device="cuda")
+    dl = torch.zeros(T * S, dtype=torch.int32, device="cuda")
+    ds = torch.zeros(T * S, dtype=torch.int32, device="cuda")
+    dd.dd_query(ctx, mid, wl.targets, wl.sources, 3, 0, dd.DD_F_KL, mp, df, dxy, dl, ds)
+    dd.dd_sync(ctx)
+    assert np.array_equal(hf, df.cpu().numpy())
+    assert np.array_equal(hl, dl.cpu().numpy()) and np.array_equal(hs, ds.cpu().numpy())
+    for i in range(T * S):
+        assert np.array_equal(hxy[i, :hl[i]], dxy[i, :hl[i]].cpu().numpy())
+    dd.dd_unload_mesh(ctx, mid)
+
+
+def test_errors(env):
+    dd, ctx = env
+    wl, po, P = case("grid24")
+    mesh = wl.mesh
+    mid = load(dd, ctx, mesh)
+    out = torch.empty((1, 1, mesh.n_v), dtype=torch.float32, device="cuda")
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_distance(ctx, mid, [int(wl.targets[0])], dd.DD_F_KL, 0, out)
+    assert e.value.status == dd.DD_ESTATE
+    dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_distance(ctx, mid, [int(po.B[0])], dd.DD_F_KL, 0, out)
+    assert e.value.status == dd.DD_EINVAL
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_distance(ctx, mid, [int(wl.targets[0])], 4, 0, out)
+    assert e.value.status == dd.DD_EINVAL
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_distance(ctx, 99, [int(wl.targets[0])], 1, 0, out)
+    assert e.value.status == dd.DD_EINVAL
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_poisson_kernel(ctx, mid, 1e-30, 3)
+    assert e.value.status == dd.DD_ENOTCONV
+    dd.dd_unload_mesh(ctx, mid)

@@ -1,0 +1,40 @@
+"""The C-ABI library loads without a GPU and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1708_02845_gb300.build import build
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dd_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("dd_create", "dd_destroy", "dd_load_mesh", "dd_poisson_kernel", "dd_distance", "dd_trace",
+              "dd_trace_fields", "dd_query", "dd_last_error", "dd_check_mesh"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header():
+    from paper_1708_02845_gb300 import dd
+    for n in declared_functions():
+        assert hasattr(dd, n), n
+    assert dd.dd_version() == 100
