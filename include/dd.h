@@ -200,6 +200,30 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
                    uint32_t trace_f, int32_t max_pts, float *out_fields,
                    float *out_xy, int32_t *out_len, int32_t *out_status);
 
+/* dd_distance without any device allocation.  The paper has no counterpart:
+ * this is a deployment variant of dd_distance for callers that may not call
+ * cudaMalloc -- e.g. a robot's real-time control loop that allocates only at
+ * start-up, because an allocation can stall the device and overrun the
+ * loop's deadline, or a plugin whose host framework owns all device memory.
+ * The caller passes everything in its own device memory; no context is used.
+ *   P        device float32 [n_v][k_pad] Poisson kernel (e.g. copied from
+ *            dd_get_poisson_kernel and padded), k_pad a multiple of 4 with
+ *            zero padding columns, 16-byte aligned
+ *   targets  device int32 [T] interior vertex ids (not checked)
+ *   f_mask   DD_F_KL | DD_F_TV as in dd_distance
+ *   out      device float32 [nf][T][n_v], layout as in dd_distance
+ *   cuda_stream  stream for the work (NULL = legacy default stream)
+ * Scratch: one fixed device array per GPU (12 MiB, held until the process
+ * exits) holds the staged target rows, so T * k_pad must not exceed 1,048,576
+ * (DD_EINVAL otherwise).  Every call shares that array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  The call
+ * returns after the work finished (it synchronises the stream).
+ * Errors: DD_EINVAL, DD_ECUDA, DD_ETIMEOUT (a bounded device wait gave up). */
+dd_status dd_distance_noalloc(const float *P, int64_t n_v, int64_t k_pad, const int32_t *targets,
+                              int32_t T, uint32_t f_mask, float *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,7 @@ _SIGS = {
     "dd_trace": (_i32, [_p, _i32, _i32, _u32, _p, _i32, _i32, _p, _p, _p]),
     "dd_trace_fields": (_i32, [_p, _i32, _p, _p, _i32, _p, _i32, _i32, _p, _p, _p]),
     "dd_query": (_i32, [_p, _i32, _p, _i32, _p, _i32, _u32, _i32, _u32, _i32, _p, _p, _p, _p]),
+    "dd_distance_noalloc": (_i32, [_p, _i64, _i64, _p, _i32, _u32, _p, _p]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -202,3 +203,11 @@ def dd_query(ctx, mesh: int, targets, sources, f_mask: int, prec: int, trace_f: 
     s = np.ascontiguousarray(_host_i32(sources).reshape(len(t), -1))
     _check(ctx, lib.dd_query(ctx, mesh, ptr(t), len(t), ptr(s), s.shape[1], f_mask, prec, trace_f, max_pts,
                              ptr(out_fields), ptr(out_xy), ptr(out_len), ptr(out_status)))
+
+
+def dd_distance_noalloc(P, n_v: int, k_pad: int, targets, T: int, f_mask: int, out, stream: int = 0):
+    """Fields without device allocation: P, targets and out are device buffers."""
+    st = lib.dd_distance_noalloc(ptr(P), n_v, k_pad, ptr(targets), T, f_mask, ptr(out), stream or None)
+    if st != DD_OK:
+        raise DDError(st, "dd_distance_noalloc failed")
+    return out
