@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 
 METRIC = "distance fields/s (KL+TV, one target over all vertices) with traced paths"
 UNIT = "fields/s"
-T_BATCH, S_PER_TARGET, MAX_PTS = 64, 256, 512
+T_BATCH, S_PER_TARGET, MAX_PTS = 64, 256, 1024
 N_BATCHES = 8
 
 
@@ -241,8 +241,49 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
+    if args.stream:
+        line["stream"] = stream_roofline(dd, ctx, dev, stream, flush, pk, pk_kind, clocks)
     dd.dd_destroy(ctx)
     return line
+
+
+def stream_roofline(dd, ctx, dev, stream, flush, pk, pk_kind, clocks, reps: int = 10):
+    """Single-target KL+TV sweeps over the grid450 Poisson kernel (3.0 GB, far above L2).
+
+    The streaming kernel reads P once per target; achieved GB/s = 4 n k_pad
+    bytes / event-timed duration of dd_distance (stage + stream kernels)."""
+    import torch
+    from synthetic import workloads
+    wl = workloads.grid450(T=reps)
+    idx, off = wl.mesh.loop_arrays()
+    mid = dd.dd_load_mesh(ctx, wl.mesh.xy, wl.mesh.tri, idx, off)
+    t0 = time.perf_counter()
+    iters, resid = dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+    pre = time.perf_counter() - t0
+    info = dd.dd_mesh_info(ctx, mid)
+    n_v, k_pad = info["n_v"], info["k_pad"]
+    out = torch.empty((2, 1, n_v), dtype=torch.float32, device=dev)
+    for t in wl.targets[:3]:
+        dd.dd_distance(ctx, mid, [int(t)], 3, 0, out)
+    ms = []
+    for t in wl.targets:
+        flush.fill_(0.5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dd.dd_distance(ctx, mid, [int(t)], 3, 0, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    med = statistics.median(ms)
+    nbytes = 4.0 * n_v * k_pad + 2 * 4.0 * n_v
+    achieved = nbytes / (med / 1e3) / 1e9
+    dd.dd_unload_mesh(ctx, mid)
+    return {"workload": "grid450 single target: n=%d, k_pad=%d, P=%.2f GB FP32" % (n_v, k_pad, 4.0 * n_v * k_pad / 1e9),
+            "kernel": "field_stream_kernel (+ stage_targets_kernel)", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+            "frac": round(achieved / pk.get("hbm_gbs", 6672.5), 4), "peak_source": pk_kind,
+            "ms_per_field_pair": round(med, 4), "fields_per_s": round(2 / (med / 1e3), 1), "traffic": None,
+            "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(pre, 2)}}
 
 
 class OracleStep:
@@ -292,6 +333,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stream", dest="stream", action="store_false",
+                    help="skip the grid450 single-target HBM-stream measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

@@ -12,7 +12,7 @@
 
 namespace {
 
-enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_COUNT };
+enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_COUNT };
 
 struct MeshSlot {
     bool live = false;
@@ -293,10 +293,22 @@ dd_status dd_load_mesh(dd_ctx *ctx, const double *xy, int64_t n_v, const int32_t
             nbr4[t] = make_int4(h.tnbr[3 * t], h.tnbr[3 * t + 1], h.tnbr[3 * t + 2], 0);
         }
         std::vector<float4> g4(2 * h.n_t);
+        std::vector<int4> rec(4 * h.n_t);
+        auto fbits = [](float x) {
+            int i;
+            std::memcpy(&i, &x, sizeof i);
+            return i;
+        };
         for (int64_t t = 0; t < h.n_t; ++t) {
             const float *g = &h.gphi[6 * t];
             g4[2 * t] = make_float4(g[0], g[1], g[2], g[3]);
             g4[2 * t + 1] = make_float4(g[4], g[5], 0.f, 0.f);
+            const int32_t *v = &h.tri[3 * t], *nb = &h.tnbr[3 * t];
+            const float2 p0 = xyf[v[0]], p1 = xyf[v[1]], p2 = xyf[v[2]];
+            rec[4 * t] = make_int4(v[0], v[1], v[2], nb[0]);
+            rec[4 * t + 1] = make_int4(nb[1], nb[2], fbits(g[0]), fbits(g[1]));
+            rec[4 * t + 2] = make_int4(fbits(g[2]), fbits(g[3]), fbits(p0.x), fbits(p0.y));
+            rec[4 * t + 3] = make_int4(fbits(p1.x), fbits(p1.y), fbits(p2.x), fbits(p2.y));
         }
         auto undo = [&](dd_status s2) {
             free_mesh(m);
@@ -306,6 +318,7 @@ dd_status dd_load_mesh(dd_ctx *ctx, const double *xy, int64_t n_v, const int32_t
         if ((st = dev_copy(ctx, m, &m.tri, tri4.data(), tri4.size())) != DD_OK) return undo(st);
         if ((st = dev_copy(ctx, m, &m.tnbr, nbr4.data(), nbr4.size())) != DD_OK) return undo(st);
         if ((st = dev_copy(ctx, m, &m.gphi, g4.data(), g4.size())) != DD_OK) return undo(st);
+        if ((st = dev_copy(ctx, m, &m.trec, rec.data(), rec.size())) != DD_OK) return undo(st);
         if ((st = dev_copy(ctx, m, &m.vt_off, h.vt_off.data(), h.vt_off.size())) != DD_OK) return undo(st);
         if ((st = dev_copy(ctx, m, &m.vt, h.vt.data(), h.vt.size())) != DD_OK) return undo(st);
         if ((st = dev_copy(ctx, m, &m.vn_off, h.vn_off.data(), h.vn_off.size())) != DD_OK) return undo(st);
@@ -470,9 +483,10 @@ dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32
         if ((st = ensure_scratch(ctx, S_STATUS, n * sizeof(int32_t))) != DD_OK) return st;
         dst = reinterpret_cast<int32_t *>(ctx->scratch[S_STATUS]);
     }
+    if ((st = ensure_scratch(ctx, S_GRAD, (size_t)T * m.n_t * sizeof(float2))) != DD_OK) return st;
     launch_trace(m, d_fields, m.n_v, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
                  reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), T, S, max_pts, dxy, dlen, dst,
-                 ctx->stream);
+                 reinterpret_cast<float2 *>(ctx->scratch[S_GRAD]), ctx->stream);
     CK(cudaGetLastError(), "trace kernel launch");
     bool host = false;
     if (sx == 0) {

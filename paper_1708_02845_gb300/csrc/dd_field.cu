@@ -31,20 +31,85 @@ namespace {
 
 constexpr float kLn2 = 0.693147180559945309f;
 
+// ---- packed FP32x2 helpers (two IEEE round-to-nearest operations per instruction)
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t pk(float a, float b) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2_t r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+constexpr float kC3 = 2.0f / 3.0f, kC5 = 2.0f / 5.0f, kC7 = 2.0f / 7.0f, kC9 = 2.0f / 9.0f;
+constexpr int kMagicE = 0x4B400000;              // float 12582912 = 1.5 * 2^23: + e keeps e exact
+constexpr float kMagicEf = 12582912.0f;
+
+// split logarithm of max(p, FLT_MIN): log = E ln2 + lm.  The reciprocal is a
+// hardware approximation refined by one Newton step; every other step is an
+// IEEE round-to-nearest operation, and split_log2 below performs the same
+// operations lane by lane, so both give bit-identical results.
 __device__ __forceinline__ void split_log(float p, float &lm, float &E) {
     p = fmaxf(p, FLT_MIN);
     const int i = __float_as_int(p);
     const int e = (i - 0x3f3504f3) >> 23;            // m = p 2^-e in [1/sqrt2, sqrt2)
     const float m = __int_as_float(i - (e << 23));
-    const float u = __fsub_rn(m, 1.0f);               // exact (Sterbenz)
+    E = __fadd_rn(__int_as_float(e + kMagicE), -kMagicEf);
+    const float u = __fadd_rn(m, -1.0f);              // exact (Sterbenz)
     const float v = __fadd_rn(m, 1.0f);
-    const float s = __fmul_rn(u, __frcp_rn(v));
+    float r = rcp_approx(v);
+    const float er = __fmaf_rn(__fmaf_rn(m, -1.0f, -1.0f), r, 1.0f);
+    r = __fmaf_rn(r, er, r);
+    const float s = __fmul_rn(u, r);
     const float z = __fmul_rn(s, s);
-    float q = __fmaf_rn(z, 2.0f / 9.0f, 2.0f / 7.0f);
-    q = __fmaf_rn(q, z, 2.0f / 5.0f);
-    q = __fmaf_rn(q, z, 2.0f / 3.0f);
+    float q = __fmaf_rn(z, kC9, kC7);
+    q = __fmaf_rn(q, z, kC5);
+    q = __fmaf_rn(q, z, kC3);
     lm = __fmaf_rn(__fmul_rn(s, z), q, __fadd_rn(s, s));
-    E = (float)e;
+}
+
+// the same for two values at once (packed lanes)
+__device__ __forceinline__ void split_log2(float p0, float p1, f2_t &lm, f2_t &E) {
+    p0 = fmaxf(p0, FLT_MIN);
+    p1 = fmaxf(p1, FLT_MIN);
+    const int i0 = __float_as_int(p0), i1 = __float_as_int(p1);
+    const int e0 = (i0 - 0x3f3504f3) >> 23, e1 = (i1 - 0x3f3504f3) >> 23;
+    const f2_t m = pk(__int_as_float(i0 - (e0 << 23)), __int_as_float(i1 - (e1 << 23)));
+    const f2_t one = pk(1.0f, 1.0f), mone = pk(-1.0f, -1.0f);
+    E = add2(pk(__int_as_float(e0 + kMagicE), __int_as_float(e1 + kMagicE)), pk(-kMagicEf, -kMagicEf));
+    const f2_t u = add2(m, mone);
+    const f2_t v = add2(m, one);
+    float v0, v1;
+    upk(v, v0, v1);
+    f2_t r = pk(rcp_approx(v0), rcp_approx(v1));
+    const f2_t er = fma2(fma2(m, mone, mone), r, one);
+    r = fma2(r, er, r);
+    const f2_t sv = mul2(u, r);
+    const f2_t z = mul2(sv, sv);
+    f2_t q = fma2(z, pk(kC9, kC9), pk(kC7, kC7));
+    q = fma2(q, z, pk(kC5, kC5));
+    q = fma2(q, z, pk(kC3, kC3));
+    lm = fma2(mul2(sv, z), q, add2(sv, sv));
 }
 
 // one term of each sum; accumulators updated in place
@@ -55,6 +120,18 @@ __device__ __forceinline__ void accumulate(float px, float lmx, float ex, float 
     const float lr = __fmaf_rn(de, kLn2, d);          // log(P_x / P_t)
     kl = __fmaf_rn(px, lr, kl);
     tv = __fadd_rn(tv, fabsf(__fadd_rn(px, -pt)));
+}
+
+// packed: two (x, b) terms against the matching target entries
+__device__ __forceinline__ void accumulate2(f2_t px, f2_t lmx, f2_t ex, f2_t pt, f2_t lmt, f2_t et, f2_t &kl,
+                                            f2_t &tv) {
+    const f2_t mone = pk(-1.0f, -1.0f);
+    const f2_t d = fma2(lmt, mone, lmx);
+    const f2_t de = fma2(et, mone, ex);
+    const f2_t lr = fma2(de, pk(kLn2, kLn2), d);
+    kl = fma2(px, lr, kl);
+    const f2_t dp = fma2(pt, mone, px);
+    tv = add2(tv, dp & 0x7fffffff7fffffffULL);
 }
 
 // stage_P / stage_L / stage_E: [T][k_pad] target row, its mantissa log and exponent
@@ -155,56 +232,74 @@ __global__ void __launch_bounds__(256) field_stream_kernel(const float *__restri
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nvec = k_pad >> 2;          // float4 per row
-    for (int64_t x = warp; x < n_v; x += nwarps) {
+    const int64_t nvec = k_pad >> 2;                       // float4 per row
+    constexpr int U = 4;                                   // float4 per lane per chunk
+    const int64_t nchunk = (nvec + 32 * U - 1) / (32 * U);
+    // software pipeline over (row, chunk): the loads of the next chunk are in
+    // flight while the current one is computed
+    float4 nxt[U];
+    auto fetch = [&](int64_t x, int64_t ch) {
         const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
-        float kl[TT], tv[TT];
 #pragma unroll
-        for (int j = 0; j < TT; ++j) kl[j] = tv[j] = 0.0f;
-        for (int64_t c0 = 0; c0 < nvec; c0 += 4 * 32) {
-            float4 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t c = c0 + u * 32 + lane;
-                v[u] = c < nvec ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t c = c0 + u * 32 + lane;
-                if (c >= nvec) continue;
-                const float px[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-                float lmx[4], ex[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) split_log(px[e], lmx[e], ex[e]);
-#pragma unroll
-                for (int j = 0; j < TT; ++j) {
-                    if (j >= nt) break;
-                    const float4 p4 = reinterpret_cast<const float4 *>(tP + j * k_pad)[c];
-                    const float4 l4 = reinterpret_cast<const float4 *>(tL + j * k_pad)[c];
-                    const float4 e4 = reinterpret_cast<const float4 *>(tE + j * k_pad)[c];
-                    accumulate(px[0], lmx[0], ex[0], p4.x, l4.x, e4.x, kl[j], tv[j]);
-                    accumulate(px[1], lmx[1], ex[1], p4.y, l4.y, e4.y, kl[j], tv[j]);
-                    accumulate(px[2], lmx[2], ex[2], p4.z, l4.z, e4.z, kl[j], tv[j]);
-                    accumulate(px[3], lmx[3], ex[3], p4.w, l4.w, e4.w, kl[j], tv[j]);
-                }
-            }
+        for (int u = 0; u < U; ++u) {
+            const int64_t c = ch * 32 * U + u * 32 + lane;
+            nxt[u] = c < nvec ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+    };
+    int64_t x = warp, ch = 0;
+    if (x < n_v) fetch(x, 0);
+    f2_t kl[TT], tv[TT];
 #pragma unroll
-        for (int j = 0; j < TT; ++j) {
+    for (int j = 0; j < TT; ++j) kl[j] = tv[j] = 0ULL;
+    while (x < n_v) {
+        float4 cur[U];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                kl[j] += __shfl_xor_sync(0xffffffffu, kl[j], o);
-                tv[j] += __shfl_xor_sync(0xffffffffu, tv[j], o);
-            }
+        for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+        int64_t xn = x, chn = ch + 1;
+        if (chn == nchunk) {
+            chn = 0;
+            xn += nwarps;
         }
-        if (lane == 0) {
+        if (xn < n_v) fetch(xn, chn);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t c = ch * 32 * U + u * 32 + lane;
+            if (c >= nvec) continue;
+            f2_t lm01, e01, lm23, e23;
+            split_log2(cur[u].x, cur[u].y, lm01, e01);
+            split_log2(cur[u].z, cur[u].w, lm23, e23);
+            const f2_t p01 = pk(cur[u].x, cur[u].y), p23 = pk(cur[u].z, cur[u].w);
 #pragma unroll
             for (int j = 0; j < TT; ++j) {
                 if (j >= nt) break;
-                if (out_kl) out_kl[(int64_t)(a0 + j) * n_v + x] = kl[j];
-                if (out_tv) out_tv[(int64_t)(a0 + j) * n_v + x] = tv[j];
+                const float4 p4 = reinterpret_cast<const float4 *>(tP + j * k_pad)[c];
+                const float4 l4 = reinterpret_cast<const float4 *>(tL + j * k_pad)[c];
+                const float4 e4 = reinterpret_cast<const float4 *>(tE + j * k_pad)[c];
+                accumulate2(p01, lm01, e01, pk(p4.x, p4.y), pk(l4.x, l4.y), pk(e4.x, e4.y), kl[j], tv[j]);
+                accumulate2(p23, lm23, e23, pk(p4.z, p4.w), pk(l4.z, l4.w), pk(e4.z, e4.w), kl[j], tv[j]);
             }
         }
+        if (ch == nchunk - 1) {
+#pragma unroll
+            for (int j = 0; j < TT; ++j) {
+                float k0, k1, t0v, t1v;
+                upk(kl[j], k0, k1);
+                upk(tv[j], t0v, t1v);
+                float skl = k0 + k1, stv = t0v + t1v;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    skl += __shfl_xor_sync(0xffffffffu, skl, o);
+                    stv += __shfl_xor_sync(0xffffffffu, stv, o);
+                }
+                if (lane == 0 && j < nt) {
+                    if (out_kl) out_kl[(int64_t)(a0 + j) * n_v + x] = skl;
+                    if (out_tv) out_tv[(int64_t)(a0 + j) * n_v + x] = stv;
+                }
+                kl[j] = tv[j] = 0ULL;
+            }
+        }
+        x = xn;
+        ch = chn;
     }
 }
 

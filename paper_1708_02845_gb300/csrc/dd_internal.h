@@ -46,6 +46,7 @@ struct DevMesh {
     int4 *tri = nullptr;       // [n_t] (v0, v1, v2, 0)
     int4 *tnbr = nullptr;      // [n_t] (t0, t1, t2, 0)
     float4 *gphi = nullptr;    // [n_t][2]: (g0x, g0y, g1x, g1y), (g2x, g2y, 0, 0)
+    int4 *trec = nullptr;      // [n_t][4] tracer records: (v0,v1,v2,n0) (n1,n2,g0x,g0y) (g1x,g1y,p0x,p0y) (p1x,p1y,p2x,p2y)
     int32_t *vt_off = nullptr, *vt = nullptr;
     int32_t *vn_off = nullptr, *vn = nullptr;
     int32_t *interior = nullptr;   // [m]
@@ -78,10 +79,10 @@ void launch_stage_targets(const float *P, int64_t k_pad, int64_t k, const int32_
 // FP32 fields.  out_kl / out_tv: [T][n_v] (either may be null).
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T,
                         float *out_kl, float *out_tv, int *err_flag, cudaStream_t s);
-// Tracer: T*S paths.
+// Tracer: per-field triangle gradients into grads [T][n_t], then T*S paths.
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,
                   const int32_t *sources, int32_t T, int32_t S, int32_t max_pts, float2 *out_xy,
-                  int32_t *out_len, int32_t *out_status, cudaStream_t s);
+                  int32_t *out_len, int32_t *out_status, float2 *grads, cudaStream_t s);
 
 #define DD_CUDA_TRY(expr, errstr)                                                   \
     do {                                                                            \

@@ -19,7 +19,6 @@
 
 namespace {
 
-constexpr int kRowsPerBlock = 256;   // rows of one CTA in the row-block kernels
 constexpr int kColsPerBlock = 128;   // columns (threads) of one CTA
 
 struct Work {
@@ -35,11 +34,11 @@ struct Work {
 __global__ void spmm_dot_kernel(int64_t m, int64_t kc, const int64_t *__restrict__ a_off,
                                 const int32_t *__restrict__ a_col, const double *__restrict__ a_val,
                                 const double *__restrict__ Pd, double *__restrict__ AP,
-                                double *__restrict__ part) {
+                                double *__restrict__ part, int rpb) {
     const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
     if (c >= kc) return;
-    const int64_t r0 = (int64_t)blockIdx.x * kRowsPerBlock;
-    const int64_t r1 = r0 + kRowsPerBlock < m ? r0 + kRowsPerBlock : m;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
     double acc = 0.0;
     for (int64_t r = r0; r < r1; ++r) {
         double s = 0.0;
@@ -55,11 +54,11 @@ __global__ void update_xr_kernel(int64_t m, int64_t kc, const double *__restrict
                                  const double *__restrict__ dinv, double *__restrict__ X,
                                  double *__restrict__ R, const double *__restrict__ Pd,
                                  const double *__restrict__ AP, double *__restrict__ part_rz,
-                                 double *__restrict__ part_rr) {
+                                 double *__restrict__ part_rr, int rpb) {
     const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
     if (c >= kc) return;
-    const int64_t r0 = (int64_t)blockIdx.x * kRowsPerBlock;
-    const int64_t r1 = r0 + kRowsPerBlock < m ? r0 + kRowsPerBlock : m;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
     const double a = alpha[c];
     double srz = 0.0, srr = 0.0;
     for (int64_t r = r0; r < r1; ++r) {
@@ -80,11 +79,11 @@ __global__ void update_xr_kernel(int64_t m, int64_t kc, const double *__restrict
 // Pd = D^-1 R + beta Pd
 __global__ void update_p_kernel(int64_t m, int64_t kc, const double *__restrict__ beta,
                                 const double *__restrict__ dinv, const double *__restrict__ R,
-                                double *__restrict__ Pd) {
+                                double *__restrict__ Pd, int rpb) {
     const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
     if (c >= kc) return;
-    const int64_t r0 = (int64_t)blockIdx.x * kRowsPerBlock;
-    const int64_t r1 = r0 + kRowsPerBlock < m ? r0 + kRowsPerBlock : m;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
     const double b = beta[c];
     for (int64_t r = r0; r < r1; ++r) {
         const int64_t i = r * kc + c;
@@ -155,11 +154,11 @@ __global__ void dinv_kernel(int64_t m, const double *__restrict__ diag, double *
 // initial Pd = Z = D^-1 R and per-column partials of R.Z and R.R
 __global__ void init_p_kernel(int64_t m, int64_t kc, const double *__restrict__ dinv,
                               const double *__restrict__ R, double *__restrict__ Pd,
-                              double *__restrict__ part_rz, double *__restrict__ part_rr) {
+                              double *__restrict__ part_rz, double *__restrict__ part_rr, int rpb) {
     const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
     if (c >= kc) return;
-    const int64_t r0 = (int64_t)blockIdx.x * kRowsPerBlock;
-    const int64_t r1 = r0 + kRowsPerBlock < m ? r0 + kRowsPerBlock : m;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
     double srz = 0.0, srr = 0.0;
     for (int64_t r = r0; r < r1; ++r) {
         const int64_t i = r * kc + c;
@@ -189,11 +188,11 @@ __global__ void init_scalars_kernel(int64_t nrb, int64_t kc, const double *__res
 // P[I[r], c0 + c] = X[r, c] as FP32, negatives clamped to 0 and values below FLT_MIN flushed
 __global__ void pack_chunk_kernel(int64_t m, int64_t ncols, int64_t ld, int64_t c0, int64_t k_pad,
                                   const int32_t *__restrict__ interior, const double *__restrict__ X,
-                                  float *__restrict__ P) {
+                                  float *__restrict__ P, int rpb) {
     const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
     if (c >= ncols) return;
-    const int64_t r0 = (int64_t)blockIdx.x * kRowsPerBlock;
-    const int64_t r1 = r0 + kRowsPerBlock < m ? r0 + kRowsPerBlock : m;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
     for (int64_t r = r0; r < r1; ++r) {
         double v = X[r * ld + c];
         float f = v < (double)FLT_MIN ? 0.0f : (float)v;
@@ -253,7 +252,18 @@ dd_status run_pcg(DevMesh &M, double rtol, int32_t max_iter, cudaStream_t s, int
     Work w;
     w.m = m;
     w.kc = kc;
-    w.nrb = (m + kRowsPerBlock - 1) / kRowsPerBlock;
+    // rows per CTA: enough CTAs (about 16 per SM) for small meshes, 256 rows for large ones
+    int rpb = 256;
+    {
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+        const int64_t colblocks = (kc + kColsPerBlock - 1) / kColsPerBlock;
+        const int64_t want = m * colblocks / (16LL * sms);
+        while (rpb > 8 && rpb > want) rpb >>= 1;
+    }
+    w.nrb = (m + rpb - 1) / rpb;
     std::vector<void *> tmp;
     cudaError_t ce = cudaSuccess;
     size_t vec = (size_t)m * kc;
@@ -295,19 +305,19 @@ dd_status run_pcg(DevMesh &M, double rtol, int32_t max_iter, cudaStream_t s, int
         if (M.n_rb > 0)
             scatter_rhs_kernel<<<(unsigned)((M.n_rb + 255) / 256), 256, 0, s>>>(M.n_rb, M.rb_row, M.rb_col,
                                                                                 M.rb_val, c0, kcur, kc, w.R);
-        init_p_kernel<<<g2, kColsPerBlock, 0, s>>>(m, kc, w.dinv, w.R, w.Pd, w.part0, w.part1);
+        init_p_kernel<<<g2, kColsPerBlock, 0, s>>>(m, kc, w.dinv, w.R, w.Pd, w.part0, w.part1, rpb);
         init_scalars_kernel<<<gc, bc, 0, s>>>(w.nrb, kc, w.part0, w.part1, w.rz, w.bnorm, w.done);
         int32_t it = 0;
         double res = 1.0;
         for (it = 1; it <= max_iter; ++it) {
-            spmm_dot_kernel<<<g2, kColsPerBlock, 0, s>>>(m, kc, M.a_off, M.a_col, M.a_val, w.Pd, w.AP, w.part0);
+            spmm_dot_kernel<<<g2, kColsPerBlock, 0, s>>>(m, kc, M.a_off, M.a_col, M.a_val, w.Pd, w.AP, w.part0, rpb);
             alpha_kernel<<<gc, bc, 0, s>>>(w.nrb, kc, w.part0, w.rz, w.done, w.alpha);
             update_xr_kernel<<<g2, kColsPerBlock, 0, s>>>(m, kc, w.alpha, w.dinv, w.X, w.R, w.Pd, w.AP, w.part0,
-                                                          w.part1);
+                                                          w.part1, rpb);
             cudaMemsetAsync(w.maxres, 0, sizeof(unsigned long long), s);
             beta_kernel<<<gc, bc, 0, s>>>(w.nrb, kc, w.part0, w.part1, w.bnorm, w.rz, w.done, w.beta,
                                           w.maxres);
-            update_p_kernel<<<g2, kColsPerBlock, 0, s>>>(m, kc, w.beta, w.dinv, w.R, w.Pd);
+            update_p_kernel<<<g2, kColsPerBlock, 0, s>>>(m, kc, w.beta, w.dinv, w.R, w.Pd, rpb);
             if (it % check_every == 0 || it == max_iter) {
                 unsigned long long bits = 0;
                 cudaError_t e1 = cudaMemcpyAsync(&bits, w.maxres, sizeof bits, cudaMemcpyDeviceToHost, s);
@@ -330,7 +340,7 @@ dd_status run_pcg(DevMesh &M, double rtol, int32_t max_iter, cudaStream_t s, int
         if (it > iters_max) iters_max = it;
         if (res > res_max) res_max = res;
         pack_chunk_kernel<<<dim3((unsigned)w.nrb, (unsigned)((kcur + kColsPerBlock - 1) / kColsPerBlock)),
-                            kColsPerBlock, 0, s>>>(m, kcur, kc, c0, M.k_pad, M.interior, w.X, M.P);
+                            kColsPerBlock, 0, s>>>(m, kcur, kc, c0, M.k_pad, M.interior, w.X, M.P, rpb);
     }
     cudaError_t e = cudaStreamSynchronize(s);
     release();

@@ -18,6 +18,13 @@
 //  * an exit whose barycentric coordinate is <= kEpsBary lands on the vertex.
 // Geometry and gradients are FP32; the hat-function gradients are computed in
 // FP64 on the host and rounded once.
+//
+// Layout for latency: every triangle is one 64-byte record (vertex ids,
+// neighbour ids, hat gradients of vertices 0 and 1 -- the third is minus their
+// sum -- and vertex positions), and the per-field triangle gradients are
+// computed once per field by tri_grad_kernel.  Crossing a triangle then needs
+// a single dependent load level: the record and gradient of the next triangle,
+// whose id sits in the current record.
 #include <cfloat>
 #include <cmath>
 
@@ -29,13 +36,12 @@ constexpr float kEpsBary = 1e-6f;    // barycentric snap to a vertex
 constexpr float kEpsWedge = 1e-6f;   // relative tolerance of the wedge / entry tests
 
 struct TraceParams {
-    const int4 *tri;
-    const int4 *tnbr;
-    const float4 *gphi;
+    const int4 *rec;               // [n_t][4] triangle records
+    const float2 *grads;           // [T][n_t] per-field triangle gradients
     const float2 *xy;
-    const int32_t *vt_off, *vt, *vn_off, *vn;
+    const int32_t *vt_off, *vt;
     const float *fields;
-    int64_t field_stride;
+    int64_t field_stride, n_t;
     const int32_t *targets, *sources;
     int64_t total;
     int32_t S, max_pts, max_steps;
@@ -43,38 +49,88 @@ struct TraceParams {
     int32_t *out_len, *out_status;
 };
 
-__device__ __forceinline__ int comp(const int4 v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : v.z); }
+struct Tri {
+    int v0, v1, v2, n0, n1, n2;
+    float2 g0, g1, p0, p1, p2;
+};
 
-__device__ __forceinline__ int local_of(const int4 v, int x) { return v.x == x ? 0 : (v.y == x ? 1 : 2); }
-
-__device__ __forceinline__ void load_gphi(const float4 *gphi, int t, float2 g[3]) {
-    const float4 a = gphi[2 * t], b = gphi[2 * t + 1];
-    g[0] = make_float2(a.x, a.y);
-    g[1] = make_float2(a.z, a.w);
-    g[2] = make_float2(b.x, b.y);
+__device__ __forceinline__ Tri load_tri(const int4 *__restrict__ rec, int t) {
+    const int4 a = __ldg(rec + 4 * t), b = __ldg(rec + 4 * t + 1);
+    const float4 c = __ldg(reinterpret_cast<const float4 *>(rec) + 4 * t + 2);
+    const float4 d = __ldg(reinterpret_cast<const float4 *>(rec) + 4 * t + 3);
+    Tri T;
+    T.v0 = a.x;
+    T.v1 = a.y;
+    T.v2 = a.z;
+    T.n0 = a.w;
+    T.n1 = b.x;
+    T.n2 = b.y;
+    T.g0 = make_float2(__int_as_float(b.z), __int_as_float(b.w));
+    T.g1 = make_float2(c.x, c.y);
+    T.p0 = make_float2(c.z, c.w);
+    T.p1 = make_float2(d.x, d.y);
+    T.p2 = make_float2(d.z, d.w);
+    return T;
 }
 
+__device__ __forceinline__ int vid(const Tri &T, int i) { return i == 0 ? T.v0 : (i == 1 ? T.v1 : T.v2); }
+__device__ __forceinline__ int nid(const Tri &T, int i) { return i == 0 ? T.n0 : (i == 1 ? T.n1 : T.n2); }
+__device__ __forceinline__ float2 pos(const Tri &T, int i) { return i == 0 ? T.p0 : (i == 1 ? T.p1 : T.p2); }
+__device__ __forceinline__ float2 gphi(const Tri &T, int i) {
+    return i == 0 ? T.g0 : (i == 1 ? T.g1 : make_float2(-(T.g0.x + T.g1.x), -(T.g0.y + T.g1.y)));
+}
+__device__ __forceinline__ int local_of(const Tri &T, int x) { return T.v0 == x ? 0 : (T.v1 == x ? 1 : 2); }
 __device__ __forceinline__ float dot2(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
+__device__ __forceinline__ float norm2(float2 a) { return sqrtf(a.x * a.x + a.y * a.y); }
 
-__device__ __forceinline__ float2 tri_grad(const float *f, const int4 tv, const float2 g[3]) {
-    const float f0 = f[tv.x], d1 = f[tv.y] - f0, d2 = f[tv.z] - f0;
-    return make_float2(d1 * g[1].x + d2 * g[2].x, d1 * g[1].y + d2 * g[2].y);
+// g = f0 grad(phi_0) + f1 grad(phi_1) + f2 grad(phi_2) = (f0 - f2) g0 + (f1 - f2) g1
+__global__ void tri_grad_kernel(const int4 *__restrict__ rec, int64_t n_t, const float *__restrict__ fields,
+                                int64_t field_stride, float2 *__restrict__ grads) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_t) return;
+    const int a = blockIdx.y;
+    const Tri T = load_tri(rec, (int)t);
+    const float *f = fields + (int64_t)a * field_stride;
+    const float f2 = f[T.v2], d0 = f[T.v0] - f2, d1 = f[T.v1] - f2;
+    grads[(int64_t)a * n_t + t] = make_float2(d0 * T.g0.x + d1 * T.g1.x, d0 * T.g0.y + d1 * T.g1.y);
 }
 
-__global__ void __launch_bounds__(128) trace_kernel(const TraceParams p) {
+// Loop structure: every iteration loads one triangle record (and its field
+// gradient) and advances one thread's state by it, so the threads of a warp
+// issue their loads together.  A vertex state walks the fan of triangles
+// around the vertex through the neighbour links (counter-clockwise from a
+// known incident triangle, then clockwise from it if the fan is open),
+// evaluating one triangle per iteration.  Quantities on the critical path use
+// squared norms and approximate reciprocals; the decisions they feed (wedge
+// and entry tests, vertex snapping) carry relative tolerances.
+__global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= p.total) return;
     const int a = (int)(id / p.S);
     const int target = p.targets[a];
     const float *f = p.fields + (int64_t)a * p.field_stride;
+    const float2 *grads = p.grads + (int64_t)a * p.n_t;
     float2 *out = p.out_xy + id * p.max_pts;
+    const float eps2 = kEpsWedge * kEpsWedge;
     int v = p.sources[id];
     int len = 0;
     int status = DD_TRACE_STEP_LIMIT;
+    int states = 0;                // vertex and edge states visited (the step cap counts these)
     out[len++] = p.xy[v];
-    bool at_vertex = true;
-    int tc = -1, ic = 0;          // edge state: left triangle tc through the edge opposite local ic
-    float la = 0.f, lb = 0.f;     // barycentric weights of its endpoints (ic+1, ic+2)
+
+    // vertex-scan state
+    bool scanning = true;
+    int t0 = p.vt[p.vt_off[v]];    // a triangle incident on the start vertex
+    int scan_t = t0, t0_cw = -1;   // triangle being examined; clockwise neighbour of t0
+    bool ccw = true, adj = false;
+    int best = -1, best_i = 0;
+    float best_g2 = 0.f, baj = 0.f, bak = 0.f;
+    Tri best_T;
+    // edge state: leaving `cur` (id cur_id) through the edge opposite local ic
+    Tri cur;
+    int cur_id = -1, ic = 0;
+    float la = 0.f, lb = 0.f;
+    ++states;
 
 #define DD_PUSH(pt)                              \
     do {                                         \
@@ -84,173 +140,201 @@ __global__ void __launch_bounds__(128) trace_kernel(const TraceParams p) {
         }                                        \
         out[len++] = (pt);                       \
     } while (0)
+#define DD_ENTER_VERTEX(vert, tri_id)            \
+    do {                                         \
+        v = (vert);                              \
+        scanning = true;                         \
+        t0 = (tri_id);                           \
+        scan_t = t0;                             \
+        t0_cw = -1;                              \
+        ccw = true;                              \
+        adj = false;                             \
+        best = -1;                               \
+        best_g2 = 0.f;                           \
+        if (++states > p.max_steps) goto done;   \
+    } while (0)
 
-    for (int step = 0; step < p.max_steps; ++step) {
-        if (at_vertex) {
-            if (v == target) {
-                status = DD_TRACE_OK;
-                goto done;
+    for (int64_t iter = 0; iter < 16LL * p.max_steps; ++iter) {
+        if (scanning && v == target) {
+            status = DD_TRACE_OK;
+            goto done;
+        }
+        const int tl = scanning ? scan_t : nid(cur, ic);
+        if (!scanning && tl < 0) {     // boundary edge: slide to the lower endpoint
+            const int av = vid(cur, (ic + 1) % 3), bv = vid(cur, (ic + 2) % 3);
+            const float fa = f[av], fb = f[bv];
+            const bool a_low = fa < fb || (fa == fb && av < bv);
+            DD_PUSH(a_low ? pos(cur, (ic + 1) % 3) : pos(cur, (ic + 2) % 3));
+            DD_ENTER_VERTEX(a_low ? av : bv, cur_id);
+            continue;
+        }
+        const Tri T = load_tri(p.rec, tl);
+        const float2 g = grads[tl];
+        if (scanning) {
+            // ---- one triangle of the fan around v
+            const int i = local_of(T, v), j = (i + 1) % 3, k = (i + 2) % 3;
+            adj |= (T.v0 == target) | (T.v1 == target) | (T.v2 == target);
+            const float g2 = g.x * g.x + g.y * g.y;
+            if (g2 > 0.f) {
+                const float2 gj = gphi(T, j), gk = gphi(T, k);
+                const float aj = -dot2(gj, g), ak = -dot2(gk, g);
+                const float tol2 = eps2 * g2 * fmaxf(dot2(gj, gj), dot2(gk, gk));
+                const bool in_j = aj >= 0.f || aj * aj <= tol2;
+                const bool in_k = ak >= 0.f || ak * ak <= tol2;
+                if (in_j && in_k && aj + ak > 0.f && (g2 > best_g2 || (g2 == best_g2 && tl < best))) {
+                    best = tl;
+                    best_i = i;
+                    best_g2 = g2;
+                    baj = fmaxf(aj, 0.f);
+                    bak = fmaxf(ak, 0.f);
+                    best_T = T;
+                }
             }
-            bool adj = false;
-            for (int q = p.vn_off[v]; q < p.vn_off[v + 1]; ++q) adj |= (p.vn[q] == target);
-            if (adj) {
+            if (tl == t0) t0_cw = nid(T, k);
+            int next = ccw ? nid(T, j) : nid(T, k);
+            if (ccw && next == t0) {
+                next = -1;                       // closed fan: done
+            } else if (ccw && next < 0) {
+                ccw = false;                     // open fan: continue clockwise from t0
+                next = t0_cw;
+            }
+            if (next >= 0) {
+                scan_t = next;
+                continue;
+            }
+            // fan complete
+            if (adj) {                           // v lies on an edge incident on the target
                 DD_PUSH(p.xy[target]);
                 status = DD_TRACE_OK;
                 goto done;
             }
-            int best = -1, best_i = 0;
-            float best_g = 0.f, baj = 0.f, bak = 0.f;
-            for (int q = p.vt_off[v]; q < p.vt_off[v + 1]; ++q) {
-                const int t = p.vt[q];
-                const int4 tv = p.tri[t];
-                float2 g3[3];
-                load_gphi(p.gphi, t, g3);
-                const float2 g = tri_grad(f, tv, g3);
-                const float gn = sqrtf(g.x * g.x + g.y * g.y);
-                if (!(gn > 0.f)) continue;
-                const int i = local_of(tv, v), j = (i + 1) % 3, k = (i + 2) % 3;
-                const float aj = -dot2(g3[j], g), ak = -dot2(g3[k], g);
-                const float tol = kEpsWedge * gn * fmaxf(sqrtf(dot2(g3[j], g3[j])), sqrtf(dot2(g3[k], g3[k])));
-                if (aj >= -tol && ak >= -tol && aj + ak > 0.f && gn > best_g) {
-                    best = t;
-                    best_i = i;
-                    best_g = gn;
-                    baj = fmaxf(aj, 0.f);
-                    bak = fmaxf(ak, 0.f);
-                }
-            }
             if (best >= 0) {
-                const int4 tv = p.tri[best];
-                const int vj = comp(tv, (best_i + 1) % 3), vk = comp(tv, (best_i + 2) % 3);
-                const float s = 1.0f / (baj + bak);
+                cur = best_T;
+                cur_id = best;
+                const int bj = (best_i + 1) % 3, bk = (best_i + 2) % 3;
+                const float s = __fdividef(1.0f, baj + bak);
                 const float lj = s * baj, lk = s * bak;
                 if (lj <= kEpsBary) {
-                    DD_PUSH(p.xy[vk]);
-                    v = vk;
+                    DD_PUSH(pos(cur, bk));
+                    DD_ENTER_VERTEX(vid(cur, bk), cur_id);
                 } else if (lk <= kEpsBary) {
-                    DD_PUSH(p.xy[vj]);
-                    v = vj;
+                    DD_PUSH(pos(cur, bj));
+                    DD_ENTER_VERTEX(vid(cur, bj), cur_id);
                 } else {
-                    const float2 pj = p.xy[vj], pk = p.xy[vk];
+                    const float2 pj = pos(cur, bj), pk = pos(cur, bk);
                     DD_PUSH(make_float2(lj * pj.x + lk * pk.x, lj * pj.y + lk * pk.y));
-                    at_vertex = false;
-                    tc = best;
+                    scanning = false;
                     ic = best_i;
                     la = lj;
                     lb = lk;
+                    if (++states > p.max_steps) goto done;
                 }
                 continue;
             }
-            // edge fallback
-            int best_u = -1;
-            float best_s = 0.f;
-            const float fv = f[v];
-            const float2 pv = p.xy[v];
-            for (int q = p.vn_off[v]; q < p.vn_off[v + 1]; ++q) {
-                const int u = p.vn[q];
-                const float2 pu = p.xy[u];
-                const float dx = pv.x - pu.x, dy = pv.y - pu.y;
-                const float slope = (fv - f[u]) / sqrtf(dx * dx + dy * dy);
-                if (slope > best_s) {
-                    best_s = slope;
-                    best_u = u;
+            // no descending triangle: the incident edge of largest positive slope
+            // (ties to the lower id); rare, so it walks the vertex's triangle list
+            {
+                int best_u = -1, best_ut = -1;
+                float best_s = 0.f;
+                float2 best_p = make_float2(0.f, 0.f);
+                const float fv = f[v];
+                const float2 pv = p.xy[v];
+                for (int q = p.vt_off[v]; q < p.vt_off[v + 1]; ++q) {
+                    const int tq = p.vt[q];
+                    const Tri Q = load_tri(p.rec, tq);
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        const int u = vid(Q, e);
+                        if (u == v) continue;
+                        const float2 pu = pos(Q, e);
+                        const float dx = pv.x - pu.x, dy = pv.y - pu.y;
+                        const float slope = (fv - f[u]) / sqrtf(dx * dx + dy * dy);
+                        if (slope > 0.f && (slope > best_s || (slope == best_s && u < best_u))) {
+                            best_s = slope;
+                            best_u = u;
+                            best_p = pu;
+                            best_ut = tq;
+                        }
+                    }
                 }
+                if (best_u < 0) {
+                    status = DD_TRACE_STUCK;
+                    goto done;
+                }
+                DD_PUSH(best_p);
+                DD_ENTER_VERTEX(best_u, best_ut);
+                continue;
             }
-            if (best_u < 0) {
-                status = DD_TRACE_STUCK;
-                goto done;
-            }
-            DD_PUSH(p.xy[best_u]);
-            v = best_u;
-            continue;
         }
-        // ---- edge state
+        // ---- edge state: entering T (id tl) across the edge (av, bv) of cur
         {
-            const int4 tv = p.tri[tc];
-            const int av = comp(tv, (ic + 1) % 3), bv = comp(tv, (ic + 2) % 3);
-            if (av == target || bv == target) {
-                DD_PUSH(p.xy[target]);
-                status = DD_TRACE_OK;
-                goto done;
-            }
-            const int t2 = comp(p.tnbr[tc], ic);
-            bool slide = t2 < 0;
-            int4 tv2 = make_int4(0, 0, 0, 0);
-            float2 g3[3], g2 = make_float2(0.f, 0.f);
-            int ia = 0, ib = 0, c2 = 0;
-            float rc = 0.f;
+            const int ia0 = (ic + 1) % 3, ib0 = (ic + 2) % 3;
+            const int av = vid(cur, ia0), bv = vid(cur, ib0);
+            const int ia = local_of(T, av), ib = local_of(T, bv), c2 = 3 - ia - ib;
+            const float2 gc = gphi(T, c2);
+            const float rc = -dot2(gc, g);
+            bool slide = !(rc > 0.f && rc * rc > eps2 * dot2(g, g) * dot2(gc, gc));
+            float ra = 0.f, rb = 0.f, sa = INFINITY, sb = INFINITY;
             if (!slide) {
-                tv2 = p.tri[t2];
-                load_gphi(p.gphi, t2, g3);
-                g2 = tri_grad(f, tv2, g3);
-                ia = local_of(tv2, av);
-                ib = local_of(tv2, bv);
-                c2 = 3 - ia - ib;
-                rc = -dot2(g3[c2], g2);
-                const float gn = sqrtf(g2.x * g2.x + g2.y * g2.y);
-                const float tol = kEpsWedge * gn * sqrtf(dot2(g3[c2], g3[c2]));
-                slide = !(rc > tol);
+                ra = -dot2(gphi(T, ia), g);
+                rb = -dot2(gphi(T, ib), g);
+                sa = ra < 0.f ? __fdividef(la, -ra) : INFINITY;
+                sb = rb < 0.f ? __fdividef(lb, -rb) : INFINITY;
+                slide = !(fminf(sa, sb) < INFINITY);   // no exit edge: treat as a valley edge
             }
-            if (slide) {
+            if (slide) {               // valley edge: to the lower endpoint
                 const float fa = f[av], fb = f[bv];
-                const int low = (fa < fb || (fa == fb && av < bv)) ? av : bv;
-                DD_PUSH(p.xy[low]);
-                v = low;
-                at_vertex = true;
+                const bool a_low = fa < fb || (fa == fb && av < bv);
+                DD_PUSH(a_low ? pos(cur, ia0) : pos(cur, ib0));
+                DD_ENTER_VERTEX(a_low ? av : bv, cur_id);
                 continue;
             }
-            const float ra = -dot2(g3[ia], g2), rb = -dot2(g3[ib], g2);
-            const float sa = ra < 0.f ? la / -ra : INFINITY;
-            const float sb = rb < 0.f ? lb / -rb : INFINITY;
-            if (!(fminf(sa, sb) < INFINITY)) {     // no exit edge found: treat as a valley edge
-                const float fa = f[av], fb = f[bv];
-                const int low = (fa < fb || (fa == fb && av < bv)) ? av : bv;
-                DD_PUSH(p.xy[low]);
-                v = low;
-                at_vertex = true;
-                continue;
-            }
-            const int cv = comp(tv2, c2);
-            int exit_local, keep_v;        // exit through the edge opposite exit_local; keep_v stays on it
+            int exit_local, keep_local;    // exit through the edge opposite exit_local
             float lkeep, lc2;
             if (sa <= sb) {
                 lkeep = fmaxf(lb + sa * rb, 0.f);
                 lc2 = fmaxf(sa * rc, 0.f);
                 exit_local = ia;
-                keep_v = bv;
+                keep_local = ib;
             } else {
                 lkeep = fmaxf(la + sb * ra, 0.f);
                 lc2 = fmaxf(sb * rc, 0.f);
                 exit_local = ib;
-                keep_v = av;
+                keep_local = ia;
             }
-            const float tot = lkeep + lc2;
-            lkeep /= tot;
-            lc2 /= tot;
+            const float inv = __fdividef(1.0f, lkeep + lc2);
+            lkeep *= inv;
+            lc2 *= inv;
             if (lkeep <= kEpsBary) {
-                DD_PUSH(p.xy[cv]);
-                v = cv;
-                at_vertex = true;
+                DD_PUSH(pos(T, c2));
+                DD_ENTER_VERTEX(vid(T, c2), tl);
                 continue;
             }
             if (lc2 <= kEpsBary) {
-                DD_PUSH(p.xy[keep_v]);
-                v = keep_v;
-                at_vertex = true;
+                DD_PUSH(pos(T, keep_local));
+                DD_ENTER_VERTEX(vid(T, keep_local), tl);
                 continue;
             }
-            const int e1 = comp(tv2, (exit_local + 1) % 3), e2 = comp(tv2, (exit_local + 2) % 3);
-            const float l1 = e1 == cv ? lc2 : lkeep, l2 = e2 == cv ? lc2 : lkeep;
-            const float2 p1 = p.xy[e1], p2 = p.xy[e2];
+            const int e1 = (exit_local + 1) % 3, e2 = (exit_local + 2) % 3;
+            const float l1 = e1 == c2 ? lc2 : lkeep, l2 = e2 == c2 ? lc2 : lkeep;
+            const float2 p1 = pos(T, e1), p2 = pos(T, e2);
             DD_PUSH(make_float2(l1 * p1.x + l2 * p2.x, l1 * p1.y + l2 * p2.y));
-            tc = t2;
+            cur = T;
+            cur_id = tl;
             ic = exit_local;
             la = l1;
             lb = l2;
+            if (++states > p.max_steps) goto done;
+            if (vid(T, e1) == target || vid(T, e2) == target) {   // an edge incident on the target
+                DD_PUSH(p.xy[target]);
+                status = DD_TRACE_OK;
+                goto done;
+            }
         }
     }
 done:
 #undef DD_PUSH
+#undef DD_ENTER_VERTEX
     p.out_len[id] = len;
     p.out_status[id] = status;
 }
@@ -259,18 +343,16 @@ done:
 
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,
                   const int32_t *sources, int32_t T, int32_t S, int32_t max_pts, float2 *out_xy, int32_t *out_len,
-                  int32_t *out_status, cudaStream_t s) {
+                  int32_t *out_status, float2 *grads, cudaStream_t s) {
     TraceParams p;
-    p.tri = m.tri;
-    p.tnbr = m.tnbr;
-    p.gphi = m.gphi;
+    p.rec = m.trec;
+    p.grads = grads;
     p.xy = m.xy;
     p.vt_off = m.vt_off;
     p.vt = m.vt;
-    p.vn_off = m.vn_off;
-    p.vn = m.vn;
     p.fields = fields;
     p.field_stride = field_stride;
+    p.n_t = m.n_t;
     p.targets = targets;
     p.sources = sources;
     p.total = (int64_t)T * S;
@@ -282,5 +364,7 @@ void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, c
     p.out_len = out_len;
     p.out_status = out_status;
     if (p.total == 0) return;
-    trace_kernel<<<(unsigned)((p.total + 127) / 128), 128, 0, s>>>(p);
+    dim3 gg((unsigned)((m.n_t + 255) / 256), (unsigned)T);
+    tri_grad_kernel<<<gg, 256, 0, s>>>(m.trec, m.n_t, fields, field_stride, grads);
+    trace_kernel<<<(unsigned)((p.total + 63) / 64), 64, 0, s>>>(p);
 }
