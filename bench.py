@@ -242,48 +242,74 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
     }
     if args.stream:
-        line["stream"] = stream_roofline(dd, ctx, dev, stream, flush, pk, pk_kind, clocks)
+        line["stream"], line["gemm"] = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
     dd.dd_destroy(ctx)
     return line
 
 
-def stream_roofline(dd, ctx, dev, stream, flush, pk, pk_kind, clocks, reps: int = 10):
-    """Single-target KL+TV sweeps over the grid450 Poisson kernel (3.0 GB, far above L2).
+def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10):
+    """grid450 (n = 192,360, k = 3,936; P = 3.0 GB FP32, far above L2).
 
-    The streaming kernel reads P once per target; achieved GB/s = 4 n k_pad
-    bytes / event-timed duration of dd_distance (stage + stream kernels)."""
+    stream: single-target KL+TV sweeps; the streaming kernel reads P once per
+      target, achieved GB/s = (4 n k_pad + 8 n) bytes / event-timed dd_distance.
+    gemm: 1,024 targets, KL through the split-BF16 tcgen05 GEMM; algorithmic
+      2 n k T flop (three BF16 products issued), against the FP32 CUDA-core
+      path for the same KL fields."""
     import torch
     from synthetic import workloads
-    wl = workloads.grid450(T=reps)
+    T_big = 1024
+    wl = workloads.grid450(T=T_big)
     idx, off = wl.mesh.loop_arrays()
     mid = dd.dd_load_mesh(ctx, wl.mesh.xy, wl.mesh.tri, idx, off)
     t0 = time.perf_counter()
     iters, resid = dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
     pre = time.perf_counter() - t0
     info = dd.dd_mesh_info(ctx, mid)
-    n_v, k_pad = info["n_v"], info["k_pad"]
-    out = torch.empty((2, 1, n_v), dtype=torch.float32, device=dev)
-    for t in wl.targets[:3]:
-        dd.dd_distance(ctx, mid, [int(t)], 3, 0, out)
-    ms = []
-    for t in wl.targets:
-        flush.fill_(0.5)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        dd.dd_distance(ctx, mid, [int(t)], 3, 0, out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    med = statistics.median(ms)
+    n_v, k, k_pad = info["n_v"], info["k"], info["k_pad"]
+
+    def timed(fn, n_rep):
+        ms = []
+        for _ in range(n_rep):
+            flush.fill_(0.5)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    out1 = torch.empty((2, 1, n_v), dtype=torch.float32, device=dev)
+    tl = [int(t) for t in wl.targets]
+    for t in tl[:3]:
+        dd.dd_distance(ctx, mid, [t], 3, 0, out1)
+    it = iter(tl * 4)
+    med = timed(lambda: dd.dd_distance(ctx, mid, [next(it)], 3, 0, out1), reps)
     nbytes = 4.0 * n_v * k_pad + 2 * 4.0 * n_v
     achieved = nbytes / (med / 1e3) / 1e9
+    stream_sec = {"workload": "grid450 single target: n=%d, k_pad=%d, P=%.2f GB FP32" % (n_v, k_pad, 4.0 * n_v * k_pad / 1e9),
+                  "kernel": "field_stream_kernel (+ stage_targets_kernel)", "bound": "hbm",
+                  "achieved": round(achieved, 1), "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                  "frac": round(achieved / pk.get("hbm_gbs", 6672.5), 4), "peak_source": pk_kind,
+                  "ms_per_field_pair": round(med, 4), "fields_per_s": round(2 / (med / 1e3), 1), "traffic": None,
+                  "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(pre, 2)}}
+
+    outk = torch.empty((1, T_big, n_v), dtype=torch.float32, device=dev)
+    dd.dd_distance(ctx, mid, tl, dd.DD_F_KL, dd.DD_PREC_BF16X3, outk)   # builds the BF16 split of P once
+    torch.cuda.synchronize()
+    g_ms = timed(lambda: dd.dd_distance(ctx, mid, tl, dd.DD_F_KL, dd.DD_PREC_BF16X3, outk), 5)
+    f_ms = timed(lambda: dd.dd_distance(ctx, mid, tl, dd.DD_F_KL, dd.DD_PREC_FP32, outk), 2)
+    flop_alg = 2.0 * n_v * k * T_big
+    tf_alg = flop_alg / (g_ms / 1e3) / 1e12
+    tf_iss = 3 * tf_alg
+    peak_bf16 = pk.get("bf16_tflops", 1916.1)
+    gemm_sec = {"workload": "grid450, %d targets, KL only" % T_big, "kernel": "kl_gemm_kernel (+ split_targets_kernel)",
+                "bound": "tensor", "achieved": round(tf_iss, 1), "achieved_algorithmic": round(tf_alg, 1),
+                "peak": peak_bf16, "unit": "TFLOP/s", "frac": round(tf_iss / peak_bf16, 4), "peak_source": pk_kind,
+                "ms": round(g_ms, 3), "kl_fields_per_s": round(T_big / (g_ms / 1e3), 1),
+                "fp32_path_ms": round(f_ms, 3), "speedup_vs_fp32_path": round(f_ms / g_ms, 2), "traffic": None}
     dd.dd_unload_mesh(ctx, mid)
-    return {"workload": "grid450 single target: n=%d, k_pad=%d, P=%.2f GB FP32" % (n_v, k_pad, 4.0 * n_v * k_pad / 1e9),
-            "kernel": "field_stream_kernel (+ stage_targets_kernel)", "bound": "hbm",
-            "achieved": round(achieved, 1), "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-            "frac": round(achieved / pk.get("hbm_gbs", 6672.5), 4), "peak_source": pk_kind,
-            "ms_per_field_pair": round(med, 4), "fields_per_s": round(2 / (med / 1e3), 1), "traffic": None,
-            "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(pre, 2)}}
+    return stream_sec, gemm_sec
 
 
 class OracleStep:
@@ -334,7 +360,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", dest="stream", action="store_false",
-                    help="skip the grid450 single-target HBM-stream measurement")
+                    help="skip the grid450 measurements (single-target HBM stream, BF16 tensor-core KL)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

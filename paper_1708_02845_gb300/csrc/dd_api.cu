@@ -12,7 +12,7 @@
 
 namespace {
 
-enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_COUNT };
+enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_COUNT };
 
 struct MeshSlot {
     bool live = false;
@@ -161,13 +161,25 @@ dd_status check_kernel_flag(dd_ctx *ctx) {
 }
 
 // fields of T targets into dst [nf][T][n_v] (device), targets already in scratch
-dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t T, uint32_t f_mask, float *dst) {
-    dd_status st = ensure_scratch(ctx, S_STAGE, 3 * (size_t)T * m.k_pad * sizeof(float));
+dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t T, uint32_t f_mask, int32_t prec,
+                      float *dst) {
+    float *kl = (f_mask & DD_F_KL) ? dst : nullptr;
+    float *tv = (f_mask & DD_F_TV) ? dst + ((f_mask & DD_F_KL) ? (int64_t)T * m.n_v : 0) : nullptr;
+    dd_status st;
+    if (prec == DD_PREC_BF16X3 && kl) {
+        // KL through the split-BF16 tensor-core GEMM; TV (if asked) stays FP32 below
+        std::string err;
+        if ((st = prepare_bf16(m, ctx->stream, err)) != DD_OK) return set_err(ctx, st, err);
+        if ((st = ensure_scratch(ctx, S_GEMM, gemm_target_scratch_bytes(m, T))) != DD_OK) return st;
+        if ((st = launch_kl_gemm(m, d_targets, T, ctx->scratch[S_GEMM], kl, ctx->d_err, ctx->stream, err)) != DD_OK)
+            return set_err(ctx, st, err);
+        kl = nullptr;
+        if (!tv) return DD_OK;
+    }
+    st = ensure_scratch(ctx, S_STAGE, 3 * (size_t)T * m.k_pad * sizeof(float));
     if (st != DD_OK) return st;
     float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
     launch_stage_targets(m.P, m.k_pad, m.k, d_targets, T, stage, ctx->stream);
-    float *kl = (f_mask & DD_F_KL) ? dst : nullptr;
-    float *tv = (f_mask & DD_F_TV) ? dst + ((f_mask & DD_F_KL) ? (int64_t)T * m.n_v : 0) : nullptr;
     launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream);
     CK(cudaGetLastError(), "field kernel launch");
     return DD_OK;
@@ -427,7 +439,7 @@ dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t
         if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
         if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV)))
             return set_err(ctx, DD_EINVAL, "f_mask must be a non-empty combination of DD_F_KL and DD_F_TV");
-        if (prec != DD_PREC_FP32) return set_err(ctx, DD_EINVAL, "unsupported precision");
+        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3) return set_err(ctx, DD_EINVAL, "unsupported precision");
         if (!out) return set_err(ctx, DD_EINVAL, "out is null");
         if ((st = check_targets(ctx, *m, targets, T, true, "targets")) != DD_OK) return st;
         const int sp = pointer_space(ctx, out);
@@ -440,7 +452,7 @@ dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t
             if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
             dst = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
         }
-        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, dst);
+        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst);
         if (st != DD_OK) return st;
         if (sp == 0) {
             CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy fields to host");
@@ -554,7 +566,8 @@ dd_status dd_trace(dd_ctx *ctx, int32_t mesh, int32_t target, uint32_t f, const 
         if ((st = upload(ctx, S_TARGETS, &target, sizeof(int32_t))) != DD_OK) return st;
         if ((st = ensure_scratch(ctx, S_FIELDS, (size_t)m->n_v * sizeof(float))) != DD_OK) return st;
         float *field = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
-        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), 1, f, field);
+        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), 1, f, DD_PREC_FP32,
+                         field);
         if (st != DD_OK) return st;
         return trace_into(ctx, *m, field, &target, 1, sources, S, max_pts, out_xy, out_len, out_status, true);
     } catch (...) {
@@ -575,7 +588,7 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
             return set_err(ctx, DD_EINVAL, "bad f_mask");
         if ((trace_f != DD_F_KL && trace_f != DD_F_TV) || !(f_mask & trace_f))
             return set_err(ctx, DD_EINVAL, "trace_f must be one bit of f_mask");
-        if (prec != DD_PREC_FP32) return set_err(ctx, DD_EINVAL, "unsupported precision");
+        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3) return set_err(ctx, DD_EINVAL, "unsupported precision");
         if (!out_fields) return set_err(ctx, DD_EINVAL, "out_fields is null");
         if ((st = check_path_args(ctx, S, max_pts, out_xy, out_len, out_status)) != DD_OK) return st;
         if ((st = check_targets(ctx, *m, targets, T, true, "targets")) != DD_OK) return st;
@@ -590,7 +603,7 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
             if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
             dst = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
         }
-        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, dst);
+        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst);
         if (st != DD_OK) return st;
         const float *trace_field = dst + ((trace_f == DD_F_TV && (f_mask & DD_F_KL)) ? (int64_t)T * m->n_v : 0);
         if (sf == 0)

@@ -59,6 +59,9 @@ struct DevMesh {
     double *rb_val = nullptr;
     float *P = nullptr;        // [n_v][k_pad] FP32 Poisson kernel
     bool has_P = false;
+    void *p_hi = nullptr, *p_lo = nullptr;   // BF16 split of P, [n_v][kb] (built on first BF16 request)
+    float *ex = nullptr;                     // [n_v] sum_b P log P (FP64-accumulated)
+    int64_t kb = 0;                          // BF16 row pitch: k rounded up to 64
     int64_t bytes = 0;
     std::vector<void *> owned;
     std::vector<uint8_t> is_boundary;  // host copy: vertex flags
@@ -83,6 +86,14 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,
                   const int32_t *sources, int32_t T, int32_t S, int32_t max_pts, float2 *out_xy,
                   int32_t *out_len, int32_t *out_status, float2 *grads, cudaStream_t s);
+
+// Split-BF16 tensor-core KL (tcgen05): BF16 split of P and e_x once per mesh,
+// then KL [T][n_v] for T staged targets (scratch: gemm_target_scratch_bytes).
+int64_t gemm_kb(int64_t k);
+dd_status prepare_bf16(DevMesh &m, cudaStream_t s, std::string &err);
+size_t gemm_target_scratch_bytes(const DevMesh &m, int32_t T);
+dd_status launch_kl_gemm(const DevMesh &m, const int32_t *d_targets, int32_t T, void *scratch, float *out_kl,
+                         int *err_flag, cudaStream_t s, std::string &err);
 
 #define DD_CUDA_TRY(expr, errstr)                                                   \
     do {                                                                            \

@@ -87,3 +87,25 @@ def test_paths_properties(big):
         assert np.allclose(xy[s, 0], mesh.xy[src[s]], atol=1e-6)
         if st[s] == dd.DD_TRACE_OK:
             assert np.allclose(xy[s, ln[s] - 1], mesh.xy[t], atol=1e-6)
+
+
+def test_bf16x3_sampled_rows(big):
+    """Split-BF16 tensor-core KL at full size: 256 targets, sampled rows."""
+    dd, ctx, wl, mid, po, rows, targets, Prow, _ = big
+    n_v = wl.mesh.n_v
+    rng = np.random.default_rng(21)
+    tg = [int(t) for t in po.I[rng.choice(po.m, 256, replace=False)]]
+    Pt = po.rows(tg)
+    out = torch.empty((1, len(tg), n_v), dtype=torch.float32, device="cuda")
+    dd.dd_distance(ctx, mid, tg, dd.DD_F_KL, dd.DD_PREC_BF16X3, out)
+    dd.dd_sync(ctx)
+    got = out[0][:, torch.as_tensor(rows.astype(np.int64), device="cuda")].cpu().numpy()
+    R = Prow[:len(rows)]
+    worst = 0.0
+    for a in range(len(tg)):
+        ref = kl_field_fast(R, Pt[a])
+        with np.errstate(divide="ignore"):
+            S = R @ np.abs(np.log(np.maximum(Pt[a], 1e-300)))
+        fin = np.isfinite(ref)
+        worst = max(worst, float(np.max(np.abs(got[a][fin] - ref[fin]) / np.maximum(np.abs(ref[fin]), S[fin]))))
+    assert worst <= 1e-4, worst
