@@ -112,6 +112,12 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     ctx = dd.dd_create(local_rank, stream.cuda_stream)
+    if args.section == "grid450":
+        pk, pk_kind = peaks()
+        flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev)
+        st_sec, gm_sec = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
+        dd.dd_destroy(ctx)
+        return {"metric": "grid450 sections only", "stream": st_sec, "gemm": gm_sec}
     wl, batches = workload_batches(rank)
     mesh = wl.mesh
     idx, off = mesh.loop_arrays()
@@ -241,7 +247,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
-    if args.stream:
+    if args.stream and args.section == "all":
         line["stream"], line["gemm"] = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
     dd.dd_destroy(ctx)
     return line
@@ -361,6 +367,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", dest="stream", action="store_false",
                     help="skip the grid450 measurements (single-target HBM stream, BF16 tensor-core KL)")
+    ap.add_argument("--section", choices=["all", "step", "grid450"], default="all",
+                    help="step: only the grid140 query step; grid450: only the grid450 measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -396,7 +404,7 @@ def main():
         dist.init_process_group("nccl")
     line = run_ours(args, rank, world, local_rank)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and args.section != "grid450":
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
     if world > 1:

@@ -74,14 +74,9 @@ __device__ __forceinline__ Tri load_tri(const int4 *__restrict__ rec, int t) {
 }
 
 __device__ __forceinline__ int vid(const Tri &T, int i) { return i == 0 ? T.v0 : (i == 1 ? T.v1 : T.v2); }
-__device__ __forceinline__ int nid(const Tri &T, int i) { return i == 0 ? T.n0 : (i == 1 ? T.n1 : T.n2); }
 __device__ __forceinline__ float2 pos(const Tri &T, int i) { return i == 0 ? T.p0 : (i == 1 ? T.p1 : T.p2); }
-__device__ __forceinline__ float2 gphi(const Tri &T, int i) {
-    return i == 0 ? T.g0 : (i == 1 ? T.g1 : make_float2(-(T.g0.x + T.g1.x), -(T.g0.y + T.g1.y)));
-}
 __device__ __forceinline__ int local_of(const Tri &T, int x) { return T.v0 == x ? 0 : (T.v1 == x ? 1 : 2); }
 __device__ __forceinline__ float dot2(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
-__device__ __forceinline__ float norm2(float2 a) { return sqrtf(a.x * a.x + a.y * a.y); }
 
 // g = f0 grad(phi_0) + f1 grad(phi_1) + f2 grad(phi_2) = (f0 - f2) g0 + (f1 - f2) g1
 __global__ void tri_grad_kernel(const int4 *__restrict__ rec, int64_t n_t, const float *__restrict__ fields,
@@ -100,9 +95,16 @@ __global__ void tri_grad_kernel(const int4 *__restrict__ rec, int64_t n_t, const
 // issue their loads together.  A vertex state walks the fan of triangles
 // around the vertex through the neighbour links (counter-clockwise from a
 // known incident triangle, then clockwise from it if the fan is open),
-// evaluating one triangle per iteration.  Quantities on the critical path use
-// squared norms and approximate reciprocals; the decisions they feed (wedge
-// and entry tests, vertex snapping) carry relative tolerances.
+// evaluating one triangle per iteration.  Both states share one rotated view
+// of the loaded triangle: a reference vertex R (the fan vertex, or the
+// second endpoint b of the entry edge) and the two that follow it
+// counter-clockwise, X and Y.  For an entry edge (a, b) of the previous
+// triangle, consistent orientation puts a at X and the opposite vertex at Y.
+// Quantities on the critical path use squared norms and approximate
+// reciprocals; the decisions they feed carry relative tolerances.
+__device__ __forceinline__ float sel3f(int i, float a, float b, float c) { return i == 0 ? a : (i == 1 ? b : c); }
+__device__ __forceinline__ int sel3i(int i, int a, int b, int c) { return i == 0 ? a : (i == 1 ? b : c); }
+
 __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= p.total) return;
@@ -115,22 +117,23 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
     int v = p.sources[id];
     int len = 0;
     int status = DD_TRACE_STEP_LIMIT;
-    int states = 0;                // vertex and edge states visited (the step cap counts these)
+    int states = 1;                // vertex and edge states entered (the step cap counts these)
     out[len++] = p.xy[v];
 
-    // vertex-scan state
+    // vertex (fan-scan) state
     bool scanning = true;
-    int t0 = p.vt[p.vt_off[v]];    // a triangle incident on the start vertex
-    int scan_t = t0, t0_cw = -1;   // triangle being examined; clockwise neighbour of t0
+    int t0 = p.vt[p.vt_off[v]];
+    int scan_t = t0, t0_cw = -1;
     bool ccw = true, adj = false;
-    int best = -1, best_i = 0;
+    int best = -1;
     float best_g2 = 0.f, baj = 0.f, bak = 0.f;
-    Tri best_T;
-    // edge state: leaving `cur` (id cur_id) through the edge opposite local ic
-    Tri cur;
-    int cur_id = -1, ic = 0;
+    int b_vj = 0, b_vk = 0, b_next = -1;
+    float2 b_pj = make_float2(0.f, 0.f), b_pk = b_pj;
+    // edge state: the path sits on edge (ea, eb) of triangle cur_id, weights (la, lb),
+    // and enters t_next (the triangle across that edge, -1 on the boundary)
+    int cur_id = -1, t_next = -1, ea = 0, eb = 0;
     float la = 0.f, lb = 0.f;
-    ++states;
+    float2 pa = make_float2(0.f, 0.f), pb = pa;
 
 #define DD_PUSH(pt)                              \
     do {                                         \
@@ -152,46 +155,62 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
         best = -1;                               \
         best_g2 = 0.f;                           \
         if (++states > p.max_steps) goto done;   \
+        if (v == target) {                       \
+            status = DD_TRACE_OK;                \
+            goto done;                           \
+        }                                        \
+    } while (0)
+#define DD_SLIDE()                                                     \
+    do {                                                               \
+        const float fa = f[ea], fb = f[eb];                            \
+        const bool a_low = fa < fb || (fa == fb && ea < eb);           \
+        DD_PUSH(a_low ? pa : pb);                                      \
+        DD_ENTER_VERTEX(a_low ? ea : eb, cur_id);                      \
     } while (0)
 
+    if (v == target) {
+        status = DD_TRACE_OK;
+        goto done;
+    }
     for (int64_t iter = 0; iter < 16LL * p.max_steps; ++iter) {
-        if (scanning && v == target) {
-            status = DD_TRACE_OK;
-            goto done;
-        }
-        const int tl = scanning ? scan_t : nid(cur, ic);
-        if (!scanning && tl < 0) {     // boundary edge: slide to the lower endpoint
-            const int av = vid(cur, (ic + 1) % 3), bv = vid(cur, (ic + 2) % 3);
-            const float fa = f[av], fb = f[bv];
-            const bool a_low = fa < fb || (fa == fb && av < bv);
-            DD_PUSH(a_low ? pos(cur, (ic + 1) % 3) : pos(cur, (ic + 2) % 3));
-            DD_ENTER_VERTEX(a_low ? av : bv, cur_id);
+        if (!scanning && t_next < 0) {     // boundary edge: slide to the lower endpoint
+            DD_SLIDE();
             continue;
         }
+        const int tl = scanning ? scan_t : t_next;
         const Tri T = load_tri(p.rec, tl);
         const float2 g = grads[tl];
+        // ---- shared rotated view: R = reference vertex, X = R+1, Y = R+2 (counter-clockwise)
+        const int refv = scanning ? v : eb;
+        const int L = local_of(T, refv), X = L == 2 ? 0 : L + 1, Y = L == 0 ? 2 : L - 1;
+        const float r0 = -dot2(T.g0, g), r1 = -dot2(T.g1, g), r2 = -(r0 + r1);   // d(lambda_i)/ds along -g
+        const float2 g2v = make_float2(-(T.g0.x + T.g1.x), -(T.g0.y + T.g1.y));
+        const float q0 = dot2(T.g0, T.g0), q1 = dot2(T.g1, T.g1), q2 = dot2(g2v, g2v);
+        const float gg = dot2(g, g);
+        const float rX = sel3f(X, r0, r1, r2), rY = sel3f(Y, r0, r1, r2);
+        const float qX = sel3f(X, q0, q1, q2), qY = sel3f(Y, q0, q1, q2);
+        const int vX = sel3i(X, T.v0, T.v1, T.v2), vY = sel3i(Y, T.v0, T.v1, T.v2);
+        const float2 pY = make_float2(sel3f(Y, T.p0.x, T.p1.x, T.p2.x), sel3f(Y, T.p0.y, T.p1.y, T.p2.y));
+        const int nL = sel3i(L, T.n0, T.n1, T.n2), nX = sel3i(X, T.n0, T.n1, T.n2), nY = sel3i(Y, T.n0, T.n1, T.n2);
         if (scanning) {
-            // ---- one triangle of the fan around v
-            const int i = local_of(T, v), j = (i + 1) % 3, k = (i + 2) % 3;
-            adj |= (T.v0 == target) | (T.v1 == target) | (T.v2 == target);
-            const float g2 = g.x * g.x + g.y * g.y;
-            if (g2 > 0.f) {
-                const float2 gj = gphi(T, j), gk = gphi(T, k);
-                const float aj = -dot2(gj, g), ak = -dot2(gk, g);
-                const float tol2 = eps2 * g2 * fmaxf(dot2(gj, gj), dot2(gk, gk));
-                const bool in_j = aj >= 0.f || aj * aj <= tol2;
-                const bool in_k = ak >= 0.f || ak * ak <= tol2;
-                if (in_j && in_k && aj + ak > 0.f && (g2 > best_g2 || (g2 == best_g2 && tl < best))) {
-                    best = tl;
-                    best_i = i;
-                    best_g2 = g2;
-                    baj = fmaxf(aj, 0.f);
-                    bak = fmaxf(ak, 0.f);
-                    best_T = T;
-                }
+            // ---- one triangle of the fan around v (v = R, the candidate exit edge is X-Y)
+            adj |= (vX == target) | (vY == target);
+            const float tol2 = eps2 * gg * fmaxf(qX, qY);
+            const bool in_x = rX >= 0.f || rX * rX <= tol2;
+            const bool in_y = rY >= 0.f || rY * rY <= tol2;
+            if (gg > 0.f && in_x && in_y && rX + rY > 0.f && (gg > best_g2 || (gg == best_g2 && tl < best))) {
+                best = tl;
+                best_g2 = gg;
+                baj = fmaxf(rX, 0.f);
+                bak = fmaxf(rY, 0.f);
+                b_vj = vX;
+                b_vk = vY;
+                b_pj = make_float2(sel3f(X, T.p0.x, T.p1.x, T.p2.x), sel3f(X, T.p0.y, T.p1.y, T.p2.y));
+                b_pk = pY;
+                b_next = nL;
             }
-            if (tl == t0) t0_cw = nid(T, k);
-            int next = ccw ? nid(T, j) : nid(T, k);
+            if (tl == t0) t0_cw = nY;
+            int next = ccw ? nX : nY;
             if (ccw && next == t0) {
                 next = -1;                       // closed fan: done
             } else if (ccw && next < 0) {
@@ -202,29 +221,30 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
                 scan_t = next;
                 continue;
             }
-            // fan complete
+            // ---- fan complete
             if (adj) {                           // v lies on an edge incident on the target
                 DD_PUSH(p.xy[target]);
                 status = DD_TRACE_OK;
                 goto done;
             }
             if (best >= 0) {
-                cur = best_T;
-                cur_id = best;
-                const int bj = (best_i + 1) % 3, bk = (best_i + 2) % 3;
                 const float s = __fdividef(1.0f, baj + bak);
                 const float lj = s * baj, lk = s * bak;
                 if (lj <= kEpsBary) {
-                    DD_PUSH(pos(cur, bk));
-                    DD_ENTER_VERTEX(vid(cur, bk), cur_id);
+                    DD_PUSH(b_pk);
+                    DD_ENTER_VERTEX(b_vk, best);
                 } else if (lk <= kEpsBary) {
-                    DD_PUSH(pos(cur, bj));
-                    DD_ENTER_VERTEX(vid(cur, bj), cur_id);
+                    DD_PUSH(b_pj);
+                    DD_ENTER_VERTEX(b_vj, best);
                 } else {
-                    const float2 pj = pos(cur, bj), pk = pos(cur, bk);
-                    DD_PUSH(make_float2(lj * pj.x + lk * pk.x, lj * pj.y + lk * pk.y));
+                    DD_PUSH(make_float2(lj * b_pj.x + lk * b_pk.x, lj * b_pj.y + lk * b_pk.y));
                     scanning = false;
-                    ic = best_i;
+                    cur_id = best;
+                    t_next = b_next;
+                    ea = b_vj;
+                    eb = b_vk;
+                    pa = b_pj;
+                    pb = b_pk;
                     la = lj;
                     lb = lk;
                     if (++states > p.max_steps) goto done;
@@ -266,66 +286,57 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
                 continue;
             }
         }
-        // ---- edge state: entering T (id tl) across the edge (av, bv) of cur
+        // ---- edge state: entering T across (ea, eb); ea = X, eb = R, the opposite vertex is Y
         {
-            const int ia0 = (ic + 1) % 3, ib0 = (ic + 2) % 3;
-            const int av = vid(cur, ia0), bv = vid(cur, ib0);
-            const int ia = local_of(T, av), ib = local_of(T, bv), c2 = 3 - ia - ib;
-            const float2 gc = gphi(T, c2);
-            const float rc = -dot2(gc, g);
-            bool slide = !(rc > 0.f && rc * rc > eps2 * dot2(g, g) * dot2(gc, gc));
-            float ra = 0.f, rb = 0.f, sa = INFINITY, sb = INFINITY;
-            if (!slide) {
-                ra = -dot2(gphi(T, ia), g);
-                rb = -dot2(gphi(T, ib), g);
-                sa = ra < 0.f ? __fdividef(la, -ra) : INFINITY;
-                sb = rb < 0.f ? __fdividef(lb, -rb) : INFINITY;
-                slide = !(fminf(sa, sb) < INFINITY);   // no exit edge: treat as a valley edge
-            }
-            if (slide) {               // valley edge: to the lower endpoint
-                const float fa = f[av], fb = f[bv];
-                const bool a_low = fa < fb || (fa == fb && av < bv);
-                DD_PUSH(a_low ? pos(cur, ia0) : pos(cur, ib0));
-                DD_ENTER_VERTEX(a_low ? av : bv, cur_id);
+            const float ra = rX, rb = sel3f(L, r0, r1, r2), rc = rY;
+            const bool enters = rc > 0.f && rc * rc > eps2 * gg * qY;
+            const float sa = ra < 0.f ? __fdividef(la, -ra) : INFINITY;
+            const float sb = rb < 0.f ? __fdividef(lb, -rb) : INFINITY;
+            if (!enters || !(fminf(sa, sb) < INFINITY)) {   // valley edge (or no exit): lower endpoint
+                DD_SLIDE();
                 continue;
             }
-            int exit_local, keep_local;    // exit through the edge opposite exit_local
-            float lkeep, lc2;
-            if (sa <= sb) {
-                lkeep = fmaxf(lb + sa * rb, 0.f);
-                lc2 = fmaxf(sa * rc, 0.f);
-                exit_local = ia;
-                keep_local = ib;
-            } else {
-                lkeep = fmaxf(la + sb * ra, 0.f);
-                lc2 = fmaxf(sb * rc, 0.f);
-                exit_local = ib;
-                keep_local = ia;
-            }
+            const bool via_a = sa <= sb;                      // exit through the edge opposite a (= Y-R edge)
+            const float s = via_a ? sa : sb;
+            float lkeep = fmaxf(via_a ? lb + s * rb : la + s * ra, 0.f);
+            float lc2 = fmaxf(s * rc, 0.f);
             const float inv = __fdividef(1.0f, lkeep + lc2);
             lkeep *= inv;
             lc2 *= inv;
+            const int keep_v = via_a ? eb : ea;
+            const float2 keep_p = via_a ? pb : pa;
             if (lkeep <= kEpsBary) {
-                DD_PUSH(pos(T, c2));
-                DD_ENTER_VERTEX(vid(T, c2), tl);
+                DD_PUSH(pY);
+                DD_ENTER_VERTEX(vY, tl);
                 continue;
             }
             if (lc2 <= kEpsBary) {
-                DD_PUSH(pos(T, keep_local));
-                DD_ENTER_VERTEX(vid(T, keep_local), tl);
+                DD_PUSH(keep_p);
+                DD_ENTER_VERTEX(keep_v, tl);
                 continue;
             }
-            const int e1 = (exit_local + 1) % 3, e2 = (exit_local + 2) % 3;
-            const float l1 = e1 == c2 ? lc2 : lkeep, l2 = e2 == c2 ? lc2 : lkeep;
-            const float2 p1 = pos(T, e1), p2 = pos(T, e2);
-            DD_PUSH(make_float2(l1 * p1.x + l2 * p2.x, l1 * p1.y + l2 * p2.y));
-            cur = T;
+            DD_PUSH(make_float2(lkeep * keep_p.x + lc2 * pY.x, lkeep * keep_p.y + lc2 * pY.y));
+            // new edge in T's counter-clockwise order: via a -> (Y, R) = (c, b); via b -> (X, Y) = (a, c)
             cur_id = tl;
-            ic = exit_local;
-            la = l1;
-            lb = l2;
+            if (via_a) {
+                t_next = nX;
+                ea = vY;
+                eb = keep_v;
+                pa = pY;
+                pb = keep_p;
+                la = lc2;
+                lb = lkeep;
+            } else {
+                t_next = nL;
+                ea = keep_v;
+                eb = vY;
+                pa = keep_p;
+                pb = pY;
+                la = lkeep;
+                lb = lc2;
+            }
             if (++states > p.max_steps) goto done;
-            if (vid(T, e1) == target || vid(T, e2) == target) {   // an edge incident on the target
+            if (ea == target || eb == target) {   // an edge incident on the target
                 DD_PUSH(p.xy[target]);
                 status = DD_TRACE_OK;
                 goto done;
@@ -335,6 +346,7 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
 done:
 #undef DD_PUSH
 #undef DD_ENTER_VERTEX
+#undef DD_SLIDE
     p.out_len[id] = len;
     p.out_status[id] = status;
 }
