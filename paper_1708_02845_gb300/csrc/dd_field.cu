@@ -6,24 +6,30 @@
 // Near the target the two logarithms agree to many digits and KL is a small
 // sum of nearly-cancelling terms, so each log is kept as an exact split
 //   log p = E ln2 + lm,   E integer,  lm = log(m) for the mantissa m in [1/sqrt2, sqrt2)
-// and the difference is formed as (lm_x - lm_t) + (E_x - E_t) ln2: the mantissa
-// logs carry relative (not absolute) error, the exponent difference is exact,
-// and x = t gives exactly 0 (the same code runs on both operands).  lm uses
-// the series log m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9),
-// s = (m - 1)/(m + 1), |s| <= 0.1716, truncation error below 2e-9 relative.
-// Every step uses explicit round-to-nearest intrinsics so all call sites
-// produce bit-identical values.  Arguments below FLT_MIN (including the
-// 0 log 0 terms, whose weight P[x,b] is 0) are evaluated at FLT_MIN.
+// and the difference is formed as (lm_x - lm_t) + (E_x - E_t) ln2: |lm| <= 0.35
+// carries a small absolute error, the exponent difference is exact, and x = t
+// gives exactly 0 (the same code runs on both operands).  lm is table driven
+// (Tang, "Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic", ACM TOMS 1990): a 128-entry table of
+// r_j = 1/c_j and log c_j over [1/2, 2), u = m r_j - 1 (|u| <= 1/128, one
+// rounding) and log(1 + u) from its degree-4 Taylor polynomial (truncation
+// below 1e-11).  The table is computed in FP64 by each CTA.  Every step uses
+// explicit round-to-nearest operations so all call sites produce bit-identical
+// values.  Arguments below FLT_MIN (including the 0 log 0 terms, whose weight
+// P[x,b] is 0) are evaluated at FLT_MIN.
 //
 // Two kernels:
 //  * field_stream (few targets): one warp per row, lanes along b, 16-byte
-//    loads of P, the target rows staged in shared memory by a bulk async
-//    copy completing on an mbarrier, warp-shuffle reductions.  HBM-bound.
+//    loads of P software-pipelined U float4 per lane ahead of the arithmetic,
+//    the target row and its logs staged in shared memory by a bulk async copy
+//    completing on an mbarrier, warp-shuffle reductions.  HBM-bound.
 //  * field_tile (many targets): 64 rows x 64 targets per CTA, b in chunks of
 //    32 staged through shared memory, 4 x 4 register micro-tiles.  Each P
 //    element's logarithm is computed once per CTA and reused for 64 targets.
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
+#include <cstdlib>
 
 #include "dd_internal.h"
 
@@ -55,61 +61,46 @@ __device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
-constexpr float kC3 = 2.0f / 3.0f, kC5 = 2.0f / 5.0f, kC7 = 2.0f / 7.0f, kC9 = 2.0f / 9.0f;
+constexpr int kLogTab = 128;                     // entries over [1/2, 2): 64 per binade
 constexpr int kMagicE = 0x4B400000;              // float 12582912 = 1.5 * 2^23: + e keeps e exact
 constexpr float kMagicEf = 12582912.0f;
 
-// split logarithm of max(p, FLT_MIN): log = E ln2 + lm.  The reciprocal is a
-// hardware approximation refined by one Newton step; every other step is an
-// IEEE round-to-nearest operation, and split_log2 below performs the same
-// operations lane by lane, so both give bit-identical results.
-__device__ __forceinline__ void split_log(float p, float &lm, float &E) {
-    p = fmaxf(p, FLT_MIN);
-    const int i = __float_as_int(p);
-    const int e = (i - 0x3f3504f3) >> 23;            // m = p 2^-e in [1/sqrt2, sqrt2)
-    const float m = __int_as_float(i - (e << 23));
-    E = __fadd_rn(__int_as_float(e + kMagicE), -kMagicEf);
-    const float u = __fadd_rn(m, -1.0f);              // exact (Sterbenz)
-    const float v = __fadd_rn(m, 1.0f);
-    float r = rcp_approx(v);
-    const float er = __fmaf_rn(__fmaf_rn(m, -1.0f, -1.0f), r, 1.0f);
-    r = __fmaf_rn(r, er, r);
-    const float s = __fmul_rn(u, r);
-    const float z = __fmul_rn(s, s);
-    float q = __fmaf_rn(z, kC9, kC7);
-    q = __fmaf_rn(q, z, kC5);
-    q = __fmaf_rn(q, z, kC3);
-    lm = __fmaf_rn(__fmul_rn(s, z), q, __fadd_rn(s, s));
+// table entry j covers the mantissa range of float bits 17..23 == j (m in [1/2, 2)):
+// c_j is the range's midpoint, r_j = 1/c_j rounded, L_j = -log r_j
+__device__ __forceinline__ void build_log_table(float2 *tab) {
+    for (int j = threadIdx.x; j < kLogTab; j += blockDim.x) {
+        const double c = j < 64 ? 0.5 + (j + 0.5) / 128.0 : 1.0 + (j - 64 + 0.5) / 64.0;
+        const float r = (float)(1.0 / c);
+        tab[j] = make_float2(r, (float)(-log((double)r)));
+    }
 }
 
-// the same for two values at once (packed lanes)
-__device__ __forceinline__ void split_log2(float p0, float p1, f2_t &lm, f2_t &E) {
+// split logarithm of max(p, FLT_MIN): log = E ln2 + lm, m = p 2^-E in [1/sqrt2, sqrt2)
+__device__ __forceinline__ void split_log(float p, const float2 *tab, float &lm, float &E) {
+    p = fmaxf(p, FLT_MIN);
+    const int i = __float_as_int(p);
+    const int e = (i - 0x3f3504f3) >> 23;
+    const int mb = i - (e << 23);
+    E = __fadd_rn(__int_as_float(e + kMagicE), -kMagicEf);
+    const float2 t = tab[(mb >> 17) & (kLogTab - 1)];
+    const float u = __fmaf_rn(__int_as_float(mb), t.x, -1.0f);          // m/c - 1, one rounding
+    const float w = __fmaf_rn(__fmaf_rn(u, -0.25f, 1.0f / 3.0f), u, -0.5f);
+    lm = __fadd_rn(t.y, __fmaf_rn(__fmul_rn(u, u), w, u));             // log c + log(1 + u)
+}
+
+// the same for two values at once (packed lanes; bit-identical to split_log)
+__device__ __forceinline__ void split_log2(float p0, float p1, const float2 *tab, f2_t &lm, f2_t &E) {
     p0 = fmaxf(p0, FLT_MIN);
     p1 = fmaxf(p1, FLT_MIN);
     const int i0 = __float_as_int(p0), i1 = __float_as_int(p1);
     const int e0 = (i0 - 0x3f3504f3) >> 23, e1 = (i1 - 0x3f3504f3) >> 23;
-    const f2_t m = pk(__int_as_float(i0 - (e0 << 23)), __int_as_float(i1 - (e1 << 23)));
-    const f2_t one = pk(1.0f, 1.0f), mone = pk(-1.0f, -1.0f);
+    const int mb0 = i0 - (e0 << 23), mb1 = i1 - (e1 << 23);
     E = add2(pk(__int_as_float(e0 + kMagicE), __int_as_float(e1 + kMagicE)), pk(-kMagicEf, -kMagicEf));
-    const f2_t u = add2(m, mone);
-    const f2_t v = add2(m, one);
-    float v0, v1;
-    upk(v, v0, v1);
-    f2_t r = pk(rcp_approx(v0), rcp_approx(v1));
-    const f2_t er = fma2(fma2(m, mone, mone), r, one);
-    r = fma2(r, er, r);
-    const f2_t sv = mul2(u, r);
-    const f2_t z = mul2(sv, sv);
-    f2_t q = fma2(z, pk(kC9, kC9), pk(kC7, kC7));
-    q = fma2(q, z, pk(kC5, kC5));
-    q = fma2(q, z, pk(kC3, kC3));
-    lm = fma2(mul2(sv, z), q, add2(sv, sv));
+    const float2 t0 = tab[(mb0 >> 17) & (kLogTab - 1)], t1 = tab[(mb1 >> 17) & (kLogTab - 1)];
+    const f2_t u = fma2(pk(__int_as_float(mb0), __int_as_float(mb1)), pk(t0.x, t1.x), pk(-1.0f, -1.0f));
+    const f2_t w = fma2(fma2(u, pk(-0.25f, -0.25f), pk(1.0f / 3.0f, 1.0f / 3.0f)), u, pk(-0.5f, -0.5f));
+    lm = add2(pk(t0.y, t1.y), fma2(mul2(u, u), w, u));
 }
 
 // one term of each sum; accumulators updated in place
@@ -138,12 +129,15 @@ __device__ __forceinline__ void accumulate2(f2_t px, f2_t lmx, f2_t ex, f2_t pt,
 __global__ void stage_targets_kernel(const float *__restrict__ P, int64_t k_pad, const int32_t *__restrict__ targets,
                                      int32_t T, float *__restrict__ sP, float *__restrict__ sL,
                                      float *__restrict__ sE) {
+    __shared__ float2 tab[kLogTab];
+    build_log_table(tab);
+    __syncthreads();
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
     if (b >= k_pad || a >= T) return;
     const float p = P[(int64_t)targets[a] * k_pad + b];
     float lm, E;
-    split_log(p, lm, E);
+    split_log(p, tab, lm, E);
     sP[(int64_t)a * k_pad + b] = p;
     sL[(int64_t)a * k_pad + b] = lm;
     sE[(int64_t)a * k_pad + b] = E;
@@ -163,15 +157,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
 
 // bulk global -> shared copy (no tensor map, no multicast); size multiple of 16
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -182,11 +167,30 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-constexpr uint32_t kMaxWaitIters = 1u << 26;   // bounded spin; then the error flag is set
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr uint32_t kWaitLimit = 1u << 25;   // bounded spins of a non-suspending test (about a second)
+
+// bounded wait: true when the phase completed; false (error flag set) when the limit expired
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i)
+        if (mbar_test(bar, parity)) return true;
+    atomicExch(err, 1);
+    return false;
+}
+
 
 // ------------------------------------------------------------------ few targets
 // smem: for each of TT targets, three k_pad float arrays (P, lm, E); grid.y walks target groups.
-template <int TT>
+template <int TT, int U>
 __global__ void __launch_bounds__(256) field_stream_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
                                                            const float *__restrict__ sP, const float *__restrict__ sL,
                                                            const float *__restrict__ sE, int32_t T,
@@ -194,6 +198,8 @@ __global__ void __launch_bounds__(256) field_stream_kernel(const float *__restri
                                                            int *__restrict__ err_flag) {
     extern __shared__ __align__(16) float smem[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ float2 tab[kLogTab];
+    build_log_table(tab);
     const int a0 = blockIdx.y * TT;
     const int nt = (T - a0) < TT ? (T - a0) : TT;
     float *tP = smem;                          // [TT][k_pad]
@@ -213,19 +219,10 @@ __global__ void __launch_bounds__(256) field_stream_kernel(const float *__restri
             bulk_g2s(tE + j * k_pad, sE + (int64_t)(a0 + j) * k_pad, row_bytes, &bar);
         }
     }
-    uint32_t it = 0;
-    while (!mbar_try_wait(&bar, 0)) {
-        if (++it == kMaxWaitIters) {
-            atomicExch(err_flag, 1);
-            break;
-        }
-    }
-    // a CTA whose wait gave up must not return while its copies may still land;
-    // wait once more (also bounded) before touching the data or exiting
-    if (it == kMaxWaitIters) {
-        uint32_t it2 = 0;
-        while (!mbar_try_wait(&bar, 0) && ++it2 < kMaxWaitIters) {
-        }
+    if (!mbar_wait(&bar, 0, err_flag)) {
+        // a CTA whose wait gave up must not return while its copies may still land:
+        // wait once more (also bounded) before exiting
+        mbar_wait(&bar, 0, err_flag);
         return;
     }
 
@@ -233,7 +230,6 @@ __global__ void __launch_bounds__(256) field_stream_kernel(const float *__restri
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nvec = k_pad >> 2;                       // float4 per row
-    constexpr int U = 4;                                   // float4 per lane per chunk
     const int64_t nchunk = (nvec + 32 * U - 1) / (32 * U);
     // software pipeline over (row, chunk): the loads of the next chunk are in
     // flight while the current one is computed
@@ -266,8 +262,8 @@ __global__ void __launch_bounds__(256) field_stream_kernel(const float *__restri
             const int64_t c = ch * 32 * U + u * 32 + lane;
             if (c >= nvec) continue;
             f2_t lm01, e01, lm23, e23;
-            split_log2(cur[u].x, cur[u].y, lm01, e01);
-            split_log2(cur[u].z, cur[u].w, lm23, e23);
+            split_log2(cur[u].x, cur[u].y, tab, lm01, e01);
+            split_log2(cur[u].z, cur[u].w, tab, lm23, e23);
             const f2_t p01 = pk(cur[u].x, cur[u].y), p23 = pk(cur[u].z, cur[u].w);
 #pragma unroll
             for (int j = 0; j < TT; ++j) {
@@ -310,12 +306,18 @@ __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restr
                                                          const float *__restrict__ sP, const float *__restrict__ sL,
                                                          const float *__restrict__ sE, int32_t T,
                                                          float *__restrict__ out_kl, float *__restrict__ out_tv) {
-    __shared__ __align__(16) float xP[kTileB][kTileRows];
-    __shared__ __align__(16) float xL[kTileB][kTileRows];
-    __shared__ __align__(16) float xE[kTileB][kTileRows];
-    __shared__ __align__(16) float yP[kTileB][kTileTargets];
-    __shared__ __align__(16) float yL[kTileB][kTileTargets];
-    __shared__ __align__(16) float yE[kTileB][kTileTargets];
+    extern __shared__ __align__(16) float tsm[];
+    float (*xP)[kTileRows] = reinterpret_cast<float (*)[kTileRows]>(tsm);
+    float (*xL)[kTileRows] = reinterpret_cast<float (*)[kTileRows]>(tsm + 1 * kTileB * kTileRows);
+    float (*xE)[kTileRows] = reinterpret_cast<float (*)[kTileRows]>(tsm + 2 * kTileB * kTileRows);
+    float (*yP)[kTileTargets] = reinterpret_cast<float (*)[kTileTargets]>(tsm + 3 * kTileB * kTileRows);
+    float (*yL)[kTileTargets] =
+        reinterpret_cast<float (*)[kTileTargets]>(tsm + 3 * kTileB * kTileRows + 1 * kTileB * kTileTargets);
+    float (*yE)[kTileTargets] =
+        reinterpret_cast<float (*)[kTileTargets]>(tsm + 3 * kTileB * kTileRows + 2 * kTileB * kTileTargets);
+    float2 *tab = reinterpret_cast<float2 *>(tsm + 3 * kTileB * (kTileRows + kTileTargets));
+    build_log_table(tab);
+    __syncthreads();
 
     const int tid = threadIdx.x;
     const int tx = tid & 15;          // target group: targets tx*4 .. tx*4+3
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restr
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 float lm, E;
-                split_log(vals[e], lm, E);
+                split_log(vals[e], tab, lm, E);
                 xP[cb + e][r] = vals[e];
                 xL[cb + e][r] = lm;
                 xE[cb + e][r] = E;
@@ -426,6 +428,17 @@ __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restr
 
 int g_num_sms = 0;
 
+// prefetch depth of the streaming kernel (float4 per lane in flight): 8 unless
+// DD_STREAM_UNROLL=4 asks for the shallower variant
+int stream_unroll() {
+    static int u = 0;
+    if (u == 0) {
+        const char *e = getenv("DD_STREAM_UNROLL");
+        u = (e && atoi(e) == 4) ? 4 : 8;
+    }
+    return u;
+}
+
 int num_sms() {
     if (g_num_sms == 0) {
         int dev = 0;
@@ -452,23 +465,32 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
     const float *sP = reinterpret_cast<const float *>(stage);
     const float *sL = sP + (int64_t)T * k_pad;
     const float *sE = sL + (int64_t)T * k_pad;
-    if (T <= 2) {
-        constexpr int TT = 1;
-        const size_t smem = 3 * TT * (size_t)k_pad * sizeof(float);
-        cudaFuncSetAttribute(field_stream_kernel<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, field_stream_kernel<TT>, 256, smem);
-        if (per_sm < 1) per_sm = 1;
+    if (T <= 2 && 3 * (size_t)k_pad * sizeof(float) <= 200 * 1024) {
+        // one target per grid row; loads run `U` float4 per lane ahead of the arithmetic
+        const size_t smem = 3 * (size_t)k_pad * sizeof(float);
+        const int U = stream_unroll();
         int64_t rows_blocks = (n_v + 7) / 8;
-        int64_t grid_x = (int64_t)num_sms() * per_sm / T;
-        if (grid_x < 1) grid_x = 1;
-        if (grid_x > rows_blocks) grid_x = rows_blocks;
-        dim3 g((unsigned)grid_x, (unsigned)T);
-        field_stream_kernel<TT><<<g, 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, err_flag);
+        auto go = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+            if (per_sm < 1) per_sm = 1;
+            int64_t grid_x = (int64_t)num_sms() * per_sm / T;
+            if (grid_x < 1) grid_x = 1;
+            if (grid_x > rows_blocks) grid_x = rows_blocks;
+            kern<<<dim3((unsigned)grid_x, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv,
+                                                                       err_flag);
+        };
+        if (U == 8)
+            go(field_stream_kernel<1, 8>);
+        else
+            go(field_stream_kernel<1, 4>);
         return;
     }
     dim3 g((unsigned)((n_v + kTileRows - 1) / kTileRows), (unsigned)((T + kTileTargets - 1) / kTileTargets));
-    field_tile_kernel<<<g, 256, 0, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv);
+    const int tile_smem = (int)(3 * kTileB * (kTileRows + kTileTargets) * sizeof(float) + kLogTab * sizeof(float2));
+    cudaFuncSetAttribute(field_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem);
+    field_tile_kernel<<<g, 256, tile_smem, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv);
 }
 
 size_t field_smem_limit_ok(int64_t k_pad) { return 3 * (size_t)k_pad * sizeof(float); }
