@@ -200,6 +200,35 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
                    uint32_t trace_f, int32_t max_pts, float *out_fields,
                    float *out_xy, int32_t *out_len, int32_t *out_status);
 
+/* Fields and paths for targets on several loaded meshes in one pass (a batch
+ * of uneven domains).  Item i is mesh mesh_ids[i] with T_per[i] targets; the
+ * fields of all items are computed by one persistent launch whose tile shape
+ * per item is chosen by the autotuner (dd_tuning_table), then the paths of
+ * all items by one tracer launch.  Same arithmetic as dd_query with FP32.
+ *   n_items   number of items (>= 1)
+ *   mesh_ids  host [n_items] loaded meshes with a Poisson kernel
+ *   T_per     host [n_items] targets per item (>= 1)
+ *   targets   host [sum T] interior vertex ids, item after item
+ *   sources   host [sum T][S] vertex ids (ignored when S = 0)
+ *   S         sources per target (0: fields only)
+ *   f_mask    DD_F_KL | DD_F_TV;  trace_f: one bit of f_mask (when S > 0)
+ *   out_fields  device or host float32: item i's block [nf][T_i][n_i] starts
+ *             at sum_{j<i} nf T_j n_j
+ *   out_xy, out_len, out_status  as dd_trace_fields over sum T x S paths in
+ *             target order (may be NULL when S = 0)
+ * The first call that meets a new (size, k, T) class runs timed launches of
+ * each tile shape before the batch.  Errors: DD_EINVAL, DD_ESTATE, DD_ENOMEM,
+ * DD_ECUDA, DD_ETIMEOUT. */
+dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, const int32_t *T_per,
+                         const int32_t *targets, const int32_t *sources, int32_t S, uint32_t f_mask,
+                         uint32_t trace_f, int32_t max_pts, float *out_fields, float *out_xy,
+                         int32_t *out_len, int32_t *out_status);
+
+/* The autotuner's decisions so far as text, one line per size class
+ * ("rows<=2^r k_pad<=2^c T<=2^t: 64x64").  Writes at most len bytes (NUL
+ * terminated) into buf (may be NULL) and returns the full length. */
+int32_t dd_tuning_table(char *buf, int32_t len);
+
 /* dd_distance without any device allocation.  The paper has no counterpart:
  * this is a deployment variant of dd_distance for callers that may not call
  * cudaMalloc -- e.g. a robot's real-time control loop that allocates only at

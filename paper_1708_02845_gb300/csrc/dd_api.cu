@@ -2,6 +2,7 @@
 // Every entry point returns a dd_status and never lets a C++ exception out.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -12,7 +13,7 @@
 
 namespace {
 
-enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_COUNT };
+enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_META, S_COUNT };
 
 struct MeshSlot {
     bool live = false;
@@ -617,6 +618,215 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
         return DD_OK;
     } catch (...) {
         return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
+
+namespace {
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+}  // namespace
+
+dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, const int32_t *T_per,
+                         const int32_t *targets, const int32_t *sources, int32_t S, uint32_t f_mask, uint32_t trace_f,
+                         int32_t max_pts, float *out_fields, float *out_xy, int32_t *out_len, int32_t *out_status) {
+    if (!ctx) return DD_EINVAL;
+    try {
+        if (n_items < 1 || !mesh_ids || !T_per) return set_err(ctx, DD_EINVAL, "need at least one item");
+        if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV))) return set_err(ctx, DD_EINVAL, "bad f_mask");
+        if (S < 0) return set_err(ctx, DD_EINVAL, "S must be >= 0");
+        if (S > 0) {
+            if ((trace_f != DD_F_KL && trace_f != DD_F_TV) || !(f_mask & trace_f))
+                return set_err(ctx, DD_EINVAL, "trace_f must be one bit of f_mask");
+            dd_status st = check_path_args(ctx, S, max_pts, out_xy, out_len, out_status);
+            if (st != DD_OK) return st;
+        }
+        if (!out_fields) return set_err(ctx, DD_EINVAL, "out_fields is null");
+        const int nf = popcount2(f_mask);
+        std::vector<DevMesh *> ms(n_items);
+        std::vector<int64_t> foff(n_items + 1, 0), toff(n_items + 1, 0);
+        int64_t stage_floats = 0, grad_pairs = 0, max_nt = 0, max_k = 0;
+        for (int i = 0; i < n_items; ++i) {
+            dd_status st = get_mesh(ctx, mesh_ids[i], &ms[i]);
+            if (st != DD_OK) return st;
+            if (!ms[i]->has_P) return set_err(ctx, DD_ESTATE, "item " + std::to_string(i) + " has no Poisson kernel");
+            if (T_per[i] < 1) return set_err(ctx, DD_EINVAL, "every item needs T >= 1");
+            toff[i + 1] = toff[i] + T_per[i];
+            foff[i + 1] = foff[i] + (int64_t)nf * T_per[i] * ms[i]->n_v;
+            stage_floats += 3LL * T_per[i] * ms[i]->k_pad;
+            grad_pairs += (int64_t)T_per[i] * ms[i]->n_t;
+            max_nt = std::max(max_nt, ms[i]->n_t);
+            max_k = std::max(max_k, ms[i]->k_pad);
+        }
+        const int32_t nT = (int32_t)toff[n_items];
+        if (!targets || pointer_space(ctx, targets) != 0) return set_err(ctx, DD_EINVAL, "targets must be host memory");
+        for (int i = 0; i < n_items; ++i) {
+            dd_status st = check_targets(ctx, *ms[i], targets + toff[i], T_per[i], true, "targets");
+            if (st != DD_OK) return st;
+            if (S > 0 && (st = check_targets(ctx, *ms[i], sources + toff[i] * S, (int64_t)T_per[i] * S, false,
+                                             "sources")) != DD_OK)
+                return st;
+        }
+        const int sf = pointer_space(ctx, out_fields);
+        if (sf < 0) return set_err(ctx, DD_EINVAL, "out_fields is on another device");
+        dd_status st = select_device(ctx);
+        if (st != DD_OK) return st;
+
+        // metadata block: tprob, tloc, problems, items, trace domains, counter
+        std::vector<int32_t> tprob(nT), tloc(nT);
+        for (int i = 0; i < n_items; ++i)
+            for (int a = 0; a < T_per[i]; ++a) {
+                tprob[toff[i] + a] = i;
+                tloc[toff[i] + a] = a;
+            }
+        if ((st = upload(ctx, S_TARGETS, targets, (size_t)nT * sizeof(int32_t))) != DD_OK) return st;
+        if (S > 0 && (st = upload(ctx, S_SOURCES, sources, (size_t)nT * S * sizeof(int32_t))) != DD_OK) return st;
+        const size_t out_bytes = (size_t)foff[n_items] * sizeof(float);
+        float *dfields = out_fields;
+        if (sf == 0) {
+            if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
+            dfields = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
+        }
+        if ((st = ensure_scratch(ctx, S_STAGE, (size_t)stage_floats * sizeof(float))) != DD_OK) return st;
+        if (S > 0 && (st = ensure_scratch(ctx, S_GRAD, (size_t)grad_pairs * sizeof(float2))) != DD_OK) return st;
+        float *stage = reinterpret_cast<float *>(ctx->scratch[S_STAGE]);
+        float2 *grads = reinterpret_cast<float2 *>(ctx->scratch[S_GRAD]);
+
+        std::vector<BatchProblem> probs(n_items);
+        int64_t so = 0;
+        for (int i = 0; i < n_items; ++i) {
+            BatchProblem &q = probs[i];
+            const DevMesh &m = *ms[i];
+            const int64_t blk = (int64_t)T_per[i] * m.k_pad;
+            q.P = m.P;
+            q.n_v = m.n_v;
+            q.k_pad = m.k_pad;
+            q.sP = stage + so;
+            q.sL = stage + so + blk;
+            q.sE = stage + so + 2 * blk;
+            so += 3 * blk;
+            q.T = T_per[i];
+            q.variant = 0;
+            float *base = dfields + foff[i];
+            q.out_kl = (f_mask & DD_F_KL) ? base : nullptr;
+            q.out_tv = (f_mask & DD_F_TV) ? base + ((f_mask & DD_F_KL) ? (int64_t)T_per[i] * m.n_v : 0) : nullptr;
+        }
+        const size_t o_tprob = 0, o_tloc = align256(nT * sizeof(int32_t));
+        const size_t o_probs = o_tloc + align256(nT * sizeof(int32_t));
+        const size_t o_doms = o_probs + align256(n_items * sizeof(BatchProblem));
+        const size_t dom_bytes = batch_trace_dom_bytes();
+        const size_t o_counter = o_doms + align256(n_items * dom_bytes);
+        const size_t o_items = o_counter + 256;
+        // stage all targets first (the autotuner times shapes on the staged data)
+        std::vector<uint8_t> meta(o_items);
+        std::memcpy(meta.data() + o_tprob, tprob.data(), nT * sizeof(int32_t));
+        std::memcpy(meta.data() + o_tloc, tloc.data(), nT * sizeof(int32_t));
+        std::memcpy(meta.data() + o_probs, probs.data(), n_items * sizeof(BatchProblem));
+        if ((st = upload(ctx, S_META, meta.data(), meta.size())) != DD_OK) return st;
+        uint8_t *dmeta = reinterpret_cast<uint8_t *>(ctx->scratch[S_META]);
+        launch_batch_stage(reinterpret_cast<const BatchProblem *>(dmeta + o_probs),
+                           reinterpret_cast<const int32_t *>(dmeta + o_tprob),
+                           reinterpret_cast<const int32_t *>(dmeta + o_tloc),
+                           reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), nT, max_k, ctx->stream);
+        CK(cudaGetLastError(), "batch staging launch");
+        for (int i = 0; i < n_items; ++i)
+            probs[i].variant = tile_variant_for(probs[i].P, probs[i].n_v, probs[i].k_pad, probs[i].sP, probs[i].sL,
+                                                probs[i].sE, probs[i].T, probs[i].out_kl, probs[i].out_tv, ctx->stream);
+        // items: every output tile, larger row extents first for balance
+        std::vector<std::pair<int64_t, BatchItem>> order;
+        for (int i = 0; i < n_items; ++i) {
+            const int tr = tile_rows(probs[i].variant), tt = tile_targets(probs[i].variant);
+            const int64_t cost = ms[i]->k_pad * tr * (int64_t)tt;
+            for (int64_t xt = 0; xt * tr < ms[i]->n_v; ++xt)
+                for (int at = 0; at * tt < T_per[i]; ++at) order.push_back({cost, BatchItem{i, (int32_t)xt, at, 0}});
+        }
+        std::stable_sort(order.begin(), order.end(),
+                         [](const std::pair<int64_t, BatchItem> &x, const std::pair<int64_t, BatchItem> &y) {
+                             return x.first > y.first;
+                         });
+        meta.resize(o_items + order.size() * sizeof(BatchItem));
+        std::memcpy(meta.data() + o_probs, probs.data(), n_items * sizeof(BatchProblem));
+        // trace domains; gradients per item in consecutive blocks [T_i][n_t_i]
+        {
+            int64_t go = 0;
+            for (int i = 0; i < n_items; ++i) {
+                fill_batch_trace_dom(meta.data() + o_doms + i * dom_bytes, *ms[i],
+                                     (trace_f == DD_F_TV && probs[i].out_tv) ? probs[i].out_tv : probs[i].out_kl,
+                                     grads + go);
+                go += (int64_t)T_per[i] * ms[i]->n_t;
+            }
+        }
+        for (size_t j = 0; j < order.size(); ++j)
+            std::memcpy(meta.data() + o_items + j * sizeof(BatchItem), &order[j].second, sizeof(BatchItem));
+        if ((st = upload(ctx, S_META, meta.data(), meta.size())) != DD_OK) return st;
+        dmeta = reinterpret_cast<uint8_t *>(ctx->scratch[S_META]);
+        launch_batch_fields(reinterpret_cast<const BatchProblem *>(dmeta + o_probs),
+                            reinterpret_cast<const BatchItem *>(dmeta + o_items), (int32_t)order.size(),
+                            reinterpret_cast<int32_t *>(dmeta + o_counter), ctx->stream);
+        CK(cudaGetLastError(), "batch field launch");
+        bool host = false;
+        if (sf == 0) {
+            CK(cudaMemcpyAsync(out_fields, dfields, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy fields");
+            host = true;
+        }
+        if (S > 0) {
+            const int sx = pointer_space(ctx, out_xy), sl = pointer_space(ctx, out_len),
+                      ss = pointer_space(ctx, out_status);
+            if (sx < 0 || sl < 0 || ss < 0) return set_err(ctx, DD_EINVAL, "path outputs on another device");
+            const size_t n = (size_t)nT * S;
+            float2 *dxy = reinterpret_cast<float2 *>(out_xy);
+            int32_t *dlen = out_len, *dst = out_status;
+            if (sx == 0) {
+                if ((st = ensure_scratch(ctx, S_XY, n * max_pts * sizeof(float2))) != DD_OK) return st;
+                dxy = reinterpret_cast<float2 *>(ctx->scratch[S_XY]);
+            }
+            if (sl == 0) {
+                if ((st = ensure_scratch(ctx, S_LEN, n * sizeof(int32_t))) != DD_OK) return st;
+                dlen = reinterpret_cast<int32_t *>(ctx->scratch[S_LEN]);
+            }
+            if (ss == 0) {
+                if ((st = ensure_scratch(ctx, S_STATUS, n * sizeof(int32_t))) != DD_OK) return st;
+                dst = reinterpret_cast<int32_t *>(ctx->scratch[S_STATUS]);
+            }
+            launch_batch_trace(dmeta + o_doms, reinterpret_cast<const int32_t *>(dmeta + o_tprob),
+                               reinterpret_cast<const int32_t *>(dmeta + o_tloc),
+                               reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
+                               reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), nT, S, max_nt, max_pts, dxy,
+                               dlen, dst, ctx->stream);
+            CK(cudaGetLastError(), "batch trace launch");
+            if (sx == 0) {
+                CK(cudaMemcpyAsync(out_xy, dxy, n * max_pts * sizeof(float2), cudaMemcpyDeviceToHost, ctx->stream),
+                   "copy paths");
+                host = true;
+            }
+            if (sl == 0) {
+                CK(cudaMemcpyAsync(out_len, dlen, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "copy len");
+                host = true;
+            }
+            if (ss == 0) {
+                CK(cudaMemcpyAsync(out_status, dst, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
+                   "copy status");
+                host = true;
+            }
+        }
+        if (host) {
+            CK(cudaStreamSynchronize(ctx->stream), "batch query");
+            return check_kernel_flag(ctx);
+        }
+        return DD_OK;
+    } catch (const std::bad_alloc &) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    } catch (...) {
+        return set_err(ctx, DD_EINVAL, "unexpected failure in dd_query_batch");
+    }
+}
+
+int32_t dd_tuning_table(char *buf, int32_t len) {
+    try {
+        const std::string t = tuning_table();
+        if (buf && len > 0) std::snprintf(buf, (size_t)len, "%s", t.c_str());
+        return (int32_t)t.size();
+    } catch (...) {
+        return -1;
     }
 }
 

@@ -27,6 +27,11 @@
 //    32 staged through shared memory, 4 x 4 register micro-tiles.  Each P
 //    element's logarithm is computed once per CTA and reused for 64 targets.
 #include <algorithm>
+#include <string>
+#include <cstdio>
+#include <tuple>
+#include <mutex>
+#include <map>
 #include <cfloat>
 #include <cstdint>
 #include <cstdlib>
@@ -300,110 +305,119 @@ __global__ void __launch_bounds__(256) field_stream_kernel(const float *__restri
 }
 
 // ------------------------------------------------------------------ many targets
-constexpr int kTileRows = 64, kTileTargets = 64, kTileB = 32;
+// Tile shapes: TM rows x TN targets per CTA, 256 threads arranged as
+// (TM/RM) row groups x (TN/CN) target groups, each thread an RM x CN micro-tile.
+// b runs in chunks of BK = 32 staged through shared memory.  Wide target
+// tiles suit many targets; tall row tiles waste less on few targets.
+constexpr int kTileB = 32;
 
-__global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
-                                                         const float *__restrict__ sP, const float *__restrict__ sL,
-                                                         const float *__restrict__ sE, int32_t T,
-                                                         float *__restrict__ out_kl, float *__restrict__ out_tv) {
-    extern __shared__ __align__(16) float tsm[];
-    float (*xP)[kTileRows] = reinterpret_cast<float (*)[kTileRows]>(tsm);
-    float (*xL)[kTileRows] = reinterpret_cast<float (*)[kTileRows]>(tsm + 1 * kTileB * kTileRows);
-    float (*xE)[kTileRows] = reinterpret_cast<float (*)[kTileRows]>(tsm + 2 * kTileB * kTileRows);
-    float (*yP)[kTileTargets] = reinterpret_cast<float (*)[kTileTargets]>(tsm + 3 * kTileB * kTileRows);
-    float (*yL)[kTileTargets] =
-        reinterpret_cast<float (*)[kTileTargets]>(tsm + 3 * kTileB * kTileRows + 1 * kTileB * kTileTargets);
-    float (*yE)[kTileTargets] =
-        reinterpret_cast<float (*)[kTileTargets]>(tsm + 3 * kTileB * kTileRows + 2 * kTileB * kTileTargets);
-    float2 *tab = reinterpret_cast<float2 *>(tsm + 3 * kTileB * (kTileRows + kTileTargets));
-    build_log_table(tab);
-    __syncthreads();
+template <int TM, int TN, int RM, int CN>
+struct TileShape {
+    static constexpr int ROWG = TM / RM, COLG = TN / CN;
+    static_assert(ROWG * COLG == 256, "256 threads");
+    static constexpr size_t smem_bytes = (3 * kTileB * (TM + TN)) * sizeof(float) + kLogTab * sizeof(float2);
+};
 
+// one output tile (rows x0.., targets a0..) of one problem; tsm holds the
+// staging arrays followed by the log table (built by the caller)
+template <int TM, int TN, int RM, int CN>
+__device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
+                                          const float *__restrict__ sP, const float *__restrict__ sL,
+                                          const float *__restrict__ sE, int32_t T, float *__restrict__ out_kl,
+                                          float *__restrict__ out_tv, int64_t x0, int a0, float *tsm,
+                                          const float2 *tab) {
+    constexpr int COLG = TN / CN;
+    float (*xP)[TM] = reinterpret_cast<float (*)[TM]>(tsm);
+    float (*xL)[TM] = reinterpret_cast<float (*)[TM]>(tsm + 1 * kTileB * TM);
+    float (*xE)[TM] = reinterpret_cast<float (*)[TM]>(tsm + 2 * kTileB * TM);
+    float (*yP)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 3 * kTileB * TM);
+    float (*yL)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 3 * kTileB * TM + 1 * kTileB * TN);
+    float (*yE)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 3 * kTileB * TM + 2 * kTileB * TN);
     const int tid = threadIdx.x;
-    const int tx = tid & 15;          // target group: targets tx*4 .. tx*4+3
-    const int ty = tid >> 4;          // row group: rows ty*4 .. ty*4+3
-    const int64_t x0 = (int64_t)blockIdx.x * kTileRows;
-    const int a0 = blockIdx.y * kTileTargets;
+    const int tx = tid % COLG;        // target group: targets tx*CN ..
+    const int ty = tid / COLG;        // row group: rows ty*RM ..
 
     // two-level summation: 32-term chunk sums, added into the totals with a
     // compensated (Kahan) sum for KL, whose terms cancel near the target
-    float kl[4][4], tv[4][4], klc[4][4];
+    float kl[RM][CN], tv[RM][CN], klc[RM][CN];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < RM; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) kl[r][c] = tv[r][c] = klc[r][c] = 0.0f;
+        for (int c = 0; c < CN; ++c) kl[r][c] = tv[r][c] = klc[r][c] = 0.0f;
 
+    constexpr int FR = TM * kTileB / 256;     // row floats per thread per chunk (multiple of 4)
+    constexpr int FT = TN * kTileB / 256;     // target floats per thread per chunk (2, 4 or 8)
     for (int64_t b0 = 0; b0 < k_pad; b0 += kTileB) {
-        float ckl[4][4], ctv[4][4];
+        float ckl[RM][CN], ctv[RM][CN];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < RM; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) ckl[r][c] = ctv[r][c] = 0.0f;
-        // rows: 64 x 32 floats, 256 threads x two float4 (8 consecutive b of one row)
+            for (int c = 0; c < CN; ++c) ckl[r][c] = ctv[r][c] = 0.0f;
         {
-            const int r = tid >> 2, cb = (tid & 3) * 8;
+            const int r = tid / (kTileB / FR), cb = (tid % (kTileB / FR)) * FR;
             const int64_t x = x0 + r;
-            float vals[8];
 #pragma unroll
-            for (int e = 0; e < 8; e += 4) {
+            for (int e = 0; e < FR; e += 4) {
                 float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (x < n_v && b0 + cb + e < k_pad)
                     v4 = __ldg(reinterpret_cast<const float4 *>(P + x * k_pad + b0 + cb + e));
-                vals[e] = v4.x;
-                vals[e + 1] = v4.y;
-                vals[e + 2] = v4.z;
-                vals[e + 3] = v4.w;
-            }
+                const float vals[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                float lm, E;
-                split_log(vals[e], tab, lm, E);
-                xP[cb + e][r] = vals[e];
-                xL[cb + e][r] = lm;
-                xE[cb + e][r] = E;
+                for (int q = 0; q < 4; ++q) {
+                    float lm, E;
+                    split_log(vals[q], tab, lm, E);
+                    xP[cb + e + q][r] = vals[q];
+                    xL[cb + e + q][r] = lm;
+                    xE[cb + e + q][r] = E;
+                }
             }
         }
-        // targets: 64 x 32 floats of each staged array
         {
-            const int a = tid >> 2, cb = (tid & 3) * 8;
+            const int a = tid / (kTileB / FT), cb = (tid % (kTileB / FT)) * FT;
             const int ag = a0 + a;
 #pragma unroll
-            for (int e = 0; e < 8; e += 4) {
-                float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f), l4 = p4, e4 = p4;
+            for (int e = 0; e < FT; e += 2) {
+                float2 p2 = make_float2(0.f, 0.f), l2 = p2, e2 = p2;
                 if (ag < T && b0 + cb + e < k_pad) {
                     const int64_t off = (int64_t)ag * k_pad + b0 + cb + e;
-                    p4 = __ldg(reinterpret_cast<const float4 *>(sP + off));
-                    l4 = __ldg(reinterpret_cast<const float4 *>(sL + off));
-                    e4 = __ldg(reinterpret_cast<const float4 *>(sE + off));
+                    p2 = __ldg(reinterpret_cast<const float2 *>(sP + off));
+                    l2 = __ldg(reinterpret_cast<const float2 *>(sL + off));
+                    e2 = __ldg(reinterpret_cast<const float2 *>(sE + off));
                 }
-                yP[cb + e][a] = p4.x; yP[cb + e + 1][a] = p4.y; yP[cb + e + 2][a] = p4.z; yP[cb + e + 3][a] = p4.w;
-                yL[cb + e][a] = l4.x; yL[cb + e + 1][a] = l4.y; yL[cb + e + 2][a] = l4.z; yL[cb + e + 3][a] = l4.w;
-                yE[cb + e][a] = e4.x; yE[cb + e + 1][a] = e4.y; yE[cb + e + 2][a] = e4.z; yE[cb + e + 3][a] = e4.w;
+                yP[cb + e][a] = p2.x;
+                yP[cb + e + 1][a] = p2.y;
+                yL[cb + e][a] = l2.x;
+                yL[cb + e + 1][a] = l2.y;
+                yE[cb + e][a] = e2.x;
+                yE[cb + e + 1][a] = e2.y;
             }
         }
         __syncthreads();
 #pragma unroll 4
         for (int b = 0; b < kTileB; ++b) {
-            const float4 rp = *reinterpret_cast<const float4 *>(&xP[b][ty * 4]);
-            const float4 rl = *reinterpret_cast<const float4 *>(&xL[b][ty * 4]);
-            const float4 re = *reinterpret_cast<const float4 *>(&xE[b][ty * 4]);
-            const float4 cp = *reinterpret_cast<const float4 *>(&yP[b][tx * 4]);
-            const float4 cl = *reinterpret_cast<const float4 *>(&yL[b][tx * 4]);
-            const float4 ce = *reinterpret_cast<const float4 *>(&yE[b][tx * 4]);
-            const float rP[4] = {rp.x, rp.y, rp.z, rp.w}, rL[4] = {rl.x, rl.y, rl.z, rl.w},
-                        rE[4] = {re.x, re.y, re.z, re.w};
-            const float cP[4] = {cp.x, cp.y, cp.z, cp.w}, cL[4] = {cl.x, cl.y, cl.z, cl.w},
-                        cE[4] = {ce.x, ce.y, ce.z, ce.w};
+            float rP[RM], rL[RM], rE[RM], cP[CN], cL[CN], cE[CN];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < RM; ++r) {
+                rP[r] = xP[b][ty * RM + r];
+                rL[r] = xL[b][ty * RM + r];
+                rE[r] = xE[b][ty * RM + r];
+            }
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
+            for (int c = 0; c < CN; ++c) {
+                cP[c] = yP[b][tx * CN + c];
+                cL[c] = yL[b][tx * CN + c];
+                cE[c] = yE[b][tx * CN + c];
+            }
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int c = 0; c < CN; ++c)
                     accumulate(rP[r], rL[r], rE[r], cP[c], cL[c], cE[c], ckl[r][c], ctv[r][c]);
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < RM; ++r)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < CN; ++c) {
                 const float y = __fsub_rn(ckl[r][c], klc[r][c]);
                 const float t = __fadd_rn(kl[r][c], y);
                 klc[r][c] = __fsub_rn(__fsub_rn(t, kl[r][c]), y);
@@ -413,17 +427,44 @@ __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restr
         __syncthreads();
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int64_t x = x0 + ty * 4 + r;
+    for (int r = 0; r < RM; ++r) {
+        const int64_t x = x0 + ty * RM + r;
         if (x >= n_v) continue;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int a = a0 + tx * 4 + c;
+        for (int c = 0; c < CN; ++c) {
+            const int a = a0 + tx * CN + c;
             if (a >= T) continue;
             if (out_kl) out_kl[(int64_t)a * n_v + x] = kl[r][c];
             if (out_tv) out_tv[(int64_t)a * n_v + x] = tv[r][c];
         }
     }
+}
+
+// the three shapes the autotuner chooses from
+typedef TileShape<64, 64, 4, 4> TileA;
+typedef TileShape<128, 32, 4, 4> TileB;
+typedef TileShape<256, 16, 8, 2> TileC;
+
+template <int TM, int TN, int RM, int CN>
+__global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
+                                                         const float *__restrict__ sP, const float *__restrict__ sL,
+                                                         const float *__restrict__ sE, int32_t T,
+                                                         float *__restrict__ out_kl, float *__restrict__ out_tv) {
+    extern __shared__ __align__(16) float tsm[];
+    float2 *tab = reinterpret_cast<float2 *>(tsm + 3 * kTileB * (TM + TN));
+    build_log_table(tab);
+    __syncthreads();
+    tile_body<TM, TN, RM, CN>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, (int64_t)blockIdx.x * TM,
+                              blockIdx.y * TN, tsm, tab);
+}
+
+template <class S, int TM, int TN, int RM, int CN>
+void launch_tile(const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL, const float *sE,
+                 int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
+    dim3 g((unsigned)((n_v + TM - 1) / TM), (unsigned)((T + TN - 1) / TN));
+    auto kern = field_tile_kernel<TM, TN, RM, CN>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
+    kern<<<g, 256, S::smem_bytes, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv);
 }
 
 int g_num_sms = 0;
@@ -447,6 +488,128 @@ int num_sms() {
         if (g_num_sms <= 0) g_num_sms = 1;
     }
     return g_num_sms;
+}
+
+
+// ------------------------------------------------------------------ multi-problem persistent launch
+// Work items are output tiles of several problems (domains); CTAs pull items
+// from an atomic counter, largest rows first, and run the item's tile shape.
+__global__ void __launch_bounds__(256, 2) batch_tile_kernel(const BatchProblem *__restrict__ probs,
+                                                         const BatchItem *__restrict__ items, int32_t n_items,
+                                                         int32_t *__restrict__ counter) {
+    extern __shared__ __align__(16) float tsm[];
+    __shared__ float2 tab[kLogTab];
+    __shared__ int cur;
+    build_log_table(tab);
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = cur;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        const BatchProblem q = probs[w.prob];
+        switch (q.variant) {
+            case 0:
+                tile_body<64, 64, 4, 4>(q.P, q.n_v, q.k_pad, q.sP, q.sL, q.sE, q.T, q.out_kl, q.out_tv,
+                                        (int64_t)w.x_tile * 64, w.a_tile * 64, tsm, tab);
+                break;
+            case 1:
+                tile_body<128, 32, 4, 4>(q.P, q.n_v, q.k_pad, q.sP, q.sL, q.sE, q.T, q.out_kl, q.out_tv,
+                                         (int64_t)w.x_tile * 128, w.a_tile * 32, tsm, tab);
+                break;
+            default:
+                tile_body<256, 16, 8, 2>(q.P, q.n_v, q.k_pad, q.sP, q.sL, q.sE, q.T, q.out_kl, q.out_tv,
+                                         (int64_t)w.x_tile * 256, w.a_tile * 16, tsm, tab);
+                break;
+        }
+    }
+}
+
+// staging of the targets of several problems in one launch: blockIdx.y = global target
+__global__ void batch_stage_kernel(const BatchProblem *__restrict__ probs, const int32_t *__restrict__ tprob,
+                                   const int32_t *__restrict__ tlocal, const int32_t *__restrict__ targets,
+                                   int64_t k_max) {
+    __shared__ float2 tab[kLogTab];
+    build_log_table(tab);
+    __syncthreads();
+    const int g = blockIdx.y;
+    const BatchProblem q = probs[tprob[g]];
+    const int a = tlocal[g];
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < q.k_pad; b += (int64_t)gridDim.x * blockDim.x) {
+        const float p = q.P[(int64_t)targets[g] * q.k_pad + b];
+        float lm, E;
+        split_log(p, tab, lm, E);
+        const int64_t o = (int64_t)a * q.k_pad + b;
+        const_cast<float *>(q.sP)[o] = p;
+        const_cast<float *>(q.sL)[o] = lm;
+        const_cast<float *>(q.sE)[o] = E;
+    }
+    (void)k_max;
+}
+
+const int kShapeRows[3] = {64, 128, 256}, kShapeTargets[3] = {64, 32, 16};
+
+void launch_variant(int v, const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL,
+                    const float *sE, int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
+    if (v == 0)
+        launch_tile<TileA, 64, 64, 4, 4>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+    else if (v == 1)
+        launch_tile<TileB, 128, 32, 4, 4>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+    else
+        launch_tile<TileC, 256, 16, 8, 2>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+}
+
+// ------------------------------------------------------------------ autotuner
+// The first time a (rows, columns, targets) class is seen, every tile shape
+// runs on the actual problem (three timed launches each, after a warm-up) and
+// the fastest is kept for the class.  Classes: rows and k_pad in powers of
+// two, targets in powers of two up to 256.
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int>, int> g_tune;
+
+int ilog2_ceil(int64_t x) {
+    int r = 0;
+    while ((int64_t(1) << r) < x) ++r;
+    return r;
+}
+
+std::tuple<int, int, int> tune_key(int64_t n_v, int64_t k_pad, int32_t T) {
+    return std::make_tuple(ilog2_ceil(n_v), ilog2_ceil(k_pad), std::min(ilog2_ceil(T), 8));
+}
+
+int tune_variant(const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL, const float *sE,
+                 int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
+    const auto key = tune_key(n_v, k_pad, T);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < 3; ++v) {
+        launch_variant(v, P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);   // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch_variant(v, P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune[key] = best;
+    return best;
 }
 
 }  // namespace
@@ -487,10 +650,49 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
             go(field_stream_kernel<1, 4>);
         return;
     }
-    dim3 g((unsigned)((n_v + kTileRows - 1) / kTileRows), (unsigned)((T + kTileTargets - 1) / kTileTargets));
-    const int tile_smem = (int)(3 * kTileB * (kTileRows + kTileTargets) * sizeof(float) + kLogTab * sizeof(float2));
-    cudaFuncSetAttribute(field_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem);
-    field_tile_kernel<<<g, 256, tile_smem, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv);
+    const int v = tune_variant(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+    launch_variant(v, P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
 }
 
-size_t field_smem_limit_ok(int64_t k_pad) { return 3 * (size_t)k_pad * sizeof(float); }
+
+int tile_variant_for(const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL, const float *sE,
+                     int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
+    return tune_variant(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+}
+
+int tile_rows(int variant) { return kShapeRows[variant]; }
+int tile_targets(int variant) { return kShapeTargets[variant]; }
+
+void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, const int32_t *d_tlocal,
+                        const int32_t *d_targets, int32_t n_targets, int64_t k_max, cudaStream_t s) {
+    if (n_targets <= 0) return;
+    dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(8, (k_max + 255) / 256)), (unsigned)n_targets);
+    batch_stage_kernel<<<g, 256, 0, s>>>(d_probs, d_tprob, d_tlocal, d_targets, k_max);
+}
+
+void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, int32_t n_items, int32_t *d_counter,
+                         cudaStream_t s) {
+    if (n_items <= 0) return;
+    const size_t smem = (size_t)3 * kTileB * (256 + 16) * sizeof(float);
+    cudaFuncSetAttribute(batch_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tile_kernel, 256, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms() * per_sm;
+    if (grid > n_items) grid = n_items;
+    cudaMemsetAsync(d_counter, 0, sizeof(int32_t), s);
+    batch_tile_kernel<<<(unsigned)grid, 256, smem, s>>>(d_probs, d_items, n_items, d_counter);
+}
+
+std::string tuning_table() {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    std::string out;
+    const char *names[3] = {"64x64", "128x32", "256x16"};
+    for (auto &kv : g_tune) {
+        char buf[128];
+        std::snprintf(buf, sizeof buf, "rows<=2^%d k_pad<=2^%d T<=2^%d: %s\n", std::get<0>(kv.first),
+                      std::get<1>(kv.first), std::get<2>(kv.first), names[kv.second]);
+        out += buf;
+    }
+    return out;
+}

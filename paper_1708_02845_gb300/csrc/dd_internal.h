@@ -82,6 +82,28 @@ void launch_stage_targets(const float *P, int64_t k_pad, int64_t k, const int32_
 // FP32 fields.  out_kl / out_tv: [T][n_v] (either may be null).
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T,
                         float *out_kl, float *out_tv, int *err_flag, cudaStream_t s);
+// One problem of a multi-domain field launch, and one output tile of it.
+struct BatchProblem {
+    const float *P;
+    int64_t n_v, k_pad;
+    const float *sP, *sL, *sE;   // staged targets [T][k_pad] each
+    int32_t T, variant;          // targets; tile shape (0: 64x64, 1: 128x32, 2: 256x16)
+    float *out_kl, *out_tv;      // [T][n_v] each (either may be null)
+};
+struct BatchItem {
+    int32_t prob, x_tile, a_tile, pad;
+};
+// autotuned tile shape for one problem (may run timed launches the first time)
+int tile_variant_for(const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL, const float *sE,
+                     int32_t T, float *out_kl, float *out_tv, cudaStream_t s);
+int tile_rows(int variant);
+int tile_targets(int variant);
+void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, const int32_t *d_tlocal,
+                        const int32_t *d_targets, int32_t n_targets, int64_t k_max, cudaStream_t s);
+void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, int32_t n_items, int32_t *d_counter,
+                         cudaStream_t s);
+std::string tuning_table();
+
 // Tracer: per-field triangle gradients into grads [T][n_t], then T*S paths.
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,
                   const int32_t *sources, int32_t T, int32_t S, int32_t max_pts, float2 *out_xy,
@@ -94,6 +116,13 @@ dd_status prepare_bf16(DevMesh &m, cudaStream_t s, std::string &err);
 size_t gemm_target_scratch_bytes(const DevMesh &m, int32_t T);
 dd_status launch_kl_gemm(const DevMesh &m, const int32_t *d_targets, int32_t T, void *scratch, float *out_kl,
                          int *err_flag, cudaStream_t s, std::string &err);
+
+// Tracer over several meshes in one launch (descriptors built on the host).
+size_t batch_trace_dom_bytes();
+void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, float2 *grads);
+void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t *d_tloc, const int32_t *d_targets,
+                        const int32_t *d_sources, int32_t n_targets, int32_t S, int64_t max_nt, int32_t max_pts,
+                        float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s);
 
 #define DD_CUDA_TRY(expr, errstr)                                                   \
     do {                                                                            \

@@ -26,6 +26,8 @@
 // a single dependent load level: the record and gradient of the next triangle,
 // whose id sits in the current record.
 #include <cfloat>
+#include <cstring>
+#include <algorithm>
 #include <cmath>
 
 #include "dd_internal.h"
@@ -105,16 +107,20 @@ __global__ void tri_grad_kernel(const int4 *__restrict__ rec, int64_t n_t, const
 __device__ __forceinline__ float sel3f(int i, float a, float b, float c) { return i == 0 ? a : (i == 1 ? b : c); }
 __device__ __forceinline__ int sel3i(int i, int a, int b, int c) { return i == 0 ? a : (i == 1 ? b : c); }
 
-__global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= p.total) return;
-    const int a = (int)(id / p.S);
-    const int target = p.targets[a];
-    const float *f = p.fields + (int64_t)a * p.field_stride;
-    const float2 *grads = p.grads + (int64_t)a * p.n_t;
-    float2 *out = p.out_xy + id * p.max_pts;
+struct TraceDom {
+    const int4 *rec;
+    const float2 *xy;
+    const int32_t *vt_off, *vt;
+    int64_t n_t;
+};
+
+// one path: walk from `source` to `target` on field f (triangle gradients `grads`)
+__device__ __forceinline__ void trace_path(const TraceDom &p, const float *__restrict__ f,
+                                           const float2 *__restrict__ grads, int target, int source,
+                                           float2 *__restrict__ out, int32_t max_pts, int32_t max_steps,
+                                           int32_t *len_out, int32_t *status_out) {
     const float eps2 = kEpsWedge * kEpsWedge;
-    int v = p.sources[id];
+    int v = source;
     int len = 0;
     int status = DD_TRACE_STEP_LIMIT;
     int states = 1;                // vertex and edge states entered (the step cap counts these)
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
 
 #define DD_PUSH(pt)                              \
     do {                                         \
-        if (len >= p.max_pts) {                  \
+        if (len >= max_pts) {                  \
             status = DD_TRACE_TRUNCATED;         \
             goto done;                           \
         }                                        \
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
         adj = false;                             \
         best = -1;                               \
         best_g2 = 0.f;                           \
-        if (++states > p.max_steps) goto done;   \
+        if (++states > max_steps) goto done;   \
         if (v == target) {                       \
             status = DD_TRACE_OK;                \
             goto done;                           \
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
         status = DD_TRACE_OK;
         goto done;
     }
-    for (int64_t iter = 0; iter < 16LL * p.max_steps; ++iter) {
+    for (int64_t iter = 0; iter < 16LL * max_steps; ++iter) {
         if (!scanning && t_next < 0) {     // boundary edge: slide to the lower endpoint
             DD_SLIDE();
             continue;
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
                     pb = b_pk;
                     la = lj;
                     lb = lk;
-                    if (++states > p.max_steps) goto done;
+                    if (++states > max_steps) goto done;
                 }
                 continue;
             }
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
                 la = lkeep;
                 lb = lc2;
             }
-            if (++states > p.max_steps) goto done;
+            if (++states > max_steps) goto done;
             if (ea == target || eb == target) {   // an edge incident on the target
                 DD_PUSH(p.xy[target]);
                 status = DD_TRACE_OK;
@@ -347,8 +353,60 @@ done:
 #undef DD_PUSH
 #undef DD_ENTER_VERTEX
 #undef DD_SLIDE
-    p.out_len[id] = len;
-    p.out_status[id] = status;
+    *len_out = len;
+    *status_out = status;
+}
+
+__global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= p.total) return;
+    const int a = (int)(id / p.S);
+    TraceDom d;
+    d.rec = p.rec;
+    d.xy = p.xy;
+    d.vt_off = p.vt_off;
+    d.vt = p.vt;
+    d.n_t = p.n_t;
+    trace_path(d, p.fields + (int64_t)a * p.field_stride, p.grads + (int64_t)a * p.n_t, p.targets[a], p.sources[id],
+               p.out_xy + id * p.max_pts, p.max_pts, p.max_steps, p.out_len + id, p.out_status + id);
+}
+
+// ---- several meshes in one launch: global target g belongs to domain tdom[g] (local index tloc[g])
+struct BatchTraceDom {
+    TraceDom d;
+    const float *fields;      // [T_d][n_v]
+    float2 *grads;            // [T_d][n_t]
+    int64_t n_v;
+    int32_t max_steps, pad;
+};
+
+__global__ void batch_grad_kernel(const BatchTraceDom *__restrict__ doms, const int32_t *__restrict__ tdom,
+                                  const int32_t *__restrict__ tloc) {
+    const int g = blockIdx.y;
+    const BatchTraceDom q = doms[tdom[g]];
+    const int a = tloc[g];
+    const float *f = q.fields + (int64_t)a * q.n_v;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < q.d.n_t; t += (int64_t)gridDim.x * blockDim.x) {
+        const Tri T = load_tri(q.d.rec, (int)t);
+        const float f2 = f[T.v2], d0 = f[T.v0] - f2, d1 = f[T.v1] - f2;
+        q.grads[(int64_t)a * q.d.n_t + t] = make_float2(d0 * T.g0.x + d1 * T.g1.x, d0 * T.g0.y + d1 * T.g1.y);
+    }
+}
+
+__global__ void __launch_bounds__(64) batch_trace_kernel(const BatchTraceDom *__restrict__ doms,
+                                                        const int32_t *__restrict__ tdom,
+                                                        const int32_t *__restrict__ tloc,
+                                                        const int32_t *__restrict__ targets,
+                                                        const int32_t *__restrict__ sources, int64_t total, int32_t S,
+                                                        int32_t max_pts, float2 *__restrict__ out_xy,
+                                                        int32_t *__restrict__ out_len, int32_t *__restrict__ out_status) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    const int g = (int)(id / S);
+    const BatchTraceDom q = doms[tdom[g]];
+    const int a = tloc[g];
+    trace_path(q.d, q.fields + (int64_t)a * q.n_v, q.grads + (int64_t)a * q.d.n_t, targets[g], sources[id],
+               out_xy + id * max_pts, max_pts, q.max_steps, out_len + id, out_status + id);
 }
 
 }  // namespace
@@ -379,4 +437,36 @@ void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, c
     dim3 gg((unsigned)((m.n_t + 255) / 256), (unsigned)T);
     tri_grad_kernel<<<gg, 256, 0, s>>>(m.trec, m.n_t, fields, field_stride, grads);
     trace_kernel<<<(unsigned)((p.total + 63) / 64), 64, 0, s>>>(p);
+}
+
+size_t batch_trace_dom_bytes() { return sizeof(BatchTraceDom); }
+
+// host-side builder of one domain descriptor (into a byte buffer uploaded by the caller)
+void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, float2 *grads) {
+    BatchTraceDom q;
+    q.d.rec = m.trec;
+    q.d.xy = m.xy;
+    q.d.vt_off = m.vt_off;
+    q.d.vt = m.vt;
+    q.d.n_t = m.n_t;
+    q.fields = fields;
+    q.grads = grads;
+    q.n_v = m.n_v;
+    const int64_t cap = 4 * m.n_t;
+    q.max_steps = cap > (int64_t)INT32_MAX ? INT32_MAX : (int32_t)cap;
+    q.pad = 0;
+    std::memcpy(dst, &q, sizeof q);
+}
+
+void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t *d_tloc, const int32_t *d_targets,
+                        const int32_t *d_sources, int32_t n_targets, int32_t S, int64_t max_nt, int32_t max_pts,
+                        float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s) {
+    if (n_targets <= 0) return;
+    const BatchTraceDom *doms = reinterpret_cast<const BatchTraceDom *>(d_doms);
+    dim3 gg((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_nt + 255) / 256)), (unsigned)n_targets);
+    batch_grad_kernel<<<gg, 256, 0, s>>>(doms, d_tdom, d_tloc);
+    const int64_t total = (int64_t)n_targets * S;
+    if (total == 0) return;
+    batch_trace_kernel<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(doms, d_tdom, d_tloc, d_targets, d_sources, total, S,
+                                                                    max_pts, out_xy, out_len, out_status);
 }

@@ -52,6 +52,8 @@ _SIGS = {
     "dd_trace_fields": (_i32, [_p, _i32, _p, _p, _i32, _p, _i32, _i32, _p, _p, _p]),
     "dd_query": (_i32, [_p, _i32, _p, _i32, _p, _i32, _u32, _i32, _u32, _i32, _p, _p, _p, _p]),
     "dd_distance_noalloc": (_i32, [_p, _i64, _i64, _p, _i32, _u32, _p, _p]),
+    "dd_query_batch": (_i32, [_p, _i32, _p, _p, _p, _p, _i32, _u32, _u32, _i32, _p, _p, _p, _p]),
+    "dd_tuning_table": (_i32, [ctypes.c_char_p, _i32]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -211,3 +213,21 @@ def dd_distance_noalloc(P, n_v: int, k_pad: int, targets, T: int, f_mask: int, o
     if st != DD_OK:
         raise DDError(st, "dd_distance_noalloc failed")
     return out
+
+
+def dd_query_batch(ctx, mesh_ids, T_per, targets, sources, S: int, f_mask: int, trace_f: int, max_pts: int,
+                   out_fields, out_xy=None, out_len=None, out_status=None):
+    """Several meshes in one pass; targets/sources concatenated item after item."""
+    mids = _host_i32(mesh_ids)
+    tp = _host_i32(T_per)
+    t = _host_i32(targets)
+    s = _host_i32(sources) if S > 0 else np.zeros(1, np.int32)
+    _check(ctx, lib.dd_query_batch(ctx, len(mids), ptr(mids), ptr(tp), ptr(t), ptr(s), S, f_mask, trace_f, max_pts,
+                                   ptr(out_fields), ptr(out_xy), ptr(out_len), ptr(out_status)))
+
+
+def dd_tuning_table() -> str:
+    n = lib.dd_tuning_table(None, 0)
+    buf = ctypes.create_string_buffer(max(n, 0) + 1)
+    lib.dd_tuning_table(buf, len(buf))
+    return buf.value.decode()
