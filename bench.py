@@ -112,12 +112,16 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     ctx = dd.dd_create(local_rank, stream.cuda_stream)
-    if args.section == "grid450":
+    if args.section in ("grid450", "batch"):
         pk, pk_kind = peaks()
         flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev)
-        st_sec, gm_sec = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
+        if args.section == "grid450":
+            st_sec, gm_sec = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
+            out = {"metric": "grid450 sections only", "stream": st_sec, "gemm": gm_sec}
+        else:
+            out = {"metric": "batch64 section only", "batch": batch_section(dd, ctx, dev, stream, flush, args)}
         dd.dd_destroy(ctx)
-        return {"metric": "grid450 sections only", "stream": st_sec, "gemm": gm_sec}
+        return out
     wl, batches = workload_batches(rank)
     mesh = wl.mesh
     idx, off = mesh.loop_arrays()
@@ -249,6 +253,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if args.stream and args.section == "all":
         line["stream"], line["gemm"] = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
+        line["batch"] = batch_section(dd, ctx, dev, stream, flush, args)
     dd.dd_destroy(ctx)
     return line
 
@@ -318,6 +323,68 @@ def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10):
     return stream_sec, gemm_sec
 
 
+def batch_section(dd, ctx, dev, stream, flush, args, S: int = 64, max_pts: int = 1536):
+    """64 uneven grid domains (n log-uniform in [5k, 100k], 0..16 obstacles,
+    16..256 targets each, 64 traced paths per target): one dd_query_batch per
+    step -- all KL+TV fields in one persistent launch with autotuned tiles,
+    all paths in one tracer launch."""
+    import torch
+    from synthetic import workloads
+    wls = workloads.batch64(S=S)
+    mids, Ts, tg, sr = [], [], [], []
+    t0 = time.perf_counter()
+    pcg_iters = 0
+    for wl in wls:
+        idx, off = wl.mesh.loop_arrays()
+        mid = dd.dd_load_mesh(ctx, wl.mesh.xy, wl.mesh.tri, idx, off)
+        it, _ = dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+        pcg_iters += it
+        mids.append(mid)
+        Ts.append(len(wl.targets))
+        tg.append(np.asarray(wl.targets, np.int32))
+        sr.append(np.asarray(wl.sources, np.int32).reshape(-1))
+    pre = time.perf_counter() - t0
+    tg = np.concatenate(tg)
+    sr = np.concatenate(sr)
+    n_vs = [wl.mesh.n_v for wl in wls]
+    ks = [dd.dd_mesh_info(ctx, m)["k"] for m in mids]
+    nT = int(sum(Ts))
+    n_f = int(sum(2 * T * n for T, n in zip(Ts, n_vs)))
+    out = torch.empty(n_f, dtype=torch.float32, device=dev)
+    xy = torch.empty((nT * S, max_pts, 2), dtype=torch.float32, device=dev)
+    ln = torch.empty(nT * S, dtype=torch.int32, device=dev)
+    st = torch.empty(nT * S, dtype=torch.int32, device=dev)
+
+    def q():
+        dd.dd_query_batch(ctx, mids, Ts, tg, sr, S, 3, 1, max_pts, out, xy, ln, st)
+
+    q()                       # first call runs the autotuner for new size classes
+    for _ in range(2):
+        q()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.fill_(0.25)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    med = statistics.median(ms)
+    stn = st.cpu().numpy()
+    elem_targets = float(sum(T * n * k for T, n, k in zip(Ts, n_vs, ks)))
+    for mid in mids:
+        dd.dd_unload_mesh(ctx, mid)
+    return {"workload": "batch64: %d grid domains, n %d..%d, k %d..%d, %d targets (16..256 per domain), %d paths"
+                        % (len(wls), min(n_vs), max(n_vs), min(ks), max(ks), nT, nT * S),
+            "ms_per_batch": round(med, 3), "fields_per_s": round(2 * nT / (med / 1e3), 1),
+            "paths_per_s": round(nT * S / (med / 1e3), 1),
+            "field_flop_per_batch": 8.0 * elem_targets, "paths_ok_frac": float(np.mean(stn == 0)),
+            "tile_shapes": dd.dd_tuning_table().strip().splitlines(),
+            "preproc": {"pcg_iters_total": pcg_iters, "seconds": round(pre, 2)}, "launches_per_batch": 5}
+
+
 class OracleStep:
     """The FP64 oracle on a bounded sample of the grid140 step (fields/s)."""
 
@@ -367,8 +434,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", dest="stream", action="store_false",
                     help="skip the grid450 measurements (single-target HBM stream, BF16 tensor-core KL)")
-    ap.add_argument("--section", choices=["all", "step", "grid450"], default="all",
-                    help="step: only the grid140 query step; grid450: only the grid450 measurements")
+    ap.add_argument("--section", choices=["all", "step", "grid450", "batch"], default="all",
+                    help="step: only the grid140 query step; grid450 / batch: only that measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
