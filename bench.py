@@ -112,14 +112,16 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     ctx = dd.dd_create(local_rank, stream.cuda_stream)
-    if args.section in ("grid450", "batch"):
+    if args.section in ("grid450", "batch", "serve"):
         pk, pk_kind = peaks()
         flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev)
         if args.section == "grid450":
             st_sec, gm_sec = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
             out = {"metric": "grid450 sections only", "stream": st_sec, "gemm": gm_sec}
-        else:
+        elif args.section == "batch":
             out = {"metric": "batch64 section only", "batch": batch_section(dd, ctx, dev, stream, flush, args)}
+        else:
+            out = {"metric": "serving section only", "serve": serve_section(dd, ctx, args, n_domains=8, seconds=10.0)}
         dd.dd_destroy(ctx)
         return out
     wl, batches = workload_batches(rank)
@@ -254,6 +256,7 @@ def run_ours(args, rank, world, local_rank):
     if args.stream and args.section == "all":
         line["stream"], line["gemm"] = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
         line["batch"] = batch_section(dd, ctx, dev, stream, flush, args)
+        line["serve"] = serve_section(dd, ctx, args, n_domains=5, seconds=3.0)
     dd.dd_destroy(ctx)
     return line
 
@@ -385,6 +388,94 @@ def batch_section(dd, ctx, dev, stream, flush, args, S: int = 64, max_pts: int =
             "preproc": {"pcg_iters_total": pcg_iters, "seconds": round(pre, 2)}, "launches_per_batch": 5}
 
 
+def serve_section(dd, ctx, args, n_domains: int, seconds: float, rate: float = 2000.0, max_pts: int = 2048):
+    """Served (continuous batching) vs plain per-query form on the serving workload.
+
+    Resident grid domains (n log-uniform in [10k, 500k]; n_domains smallest of
+    the 8-domain recipe when fewer are asked), Poisson arrivals at `rate` q/s
+    for `seconds`; each query = a random interior target plus S sources,
+    S log-uniform in [1, 1024].  Both forms replay the arrivals in real time;
+    latency = arrival -> paths in host memory."""
+    from synthetic import workloads
+    doms = workloads.serving_domains()
+    order = sorted(range(len(doms)), key=lambda i: doms[i].mesh.n_v)[:n_domains]
+    doms = [doms[i] for i in sorted(order)]
+    t0 = time.perf_counter()
+    mids = []
+    for wl in doms:
+        idx, off = wl.mesh.loop_arrays()
+        mid = dd.dd_load_mesh(ctx, wl.mesh.xy, wl.mesh.tri, idx, off)
+        dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+        mids.append(mid)
+    pre = time.perf_counter() - t0
+    qs = workloads.serving_queries(doms, rate_qps=rate, duration_s=seconds)
+    # ---- served
+    sv = dd.dd_server_create(ctx, 24 << 30, n_slots=3, max_batch=64, max_pts=max_pts)
+    lat = {}
+    refused = 0
+    start = time.perf_counter()
+    pos = 0
+    while pos < len(qs):
+        now = time.perf_counter() - start
+        while pos < len(qs) and qs[pos][0] <= now:
+            t, d, tgt, src = qs[pos]
+            if dd.dd_server_submit(sv, pos, mids[d], tgt, src) != dd.DD_OK:
+                refused += 1
+            pos += 1
+        ids, sts, ls = dd.dd_server_poll(sv)
+        for i, l in zip(ids, ls):
+            lat[int(i)] = float(l)
+        time.sleep(0.0002)
+    dd.dd_server_wait_idle(sv, 600.0)
+    served_wall = time.perf_counter() - start
+    ids, sts, ls = dd.dd_server_poll(sv, 1 << 20)
+    for i, l in zip(ids, ls):
+        lat[int(i)] = float(l)
+    paths_ok = []
+    for i in list(lat.keys())[:200]:
+        S = len(qs[i][3])
+        _, _, st = dd.dd_server_take(sv, i, S, max_pts)
+        paths_ok.append(float(np.mean(st == 0)))
+    dd.dd_server_destroy(sv)
+    L = np.asarray(list(lat.values()))
+    # ---- plain per-query form (same arrivals, one query at a time, host buffers)
+    n_plain = min(len(qs), int(rate * min(seconds, 2.0)))
+    plat = []
+    start = time.perf_counter()
+    for i in range(n_plain):
+        t, d, tgt, src = qs[i]
+        while time.perf_counter() - start < t:
+            pass
+        S = len(src)
+        hf = np.empty((1, 1, doms[d].mesh.n_v), np.float32)
+        hxy = np.empty((S, max_pts, 2), np.float32)
+        hl = np.empty(S, np.int32)
+        hs = np.empty(S, np.int32)
+        dd.dd_query(ctx, mids[d], [tgt], src.reshape(1, -1), dd.DD_F_KL, dd.DD_PREC_FP32, dd.DD_F_KL, max_pts,
+                    hf, hxy, hl, hs)
+        plat.append((time.perf_counter() - start - t) * 1e3)
+    for mid in mids:
+        dd.dd_unload_mesh(ctx, mid)
+    PL = np.asarray(plat)
+    return {"workload": "serving: %d resident grid domains (n %d..%d, k %d..%d), Poisson arrivals %.0f q/s for %.1f s, "
+                        "S log-uniform in [1, 1024]" % (len(doms), min(w.mesh.n_v for w in doms),
+                                                         max(w.mesh.n_v for w in doms),
+                                                         min(sum(len(l) for l in w.mesh.loops) for w in doms),
+                                                         max(sum(len(l) for l in w.mesh.loops) for w in doms),
+                                                         rate, seconds),
+            "served": {"queries": len(qs), "completed": int(L.size), "refused": refused,
+                       "qps": round(L.size / served_wall, 1),
+                       "p50_ms": round(float(np.percentile(L, 50)), 3), "p99_ms": round(float(np.percentile(L, 99)), 3),
+                       "paths_ok_frac_sample": round(float(np.mean(paths_ok)), 4) if paths_ok else None,
+                       "slots": 3, "max_batch": 64},
+            "plain": {"queries": n_plain, "p50_ms": round(float(np.percentile(PL, 50)), 3),
+                      "p99_ms": round(float(np.percentile(PL, 99)), 3),
+                      "qps": round(n_plain / (time.perf_counter() - start), 1),
+                      "form": "one dd_query per query (T=1, host buffers), in arrival order, first %d queries"
+                              % n_plain},
+            "preproc_s": round(pre, 2)}
+
+
 class OracleStep:
     """The FP64 oracle on a bounded sample of the grid140 step (fields/s)."""
 
@@ -434,7 +525,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", dest="stream", action="store_false",
                     help="skip the grid450 measurements (single-target HBM stream, BF16 tensor-core KL)")
-    ap.add_argument("--section", choices=["all", "step", "grid450", "batch"], default="all",
+    ap.add_argument("--section", choices=["all", "step", "grid450", "batch", "serve"], default="all",
                     help="step: only the grid140 query step; grid450 / batch: only that measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

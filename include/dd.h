@@ -229,6 +229,51 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
  * terminated) into buf (may be NULL) and returns the full length. */
 int32_t dd_tuning_table(char *buf, int32_t len);
 
+/* ---- query server: continuous batching of path queries ------------------
+ * A query asks for the paths from S sources to one interior target of a
+ * loaded mesh, traced on the target's KL field (Section IV).  A server runs a
+ * worker thread that keeps up to n_slots batches in flight, each on its own
+ * CUDA stream: whenever a slot is free it takes the queries that have
+ * arrived (in arrival order, up to max_batch and what fits the slot), groups
+ * them by mesh and runs one staging, one persistent field launch and one
+ * tracer launch for all of them, then copies the paths to host memory.
+ * Queries arriving while batches run join the next batch, whose work
+ * overlaps on the device with the running ones.  The device budget is split
+ * evenly over the slots and allocated at creation; nothing is allocated on
+ * the device while serving.  While a server runs, meshes of its context must
+ * stay loaded and other calls on the context must not run concurrently. */
+typedef struct dd_server dd_server;
+
+/* budget_bytes: device memory for the slots (>= 1 MiB); n_slots 1..16;
+ * max_batch: queries per batch (>= 1); max_pts: polyline capacity (>= 2).
+ * Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA. */
+dd_status dd_server_create(dd_ctx *ctx, int64_t budget_bytes, int32_t n_slots, int32_t max_batch,
+                           int32_t max_pts, dd_server **out);
+
+/* Enqueue a query (thread-safe, returns at once).  sources: host [S] vertex
+ * ids, copied.  query_id must be unique among unreleased queries.  Errors:
+ * DD_EINVAL (ids), DD_ESTATE (no Poisson kernel), DD_EBUDGET (the query can
+ * never fit one slot). */
+dd_status dd_server_submit(dd_server *sv, int64_t query_id, int32_t mesh, int32_t target,
+                           const int32_t *sources, int32_t S);
+
+/* Report up to max_n queries completed since the last poll: ids, their
+ * status (DD_OK or an error) and latency in ms from submission to the paths
+ * being in host memory.  Returns how many were written (0 if none). */
+int32_t dd_server_poll(dd_server *sv, int32_t max_n, int64_t *ids, int32_t *statuses, double *latency_ms);
+
+/* Copy out and release a completed query: xy host [S][max_pts][2], len and
+ * status host [S] (any may be NULL).  Returns the query's status, or
+ * DD_ESTATE if it is not complete (or already released). */
+dd_status dd_server_take(dd_server *sv, int64_t query_id, float *xy, int32_t *len, int32_t *status);
+
+/* Block until no query is pending or in flight, or timeout_s passed
+ * (DD_ETIMEOUT). */
+dd_status dd_server_wait_idle(dd_server *sv, double timeout_s);
+
+/* Finish all queries, stop the worker and free the server. */
+void dd_server_destroy(dd_server *sv);
+
 /* dd_distance without any device allocation.  The paper has no counterpart:
  * this is a deployment variant of dd_distance for callers that may not call
  * cudaMalloc -- e.g. a robot's real-time control loop that allocates only at

@@ -13,30 +13,6 @@
 
 namespace {
 
-enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_META, S_COUNT };
-
-struct MeshSlot {
-    bool live = false;
-    DevMesh dev;
-};
-
-}  // namespace
-
-struct dd_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    std::string err;
-    std::vector<MeshSlot> meshes;
-    void *scratch[S_COUNT] = {};
-    size_t scratch_cap[S_COUNT] = {};
-    int *d_err = nullptr;                     // device error flag written by kernels
-    void *pinned[S_COUNT] = {};               // host staging for index uploads, one per scratch id
-    size_t pinned_cap[S_COUNT] = {};
-    cudaEvent_t pinned_free[S_COUNT] = {};    // recorded after the last upload from pinned[id]
-};
-
-namespace {
-
 dd_status set_err(dd_ctx *c, dd_status s, const std::string &msg) {
     if (c) c->err = msg;
     return s;

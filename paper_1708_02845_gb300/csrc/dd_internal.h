@@ -122,7 +122,29 @@ size_t batch_trace_dom_bytes();
 void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, float2 *grads);
 void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t *d_tloc, const int32_t *d_targets,
                         const int32_t *d_sources, int32_t n_targets, int32_t S, int64_t max_nt, int32_t max_pts,
-                        float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s);
+                        float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s,
+                        const int32_t *d_path_target = nullptr, int64_t n_paths = 0);
+
+// ---------------------------------------------------------------- context
+enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_META, S_COUNT };
+
+struct MeshSlot {
+    bool live = false;
+    DevMesh dev;
+};
+
+struct dd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<MeshSlot> meshes;
+    void *scratch[S_COUNT] = {};
+    size_t scratch_cap[S_COUNT] = {};
+    int *d_err = nullptr;                     // device error flag written by kernels
+    void *pinned[S_COUNT] = {};               // host staging for index uploads, one per scratch id
+    size_t pinned_cap[S_COUNT] = {};
+    cudaEvent_t pinned_free[S_COUNT] = {};    // recorded after the last upload from pinned[id]
+};
 
 #define DD_CUDA_TRY(expr, errstr)                                                   \
     do {                                                                            \

@@ -393,16 +393,18 @@ __global__ void batch_grad_kernel(const BatchTraceDom *__restrict__ doms, const 
     }
 }
 
+// path id -> global target: id / S, or path_target[id] when sources per target vary
 __global__ void __launch_bounds__(64) batch_trace_kernel(const BatchTraceDom *__restrict__ doms,
                                                         const int32_t *__restrict__ tdom,
                                                         const int32_t *__restrict__ tloc,
                                                         const int32_t *__restrict__ targets,
-                                                        const int32_t *__restrict__ sources, int64_t total, int32_t S,
-                                                        int32_t max_pts, float2 *__restrict__ out_xy,
+                                                        const int32_t *__restrict__ sources,
+                                                        const int32_t *__restrict__ path_target, int64_t total,
+                                                        int32_t S, int32_t max_pts, float2 *__restrict__ out_xy,
                                                         int32_t *__restrict__ out_len, int32_t *__restrict__ out_status) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= total) return;
-    const int g = (int)(id / S);
+    const int g = path_target ? path_target[id] : (int)(id / S);
     const BatchTraceDom q = doms[tdom[g]];
     const int a = tloc[g];
     trace_path(q.d, q.fields + (int64_t)a * q.n_v, q.grads + (int64_t)a * q.d.n_t, targets[g], sources[id],
@@ -460,13 +462,15 @@ void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, floa
 
 void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t *d_tloc, const int32_t *d_targets,
                         const int32_t *d_sources, int32_t n_targets, int32_t S, int64_t max_nt, int32_t max_pts,
-                        float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s) {
+                        float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s,
+                        const int32_t *d_path_target, int64_t n_paths) {
     if (n_targets <= 0) return;
     const BatchTraceDom *doms = reinterpret_cast<const BatchTraceDom *>(d_doms);
     dim3 gg((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_nt + 255) / 256)), (unsigned)n_targets);
     batch_grad_kernel<<<gg, 256, 0, s>>>(doms, d_tdom, d_tloc);
-    const int64_t total = (int64_t)n_targets * S;
+    const int64_t total = d_path_target ? n_paths : (int64_t)n_targets * S;
     if (total == 0) return;
-    batch_trace_kernel<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(doms, d_tdom, d_tloc, d_targets, d_sources, total, S,
-                                                                    max_pts, out_xy, out_len, out_status);
+    batch_trace_kernel<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(doms, d_tdom, d_tloc, d_targets, d_sources,
+                                                                    d_path_target, total, S, max_pts, out_xy, out_len,
+                                                                    out_status);
 }

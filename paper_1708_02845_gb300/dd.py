@@ -54,6 +54,12 @@ _SIGS = {
     "dd_distance_noalloc": (_i32, [_p, _i64, _i64, _p, _i32, _u32, _p, _p]),
     "dd_query_batch": (_i32, [_p, _i32, _p, _p, _p, _p, _i32, _u32, _u32, _i32, _p, _p, _p, _p]),
     "dd_tuning_table": (_i32, [ctypes.c_char_p, _i32]),
+    "dd_server_create": (_i32, [_p, _i64, _i32, _i32, _i32, ctypes.POINTER(_p)]),
+    "dd_server_submit": (_i32, [_p, _i64, _i32, _i32, _p, _i32]),
+    "dd_server_poll": (_i32, [_p, _i32, _p, _p, _p]),
+    "dd_server_take": (_i32, [_p, _i64, _p, _p, _p]),
+    "dd_server_wait_idle": (_i32, [_p, _f64]),
+    "dd_server_destroy": (None, [_p]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -231,3 +237,48 @@ def dd_tuning_table() -> str:
     buf = ctypes.create_string_buffer(max(n, 0) + 1)
     lib.dd_tuning_table(buf, len(buf))
     return buf.value.decode()
+
+
+def dd_server_create(ctx, budget_bytes: int, n_slots: int = 3, max_batch: int = 64, max_pts: int = 2048):
+    h = _p()
+    st = lib.dd_server_create(ctx, int(budget_bytes), n_slots, max_batch, max_pts, ctypes.byref(h))
+    if st != DD_OK:
+        raise DDError(st, "dd_server_create failed")
+    return h
+
+
+def dd_server_submit(sv, query_id: int, mesh: int, target: int, sources) -> int:
+    """Returns the status (DD_OK, or DD_EBUDGET for a query that can never fit); raises on bad arguments."""
+    s = _host_i32(sources)
+    st = lib.dd_server_submit(sv, int(query_id), int(mesh), int(target), ptr(s), len(s))
+    if st not in (DD_OK, DD_EBUDGET):
+        raise DDError(st, "dd_server_submit failed")
+    return st
+
+
+def dd_server_poll(sv, max_n: int = 4096):
+    ids = np.zeros(max_n, np.int64)
+    sts = np.zeros(max_n, np.int32)
+    lat = np.zeros(max_n, np.float64)
+    n = lib.dd_server_poll(sv, max_n, ptr(ids), ptr(sts), ptr(lat))
+    return ids[:n], sts[:n], lat[:n]
+
+
+def dd_server_take(sv, query_id: int, S: int, max_pts: int):
+    xy = np.zeros((S, max_pts, 2), np.float32)
+    ln = np.zeros(S, np.int32)
+    st = np.zeros(S, np.int32)
+    code = lib.dd_server_take(sv, int(query_id), ptr(xy), ptr(ln), ptr(st))
+    if code != DD_OK:
+        raise DDError(code, "dd_server_take failed")
+    return xy, ln, st
+
+
+def dd_server_wait_idle(sv, timeout_s: float = 60.0):
+    st = lib.dd_server_wait_idle(sv, float(timeout_s))
+    if st != DD_OK:
+        raise DDError(st, "dd_server_wait_idle timed out")
+
+
+def dd_server_destroy(sv):
+    lib.dd_server_destroy(sv)
