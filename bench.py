@@ -43,13 +43,26 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_batches(rank: int):
     from synthetic import workloads
     from synthetic.rng import SplitMix64
     wl = workloads.grid140(T=T_BATCH, S=S_PER_TARGET)
-    batches = [(wl.targets, wl.sources)]
+    # rank 0 starts with the workload's own batch; every other batch (and all of
+    # another rank's) is drawn from a rank-seeded stream, so ranks share no work
+    batches = [(wl.targets, wl.sources)] if rank == 0 else []
     rng = SplitMix64(workloads.BASE_SEED + 1000 + rank)
-    for _ in range(N_BATCHES - 1):
+    while len(batches) < N_BATCHES:
         t = workloads.draw_targets(rng, wl.mesh, T_BATCH)
         s = workloads.draw_sources(rng, wl.mesh, t, S_PER_TARGET)
         batches.append((t, s))
@@ -192,9 +205,7 @@ def run_ours(args, rank, world, local_rank):
     dev_ms = float(sum(step_ms))
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dev_ms = float(tt.item())
+        dev_ms = max_over_ranks(dev_ms, dev)
         dist.barrier()
     status = pst.cpu().numpy()
     lens = plen.cpu().numpy()
