@@ -118,17 +118,18 @@ struct TraceDom {
 __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__restrict__ f,
                                            const float2 *__restrict__ grads, int target, int source,
                                            float2 *__restrict__ out, int32_t max_pts, int32_t max_steps,
-                                           int32_t *len_out, int32_t *status_out) {
+                                           int32_t *len_out, int32_t *status_out, bool active) {
     const float eps2 = kEpsWedge * kEpsWedge;
     int v = source;
     int len = 0;
     int status = DD_TRACE_STEP_LIMIT;
     int states = 1;                // vertex and edge states entered (the step cap counts these)
-    out[len++] = p.xy[v];
+    bool fin = !active;            // finished (or a padding lane): idles until the warp is done
+    if (active) out[len++] = p.xy[v];
 
     // vertex (fan-scan) state
     bool scanning = true;
-    int t0 = p.vt[p.vt_off[v]];
+    int t0 = active ? p.vt[p.vt_off[v]] : 0;
     int scan_t = t0, t0_cw = -1;
     bool ccw = true, adj = false;
     int best = -1;
@@ -141,44 +142,55 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
     float la = 0.f, lb = 0.f;
     float2 pa = make_float2(0.f, 0.f), pb = pa;
 
+// The macros end the current iteration with `continue` when the path ends;
+// they are used as statements inside braces (no do-while wrapper, so that
+// `continue` reaches the walk loop).
 #define DD_PUSH(pt)                              \
-    do {                                         \
-        if (len >= max_pts) {                  \
-            status = DD_TRACE_TRUNCATED;         \
-            goto done;                           \
-        }                                        \
-        out[len++] = (pt);                       \
-    } while (0)
+    if (len >= max_pts) {                        \
+        status = DD_TRACE_TRUNCATED;             \
+        fin = true;                              \
+        continue;                                \
+    }                                            \
+    out[len++] = (pt);
 #define DD_ENTER_VERTEX(vert, tri_id)            \
-    do {                                         \
-        v = (vert);                              \
-        scanning = true;                         \
-        t0 = (tri_id);                           \
-        scan_t = t0;                             \
-        t0_cw = -1;                              \
-        ccw = true;                              \
-        adj = false;                             \
-        best = -1;                               \
-        best_g2 = 0.f;                           \
-        if (++states > max_steps) goto done;   \
-        if (v == target) {                       \
-            status = DD_TRACE_OK;                \
-            goto done;                           \
-        }                                        \
-    } while (0)
+    v = (vert);                                  \
+    scanning = true;                             \
+    t0 = (tri_id);                               \
+    scan_t = t0;                                 \
+    t0_cw = -1;                                  \
+    ccw = true;                                  \
+    adj = false;                                 \
+    best = -1;                                   \
+    best_g2 = 0.f;                               \
+    if (++states > max_steps) {                  \
+        fin = true;                              \
+        continue;                                \
+    }                                            \
+    if (v == target) {                           \
+        status = DD_TRACE_OK;                    \
+        fin = true;                              \
+        continue;                                \
+    }
 #define DD_SLIDE()                                                     \
-    do {                                                               \
+    {                                                                  \
         const float fa = f[ea], fb = f[eb];                            \
         const bool a_low = fa < fb || (fa == fb && ea < eb);           \
         DD_PUSH(a_low ? pa : pb);                                      \
         DD_ENTER_VERTEX(a_low ? ea : eb, cur_id);                      \
-    } while (0)
-
-    if (v == target) {
-        status = DD_TRACE_OK;
-        goto done;
     }
-    for (int64_t iter = 0; iter < 16LL * max_steps; ++iter) {
+
+    if (active && v == target) {
+        status = DD_TRACE_OK;
+        fin = true;
+    }
+    // The warp votes at the top of every iteration, so its threads reconverge
+    // once per step instead of drifting into different iterations; finished
+    // threads idle here until the last path of the warp ends.
+    const int64_t iter_cap = 16LL * max_steps;
+    for (int64_t iter = 0;; ++iter) {
+        if (!fin && iter >= iter_cap) fin = true;
+        if (!__any_sync(0xffffffffu, !fin)) break;
+        if (fin) continue;
         if (!scanning && t_next < 0) {     // boundary edge: slide to the lower endpoint
             DD_SLIDE();
             continue;
@@ -231,7 +243,8 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
             if (adj) {                           // v lies on an edge incident on the target
                 DD_PUSH(p.xy[target]);
                 status = DD_TRACE_OK;
-                goto done;
+                fin = true;
+                continue;
             }
             if (best >= 0) {
                 const float s = __fdividef(1.0f, baj + bak);
@@ -253,7 +266,10 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
                     pb = b_pk;
                     la = lj;
                     lb = lk;
-                    if (++states > max_steps) goto done;
+                    if (++states > max_steps) {
+                        fin = true;
+                        continue;
+                    }
                 }
                 continue;
             }
@@ -285,7 +301,8 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
                 }
                 if (best_u < 0) {
                     status = DD_TRACE_STUCK;
-                    goto done;
+                    fin = true;
+                    continue;
                 }
                 DD_PUSH(best_p);
                 DD_ENTER_VERTEX(best_u, best_ut);
@@ -341,25 +358,31 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
                 la = lkeep;
                 lb = lc2;
             }
-            if (++states > max_steps) goto done;
+            if (++states > max_steps) {
+                fin = true;
+                continue;
+            }
             if (ea == target || eb == target) {   // an edge incident on the target
                 DD_PUSH(p.xy[target]);
                 status = DD_TRACE_OK;
-                goto done;
+                fin = true;
+                continue;
             }
         }
     }
-done:
 #undef DD_PUSH
 #undef DD_ENTER_VERTEX
 #undef DD_SLIDE
-    *len_out = len;
-    *status_out = status;
+    if (active) {
+        *len_out = len;
+        *status_out = status;
+    }
 }
 
 __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= p.total) return;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = gid < p.total;       // padding lanes stay in the warp's walk loop, idle
+    const int64_t id = active ? gid : 0;
     const int a = (int)(id / p.S);
     TraceDom d;
     d.rec = p.rec;
@@ -368,7 +391,7 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
     d.vt = p.vt;
     d.n_t = p.n_t;
     trace_path(d, p.fields + (int64_t)a * p.field_stride, p.grads + (int64_t)a * p.n_t, p.targets[a], p.sources[id],
-               p.out_xy + id * p.max_pts, p.max_pts, p.max_steps, p.out_len + id, p.out_status + id);
+               p.out_xy + id * p.max_pts, p.max_pts, p.max_steps, p.out_len + id, p.out_status + id, active);
 }
 
 // ---- several meshes in one launch: global target g belongs to domain tdom[g] (local index tloc[g])
@@ -402,13 +425,14 @@ __global__ void __launch_bounds__(64) batch_trace_kernel(const BatchTraceDom *__
                                                         const int32_t *__restrict__ path_target, int64_t total,
                                                         int32_t S, int32_t max_pts, float2 *__restrict__ out_xy,
                                                         int32_t *__restrict__ out_len, int32_t *__restrict__ out_status) {
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= total) return;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = gid < total;         // padding lanes stay in the warp's walk loop, idle
+    const int64_t id = active ? gid : 0;
     const int g = path_target ? path_target[id] : (int)(id / S);
     const BatchTraceDom q = doms[tdom[g]];
     const int a = tloc[g];
     trace_path(q.d, q.fields + (int64_t)a * q.n_v, q.grads + (int64_t)a * q.d.n_t, targets[g], sources[id],
-               out_xy + id * max_pts, max_pts, q.max_steps, out_len + id, out_status + id);
+               out_xy + id * max_pts, max_pts, q.max_steps, out_len + id, out_status + id, active);
 }
 
 }  // namespace
