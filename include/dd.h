@@ -55,11 +55,29 @@ typedef enum {
 enum { DD_F_KL = 1, DD_F_TV = 2 };
 
 /* arithmetic of the field evaluation:
- *  DD_PREC_FP32   FP32 CUDA-core evaluation of Eq. 34-35 term by term
+ *  DD_PREC_FP32   FP32 CUDA-core evaluation of Eq. 34-35 term by term, each
+ *                 log split into an exact exponent and a mantissa log.  For
+ *                 one or two targets the mantissa logs of a first pass come
+ *                 from the hardware base-2 logarithm; every row whose KL there
+ *                 is below DD_EXACT_BELOW (the rows near the target, x = t
+ *                 among them) is recomputed with the table-driven logarithm
+ *                 used for more targets.  The first pass's KL is within
+ *                 ln2 * DD_FAST_LOG_SPREAD of the table form (see
+ *                 dd_check_fast_log), so both keep 1e-5 relative accuracy.
  *  DD_PREC_BF16X3 KL cross term sum_b P[x,b] log P[t,b] as a tensor-core GEMM
  *                 of split BF16 hi/lo operands (hi*hi + hi*lo + lo*hi, FP32
  *                 accumulation); TV is always FP32 */
 enum { DD_PREC_FP32 = 0, DD_PREC_BF16X3 = 1 };
+#define DD_FAST_LOG_SPREAD 5.0e-7
+#define DD_EXACT_BELOW 0.05
+
+/* Measures, on the current device, the spread (maximum minus minimum) of the
+ * error of the hardware base-2 logarithm used by the FP32 first pass, over
+ * every float mantissa in [1, 2) against an FP64 reference, and writes it to
+ * *spread.  The FP32 path's error bound assumes *spread <= DD_FAST_LOG_SPREAD.
+ * Allocates and frees 512 KB of device memory.  Errors: DD_EINVAL (null),
+ * DD_ENOMEM, DD_ECUDA. */
+dd_status dd_check_fast_log(double *spread);
 
 /* per-path status written by the tracer */
 enum {
@@ -287,7 +305,7 @@ void dd_server_destroy(dd_server *sv);
  *   f_mask   DD_F_KL | DD_F_TV as in dd_distance
  *   out      device float32 [nf][T][n_v], layout as in dd_distance
  *   cuda_stream  stream for the work (NULL = legacy default stream)
- * Scratch: one fixed device array per GPU (12 MiB, held until the process
+ * Scratch: one fixed device array per GPU (16 MiB, held until the process
  * exits) holds the staged target rows, so T * k_pad must not exceed 1,048,576
  * (DD_EINVAL otherwise).  Every call shares that array: calls whose work
  * overlaps on the GPU (other streams, other host threads) race and must be

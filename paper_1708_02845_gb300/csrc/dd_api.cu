@@ -153,7 +153,7 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
         kl = nullptr;
         if (!tv) return DD_OK;
     }
-    st = ensure_scratch(ctx, S_STAGE, 3 * (size_t)T * m.k_pad * sizeof(float));
+    st = ensure_scratch(ctx, S_STAGE, 4 * (size_t)T * m.k_pad * sizeof(float));
     if (st != DD_OK) return st;
     float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
     launch_stage_targets(m.P, m.k_pad, m.k, d_targets, T, stage, ctx->stream);
@@ -793,6 +793,16 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
         return set_err(ctx, DD_ENOMEM, "host allocation failed");
     } catch (...) {
         return set_err(ctx, DD_EINVAL, "unexpected failure in dd_query_batch");
+    }
+}
+
+dd_status dd_check_fast_log(double *spread) {
+    if (!spread) return DD_EINVAL;
+    try {
+        std::string err;
+        return fast_log_spread(spread, err);
+    } catch (...) {
+        return DD_ENOMEM;
     }
 }
 

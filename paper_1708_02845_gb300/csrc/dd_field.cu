@@ -5,28 +5,32 @@
 //
 // Near the target the two logarithms agree to many digits and KL is a small
 // sum of nearly-cancelling terms, so each log is kept as an exact split
-//   log p = E ln2 + lm,   E integer,  lm = log(m) for the mantissa m in [1/sqrt2, sqrt2)
-// and the difference is formed as (lm_x - lm_t) + (E_x - E_t) ln2: |lm| <= 0.35
-// carries a small absolute error, the exponent difference is exact, and x = t
-// gives exactly 0 (the same code runs on both operands).  lm is table driven
-// (Tang, "Table-driven implementation of the logarithm function in IEEE
-// floating-point arithmetic", ACM TOMS 1990): a 128-entry table of
-// r_j = 1/c_j and log c_j over [1/2, 2), u = m r_j - 1 (|u| <= 1/128, one
-// rounding) and log(1 + u) from its degree-4 Taylor polynomial (truncation
-// below 1e-11).  The table is computed in FP64 by each CTA.  Every step uses
-// explicit round-to-nearest operations so all call sites produce bit-identical
-// values.  Arguments below FLT_MIN (including the 0 log 0 terms, whose weight
-// P[x,b] is 0) are evaluated at FLT_MIN.
+//   log p = E ln2 + lm,   E integer,  lm = log(m) for the mantissa m in [1, 2)
+// and the difference is formed as (lm_x - lm_t) + (E_x - E_t) ln2: lm < 0.7
+// carries an absolute error below 2^-25, the exponent difference is exact,
+// and x = t gives exactly 0 (the same code runs on both operands).  lm is
+// table driven (Tang, "Table-driven implementation of the logarithm function
+// in IEEE floating-point arithmetic", ACM TOMS 1990): a 128-entry table of
+// r_j = 1/c_j and log c_j over [1, 2) indexed by the top 7 mantissa bits,
+// u = m r_j - 1 (|u| <= 2^-8, one rounding) and log(1 + u) from its degree-3
+// Taylor polynomial (truncation |u|^4/4 <= 2^-34, far below the final
+// rounding of lm).  The table is computed in FP64 by each CTA.  Every step
+// uses explicit round-to-nearest operations so all call sites produce
+// bit-identical values.  Target-side arguments below FLT_MIN are evaluated
+// at FLT_MIN; row-side terms with P[x,b] = 0 contribute 0 (the 0 log 0 rule).
 //
 // Two kernels:
-//  * field_stream (few targets): one warp per row, lanes along b, 16-byte
-//    loads of P software-pipelined U float4 per lane ahead of the arithmetic,
-//    the target row and its logs staged in shared memory by a bulk async copy
-//    completing on an mbarrier, warp-shuffle reductions.  HBM-bound.
+//  * field_stream (few targets): one warp per group of R rows, lanes along b,
+//    16-byte loads of P software-pipelined U float4 per lane and row ahead
+//    of the arithmetic, the target row and its logs staged in shared memory
+//    by a bulk async copy completing on an mbarrier, a lane-replicated copy
+//    of the log table (no bank conflicts), warp-shuffle reductions.
 //  * field_tile (many targets): 64 rows x 64 targets per CTA, b in chunks of
 //    32 staged through shared memory, 4 x 4 register micro-tiles.  Each P
 //    element's logarithm is computed once per CTA and reused for 64 targets.
 #include <algorithm>
+#include <vector>
+#include <type_traits>
 #include <string>
 #include <cstdio>
 #include <tuple>
@@ -67,45 +71,53 @@ __device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
     return r;
 }
 
-constexpr int kLogTab = 128;                     // entries over [1/2, 2): 64 per binade
-constexpr int kMagicE = 0x4B400000;              // float 12582912 = 1.5 * 2^23: + e keeps e exact
-constexpr float kMagicEf = 12582912.0f;
+constexpr int kLogTab = 128;                     // entries over [1, 2)
+constexpr int kMagicHi = 0x4B400000 >> 9;        // funnel-shift high word: 0x4B400000 | (bits >> 23)
 
-// table entry j covers the mantissa range of float bits 17..23 == j (m in [1/2, 2)):
-// c_j is the range's midpoint, r_j = 1/c_j rounded, L_j = -log r_j
-__device__ __forceinline__ void build_log_table(float2 *tab) {
+// Entry j covers the mantissas m in [1 + j/128, 1 + (j+1)/128): r_j = 1/c_j
+// rounded (c_j the midpoint) at tab[j], L_j = -log r_j at tab[kLogTab + j],
+// both computed in FP64.
+__device__ __forceinline__ void build_log_table(float *tab) {
     for (int j = threadIdx.x; j < kLogTab; j += blockDim.x) {
-        const double c = j < 64 ? 0.5 + (j + 0.5) / 128.0 : 1.0 + (j - 64 + 0.5) / 64.0;
+        const double c = 1.0 + (j + 0.5) / kLogTab;
         const float r = (float)(1.0 / c);
-        tab[j] = make_float2(r, (float)(-log((double)r)));
+        tab[j] = r;
+        tab[kLogTab + j] = (float)(-log((double)r));
     }
 }
 
-// split logarithm of max(p, FLT_MIN): log = E ln2 + lm, m = p 2^-E in [1/sqrt2, sqrt2)
-__device__ __forceinline__ void split_log(float p, const float2 *tab, float &lm, float &E) {
-    p = fmaxf(p, FLT_MIN);
+// Split logarithm: log p = E ln2 + lm, p = m 2^E with m in [1, 2).
+// split_log_parts: the integer steps.  The exponent comes back biased, as the
+// float 12582912 + 127 + E (exact), so that a difference of two is the exact
+// exponent difference; one funnel shift forms it from the bit pattern.  Only
+// positive normal arguments give the logarithm; for +0 and -0 (and
+// subnormals) the result is finite and meaningless, which is harmless where
+// the argument is also the term's weight (the row side, P[x,b]) and is why
+// CLAMP (max with FLT_MIN, used for the target side) exists.  The library's
+// P holds no subnormals or -0.  split_log_tail: the floating-point steps from
+// the table entry (r, L).  Every caller runs exactly these operations, so
+// equal arguments give bit-identical results at every call site.
+template <bool CLAMP>
+__device__ __forceinline__ void split_log_parts(float p, int &mb, float &Eb, int &j) {
+    if (CLAMP) p = fmaxf(p, FLT_MIN);
     const int i = __float_as_int(p);
-    const int e = (i - 0x3f3504f3) >> 23;
-    const int mb = i - (e << 23);
-    E = __fadd_rn(__int_as_float(e + kMagicE), -kMagicEf);
-    const float2 t = tab[(mb >> 17) & (kLogTab - 1)];
-    const float u = __fmaf_rn(__int_as_float(mb), t.x, -1.0f);          // m/c - 1, one rounding
-    const float w = __fmaf_rn(__fmaf_rn(u, -0.25f, 1.0f / 3.0f), u, -0.5f);
-    lm = __fadd_rn(t.y, __fmaf_rn(__fmul_rn(u, u), w, u));             // log c + log(1 + u)
+    Eb = __int_as_float((int)__funnelshift_r((unsigned)i, (unsigned)kMagicHi, 23));
+    mb = (i & 0x007FFFFF) | 0x3F800000;
+    j = (i >> 16) & (kLogTab - 1);
 }
 
-// the same for two values at once (packed lanes; bit-identical to split_log)
-__device__ __forceinline__ void split_log2(float p0, float p1, const float2 *tab, f2_t &lm, f2_t &E) {
-    p0 = fmaxf(p0, FLT_MIN);
-    p1 = fmaxf(p1, FLT_MIN);
-    const int i0 = __float_as_int(p0), i1 = __float_as_int(p1);
-    const int e0 = (i0 - 0x3f3504f3) >> 23, e1 = (i1 - 0x3f3504f3) >> 23;
-    const int mb0 = i0 - (e0 << 23), mb1 = i1 - (e1 << 23);
-    E = add2(pk(__int_as_float(e0 + kMagicE), __int_as_float(e1 + kMagicE)), pk(-kMagicEf, -kMagicEf));
-    const float2 t0 = tab[(mb0 >> 17) & (kLogTab - 1)], t1 = tab[(mb1 >> 17) & (kLogTab - 1)];
-    const f2_t u = fma2(pk(__int_as_float(mb0), __int_as_float(mb1)), pk(t0.x, t1.x), pk(-1.0f, -1.0f));
-    const f2_t w = fma2(fma2(u, pk(-0.25f, -0.25f), pk(1.0f / 3.0f, 1.0f / 3.0f)), u, pk(-0.5f, -0.5f));
-    lm = add2(pk(t0.y, t1.y), fma2(mul2(u, u), w, u));
+__device__ __forceinline__ float split_log_tail(int mb, float r, float L) {
+    const float u = __fmaf_rn(__int_as_float(mb), r, -1.0f);            // m/c - 1, one rounding
+    const float w = __fmaf_rn(u, 1.0f / 3.0f, -0.5f);
+    return __fadd_rn(L, __fmaf_rn(__fmul_rn(u, u), w, u));              // log c + log(1 + u)
+}
+
+// table with one copy (stride 1)
+template <bool CLAMP>
+__device__ __forceinline__ void split_log(float p, const float *tab, float &lm, float &Eb) {
+    int mb, j;
+    split_log_parts<CLAMP>(p, mb, Eb, j);
+    lm = split_log_tail(mb, tab[j], tab[kLogTab + j]);
 }
 
 // one term of each sum; accumulators updated in place
@@ -130,11 +142,22 @@ __device__ __forceinline__ void accumulate2(f2_t px, f2_t lmx, f2_t ex, f2_t pt,
     tv = add2(tv, dp & 0x7fffffff7fffffffULL);
 }
 
-// stage_P / stage_L / stage_E: [T][k_pad] target row, its mantissa log and exponent
+// Hardware base-2 logarithm (lg2.approx) of the mantissa m in [1, 2) of a
+// float bit pattern i; the result lies in [0, 1].  Its error over all 2^23
+// mantissas spans at most kLg2Spread (checked exhaustively by the tests).
+__device__ __forceinline__ float lg2_mant(int i) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__int_as_float((i & 0x007FFFFF) | 0x3F800000)));
+    return y;
+}
+
+// stage_P / stage_L / stage_E / stage_F: [T][k_pad] target row, its mantissa
+// log (table), biased exponent and mantissa log2 (hardware), the target-side
+// arguments clamped at FLT_MIN
 __global__ void stage_targets_kernel(const float *__restrict__ P, int64_t k_pad, const int32_t *__restrict__ targets,
                                      int32_t T, float *__restrict__ sP, float *__restrict__ sL,
-                                     float *__restrict__ sE) {
-    __shared__ float2 tab[kLogTab];
+                                     float *__restrict__ sE, float *__restrict__ sF) {
+    __shared__ float tab[2 * kLogTab];
     build_log_table(tab);
     __syncthreads();
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,10 +165,11 @@ __global__ void stage_targets_kernel(const float *__restrict__ P, int64_t k_pad,
     if (b >= k_pad || a >= T) return;
     const float p = P[(int64_t)targets[a] * k_pad + b];
     float lm, E;
-    split_log(p, tab, lm, E);
+    split_log<true>(p, tab, lm, E);
     sP[(int64_t)a * k_pad + b] = p;
     sL[(int64_t)a * k_pad + b] = lm;
     sE[(int64_t)a * k_pad + b] = E;
+    sF[(int64_t)a * k_pad + b] = lg2_mant(__float_as_int(fmaxf(p, FLT_MIN)));
 }
 
 // ------------------------------------------------------------------ mbarrier helpers
@@ -194,22 +218,78 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
 
 
 // ------------------------------------------------------------------ few targets
-// smem: for each of TT targets, three k_pad float arrays (P, lm, E); grid.y walks target groups.
-template <int TT, int U>
-__global__ void __launch_bounds__(256) field_stream_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
-                                                           const float *__restrict__ sP, const float *__restrict__ sL,
-                                                           const float *__restrict__ sE, int32_t T,
-                                                           float *__restrict__ out_kl, float *__restrict__ out_tv,
-                                                           int *__restrict__ err_flag) {
+// streaming 16-byte load, issued where it is written (the asm is volatile and
+// ordered against the shared-memory reads that follow it)
+__device__ __forceinline__ float4 ld_stream(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+
+// Error bound of the fast pass.  DD_FAST_LOG_SPREAD bounds max - min of the
+// error of lg2_mant over [1, 2) (base-2 units; about 3.2e-7 measured,
+// dd_check_fast_log re-measures it).  A row's fast KL then differs from the
+// exact split form by at most ln2 * spread * sum_b P[x,b] = ln2 * spread: the
+// constant part of the error cancels between the row and target sides.  Rows
+// whose fast KL lies below DD_EXACT_BELOW are recomputed with the table
+// logarithm, so every row meets 1e-5 relative: ln2 * 5e-7 / 0.05 = 7e-6.
+constexpr float kExactBelow = (float)DD_EXACT_BELOW;
+
+// exact (table) KL of row x for one warp, from the staged target arrays
+__device__ __forceinline__ float kl_row_exact(const float *__restrict__ P, int64_t x, int64_t k_pad, int nvec,
+                                              const float *tP, const float *tL, const float *tE, const float *tab,
+                                              int lane) {
+    const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+    float k0 = 0.0f, k1 = 0.0f;
+    for (int c = lane; c < nvec; c += 32) {
+        const float4 v = __ldcg(row + c);
+        const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
+        const float4 l4 = reinterpret_cast<const float4 *>(tL)[c];
+        const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
+        const float px[4] = {v.x, v.y, v.z, v.w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
+        const float lt[4] = {l4.x, l4.y, l4.z, l4.w}, et[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float lm, Eb, tvd = 0.0f;
+            split_log<false>(px[q], tab, lm, Eb);
+            accumulate(px[q], lm, Eb, pt[q], lt[q], et[q], (q & 1) ? k1 : k0, tvd);
+        }
+    }
+    float skl = k0 + k1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) skl += __shfl_xor_sync(0xffffffffu, skl, o);
+    return skl;
+}
+
+// One target per grid row (blockIdx.y).  Dynamic smem: the target's four
+// k_pad arrays (P, lm, E, lg2 m) from one bulk copy each; static smem: the
+// log table for the exact recompute.  Each warp streams rows; per (row,
+// chunk of 32 U float4 columns) every lane loads U float4.  Two register
+// buffers alternate, so the loads of the next (row, chunk) are in flight
+// while the current one is computed.
+//
+// Fast pass per element: log2 P[x,b] - log2 P[t,b] = (lg2 m_x - lg2 m_t) +
+// (E_x - E_t), the exponent difference exact and the mantissa logs from the
+// hardware (lg2_mant); KL = ln2 * sum.  TV is exact.  A row whose KL is below
+// kExactBelow (the rows near the target, x = t among them) is recomputed
+// with the exact split form by its warp.
+template <int U>
+__global__ void __launch_bounds__(256, 2) field_stream_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
+                                                              const float *__restrict__ sP, const float *__restrict__ sL,
+                                                              const float *__restrict__ sE, const float *__restrict__ sF,
+                                                              int32_t T, float *__restrict__ out_kl,
+                                                              float *__restrict__ out_tv, int *__restrict__ err_flag) {
     extern __shared__ __align__(16) float smem[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ float2 tab[kLogTab];
-    build_log_table(tab);
-    const int a0 = blockIdx.y * TT;
-    const int nt = (T - a0) < TT ? (T - a0) : TT;
-    float *tP = smem;                          // [TT][k_pad]
-    float *tL = smem + TT * k_pad;
-    float *tE = smem + 2 * TT * k_pad;
+    __shared__ float tab[2 * kLogTab];
+    float *tP = smem;
+    float *tL = tP + k_pad;
+    float *tE = tL + k_pad;
+    float *tF = tE + k_pad;
+    const int a = blockIdx.y;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -217,13 +297,14 @@ __global__ void __launch_bounds__(256) field_stream_kernel(const float *__restri
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t row_bytes = (uint32_t)(k_pad * sizeof(float));
-        mbar_expect_tx(&bar, 3u * nt * row_bytes);
-        for (int j = 0; j < nt; ++j) {
-            bulk_g2s(tP + j * k_pad, sP + (int64_t)(a0 + j) * k_pad, row_bytes, &bar);
-            bulk_g2s(tL + j * k_pad, sL + (int64_t)(a0 + j) * k_pad, row_bytes, &bar);
-            bulk_g2s(tE + j * k_pad, sE + (int64_t)(a0 + j) * k_pad, row_bytes, &bar);
-        }
+        mbar_expect_tx(&bar, 4u * row_bytes);
+        bulk_g2s(tP, sP + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(tL, sL + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(tE, sE + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(tF, sF + (int64_t)a * k_pad, row_bytes, &bar);
     }
+    build_log_table(tab);
+    __syncthreads();
     if (!mbar_wait(&bar, 0, err_flag)) {
         // a CTA whose wait gave up must not return while its copies may still land:
         // wait once more (also bounded) before exiting
@@ -234,73 +315,102 @@ __global__ void __launch_bounds__(256) field_stream_kernel(const float *__restri
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nvec = k_pad >> 2;                       // float4 per row
+    const int nvec = (int)(k_pad >> 2);                    // float4 per row
     const int64_t nchunk = (nvec + 32 * U - 1) / (32 * U);
-    // software pipeline over (row, chunk): the loads of the next chunk are in
-    // flight while the current one is computed
-    float4 nxt[U];
-    auto fetch = [&](int64_t x, int64_t ch) {
-        const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+    const int64_t nfull = nvec / (32 * U);                 // chunks with every lane's U float4 in the row
+    float *okl = out_kl ? out_kl + (int64_t)a * n_v : nullptr;
+    float *otv = out_tv ? out_tv + (int64_t)a * n_v : nullptr;
+    const float4 *tP4 = reinterpret_cast<const float4 *>(tP) + lane;
+    const float4 *tF4 = reinterpret_cast<const float4 *>(tF) + lane;
+    const float4 *tE4 = reinterpret_cast<const float4 *>(tE) + lane;
+
+    float4 buf[2][U];
+    f2_t kl = 0ULL, tv = 0ULL;
+
+    auto fetch = [&](float4(&b)[U], int64_t x, int64_t ch) {
+        const int c0 = (int)ch * 32 * U;
+        const bool full = ch < nfull;
+        const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad) + c0 + lane;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            b[u] = (full || c0 + u * 32 + lane < nvec) ? ld_stream(row + u * 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    // one item; FULL: every lane's U float4 lie inside the row (no per-u test)
+    auto compute = [&](const float4(&b)[U], int64_t ch, auto full_tag) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        const f2_t mone = pk(-1.0f, -1.0f);
+        const int c0 = (int)ch * 32 * U;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t c = ch * 32 * U + u * 32 + lane;
-            nxt[u] = c < nvec ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!FULL && c0 + u * 32 + lane >= nvec) break;
+            const float4 p4 = tP4[c0 + u * 32];
+            const float4 f4 = tF4[c0 + u * 32];
+            const float4 e4 = tE4[c0 + u * 32];
+            const float px[4] = {b[u].x, b[u].y, b[u].z, b[u].w};
+            float lf[4], eb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = __float_as_int(px[q]);
+                lf[q] = lg2_mant(i);
+                eb[q] = __int_as_float((int)__funnelshift_r((unsigned)i, (unsigned)kMagicHi, 23));
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const f2_t p2 = pk(px[2 * h], px[2 * h + 1]);
+                const f2_t pt2 = h ? pk(p4.z, p4.w) : pk(p4.x, p4.y);
+                const f2_t ft2 = h ? pk(f4.z, f4.w) : pk(f4.x, f4.y);
+                const f2_t et2 = h ? pk(e4.z, e4.w) : pk(e4.x, e4.y);
+                const f2_t d = fma2(ft2, mone, pk(lf[2 * h], lf[2 * h + 1]));
+                const f2_t de = fma2(et2, mone, pk(eb[2 * h], eb[2 * h + 1]));
+                kl = fma2(p2, add2(d, de), kl);
+                tv = add2(tv, fma2(pt2, mone, p2) & 0x7fffffff7fffffffULL);
+            }
         }
     };
-    int64_t x = warp, ch = 0;
-    if (x < n_v) fetch(x, 0);
-    f2_t kl[TT], tv[TT];
+    auto finish = [&](int64_t x) {
+        float k0, k1, t0v, t1v;
+        upk(kl, k0, k1);
+        upk(tv, t0v, t1v);
+        float skl = k0 + k1, stv = t0v + t1v;
 #pragma unroll
-    for (int j = 0; j < TT; ++j) kl[j] = tv[j] = 0ULL;
-    while (x < n_v) {
-        float4 cur[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) cur[u] = nxt[u];
-        int64_t xn = x, chn = ch + 1;
-        if (chn == nchunk) {
-            chn = 0;
-            xn += nwarps;
+        for (int o = 16; o > 0; o >>= 1) {
+            skl += __shfl_xor_sync(0xffffffffu, skl, o);
+            stv += __shfl_xor_sync(0xffffffffu, stv, o);
         }
-        if (xn < n_v) fetch(xn, chn);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t c = ch * 32 * U + u * 32 + lane;
-            if (c >= nvec) continue;
-            f2_t lm01, e01, lm23, e23;
-            split_log2(cur[u].x, cur[u].y, tab, lm01, e01);
-            split_log2(cur[u].z, cur[u].w, tab, lm23, e23);
-            const f2_t p01 = pk(cur[u].x, cur[u].y), p23 = pk(cur[u].z, cur[u].w);
-#pragma unroll
-            for (int j = 0; j < TT; ++j) {
-                if (j >= nt) break;
-                const float4 p4 = reinterpret_cast<const float4 *>(tP + j * k_pad)[c];
-                const float4 l4 = reinterpret_cast<const float4 *>(tL + j * k_pad)[c];
-                const float4 e4 = reinterpret_cast<const float4 *>(tE + j * k_pad)[c];
-                accumulate2(p01, lm01, e01, pk(p4.x, p4.y), pk(l4.x, l4.y), pk(e4.x, e4.y), kl[j], tv[j]);
-                accumulate2(p23, lm23, e23, pk(p4.z, p4.w), pk(l4.z, l4.w), pk(e4.z, e4.w), kl[j], tv[j]);
-            }
+        skl *= kLn2;
+        if (okl && skl < kExactBelow)   // warp-uniform: every lane holds the same sum
+            skl = kl_row_exact(P, x, k_pad, nvec, tP, tL, tE, tab, lane);
+        if (lane == 0) {
+            if (okl) okl[x] = skl;
+            if (otv) otv[x] = stv;
         }
-        if (ch == nchunk - 1) {
-#pragma unroll
-            for (int j = 0; j < TT; ++j) {
-                float k0, k1, t0v, t1v;
-                upk(kl[j], k0, k1);
-                upk(tv[j], t0v, t1v);
-                float skl = k0 + k1, stv = t0v + t1v;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    skl += __shfl_xor_sync(0xffffffffu, skl, o);
-                    stv += __shfl_xor_sync(0xffffffffu, stv, o);
-                }
-                if (lane == 0 && j < nt) {
-                    if (out_kl) out_kl[(int64_t)(a0 + j) * n_v + x] = skl;
-                    if (out_tv) out_tv[(int64_t)(a0 + j) * n_v + x] = stv;
-                }
-                kl[j] = tv[j] = 0ULL;
-            }
+        kl = tv = 0ULL;
+    };
+    // (row, chunk) items in order: row x = warp, warp + nwarps, ...
+    auto advance = [&](int64_t &x, int64_t &ch) {
+        if (++ch == nchunk) {
+            ch = 0;
+            x += nwarps;
         }
-        x = xn;
-        ch = chn;
+    };
+    int64_t x = warp, ch = 0;     // item being computed
+    int64_t xf = warp, chf = 0;   // next item to fetch
+    if (x >= n_v) return;
+    fetch(buf[0], xf, chf);
+    advance(xf, chf);
+    for (;;) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (xf < n_v) fetch(buf[s ^ 1], xf, chf);
+            advance(xf, chf);
+            if (ch < nfull)
+                compute(buf[s], ch, std::true_type());
+            else
+                compute(buf[s], ch, std::false_type());
+            if (ch == nchunk - 1) finish(x);
+            advance(x, ch);
+            if (x >= n_v) return;
+        }
     }
 }
 
@@ -315,7 +425,7 @@ template <int TM, int TN, int RM, int CN>
 struct TileShape {
     static constexpr int ROWG = TM / RM, COLG = TN / CN;
     static_assert(ROWG * COLG == 256, "256 threads");
-    static constexpr size_t smem_bytes = (3 * kTileB * (TM + TN)) * sizeof(float) + kLogTab * sizeof(float2);
+    static constexpr size_t smem_bytes = (3 * kTileB * (TM + TN) + 2 * kLogTab) * sizeof(float);
 };
 
 // one output tile (rows x0.., targets a0..) of one problem; tsm holds the
@@ -325,7 +435,7 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
                                           const float *__restrict__ sP, const float *__restrict__ sL,
                                           const float *__restrict__ sE, int32_t T, float *__restrict__ out_kl,
                                           float *__restrict__ out_tv, int64_t x0, int a0, float *tsm,
-                                          const float2 *tab) {
+                                          const float *tab) {
     constexpr int COLG = TN / CN;
     float (*xP)[TM] = reinterpret_cast<float (*)[TM]>(tsm);
     float (*xL)[TM] = reinterpret_cast<float (*)[TM]>(tsm + 1 * kTileB * TM);
@@ -365,7 +475,7 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     float lm, E;
-                    split_log(vals[q], tab, lm, E);
+                    split_log<false>(vals[q], tab, lm, E);
                     xP[cb + e + q][r] = vals[q];
                     xL[cb + e + q][r] = lm;
                     xE[cb + e + q][r] = E;
@@ -451,7 +561,7 @@ __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restr
                                                          const float *__restrict__ sE, int32_t T,
                                                          float *__restrict__ out_kl, float *__restrict__ out_tv) {
     extern __shared__ __align__(16) float tsm[];
-    float2 *tab = reinterpret_cast<float2 *>(tsm + 3 * kTileB * (TM + TN));
+    float *tab = tsm + 3 * kTileB * (TM + TN);
     build_log_table(tab);
     __syncthreads();
     tile_body<TM, TN, RM, CN>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, (int64_t)blockIdx.x * TM,
@@ -468,17 +578,6 @@ void launch_tile(const float *P, int64_t n_v, int64_t k_pad, const float *sP, co
 }
 
 int g_num_sms = 0;
-
-// prefetch depth of the streaming kernel (float4 per lane in flight): 8 unless
-// DD_STREAM_UNROLL=4 asks for the shallower variant
-int stream_unroll() {
-    static int u = 0;
-    if (u == 0) {
-        const char *e = getenv("DD_STREAM_UNROLL");
-        u = (e && atoi(e) == 4) ? 4 : 8;
-    }
-    return u;
-}
 
 int num_sms() {
     if (g_num_sms == 0) {
@@ -498,7 +597,7 @@ __global__ void __launch_bounds__(256, 2) batch_tile_kernel(const BatchProblem *
                                                          const BatchItem *__restrict__ items, int32_t n_items,
                                                          int32_t *__restrict__ counter) {
     extern __shared__ __align__(16) float tsm[];
-    __shared__ float2 tab[kLogTab];
+    __shared__ float tab[2 * kLogTab];
     __shared__ int cur;
     build_log_table(tab);
     __syncthreads();
@@ -531,7 +630,7 @@ __global__ void __launch_bounds__(256, 2) batch_tile_kernel(const BatchProblem *
 __global__ void batch_stage_kernel(const BatchProblem *__restrict__ probs, const int32_t *__restrict__ tprob,
                                    const int32_t *__restrict__ tlocal, const int32_t *__restrict__ targets,
                                    int64_t k_max) {
-    __shared__ float2 tab[kLogTab];
+    __shared__ float tab[2 * kLogTab];
     build_log_table(tab);
     __syncthreads();
     const int g = blockIdx.y;
@@ -540,7 +639,7 @@ __global__ void batch_stage_kernel(const BatchProblem *__restrict__ probs, const
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < q.k_pad; b += (int64_t)gridDim.x * blockDim.x) {
         const float p = q.P[(int64_t)targets[g] * q.k_pad + b];
         float lm, E;
-        split_log(p, tab, lm, E);
+        split_log<true>(p, tab, lm, E);
         const int64_t o = (int64_t)a * q.k_pad + b;
         const_cast<float *>(q.sP)[o] = p;
         const_cast<float *>(q.sL)[o] = lm;
@@ -619,8 +718,9 @@ void launch_stage_targets(const float *P, int64_t k_pad, int64_t /*k*/, const in
     float *sP = reinterpret_cast<float *>(stage);
     float *sL = sP + (int64_t)T * k_pad;
     float *sE = sL + (int64_t)T * k_pad;
+    float *sF = sE + (int64_t)T * k_pad;
     dim3 g((unsigned)((k_pad + 255) / 256), (unsigned)T);
-    stage_targets_kernel<<<g, 256, 0, s>>>(P, k_pad, targets, T, sP, sL, sE);
+    stage_targets_kernel<<<g, 256, 0, s>>>(P, k_pad, targets, T, sP, sL, sE, sF);
 }
 
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, float *out_kl,
@@ -628,26 +728,21 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
     const float *sP = reinterpret_cast<const float *>(stage);
     const float *sL = sP + (int64_t)T * k_pad;
     const float *sE = sL + (int64_t)T * k_pad;
-    if (T <= 2 && 3 * (size_t)k_pad * sizeof(float) <= 200 * 1024) {
-        // one target per grid row; loads run `U` float4 per lane ahead of the arithmetic
-        const size_t smem = 3 * (size_t)k_pad * sizeof(float);
-        const int U = stream_unroll();
-        int64_t rows_blocks = (n_v + 7) / 8;
-        auto go = [&](auto kern) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
-            if (per_sm < 1) per_sm = 1;
-            int64_t grid_x = (int64_t)num_sms() * per_sm / T;
-            if (grid_x < 1) grid_x = 1;
-            if (grid_x > rows_blocks) grid_x = rows_blocks;
-            kern<<<dim3((unsigned)grid_x, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv,
-                                                                       err_flag);
-        };
-        if (U == 8)
-            go(field_stream_kernel<1, 8>);
-        else
-            go(field_stream_kernel<1, 4>);
+    const float *sF = sE + (int64_t)T * k_pad;
+    const size_t smem = 4 * (size_t)k_pad * sizeof(float);
+    if (T <= 2 && smem <= 200 * 1024) {
+        // one target per grid row; loads run 8 float4 per lane ahead of the arithmetic
+        auto kern = field_stream_kernel<8>;
+        const int64_t row_blocks = (n_v + 7) / 8;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+        if (per_sm < 1) per_sm = 1;
+        int64_t grid_x = (int64_t)num_sms() * per_sm / T;
+        if (grid_x < 1) grid_x = 1;
+        if (grid_x > row_blocks) grid_x = row_blocks;
+        kern<<<dim3((unsigned)grid_x, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv,
+                                                                   err_flag);
         return;
     }
     const int v = tune_variant(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
@@ -695,4 +790,54 @@ std::string tuning_table() {
         out += buf;
     }
     return out;
+}
+
+// ------------------------------------------------------------------ fast-log self-check
+namespace {
+// per block: min and max of lg2_mant(m) - log2(m) over 256 consecutive mantissas
+__global__ void fast_log_error_kernel(double *__restrict__ bmin, double *__restrict__ bmax) {
+    __shared__ double smin[256], smax[256];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;           // mantissa bits, 0 .. 2^23 - 1
+    const int bits = 0x3F800000 | j;
+    const double e = (double)lg2_mant(bits) - log2((double)__int_as_float(bits));
+    smin[threadIdx.x] = e;
+    smax[threadIdx.x] = e;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bmin[blockIdx.x] = smin[0];
+        bmax[blockIdx.x] = smax[0];
+    }
+}
+}  // namespace
+
+dd_status fast_log_spread(double *spread, std::string &err) {
+    constexpr int kBlocks = (1 << 23) / 256;
+    double *d = nullptr;
+    if (cudaMalloc(&d, 2 * kBlocks * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        err = "fast-log check: device allocation failed";
+        return DD_ENOMEM;
+    }
+    fast_log_error_kernel<<<kBlocks, 256>>>(d, d + kBlocks);
+    std::vector<double> h(2 * kBlocks);
+    cudaError_t e = cudaMemcpy(h.data(), d, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        err = std::string("fast-log check: ") + cudaGetErrorString(e);
+        return DD_ECUDA;
+    }
+    double lo = h[0], hi = h[kBlocks];
+    for (int b = 0; b < kBlocks; ++b) {
+        lo = std::min(lo, h[b]);
+        hi = std::max(hi, h[kBlocks + b]);
+    }
+    *spread = hi - lo;
+    return DD_OK;
 }

@@ -75,8 +75,10 @@ dd_status run_pcg(DevMesh &m, double rtol, int32_t max_iter, cudaStream_t s, int
 // Store a host FP64 P [n_v][k] into m.P with the same clamp/flush as the solver.
 dd_status store_poisson(DevMesh &m, const double *P, cudaStream_t s, std::string &err);
 
-// Per-target staging of P[t,:] and its split logarithm: stage[a][b] =
-// (P[t_a,b], log-mantissa, exponent, 0).
+// Per-target staging of P[t,:] and its split logarithm: four [T][k_pad] float
+// arrays back to back -- P[t_a,b], the log-mantissa lm (table), the exponent E
+// as the biased float 12582912 + 127 + E (exact; only differences of two are
+// used), and the hardware base-2 log of the mantissa (streaming kernel).
 void launch_stage_targets(const float *P, int64_t k_pad, int64_t k, const int32_t *targets, int32_t T,
                           float4 *stage, cudaStream_t s);
 // FP32 fields.  out_kl / out_tv: [T][n_v] (either may be null).
@@ -103,6 +105,8 @@ void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, con
 void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, int32_t n_items, int32_t *d_counter,
                          cudaStream_t s);
 std::string tuning_table();
+// spread (max - min) of the hardware mantissa log's error over [1, 2), in base-2 units
+dd_status fast_log_spread(double *spread, std::string &err);
 
 // Tracer: per-field triangle gradients into grads [T][n_t], then T*S paths.
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,

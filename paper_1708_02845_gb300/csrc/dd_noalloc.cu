@@ -22,7 +22,7 @@
 
 namespace {
 
-constexpr int64_t kNoallocStageFloats = 3LL * (1LL << 20);   // 3 arrays x T*k_pad <= 2^20 floats (12 MiB)
+constexpr int64_t kNoallocStageFloats = 4LL * (1LL << 20);   // 4 arrays x T*k_pad <= 2^20 floats (16 MiB)
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) float g_noalloc_stage[kNoallocStageFloats];
@@ -58,7 +58,7 @@ extern "C" dd_status dd_distance_noalloc(const float *P, int64_t n_v, int64_t k_
     if (!P || !targets || !out) return DD_EINVAL;
     if (n_v < 1 || T < 1 || k_pad < 4 || (k_pad % 4) != 0) return DD_EINVAL;
     if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV))) return DD_EINVAL;
-    if ((int64_t)T * k_pad > kNoallocStageFloats / 3) return DD_EINVAL;   // beyond the fixed scratch
+    if ((int64_t)T * k_pad > kNoallocStageFloats / 4) return DD_EINVAL;   // beyond the fixed scratch
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libdd.so")
 DD_OK, DD_EINVAL, DD_ENOMEM, DD_ECUDA, DD_ESTATE, DD_ENOTCONV, DD_ETIMEOUT, DD_EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7
 DD_F_KL, DD_F_TV = 1, 2
 DD_PREC_FP32, DD_PREC_BF16X3 = 0, 1
+DD_FAST_LOG_SPREAD, DD_EXACT_BELOW = 5.0e-7, 0.05
 DD_TRACE_OK, DD_TRACE_STUCK, DD_TRACE_STEP_LIMIT, DD_TRACE_TRUNCATED = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "DD_OK", -1: "DD_EINVAL", -2: "DD_ENOMEM", -3: "DD_ECUDA", -4: "DD_ESTATE",
@@ -54,6 +55,7 @@ _SIGS = {
     "dd_distance_noalloc": (_i32, [_p, _i64, _i64, _p, _i32, _u32, _p, _p]),
     "dd_query_batch": (_i32, [_p, _i32, _p, _p, _p, _p, _i32, _u32, _u32, _i32, _p, _p, _p, _p]),
     "dd_tuning_table": (_i32, [ctypes.c_char_p, _i32]),
+    "dd_check_fast_log": (_i32, [ctypes.POINTER(ctypes.c_double)]),
     "dd_server_create": (_i32, [_p, _i64, _i32, _i32, _i32, ctypes.POINTER(_p)]),
     "dd_server_submit": (_i32, [_p, _i64, _i32, _i32, _p, _i32]),
     "dd_server_poll": (_i32, [_p, _i32, _p, _p, _p]),
@@ -230,6 +232,15 @@ def dd_query_batch(ctx, mesh_ids, T_per, targets, sources, S: int, f_mask: int, 
     s = _host_i32(sources) if S > 0 else np.zeros(1, np.int32)
     _check(ctx, lib.dd_query_batch(ctx, len(mids), ptr(mids), ptr(tp), ptr(t), ptr(s), S, f_mask, trace_f, max_pts,
                                    ptr(out_fields), ptr(out_xy), ptr(out_len), ptr(out_status)))
+
+
+def dd_check_fast_log() -> float:
+    """Spread (max - min) of the hardware base-2 log's error over [1, 2)."""
+    v = ctypes.c_double()
+    st = lib.dd_check_fast_log(ctypes.byref(v))
+    if st != DD_OK:
+        raise DDError(st, "dd_check_fast_log failed")
+    return v.value
 
 
 def dd_tuning_table() -> str:

@@ -79,7 +79,8 @@ def _fields(dd, ctx, mid, n_v, targets, host=False):
 
 
 @pytest.mark.parametrize("name,T", [("disk", 1), ("grid24", 1), ("grid24", 2), ("grid24", 5),
-                                    ("grid37", 3), ("grid37", 70), ("grid140", 8)])
+                                    ("grid37", 3), ("grid37", 70), ("grid140", 1), ("grid140", 2),
+                                    ("grid140", 8)])
 def test_fields_on_oracle_kernel(env, name, T):
     """Field kernels alone: the oracle's P installed, fields vs the oracle's fields."""
     dd, ctx = env
@@ -97,6 +98,40 @@ def test_fields_on_oracle_kernel(env, name, T):
         inf = ~np.isfinite(ref_kl)
         assert np.all(got[0, a][inf] >= 87.0)            # +inf rows: log argument clamped at FLT_MIN
         assert np.all(np.isfinite(got[:, a]))
+    dd.dd_unload_mesh(ctx, mid)
+
+
+def test_fast_log_spread(env):
+    """The hardware mantissa log's error spread stays inside the bound the FP32
+    streaming pass relies on (measured over all 2^23 mantissas)."""
+    dd, _ = env
+    spread = dd.dd_check_fast_log()
+    assert 0.0 < spread <= dd.DD_FAST_LOG_SPREAD, spread
+
+
+@pytest.mark.parametrize("name", ["disk", "grid140"])
+def test_stream_pass_against_table_path(env, name):
+    """One target (streaming kernel, hardware mantissa log with exact recompute
+    of rows below DD_EXACT_BELOW) against the same target among three (tile
+    kernel, table log): rows below the threshold agree to FP32 summation
+    rounding, the others within ln2 * DD_FAST_LOG_SPREAD plus rounding."""
+    dd, ctx = env
+    wl, po, P = case(name)
+    mid = load(dd, ctx, wl.mesh)
+    dd.dd_set_poisson_kernel(ctx, mid, P)
+    n = wl.mesh.n_v
+    for t in list(wl.targets[:4]):
+        others = [int(po.I[(i * 7919) % po.m]) for i in (1, 2)]
+        one = _fields(dd, ctx, mid, n, [t])
+        three = _fields(dd, ctx, mid, n, [t] + others)
+        kl1, kl3 = one[0, 0].astype(np.float64), three[0, 0].astype(np.float64)
+        assert np.all(np.abs(one[1, 0] - three[1, 0]) <= 2e-6 * np.maximum(three[1, 0], 1.0))   # TV: summation order
+        near = kl3 < dd.DD_EXACT_BELOW
+        assert np.all(np.abs(kl1 - kl3)[near] <= 2e-6 * np.maximum(kl3[near], 1e-2))
+        far = ~near & np.isfinite(kl3)
+        bound = math.log(2.0) * dd.DD_FAST_LOG_SPREAD + 1e-6 * kl3[far]
+        assert np.all(np.abs(kl1 - kl3)[far] <= bound)
+        assert one[0, 0, t] == 0.0
     dd.dd_unload_mesh(ctx, mid)
 
 
