@@ -294,9 +294,13 @@ dd_status dd_load_mesh(dd_ctx *ctx, const double *xy, int64_t n_v, const int32_t
             g4[2 * t + 1] = make_float4(g[4], g[5], 0.f, 0.f);
             const int32_t *v = &h.tri[3 * t], *nb = &h.tnbr[3 * t];
             const float2 p0 = xyf[v[0]], p1 = xyf[v[1]], p2 = xyf[v[2]];
+            // squared norms of the three hat gradients (the third is minus the sum of the others)
+            const double q0 = (double)g[0] * g[0] + (double)g[1] * g[1];
+            const double q1 = (double)g[2] * g[2] + (double)g[3] * g[3];
+            const double q2 = (double)g[4] * g[4] + (double)g[5] * g[5];
             rec[4 * t] = make_int4(v[0], v[1], v[2], nb[0]);
-            rec[4 * t + 1] = make_int4(nb[1], nb[2], fbits(g[0]), fbits(g[1]));
-            rec[4 * t + 2] = make_int4(fbits(g[2]), fbits(g[3]), fbits(p0.x), fbits(p0.y));
+            rec[4 * t + 1] = make_int4(nb[1], nb[2], fbits((float)q0), fbits((float)q1));
+            rec[4 * t + 2] = make_int4(fbits((float)q2), 0, fbits(p0.x), fbits(p0.y));
             rec[4 * t + 3] = make_int4(fbits(p1.x), fbits(p1.y), fbits(p2.x), fbits(p2.y));
         }
         auto undo = [&](dd_status s2) {
@@ -472,10 +476,10 @@ dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32
         if ((st = ensure_scratch(ctx, S_STATUS, n * sizeof(int32_t))) != DD_OK) return st;
         dst = reinterpret_cast<int32_t *>(ctx->scratch[S_STATUS]);
     }
-    if ((st = ensure_scratch(ctx, S_GRAD, (size_t)T * m.n_t * sizeof(float2))) != DD_OK) return st;
+    if ((st = ensure_scratch(ctx, S_GRAD, trace_scratch_bytes(m, T))) != DD_OK) return st;
     launch_trace(m, d_fields, m.n_v, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
                  reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), T, S, max_pts, dxy, dlen, dst,
-                 reinterpret_cast<float2 *>(ctx->scratch[S_GRAD]), ctx->stream);
+                 ctx->scratch[S_GRAD], ctx->stream);
     CK(cudaGetLastError(), "trace kernel launch");
     bool host = false;
     if (sx == 0) {
@@ -620,7 +624,7 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
         const int nf = popcount2(f_mask);
         std::vector<DevMesh *> ms(n_items);
         std::vector<int64_t> foff(n_items + 1, 0), toff(n_items + 1, 0);
-        int64_t stage_floats = 0, grad_pairs = 0, max_nt = 0, max_k = 0;
+        int64_t stage_floats = 0, grad_bytes = 0, max_nt = 0, max_nv = 0, max_k = 0;
         for (int i = 0; i < n_items; ++i) {
             dd_status st = get_mesh(ctx, mesh_ids[i], &ms[i]);
             if (st != DD_OK) return st;
@@ -629,8 +633,9 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
             toff[i + 1] = toff[i] + T_per[i];
             foff[i + 1] = foff[i] + (int64_t)nf * T_per[i] * ms[i]->n_v;
             stage_floats += 3LL * T_per[i] * ms[i]->k_pad;
-            grad_pairs += (int64_t)T_per[i] * ms[i]->n_t;
+            grad_bytes += (int64_t)trace_scratch_bytes(*ms[i], T_per[i]);
             max_nt = std::max(max_nt, ms[i]->n_t);
+            max_nv = std::max(max_nv, ms[i]->n_v);
             max_k = std::max(max_k, ms[i]->k_pad);
         }
         const int32_t nT = (int32_t)toff[n_items];
@@ -663,9 +668,9 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
             dfields = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
         }
         if ((st = ensure_scratch(ctx, S_STAGE, (size_t)stage_floats * sizeof(float))) != DD_OK) return st;
-        if (S > 0 && (st = ensure_scratch(ctx, S_GRAD, (size_t)grad_pairs * sizeof(float2))) != DD_OK) return st;
+        if (S > 0 && (st = ensure_scratch(ctx, S_GRAD, (size_t)grad_bytes)) != DD_OK) return st;
         float *stage = reinterpret_cast<float *>(ctx->scratch[S_STAGE]);
-        float2 *grads = reinterpret_cast<float2 *>(ctx->scratch[S_GRAD]);
+        char *grads = reinterpret_cast<char *>(ctx->scratch[S_GRAD]);
 
         std::vector<BatchProblem> probs(n_items);
         int64_t so = 0;
@@ -727,8 +732,8 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
             for (int i = 0; i < n_items; ++i) {
                 fill_batch_trace_dom(meta.data() + o_doms + i * dom_bytes, *ms[i],
                                      (trace_f == DD_F_TV && probs[i].out_tv) ? probs[i].out_tv : probs[i].out_kl,
-                                     grads + go);
-                go += (int64_t)T_per[i] * ms[i]->n_t;
+                                     T_per[i], grads ? grads + go : nullptr);
+                go += (int64_t)trace_scratch_bytes(*ms[i], T_per[i]);
             }
         }
         for (size_t j = 0; j < order.size(); ++j)
@@ -766,7 +771,7 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
             launch_batch_trace(dmeta + o_doms, reinterpret_cast<const int32_t *>(dmeta + o_tprob),
                                reinterpret_cast<const int32_t *>(dmeta + o_tloc),
                                reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
-                               reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), nT, S, max_nt, max_pts, dxy,
+                               reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), nT, S, max_nt, max_nv, max_pts, dxy,
                                dlen, dst, ctx->stream);
             CK(cudaGetLastError(), "batch trace launch");
             if (sx == 0) {

@@ -46,7 +46,8 @@ struct DevMesh {
     int4 *tri = nullptr;       // [n_t] (v0, v1, v2, 0)
     int4 *tnbr = nullptr;      // [n_t] (t0, t1, t2, 0)
     float4 *gphi = nullptr;    // [n_t][2]: (g0x, g0y, g1x, g1y), (g2x, g2y, 0, 0)
-    int4 *trec = nullptr;      // [n_t][4] tracer records: (v0,v1,v2,n0) (n1,n2,g0x,g0y) (g1x,g1y,p0x,p0y) (p1x,p1y,p2x,p2y)
+    int4 *trec = nullptr;      // [n_t][4] tracer records: (v0,v1,v2,n0) (n1,n2,q0,q1) (q2,0,p0x,p0y) (p1x,p1y,p2x,p2y),
+                               // q_i = |grad phi_i|^2
     int32_t *vt_off = nullptr, *vt = nullptr;
     int32_t *vn_off = nullptr, *vn = nullptr;
     int32_t *interior = nullptr;   // [m]
@@ -108,10 +109,12 @@ std::string tuning_table();
 // spread (max - min) of the hardware mantissa log's error over [1, 2), in base-2 units
 dd_status fast_log_spread(double *spread, std::string &err);
 
-// Tracer: per-field triangle gradients into grads [T][n_t], then T*S paths.
+// Tracer: per-field triangle rates and vertex decisions into `scratch`
+// (trace_scratch_bytes(m, T) bytes), then T*S paths.
+size_t trace_scratch_bytes(const DevMesh &m, int32_t T);
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,
                   const int32_t *sources, int32_t T, int32_t S, int32_t max_pts, float2 *out_xy,
-                  int32_t *out_len, int32_t *out_status, float2 *grads, cudaStream_t s);
+                  int32_t *out_len, int32_t *out_status, void *scratch, cudaStream_t s);
 
 // Split-BF16 tensor-core KL (tcgen05): BF16 split of P and e_x once per mesh,
 // then KL [T][n_v] for T staged targets (scratch: gemm_target_scratch_bytes).
@@ -121,12 +124,13 @@ size_t gemm_target_scratch_bytes(const DevMesh &m, int32_t T);
 dd_status launch_kl_gemm(const DevMesh &m, const int32_t *d_targets, int32_t T, void *scratch, float *out_kl,
                          int *err_flag, cudaStream_t s, std::string &err);
 
-// Tracer over several meshes in one launch (descriptors built on the host).
+// Tracer over several meshes in one launch (descriptors built on the host;
+// each item's scratch: trace_scratch_bytes(m, T_item) bytes).
 size_t batch_trace_dom_bytes();
-void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, float2 *grads);
+void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, int32_t T, void *scratch);
 void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t *d_tloc, const int32_t *d_targets,
-                        const int32_t *d_sources, int32_t n_targets, int32_t S, int64_t max_nt, int32_t max_pts,
-                        float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s,
+                        const int32_t *d_sources, int32_t n_targets, int32_t S, int64_t max_nt, int64_t max_nv,
+                        int32_t max_pts, float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s,
                         const int32_t *d_path_target = nullptr, int64_t n_paths = 0);
 
 // ---------------------------------------------------------------- context

@@ -90,7 +90,7 @@ namespace {
 
 // device bytes one query needs inside a batch
 size_t query_need(const DevMesh &m, int32_t S, int32_t max_pts) {
-    return al((size_t)m.n_v * 4) + al((size_t)3 * m.k_pad * 4) + al((size_t)m.n_t * 8) +
+    return al((size_t)m.n_v * 4) + al((size_t)3 * m.k_pad * 4) + al(trace_scratch_bytes(m, 1)) +
            al((size_t)S * ((size_t)max_pts * 8 + 8)) + al((size_t)S * 8) + 4096;
 }
 
@@ -114,10 +114,11 @@ bool launch_batch(dd_server *sv, Slot &sl) {
     }
     const int n_items = (int)ms.size();
     const int32_t nT = (int32_t)order.size();
-    int64_t n_paths = 0, max_nt = 0, max_k = 0;
+    int64_t n_paths = 0, max_nt = 0, max_nv = 0, max_k = 0;
     for (Query *q : order) n_paths += q->S;
     for (DevMesh *m : ms) {
         max_nt = std::max(max_nt, m->n_t);
+        max_nv = std::max(max_nv, m->n_v);
         max_k = std::max(max_k, m->k_pad);
     }
     // ---- device arena layout
@@ -142,13 +143,13 @@ bool launch_batch(dd_server *sv, Slot &sl) {
     }
     const size_t o_items = take(n_tiles * sizeof(BatchItem));
     const size_t meta_end = o;
-    size_t stage_f = 0, field_f = 0, grad_p = 0;
+    size_t stage_f = 0, field_f = 0, grad_b = 0;
     for (int i = 0; i < n_items; ++i) {
         stage_f += (size_t)3 * Ts[i] * ms[i]->k_pad;
         field_f += (size_t)Ts[i] * ms[i]->n_v;
-        grad_p += (size_t)Ts[i] * ms[i]->n_t;
+        grad_b += trace_scratch_bytes(*ms[i], Ts[i]);
     }
-    const size_t o_stage = take(stage_f * 4), o_fields = take(field_f * 4), o_grads = take(grad_p * 8);
+    const size_t o_stage = take(stage_f * 4), o_fields = take(field_f * 4), o_grads = take(grad_b);
     const size_t o_xy = take((size_t)n_paths * sv->max_pts * 8), o_len = take(n_paths * 4), o_st = take(n_paths * 4);
     if (o > sl.dev_cap || meta_end > sl.pin_in_cap) {
         for (Query *q : sl.qs) q->err = DD_EBUDGET;
@@ -194,9 +195,9 @@ bool launch_batch(dd_server *sv, Slot &sl) {
             q.variant = var[i];
             q.out_kl = reinterpret_cast<float *>(d + o_fields) + fo;
             q.out_tv = nullptr;
-            fill_batch_trace_dom(h + o_doms + i * dom_bytes, m, q.out_kl, reinterpret_cast<float2 *>(d + o_grads) + go);
+            fill_batch_trace_dom(h + o_doms + i * dom_bytes, m, q.out_kl, Ts[i], d + o_grads + go);
             fo += (size_t)Ts[i] * m.n_v;
-            go += (size_t)Ts[i] * m.n_t;
+            go += trace_scratch_bytes(m, Ts[i]);
         }
         std::memcpy(h + o_probs, probs.data(), n_items * sizeof(BatchProblem));
         size_t j = 0;
@@ -218,7 +219,7 @@ bool launch_batch(dd_server *sv, Slot &sl) {
                             reinterpret_cast<int32_t *>(d + o_counter), s);
         launch_batch_trace(d + o_doms, reinterpret_cast<const int32_t *>(d + o_tprob),
                            reinterpret_cast<const int32_t *>(d + o_tloc), reinterpret_cast<const int32_t *>(d + o_targets),
-                           reinterpret_cast<const int32_t *>(d + o_sources), nT, 0, max_nt, sv->max_pts,
+                           reinterpret_cast<const int32_t *>(d + o_sources), nT, 0, max_nt, max_nv, sv->max_pts,
                            reinterpret_cast<float2 *>(d + o_xy), reinterpret_cast<int32_t *>(d + o_len),
                            reinterpret_cast<int32_t *>(d + o_st), s, reinterpret_cast<const int32_t *>(d + o_ptarget),
                            n_paths);

@@ -2,7 +2,7 @@
 // path generation"), one thread per (target, source) pair.
 //
 // The field is piecewise linear, so triangle tau has the constant gradient
-// g = (f1 - f0) grad(phi_1) + (f2 - f0) grad(phi_2) and the path follows -g.
+// g = (f0 - f2) grad(phi_0) + (f1 - f2) grad(phi_1) and the path follows -g.
 // The walk, made precise from the paper's prose:
 //  * vertex v: stop at the target; if v neighbours the target, the path lies
 //    on an edge incident on it: append the target and stop.  Otherwise follow
@@ -19,12 +19,15 @@
 // Geometry and gradients are FP32; the hat-function gradients are computed in
 // FP64 on the host and rounded once.
 //
-// Layout for latency: every triangle is one 64-byte record (vertex ids,
-// neighbour ids, hat gradients of vertices 0 and 1 -- the third is minus their
-// sum -- and vertex positions), and the per-field triangle gradients are
-// computed once per field by tri_grad_kernel.  Crossing a triangle then needs
-// a single dependent load level: the record and gradient of the next triangle,
-// whose id sits in the current record.
+// Work split for latency.  What a vertex state decides depends only on the
+// field and the vertex (the best triangle is the steepest, ties by id, so the
+// order in which the incident triangles are examined does not matter), so it
+// is computed for every vertex of every field before the walk
+// (vertex_decision_kernel), after the barycentric rates of every triangle
+// (rates_kernel).  The walk then does one thing per iteration: cross one
+// triangle from an edge (one 64-byte record and one 16-byte rate load, both
+// addressed by the id the previous step found), apply one vertex decision
+// (one 48-byte load), or slide along a valley or boundary edge.
 #include <cfloat>
 #include <cstring>
 #include <algorithm>
@@ -37,23 +40,13 @@ namespace {
 constexpr float kEpsBary = 1e-6f;    // barycentric snap to a vertex
 constexpr float kEpsWedge = 1e-6f;   // relative tolerance of the wedge / entry tests
 
-struct TraceParams {
-    const int4 *rec;               // [n_t][4] triangle records
-    const float2 *grads;           // [T][n_t] per-field triangle gradients
-    const float2 *xy;
-    const int32_t *vt_off, *vt;
-    const float *fields;
-    int64_t field_stride, n_t;
-    const int32_t *targets, *sources;
-    int64_t total;
-    int32_t S, max_pts, max_steps;
-    float2 *out_xy;
-    int32_t *out_len, *out_status;
-};
-
+// Triangle record (64 bytes): vertex ids, the ids of the triangles across the
+// edges opposite each vertex (-1 on the boundary), the squared norms q_i of
+// the hat gradients, and the vertex positions.
 struct Tri {
     int v0, v1, v2, n0, n1, n2;
-    float2 g0, g1, p0, p1, p2;
+    float q0, q1, q2;
+    float2 p0, p1, p2;
 };
 
 __device__ __forceinline__ Tri load_tri(const int4 *__restrict__ rec, int t) {
@@ -67,8 +60,9 @@ __device__ __forceinline__ Tri load_tri(const int4 *__restrict__ rec, int t) {
     T.n0 = a.w;
     T.n1 = b.x;
     T.n2 = b.y;
-    T.g0 = make_float2(__int_as_float(b.z), __int_as_float(b.w));
-    T.g1 = make_float2(c.x, c.y);
+    T.q0 = __int_as_float(b.z);
+    T.q1 = __int_as_float(b.w);
+    T.q2 = c.x;
     T.p0 = make_float2(c.z, c.w);
     T.p1 = make_float2(d.x, d.y);
     T.p2 = make_float2(d.z, d.w);
@@ -78,69 +72,175 @@ __device__ __forceinline__ Tri load_tri(const int4 *__restrict__ rec, int t) {
 __device__ __forceinline__ int vid(const Tri &T, int i) { return i == 0 ? T.v0 : (i == 1 ? T.v1 : T.v2); }
 __device__ __forceinline__ float2 pos(const Tri &T, int i) { return i == 0 ? T.p0 : (i == 1 ? T.p1 : T.p2); }
 __device__ __forceinline__ int local_of(const Tri &T, int x) { return T.v0 == x ? 0 : (T.v1 == x ? 1 : 2); }
-__device__ __forceinline__ float dot2(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
-
-// g = f0 grad(phi_0) + f1 grad(phi_1) + f2 grad(phi_2) = (f0 - f2) g0 + (f1 - f2) g1
-__global__ void tri_grad_kernel(const int4 *__restrict__ rec, int64_t n_t, const float *__restrict__ fields,
-                                int64_t field_stride, float2 *__restrict__ grads) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_t) return;
-    const int a = blockIdx.y;
-    const Tri T = load_tri(rec, (int)t);
-    const float *f = fields + (int64_t)a * field_stride;
-    const float f2 = f[T.v2], d0 = f[T.v0] - f2, d1 = f[T.v1] - f2;
-    grads[(int64_t)a * n_t + t] = make_float2(d0 * T.g0.x + d1 * T.g1.x, d0 * T.g0.y + d1 * T.g1.y);
-}
-
-// Loop structure: every iteration loads one triangle record (and its field
-// gradient) and advances one thread's state by it, so the threads of a warp
-// issue their loads together.  A vertex state walks the fan of triangles
-// around the vertex through the neighbour links (counter-clockwise from a
-// known incident triangle, then clockwise from it if the fan is open),
-// evaluating one triangle per iteration.  Both states share one rotated view
-// of the loaded triangle: a reference vertex R (the fan vertex, or the
-// second endpoint b of the entry edge) and the two that follow it
-// counter-clockwise, X and Y.  For an entry edge (a, b) of the previous
-// triangle, consistent orientation puts a at X and the opposite vertex at Y.
-// Quantities on the critical path use squared norms and approximate
-// reciprocals; the decisions they feed carry relative tolerances.
 __device__ __forceinline__ float sel3f(int i, float a, float b, float c) { return i == 0 ? a : (i == 1 ? b : c); }
 __device__ __forceinline__ int sel3i(int i, int a, int b, int c) { return i == 0 ? a : (i == 1 ? b : c); }
 
-struct TraceDom {
-    const int4 *rec;
-    const float2 *xy;
-    const int32_t *vt_off, *vt;
-    int64_t n_t;
+// Per (field, triangle): (r0, r1, r2, |g|^2) with r_i = -grad(phi_i) . g the
+// rate of change of barycentric coordinate i along the descent direction -g.
+// g = f0 grad(phi_0) + f1 grad(phi_1) + f2 grad(phi_2) = (f0 - f2) g0 + (f1 - f2) g1.
+__device__ __forceinline__ float4 tri_rates(const float4 *__restrict__ gphi, const int4 *__restrict__ rec, int64_t t,
+                                            const float *__restrict__ f) {
+    const int4 a = __ldg(rec + 4 * t);
+    const float4 h = __ldg(gphi + 2 * t);                 // (g0x, g0y, g1x, g1y)
+    const float f2 = f[a.z], d0 = f[a.x] - f2, d1 = f[a.y] - f2;
+    const float gx = d0 * h.x + d1 * h.z, gy = d0 * h.y + d1 * h.w;
+    const float r0 = -(h.x * gx + h.y * gy), r1 = -(h.z * gx + h.w * gy);
+    return make_float4(r0, r1, -(r0 + r1), gx * gx + gy * gy);
+}
+
+__global__ void rates_kernel(const float4 *__restrict__ gphi, const int4 *__restrict__ rec, int64_t n_t,
+                             const float *__restrict__ fields, int64_t field_stride, float4 *__restrict__ rates) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_t) return;
+    const int a = blockIdx.y;
+    rates[(int64_t)a * n_t + t] = tri_rates(gphi, rec, t, fields + (int64_t)a * field_stride);
+}
+
+// What the walk does at a vertex (48 bytes)
+enum { kVCross = 0, kVVertex = 1, kVAdjacent = 2, kVStuck = 3 };
+struct VDec {
+    int4 h;      // kind, then: cross (ea, eb, t_next) | vertex (u, -, -) | adjacent (target, -, -)
+    float4 w;    // cross (la, lb, point) | vertex, adjacent (position, -, -)
+    float4 e;    // cross: positions of ea and eb
 };
 
-// one path: walk from `source` to `target` on field f (triangle gradients `grads`)
-__device__ __forceinline__ void trace_path(const TraceDom &p, const float *__restrict__ f,
-                                           const float2 *__restrict__ grads, int target, int source,
-                                           float2 *__restrict__ out, int32_t max_pts, int32_t max_steps,
-                                           int32_t *len_out, int32_t *status_out, bool active) {
-    const float eps2 = kEpsWedge * kEpsWedge;
-    int v = source;
-    int len = 0;
-    int status = DD_TRACE_STEP_LIMIT;
-    int states = 1;                // vertex and edge states entered (the step cap counts these)
-    bool fin = !active;            // finished (or a padding lane): idles until the warp is done
-    if (active) out[len++] = p.xy[v];
+struct TraceDom {
+    const int4 *rec;
+    const float4 *gphi;
+    const float2 *xy;
+    const int32_t *vt_off, *vt;
+    int64_t n_t, n_v;
+};
 
-    // vertex (fan-scan) state
-    bool scanning = true;
-    int t0 = active ? p.vt[p.vt_off[v]] : 0;
-    int scan_t = t0, t0_cw = -1;
-    bool ccw = true, adj = false;
+// the vertex state's decision at v for field f (with that field's rates)
+__device__ __forceinline__ VDec vertex_decision(const TraceDom &p, const float *__restrict__ f,
+                                                const float4 *__restrict__ rates, int target, int v) {
+    const float eps2 = kEpsWedge * kEpsWedge;
+    bool adj = false;
     int best = -1;
     float best_g2 = 0.f, baj = 0.f, bak = 0.f;
     int b_vj = 0, b_vk = 0, b_next = -1;
     float2 b_pj = make_float2(0.f, 0.f), b_pk = b_pj;
-    // edge state: the path sits on edge (ea, eb) of triangle cur_id, weights (la, lb),
-    // and enters t_next (the triangle across that edge, -1 on the boundary)
-    int cur_id = -1, t_next = -1, ea = 0, eb = 0;
+    const int q0 = p.vt_off[v], q1 = p.vt_off[v + 1];
+    for (int q = q0; q < q1; ++q) {
+        const int tl = p.vt[q];
+        const Tri T = load_tri(p.rec, tl);
+        const float4 R = __ldg(rates + tl);
+        // rotated view: v is local vertex L, then X and Y counter-clockwise; the exit edge is X-Y
+        const int L = local_of(T, v), X = L == 2 ? 0 : L + 1, Y = L == 0 ? 2 : L - 1;
+        const float rX = sel3f(X, R.x, R.y, R.z), rY = sel3f(Y, R.x, R.y, R.z);
+        const float qX = sel3f(X, T.q0, T.q1, T.q2), qY = sel3f(Y, T.q0, T.q1, T.q2);
+        const int vX = sel3i(X, T.v0, T.v1, T.v2), vY = sel3i(Y, T.v0, T.v1, T.v2);
+        const float gg = R.w;
+        adj |= (vX == target) | (vY == target);
+        const float tol2 = eps2 * gg * fmaxf(qX, qY);
+        const bool in_x = rX >= 0.f || rX * rX <= tol2;
+        const bool in_y = rY >= 0.f || rY * rY <= tol2;
+        if (gg > 0.f && in_x && in_y && rX + rY > 0.f && (gg > best_g2 || (gg == best_g2 && tl < best))) {
+            best = tl;
+            best_g2 = gg;
+            baj = fmaxf(rX, 0.f);
+            bak = fmaxf(rY, 0.f);
+            b_vj = vX;
+            b_vk = vY;
+            b_pj = pos(T, X);
+            b_pk = pos(T, Y);
+            b_next = sel3i(L, T.n0, T.n1, T.n2);
+        }
+    }
+    VDec d;
+    d.e = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (adj) {                                   // v lies on an edge incident on the target
+        const float2 pt = p.xy[target];
+        d.h = make_int4(kVAdjacent, target, 0, 0);
+        d.w = make_float4(pt.x, pt.y, 0.f, 0.f);
+        return d;
+    }
+    if (best >= 0) {
+        const float s = __fdividef(1.0f, baj + bak);
+        const float lj = s * baj, lk = s * bak;
+        if (lj <= kEpsBary) {
+            d.h = make_int4(kVVertex, b_vk, 0, 0);
+            d.w = make_float4(b_pk.x, b_pk.y, 0.f, 0.f);
+        } else if (lk <= kEpsBary) {
+            d.h = make_int4(kVVertex, b_vj, 0, 0);
+            d.w = make_float4(b_pj.x, b_pj.y, 0.f, 0.f);
+        } else {
+            d.h = make_int4(kVCross, b_vj, b_vk, b_next);
+            d.w = make_float4(lj, lk, lj * b_pj.x + lk * b_pk.x, lj * b_pj.y + lk * b_pk.y);
+            d.e = make_float4(b_pj.x, b_pj.y, b_pk.x, b_pk.y);
+        }
+        return d;
+    }
+    // no descending triangle: the incident edge of largest positive slope (ties to the lower id)
+    int best_u = -1;
+    float best_s = 0.f;
+    float2 best_p = make_float2(0.f, 0.f);
+    const float fv = f[v];
+    const float2 pv = p.xy[v];
+    for (int q = q0; q < q1; ++q) {
+        const Tri Q = load_tri(p.rec, p.vt[q]);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int u = vid(Q, e);
+            if (u == v) continue;
+            const float2 pu = pos(Q, e);
+            const float dx = pv.x - pu.x, dy = pv.y - pu.y;
+            const float slope = (fv - f[u]) / sqrtf(dx * dx + dy * dy);
+            if (slope > 0.f && (slope > best_s || (slope == best_s && u < best_u))) {
+                best_s = slope;
+                best_u = u;
+                best_p = pu;
+            }
+        }
+    }
+    if (best_u < 0) {
+        d.h = make_int4(kVStuck, 0, 0, 0);
+        d.w = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        d.h = make_int4(kVVertex, best_u, 0, 0);
+        d.w = make_float4(best_p.x, best_p.y, 0.f, 0.f);
+    }
+    return d;
+}
+
+__global__ void vertex_decision_kernel(const TraceDom p, const float *__restrict__ fields, int64_t field_stride,
+                                       const float4 *__restrict__ rates, const int32_t *__restrict__ targets,
+                                       VDec *__restrict__ dec) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= p.n_v) return;
+    const int a = blockIdx.y;
+    dec[(int64_t)a * p.n_v + v] = vertex_decision(p, fields + (int64_t)a * field_stride, rates + (int64_t)a * p.n_t,
+                                                  targets[a], (int)v);
+}
+
+// One path: walk from `source` to `target` on field f, with that field's
+// triangle rates and vertex decisions.  The warp votes at the top of every
+// iteration, so its threads reconverge once per step; finished threads (and
+// padding lanes) idle there until the last path of the warp ends.
+__device__ __forceinline__ void trace_path(const TraceDom &p, const float *__restrict__ f,
+                                           const float4 *__restrict__ rates, const VDec *__restrict__ dec, int target,
+                                           int source, float2 *__restrict__ out, int32_t max_pts, int32_t max_steps,
+                                           int32_t *len_out, int32_t *status_out, bool active) {
+    const float eps2 = kEpsWedge * kEpsWedge;
+    int len = 0;
+    int status = DD_TRACE_STEP_LIMIT;
+    int states = 1;                // vertex and edge states entered (the step cap counts these)
+    bool fin = !active;
+    bool at_vertex = true;
+    int v = source;
+    // edge state: the path sits on edge (ea, eb) at weights (la, lb) and enters
+    // t_next (the triangle across that edge, -1 on the boundary)
+    int t_next = -1, ea = 0, eb = 0;
     float la = 0.f, lb = 0.f;
     float2 pa = make_float2(0.f, 0.f), pb = pa;
+    if (active) {
+        out[len++] = p.xy[v];
+        if (v == target) {
+            status = DD_TRACE_OK;
+            fin = true;
+        }
+    }
 
 // The macros end the current iteration with `continue` when the path ends;
 // they are used as statements inside braces (no do-while wrapper, so that
@@ -152,16 +252,9 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
         continue;                                \
     }                                            \
     out[len++] = (pt);
-#define DD_ENTER_VERTEX(vert, tri_id)            \
+#define DD_ENTER_VERTEX(vert)                    \
     v = (vert);                                  \
-    scanning = true;                             \
-    t0 = (tri_id);                               \
-    scan_t = t0;                                 \
-    t0_cw = -1;                                  \
-    ccw = true;                                  \
-    adj = false;                                 \
-    best = -1;                                   \
-    best_g2 = 0.f;                               \
+    at_vertex = true;                            \
     if (++states > max_steps) {                  \
         fin = true;                              \
         continue;                                \
@@ -176,198 +269,115 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
         const float fa = f[ea], fb = f[eb];                            \
         const bool a_low = fa < fb || (fa == fb && ea < eb);           \
         DD_PUSH(a_low ? pa : pb);                                      \
-        DD_ENTER_VERTEX(a_low ? ea : eb, cur_id);                      \
+        DD_ENTER_VERTEX(a_low ? ea : eb);                              \
     }
 
-    if (active && v == target) {
-        status = DD_TRACE_OK;
-        fin = true;
-    }
-    // The warp votes at the top of every iteration, so its threads reconverge
-    // once per step instead of drifting into different iterations; finished
-    // threads idle here until the last path of the warp ends.
-    const int64_t iter_cap = 16LL * max_steps;
+    const int64_t iter_cap = 4LL * max_steps + 16;
     for (int64_t iter = 0;; ++iter) {
         if (!fin && iter >= iter_cap) fin = true;
         if (!__any_sync(0xffffffffu, !fin)) break;
         if (fin) continue;
-        if (!scanning && t_next < 0) {     // boundary edge: slide to the lower endpoint
+        if (at_vertex) {
+            // ---- vertex state: apply the precomputed decision
+            const VDec *dv = dec + v;
+            const int4 h = __ldg(&dv->h);
+            const float4 w = __ldg(&dv->w);
+            if (h.x == kVStuck) {
+                status = DD_TRACE_STUCK;
+                fin = true;
+                continue;
+            }
+            const bool cross = h.x == kVCross;
+            DD_PUSH(make_float2(cross ? w.z : w.x, cross ? w.w : w.y));
+            if (h.x == kVAdjacent) {
+                status = DD_TRACE_OK;
+                fin = true;
+                continue;
+            }
+            if (!cross) {
+                DD_ENTER_VERTEX(h.y);
+                continue;
+            }
+            const float4 e = __ldg(&dv->e);
+            at_vertex = false;
+            ea = h.y;
+            eb = h.z;
+            t_next = h.w;
+            la = w.x;
+            lb = w.y;
+            pa = make_float2(e.x, e.y);
+            pb = make_float2(e.z, e.w);
+            if (++states > max_steps) fin = true;
+            continue;
+        }
+        if (t_next < 0) {                // boundary edge: slide to the lower endpoint
             DD_SLIDE();
             continue;
         }
-        const int tl = scanning ? scan_t : t_next;
+        // ---- edge state: entering T across (ea, eb); in T's counter-clockwise order
+        // eb is local vertex L, ea is X, and the opposite vertex is Y
+        const int tl = t_next;
         const Tri T = load_tri(p.rec, tl);
-        const float2 g = grads[tl];
-        // ---- shared rotated view: R = reference vertex, X = R+1, Y = R+2 (counter-clockwise)
-        const int refv = scanning ? v : eb;
-        const int L = local_of(T, refv), X = L == 2 ? 0 : L + 1, Y = L == 0 ? 2 : L - 1;
-        const float r0 = -dot2(T.g0, g), r1 = -dot2(T.g1, g), r2 = -(r0 + r1);   // d(lambda_i)/ds along -g
-        const float2 g2v = make_float2(-(T.g0.x + T.g1.x), -(T.g0.y + T.g1.y));
-        const float q0 = dot2(T.g0, T.g0), q1 = dot2(T.g1, T.g1), q2 = dot2(g2v, g2v);
-        const float gg = dot2(g, g);
-        const float rX = sel3f(X, r0, r1, r2), rY = sel3f(Y, r0, r1, r2);
-        const float qX = sel3f(X, q0, q1, q2), qY = sel3f(Y, q0, q1, q2);
-        const int vX = sel3i(X, T.v0, T.v1, T.v2), vY = sel3i(Y, T.v0, T.v1, T.v2);
-        const float2 pY = make_float2(sel3f(Y, T.p0.x, T.p1.x, T.p2.x), sel3f(Y, T.p0.y, T.p1.y, T.p2.y));
-        const int nL = sel3i(L, T.n0, T.n1, T.n2), nX = sel3i(X, T.n0, T.n1, T.n2), nY = sel3i(Y, T.n0, T.n1, T.n2);
-        if (scanning) {
-            // ---- one triangle of the fan around v (v = R, the candidate exit edge is X-Y)
-            adj |= (vX == target) | (vY == target);
-            const float tol2 = eps2 * gg * fmaxf(qX, qY);
-            const bool in_x = rX >= 0.f || rX * rX <= tol2;
-            const bool in_y = rY >= 0.f || rY * rY <= tol2;
-            if (gg > 0.f && in_x && in_y && rX + rY > 0.f && (gg > best_g2 || (gg == best_g2 && tl < best))) {
-                best = tl;
-                best_g2 = gg;
-                baj = fmaxf(rX, 0.f);
-                bak = fmaxf(rY, 0.f);
-                b_vj = vX;
-                b_vk = vY;
-                b_pj = make_float2(sel3f(X, T.p0.x, T.p1.x, T.p2.x), sel3f(X, T.p0.y, T.p1.y, T.p2.y));
-                b_pk = pY;
-                b_next = nL;
-            }
-            if (tl == t0) t0_cw = nY;
-            int next = ccw ? nX : nY;
-            if (ccw && next == t0) {
-                next = -1;                       // closed fan: done
-            } else if (ccw && next < 0) {
-                ccw = false;                     // open fan: continue clockwise from t0
-                next = t0_cw;
-            }
-            if (next >= 0) {
-                scan_t = next;
-                continue;
-            }
-            // ---- fan complete
-            if (adj) {                           // v lies on an edge incident on the target
-                DD_PUSH(p.xy[target]);
-                status = DD_TRACE_OK;
-                fin = true;
-                continue;
-            }
-            if (best >= 0) {
-                const float s = __fdividef(1.0f, baj + bak);
-                const float lj = s * baj, lk = s * bak;
-                if (lj <= kEpsBary) {
-                    DD_PUSH(b_pk);
-                    DD_ENTER_VERTEX(b_vk, best);
-                } else if (lk <= kEpsBary) {
-                    DD_PUSH(b_pj);
-                    DD_ENTER_VERTEX(b_vj, best);
-                } else {
-                    DD_PUSH(make_float2(lj * b_pj.x + lk * b_pk.x, lj * b_pj.y + lk * b_pk.y));
-                    scanning = false;
-                    cur_id = best;
-                    t_next = b_next;
-                    ea = b_vj;
-                    eb = b_vk;
-                    pa = b_pj;
-                    pb = b_pk;
-                    la = lj;
-                    lb = lk;
-                    if (++states > max_steps) {
-                        fin = true;
-                        continue;
-                    }
-                }
-                continue;
-            }
-            // no descending triangle: the incident edge of largest positive slope
-            // (ties to the lower id); rare, so it walks the vertex's triangle list
-            {
-                int best_u = -1, best_ut = -1;
-                float best_s = 0.f;
-                float2 best_p = make_float2(0.f, 0.f);
-                const float fv = f[v];
-                const float2 pv = p.xy[v];
-                for (int q = p.vt_off[v]; q < p.vt_off[v + 1]; ++q) {
-                    const int tq = p.vt[q];
-                    const Tri Q = load_tri(p.rec, tq);
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const int u = vid(Q, e);
-                        if (u == v) continue;
-                        const float2 pu = pos(Q, e);
-                        const float dx = pv.x - pu.x, dy = pv.y - pu.y;
-                        const float slope = (fv - f[u]) / sqrtf(dx * dx + dy * dy);
-                        if (slope > 0.f && (slope > best_s || (slope == best_s && u < best_u))) {
-                            best_s = slope;
-                            best_u = u;
-                            best_p = pu;
-                            best_ut = tq;
-                        }
-                    }
-                }
-                if (best_u < 0) {
-                    status = DD_TRACE_STUCK;
-                    fin = true;
-                    continue;
-                }
-                DD_PUSH(best_p);
-                DD_ENTER_VERTEX(best_u, best_ut);
-                continue;
-            }
+        const float4 Rt = __ldg(rates + tl);
+        const int L = local_of(T, eb), X = L == 2 ? 0 : L + 1, Y = L == 0 ? 2 : L - 1;
+        const float ra = sel3f(X, Rt.x, Rt.y, Rt.z), rb = sel3f(L, Rt.x, Rt.y, Rt.z), rc = sel3f(Y, Rt.x, Rt.y, Rt.z);
+        const float qY = sel3f(Y, T.q0, T.q1, T.q2);
+        const bool enters = rc > 0.f && rc * rc > eps2 * Rt.w * qY;
+        const float sa = ra < 0.f ? __fdividef(la, -ra) : INFINITY;
+        const float sb = rb < 0.f ? __fdividef(lb, -rb) : INFINITY;
+        if (!enters || !(fminf(sa, sb) < INFINITY)) {   // valley edge (or no exit): lower endpoint
+            DD_SLIDE();
+            continue;
         }
-        // ---- edge state: entering T across (ea, eb); ea = X, eb = R, the opposite vertex is Y
-        {
-            const float ra = rX, rb = sel3f(L, r0, r1, r2), rc = rY;
-            const bool enters = rc > 0.f && rc * rc > eps2 * gg * qY;
-            const float sa = ra < 0.f ? __fdividef(la, -ra) : INFINITY;
-            const float sb = rb < 0.f ? __fdividef(lb, -rb) : INFINITY;
-            if (!enters || !(fminf(sa, sb) < INFINITY)) {   // valley edge (or no exit): lower endpoint
-                DD_SLIDE();
-                continue;
-            }
-            const bool via_a = sa <= sb;                      // exit through the edge opposite a (= Y-R edge)
-            const float s = via_a ? sa : sb;
-            float lkeep = fmaxf(via_a ? lb + s * rb : la + s * ra, 0.f);
-            float lc2 = fmaxf(s * rc, 0.f);
-            const float inv = __fdividef(1.0f, lkeep + lc2);
-            lkeep *= inv;
-            lc2 *= inv;
-            const int keep_v = via_a ? eb : ea;
-            const float2 keep_p = via_a ? pb : pa;
-            if (lkeep <= kEpsBary) {
-                DD_PUSH(pY);
-                DD_ENTER_VERTEX(vY, tl);
-                continue;
-            }
-            if (lc2 <= kEpsBary) {
-                DD_PUSH(keep_p);
-                DD_ENTER_VERTEX(keep_v, tl);
-                continue;
-            }
-            DD_PUSH(make_float2(lkeep * keep_p.x + lc2 * pY.x, lkeep * keep_p.y + lc2 * pY.y));
-            // new edge in T's counter-clockwise order: via a -> (Y, R) = (c, b); via b -> (X, Y) = (a, c)
-            cur_id = tl;
-            if (via_a) {
-                t_next = nX;
-                ea = vY;
-                eb = keep_v;
-                pa = pY;
-                pb = keep_p;
-                la = lc2;
-                lb = lkeep;
-            } else {
-                t_next = nL;
-                ea = keep_v;
-                eb = vY;
-                pa = keep_p;
-                pb = pY;
-                la = lkeep;
-                lb = lc2;
-            }
-            if (++states > max_steps) {
-                fin = true;
-                continue;
-            }
-            if (ea == target || eb == target) {   // an edge incident on the target
-                DD_PUSH(p.xy[target]);
-                status = DD_TRACE_OK;
-                fin = true;
-                continue;
-            }
+        const int vY = sel3i(Y, T.v0, T.v1, T.v2);
+        const float2 pY = pos(T, Y);
+        const bool via_a = sa <= sb;                      // exit through the edge opposite a (the Y-R edge)
+        const float s = via_a ? sa : sb;
+        float lkeep = fmaxf(via_a ? lb + s * rb : la + s * ra, 0.f);
+        float lc2 = fmaxf(s * rc, 0.f);
+        const float inv = __fdividef(1.0f, lkeep + lc2);
+        lkeep *= inv;
+        lc2 *= inv;
+        const int keep_v = via_a ? eb : ea;
+        const float2 keep_p = via_a ? pb : pa;
+        if (lkeep <= kEpsBary) {
+            DD_PUSH(pY);
+            DD_ENTER_VERTEX(vY);
+            continue;
+        }
+        if (lc2 <= kEpsBary) {
+            DD_PUSH(keep_p);
+            DD_ENTER_VERTEX(keep_v);
+            continue;
+        }
+        DD_PUSH(make_float2(lkeep * keep_p.x + lc2 * pY.x, lkeep * keep_p.y + lc2 * pY.y));
+        // new edge in T's counter-clockwise order: via a -> (Y, R) = (c, b); via b -> (X, Y) = (a, c)
+        if (via_a) {
+            t_next = sel3i(X, T.n0, T.n1, T.n2);
+            ea = vY;
+            eb = keep_v;
+            pa = pY;
+            pb = keep_p;
+            la = lc2;
+            lb = lkeep;
+        } else {
+            t_next = sel3i(L, T.n0, T.n1, T.n2);
+            ea = keep_v;
+            eb = vY;
+            pa = keep_p;
+            pb = pY;
+            la = lkeep;
+            lb = lc2;
+        }
+        if (++states > max_steps) {
+            fin = true;
+            continue;
+        }
+        if (ea == target || eb == target) {   // an edge incident on the target
+            DD_PUSH(p.xy[target]);
+            status = DD_TRACE_OK;
+            fin = true;
+            continue;
         }
     }
 #undef DD_PUSH
@@ -379,41 +389,57 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
     }
 }
 
+struct TraceParams {
+    TraceDom d;
+    const float4 *rates;           // [T][n_t]
+    const VDec *dec;               // [T][n_v]
+    const float *fields;
+    int64_t field_stride;
+    const int32_t *targets, *sources;
+    int64_t total;
+    int32_t S, max_pts, max_steps;
+    float2 *out_xy;
+    int32_t *out_len, *out_status;
+};
+
 __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = gid < p.total;       // padding lanes stay in the warp's walk loop, idle
     const int64_t id = active ? gid : 0;
     const int a = (int)(id / p.S);
-    TraceDom d;
-    d.rec = p.rec;
-    d.xy = p.xy;
-    d.vt_off = p.vt_off;
-    d.vt = p.vt;
-    d.n_t = p.n_t;
-    trace_path(d, p.fields + (int64_t)a * p.field_stride, p.grads + (int64_t)a * p.n_t, p.targets[a], p.sources[id],
-               p.out_xy + id * p.max_pts, p.max_pts, p.max_steps, p.out_len + id, p.out_status + id, active);
+    trace_path(p.d, p.fields + (int64_t)a * p.field_stride, p.rates + (int64_t)a * p.d.n_t,
+               p.dec + (int64_t)a * p.d.n_v, p.targets[a], p.sources[id], p.out_xy + id * p.max_pts, p.max_pts,
+               p.max_steps, p.out_len + id, p.out_status + id, active);
 }
 
 // ---- several meshes in one launch: global target g belongs to domain tdom[g] (local index tloc[g])
 struct BatchTraceDom {
     TraceDom d;
     const float *fields;      // [T_d][n_v]
-    float2 *grads;            // [T_d][n_t]
-    int64_t n_v;
+    float4 *rates;            // [T_d][n_t]
+    VDec *dec;                // [T_d][n_v]
     int32_t max_steps, pad;
 };
 
-__global__ void batch_grad_kernel(const BatchTraceDom *__restrict__ doms, const int32_t *__restrict__ tdom,
-                                  const int32_t *__restrict__ tloc) {
+__global__ void batch_rates_kernel(const BatchTraceDom *__restrict__ doms, const int32_t *__restrict__ tdom,
+                                   const int32_t *__restrict__ tloc) {
     const int g = blockIdx.y;
     const BatchTraceDom q = doms[tdom[g]];
     const int a = tloc[g];
-    const float *f = q.fields + (int64_t)a * q.n_v;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < q.d.n_t; t += (int64_t)gridDim.x * blockDim.x) {
-        const Tri T = load_tri(q.d.rec, (int)t);
-        const float f2 = f[T.v2], d0 = f[T.v0] - f2, d1 = f[T.v1] - f2;
-        q.grads[(int64_t)a * q.d.n_t + t] = make_float2(d0 * T.g0.x + d1 * T.g1.x, d0 * T.g0.y + d1 * T.g1.y);
-    }
+    const float *f = q.fields + (int64_t)a * q.d.n_v;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < q.d.n_t; t += (int64_t)gridDim.x * blockDim.x)
+        q.rates[(int64_t)a * q.d.n_t + t] = tri_rates(q.d.gphi, q.d.rec, t, f);
+}
+
+__global__ void batch_decision_kernel(const BatchTraceDom *__restrict__ doms, const int32_t *__restrict__ tdom,
+                                      const int32_t *__restrict__ tloc, const int32_t *__restrict__ targets) {
+    const int g = blockIdx.y;
+    const BatchTraceDom q = doms[tdom[g]];
+    const int a = tloc[g];
+    const float *f = q.fields + (int64_t)a * q.d.n_v;
+    const float4 *r = q.rates + (int64_t)a * q.d.n_t;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < q.d.n_v; v += (int64_t)gridDim.x * blockDim.x)
+        q.dec[(int64_t)a * q.d.n_v + v] = vertex_decision(q.d, f, r, targets[g], (int)v);
 }
 
 // path id -> global target: id / S, or path_target[id] when sources per target vary
@@ -431,69 +457,93 @@ __global__ void __launch_bounds__(64) batch_trace_kernel(const BatchTraceDom *__
     const int g = path_target ? path_target[id] : (int)(id / S);
     const BatchTraceDom q = doms[tdom[g]];
     const int a = tloc[g];
-    trace_path(q.d, q.fields + (int64_t)a * q.n_v, q.grads + (int64_t)a * q.d.n_t, targets[g], sources[id],
-               out_xy + id * max_pts, max_pts, q.max_steps, out_len + id, out_status + id, active);
+    trace_path(q.d, q.fields + (int64_t)a * q.d.n_v, q.rates + (int64_t)a * q.d.n_t, q.dec + (int64_t)a * q.d.n_v,
+               targets[g], sources[id], out_xy + id * max_pts, max_pts, q.max_steps, out_len + id, out_status + id,
+               active);
+}
+
+TraceDom make_dom(const DevMesh &m) {
+    TraceDom d;
+    d.rec = m.trec;
+    d.gphi = m.gphi;
+    d.xy = m.xy;
+    d.vt_off = m.vt_off;
+    d.vt = m.vt;
+    d.n_t = m.n_t;
+    d.n_v = m.n_v;
+    return d;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int32_t step_cap(const DevMesh &m) {
+    const int64_t cap = 4 * m.n_t;
+    return cap > (int64_t)INT32_MAX ? INT32_MAX : (int32_t)cap;
 }
 
 }  // namespace
 
+size_t trace_scratch_bytes(const DevMesh &m, int32_t T) {
+    return align256((size_t)T * m.n_t * sizeof(float4)) + align256((size_t)T * m.n_v * sizeof(VDec));
+}
+
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,
                   const int32_t *sources, int32_t T, int32_t S, int32_t max_pts, float2 *out_xy, int32_t *out_len,
-                  int32_t *out_status, float2 *grads, cudaStream_t s) {
+                  int32_t *out_status, void *scratch, cudaStream_t s) {
     TraceParams p;
-    p.rec = m.trec;
-    p.grads = grads;
-    p.xy = m.xy;
-    p.vt_off = m.vt_off;
-    p.vt = m.vt;
+    float4 *rates = reinterpret_cast<float4 *>(scratch);
+    VDec *dec = reinterpret_cast<VDec *>(reinterpret_cast<char *>(scratch) +
+                                         align256((size_t)T * m.n_t * sizeof(float4)));
+    p.d = make_dom(m);
+    p.rates = rates;
+    p.dec = dec;
     p.fields = fields;
     p.field_stride = field_stride;
-    p.n_t = m.n_t;
     p.targets = targets;
     p.sources = sources;
     p.total = (int64_t)T * S;
     p.S = S;
     p.max_pts = max_pts;
-    const int64_t cap = 4 * m.n_t;
-    p.max_steps = cap > (int64_t)INT32_MAX ? INT32_MAX : (int32_t)cap;
+    p.max_steps = step_cap(m);
     p.out_xy = out_xy;
     p.out_len = out_len;
     p.out_status = out_status;
     if (p.total == 0) return;
-    dim3 gg((unsigned)((m.n_t + 255) / 256), (unsigned)T);
-    tri_grad_kernel<<<gg, 256, 0, s>>>(m.trec, m.n_t, fields, field_stride, grads);
+    rates_kernel<<<dim3((unsigned)((m.n_t + 255) / 256), (unsigned)T), 256, 0, s>>>(m.gphi, m.trec, m.n_t, fields,
+                                                                                      field_stride, rates);
+    vertex_decision_kernel<<<dim3((unsigned)((m.n_v + 127) / 128), (unsigned)T), 128, 0, s>>>(
+        p.d, fields, field_stride, rates, targets, dec);
     trace_kernel<<<(unsigned)((p.total + 63) / 64), 64, 0, s>>>(p);
 }
 
 size_t batch_trace_dom_bytes() { return sizeof(BatchTraceDom); }
 
-// host-side builder of one domain descriptor (into a byte buffer uploaded by the caller)
-void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, float2 *grads) {
+// host-side builder of one domain descriptor (into a byte buffer uploaded by the
+// caller); scratch: trace_scratch_bytes(m, T) bytes of device memory
+void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, int32_t T, void *scratch) {
     BatchTraceDom q;
-    q.d.rec = m.trec;
-    q.d.xy = m.xy;
-    q.d.vt_off = m.vt_off;
-    q.d.vt = m.vt;
-    q.d.n_t = m.n_t;
+    q.d = make_dom(m);
     q.fields = fields;
-    q.grads = grads;
-    q.n_v = m.n_v;
-    const int64_t cap = 4 * m.n_t;
-    q.max_steps = cap > (int64_t)INT32_MAX ? INT32_MAX : (int32_t)cap;
+    q.rates = reinterpret_cast<float4 *>(scratch);
+    q.dec = reinterpret_cast<VDec *>(reinterpret_cast<char *>(scratch) +
+                                     align256((size_t)T * m.n_t * sizeof(float4)));
+    q.max_steps = step_cap(m);
     q.pad = 0;
     std::memcpy(dst, &q, sizeof q);
 }
 
 void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t *d_tloc, const int32_t *d_targets,
-                        const int32_t *d_sources, int32_t n_targets, int32_t S, int64_t max_nt, int32_t max_pts,
-                        float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s,
+                        const int32_t *d_sources, int32_t n_targets, int32_t S, int64_t max_nt, int64_t max_nv,
+                        int32_t max_pts, float2 *out_xy, int32_t *out_len, int32_t *out_status, cudaStream_t s,
                         const int32_t *d_path_target, int64_t n_paths) {
     if (n_targets <= 0) return;
     const BatchTraceDom *doms = reinterpret_cast<const BatchTraceDom *>(d_doms);
-    dim3 gg((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_nt + 255) / 256)), (unsigned)n_targets);
-    batch_grad_kernel<<<gg, 256, 0, s>>>(doms, d_tdom, d_tloc);
     const int64_t total = d_path_target ? n_paths : (int64_t)n_targets * S;
     if (total == 0) return;
+    dim3 gr((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_nt + 255) / 256)), (unsigned)n_targets);
+    batch_rates_kernel<<<gr, 256, 0, s>>>(doms, d_tdom, d_tloc);
+    dim3 gd((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_nv + 127) / 128)), (unsigned)n_targets);
+    batch_decision_kernel<<<gd, 128, 0, s>>>(doms, d_tdom, d_tloc, d_targets);
     batch_trace_kernel<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(doms, d_tdom, d_tloc, d_targets, d_sources,
                                                                     d_path_target, total, S, max_pts, out_xy, out_len,
                                                                     out_status);
