@@ -32,6 +32,9 @@ if ROOT not in sys.path:
 METRIC = "distance fields/s (KL+TV, one target over all vertices) with traced paths"
 UNIT = "fields/s"
 T_BATCH, S_PER_TARGET, MAX_PTS = 64, 256, 1024
+# kernels one dd_query step launches: target staging, field tile, triangle rates,
+# vertex decisions, path walk
+STEP_LAUNCHES = 5
 N_BATCHES = 8
 
 
@@ -261,7 +264,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "peaks": pk_kind,
         "e2e": {"value": round(world * fields_per_step * e2e_steps / e2e_s, 1), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": STEP_LAUNCHES * args.steps,
         "clocks": clocks,
     }
     if args.stream and args.section == "all":
