@@ -305,14 +305,15 @@ void worker_loop(dd_server *sv) {
                     batch.push_back(q);
                     sv->pending.pop_front();
                 }
+                // counted in flight from the moment they leave the queue, so that
+                // wait_idle never sees an empty queue with a batch not yet launched
+                if (!batch.empty()) ++sv->in_flight;
             }
             if (batch.empty()) break;
             sl.qs = batch;
             if (launch_batch(sv, sl)) {
                 sl.busy = true;
                 any_busy = true;
-                std::lock_guard<std::mutex> lock(sv->mu);
-                ++sv->in_flight;
             } else {
                 std::lock_guard<std::mutex> lock(sv->mu);
                 for (Query *x : sl.qs) {
@@ -321,6 +322,7 @@ void worker_loop(dd_server *sv) {
                     sv->finished[x->id] = x;
                 }
                 sl.qs.clear();
+                --sv->in_flight;
                 sv->cv.notify_all();
             }
         }

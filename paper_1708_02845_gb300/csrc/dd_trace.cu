@@ -24,7 +24,10 @@
 // order in which the incident triangles are examined does not matter), so it
 // is computed for every vertex of every field before the walk
 // (vertex_decision_kernel), after the barycentric rates of every triangle
-// (rates_kernel).  The walk then does one thing per iteration: cross one
+// (rates_kernel).  Both are stored field-minor ([triangle][field],
+// [vertex][field]): a warp of the decision kernel handles one vertex for 32
+// fields, so the triangle records it reads are shared by all its lanes and
+// the rates it reads are contiguous.  The walk then does one thing per iteration: cross one
 // triangle from an edge (one 64-byte record and one 16-byte rate load, both
 // addressed by the id the previous step found), apply one vertex decision
 // (one 48-byte load), or slide along a valley or boundary edge.
@@ -88,12 +91,14 @@ __device__ __forceinline__ float4 tri_rates(const float4 *__restrict__ gphi, con
     return make_float4(r0, r1, -(r0 + r1), gx * gx + gy * gy);
 }
 
-__global__ void rates_kernel(const float4 *__restrict__ gphi, const int4 *__restrict__ rec, int64_t n_t,
+// rates[t * T + a] for every triangle t and field a (field-minor)
+__global__ void rates_kernel(const float4 *__restrict__ gphi, const int4 *__restrict__ rec, int64_t n_t, int32_t T,
                              const float *__restrict__ fields, int64_t field_stride, float4 *__restrict__ rates) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_t) return;
-    const int a = blockIdx.y;
-    rates[(int64_t)a * n_t + t] = tri_rates(gphi, rec, t, fields + (int64_t)a * field_stride);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_t * T) return;
+    const int64_t t = i / T;
+    const int a = (int)(i - t * T);
+    rates[i] = tri_rates(gphi, rec, t, fields + (int64_t)a * field_stride);
 }
 
 // What the walk does at a vertex (48 bytes)
@@ -113,8 +118,9 @@ struct TraceDom {
 };
 
 // the vertex state's decision at v for field f (with that field's rates)
+// (rates of field a start at `rates`, one entry per triangle every `rstride`)
 __device__ __forceinline__ VDec vertex_decision(const TraceDom &p, const float *__restrict__ f,
-                                                const float4 *__restrict__ rates, int target, int v) {
+                                                const float4 *__restrict__ rates, int64_t rstride, int target, int v) {
     const float eps2 = kEpsWedge * kEpsWedge;
     bool adj = false;
     int best = -1;
@@ -125,7 +131,7 @@ __device__ __forceinline__ VDec vertex_decision(const TraceDom &p, const float *
     for (int q = q0; q < q1; ++q) {
         const int tl = p.vt[q];
         const Tri T = load_tri(p.rec, tl);
-        const float4 R = __ldg(rates + tl);
+        const float4 R = __ldg(rates + (int64_t)tl * rstride);
         // rotated view: v is local vertex L, then X and Y counter-clockwise; the exit edge is X-Y
         const int L = local_of(T, v), X = L == 2 ? 0 : L + 1, Y = L == 0 ? 2 : L - 1;
         const float rX = sel3f(X, R.x, R.y, R.z), rY = sel3f(Y, R.x, R.y, R.z);
@@ -204,24 +210,29 @@ __device__ __forceinline__ VDec vertex_decision(const TraceDom &p, const float *
     return d;
 }
 
-__global__ void vertex_decision_kernel(const TraceDom p, const float *__restrict__ fields, int64_t field_stride,
-                                       const float4 *__restrict__ rates, const int32_t *__restrict__ targets,
-                                       VDec *__restrict__ dec) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= p.n_v) return;
-    const int a = blockIdx.y;
-    dec[(int64_t)a * p.n_v + v] = vertex_decision(p, fields + (int64_t)a * field_stride, rates + (int64_t)a * p.n_t,
-                                                  targets[a], (int)v);
+// one warp per (vertex, group of 32 fields), lane = field: dec[v * T + a]
+__global__ void vertex_decision_kernel(const TraceDom p, int32_t T, const float *__restrict__ fields,
+                                       int64_t field_stride, const float4 *__restrict__ rates,
+                                       const int32_t *__restrict__ targets, VDec *__restrict__ dec) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int groups = (T + 31) >> 5;
+    const int64_t v = w / groups;
+    const int a = (int)(w - v * groups) * 32 + (threadIdx.x & 31);
+    if (v >= p.n_v || a >= T) return;
+    dec[v * T + a] = vertex_decision(p, fields + (int64_t)a * field_stride, rates + a, T, targets[a], (int)v);
 }
 
 // One path: walk from `source` to `target` on field f, with that field's
 // triangle rates and vertex decisions.  The warp votes at the top of every
 // iteration, so its threads reconverge once per step; finished threads (and
 // padding lanes) idle there until the last path of the warp ends.
+// (rates and decisions of this field start at `rates` and `dec`, one entry
+// per triangle or vertex every `stride` -- the number of fields)
 __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__restrict__ f,
-                                           const float4 *__restrict__ rates, const VDec *__restrict__ dec, int target,
-                                           int source, float2 *__restrict__ out, int32_t max_pts, int32_t max_steps,
-                                           int32_t *len_out, int32_t *status_out, bool active) {
+                                           const float4 *__restrict__ rates, const VDec *__restrict__ dec,
+                                           int64_t stride, int target, int source, float2 *__restrict__ out,
+                                           int32_t max_pts, int32_t max_steps, int32_t *len_out,
+                                           int32_t *status_out, bool active) {
     const float eps2 = kEpsWedge * kEpsWedge;
     int len = 0;
     int status = DD_TRACE_STEP_LIMIT;
@@ -279,7 +290,7 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
         if (fin) continue;
         if (at_vertex) {
             // ---- vertex state: apply the precomputed decision
-            const VDec *dv = dec + v;
+            const VDec *dv = dec + (int64_t)v * stride;
             const int4 h = __ldg(&dv->h);
             const float4 w = __ldg(&dv->w);
             if (h.x == kVStuck) {
@@ -318,7 +329,7 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
         // eb is local vertex L, ea is X, and the opposite vertex is Y
         const int tl = t_next;
         const Tri T = load_tri(p.rec, tl);
-        const float4 Rt = __ldg(rates + tl);
+        const float4 Rt = __ldg(rates + (int64_t)tl * stride);
         const int L = local_of(T, eb), X = L == 2 ? 0 : L + 1, Y = L == 0 ? 2 : L - 1;
         const float ra = sel3f(X, Rt.x, Rt.y, Rt.z), rb = sel3f(L, Rt.x, Rt.y, Rt.z), rc = sel3f(Y, Rt.x, Rt.y, Rt.z);
         const float qY = sel3f(Y, T.q0, T.q1, T.q2);
@@ -391,13 +402,13 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
 
 struct TraceParams {
     TraceDom d;
-    const float4 *rates;           // [T][n_t]
-    const VDec *dec;               // [T][n_v]
+    const float4 *rates;           // [n_t][T]
+    const VDec *dec;               // [n_v][T]
     const float *fields;
     int64_t field_stride;
     const int32_t *targets, *sources;
     int64_t total;
-    int32_t S, max_pts, max_steps;
+    int32_t S, max_pts, max_steps, T;
     float2 *out_xy;
     int32_t *out_len, *out_status;
 };
@@ -407,18 +418,17 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
     const bool active = gid < p.total;       // padding lanes stay in the warp's walk loop, idle
     const int64_t id = active ? gid : 0;
     const int a = (int)(id / p.S);
-    trace_path(p.d, p.fields + (int64_t)a * p.field_stride, p.rates + (int64_t)a * p.d.n_t,
-               p.dec + (int64_t)a * p.d.n_v, p.targets[a], p.sources[id], p.out_xy + id * p.max_pts, p.max_pts,
-               p.max_steps, p.out_len + id, p.out_status + id, active);
+    trace_path(p.d, p.fields + (int64_t)a * p.field_stride, p.rates + a, p.dec + a, p.T, p.targets[a], p.sources[id],
+               p.out_xy + id * p.max_pts, p.max_pts, p.max_steps, p.out_len + id, p.out_status + id, active);
 }
 
 // ---- several meshes in one launch: global target g belongs to domain tdom[g] (local index tloc[g])
 struct BatchTraceDom {
     TraceDom d;
     const float *fields;      // [T_d][n_v]
-    float4 *rates;            // [T_d][n_t]
-    VDec *dec;                // [T_d][n_v]
-    int32_t max_steps, pad;
+    float4 *rates;            // [n_t][T_d]
+    VDec *dec;                // [n_v][T_d]
+    int32_t max_steps, T;
 };
 
 __global__ void batch_rates_kernel(const BatchTraceDom *__restrict__ doms, const int32_t *__restrict__ tdom,
@@ -428,7 +438,7 @@ __global__ void batch_rates_kernel(const BatchTraceDom *__restrict__ doms, const
     const int a = tloc[g];
     const float *f = q.fields + (int64_t)a * q.d.n_v;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < q.d.n_t; t += (int64_t)gridDim.x * blockDim.x)
-        q.rates[(int64_t)a * q.d.n_t + t] = tri_rates(q.d.gphi, q.d.rec, t, f);
+        q.rates[t * q.T + a] = tri_rates(q.d.gphi, q.d.rec, t, f);
 }
 
 __global__ void batch_decision_kernel(const BatchTraceDom *__restrict__ doms, const int32_t *__restrict__ tdom,
@@ -437,9 +447,8 @@ __global__ void batch_decision_kernel(const BatchTraceDom *__restrict__ doms, co
     const BatchTraceDom q = doms[tdom[g]];
     const int a = tloc[g];
     const float *f = q.fields + (int64_t)a * q.d.n_v;
-    const float4 *r = q.rates + (int64_t)a * q.d.n_t;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < q.d.n_v; v += (int64_t)gridDim.x * blockDim.x)
-        q.dec[(int64_t)a * q.d.n_v + v] = vertex_decision(q.d, f, r, targets[g], (int)v);
+        q.dec[v * q.T + a] = vertex_decision(q.d, f, q.rates + a, q.T, targets[g], (int)v);
 }
 
 // path id -> global target: id / S, or path_target[id] when sources per target vary
@@ -457,9 +466,8 @@ __global__ void __launch_bounds__(64) batch_trace_kernel(const BatchTraceDom *__
     const int g = path_target ? path_target[id] : (int)(id / S);
     const BatchTraceDom q = doms[tdom[g]];
     const int a = tloc[g];
-    trace_path(q.d, q.fields + (int64_t)a * q.d.n_v, q.rates + (int64_t)a * q.d.n_t, q.dec + (int64_t)a * q.d.n_v,
-               targets[g], sources[id], out_xy + id * max_pts, max_pts, q.max_steps, out_len + id, out_status + id,
-               active);
+    trace_path(q.d, q.fields + (int64_t)a * q.d.n_v, q.rates + a, q.dec + a, q.T, targets[g], sources[id],
+               out_xy + id * max_pts, max_pts, q.max_steps, out_len + id, out_status + id, active);
 }
 
 TraceDom make_dom(const DevMesh &m) {
@@ -505,14 +513,16 @@ void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, c
     p.S = S;
     p.max_pts = max_pts;
     p.max_steps = step_cap(m);
+    p.T = T;
     p.out_xy = out_xy;
     p.out_len = out_len;
     p.out_status = out_status;
     if (p.total == 0) return;
-    rates_kernel<<<dim3((unsigned)((m.n_t + 255) / 256), (unsigned)T), 256, 0, s>>>(m.gphi, m.trec, m.n_t, fields,
-                                                                                      field_stride, rates);
-    vertex_decision_kernel<<<dim3((unsigned)((m.n_v + 127) / 128), (unsigned)T), 128, 0, s>>>(
-        p.d, fields, field_stride, rates, targets, dec);
+    rates_kernel<<<(unsigned)((m.n_t * T + 255) / 256), 256, 0, s>>>(m.gphi, m.trec, m.n_t, T, fields, field_stride,
+                                                                      rates);
+    const int64_t warps = m.n_v * ((T + 31) / 32);
+    vertex_decision_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(p.d, T, fields, field_stride, rates, targets,
+                                                                        dec);
     trace_kernel<<<(unsigned)((p.total + 63) / 64), 64, 0, s>>>(p);
 }
 
@@ -528,7 +538,7 @@ void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, int3
     q.dec = reinterpret_cast<VDec *>(reinterpret_cast<char *>(scratch) +
                                      align256((size_t)T * m.n_t * sizeof(float4)));
     q.max_steps = step_cap(m);
-    q.pad = 0;
+    q.T = T;
     std::memcpy(dst, &q, sizeof q);
 }
 
