@@ -476,7 +476,7 @@ dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32
         if ((st = ensure_scratch(ctx, S_STATUS, n * sizeof(int32_t))) != DD_OK) return st;
         dst = reinterpret_cast<int32_t *>(ctx->scratch[S_STATUS]);
     }
-    if ((st = ensure_scratch(ctx, S_GRAD, trace_scratch_bytes(m, T))) != DD_OK) return st;
+    if ((st = ensure_scratch(ctx, S_GRAD, trace_scratch_bytes(m, T, trace_dense_decisions(S)))) != DD_OK) return st;
     launch_trace(m, d_fields, m.n_v, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
                  reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), T, S, max_pts, dxy, dlen, dst,
                  ctx->scratch[S_GRAD], ctx->stream);
@@ -633,7 +633,7 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
             toff[i + 1] = toff[i] + T_per[i];
             foff[i + 1] = foff[i] + (int64_t)nf * T_per[i] * ms[i]->n_v;
             stage_floats += 3LL * T_per[i] * ms[i]->k_pad;
-            grad_bytes += (int64_t)trace_scratch_bytes(*ms[i], T_per[i]);
+            grad_bytes += (int64_t)trace_scratch_bytes(*ms[i], T_per[i], false);
             max_nt = std::max(max_nt, ms[i]->n_t);
             max_nv = std::max(max_nv, ms[i]->n_v);
             max_k = std::max(max_k, ms[i]->k_pad);
@@ -733,7 +733,7 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
                 fill_batch_trace_dom(meta.data() + o_doms + i * dom_bytes, *ms[i],
                                      (trace_f == DD_F_TV && probs[i].out_tv) ? probs[i].out_tv : probs[i].out_kl,
                                      T_per[i], grads ? grads + go : nullptr);
-                go += (int64_t)trace_scratch_bytes(*ms[i], T_per[i]);
+                go += (int64_t)trace_scratch_bytes(*ms[i], T_per[i], false);
             }
         }
         for (size_t j = 0; j < order.size(); ++j)

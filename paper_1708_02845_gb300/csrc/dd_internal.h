@@ -109,9 +109,11 @@ std::string tuning_table();
 // spread (max - min) of the hardware mantissa log's error over [1, 2), in base-2 units
 dd_status fast_log_spread(double *spread, std::string &err);
 
-// Tracer: per-field triangle rates and vertex decisions into `scratch`
-// (trace_scratch_bytes(m, T) bytes), then T*S paths.
-size_t trace_scratch_bytes(const DevMesh &m, int32_t T);
+// Tracer: per-field triangle rates (and, when trace_dense_decisions(S), vertex
+// decisions) into `scratch` (trace_scratch_bytes(m, T, dense) bytes), then
+// T*S paths.
+bool trace_dense_decisions(int32_t S);
+size_t trace_scratch_bytes(const DevMesh &m, int32_t T, bool decisions);
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,
                   const int32_t *sources, int32_t T, int32_t S, int32_t max_pts, float2 *out_xy,
                   int32_t *out_len, int32_t *out_status, void *scratch, cudaStream_t s);
@@ -125,7 +127,8 @@ dd_status launch_kl_gemm(const DevMesh &m, const int32_t *d_targets, int32_t T, 
                          int *err_flag, cudaStream_t s, std::string &err);
 
 // Tracer over several meshes in one launch (descriptors built on the host;
-// each item's scratch: trace_scratch_bytes(m, T_item) bytes).
+// each item's scratch: trace_scratch_bytes(m, T_item, false) bytes; the walk
+// computes vertex decisions itself).
 size_t batch_trace_dom_bytes();
 void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, int32_t T, void *scratch);
 void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t *d_tloc, const int32_t *d_targets,

@@ -90,7 +90,7 @@ namespace {
 
 // device bytes one query needs inside a batch
 size_t query_need(const DevMesh &m, int32_t S, int32_t max_pts) {
-    return al((size_t)m.n_v * 4) + al((size_t)3 * m.k_pad * 4) + al(trace_scratch_bytes(m, 1)) +
+    return al((size_t)m.n_v * 4) + al((size_t)3 * m.k_pad * 4) + al(trace_scratch_bytes(m, 1, false)) +
            al((size_t)S * ((size_t)max_pts * 8 + 8)) + al((size_t)S * 8) + 4096;
 }
 
@@ -147,7 +147,7 @@ bool launch_batch(dd_server *sv, Slot &sl) {
     for (int i = 0; i < n_items; ++i) {
         stage_f += (size_t)3 * Ts[i] * ms[i]->k_pad;
         field_f += (size_t)Ts[i] * ms[i]->n_v;
-        grad_b += trace_scratch_bytes(*ms[i], Ts[i]);
+        grad_b += trace_scratch_bytes(*ms[i], Ts[i], false);
     }
     const size_t o_stage = take(stage_f * 4), o_fields = take(field_f * 4), o_grads = take(grad_b);
     const size_t o_xy = take((size_t)n_paths * sv->max_pts * 8), o_len = take(n_paths * 4), o_st = take(n_paths * 4);
@@ -197,7 +197,7 @@ bool launch_batch(dd_server *sv, Slot &sl) {
             q.out_tv = nullptr;
             fill_batch_trace_dom(h + o_doms + i * dom_bytes, m, q.out_kl, Ts[i], d + o_grads + go);
             fo += (size_t)Ts[i] * m.n_v;
-            go += trace_scratch_bytes(m, Ts[i]);
+            go += trace_scratch_bytes(m, Ts[i], false);
         }
         std::memcpy(h + o_probs, probs.data(), n_items * sizeof(BatchProblem));
         size_t j = 0;

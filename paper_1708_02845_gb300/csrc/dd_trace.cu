@@ -33,6 +33,7 @@
 // (one 48-byte load), or slide along a valley or boundary edge.
 #include <cfloat>
 #include <cstring>
+#include <cstdlib>
 #include <algorithm>
 #include <cmath>
 
@@ -42,6 +43,7 @@ namespace {
 
 constexpr float kEpsBary = 1e-6f;    // barycentric snap to a vertex
 constexpr float kEpsWedge = 1e-6f;   // relative tolerance of the wedge / entry tests
+constexpr int32_t kDenseMinPaths = 128;   // paths per field from which decisions are precomputed
 
 // Triangle record (64 bytes): vertex ids, the ids of the triangles across the
 // edges opposite each vertex (-1 on the boundary), the squared norms q_i of
@@ -117,21 +119,29 @@ struct TraceDom {
     int64_t n_t, n_v;
 };
 
-// the vertex state's decision at v for field f (with that field's rates)
-// (rates of field a start at `rates`, one entry per triangle every `rstride`)
-__device__ __forceinline__ VDec vertex_decision(const TraceDom &p, const float *__restrict__ f,
-                                                const float4 *__restrict__ rates, int64_t rstride, int target, int v) {
-    const float eps2 = kEpsWedge * kEpsWedge;
-    bool adj = false;
-    int best = -1;
-    float best_g2 = 0.f, baj = 0.f, bak = 0.f;
-    int b_vj = 0, b_vk = 0, b_next = -1;
-    float2 b_pj = make_float2(0.f, 0.f), b_pk = b_pj;
-    const int q0 = p.vt_off[v], q1 = p.vt_off[v + 1];
-    for (int q = q0; q < q1; ++q) {
-        const int tl = p.vt[q];
-        const Tri T = load_tri(p.rec, tl);
-        const float4 R = __ldg(rates + (int64_t)tl * rstride);
+// The vertex state at v, one incident triangle at a time: add() examines a
+// triangle of v's fan, finish() turns the fan's best candidate into the
+// decision.  Both the decision kernel (a whole fan in one call) and the walk
+// without precomputed decisions (one triangle per iteration) use it, so the
+// two give the same decision bit for bit.
+struct FanScan {
+    bool adj;
+    int best, b_vj, b_vk, b_next;
+    float best_g2, baj, bak;
+    float2 b_pj, b_pk;
+
+    __device__ __forceinline__ void begin() {
+        adj = false;
+        best = -1;
+        b_vj = b_vk = 0;
+        b_next = -1;
+        best_g2 = baj = bak = 0.f;
+        b_pj = b_pk = make_float2(0.f, 0.f);
+    }
+
+    // triangle tl (record T, rates R of the field) incident on v
+    __device__ __forceinline__ void add(int v, int target, int tl, const Tri &T, const float4 &R) {
+        const float eps2 = kEpsWedge * kEpsWedge;
         // rotated view: v is local vertex L, then X and Y counter-clockwise; the exit edge is X-Y
         const int L = local_of(T, v), X = L == 2 ? 0 : L + 1, Y = L == 0 ? 2 : L - 1;
         const float rX = sel3f(X, R.x, R.y, R.z), rY = sel3f(Y, R.x, R.y, R.z);
@@ -154,60 +164,76 @@ __device__ __forceinline__ VDec vertex_decision(const TraceDom &p, const float *
             b_next = sel3i(L, T.n0, T.n1, T.n2);
         }
     }
-    VDec d;
-    d.e = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (adj) {                                   // v lies on an edge incident on the target
-        const float2 pt = p.xy[target];
-        d.h = make_int4(kVAdjacent, target, 0, 0);
-        d.w = make_float4(pt.x, pt.y, 0.f, 0.f);
-        return d;
-    }
-    if (best >= 0) {
-        const float s = __fdividef(1.0f, baj + bak);
-        const float lj = s * baj, lk = s * bak;
-        if (lj <= kEpsBary) {
-            d.h = make_int4(kVVertex, b_vk, 0, 0);
-            d.w = make_float4(b_pk.x, b_pk.y, 0.f, 0.f);
-        } else if (lk <= kEpsBary) {
-            d.h = make_int4(kVVertex, b_vj, 0, 0);
-            d.w = make_float4(b_pj.x, b_pj.y, 0.f, 0.f);
-        } else {
-            d.h = make_int4(kVCross, b_vj, b_vk, b_next);
-            d.w = make_float4(lj, lk, lj * b_pj.x + lk * b_pk.x, lj * b_pj.y + lk * b_pk.y);
-            d.e = make_float4(b_pj.x, b_pj.y, b_pk.x, b_pk.y);
+
+    __device__ __forceinline__ VDec finish(const TraceDom &p, const float *__restrict__ f, int target, int v) const {
+        VDec d;
+        d.e = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (adj) {                                   // v lies on an edge incident on the target
+            const float2 pt = p.xy[target];
+            d.h = make_int4(kVAdjacent, target, 0, 0);
+            d.w = make_float4(pt.x, pt.y, 0.f, 0.f);
+            return d;
         }
-        return d;
-    }
-    // no descending triangle: the incident edge of largest positive slope (ties to the lower id)
-    int best_u = -1;
-    float best_s = 0.f;
-    float2 best_p = make_float2(0.f, 0.f);
-    const float fv = f[v];
-    const float2 pv = p.xy[v];
-    for (int q = q0; q < q1; ++q) {
-        const Tri Q = load_tri(p.rec, p.vt[q]);
+        if (best >= 0) {
+            const float s = __fdividef(1.0f, baj + bak);
+            const float lj = s * baj, lk = s * bak;
+            if (lj <= kEpsBary) {
+                d.h = make_int4(kVVertex, b_vk, 0, 0);
+                d.w = make_float4(b_pk.x, b_pk.y, 0.f, 0.f);
+            } else if (lk <= kEpsBary) {
+                d.h = make_int4(kVVertex, b_vj, 0, 0);
+                d.w = make_float4(b_pj.x, b_pj.y, 0.f, 0.f);
+            } else {
+                d.h = make_int4(kVCross, b_vj, b_vk, b_next);
+                d.w = make_float4(lj, lk, lj * b_pj.x + lk * b_pk.x, lj * b_pj.y + lk * b_pk.y);
+                d.e = make_float4(b_pj.x, b_pj.y, b_pk.x, b_pk.y);
+            }
+            return d;
+        }
+        // no descending triangle: the incident edge of largest positive slope (ties to the lower id)
+        int best_u = -1;
+        float best_s = 0.f;
+        float2 best_p = make_float2(0.f, 0.f);
+        const float fv = f[v];
+        const float2 pv = p.xy[v];
+        for (int q = p.vt_off[v]; q < p.vt_off[v + 1]; ++q) {
+            const Tri Q = load_tri(p.rec, p.vt[q]);
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            const int u = vid(Q, e);
-            if (u == v) continue;
-            const float2 pu = pos(Q, e);
-            const float dx = pv.x - pu.x, dy = pv.y - pu.y;
-            const float slope = (fv - f[u]) / sqrtf(dx * dx + dy * dy);
-            if (slope > 0.f && (slope > best_s || (slope == best_s && u < best_u))) {
-                best_s = slope;
-                best_u = u;
-                best_p = pu;
+            for (int e = 0; e < 3; ++e) {
+                const int u = vid(Q, e);
+                if (u == v) continue;
+                const float2 pu = pos(Q, e);
+                const float dx = pv.x - pu.x, dy = pv.y - pu.y;
+                const float slope = (fv - f[u]) / sqrtf(dx * dx + dy * dy);
+                if (slope > 0.f && (slope > best_s || (slope == best_s && u < best_u))) {
+                    best_s = slope;
+                    best_u = u;
+                    best_p = pu;
+                }
             }
         }
+        if (best_u < 0) {
+            d.h = make_int4(kVStuck, 0, 0, 0);
+            d.w = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            d.h = make_int4(kVVertex, best_u, 0, 0);
+            d.w = make_float4(best_p.x, best_p.y, 0.f, 0.f);
+        }
+        return d;
     }
-    if (best_u < 0) {
-        d.h = make_int4(kVStuck, 0, 0, 0);
-        d.w = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-        d.h = make_int4(kVVertex, best_u, 0, 0);
-        d.w = make_float4(best_p.x, best_p.y, 0.f, 0.f);
+};
+
+// the vertex state's decision at v for field f (rates of that field at
+// `rates`, one entry per triangle every `rstride`)
+__device__ __forceinline__ VDec vertex_decision(const TraceDom &p, const float *__restrict__ f,
+                                                const float4 *__restrict__ rates, int64_t rstride, int target, int v) {
+    FanScan fs;
+    fs.begin();
+    for (int q = p.vt_off[v], q1 = p.vt_off[v + 1]; q < q1; ++q) {
+        const int tl = p.vt[q];
+        fs.add(v, target, tl, load_tri(p.rec, tl), __ldg(rates + (int64_t)tl * rstride));
     }
-    return d;
+    return fs.finish(p, f, target, v);
 }
 
 // one warp per (vertex, group of 32 fields), lane = field: dec[v * T + a]
@@ -226,13 +252,15 @@ __global__ void vertex_decision_kernel(const TraceDom p, int32_t T, const float 
 // triangle rates and vertex decisions.  The warp votes at the top of every
 // iteration, so its threads reconverge once per step; finished threads (and
 // padding lanes) idle there until the last path of the warp ends.
-// (rates and decisions of this field start at `rates` and `dec`, one entry
-// per triangle or vertex every `stride` -- the number of fields)
+// (rates of this field start at `rates`, one entry per triangle every
+// `rstride`; its decisions at `dec`, one per vertex every `dstride`.  With
+// dec == nullptr a vertex state computes its decision itself -- the same
+// function, so the same result -- which pays when few paths share a field.)
 __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__restrict__ f,
-                                           const float4 *__restrict__ rates, const VDec *__restrict__ dec,
-                                           int64_t stride, int target, int source, float2 *__restrict__ out,
-                                           int32_t max_pts, int32_t max_steps, int32_t *len_out,
-                                           int32_t *status_out, bool active) {
+                                           const float4 *__restrict__ rates, int64_t rstride,
+                                           const VDec *__restrict__ dec, int64_t dstride, int target, int source,
+                                           float2 *__restrict__ out, int32_t max_pts, int32_t max_steps,
+                                           int32_t *len_out, int32_t *status_out, bool active) {
     const float eps2 = kEpsWedge * kEpsWedge;
     int len = 0;
     int status = DD_TRACE_STEP_LIMIT;
@@ -240,6 +268,15 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
     bool fin = !active;
     bool at_vertex = true;
     int v = source;
+    // fan scan of the current vertex when decisions are not precomputed: one
+    // incident triangle (from the vertex's triangle list) per iteration
+    FanScan fs;
+    fs.begin();
+    int scan_q = 0, scan_end = 0;
+    if (active && !dec) {
+        scan_q = p.vt_off[v];
+        scan_end = p.vt_off[v + 1];
+    }
     // edge state: the path sits on edge (ea, eb) at weights (la, lb) and enters
     // t_next (the triangle across that edge, -1 on the boundary)
     int t_next = -1, ea = 0, eb = 0;
@@ -266,6 +303,11 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
 #define DD_ENTER_VERTEX(vert)                    \
     v = (vert);                                  \
     at_vertex = true;                            \
+    if (!dec) {                                  \
+        fs.begin();                              \
+        scan_q = p.vt_off[v];                    \
+        scan_end = p.vt_off[v + 1];              \
+    }                                            \
     if (++states > max_steps) {                  \
         fin = true;                              \
         continue;                                \
@@ -289,18 +331,29 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
         if (!__any_sync(0xffffffffu, !fin)) break;
         if (fin) continue;
         if (at_vertex) {
-            // ---- vertex state: apply the precomputed decision
-            const VDec *dv = dec + (int64_t)v * stride;
-            const int4 h = __ldg(&dv->h);
-            const float4 w = __ldg(&dv->w);
-            if (h.x == kVStuck) {
+            // ---- vertex state: apply the decision (precomputed, or scanned here one
+            // incident triangle per iteration, so the warp's other lanes wait little)
+            const VDec *dv = dec ? dec + (int64_t)v * dstride : nullptr;
+            VDec own;
+            if (!dv) {
+                if (scan_q < scan_end) {
+                    const int tl = p.vt[scan_q++];
+                    fs.add(v, target, tl, load_tri(p.rec, tl), __ldg(rates + (int64_t)tl * rstride));
+                    continue;
+                }
+                own = fs.finish(p, f, target, v);
+            }
+            const int4 h = dv ? __ldg(&dv->h) : own.h;
+            const float4 w = dv ? __ldg(&dv->w) : own.w;
+            const int kind = h.x;
+            if (kind == kVStuck) {
                 status = DD_TRACE_STUCK;
                 fin = true;
                 continue;
             }
-            const bool cross = h.x == kVCross;
+            const bool cross = kind == kVCross;
             DD_PUSH(make_float2(cross ? w.z : w.x, cross ? w.w : w.y));
-            if (h.x == kVAdjacent) {
+            if (kind == kVAdjacent) {
                 status = DD_TRACE_OK;
                 fin = true;
                 continue;
@@ -309,7 +362,7 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
                 DD_ENTER_VERTEX(h.y);
                 continue;
             }
-            const float4 e = __ldg(&dv->e);
+            const float4 e = dv ? __ldg(&dv->e) : own.e;
             at_vertex = false;
             ea = h.y;
             eb = h.z;
@@ -329,7 +382,7 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
         // eb is local vertex L, ea is X, and the opposite vertex is Y
         const int tl = t_next;
         const Tri T = load_tri(p.rec, tl);
-        const float4 Rt = __ldg(rates + (int64_t)tl * stride);
+        const float4 Rt = __ldg(rates + (int64_t)tl * rstride);
         const int L = local_of(T, eb), X = L == 2 ? 0 : L + 1, Y = L == 0 ? 2 : L - 1;
         const float ra = sel3f(X, Rt.x, Rt.y, Rt.z), rb = sel3f(L, Rt.x, Rt.y, Rt.z), rc = sel3f(Y, Rt.x, Rt.y, Rt.z);
         const float qY = sel3f(Y, T.q0, T.q1, T.q2);
@@ -418,16 +471,16 @@ __global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
     const bool active = gid < p.total;       // padding lanes stay in the warp's walk loop, idle
     const int64_t id = active ? gid : 0;
     const int a = (int)(id / p.S);
-    trace_path(p.d, p.fields + (int64_t)a * p.field_stride, p.rates + a, p.dec + a, p.T, p.targets[a], p.sources[id],
-               p.out_xy + id * p.max_pts, p.max_pts, p.max_steps, p.out_len + id, p.out_status + id, active);
+    trace_path(p.d, p.fields + (int64_t)a * p.field_stride, p.rates + a, p.T, p.dec ? p.dec + a : nullptr, p.T,
+               p.targets[a], p.sources[id], p.out_xy + id * p.max_pts, p.max_pts, p.max_steps, p.out_len + id,
+               p.out_status + id, active);
 }
 
 // ---- several meshes in one launch: global target g belongs to domain tdom[g] (local index tloc[g])
 struct BatchTraceDom {
     TraceDom d;
     const float *fields;      // [T_d][n_v]
-    float4 *rates;            // [n_t][T_d]
-    VDec *dec;                // [n_v][T_d]
+    float4 *rates;            // [T_d][n_t] (decisions are computed by the walk itself)
     int32_t max_steps, T;
 };
 
@@ -438,17 +491,7 @@ __global__ void batch_rates_kernel(const BatchTraceDom *__restrict__ doms, const
     const int a = tloc[g];
     const float *f = q.fields + (int64_t)a * q.d.n_v;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < q.d.n_t; t += (int64_t)gridDim.x * blockDim.x)
-        q.rates[t * q.T + a] = tri_rates(q.d.gphi, q.d.rec, t, f);
-}
-
-__global__ void batch_decision_kernel(const BatchTraceDom *__restrict__ doms, const int32_t *__restrict__ tdom,
-                                      const int32_t *__restrict__ tloc, const int32_t *__restrict__ targets) {
-    const int g = blockIdx.y;
-    const BatchTraceDom q = doms[tdom[g]];
-    const int a = tloc[g];
-    const float *f = q.fields + (int64_t)a * q.d.n_v;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < q.d.n_v; v += (int64_t)gridDim.x * blockDim.x)
-        q.dec[v * q.T + a] = vertex_decision(q.d, f, q.rates + a, q.T, targets[g], (int)v);
+        q.rates[(int64_t)a * q.d.n_t + t] = tri_rates(q.d.gphi, q.d.rec, t, f);
 }
 
 // path id -> global target: id / S, or path_target[id] when sources per target vary
@@ -466,8 +509,8 @@ __global__ void __launch_bounds__(64) batch_trace_kernel(const BatchTraceDom *__
     const int g = path_target ? path_target[id] : (int)(id / S);
     const BatchTraceDom q = doms[tdom[g]];
     const int a = tloc[g];
-    trace_path(q.d, q.fields + (int64_t)a * q.d.n_v, q.rates + a, q.dec + a, q.T, targets[g], sources[id],
-               out_xy + id * max_pts, max_pts, q.max_steps, out_len + id, out_status + id, active);
+    trace_path(q.d, q.fields + (int64_t)a * q.d.n_v, q.rates + (int64_t)a * q.d.n_t, 1, nullptr, 0, targets[g],
+               sources[id], out_xy + id * max_pts, max_pts, q.max_steps, out_len + id, out_status + id, active);
 }
 
 TraceDom make_dom(const DevMesh &m) {
@@ -491,17 +534,33 @@ int32_t step_cap(const DevMesh &m) {
 
 }  // namespace
 
-size_t trace_scratch_bytes(const DevMesh &m, int32_t T) {
-    return align256((size_t)T * m.n_t * sizeof(float4)) + align256((size_t)T * m.n_v * sizeof(VDec));
+size_t trace_scratch_bytes(const DevMesh &m, int32_t T, bool decisions) {
+    return align256((size_t)T * m.n_t * sizeof(float4)) +
+           (decisions ? align256((size_t)T * m.n_v * sizeof(VDec)) : 0);
+}
+
+// Vertex decisions for every (field, vertex) before the walk pay off when
+// many paths share a field (they are reused); with few paths each vertex
+// state computes its own.  DD_TRACE_DECISIONS=dense|lazy overrides the choice
+// (for measurements).
+bool trace_dense_decisions(int32_t S) {
+    static int mode = -1;
+    if (mode < 0) {
+        const char *e = getenv("DD_TRACE_DECISIONS");
+        mode = (e && !strcmp(e, "dense")) ? 1 : (e && !strcmp(e, "lazy")) ? 0 : 2;
+    }
+    return mode == 2 ? S >= kDenseMinPaths : mode == 1;
 }
 
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,
                   const int32_t *sources, int32_t T, int32_t S, int32_t max_pts, float2 *out_xy, int32_t *out_len,
                   int32_t *out_status, void *scratch, cudaStream_t s) {
+    const bool dense = trace_dense_decisions(S);
     TraceParams p;
     float4 *rates = reinterpret_cast<float4 *>(scratch);
-    VDec *dec = reinterpret_cast<VDec *>(reinterpret_cast<char *>(scratch) +
-                                         align256((size_t)T * m.n_t * sizeof(float4)));
+    VDec *dec = dense ? reinterpret_cast<VDec *>(reinterpret_cast<char *>(scratch) +
+                                                 align256((size_t)T * m.n_t * sizeof(float4)))
+                      : nullptr;
     p.d = make_dom(m);
     p.rates = rates;
     p.dec = dec;
@@ -520,9 +579,11 @@ void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, c
     if (p.total == 0) return;
     rates_kernel<<<(unsigned)((m.n_t * T + 255) / 256), 256, 0, s>>>(m.gphi, m.trec, m.n_t, T, fields, field_stride,
                                                                       rates);
-    const int64_t warps = m.n_v * ((T + 31) / 32);
-    vertex_decision_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(p.d, T, fields, field_stride, rates, targets,
-                                                                        dec);
+    if (dense) {
+        const int64_t warps = m.n_v * ((T + 31) / 32);
+        vertex_decision_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(p.d, T, fields, field_stride, rates,
+                                                                            targets, dec);
+    }
     trace_kernel<<<(unsigned)((p.total + 63) / 64), 64, 0, s>>>(p);
 }
 
@@ -535,8 +596,6 @@ void fill_batch_trace_dom(void *dst, const DevMesh &m, const float *fields, int3
     q.d = make_dom(m);
     q.fields = fields;
     q.rates = reinterpret_cast<float4 *>(scratch);
-    q.dec = reinterpret_cast<VDec *>(reinterpret_cast<char *>(scratch) +
-                                     align256((size_t)T * m.n_t * sizeof(float4)));
     q.max_steps = step_cap(m);
     q.T = T;
     std::memcpy(dst, &q, sizeof q);
@@ -552,8 +611,7 @@ void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t
     if (total == 0) return;
     dim3 gr((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_nt + 255) / 256)), (unsigned)n_targets);
     batch_rates_kernel<<<gr, 256, 0, s>>>(doms, d_tdom, d_tloc);
-    dim3 gd((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_nv + 127) / 128)), (unsigned)n_targets);
-    batch_decision_kernel<<<gd, 128, 0, s>>>(doms, d_tdom, d_tloc, d_targets);
+    (void)max_nv;
     batch_trace_kernel<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(doms, d_tdom, d_tloc, d_targets, d_sources,
                                                                     d_path_target, total, S, max_pts, out_xy, out_len,
                                                                     out_status);
