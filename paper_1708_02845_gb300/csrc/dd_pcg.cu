@@ -1,9 +1,12 @@
 // Poisson-kernel preprocessing, Section IV Eq. (32)-(33), in FP64 on the GPU.
 //
 // Solves (-L_II) X = L_IB for all k boundary columns at once: one
-// Jacobi-preconditioned conjugate-gradient recurrence per column, run in
-// lock-step over a block of columns so that every sparse product streams the
-// whole row-major [m][kc] block.  -L_II is a symmetric positive-definite
+// preconditioned conjugate-gradient recurrence per column, run in lock-step
+// over a block of columns so that every sparse product streams the whole
+// row-major [m][kc] block.  The preconditioner is a smoothed-aggregation
+// multigrid V-cycle (dd_amg.cpp builds the hierarchy on the host); the
+// diagonal (Jacobi) preconditioner remains for tiny meshes and as the
+// fallback when no hierarchy can be built.  -L_II is a symmetric positive-definite
 // M-matrix, so CG converges; its iterates are kept in FP64 because the
 // small entries of P (shadowed boundary parts) need many correct digits for
 // the logarithms of Eq. (35).  The block stops when every column's residual
@@ -14,7 +17,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <functional>
 
+#include "dd_amg.h"
 #include "dd_internal.h"
 
 namespace {
@@ -215,9 +221,394 @@ __global__ void store_host_p_kernel(int64_t n_v, int64_t k, int64_t k_pad, const
     P[v * k_pad + c] = x < (double)FLT_MIN ? 0.0f : (float)x;
 }
 
+// ---------------------------------------------------------------- multigrid V-cycle kernels
+// Row-major [rows][kc] FP64 blocks, one thread per column, CTAs over row blocks.
+enum { kSpmmSet = 0, kSpmmResidual = 1, kSpmmAdd = 2 };
+
+// MODE kSpmmSet: Y = M X;  kSpmmResidual: Y = B - M X;  kSpmmAdd: Y += M X
+template <int MODE>
+__global__ void csr_spmm_kernel(int64_t rows, int64_t kc, const int64_t *__restrict__ off,
+                                const int32_t *__restrict__ col, const double *__restrict__ val,
+                                const double *__restrict__ X, const double *__restrict__ B, double *__restrict__ Y,
+                                int rpb) {
+    const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
+    if (c >= kc) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < rows ? r0 + rpb : rows;
+    for (int64_t r = r0; r < r1; ++r) {
+        double s = 0.0;
+        for (int64_t q = off[r]; q < off[r + 1]; ++q) s += val[q] * X[(int64_t)col[q] * kc + c];
+        const int64_t i = r * kc + c;
+        if (MODE == kSpmmSet) Y[i] = s;
+        if (MODE == kSpmmResidual) Y[i] = B[i] - s;
+        if (MODE == kSpmmAdd) Y[i] += s;
+    }
+}
+
+// X = omega D^-1 B (one Jacobi sweep from zero)
+__global__ void jacobi0_kernel(int64_t rows, int64_t kc, double omega, const double *__restrict__ dinv,
+                               const double *__restrict__ B, double *__restrict__ X, int rpb) {
+    const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
+    if (c >= kc) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < rows ? r0 + rpb : rows;
+    for (int64_t r = r0; r < r1; ++r) X[r * kc + c] = omega * dinv[r] * B[r * kc + c];
+}
+
+// X += omega D^-1 Res; with DOT, also partial column sums of Rp . X (the
+// preconditioned residual's inner product, on the fine level)
+template <bool DOT>
+__global__ void jacobi_add_kernel(int64_t rows, int64_t kc, double omega, const double *__restrict__ dinv,
+                                  const double *__restrict__ Res, double *__restrict__ X,
+                                  const double *__restrict__ Rp, double *__restrict__ part, int rpb) {
+    const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
+    if (c >= kc) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < rows ? r0 + rpb : rows;
+    double acc = 0.0;
+    for (int64_t r = r0; r < r1; ++r) {
+        const int64_t i = r * kc + c;
+        const double x = X[i] + omega * dinv[r] * Res[i];
+        X[i] = x;
+        if (DOT) acc += Rp[i] * x;
+    }
+    if (DOT) part[(int64_t)blockIdx.x * kc + c] = acc;
+}
+
+// X = Ainv B on the coarsest level (Ainv dense n x n, row-major)
+__global__ void coarse_solve_kernel(int64_t n, int64_t kc, const double *__restrict__ ainv,
+                                    const double *__restrict__ B, double *__restrict__ X) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.y;
+    if (c >= kc || i >= n) return;
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) s += ainv[i * n + j] * B[j * kc + c];
+    X[i * kc + c] = s;
+}
+
+// X += alpha Pd, R -= alpha AP; partial column sums of R.R
+__global__ void update_xr_plain_kernel(int64_t m, int64_t kc, const double *__restrict__ alpha,
+                                       double *__restrict__ X, double *__restrict__ R,
+                                       const double *__restrict__ Pd, const double *__restrict__ AP,
+                                       double *__restrict__ part_rr, int rpb) {
+    const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
+    if (c >= kc) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
+    const double a = alpha[c];
+    double srr = 0.0;
+    for (int64_t r = r0; r < r1; ++r) {
+        const int64_t i = r * kc + c;
+        double rr = R[i];
+        if (a != 0.0) {
+            X[i] += a * Pd[i];
+            rr -= a * AP[i];
+            R[i] = rr;
+        }
+        srr += rr * rr;
+    }
+    part_rr[(int64_t)blockIdx.x * kc + c] = srr;
+}
+
+// partial column sums of R.R
+__global__ void dot_rr_kernel(int64_t m, int64_t kc, const double *__restrict__ R, double *__restrict__ part,
+                              int rpb) {
+    const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
+    if (c >= kc) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
+    double acc = 0.0;
+    for (int64_t r = r0; r < r1; ++r) acc += R[r * kc + c] * R[r * kc + c];
+    part[(int64_t)blockIdx.x * kc + c] = acc;
+}
+
+// Pd = Z + beta Pd (beta = 0 on the first iteration)
+__global__ void update_p_z_kernel(int64_t m, int64_t kc, const double *__restrict__ beta,
+                                  const double *__restrict__ Z, double *__restrict__ Pd, int first, int rpb) {
+    const int64_t c = (int64_t)blockIdx.y * kColsPerBlock + threadIdx.x;
+    if (c >= kc) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = r0 + rpb < m ? r0 + rpb : m;
+    const double b = first ? 0.0 : beta[c];
+    for (int64_t r = r0; r < r1; ++r) {
+        const int64_t i = r * kc + c;
+        Pd[i] = first ? Z[i] : Z[i] + b * Pd[i];
+    }
+}
+
+// rz = column sums of part_rz, bnorm from part_rr, done flags (first iteration)
+__global__ void amg_init_scalars_kernel(int64_t nrb, int64_t kc, const double *__restrict__ part_rz,
+                                        const double *__restrict__ part_rr, double *__restrict__ rz,
+                                        double *__restrict__ bnorm, int *__restrict__ done) {
+    __shared__ double sh[8][33];
+    const int64_t c = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    double s_rz = column_sum(part_rz, nrb, kc, c, sh);
+    double s_rr = column_sum(part_rr, nrb, kc, c, sh);
+    if (threadIdx.y == 0 && c < kc) {
+        rz[c] = s_rz;
+        bnorm[c] = sqrt(s_rr);
+        done[c] = s_rr > 0.0 ? 0 : 1;   // a column with no interior support is exactly zero
+    }
+}
+
 template <typename T>
 cudaError_t alloc(T **p, size_t count) {
     return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+// rows per CTA for a [rows][kc] block: enough CTAs (about 16 per SM), at most 256 rows
+int rows_per_block(int64_t rows, int64_t kc) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    const int64_t colblocks = (kc + kColsPerBlock - 1) / kColsPerBlock;
+    const int64_t want = rows * colblocks / (16LL * sms);
+    int rpb = 256;
+    while (rpb > 4 && rpb > want) rpb >>= 1;
+    return rpb;
+}
+
+struct DevCsr {
+    int64_t rows = 0;
+    int64_t *off = nullptr;
+    int32_t *col = nullptr;
+    double *val = nullptr;
+};
+
+// Block CG with the smoothed-aggregation V-cycle as preconditioner (one
+// Jacobi pre- and post-sweep per level, exact coarsest solve): symmetric and
+// positive definite, so CG applies.  Returns DD_ENOTCONV with *fallback set
+// when the hierarchy cannot be built (the caller then uses Jacobi).
+dd_status run_pcg_amg(DevMesh &M, double rtol, int32_t max_iter, cudaStream_t s, int32_t *iters_out,
+                      double *resid_out, std::string &err, bool *fallback) {
+    *fallback = false;
+    const int64_t m = M.m, k = M.k;
+    // host copy of A = -L_II and the hierarchy
+    AmgCsr A0;
+    A0.rows = A0.cols = m;
+    A0.off.resize(m + 1);
+    DD_CUDA_TRY(cudaMemcpy(A0.off.data(), M.a_off, (m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost), err);
+    const int64_t nnz = A0.off[m];
+    A0.col.resize(nnz);
+    A0.val.resize(nnz);
+    DD_CUDA_TRY(cudaMemcpy(A0.col.data(), M.a_col, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost), err);
+    DD_CUDA_TRY(cudaMemcpy(A0.val.data(), M.a_val, nnz * sizeof(double), cudaMemcpyDeviceToHost), err);
+    AmgHierarchy H;
+    std::string why;
+    if (!build_amg(A0, H, why)) {
+        *fallback = true;
+        err = why;
+        return DD_ENOTCONV;
+    }
+    const int nl = (int)H.levels.size();
+
+    std::vector<void *> tmp;
+    cudaError_t ce = cudaSuccess;
+    auto dalloc = [&](void **p, size_t bytes) {
+        if (ce != cudaSuccess) return;
+        ce = cudaMalloc(p, bytes > 0 ? bytes : 8);
+        if (ce == cudaSuccess) tmp.push_back(*p);
+    };
+    auto upload = [&](void *dst, const void *src, size_t bytes) {
+        if (ce == cudaSuccess && bytes > 0) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    auto up_csr = [&](const AmgCsr &h, DevCsr &d) {
+        d.rows = h.rows;
+        dalloc((void **)&d.off, h.off.size() * sizeof(int64_t));
+        dalloc((void **)&d.col, h.col.size() * sizeof(int32_t));
+        dalloc((void **)&d.val, h.val.size() * sizeof(double));
+        upload(d.off, h.off.data(), h.off.size() * sizeof(int64_t));
+        upload(d.col, h.col.data(), h.col.size() * sizeof(int32_t));
+        upload(d.val, h.val.data(), h.val.size() * sizeof(double));
+    };
+    std::vector<DevCsr> dA(nl), dP(nl), dR(nl);
+    std::vector<double *> dinv(nl, nullptr);
+    for (int l = 0; l < nl; ++l) {
+        const AmgLevel &L = H.levels[l];
+        if (l == 0) {
+            dA[0].rows = m;
+            dA[0].off = M.a_off;
+            dA[0].col = M.a_col;
+            dA[0].val = M.a_val;
+        } else {
+            up_csr(L.A, dA[l]);
+        }
+        dalloc((void **)&dinv[l], L.dinv.size() * sizeof(double));
+        upload(dinv[l], L.dinv.data(), L.dinv.size() * sizeof(double));
+        if (l + 1 < nl) {
+            up_csr(L.P, dP[l]);
+            up_csr(L.R, dR[l]);
+        }
+    }
+    double *ainv = nullptr;
+    dalloc((void **)&ainv, H.coarse_inv.size() * sizeof(double));
+    upload(ainv, H.coarse_inv.data(), H.coarse_inv.size() * sizeof(double));
+
+    // chunk width: six FP64 [m][kc] vectors on the fine level, three per coarser
+    // level, within a 24 GB workspace budget
+    double per_col = 6.0 * 8.0 * (double)m;
+    for (int l = 1; l < nl; ++l) per_col += 3.0 * 8.0 * (double)H.levels[l].A.rows;
+    int64_t kc = (int64_t)(24e9 / per_col);
+    kc = kc / 128 * 128;
+    if (kc < 128) kc = 128;
+    if (kc > ((k + 3) / 4) * 4) kc = ((k + 3) / 4) * 4;
+    const int rpb0 = rows_per_block(m, kc);
+    const int64_t nrb = (m + rpb0 - 1) / rpb0;
+    std::vector<int> rpb(nl);
+    for (int l = 0; l < nl; ++l) rpb[l] = rows_per_block(H.levels[l].A.rows, kc);
+    const size_t vec = (size_t)m * kc * sizeof(double);
+    double *X = nullptr, *R = nullptr, *Z = nullptr, *Pd = nullptr, *AP = nullptr;
+    double *part0 = nullptr, *part1 = nullptr, *alpha = nullptr, *beta = nullptr, *rz = nullptr, *bnorm = nullptr;
+    int *done = nullptr;
+    unsigned long long *maxres = nullptr;
+    dalloc((void **)&X, vec);
+    dalloc((void **)&R, vec);
+    dalloc((void **)&Z, vec);
+    dalloc((void **)&Pd, vec);
+    dalloc((void **)&AP, vec);
+    std::vector<double *> lb(nl, nullptr), lx(nl, nullptr), lr(nl, nullptr);
+    for (int l = 0; l < nl; ++l) {
+        const size_t lv = (size_t)H.levels[l].A.rows * kc * sizeof(double);
+        dalloc((void **)&lr[l], lv);
+        if (l > 0) {
+            dalloc((void **)&lb[l], lv);
+            dalloc((void **)&lx[l], lv);
+        }
+    }
+    dalloc((void **)&part0, (size_t)nrb * kc * sizeof(double));
+    dalloc((void **)&part1, (size_t)nrb * kc * sizeof(double));
+    dalloc((void **)&alpha, kc * sizeof(double));
+    dalloc((void **)&beta, kc * sizeof(double));
+    dalloc((void **)&rz, kc * sizeof(double));
+    dalloc((void **)&bnorm, kc * sizeof(double));
+    dalloc((void **)&done, kc * sizeof(int));
+    dalloc((void **)&maxres, sizeof(unsigned long long));
+    auto release = [&]() {
+        cudaStreamSynchronize(s);
+        for (void *p : tmp) cudaFree(p);
+        tmp.clear();
+    };
+    if (ce != cudaSuccess) {
+        release();
+        cudaGetLastError();
+        *fallback = true;
+        err = std::string("multigrid workspace allocation failed: ") + cudaGetErrorString(ce);
+        return DD_ENOMEM;
+    }
+
+    auto grid = [&](int64_t rows, int rb) {
+        return dim3((unsigned)((rows + rb - 1) / rb), (unsigned)((kc + kColsPerBlock - 1) / kColsPerBlock));
+    };
+    // z = V(b) on level l (x must not alias b); dot: partial sums of b.x into part0 (fine level)
+    std::function<void(int, const double *, double *, bool)> vcycle = [&](int l, const double *b, double *x,
+                                                                          bool dot) {
+        const int64_t n = H.levels[l].A.rows;
+        if (l == nl - 1) {   // coarsest level (never the fine one here: nl >= 2)
+            coarse_solve_kernel<<<dim3((unsigned)((kc + 127) / 128), (unsigned)n), 128, 0, s>>>(n, kc, ainv, b, x);
+            return;
+        }
+        const double w = H.levels[l].omega;
+        const dim3 g = grid(n, rpb[l]);
+        const int64_t nc = H.levels[l + 1].A.rows;
+        jacobi0_kernel<<<g, kColsPerBlock, 0, s>>>(n, kc, w, dinv[l], b, x, rpb[l]);
+        csr_spmm_kernel<kSpmmResidual><<<g, kColsPerBlock, 0, s>>>(n, kc, dA[l].off, dA[l].col, dA[l].val, x, b,
+                                                                    lr[l], rpb[l]);
+        csr_spmm_kernel<kSpmmSet><<<grid(nc, rpb[l + 1]), kColsPerBlock, 0, s>>>(
+            nc, kc, dR[l].off, dR[l].col, dR[l].val, lr[l], nullptr, lb[l + 1], rpb[l + 1]);
+        vcycle(l + 1, lb[l + 1], lx[l + 1], false);
+        csr_spmm_kernel<kSpmmAdd><<<g, kColsPerBlock, 0, s>>>(n, kc, dP[l].off, dP[l].col, dP[l].val, lx[l + 1],
+                                                               nullptr, x, rpb[l]);
+        csr_spmm_kernel<kSpmmResidual><<<g, kColsPerBlock, 0, s>>>(n, kc, dA[l].off, dA[l].col, dA[l].val, x, b,
+                                                                    lr[l], rpb[l]);
+        if (dot)
+            jacobi_add_kernel<true><<<g, kColsPerBlock, 0, s>>>(n, kc, w, dinv[l], lr[l], x, b, part0, rpb[l]);
+        else
+            jacobi_add_kernel<false><<<g, kColsPerBlock, 0, s>>>(n, kc, w, dinv[l], lr[l], x, nullptr, nullptr,
+                                                                  rpb[l]);
+    };
+
+    dd_status st = DD_OK;
+    int32_t iters_max = 0;
+    double res_max = 0.0;
+    const int check_every = 4;
+    const dim3 g0 = grid(m, rpb0), gc((unsigned)((kc + 31) / 32)), bc(32, 8);
+    for (int64_t c0 = 0; c0 < k && st == DD_OK; c0 += kc) {
+        const int64_t kcur = (k - c0) < kc ? (k - c0) : kc;
+        cudaMemsetAsync(X, 0, vec, s);
+        cudaMemsetAsync(R, 0, vec, s);
+        if (M.n_rb > 0)
+            scatter_rhs_kernel<<<(unsigned)((M.n_rb + 255) / 256), 256, 0, s>>>(M.n_rb, M.rb_row, M.rb_col, M.rb_val,
+                                                                                c0, kcur, kc, R);
+        if (nl == 1) {   // the whole problem is the coarsest level: one exact solve
+            coarse_solve_kernel<<<dim3((unsigned)((kc + 127) / 128), (unsigned)m), 128, 0, s>>>(m, kc, ainv, R, X);
+            pack_chunk_kernel<<<dim3((unsigned)nrb, (unsigned)((kcur + kColsPerBlock - 1) / kColsPerBlock)),
+                                kColsPerBlock, 0, s>>>(m, kcur, kc, c0, M.k_pad, M.interior, X, M.P, rpb0);
+            iters_max = std::max(iters_max, 1);
+            continue;
+        }
+        vcycle(0, R, Z, true);
+        dot_rr_kernel<<<g0, kColsPerBlock, 0, s>>>(m, kc, R, part1, rpb0);
+        amg_init_scalars_kernel<<<gc, bc, 0, s>>>(nrb, kc, part0, part1, rz, bnorm, done);
+        update_p_z_kernel<<<g0, kColsPerBlock, 0, s>>>(m, kc, beta, Z, Pd, 1, rpb0);
+        int32_t it = 0;
+        double res = 1.0;
+        for (it = 1; it <= max_iter; ++it) {
+            spmm_dot_kernel<<<g0, kColsPerBlock, 0, s>>>(m, kc, M.a_off, M.a_col, M.a_val, Pd, AP, part0, rpb0);
+            alpha_kernel<<<gc, bc, 0, s>>>(nrb, kc, part0, rz, done, alpha);
+            update_xr_plain_kernel<<<g0, kColsPerBlock, 0, s>>>(m, kc, alpha, X, R, Pd, AP, part1, rpb0);
+            vcycle(0, R, Z, true);
+            cudaMemsetAsync(maxres, 0, sizeof(unsigned long long), s);
+            beta_kernel<<<gc, bc, 0, s>>>(nrb, kc, part0, part1, bnorm, rz, done, beta, maxres);
+            update_p_z_kernel<<<g0, kColsPerBlock, 0, s>>>(m, kc, beta, Z, Pd, 0, rpb0);
+            if (it % check_every == 0 || it == max_iter) {
+                unsigned long long bits = 0;
+                cudaError_t e1 = cudaMemcpyAsync(&bits, maxres, sizeof bits, cudaMemcpyDeviceToHost, s);
+                cudaError_t e2 = cudaStreamSynchronize(s);
+                if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                    err = std::string("PCG iteration failed: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2);
+                    st = DD_ECUDA;
+                    break;
+                }
+                std::memcpy(&res, &bits, sizeof res);
+                if (res <= rtol) break;
+            }
+        }
+        if (st != DD_OK) break;
+        if (it > max_iter) it = max_iter;
+        iters_max = std::max(iters_max, it);
+        res_max = std::max(res_max, res);
+        pack_chunk_kernel<<<dim3((unsigned)nrb, (unsigned)((kcur + kColsPerBlock - 1) / kColsPerBlock)),
+                            kColsPerBlock, 0, s>>>(m, kcur, kc, c0, M.k_pad, M.interior, X, M.P, rpb0);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    release();
+    if (st != DD_OK) return st;
+    if (e != cudaSuccess) {
+        err = std::string("PCG failed: ") + cudaGetErrorString(e);
+        return DD_ECUDA;
+    }
+    if (iters_out) *iters_out = iters_max;
+    if (resid_out) *resid_out = res_max;
+    M.has_P = true;
+    if (!(res_max <= rtol)) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "PCG stopped at %d iterations with relative residual %.3e > %.3e",
+                      iters_max, res_max, rtol);
+        err = buf;
+        return DD_ENOTCONV;
+    }
+    return DD_OK;
+}
+
+bool use_multigrid(int64_t m) {
+    static int mode = -1;
+    if (mode < 0) {
+        const char *e = getenv("DD_PCG_PRECOND");
+        mode = (e && !strcmp(e, "jacobi")) ? 0 : 1;
+    }
+    return mode == 1 && m >= 256;
 }
 
 }  // namespace
@@ -240,6 +631,13 @@ dd_status run_pcg(DevMesh &M, double rtol, int32_t max_iter, cudaStream_t s, int
         if (iters_out) *iters_out = 0;
         if (resid_out) *resid_out = 0.0;
         return DD_OK;
+    }
+
+    if (use_multigrid(m)) {
+        bool fallback = false;
+        const dd_status sa = run_pcg_amg(M, rtol, max_iter, s, iters_out, resid_out, err, &fallback);
+        if (!fallback) return sa;
+        err.clear();   // the hierarchy could not be built: the diagonal preconditioner below
     }
 
     // chunk width: four FP64 [m][kc] vectors within a 24 GB workspace budget
