@@ -79,6 +79,20 @@ enum { DD_PREC_FP32 = 0, DD_PREC_BF16X3 = 1 };
  * DD_ENOMEM, DD_ECUDA. */
 dd_status dd_check_fast_log(double *spread);
 
+/* Host-only check of the Poisson-kernel solver's preconditioner (no GPU
+ * needed): builds the smoothed-aggregation multigrid hierarchy of the SPD
+ * matrix A (CSR, n rows, columns ascending, diagonal included) and solves
+ * A x = b by conjugate gradients with the same V-cycle the device solver runs,
+ * to ||b - A x|| <= rtol ||b||.
+ *   a_off [n+1], a_col [nnz], a_val [nnz]   host CSR of A
+ *   b [n] host right-hand side; x [n] host output
+ *   iters, levels   outputs: CG iterations, hierarchy depth
+ * Errors: DD_EINVAL (null or n < 1), DD_ENOTCONV (no hierarchy or no
+ * convergence within max_iter). */
+dd_status dd_multigrid_check(const int64_t *a_off, const int32_t *a_col, const double *a_val, int64_t n,
+                             const double *b, double *x, double rtol, int32_t max_iter, int32_t *iters,
+                             int32_t *levels);
+
 /* per-path status written by the tracer */
 enum {
     DD_TRACE_OK = 0,          /* reached the target                                   */

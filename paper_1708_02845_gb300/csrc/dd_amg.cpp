@@ -279,3 +279,83 @@ bool build_amg(const AmgCsr &A0, AmgHierarchy &H, std::string &err) {
     err = "multigrid setup: too many levels";
     return false;
 }
+
+// ---------------------------------------------------------------- host check
+namespace {
+
+void csr_apply(const AmgCsr &A, const std::vector<double> &x, std::vector<double> &y) {
+    y.assign(A.rows, 0.0);
+    for (int64_t i = 0; i < A.rows; ++i) {
+        double s = 0.0;
+        for (int64_t p = A.off[i]; p < A.off[i + 1]; ++p) s += A.val[p] * x[A.col[p]];
+        y[i] = s;
+    }
+}
+
+// the V-cycle of the device solver, on the host: x = V(b) on level l
+void host_vcycle(const AmgHierarchy &H, size_t l, const std::vector<double> &b, std::vector<double> &x) {
+    const AmgLevel &L = H.levels[l];
+    const int64_t n = L.A.rows;
+    x.assign(n, 0.0);
+    if (l + 1 == H.levels.size()) {
+        for (int64_t i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int64_t j = 0; j < n; ++j) s += H.coarse_inv[i * n + j] * b[j];
+            x[i] = s;
+        }
+        return;
+    }
+    for (int64_t i = 0; i < n; ++i) x[i] = L.omega * L.dinv[i] * b[i];
+    std::vector<double> t, r(n), bc, xc;
+    csr_apply(L.A, x, t);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+    csr_apply(L.R, r, bc);
+    host_vcycle(H, l + 1, bc, xc);
+    csr_apply(L.P, xc, t);
+    for (int64_t i = 0; i < n; ++i) x[i] += t[i];
+    csr_apply(L.A, x, t);
+    for (int64_t i = 0; i < n; ++i) x[i] += L.omega * L.dinv[i] * (b[i] - t[i]);
+}
+
+}  // namespace
+
+bool amg_host_solve(const AmgCsr &A, const std::vector<double> &b, std::vector<double> &x, double rtol,
+                    int32_t max_iter, int32_t *iters, int32_t *levels, std::string &err) {
+    AmgHierarchy H;
+    if (!build_amg(A, H, err)) return false;
+    *levels = (int32_t)H.levels.size();
+    const int64_t n = A.rows;
+    std::vector<double> r(b), z, p, Ap;
+    x.assign(n, 0.0);
+    double bn = 0.0;
+    for (double v : b) bn += v * v;
+    bn = std::sqrt(bn);
+    *iters = 0;
+    if (!(bn > 0.0)) return true;
+    host_vcycle(H, 0, r, z);
+    p = z;
+    double rz = 0.0;
+    for (int64_t i = 0; i < n; ++i) rz += r[i] * z[i];
+    for (int32_t it = 1; it <= max_iter; ++it) {
+        csr_apply(A, p, Ap);
+        double pAp = 0.0;
+        for (int64_t i = 0; i < n; ++i) pAp += p[i] * Ap[i];
+        const double a = rz / pAp;
+        double rr = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            x[i] += a * p[i];
+            r[i] -= a * Ap[i];
+            rr += r[i] * r[i];
+        }
+        *iters = it;
+        if (std::sqrt(rr) <= rtol * bn) return true;
+        host_vcycle(H, 0, r, z);
+        double rz2 = 0.0;
+        for (int64_t i = 0; i < n; ++i) rz2 += r[i] * z[i];
+        const double beta = rz2 / rz;
+        rz = rz2;
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    }
+    err = "host multigrid PCG did not converge";
+    return false;
+}

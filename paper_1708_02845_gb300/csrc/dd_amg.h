@@ -32,3 +32,9 @@ struct AmgHierarchy {
 // Build the hierarchy for the SPD matrix A0; false (with a message) when a
 // step fails.
 bool build_amg(const AmgCsr &A0, AmgHierarchy &H, std::string &err);
+
+// The device solver's multigrid-preconditioned CG for one right-hand side, on
+// the host (a check of the hierarchy and the V-cycle without a GPU): solves
+// A x = b to ||r|| <= rtol ||b||.  *levels: hierarchy depth.
+bool amg_host_solve(const AmgCsr &A, const std::vector<double> &b, std::vector<double> &x, double rtol,
+                    int32_t max_iter, int32_t *iters, int32_t *levels, std::string &err);

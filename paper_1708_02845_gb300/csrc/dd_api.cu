@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "dd_amg.h"
 #include "dd_internal.h"
 
 namespace {
@@ -798,6 +799,30 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
         return set_err(ctx, DD_ENOMEM, "host allocation failed");
     } catch (...) {
         return set_err(ctx, DD_EINVAL, "unexpected failure in dd_query_batch");
+    }
+}
+
+dd_status dd_multigrid_check(const int64_t *a_off, const int32_t *a_col, const double *a_val, int64_t n,
+                             const double *b, double *x, double rtol, int32_t max_iter, int32_t *iters,
+                             int32_t *levels) {
+    if (!a_off || !a_col || !a_val || !b || !x || !iters || !levels || n < 1 || max_iter < 1) return DD_EINVAL;
+    try {
+        AmgCsr A;
+        A.rows = A.cols = n;
+        A.off.assign(a_off, a_off + n + 1);
+        const int64_t nnz = A.off[n];
+        if (nnz < n || A.off[0] != 0) return DD_EINVAL;
+        A.col.assign(a_col, a_col + nnz);
+        A.val.assign(a_val, a_val + nnz);
+        for (int32_t c : A.col)
+            if (c < 0 || c >= n) return DD_EINVAL;
+        std::vector<double> bb(b, b + n), xx;
+        std::string err;
+        if (!amg_host_solve(A, bb, xx, rtol, max_iter, iters, levels, err)) return DD_ENOTCONV;
+        std::copy(xx.begin(), xx.end(), x);
+        return DD_OK;
+    } catch (...) {
+        return DD_ENOMEM;
     }
 }
 

@@ -56,6 +56,7 @@ _SIGS = {
     "dd_query_batch": (_i32, [_p, _i32, _p, _p, _p, _p, _i32, _u32, _u32, _i32, _p, _p, _p, _p]),
     "dd_tuning_table": (_i32, [ctypes.c_char_p, _i32]),
     "dd_check_fast_log": (_i32, [ctypes.POINTER(ctypes.c_double)]),
+    "dd_multigrid_check": (_i32, [_p, _p, _p, _i64, _p, _p, _f64, _i32, _p, _p]),
     "dd_server_create": (_i32, [_p, _i64, _i32, _i32, _i32, ctypes.POINTER(_p)]),
     "dd_server_submit": (_i32, [_p, _i64, _i32, _i32, _p, _i32]),
     "dd_server_poll": (_i32, [_p, _i32, _p, _p, _p]),
@@ -241,6 +242,23 @@ def dd_check_fast_log() -> float:
     if st != DD_OK:
         raise DDError(st, "dd_check_fast_log failed")
     return v.value
+
+
+def dd_multigrid_check(a_off, a_col, a_val, b, rtol: float = 1e-12, max_iter: int = 200):
+    """Host-only multigrid-preconditioned CG on the CSR matrix (no GPU).
+    Returns (x, iterations, levels)."""
+    a_off = np.ascontiguousarray(a_off, dtype=np.int64)
+    a_col = np.ascontiguousarray(a_col, dtype=np.int32)
+    a_val = np.ascontiguousarray(a_val, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = len(a_off) - 1
+    x = np.zeros(n, dtype=np.float64)
+    it, lv = ctypes.c_int32(), ctypes.c_int32()
+    st = lib.dd_multigrid_check(a_off.ctypes.data, a_col.ctypes.data, a_val.ctypes.data, n, b.ctypes.data,
+                                x.ctypes.data, float(rtol), int(max_iter), ctypes.byref(it), ctypes.byref(lv))
+    if st != DD_OK:
+        raise DDError(st, "dd_multigrid_check failed")
+    return x, it.value, lv.value
 
 
 def dd_tuning_table() -> str:
