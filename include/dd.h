@@ -197,6 +197,29 @@ dd_status dd_get_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out);
 dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
                       uint32_t f_mask, int32_t prec, float *out);
 
+/* Other f-divergences of Section VI, d_f,t(x) = sum_b P[x,b] f(P[t,b]/P[x,b]),
+ * each f taken in its form with f(1) = f'(1) = 0 (the same divergence between
+ * probability vectors, with non-negative terms):
+ *   DD_DIV_CHI2        (u - 1)^2
+ *   DD_DIV_HELLINGER   (sqrt(u) - 1)^2
+ *   DD_DIV_POWER       |1 - u|^p, param = p >= 1 (p = 1 is TV, p = 2 chi2)
+ *   DD_DIV_ALPHA       4/(1-a^2)(1 - u^((1+a)/2)) + 2/(1-a)(u - 1), param = a,
+ *                      |a| != 1 (a -> -1 tends to KL, a -> 1 to the reverse KL)
+ *   DD_DIV_KL_REVERSE  u log u: sum_b P[t,b] log(P[t,b] / P[x,b])
+ * (KL and TV themselves: dd_distance.)  Evaluated in FP32 with exact split
+ * logarithms where a log ratio enters (alpha, reverse KL), so d(t,t) = 0.
+ * Where the exact value is +inf (P[x,b] = 0 < P[t,b] on boundary rows x for
+ * chi2, p > 1, a > 1) the result is at least 1e30 or +inf; for the reverse
+ * KL, whose log argument is taken at FLT_MIN there as in dd_distance, it is
+ * finite and at least about 80.
+ *   targets  host [T] interior vertex ids
+ *   out      device or host float32 [T][n_v]
+ * Errors: DD_EINVAL (family, param, ids), DD_ESTATE (no Poisson kernel),
+ * DD_ENOMEM, DD_ECUDA. */
+enum { DD_DIV_CHI2 = 1, DD_DIV_HELLINGER = 2, DD_DIV_POWER = 3, DD_DIV_ALPHA = 4, DD_DIV_KL_REVERSE = 5 };
+dd_status dd_divergence(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T, int32_t family,
+                        double param, float *out);
+
 /* Trace gradient-descent paths from S source vertices to `target` on the
  * field of divergence f (DD_F_KL or DD_F_TV), evaluated in FP32 (Section IV).
  *   sources     host [S] vertex ids

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <cmath>
+
 #include "dd_amg.h"
 #include "dd_internal.h"
 
@@ -450,6 +452,48 @@ dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t
 dd_status dd_trace_fields(dd_ctx *ctx, int32_t mesh, const float *fields, const int32_t *targets, int32_t T,
                           const int32_t *sources, int32_t S, int32_t max_pts, float *out_xy, int32_t *out_len,
                           int32_t *out_status);
+
+dd_status dd_divergence(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T, int32_t family,
+                        double param, float *out) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    try {
+        if (!m->has_P) return set_err(ctx, DD_ESTATE, "dd_divergence before dd_poisson_kernel");
+        if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
+        if (family < DD_DIV_CHI2 || family > DD_DIV_KL_REVERSE) return set_err(ctx, DD_EINVAL, "unknown family");
+        if (family == DD_DIV_POWER && !(param >= 1.0)) return set_err(ctx, DD_EINVAL, "power family needs p >= 1");
+        if (family == DD_DIV_ALPHA && !(std::fabs(std::fabs(param) - 1.0) > 1e-6))
+            return set_err(ctx, DD_EINVAL, "alpha family needs |a| != 1");
+        if (!out) return set_err(ctx, DD_EINVAL, "out is null");
+        if ((st = check_targets(ctx, *m, targets, T, true, "targets")) != DD_OK) return st;
+        const int sp = pointer_space(ctx, out);
+        if (sp < 0) return set_err(ctx, DD_EINVAL, "out is on another device");
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        if ((st = upload(ctx, S_TARGETS, targets, (size_t)T * sizeof(int32_t))) != DD_OK) return st;
+        const size_t out_bytes = (size_t)T * m->n_v * sizeof(float);
+        float *dst = out;
+        if (sp == 0) {
+            if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
+            dst = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
+        }
+        if ((st = ensure_scratch(ctx, S_STAGE, 4 * (size_t)T * m->k_pad * sizeof(float))) != DD_OK) return st;
+        float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
+        launch_stage_targets(m->P, m->k_pad, m->k, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T,
+                             stage, ctx->stream);
+        std::string err;
+        if ((st = launch_fdiv(m->P, m->n_v, m->k_pad, stage, T, family, param, dst, ctx->stream, err)) != DD_OK)
+            return set_err(ctx, st, err);
+        CK(cudaGetLastError(), "divergence kernel launch");
+        if (sp == 0) {
+            CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy fields to host");
+            CK(cudaStreamSynchronize(ctx->stream), "divergence fields");
+        }
+        return DD_OK;
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
 
 namespace {
 

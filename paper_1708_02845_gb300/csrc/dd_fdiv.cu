@@ -1,0 +1,189 @@
+// Other f-divergence fields, Section VI: for a target t and every vertex x
+//
+//   d_f,t(x) = sum_b P[x,b] f(P[t,b] / P[x,b])
+//
+// with f in the form f(1) = f'(1) = 0 (adding c (u - 1) to f does not change
+// a divergence between probability vectors), so that every term is
+// non-negative and near the target no sum cancels:
+//
+//   chi2        (u - 1)^2                 term (P_t - P_x)^2 / P_x
+//   hellinger   (sqrt u - 1)^2            term (P_t - P_x)^2 / (sqrt P_t + sqrt P_x)^2
+//   power p     |1 - u|^p, p >= 1         term |P_t - P_x| (|P_t - P_x| / P_x)^(p-1)
+//   alpha a     4/(1-a^2)(1 - u^((1+a)/2)) + 2/(1-a)(u - 1)
+//               term P_x 2/(1-a) [expm1(L) - expm1(e L)/e], e = (1+a)/2, L = log(P_t/P_x)
+//   kl_reverse  u log u                   term P_t log(P_t / P_x)
+//
+// L is formed from exact split logarithms (exponent difference exact, mantissa
+// logs from the same table as the KL kernels), so x = t gives L = 0 and a
+// zero term.  For |L| < 1/8 the alpha bracket is summed as its series
+// sum_{n>=2} (1 - e^(n-1)) L^n / n! (six terms), which has no cancellation.
+// A term with P[x,b] = 0 < P[t,b] is +inf for chi2, p > 1, alpha > 1 and
+// kl_reverse; the kernels evaluate it with P[x,b] taken as FLT_MIN, which
+// gives a finite value of order 1e30 or an FP32 overflow to +inf (for
+// kl_reverse, P[t,b] (log P[t,b] - log FLT_MIN), as dd_distance does for KL).
+//
+// One warp per row, lanes along b, 16-byte loads of P four float4 per lane
+// ahead; the target's P, log-mantissa and exponent rows staged in shared
+// memory (the arrays of stage_targets_kernel); one target per grid row.
+#include <cfloat>
+#include <cmath>
+
+#include "dd_internal.h"
+#include "dd_splitlog.cuh"
+
+namespace {
+
+constexpr float kLn2f = 0.693147180559945309f;
+
+struct FdParams {
+    float p;         // power: p; alpha: e = (1 + a)/2
+    float lin;       // alpha: 2 / (1 - a)
+    int alpha_gt1;   // alpha: a > 1
+};
+
+// log(P_t / P_x) from the split logarithms (target side staged)
+__device__ __forceinline__ float log_ratio(float px, float lmt, float Ebt, const float *tab) {
+    float lm, Eb;
+    split_log<true>(px, tab, lm, Eb);
+    return __fmaf_rn(__fadd_rn(Ebt, -Eb), kLn2f, __fadd_rn(lmt, -lm));
+}
+
+// expm1(L) - expm1(e L) / e
+__device__ __forceinline__ float alpha_bracket(float L, float e) {
+    if (fabsf(L) < 0.125f) {
+        // sum_{n>=2} (1 - e^(n-1)) L^n / n!
+        float en = e, s = 0.0f, Ln = L, fact = 1.0f;
+#pragma unroll
+        for (int n = 2; n <= 7; ++n) {
+            Ln *= L;
+            fact *= (float)n;
+            s += (1.0f - en) * Ln / fact;
+            en *= e;
+        }
+        return s;
+    }
+    return expm1f(L) - expm1f(e * L) / e;
+}
+
+enum { kChi2 = DD_DIV_CHI2, kHell = DD_DIV_HELLINGER, kPow = DD_DIV_POWER, kAlpha = DD_DIV_ALPHA,
+       kKlRev = DD_DIV_KL_REVERSE };
+
+template <int FAM>
+__device__ __forceinline__ float fterm(float px, float pt, float lmt, float Ebt, const FdParams &q, const float *tab) {
+    if (FAM == kChi2) {
+        const float d = pt - px;
+        return d * d / fmaxf(px, FLT_MIN);
+    } else if (FAM == kHell) {
+        const float d = pt - px, s = sqrtf(pt) + sqrtf(px);
+        if (s == 0.0f) return 0.0f;
+        const float r = d / s;
+        return r * r;
+    } else if (FAM == kPow) {
+        const float ad = fabsf(pt - px);
+        if (ad == 0.0f) return 0.0f;
+        return ad * powf(ad / fmaxf(px, FLT_MIN), q.p - 1.0f);
+    } else if (FAM == kAlpha) {
+        if (px == 0.0f) return pt == 0.0f ? 0.0f : (q.alpha_gt1 ? INFINITY : q.lin * pt);
+        return px * q.lin * alpha_bracket(log_ratio(px, lmt, Ebt, tab), q.p);
+    } else {   // kKlRev
+        if (pt == 0.0f) return 0.0f;
+        return pt * log_ratio(px, lmt, Ebt, tab);
+    }
+}
+
+template <int FAM>
+__global__ void __launch_bounds__(256) fdiv_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
+                                                   const float *__restrict__ sP, const float *__restrict__ sL,
+                                                   const float *__restrict__ sE, FdParams q, float *__restrict__ out) {
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ float tab[2 * kLogTab];
+    float *tP = fsm, *tL = fsm + k_pad, *tE = fsm + 2 * k_pad;
+    const int a = blockIdx.y;
+    for (int64_t b = threadIdx.x; b < k_pad; b += blockDim.x) {
+        tP[b] = sP[(int64_t)a * k_pad + b];
+        tL[b] = sL[(int64_t)a * k_pad + b];
+        tE[b] = sE[(int64_t)a * k_pad + b];
+    }
+    build_log_table(tab);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nvec = (int)(k_pad >> 2);
+    for (int64_t x = warp; x < n_v; x += nwarps) {
+        const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int c0 = 0; c0 < nvec; c0 += 128) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u * 32 + lane;
+                v[u] = c < nvec ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u * 32 + lane;
+                if (c >= nvec) break;
+                const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
+                const float4 l4 = reinterpret_cast<const float4 *>(tL)[c];
+                const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
+                s0 += fterm<FAM>(v[u].x, p4.x, l4.x, e4.x, q, tab);
+                s1 += fterm<FAM>(v[u].y, p4.y, l4.y, e4.y, q, tab);
+                s0 += fterm<FAM>(v[u].z, p4.z, l4.z, e4.z, q, tab);
+                s1 += fterm<FAM>(v[u].w, p4.w, l4.w, e4.w, q, tab);
+            }
+        }
+        float s = s0 + s1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[(int64_t)a * n_v + x] = s;
+    }
+}
+
+}  // namespace
+
+dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, int32_t family,
+                      double param, float *out, cudaStream_t s, std::string &err) {
+    const float *sP = reinterpret_cast<const float *>(stage);
+    const float *sL = sP + (int64_t)T * k_pad;
+    const float *sE = sL + (int64_t)T * k_pad;
+    const size_t smem = 3 * (size_t)k_pad * sizeof(float);
+    if (smem > 200 * 1024) {
+        err = "divergence fields: k_pad too large for the staged target row";
+        return DD_EINVAL;
+    }
+    FdParams q;
+    q.p = (float)param;
+    q.lin = 0.0f;
+    q.alpha_gt1 = 0;
+    if (family == DD_DIV_ALPHA) {
+        q.p = (float)((1.0 + param) / 2.0);
+        q.lin = (float)(2.0 / (1.0 - param));
+        q.alpha_gt1 = param > 1.0;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+        if (per_sm < 1) per_sm = 1;
+        int64_t gx = (int64_t)sms * per_sm / (T > 0 ? T : 1);
+        const int64_t rows_blocks = (n_v + 7) / 8;
+        if (gx < 1) gx = 1;
+        if (gx > rows_blocks) gx = rows_blocks;
+        kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, q, out);
+    };
+    switch (family) {
+        case DD_DIV_CHI2: go(fdiv_kernel<kChi2>); break;
+        case DD_DIV_HELLINGER: go(fdiv_kernel<kHell>); break;
+        case DD_DIV_POWER: go(fdiv_kernel<kPow>); break;
+        case DD_DIV_ALPHA: go(fdiv_kernel<kAlpha>); break;
+        case DD_DIV_KL_REVERSE: go(fdiv_kernel<kKlRev>); break;
+        default:
+            err = "unknown divergence family";
+            return DD_EINVAL;
+    }
+    return DD_OK;
+}

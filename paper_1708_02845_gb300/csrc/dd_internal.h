@@ -106,6 +106,9 @@ void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, con
 void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, int32_t n_items, int32_t *d_counter,
                          cudaStream_t s);
 std::string tuning_table();
+// other f-divergence fields [T][n_v] from staged targets (stage_targets_kernel's arrays)
+dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, int32_t family,
+                      double param, float *out, cudaStream_t s, std::string &err);
 // spread (max - min) of the hardware mantissa log's error over [1, 2), in base-2 units
 dd_status fast_log_spread(double *spread, std::string &err);
 

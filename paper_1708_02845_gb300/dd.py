@@ -18,6 +18,7 @@ DD_OK, DD_EINVAL, DD_ENOMEM, DD_ECUDA, DD_ESTATE, DD_ENOTCONV, DD_ETIMEOUT, DD_E
 DD_F_KL, DD_F_TV = 1, 2
 DD_PREC_FP32, DD_PREC_BF16X3 = 0, 1
 DD_FAST_LOG_SPREAD, DD_EXACT_BELOW = 5.0e-7, 0.05
+DD_DIV_CHI2, DD_DIV_HELLINGER, DD_DIV_POWER, DD_DIV_ALPHA, DD_DIV_KL_REVERSE = 1, 2, 3, 4, 5
 DD_TRACE_OK, DD_TRACE_STUCK, DD_TRACE_STEP_LIMIT, DD_TRACE_TRUNCATED = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "DD_OK", -1: "DD_EINVAL", -2: "DD_ENOMEM", -3: "DD_ECUDA", -4: "DD_ESTATE",
@@ -49,6 +50,7 @@ _SIGS = {
     "dd_set_poisson_kernel": (_i32, [_p, _i32, _p]),
     "dd_get_poisson_kernel": (_i32, [_p, _i32, _p]),
     "dd_distance": (_i32, [_p, _i32, _p, _i32, _u32, _i32, _p]),
+    "dd_divergence": (_i32, [_p, _i32, _p, _i32, _i32, _f64, _p]),
     "dd_trace": (_i32, [_p, _i32, _i32, _u32, _p, _i32, _i32, _p, _p, _p]),
     "dd_trace_fields": (_i32, [_p, _i32, _p, _p, _i32, _p, _i32, _i32, _p, _p, _p]),
     "dd_query": (_i32, [_p, _i32, _p, _i32, _p, _i32, _u32, _i32, _u32, _i32, _p, _p, _p, _p]),
@@ -191,6 +193,13 @@ def dd_get_poisson_kernel(ctx, mesh: int, out):
 def dd_distance(ctx, mesh: int, targets, f_mask: int, prec: int, out):
     t = _host_i32(targets)
     _check(ctx, lib.dd_distance(ctx, mesh, ptr(t), len(t), f_mask, prec, ptr(out)))
+    return out
+
+
+def dd_divergence(ctx, mesh: int, targets, family: int, param: float, out):
+    """Other f-divergence fields (DD_DIV_*), out [T][n_v] on the device or host."""
+    t = _host_i32(targets)
+    _check(ctx, lib.dd_divergence(ctx, mesh, ptr(t), len(t), int(family), float(param), ptr(out)))
     return out
 
 
