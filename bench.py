@@ -338,6 +338,20 @@ def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10):
                 "peak": peak_bf16, "unit": "TFLOP/s", "frac": round(tf_iss / peak_bf16, 4), "peak_source": pk_kind,
                 "ms": round(g_ms, 3), "kl_fields_per_s": round(T_big / (g_ms / 1e3), 1),
                 "fp32_path_ms": round(f_ms, 3), "speedup_vs_fp32_path": round(f_ms / g_ms, 2), "traffic": None}
+    # other f-divergences (Section VI): one target per call, one pass over P each
+    out_f = torch.empty((1, n_v), dtype=torch.float32, device=dev)
+    fams = [("chi2", dd.DD_DIV_CHI2, 0.0), ("hellinger", dd.DD_DIV_HELLINGER, 0.0), ("power2.5", dd.DD_DIV_POWER, 2.5),
+            ("alpha0.5", dd.DD_DIV_ALPHA, 0.5), ("kl_reverse", dd.DD_DIV_KL_REVERSE, 0.0)]
+    fdiv_sec = {"workload": stream_sec["workload"], "kernel": "fdiv_kernel (+ stage_targets_kernel)", "bound": "hbm",
+                "unit": "GB/s", "peak": pk.get("hbm_gbs"), "peak_source": pk_kind, "families": {}}
+    for name, fam, prm in fams:
+        dd.dd_divergence(ctx, mid, [tl[0]], fam, prm, out_f)
+        it2 = iter(tl * 4)
+        ms_f = timed(lambda: dd.dd_divergence(ctx, mid, [next(it2)], fam, prm, out_f), reps)
+        gbs = (4.0 * n_v * k_pad + 4.0 * n_v) / (ms_f / 1e3) / 1e9
+        fdiv_sec["families"][name] = {"ms": round(ms_f, 4), "achieved": round(gbs, 1),
+                                      "frac": round(gbs / pk.get("hbm_gbs", 6672.5), 4)}
+    stream_sec["other_f_divergences"] = fdiv_sec
     dd.dd_unload_mesh(ctx, mid)
     return stream_sec, gemm_sec
 
