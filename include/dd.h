@@ -226,7 +226,9 @@ dd_status dd_divergence(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32
  *   max_pts     capacity of each polyline in points (>= 2)
  *   out_xy      device or host float32 [S][max_pts][2]; path s occupies the
  *               first out_len[s] points, starting at the source vertex and,
- *               when the status is DD_TRACE_OK, ending at the target vertex
+ *               when the status is DD_TRACE_OK, ending at the target vertex;
+ *               the points past out_len[s] are unspecified (into host memory
+ *               only the defined prefixes are copied)
  *   out_len     device or host int32 [S]
  *   out_status  device or host int32 [S], DD_TRACE_* codes
  * Errors: DD_EINVAL, DD_ESTATE, DD_ENOMEM, DD_ECUDA. */

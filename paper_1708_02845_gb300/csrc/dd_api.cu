@@ -528,11 +528,26 @@ dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32
     CK(cudaGetLastError(), "trace kernel launch");
     bool host = false;
     if (sx == 0) {
-        CK(cudaMemcpyAsync(out_xy, dxy, n * max_pts * sizeof(float2), cudaMemcpyDeviceToHost, ctx->stream),
-           "copy paths");
+        // Only each path's prefix of len points is defined: copy, per chunk of
+        // paths, the rows up to the chunk's longest path (one strided copy
+        // each) instead of all max_pts points of every path.
+        std::vector<int32_t> lens(n);
+        int32_t *hl = sl == 0 ? out_len : lens.data();
+        CK(cudaMemcpyAsync(hl, dlen, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "copy lengths");
+        CK(cudaStreamSynchronize(ctx->stream), "path lengths");
+        const size_t chunk = 512, pitch = (size_t)max_pts * sizeof(float2);
+        for (size_t s0 = 0; s0 < n; s0 += chunk) {
+            const size_t s1 = std::min(n, s0 + chunk);
+            int32_t L = 0;
+            for (size_t i = s0; i < s1; ++i) L = std::max(L, std::min(std::max(hl[i], 0), max_pts));
+            if (L == 0) continue;
+            CK(cudaMemcpy2DAsync(reinterpret_cast<char *>(out_xy) + s0 * pitch, pitch,
+                                 reinterpret_cast<const char *>(dxy) + s0 * pitch, pitch, (size_t)L * sizeof(float2),
+                                 s1 - s0, cudaMemcpyDeviceToHost, ctx->stream),
+               "copy paths");
+        }
         host = true;
-    }
-    if (sl == 0) {
+    } else if (sl == 0) {
         CK(cudaMemcpyAsync(out_len, dlen, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "copy lengths");
         host = true;
     }
