@@ -220,6 +220,28 @@ enum { DD_DIV_CHI2 = 1, DD_DIV_HELLINGER = 2, DD_DIV_POWER = 3, DD_DIV_ALPHA = 4
 dd_status dd_divergence(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T, int32_t family,
                         double param, float *out);
 
+/* Spurious local minima (Section V, "Low resolution discretizations"): for
+ * each of T fields, the interior vertices v other than the target with no
+ * mesh neighbour of smaller value (f[v] <= f[u] for every neighbour u), where
+ * gradient descent can stop.
+ *   fields   device float32 [T][n_v] (e.g. dd_distance output)
+ *   targets  host [T] vertex ids
+ *   counts   host int32 [T]: number of such vertices per field
+ *   flags    NULL, or device or host uint8 [T][n_v]: 1 at those vertices
+ * Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA. */
+dd_status dd_local_minima(dd_ctx *ctx, int32_t mesh, const float *fields, const int32_t *targets, int32_t T,
+                          int32_t *counts, uint8_t *flags);
+
+/* Edge-following paths (Section IV, the simpler of the two tracers): from
+ * each source, move to the neighbour of smallest value among those below the
+ * current vertex (ties to the lowest id) until the target (DD_TRACE_OK) or a
+ * vertex with no lower neighbour (DD_TRACE_STUCK); DD_TRACE_STEP_LIMIT after
+ * n_v moves.  Arguments and outputs as dd_trace_fields (paths are vertex
+ * positions). */
+dd_status dd_trace_edges(dd_ctx *ctx, int32_t mesh, const float *fields, const int32_t *targets, int32_t T,
+                         const int32_t *sources, int32_t S, int32_t max_pts, float *out_xy, int32_t *out_len,
+                         int32_t *out_status);
+
 /* Trace gradient-descent paths from S source vertices to `target` on the
  * field of divergence f (DD_F_KL or DD_F_TV), evaluated in FP32 (Section IV).
  *   sources     host [S] vertex ids

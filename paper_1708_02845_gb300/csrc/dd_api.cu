@@ -331,6 +331,7 @@ dd_status dd_load_mesh(dd_ctx *ctx, const double *xy, int64_t n_v, const int32_t
         if ((st = dev_copy(ctx, m, &m.rb_val, h.rb_val.data(), h.rb_val.size())) != DD_OK) return undo(st);
         m.is_boundary.assign(h.n_v, 0);
         for (int32_t v : h.B) m.is_boundary[v] = 1;
+        if ((st = dev_copy(ctx, m, &m.isb, m.is_boundary.data(), m.is_boundary.size())) != DD_OK) return undo(st);
         slot.live = true;
         ctx->meshes.push_back(slot);
         *mesh_id = (int32_t)ctx->meshes.size() - 1;
@@ -500,7 +501,7 @@ namespace {
 // paths of T x S (target, source) pairs on device fields [T][n_v]; ids already checked
 dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32_t *targets, int32_t T,
                      const int32_t *sources, int32_t S, int32_t max_pts, float *out_xy, int32_t *out_len,
-                     int32_t *out_status, bool targets_uploaded) {
+                     int32_t *out_status, bool targets_uploaded, bool edges = false) {
     dd_status st;
     if (!targets_uploaded && (st = upload(ctx, S_TARGETS, targets, (size_t)T * sizeof(int32_t))) != DD_OK) return st;
     if ((st = upload(ctx, S_SOURCES, sources, (size_t)T * S * sizeof(int32_t))) != DD_OK) return st;
@@ -521,10 +522,17 @@ dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32
         if ((st = ensure_scratch(ctx, S_STATUS, n * sizeof(int32_t))) != DD_OK) return st;
         dst = reinterpret_cast<int32_t *>(ctx->scratch[S_STATUS]);
     }
-    if ((st = ensure_scratch(ctx, S_GRAD, trace_scratch_bytes(m, T, trace_dense_decisions(S)))) != DD_OK) return st;
-    launch_trace(m, d_fields, m.n_v, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
-                 reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), T, S, max_pts, dxy, dlen, dst,
-                 ctx->scratch[S_GRAD], ctx->stream);
+    if (edges) {
+        launch_edge_paths(m, d_fields, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
+                          reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), T, S, max_pts, dxy, dlen, dst,
+                          ctx->stream);
+    } else {
+        if ((st = ensure_scratch(ctx, S_GRAD, trace_scratch_bytes(m, T, trace_dense_decisions(S)))) != DD_OK)
+            return st;
+        launch_trace(m, d_fields, m.n_v, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
+                     reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), T, S, max_pts, dxy, dlen, dst,
+                     ctx->scratch[S_GRAD], ctx->stream);
+    }
     CK(cudaGetLastError(), "trace kernel launch");
     bool host = false;
     if (sx == 0) {
@@ -587,6 +595,62 @@ dd_status dd_trace_fields(dd_ctx *ctx, int32_t mesh, const float *fields, const 
         if ((st = check_targets(ctx, *m, sources, (int64_t)T * S, false, "sources")) != DD_OK) return st;
         if ((st = select_device(ctx)) != DD_OK) return st;
         return trace_into(ctx, *m, fields, targets, T, sources, S, max_pts, out_xy, out_len, out_status, false);
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
+dd_status dd_trace_edges(dd_ctx *ctx, int32_t mesh, const float *fields, const int32_t *targets, int32_t T,
+                         const int32_t *sources, int32_t S, int32_t max_pts, float *out_xy, int32_t *out_len,
+                         int32_t *out_status) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    try {
+        if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
+        if ((st = check_path_args(ctx, S, max_pts, out_xy, out_len, out_status)) != DD_OK) return st;
+        if (!fields || pointer_space(ctx, fields) != 1)
+            return set_err(ctx, DD_EINVAL, "fields must be device memory of the context's device");
+        if ((st = check_targets(ctx, *m, targets, T, false, "targets")) != DD_OK) return st;
+        if ((st = check_targets(ctx, *m, sources, (int64_t)T * S, false, "sources")) != DD_OK) return st;
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        return trace_into(ctx, *m, fields, targets, T, sources, S, max_pts, out_xy, out_len, out_status, false, true);
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
+dd_status dd_local_minima(dd_ctx *ctx, int32_t mesh, const float *fields, const int32_t *targets, int32_t T,
+                          int32_t *counts, uint8_t *flags) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    try {
+        if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
+        if (!counts) return set_err(ctx, DD_EINVAL, "counts is null");
+        if (!fields || pointer_space(ctx, fields) != 1)
+            return set_err(ctx, DD_EINVAL, "fields must be device memory of the context's device");
+        const int sf = flags ? pointer_space(ctx, flags) : 1;
+        if (sf < 0) return set_err(ctx, DD_EINVAL, "flags on another device");
+        if ((st = check_targets(ctx, *m, targets, T, false, "targets")) != DD_OK) return st;
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        if ((st = upload(ctx, S_TARGETS, targets, (size_t)T * sizeof(int32_t))) != DD_OK) return st;
+        // counts and (for host flags) the flags in one scratch block
+        const size_t cbytes = ((size_t)T * sizeof(int32_t) + 255) / 256 * 256;
+        const size_t fbytes = (flags && sf == 0) ? (size_t)T * m->n_v : 0;
+        if ((st = ensure_scratch(ctx, S_LEN, cbytes + fbytes)) != DD_OK) return st;
+        int32_t *dcounts = reinterpret_cast<int32_t *>(ctx->scratch[S_LEN]);
+        uint8_t *dflags = flags && sf == 0 ? reinterpret_cast<uint8_t *>(ctx->scratch[S_LEN]) + cbytes : flags;
+        CK(cudaMemsetAsync(dcounts, 0, (size_t)T * sizeof(int32_t), ctx->stream), "clear counts");
+        launch_local_minima(*m, fields, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, dcounts, dflags,
+                            ctx->stream);
+        CK(cudaGetLastError(), "census kernel launch");
+        CK(cudaMemcpyAsync(counts, dcounts, (size_t)T * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
+           "copy counts");
+        if (fbytes)
+            CK(cudaMemcpyAsync(flags, dflags, fbytes, cudaMemcpyDeviceToHost, ctx->stream), "copy flags");
+        CK(cudaStreamSynchronize(ctx->stream), "census");
+        return DD_OK;
     } catch (...) {
         return set_err(ctx, DD_ENOMEM, "host allocation failed");
     }

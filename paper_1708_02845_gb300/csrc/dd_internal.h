@@ -51,6 +51,7 @@ struct DevMesh {
     int32_t *vt_off = nullptr, *vt = nullptr;
     int32_t *vn_off = nullptr, *vn = nullptr;
     int32_t *interior = nullptr;   // [m]
+    uint8_t *isb = nullptr;        // [n_v] 1 on boundary vertices
     int32_t *boundary = nullptr;   // [k]
     int64_t *a_off = nullptr;
     int32_t *a_col = nullptr;
@@ -106,6 +107,13 @@ void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, con
 void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, int32_t n_items, int32_t *d_counter,
                          cudaStream_t s);
 std::string tuning_table();
+// spurious local minima of T fields [T][n_v] (counts host [T], flags optional [T][n_v])
+void launch_local_minima(const DevMesh &m, const float *fields, const int32_t *targets, int32_t T, int32_t *counts,
+                         uint8_t *flags, cudaStream_t s);
+// edge-following paths (T*S, sources [T][S]) on device fields [T][n_v]
+void launch_edge_paths(const DevMesh &m, const float *fields, const int32_t *targets, const int32_t *sources, int32_t T,
+                       int32_t S, int32_t max_pts, float2 *out_xy, int32_t *out_len, int32_t *out_status,
+                       cudaStream_t s);
 // other f-divergence fields [T][n_v] from staged targets (stage_targets_kernel's arrays)
 dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, int32_t family,
                       double param, float *out, cudaStream_t s, std::string &err);

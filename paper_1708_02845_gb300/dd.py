@@ -51,6 +51,8 @@ _SIGS = {
     "dd_get_poisson_kernel": (_i32, [_p, _i32, _p]),
     "dd_distance": (_i32, [_p, _i32, _p, _i32, _u32, _i32, _p]),
     "dd_divergence": (_i32, [_p, _i32, _p, _i32, _i32, _f64, _p]),
+    "dd_local_minima": (_i32, [_p, _i32, _p, _p, _i32, _p, _p]),
+    "dd_trace_edges": (_i32, [_p, _i32, _p, _p, _i32, _p, _i32, _i32, _p, _p, _p]),
     "dd_trace": (_i32, [_p, _i32, _i32, _u32, _p, _i32, _i32, _p, _p, _p]),
     "dd_trace_fields": (_i32, [_p, _i32, _p, _p, _i32, _p, _i32, _i32, _p, _p, _p]),
     "dd_query": (_i32, [_p, _i32, _p, _i32, _p, _i32, _u32, _i32, _u32, _i32, _p, _p, _p, _p]),
@@ -201,6 +203,22 @@ def dd_divergence(ctx, mesh: int, targets, family: int, param: float, out):
     t = _host_i32(targets)
     _check(ctx, lib.dd_divergence(ctx, mesh, ptr(t), len(t), int(family), float(param), ptr(out)))
     return out
+
+
+def dd_local_minima(ctx, mesh: int, fields, targets, flags=None):
+    """Spurious local minima of device fields [T][n_v]; returns counts [T]."""
+    t = _host_i32(targets)
+    counts = np.zeros(len(t), dtype=np.int32)
+    _check(ctx, lib.dd_local_minima(ctx, mesh, ptr(fields), ptr(t), len(t), counts.ctypes.data,
+                                    ptr(flags) if flags is not None else None))
+    return counts
+
+
+def dd_trace_edges(ctx, mesh: int, fields, targets, sources, max_pts: int, out_xy, out_len, out_status):
+    t = _host_i32(targets)
+    s = np.ascontiguousarray(_host_i32(sources).reshape(len(t), -1))
+    _check(ctx, lib.dd_trace_edges(ctx, mesh, ptr(fields), ptr(t), len(t), ptr(s), s.shape[1], max_pts,
+                                   ptr(out_xy), ptr(out_len), ptr(out_status)))
 
 
 def dd_trace(ctx, mesh: int, target: int, f: int, sources, max_pts: int, out_xy, out_len, out_status):
