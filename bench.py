@@ -128,7 +128,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     ctx = dd.dd_create(local_rank, stream.cuda_stream)
-    if args.section in ("grid450", "batch", "serve"):
+    if args.section in ("grid450", "batch", "serve", "census"):
         pk, pk_kind = peaks()
         flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev)
         if args.section == "grid450":
@@ -136,6 +136,8 @@ def run_ours(args, rank, world, local_rank):
             out = {"metric": "grid450 sections only", "stream": st_sec, "gemm": gm_sec}
         elif args.section == "batch":
             out = {"metric": "batch64 section only", "batch": batch_section(dd, ctx, dev, stream, flush, args)}
+        elif args.section == "census":
+            out = {"metric": "census section only", "census": census_section(dd, ctx, dev)}
         else:
             out = {"metric": "serving section only", "serve": serve_section(dd, ctx, args, n_domains=8, seconds=10.0)}
         dd.dd_destroy(ctx)
@@ -275,6 +277,7 @@ def run_ours(args, rank, world, local_rank):
         line["stream"], line["gemm"] = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
         line["batch"] = batch_section(dd, ctx, dev, stream, flush, args)
         line["serve"] = serve_section(dd, ctx, args, n_domains=5, seconds=3.0)
+        line["census"] = census_section(dd, ctx, dev)
     dd.dd_destroy(ctx)
     return line
 
@@ -422,6 +425,55 @@ def batch_section(dd, ctx, dev, stream, flush, args, S: int = 64, max_pts: int =
             "preproc": {"pcg_iters_total": pcg_iters, "seconds": round(pre, 2)}, "launches_per_batch": 5}
 
 
+def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1, 2, 3, 4),
+                   max_targets: int = 1024):
+    """Spurious-local-minimum census (Section V): on convex-holes Delaunay
+    meshes of growing resolution (the same four domains at every size), the
+    share of targets whose TV field, KL field and target-weighted KL field
+    (the reverse direction, Sum_b P[t,b] log(P[t,b]/P[x,b])) have an interior
+    vertex other than the target with no lower neighbour.  All interior
+    targets up to max_targets, else max_targets spread evenly over them.
+    Everything runs through the library: the FP64 kernel solve, the FP32
+    fields, the minimum test."""
+    import torch
+    from synthetic.meshes import convex_holes
+    rows = []
+    t0 = time.perf_counter()
+    for n_goal in sizes:
+        agg = {"n_goal": n_goal, "meshes": 0, "n_v": [], "k": [], "targets": 0,
+               "tv": [0, 0], "kl": [0, 0], "kl_target_weighted": [0, 0]}
+        for seed in seeds:
+            mesh = convex_holes(n_goal, seed=seed)
+            idx, off = mesh.loop_arrays()
+            mid = dd.dd_load_mesh(ctx, mesh.xy, mesh.tri, idx, off)
+            dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+            interior = np.nonzero(~mesh.boundary_flags())[0]
+            if len(interior) > max_targets:
+                interior = interior[np.linspace(0, len(interior) - 1, max_targets).astype(np.int64)]
+            targets = interior.astype(np.int32)
+            T = len(targets)
+            fields = torch.empty((2, T, mesh.n_v), dtype=torch.float32, device=dev)
+            dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, fields)
+            rev = torch.empty((T, mesh.n_v), dtype=torch.float32, device=dev)
+            dd.dd_divergence(ctx, mid, targets, dd.DD_DIV_KL_REVERSE, 0.0, rev)
+            for name, f in (("kl", fields[0]), ("tv", fields[1]), ("kl_target_weighted", rev)):
+                c = dd.dd_local_minima(ctx, mid, f.contiguous(), targets, None)
+                agg[name][0] += int(np.count_nonzero(c))
+                agg[name][1] += int(c.sum())
+            agg["meshes"] += 1
+            agg["n_v"].append(mesh.n_v)
+            agg["k"].append(dd.dd_mesh_info(ctx, mid)["k"])
+            agg["targets"] += T
+            dd.dd_unload_mesh(ctx, mid)
+        for name in ("tv", "kl", "kl_target_weighted"):
+            agg[name] = {"targets_with_minima": agg[name][0], "minima": agg[name][1],
+                         "share": round(agg[name][0] / agg["targets"], 4)}
+        rows.append(agg)
+    return {"workload": "convex_holes(n, seed 1..4): unit disk minus 4 convex polygons, Delaunay; "
+                        "all interior targets up to %d per mesh" % max_targets,
+            "rows": rows, "seconds": round(time.perf_counter() - t0, 2)}
+
+
 def serve_section(dd, ctx, args, n_domains: int, seconds: float, rate: float = 2000.0, max_pts: int = 2048):
     """Served (continuous batching) vs plain per-query form on the serving workload.
 
@@ -559,8 +611,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", dest="stream", action="store_false",
                     help="skip the grid450 measurements (single-target HBM stream, BF16 tensor-core KL)")
-    ap.add_argument("--section", choices=["all", "step", "grid450", "batch", "serve"], default="all",
-                    help="step: only the grid140 query step; grid450 / batch: only that measurement")
+    ap.add_argument("--section", choices=["all", "step", "grid450", "batch", "serve", "census"], default="all",
+                    help="step: only the grid140 query step; grid450 / batch / serve / census: only that part")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -596,7 +648,7 @@ def main():
         dist.init_process_group("nccl")
     line = run_ours(args, rank, world, local_rank)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1 and args.section != "grid450":
+        if not args.no_cpu_baseline and world == 1 and args.section in ("all", "step"):
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
     if world > 1:

@@ -11,6 +11,12 @@ domains are not available, so two seeded families stand in for them:
 * ``grid_obstacles``: the unit square cut into N x N cells of side h = 1/N,
   each cell split on its (i, j) -> (i+1, j+1) diagonal, with axis-aligned
   rectangular blocks of whole cells removed as obstacles (holes).
+* ``convex_holes``: the unit disk minus a few convex regular polygons, meshed
+  as the Delaunay triangulation of a jittered hexagonal point set plus points
+  spaced along every boundary loop (a stand-in for the paper's "Convex Holes"
+  domain meshed at low resolution, n = 175, Section V).  Unlike the grid, no
+  edge weight is exactly zero, and the Delaunay property keeps every interior
+  edge weight non-negative.
 
 Every mesh is returned with counter-clockwise triangles and its boundary loops:
 the outer loop counter-clockwise, one clockwise loop per obstacle (the domain
@@ -168,3 +174,123 @@ def snap_to_vertex(xy: np.ndarray, p) -> int:
     """Nearest vertex to point p; ties go to the lowest vertex id."""
     d2 = (xy[:, 0] - p[0]) ** 2 + (xy[:, 1] - p[1]) ** 2
     return int(np.argmin(d2))
+
+
+def _polygon_contains(poly: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Points strictly inside a counter-clockwise convex polygon."""
+    inside = np.ones(len(pts), dtype=bool)
+    for a in range(len(poly)):
+        p0, p1 = poly[a], poly[(a + 1) % len(poly)]
+        e = p1 - p0
+        inside &= e[0] * (pts[:, 1] - p0[1]) - e[1] * (pts[:, 0] - p0[0]) > 0.0
+    return inside
+
+
+def _polygon_distance(poly: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Distance from each point to the polygon's boundary."""
+    d = np.full(len(pts), np.inf)
+    for a in range(len(poly)):
+        p0, p1 = poly[a], poly[(a + 1) % len(poly)]
+        e = p1 - p0
+        s = np.clip(((pts - p0) @ e) / (e @ e), 0.0, 1.0)
+        d = np.minimum(d, np.linalg.norm(pts - p0 - s[:, None] * e, axis=1))
+    return d
+
+
+def convex_holes(n_goal: int = 175, n_holes: int = 4, seed: int = 1) -> Mesh:
+    """Unit disk minus convex polygonal holes, Delaunay-meshed with about n_goal vertices.
+
+    Spacing h is chosen so that the lattice points (free area over the
+    hexagonal cell area sqrt(3)/2 h^2) plus the boundary points (perimeter
+    over h) come to about n_goal vertices.  Holes are
+    regular 3- to 5-gons of circumradius 0.08..0.18, kept 0.1 from the outer
+    circle and 0.12 from each other; they are drawn before h is used, so one
+    seed gives the same domain at every resolution.  Outer-circle points are spaced at most h apart (along the
+    arc); every hole edge is cut into pieces of length <= h.  Lattice points are jittered by up to
+    0.2 h and dropped within 0.6 h of any boundary, so that the diametral
+    circle of every boundary segment is empty and each boundary segment is a
+    Delaunay edge (checked).  Triangles whose centroid falls in a hole are
+    removed.  Needs scipy (Qhull) for the triangulation.
+    """
+    from scipy.spatial import Delaunay
+
+    rng = SplitMix64(seed)
+    # n_goal ~ A / (sqrt(3)/2 h^2) + perimeter / h with A ~ 0.8 pi and a
+    # perimeter ~ 2 pi + 2.5 (circle plus holes): solve the quadratic for h
+    c2 = math.sqrt(3.0) / 2.0 * n_goal
+    per, area = 2.0 * math.pi + 2.5, 0.8 * math.pi
+    h = (per + math.sqrt(per * per + 4.0 * c2 * area)) / (2.0 * c2)
+    holes = []
+    tries = 0
+    while len(holes) < n_holes:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place holes")
+        r = 0.6 * math.sqrt(rng.uniform())
+        th = 2.0 * math.pi * rng.uniform()
+        c = (r * math.cos(th), r * math.sin(th))
+        rad = 0.08 + 0.10 * rng.uniform()
+        sides = rng.randint(3, 5)
+        rot = 2.0 * math.pi * rng.uniform()
+        if math.hypot(*c) + rad > 0.9:
+            continue
+        if any(math.hypot(c[0] - d[0], c[1] - d[1]) < rad + e + 0.12 for d, e, _ in holes):
+            continue
+        poly = np.array([(c[0] + rad * math.cos(rot + 2.0 * math.pi * i / sides),
+                          c[1] + rad * math.sin(rot + 2.0 * math.pi * i / sides)) for i in range(sides)])
+        holes.append((c, rad, poly))
+
+    pts = []
+    loops = []
+
+    def add_loop(loop_pts, reverse):
+        ids = list(range(len(pts), len(pts) + len(loop_pts)))
+        pts.extend(loop_pts)
+        if reverse:          # a hole is walked clockwise: the domain on the left
+            ids = ids[:1] + ids[1:][::-1]
+        loops.append(np.asarray(ids, dtype=np.int32))
+
+    # the outer circle: points on the circle itself (a point on a chord would
+    # lie on the convex hull's edge and drop out of the triangulation)
+    n_out = max(8, int(math.ceil(2.0 * math.pi / h)))
+    add_loop([np.array((math.cos(2.0 * math.pi * i / n_out), math.sin(2.0 * math.pi * i / n_out)))
+              for i in range(n_out)], False)
+    for _, _, poly in holes:
+        walk = []
+        for a in range(len(poly)):
+            p0, p1 = poly[a], poly[(a + 1) % len(poly)]
+            pieces = max(1, int(math.ceil(np.linalg.norm(p1 - p0) / h)))
+            walk.extend(p0 + (p1 - p0) * (s / pieces) for s in range(pieces))
+        add_loop(walk, True)
+
+    dy = h * math.sqrt(3.0) / 2.0
+    rows = int(math.ceil(1.0 / dy)) + 1
+    cols = int(math.ceil(1.0 / h)) + 1
+    lattice = []
+    for j in range(-rows, rows + 1):
+        for i in range(-cols, cols + 1):
+            jx = (2.0 * rng.uniform() - 1.0) * 0.2 * h
+            jy = (2.0 * rng.uniform() - 1.0) * 0.2 * h
+            lattice.append((i * h + (0.5 * h if j & 1 else 0.0) + jx, j * dy + jy))
+    lattice = np.asarray(lattice)
+    keep = np.hypot(lattice[:, 0], lattice[:, 1]) < 1.0 - 0.6 * h
+    for _, _, poly in holes:
+        keep &= ~_polygon_contains(poly, lattice) & (_polygon_distance(poly, lattice) >= 0.6 * h)
+    xy = np.concatenate([np.asarray(pts), lattice[keep]])
+
+    tri = Delaunay(xy).simplices.astype(np.int32)
+    cen = xy[tri].mean(axis=1)
+    drop = np.zeros(len(tri), dtype=bool)
+    for _, _, poly in holes:
+        drop |= _polygon_contains(poly, cen)
+    tri = tri[~drop]
+    a, b, c = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    cw = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0]) < 0.0
+    tri[cw] = tri[cw][:, [0, 2, 1]]
+    edges = {(min(u, v), max(u, v)) for t in tri.tolist() for u, v in ((t[0], t[1]), (t[1], t[2]), (t[2], t[0]))}
+    for l in loops:
+        for u, v in zip(l.tolist(), np.roll(l, -1).tolist()):
+            if (min(u, v), max(u, v)) not in edges:
+                raise RuntimeError("a boundary segment is not a Delaunay edge")
+    return Mesh(xy=xy, tri=tri, loops=loops, name=f"holes{n_goal}_s{seed}",
+                meta={"n_goal": n_goal, "h": h, "holes": [(c, rad, len(p)) for c, rad, p in holes]})

@@ -73,3 +73,29 @@ def test_edge_paths_descend_to_the_target(make):
             assert d[b] == min(d[u] for u in nb[a])
     pts, st = census.edge_path(d, mesh.tri, mesh.xy, int(po.I[0]), p, max_pts=2)
     assert st == census.TRUNCATED and len(pts) == 2
+
+
+@pytest.mark.parametrize("n_goal,seed", [(175, 1), (175, 3), (500, 2)])
+def test_convex_holes_mesh_and_maximum_principle(n_goal, seed):
+    """The low-resolution convex-holes meshes are valid inputs (loops are the
+    topological boundary, every edge touching the interior has a
+    non-negative cotangent weight: Delaunay), so P is a stochastic matrix and
+    the Dirichlet Green's function of every interior target has no spurious
+    minimum."""
+    from oracle.laplacian import cotan_laplacian
+    from oracle.topology import split_boundary
+    from synthetic.meshes import convex_holes
+
+    mesh = convex_holes(n_goal, seed=seed)
+    split_boundary(mesh.n_v, mesh.tri, mesh.loops)
+    assert abs(mesh.n_v - n_goal) < 0.2 * n_goal
+    bf = mesh.boundary_flags()
+    L = cotan_laplacian(mesh.xy, mesh.tri).tocoo()
+    touch = (L.row != L.col) & ~(bf[L.row] & bf[L.col])
+    assert np.all(L.data[touch] > 0.0)             # off-diagonal = +w_ij here, w_ij > 0
+    po = PoissonOracle(mesh.xy, mesh.tri, mesh.loops)
+    P = po.full()
+    assert P.min() >= -1e-14 and np.allclose(P.sum(axis=1), 1.0, atol=1e-12)
+    mask = interior_mask(po, mesh.n_v)
+    for t in po.I[::3]:
+        assert census.local_minima(dirichlet_green_column(po, int(t)), mesh.tri, mask, int(t)).size == 0
