@@ -1,13 +1,13 @@
-"""Pins for the oracle's sparse KL/TV fields (Section V, P thresholded at
-1/sqrt(n) relative to each row's largest entry) -- CPU only.
+"""Pins for the oracle's sparse KL/TV fields (Section V; the target row's
+entries below 1/sqrt(n) of its maximum merged into one bin) -- CPU only.
 
-Pinned by: a hand-worked row (which entries a threshold keeps, and the two
-sums written out), the dense fields as the theta -> 0 limit, the bounds on
-what dropping entries can change (each term removed from the KL sum is
-P[x,b] log(P[x,b]/P[t,b]); the triangle inequality for TV), exact zeros at
-the target, nested kept sets as theta grows, and the disk's centre row,
-whose entries are all equal by the mesh's rotational symmetry, so that no
-threshold below 1 drops any of them.
+Pinned by: a hand-worked example (the kept columns, the merged bin and both
+sums written out), the dense fields as the theta -> 0 limit, the
+data-processing inequality (merging columns cannot increase an f-divergence:
+0 <= KL~ <= KL, 0 <= TV~ <= TV) and the bound TV - TV~ <= 2 M_t, exact zeros
+at the target, the FP32 threshold decision, nested kept sets as theta grows,
+and the disk's centre row, whose entries are all equal by the mesh's
+rotational symmetry, so that no threshold below 1 drops any of them.
 """
 import math
 
@@ -21,28 +21,25 @@ from synthetic import workloads
 from synthetic.meshes import disk_rings
 
 
-def test_hand_row():
-    # rows sum to 1; theta = 0.01 keeps entries >= 0.01 * row max
+def test_hand_example():
+    # target row 0 keeps columns {0, 2} at theta = 0.01 (0.004 < 0.005); M_0 = 0.004
     P = np.array([[0.5, 0.004, 0.496, 0.0],
                   [0.25, 0.25, 0.25, 0.25],
                   [0.9, 0.0089, 0.0911, 0.0]])
-    keep = sparse.keep_mask(P, 0.01)
-    assert keep.tolist() == [[True, False, True, False], [True] * 4, [True, False, True, False]]
-    # KL~ of row 0 against target row 1: 0.5 log(0.5/0.25) + 0.496 log(0.496/0.25)
-    kl = sparse.sparse_kl_field(P, 1, 0.01)
-    assert kl[0] == pytest.approx(0.5 * math.log(2.0) + 0.496 * math.log(0.496 / 0.25), rel=1e-15)
-    assert kl[1] == 0.0
-    # TV~ of row 2 against target row 0: |0.9 - 0.5| + |0 - 0| + |0.0911 - 0.496| + 0
+    assert sparse.support(P, 0, 0.01).tolist() == [True, False, True, False]
+    assert sparse.merged_mass(P, 0, 0.01) == pytest.approx(0.004, abs=1e-18)
+    kl = sparse.sparse_kl_field(P, 0, 0.01)
+    # row 1: 0.25 log(0.25/0.5) + 0.25 log(0.25/0.496) + (0.5) log(0.5/0.004)
+    ref1 = 0.25 * math.log(0.5) + 0.25 * math.log(0.25 / 0.496) + 0.5 * math.log(0.5 / 0.004)
+    assert kl[1] == pytest.approx(ref1, rel=1e-14)
+    assert kl[0] == 0.0
     tv = sparse.sparse_tv_field(P, 0, 0.01)
-    assert tv[2] == pytest.approx(0.4 + 0.4049, rel=1e-14)
+    # row 2: |0.9 - 0.5| + |0.0911 - 0.496| + |0.0089 - 0.004|
+    assert tv[2] == pytest.approx(0.4 + 0.4049 + 0.0049, rel=1e-13)
     assert tv[0] == 0.0
-    # dropped mass: 0.004 from row 0, 0.0089 from row 2
-    assert sparse.dropped_mass(P, 0.01) == pytest.approx([0.004, 0.0, 0.0089], abs=1e-17)
 
 
 def test_threshold_decided_in_fp32():
-    # 0.01 * 0.5 rounds in FP32; an entry equal to the FP32 product is kept,
-    # the next FP32 value below it is not
     thr = np.float32(0.01) * np.float32(0.5)
     below = np.nextafter(thr, np.float32(0.0))
     P = np.array([[0.5, float(thr), float(below), 0.5 - float(thr) - float(below)]])
@@ -56,27 +53,27 @@ def _cases():
 
 
 @pytest.mark.parametrize("idx", [0, 1])
-def test_dense_limit_bounds_and_zeros(idx):
+def test_dense_limit_data_processing_and_zeros(idx):
     mesh, targets = _cases()[idx]
     po = PoissonOracle(mesh.xy, mesh.tri, mesh.loops)
     P = po.full()
     theta = sparse.default_theta(mesh.n_v)
-    keep = sparse.keep_mask(P, theta)
-    drop_mass = sparse.dropped_mass(P, theta)
     for t in targets:
         kl, tv = kl_field_fast(P, P[t]), tv_field(P, P[t])
-        # theta -> 0: every positive entry kept, the dense fields
-        k0 = sparse.sparse_kl_field(P, t, 1e-30)
         fin = np.isfinite(kl)
+        # theta -> 0: only the target's zero columns are merged (mass 0 in row t)
+        k0 = sparse.sparse_kl_field(P, t, 1e-30)
         assert np.allclose(k0[fin], kl[fin], rtol=1e-12, atol=1e-14)
+        assert np.all(~np.isfinite(k0[~fin]))
         assert np.allclose(sparse.sparse_tv_field(P, t, 1e-30), tv, rtol=1e-12, atol=1e-14)
         ks, ts = sparse.sparse_kl_field(P, t, theta), sparse.sparse_tv_field(P, t, theta)
         assert ks[t] == 0.0 and ts[t] == 0.0
+        assert sparse.merged_mass(P, t, theta) > 0.0 or idx == 1
+        m_t = sparse.merged_mass(P, t, theta)
         for x in po.I:
-            dropped = ~keep[x] & (P[x] > 0)
-            bound = float(np.sum(P[x][dropped] * np.abs(np.log(P[x][dropped] / P[t][dropped]))))
-            assert abs(ks[x] - kl[x]) <= bound * (1 + 1e-9) + 1e-13
-            assert abs(ts[x] - tv[x]) <= (drop_mass[x] + drop_mass[t]) * (1 + 1e-9) + 1e-13
+            assert -1e-13 <= ks[x] <= kl[x] * (1 + 1e-12) + 1e-13
+            assert -1e-13 <= ts[x] <= tv[x] * (1 + 1e-12) + 1e-13
+            assert tv[x] - ts[x] <= 2 * m_t * (1 + 1e-9) + 1e-13
 
 
 def test_nested_and_disk_centre():
@@ -91,5 +88,8 @@ def test_nested_and_disk_centre():
         prev = k
     # vertex 0 is the centre: all 48 entries equal up to the solve's rounding
     assert np.ptp(P[0]) < 1e-12
-    assert sparse.keep_mask(P[:1], 0.999).all()
-    assert sparse.sparsity(P[:1], sparse.default_theta(mesh.n_v)) == 0.0
+    assert sparse.support(P, 0, 0.999).all()
+    assert sparse.merged_mass(P, 0, sparse.default_theta(mesh.n_v)) == 0.0
+    # so with the centre as target the sparse fields are the dense ones
+    t = 0
+    assert np.allclose(sparse.sparse_tv_field(P, t, 0.5), tv_field(P, P[t]), rtol=1e-13, atol=1e-15)
