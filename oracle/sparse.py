@@ -18,16 +18,18 @@ Readings (the paper gives the threshold's value and nothing else):
   divergences between the two coarse-grained harmonic measures
   (P[y,b] for b in S_t, and M_y = sum_{b not in S_t} P[y,b]):
 
-    KL~_t(x) = sum_{b in S_t} P[x,b] log(P[x,b] / P[t,b]) + M_x log(M_x / M_t)
-    TV~_t(x) = sum_{b in S_t} |P[x,b] - P[t,b]| + |M_x - M_t|
+    KL~_t(x)  = sum_{b in S_t} P[x,b] log(P[x,b] / P[t,b]) + M_x log(M_x / M_t)
+    KLT~_t(x) = sum_{b in S_t} P[t,b] log(P[t,b] / P[x,b]) + M_t log(M_t / M_x)
+    TV~_t(x)  = sum_{b in S_t} |P[x,b] - P[t,b]| + |M_x - M_t|
 
-  (0 log 0 = 0).  Since every field row meets the same column set, the
+  (0 log 0 = 0; KLT is the KL weighted by the target's row, Eq. 35 with p
+  the target, whose dropped terms are the small ones).  Since every field row meets the same column set, the
   field is as smooth in x as the dense one; a threshold applied to each
   field row instead makes neighbouring rows keep different columns, and
   the fields jump (measured: spurious minima for most targets).  Merging
   columns can only lose information, so 0 <= KL~ <= KL and 0 <= TV~ <= TV
-  (the data-processing inequality), both are exactly 0 at x = t, and
-  TV - TV~ <= 2 M_t.
+  and 0 <= KLT~ <= KLT (the data-processing inequality), all are exactly 0
+  at x = t, and TV - TV~ <= 2 M_t.
 """
 
 import math
@@ -53,12 +55,11 @@ def support(P, t: int, theta: float) -> np.ndarray:
 
 def _xlogy_ratio(a, b):
     """a log(a / b) elementwise with 0 log 0 = 0 and a log(a/0) = +inf for a > 0."""
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    out = np.zeros(np.broadcast(a, b).shape)
+    a, b = np.broadcast_arrays(np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64))
+    out = np.zeros(a.shape)
     pos = a > 0.0
     with np.errstate(divide="ignore"):
-        out[pos] = a[pos] * np.log(a[pos] / np.broadcast_to(b, out.shape)[pos])
+        out[pos] = a[pos] * np.log(a[pos] / b[pos])
     return out
 
 
@@ -69,6 +70,16 @@ def sparse_kl_field(P, t: int, theta: float) -> np.ndarray:
     Mx = P[:, ~S].sum(axis=1)
     Mt = float(Mx[t])                      # the same sum, so that x = t gives exactly 0
     return _xlogy_ratio(P[:, S], P[t, S][None, :]).sum(axis=1) + _xlogy_ratio(Mx, Mt)
+
+
+def sparse_klt_field(P, t: int, theta: float) -> np.ndarray:
+    """KLT~_t(x) for every row x of P (+inf where a kept P[t,b] meets
+    P[x,b] = 0, e.g. every boundary row)."""
+    P = np.asarray(P, dtype=np.float64)
+    S = support(P, t, theta)
+    Mx = P[:, ~S].sum(axis=1)
+    Mt = float(Mx[t])
+    return _xlogy_ratio(P[t, S][None, :], P[:, S]).sum(axis=1) + _xlogy_ratio(Mt, Mx)
 
 
 def sparse_tv_field(P, t: int, theta: float) -> np.ndarray:

@@ -1,10 +1,10 @@
-"""Pins for the oracle's sparse KL/TV fields (Section V; the target row's
+"""Pins for the oracle's sparse KL/KLT/TV fields (Section V; the target row's
 entries below 1/sqrt(n) of its maximum merged into one bin) -- CPU only.
 
 Pinned by: a hand-worked example (the kept columns, the merged bin and both
 sums written out), the dense fields as the theta -> 0 limit, the
 data-processing inequality (merging columns cannot increase an f-divergence:
-0 <= KL~ <= KL, 0 <= TV~ <= TV) and the bound TV - TV~ <= 2 M_t, exact zeros
+0 <= KL~ <= KL, 0 <= KLT~ <= KLT, 0 <= TV~ <= TV) and the bound TV - TV~ <= 2 M_t, exact zeros
 at the target, the FP32 threshold decision, nested kept sets as theta grows,
 and the disk's centre row, whose entries are all equal by the mesh's
 rotational symmetry, so that no threshold below 1 drops any of them.
@@ -16,6 +16,7 @@ import pytest
 
 from oracle import sparse
 from oracle.divergence import kl_field_fast, tv_field
+from oracle.fdiv import kl_reverse_field
 from oracle.poisson import PoissonOracle
 from synthetic import workloads
 from synthetic.meshes import disk_rings
@@ -33,6 +34,11 @@ def test_hand_example():
     ref1 = 0.25 * math.log(0.5) + 0.25 * math.log(0.25 / 0.496) + 0.5 * math.log(0.5 / 0.004)
     assert kl[1] == pytest.approx(ref1, rel=1e-14)
     assert kl[0] == 0.0
+    klt = sparse.sparse_klt_field(P, 0, 0.01)
+    # row 2: 0.5 log(0.5/0.9) + 0.496 log(0.496/0.0911) + 0.004 log(0.004/0.0089)
+    ref2 = 0.5 * math.log(0.5 / 0.9) + 0.496 * math.log(0.496 / 0.0911) + 0.004 * math.log(0.004 / 0.0089)
+    assert klt[2] == pytest.approx(ref2, rel=1e-14)
+    assert klt[0] == 0.0
     tv = sparse.sparse_tv_field(P, 0, 0.01)
     # row 2: |0.9 - 0.5| + |0.0911 - 0.496| + |0.0089 - 0.004|
     assert tv[2] == pytest.approx(0.4 + 0.4049 + 0.0049, rel=1e-13)
@@ -66,13 +72,18 @@ def test_dense_limit_data_processing_and_zeros(idx):
         assert np.allclose(k0[fin], kl[fin], rtol=1e-12, atol=1e-14)
         assert np.all(~np.isfinite(k0[~fin]))
         assert np.allclose(sparse.sparse_tv_field(P, t, 1e-30), tv, rtol=1e-12, atol=1e-14)
+        klt = kl_reverse_field(P, P[t])
+        kt0 = sparse.sparse_klt_field(P, t, 1e-30)
+        assert np.allclose(kt0[np.isfinite(klt)], klt[np.isfinite(klt)], rtol=1e-12, atol=1e-14)
         ks, ts = sparse.sparse_kl_field(P, t, theta), sparse.sparse_tv_field(P, t, theta)
-        assert ks[t] == 0.0 and ts[t] == 0.0
+        kts = sparse.sparse_klt_field(P, t, theta)
+        assert ks[t] == 0.0 and ts[t] == 0.0 and kts[t] == 0.0
         assert sparse.merged_mass(P, t, theta) > 0.0 or idx == 1
         m_t = sparse.merged_mass(P, t, theta)
         for x in po.I:
             assert -1e-13 <= ks[x] <= kl[x] * (1 + 1e-12) + 1e-13
             assert -1e-13 <= ts[x] <= tv[x] * (1 + 1e-12) + 1e-13
+            assert -1e-13 <= kts[x] <= klt[x] * (1 + 1e-12) + 1e-13
             assert tv[x] - ts[x] <= 2 * m_t * (1 + 1e-9) + 1e-13
 
 
