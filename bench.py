@@ -359,8 +359,72 @@ def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10):
         fdiv_sec["families"][name] = {"ms": round(ms_f, 4), "achieved": round(gbs, 1),
                                       "frac": round(gbs / pk.get("hbm_gbs", 6672.5), 4)}
     stream_sec["other_f_divergences"] = fdiv_sec
+    stream_sec["sparse"] = sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, pk_kind, reps)
+    stream_sec["sparse"]["speedup_vs_dense"] = round(med / stream_sec["sparse"]["ms_per_field_pair"], 2)
     dd.dd_unload_mesh(ctx, mid)
     return stream_sec, gemm_sec
+
+
+def sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, pk_kind, reps):
+    """Sparse KL+TV of one target (Section V): the target row's entries below
+    max/sqrt(n) merged into one bin; every row of P is read only at the
+    4-column blocks holding the target's kept columns.  Algorithmic bytes of a
+    launch = 16 B x n x (the target's listed blocks) + 8 B x n (row totals) +
+    the two output fields; the listed blocks are counted on the host from the
+    exported kernel.  Accuracy against the dense FP32 fields of the same
+    targets."""
+    import torch
+    t0 = time.perf_counter()
+    kept, blocks = dd.dd_sparsify(ctx, mid)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    P32 = np.empty((n_v, k), dtype=np.float32)
+    dd.dd_get_poisson_kernel(ctx, mid, P32)
+    theta = np.float32(1.0 / math.sqrt(n_v))
+    use = tl[:reps]
+
+    def listed_blocks(t):
+        row = np.zeros(k_pad, np.float32)
+        row[:k] = P32[t]
+        keep = (row >= theta * row.max()) & (row > 0)
+        return int(keep.reshape(-1, 4).any(axis=1).sum())
+
+    out1 = torch.empty((2, 1, n_v), dtype=torch.float32, device=dev)
+    for t in use[:3]:
+        dd.dd_distance(ctx, mid, [t], 3, dd.DD_PREC_SPARSE, out1)
+    torch.cuda.synchronize()
+    ms, gbs = [], []
+    for t in use:
+        flush.fill_(0.5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dd.dd_distance(ctx, mid, [t], 3, dd.DD_PREC_SPARSE, out1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        m = e0.elapsed_time(e1)
+        ms.append(m)
+        gbs.append((16.0 * n_v * listed_blocks(t) + 8.0 * n_v + 8.0 * n_v) / (m / 1e3) / 1e9)
+    med, g = statistics.median(ms), statistics.median(gbs)
+    dense = torch.empty((3, 4, n_v), dtype=torch.float32, device=dev)
+    sp = torch.empty_like(dense)
+    dd.dd_distance(ctx, mid, tl[:4], 7, dd.DD_PREC_FP32, dense)
+    dd.dd_distance(ctx, mid, tl[:4], 7, dd.DD_PREC_SPARSE, sp)
+    torch.cuda.synchronize()
+    d, s_ = dense.cpu().numpy().astype(np.float64), sp.cpu().numpy().astype(np.float64)
+    rel = np.abs(s_ - d) / np.maximum(np.abs(d), 1e-2)
+    interior = d[2] < 40.0          # KLT is +inf (returned large) on boundary rows
+    return {"kernel": "sparse_field_kernel (+ stage_targets_kernel, sparse_stage_kernel)", "bound": "hbm",
+            "achieved": round(g, 1), "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+            "frac": round(g / pk.get("hbm_gbs", 6672.5), 4), "peak_source": pk_kind,
+            "ms_per_field_pair": round(med, 4), "fields_per_s": round(2 / (med / 1e3), 1),
+            "speedup_vs_dense": None, "sparsity": round(1.0 - kept / float(n_v * k), 4),
+            "listed_blocks_mean": round(float(np.mean([listed_blocks(t) for t in use])), 1),
+            "dense_blocks": int(k_pad // 4), "build_seconds": round(build_s, 3),
+            "vs_dense_fp32": {"kl_max_rel": float(np.max(rel[0])), "kl_median_rel": float(np.median(rel[0])),
+                              "tv_max_rel": float(np.max(rel[1])), "tv_median_rel": float(np.median(rel[1])),
+                              "klt_max_rel": float(np.max(rel[2][interior])),
+                              "klt_median_rel": float(np.median(rel[2][interior]))},
+            "traffic": None}
 
 
 def batch_section(dd, ctx, dev, stream, flush, args, S: int = 64, max_pts: int = 1536):
@@ -430,8 +494,10 @@ def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1,
     """Spurious-local-minimum census (Section V): on convex-holes Delaunay
     meshes of growing resolution (the same four domains at every size), the
     share of targets whose TV field, KL field and target-weighted KL field
-    (the reverse direction, Sum_b P[t,b] log(P[t,b]/P[x,b])) have an interior
-    vertex other than the target with no lower neighbour.  All interior
+    (the reverse direction, Sum_b P[t,b] log(P[t,b]/P[x,b])), and the sparse
+    KL, TV and target-weighted KL fields (the target row's entries below
+    1/sqrt(n) of its maximum merged into one bin), have
+    an interior vertex other than the target with no lower neighbour.  All interior
     targets up to max_targets, else max_targets spread evenly over them.
     Everything runs through the library: the FP64 kernel solve, the FP32
     fields, the minimum test."""
@@ -441,7 +507,8 @@ def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1,
     t0 = time.perf_counter()
     for n_goal in sizes:
         agg = {"n_goal": n_goal, "meshes": 0, "n_v": [], "k": [], "targets": 0,
-               "tv": [0, 0], "kl": [0, 0], "kl_target_weighted": [0, 0]}
+               "tv": [0, 0], "kl": [0, 0], "kl_target_weighted": [0, 0], "kl_sparse": [0, 0], "tv_sparse": [0, 0],
+               "kl_target_weighted_sparse": [0, 0]}
         for seed in seeds:
             mesh = convex_holes(n_goal, seed=seed)
             idx, off = mesh.loop_arrays()
@@ -456,7 +523,12 @@ def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1,
             dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, fields)
             rev = torch.empty((T, mesh.n_v), dtype=torch.float32, device=dev)
             dd.dd_divergence(ctx, mid, targets, dd.DD_DIV_KL_REVERSE, 0.0, rev)
-            for name, f in (("kl", fields[0]), ("tv", fields[1]), ("kl_target_weighted", rev)):
+            dd.dd_sparsify(ctx, mid)
+            sparse_f = torch.empty((3, T, mesh.n_v), dtype=torch.float32, device=dev)
+            dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV | dd.DD_F_KLT, dd.DD_PREC_SPARSE, sparse_f)
+            for name, f in (("kl", fields[0]), ("tv", fields[1]), ("kl_target_weighted", rev),
+                            ("kl_sparse", sparse_f[0]), ("tv_sparse", sparse_f[1]),
+                            ("kl_target_weighted_sparse", sparse_f[2])):
                 c = dd.dd_local_minima(ctx, mid, f.contiguous(), targets, None)
                 agg[name][0] += int(np.count_nonzero(c))
                 agg[name][1] += int(c.sum())
@@ -465,7 +537,7 @@ def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1,
             agg["k"].append(dd.dd_mesh_info(ctx, mid)["k"])
             agg["targets"] += T
             dd.dd_unload_mesh(ctx, mid)
-        for name in ("tv", "kl", "kl_target_weighted"):
+        for name in ("tv", "kl", "kl_target_weighted", "kl_sparse", "tv_sparse", "kl_target_weighted_sparse"):
             agg[name] = {"targets_with_minima": agg[name][0], "minima": agg[name][1],
                          "share": round(agg[name][0] / agg["targets"], 4)}
         rows.append(agg)

@@ -51,8 +51,14 @@ typedef enum {
     DD_EBUDGET = -7    /* the request exceeds the context's device-memory budget      */
 } dd_status;
 
-/* divergence selector bits (Eq. 34: TV, Eq. 35: KL) */
-enum { DD_F_KL = 1, DD_F_TV = 2 };
+/* divergence selector bits (Eq. 34: TV, Eq. 35: KL).  Eq. 35's two readings:
+ *   DD_F_KL   KL_t(x) = sum_b P[x,b] log(P[x,b]/P[t,b]), weighted by the field
+ *             row (the form the tensor-core cross term computes)
+ *   DD_F_KLT  KLT_t(x) = sum_b P[t,b] log(P[t,b]/P[x,b]), weighted by the
+ *             target row (Eq. 35 with p the target; +inf on boundary rows,
+ *             returned as a large finite value >= 50)
+ * Fields of a mask are laid out in bit order: KL, TV, KLT. */
+enum { DD_F_KL = 1, DD_F_TV = 2, DD_F_KLT = 4 };
 
 /* arithmetic of the field evaluation:
  *  DD_PREC_FP32   FP32 CUDA-core evaluation of Eq. 34-35 term by term, each
@@ -66,8 +72,19 @@ enum { DD_F_KL = 1, DD_F_TV = 2 };
  *                 dd_check_fast_log), so both keep 1e-5 relative accuracy.
  *  DD_PREC_BF16X3 KL cross term sum_b P[x,b] log P[t,b] as a tensor-core GEMM
  *                 of split BF16 hi/lo operands (hi*hi + hi*lo + lo*hi, FP32
- *                 accumulation); TV is always FP32 */
-enum { DD_PREC_FP32 = 0, DD_PREC_BF16X3 = 1 };
+ *                 accumulation); TV and KLT are always FP32
+ *  DD_PREC_SPARSE the sparse fields of Section V (small entries of P
+ *                 eliminated, see dd_sparsify), FP32 as DD_PREC_FP32.  The
+ *                 target row keeps S_t = {b : P[t,b] >= theta max_b' P[t,b']}
+ *                 (FP32 product); the other columns merge into one bin of
+ *                 mass M_y = sum_{b not in S_t} P[y,b]:
+ *                   KL~_t(x) = sum_{b in S_t} P[x,b] log(P[x,b]/P[t,b])
+ *                              + M_x log(M_x / M_t)
+ *                   TV~_t(x) = sum_{b in S_t} |P[x,b] - P[t,b]| + |M_x - M_t|
+ *                 (divergences of the coarse-grained harmonic measures:
+ *                 0 <= KL~ <= KL, 0 <= TV~ <= TV, both 0 at x = t); each row
+ *                 is read only at the 4-column blocks holding S_t */
+enum { DD_PREC_FP32 = 0, DD_PREC_BF16X3 = 1, DD_PREC_SPARSE = 2 };
 #define DD_FAST_LOG_SPREAD 5.0e-7
 #define DD_EXACT_BELOW 0.05
 
@@ -180,19 +197,37 @@ dd_status dd_set_poisson_kernel(dd_ctx *ctx, int32_t mesh, const double *P);
  * out: device or host.  Errors: DD_ESTATE if none is stored. */
 dd_status dd_get_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out);
 
+/* Prepare DD_PREC_SPARSE on this mesh (Section V: entries below a threshold
+ * of 1/sqrt(n) are eliminated before the KL sum, about 90 % of them; the
+ * paper does not say relative to what -- here, relative to the row's
+ * largest entry, applied to the target's row, see DD_PREC_SPARSE).  Stores
+ * theta and the FP64 total of every row of the stored P (8 bytes per vertex)
+ * and reports the sparsity: over all rows, how many entries the threshold
+ * keeps, each row against its own maximum.  Recomputing or replacing P
+ * (dd_poisson_kernel, dd_set_poisson_kernel) discards it.
+ *   theta   threshold relative to the row maximum, < 1; negative: 1/sqrt(n_v)
+ *   kept    NULL or out: kept entries over all rows
+ *   blocks  NULL or out: 4-column blocks holding a kept entry, over all rows
+ * Errors: DD_ESTATE before a Poisson kernel exists, DD_EINVAL (theta >= 1 or
+ * NaN, k beyond 262,144 columns), DD_ENOMEM, DD_ECUDA. */
+dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, int64_t *blocks);
+
 /* Divergence fields of T target vertices, Eq. (34)-(35):
- *   TV_t(x) = sum_b |P[x,b] - P[t,b]|
- *   KL_t(x) = sum_b P[x,b] log(P[x,b] / P[t,b])     (Eq. 17 with z = x, w = t)
+ *   TV_t(x)  = sum_b |P[x,b] - P[t,b]|
+ *   KL_t(x)  = sum_b P[x,b] log(P[x,b] / P[t,b])     (Eq. 17 with z = x, w = t)
+ *   KLT_t(x) = sum_b P[t,b] log(P[t,b] / P[x,b])     (Eq. 35 with p = t)
  * with 0 log 0 = 0, for every vertex x.
  *   targets  host [T] interior vertex ids (a boundary target is DD_EINVAL:
  *            its KL row is infinite)
- *   f_mask   DD_F_KL | DD_F_TV (at least one bit)
- *   prec     DD_PREC_FP32 or DD_PREC_BF16X3
+ *   f_mask   any non-empty combination of DD_F_KL, DD_F_TV, DD_F_KLT
+ *   prec     DD_PREC_FP32, DD_PREC_BF16X3 or DD_PREC_SPARSE (after dd_sparsify;
+ *            DD_ESTATE before)
  *   out      device or host float32 [nf][T][n_v], nf = number of bits set,
- *            KL block first when both are requested
+ *            blocks in bit order (KL, TV, KLT)
  * In FP32 a log argument below FLT_MIN is taken as FLT_MIN: where P[t,b] = 0
  * but P[x,b] > 0 (a boundary row x of a column with no interior support) the
- * exact KL is +inf and the result is finite and at least 87.
+ * exact KL is +inf and the result is finite and at least 87; KLT is +inf on
+ * every boundary row and the result there is at least 50.
  * Errors: DD_EINVAL, DD_ESTATE (no Poisson kernel), DD_ENOMEM, DD_ECUDA. */
 dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
                       uint32_t f_mask, int32_t prec, float *out);

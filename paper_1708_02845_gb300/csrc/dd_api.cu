@@ -114,6 +114,32 @@ void free_mesh(DevMesh &m) {
     m = DevMesh();
 }
 
+// free one device array of the mesh and forget it
+template <typename T>
+void release(DevMesh &m, T *&p, int64_t bytes) {
+    if (!p) return;
+    cudaFree((void *)p);
+    m.owned.erase(std::remove(m.owned.begin(), m.owned.end(), (void *)p), m.owned.end());
+    m.bytes -= bytes;
+    p = nullptr;
+}
+
+void drop_sparse(DevMesh &m) {
+    release(m, m.sp_rowsum, m.n_v * (int64_t)sizeof(long long));
+    m.sp_kept = m.sp_blocks = 0;
+    m.sp_theta = 0.f;
+}
+
+// what was derived from the stored P (the BF16 split, the row entropies, the
+// sparse rows) goes when P is recomputed or replaced
+void drop_derived(DevMesh &m) {
+    release(m, m.p_hi, m.n_v * m.kb * 2);
+    release(m, m.p_lo, m.n_v * m.kb * 2);
+    release(m, m.ex, m.n_v * (int64_t)sizeof(float));
+    m.kb = 0;
+    drop_sparse(m);
+}
+
 dd_status check_targets(dd_ctx *ctx, const DevMesh &m, const int32_t *ids, int64_t count, bool interior_only,
                         const char *what) {
     if (count > 0 && !ids) return set_err(ctx, DD_EINVAL, std::string(what) + " pointer is null");
@@ -140,32 +166,60 @@ dd_status check_kernel_flag(dd_ctx *ctx) {
     return DD_OK;
 }
 
+// the fields of a mask in bit order (KL, TV, KLT): slot of `bit` in dst [nf][T][n_v]
+float *field_slot(float *dst, uint32_t f_mask, uint32_t bit, int64_t stride) {
+    if (!(f_mask & bit)) return nullptr;
+    int slot = 0;
+    for (uint32_t b = 1; b < bit; b <<= 1) slot += (f_mask & b) ? 1 : 0;
+    return dst + slot * stride;
+}
+
 // fields of T targets into dst [nf][T][n_v] (device), targets already in scratch
 dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t T, uint32_t f_mask, int32_t prec,
                       float *dst) {
-    float *kl = (f_mask & DD_F_KL) ? dst : nullptr;
-    float *tv = (f_mask & DD_F_TV) ? dst + ((f_mask & DD_F_KL) ? (int64_t)T * m.n_v : 0) : nullptr;
+    const int64_t stride = (int64_t)T * m.n_v;
+    float *kl = field_slot(dst, f_mask, DD_F_KL, stride);
+    float *tv = field_slot(dst, f_mask, DD_F_TV, stride);
+    float *klt = field_slot(dst, f_mask, DD_F_KLT, stride);
     dd_status st;
     if (prec == DD_PREC_BF16X3 && kl) {
-        // KL through the split-BF16 tensor-core GEMM; TV (if asked) stays FP32 below
+        // KL through the split-BF16 tensor-core GEMM; TV and KLT (if asked) stay FP32 below
         std::string err;
         if ((st = prepare_bf16(m, ctx->stream, err)) != DD_OK) return set_err(ctx, st, err);
         if ((st = ensure_scratch(ctx, S_GEMM, gemm_target_scratch_bytes(m, T))) != DD_OK) return st;
         if ((st = launch_kl_gemm(m, d_targets, T, ctx->scratch[S_GEMM], kl, ctx->d_err, ctx->stream, err)) != DD_OK)
             return set_err(ctx, st, err);
         kl = nullptr;
-        if (!tv) return DD_OK;
+        if (!tv && !klt) return DD_OK;
+    }
+    if (prec == DD_PREC_SPARSE) {
+        if (!m.sp_rowsum) return set_err(ctx, DD_ESTATE, "DD_PREC_SPARSE before dd_sparsify");
+        if (sparse_field_smem(m.k_pad) > 200 * 1024)
+            return set_err(ctx, DD_EINVAL, "DD_PREC_SPARSE: k too large for the staged target row");
+        if (T > 65535) return set_err(ctx, DD_EINVAL, "DD_PREC_SPARSE: at most 65,535 targets per call");
+        if ((st = ensure_scratch(ctx, S_STAGE, sparse_stage_bytes(m.k_pad, T))) != DD_OK) return st;
+        float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
+        launch_stage_targets(m.P, m.k_pad, m.k, d_targets, T, stage, ctx->stream);
+        launch_sparse_fields(m, d_targets, stage, T, kl, tv, klt, ctx->d_err, ctx->stream);
+        CK(cudaGetLastError(), "sparse field kernel launch");
+        return DD_OK;
     }
     st = ensure_scratch(ctx, S_STAGE, 4 * (size_t)T * m.k_pad * sizeof(float));
     if (st != DD_OK) return st;
     float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
     launch_stage_targets(m.P, m.k_pad, m.k, d_targets, T, stage, ctx->stream);
-    launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream);
+    if (kl || tv) launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream);
+    if (klt) {
+        // the target-weighted KL is the reverse-KL member of the f-divergence kernels
+        std::string err;
+        if ((st = launch_fdiv(m.P, m.n_v, m.k_pad, stage, T, DD_DIV_KL_REVERSE, 0.0, klt, ctx->stream, err)) != DD_OK)
+            return set_err(ctx, st, err);
+    }
     CK(cudaGetLastError(), "field kernel launch");
     return DD_OK;
 }
 
-int popcount2(uint32_t f) { return ((f & DD_F_KL) ? 1 : 0) + ((f & DD_F_TV) ? 1 : 0); }
+int popcount2(uint32_t f) { return ((f & DD_F_KL) ? 1 : 0) + ((f & DD_F_TV) ? 1 : 0) + ((f & DD_F_KLT) ? 1 : 0); }
 
 }  // namespace
 
@@ -377,6 +431,7 @@ dd_status dd_poisson_kernel(dd_ctx *ctx, int32_t mesh, double rtol, int32_t max_
     if (!(rtol > 0.0) || max_iter < 1) return set_err(ctx, DD_EINVAL, "rtol must be > 0 and max_iter >= 1");
     try {
         if ((st = select_device(ctx)) != DD_OK) return st;
+        drop_derived(*m);
         std::string err;
         st = run_pcg(*m, rtol, max_iter, ctx->stream, iters, resid, err);
         if (st != DD_OK) set_err(ctx, st, err);
@@ -392,6 +447,7 @@ dd_status dd_set_poisson_kernel(dd_ctx *ctx, int32_t mesh, const double *P) {
     if (st != DD_OK) return st;
     if (!P || pointer_space(ctx, P) != 0) return set_err(ctx, DD_EINVAL, "P must be a host pointer");
     if ((st = select_device(ctx)) != DD_OK) return st;
+    drop_derived(*m);
     std::string err;
     st = store_poisson(*m, P, ctx->stream, err);
     if (st != DD_OK) set_err(ctx, st, err);
@@ -414,6 +470,24 @@ dd_status dd_get_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out) {
     return DD_OK;
 }
 
+dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, int64_t *blocks) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    if (!m->has_P) return set_err(ctx, DD_ESTATE, "dd_sparsify before dd_poisson_kernel");
+    if (!(theta < 1.0)) return set_err(ctx, DD_EINVAL, "theta must be < 1 (negative: 1/sqrt(n))");
+    try {
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        if (theta < 0.0) theta = 1.0 / std::sqrt((double)m->n_v);
+        drop_sparse(*m);
+        std::string err;
+        if ((st = build_sparse_rows(*m, theta, ctx->stream, kept, blocks, err)) != DD_OK) return set_err(ctx, st, err);
+        return DD_OK;
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
 dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T, uint32_t f_mask, int32_t prec,
                       float *out) {
     DevMesh *m = nullptr;
@@ -422,9 +496,10 @@ dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t
     try {
         if (!m->has_P) return set_err(ctx, DD_ESTATE, "dd_distance before dd_poisson_kernel");
         if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
-        if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV)))
-            return set_err(ctx, DD_EINVAL, "f_mask must be a non-empty combination of DD_F_KL and DD_F_TV");
-        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3) return set_err(ctx, DD_EINVAL, "unsupported precision");
+        if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV | DD_F_KLT)))
+            return set_err(ctx, DD_EINVAL, "f_mask must be a non-empty combination of DD_F_KL, DD_F_TV, DD_F_KLT");
+        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3 && prec != DD_PREC_SPARSE)
+            return set_err(ctx, DD_EINVAL, "unsupported precision");
         if (!out) return set_err(ctx, DD_EINVAL, "out is null");
         if ((st = check_targets(ctx, *m, targets, T, true, "targets")) != DD_OK) return st;
         const int sp = pointer_space(ctx, out);
@@ -689,11 +764,12 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
     try {
         if (!m->has_P) return set_err(ctx, DD_ESTATE, "dd_query before dd_poisson_kernel");
         if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
-        if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV)))
+        if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV | DD_F_KLT)))
             return set_err(ctx, DD_EINVAL, "bad f_mask");
-        if ((trace_f != DD_F_KL && trace_f != DD_F_TV) || !(f_mask & trace_f))
+        if ((trace_f != DD_F_KL && trace_f != DD_F_TV && trace_f != DD_F_KLT) || !(f_mask & trace_f))
             return set_err(ctx, DD_EINVAL, "trace_f must be one bit of f_mask");
-        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3) return set_err(ctx, DD_EINVAL, "unsupported precision");
+        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3 && prec != DD_PREC_SPARSE)
+            return set_err(ctx, DD_EINVAL, "unsupported precision");
         if (!out_fields) return set_err(ctx, DD_EINVAL, "out_fields is null");
         if ((st = check_path_args(ctx, S, max_pts, out_xy, out_len, out_status)) != DD_OK) return st;
         if ((st = check_targets(ctx, *m, targets, T, true, "targets")) != DD_OK) return st;
@@ -710,7 +786,7 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
         }
         st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst);
         if (st != DD_OK) return st;
-        const float *trace_field = dst + ((trace_f == DD_F_TV && (f_mask & DD_F_KL)) ? (int64_t)T * m->n_v : 0);
+        const float *trace_field = field_slot(dst, f_mask, trace_f, (int64_t)T * m->n_v);
         if (sf == 0)
             CK(cudaMemcpyAsync(out_fields, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy fields");
         st = trace_into(ctx, *m, trace_field, targets, T, sources, S, max_pts, out_xy, out_len, out_status, true);

@@ -41,6 +41,7 @@
 #include <cstdlib>
 
 #include "dd_internal.h"
+#include "dd_bulk.cuh"
 #include "dd_splitlog.cuh"
 
 namespace {
@@ -94,15 +95,6 @@ __device__ __forceinline__ void accumulate2(f2_t px, f2_t lmx, f2_t ex, f2_t pt,
     tv = add2(tv, dp & 0x7fffffff7fffffffULL);
 }
 
-// Hardware base-2 logarithm (lg2.approx) of the mantissa m in [1, 2) of a
-// float bit pattern i; the result lies in [0, 1].  Its error over all 2^23
-// mantissas spans at most kLg2Spread (checked exhaustively by the tests).
-__device__ __forceinline__ float lg2_mant(int i) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__int_as_float((i & 0x007FFFFF) | 0x3F800000)));
-    return y;
-}
-
 // stage_P / stage_L / stage_E / stage_F: [T][k_pad] target row, its mantissa
 // log (table), biased exponent and mantissa log2 (hardware), the target-side
 // arguments clamped at FLT_MIN
@@ -123,51 +115,6 @@ __global__ void stage_targets_kernel(const float *__restrict__ P, int64_t k_pad,
     sE[(int64_t)a * k_pad + b] = E;
     sF[(int64_t)a * k_pad + b] = lg2_mant(__float_as_int(fmaxf(p, FLT_MIN)));
 }
-
-// ------------------------------------------------------------------ mbarrier helpers
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-
-// bulk global -> shared copy (no tensor map, no multicast); size multiple of 16
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-constexpr uint32_t kWaitLimit = 1u << 25;   // bounded spins of a non-suspending test (about a second)
-
-// bounded wait: true when the phase completed; false (error flag set) when the limit expired
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
-        if (mbar_test(bar, parity)) return true;
-    atomicExch(err, 1);
-    return false;
-}
-
 
 // ------------------------------------------------------------------ few targets
 // streaming 16-byte load, issued where it is written (the asm is volatile and

@@ -1,0 +1,480 @@
+// Sparse KL and TV fields, Section V: the Poisson kernel's small entries
+// eliminated before the sums (threshold 1/sqrt(n), about 90 % of the
+// entries).  The target row decides: S_t = {b : P[t,b] >= theta max_b' P[t,b']}
+// (FP32 product), and every other column is merged into one bin, so the
+// fields are the divergences between the coarse-grained harmonic measures
+// (P[y,b] for b in S_t, and M_y = sum_{b not in S_t} P[y,b]):
+//
+//   KL~_t(x)  = sum_{b in S_t} P[x,b] log(P[x,b] / P[t,b]) + M_x log(M_x / M_t)
+//   KLT~_t(x) = sum_{b in S_t} P[t,b] log(P[t,b] / P[x,b]) + M_t log(M_t / M_x)
+//   TV~_t(x)  = sum_{b in S_t} |P[x,b] - P[t,b]| + |M_x - M_t|
+//
+// Every row meets the same columns, so the field is as smooth as the dense
+// one, and merging can only lose information: 0 <= KL~ <= KL, 0 <= KLT~ <=
+// KLT, 0 <= TV~ <= TV.
+//
+// Work: per target, the 4-column blocks of P holding a column of S_t are
+// listed once (sparse_stage_kernel, in column order; S_t lies on a few arcs
+// of the boundary, so the list is a few runs of consecutive blocks).  The
+// field kernel reads, for every row, only those blocks of the dense FP32 P
+// (16-byte loads, consecutive within a run), one warp per row, the next
+// item's loads in flight while the current one is summed.  Masses are kept
+// in 2^-62 fixed point (int64, exact for every entry above 2^-39): M_x is
+// the row's total (per mesh, dd_sparsify) minus its S_t part, exact and
+// independent of the order of the additions, so M_t from row t equals M_x at
+// x = t bit for bit and the fields are exactly 0 there.  (FP64 would serve
+// too, but its rate on this GPU is a small fraction of the integer pipes'.)
+// KL and KLT over S_t take the same two passes as the dense streaming kernel
+// (exponents exact, hardware log2 of the mantissas, rows below DD_EXACT_BELOW
+// recomputed with the table logarithm).
+#include <cfloat>
+#include <cmath>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "dd_bulk.cuh"
+#include "dd_internal.h"
+#include "dd_splitlog.cuh"
+
+namespace {
+
+constexpr float kLn2s = 0.693147180559945309f;
+constexpr float kExactBelowS = (float)DD_EXACT_BELOW;
+
+// p in units of 2^-62, from the bits: p = m 2^(e - 150) for the biased
+// exponent e and the 24-bit significand m, so p 2^62 = m 2^(e - 88); values
+// below 2^-39 are truncated, zero and subnormals give 0.  Exact for every
+// p in [2^-39, 2): the sum of a row of P (about 1) stays below 2^63.
+__device__ __forceinline__ long long fix62(float p) {
+    const unsigned u = __float_as_uint(p);
+    const int e = (int)((u >> 23) & 0xFFu);
+    if (e == 0) return 0;
+    const long long m = (long long)((u & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 88;
+    return sh >= 0 ? (m << sh) : (sh > -24 ? (m >> -sh) : 0LL);
+}
+
+__device__ __forceinline__ float unfix62(long long q) { return __ll2float_rn(q) * 0x1p-62f; }
+
+// per row: fixed-point total of the stored FP32 row, and how many entries /
+// 4-column blocks the row's own threshold keeps (the sparsity figure).  One
+// warp per row.
+__global__ void sparse_rows_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad, float theta,
+                                   long long *__restrict__ rowsum, unsigned long long *__restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (x >= n_v) return;
+    const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+    const int nb = (int)(k_pad >> 2);
+    float mx = 0.0f;
+    long long s = 0;
+    for (int j = lane; j < nb; j += 32) {
+        const float4 v = __ldg(row + j);
+        mx = fmaxf(mx, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+        s += fix62(v.x) + fix62(v.y) + fix62(v.z) + fix62(v.w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    const float t = __fmul_rn(theta, mx);
+    unsigned long long ne = 0, nbk = 0;
+    for (int j = lane; j < nb; j += 32) {
+        const float4 v = __ldg(row + j);
+        const int c = (v.x >= t && v.x > 0.f) + (v.y >= t && v.y > 0.f) + (v.z >= t && v.z > 0.f) +
+                      (v.w >= t && v.w > 0.f);
+        ne += c;
+        nbk += c > 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ne += __shfl_xor_sync(0xffffffffu, ne, o);
+        nbk += __shfl_xor_sync(0xffffffffu, nbk, o);
+    }
+    if (lane == 0) {
+        rowsum[x] = s;
+        atomicAdd(counts, ne);
+        atomicAdd(counts + 1, nbk);
+    }
+}
+
+// Per target (one CTA each), after stage_targets_kernel: zero the staged
+// row's entries below theta x its maximum (the logs stay those of the dense
+// row) and list, in column order, the blocks holding a kept entry:
+// list[a][0 .. count[a]), pitch lp.
+__global__ void sparse_stage_kernel(float *__restrict__ sP, int64_t k_pad, float theta, uint16_t *__restrict__ list,
+                                    int64_t lp, int32_t *__restrict__ count) {
+    __shared__ float red[32];
+    __shared__ int wsum[32];
+    const int a = blockIdx.x;
+    float *row = sP + (int64_t)a * k_pad;
+    uint16_t *L = list + (int64_t)a * lp;
+    const int nb = (int)(k_pad >> 2);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float mx = 0.0f;
+    for (int64_t b = threadIdx.x; b < k_pad; b += blockDim.x) mx = fmaxf(mx, row[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[wid] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float m = threadIdx.x < nw ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) red[0] = m;
+    }
+    __syncthreads();
+    const float t = __fmul_rn(theta, red[0]);
+    // blocks in rounds of blockDim.x: threshold, then compact with a block-wide prefix
+    int base = 0;
+    for (int j0 = 0; j0 < nb; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        bool keep = false;
+        if (j < nb) {
+            float4 v = reinterpret_cast<float4 *>(row)[j];
+            const bool kx = v.x >= t && v.x > 0.f, ky = v.y >= t && v.y > 0.f;
+            const bool kz = v.z >= t && v.z > 0.f, kw = v.w >= t && v.w > 0.f;
+            v.x = kx ? v.x : 0.f;
+            v.y = ky ? v.y : 0.f;
+            v.z = kz ? v.z : 0.f;
+            v.w = kw ? v.w : 0.f;
+            reinterpret_cast<float4 *>(row)[j] = v;
+            keep = kx || ky || kz || kw;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wsum[wid] = __popc(ball);
+        __syncthreads();
+        int before = base;
+        for (int w = 0; w < wid; ++w) before += wsum[w];
+        if (keep) L[before + __popc(ball & ((1u << lane) - 1u))] = (uint16_t)j;
+        int total = 0;
+        for (int w = 0; w < nw; ++w) total += wsum[w];
+        base += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) count[a] = base;
+}
+
+// S_t part of one row's mass for one warp, fixed point (exact in any order)
+__device__ __forceinline__ long long kept_mass(const float *__restrict__ P, int64_t x, int64_t k_pad,
+                                               const uint16_t *lst, int nl, const float4 *tP4, int lane) {
+    const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+    long long s = 0;
+    for (int i = lane; i < nl; i += 32) {
+        const int j = lst[i];
+        const float4 v = __ldcg(row + j);
+        const float4 p = tP4[j];
+        s += (p.x > 0.f ? fix62(v.x) : 0LL) + (p.y > 0.f ? fix62(v.y) : 0LL) + (p.z > 0.f ? fix62(v.z) : 0LL) +
+             (p.w > 0.f ? fix62(v.w) : 0LL);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// exact (table) KL over the kept columns of one row, for one warp: the row
+// weighted (TARGET_W false: sum P[x,b] log(P[x,b]/P[t,b])) or the target
+// weighted (true: sum P[t,b] log(P[t,b]/P[x,b]), the row's log at >= FLT_MIN)
+template <bool TARGET_W>
+__device__ __forceinline__ float kept_kl_exact(const float *__restrict__ P, int64_t x, int64_t k_pad,
+                                               const uint16_t *lst, int nl, const float4 *tP4, const float *tL,
+                                               const float *tE, const float *tab, int lane) {
+    const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+    float k0 = 0.0f, k1 = 0.0f;
+    for (int i = lane; i < nl; i += 32) {
+        const int j = lst[i];
+        const float4 v = __ldcg(row + j);
+        const float4 p4 = tP4[j];
+        const float4 l4 = reinterpret_cast<const float4 *>(tL)[j];
+        const float4 e4 = reinterpret_cast<const float4 *>(tE)[j];
+        const float px[4] = {v.x, v.y, v.z, v.w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
+        const float lt[4] = {l4.x, l4.y, l4.z, l4.w}, et[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!(pt[q] > 0.f)) continue;
+            float lm, Eb;
+            split_log<TARGET_W>(px[q], tab, lm, Eb);
+            const float lr = __fmaf_rn(__fadd_rn(Eb, -et[q]), kLn2s, __fadd_rn(lm, -lt[q]));   // log(P_x/P_t)
+            const float w = TARGET_W ? -pt[q] : px[q];
+            if (q & 1)
+                k1 = __fmaf_rn(w, lr, k1);
+            else
+                k0 = __fmaf_rn(w, lr, k0);
+        }
+    }
+    float s = k0 + k1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// One target per grid row (blockIdx.y).  Dynamic smem: the thresholded target
+// row, the dense row's table mantissa log, biased exponent and hardware
+// mantissa log2 (k_pad floats each) and the block list (lp uint16); one bulk
+// copy each.  Items are (row, group of 32 U listed blocks).  The row-side
+// logarithms are taken at max(P[x,b], FLT_MIN): a zero entry contributes 0 to
+// KL (weight 0) and a large finite term to KLT (the exact value is +inf).
+template <int U, bool KL, bool TV, bool KLT>
+__global__ void __launch_bounds__(256, 3) sparse_field_kernel(
+    const float *__restrict__ P, int64_t n_v, int64_t k_pad, const float *__restrict__ sP,
+    const float *__restrict__ sL, const float *__restrict__ sE, const float *__restrict__ sF,
+    const uint16_t *__restrict__ sList, int64_t lp, const int32_t *__restrict__ sCount,
+    const long long *__restrict__ rowsum, const int32_t *__restrict__ targets, float *__restrict__ out_kl,
+    float *__restrict__ out_tv, float *__restrict__ out_klt, int *__restrict__ err_flag) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float tab[2 * kLogTab];
+    __shared__ long long sh_mt;
+    float *tP = smem;
+    float *tL = tP + k_pad;
+    float *tE = tL + k_pad;
+    float *tF = tE + k_pad;
+    uint16_t *lst = reinterpret_cast<uint16_t *>(tF + k_pad);
+    const int a = blockIdx.y;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t row_bytes = (uint32_t)(k_pad * sizeof(float));
+        const uint32_t l_bytes = (uint32_t)(lp * sizeof(uint16_t));
+        mbar_expect_tx(&bar, 4u * row_bytes + l_bytes);
+        bulk_g2s(tP, sP + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(tL, sL + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(tE, sE + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(tF, sF + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(lst, sList + (int64_t)a * lp, l_bytes, &bar);
+    }
+    build_log_table(tab);
+    __syncthreads();
+    if (!mbar_wait(&bar, 0, err_flag)) {
+        mbar_wait(&bar, 0, err_flag);     // copies may still land: wait once more (bounded) before exiting
+        return;
+    }
+    const int nl = sCount[a];
+    const int lane = threadIdx.x & 31;
+    const float4 *tP4 = reinterpret_cast<const float4 *>(tP);
+    const float4 *tF4 = reinterpret_cast<const float4 *>(tF);
+    const float4 *tE4 = reinterpret_cast<const float4 *>(tE);
+    if (threadIdx.x < 32) {
+        const int64_t t_row = targets[a];
+        const long long mt = rowsum[t_row] - kept_mass(P, t_row, k_pad, lst, nl, tP4, lane);
+        if (lane == 0) sh_mt = mt;
+    }
+    __syncthreads();
+    const long long Mt_q = sh_mt;
+    const float Mt = unfix62(Mt_q);
+
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int ngroups = nl > 0 ? (nl + 32 * U - 1) / (32 * U) : 1;
+    float *okl = KL ? out_kl + (int64_t)a * n_v : nullptr;
+    float *otv = TV ? out_tv + (int64_t)a * n_v : nullptr;
+    float *okt = KLT ? out_klt + (int64_t)a * n_v : nullptr;
+
+    float4 buf[2][U];
+    long long rsb[2];                  // the fetched row's total, loaded with its blocks
+    float kl = 0.f, tv = 0.f, kt = 0.f;
+    long long ks = 0;
+
+    // S: which register buffer (a compile-time index, so the buffers stay in registers)
+    auto fetch = [&](auto S_, int64_t x, int g) {
+        constexpr int s = decltype(S_)::value;
+        const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+        rsb[s] = rowsum[x];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = g * 32 * U + u * 32 + lane;
+            buf[s][u] = i < nl ? __ldcs(row + lst[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto compute = [&](auto S_, int g) {
+        constexpr int s = decltype(S_)::value;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = g * 32 * U + u * 32 + lane;
+            if (i >= nl) break;
+            const int j = lst[i];
+            const float4 p4 = tP4[j], f4 = tF4[j], e4 = tE4[j];
+            const float px[4] = {buf[s][u].x, buf[s][u].y, buf[s][u].z, buf[s][u].w};
+            const float pt[4] = {p4.x, p4.y, p4.z, p4.w}, ft[4] = {f4.x, f4.y, f4.z, f4.w};
+            const float et[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!(pt[q] > 0.f)) continue;          // a dropped column of a listed block: merged bin
+                ks += fix62(px[q]);
+                if (TV) tv = __fadd_rn(tv, fabsf(__fadd_rn(px[q], -pt[q])));
+                if (KL || KLT) {
+                    const int bits = __float_as_int(fmaxf(px[q], FLT_MIN));
+                    const float lf = lg2_mant(bits);
+                    const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
+                    const float d = __fadd_rn(__fadd_rn(lf, -ft[q]), __fadd_rn(eb, -et[q]));   // log2(P_x/P_t)
+                    if (KL) kl = __fmaf_rn(px[q], d, kl);
+                    if (KLT) kt = __fmaf_rn(-pt[q], d, kt);
+                }
+            }
+        }
+    };
+    auto finish = [&](auto S_, int64_t x) {
+        constexpr int s = decltype(S_)::value;
+        float skl = kl, stv = tv, skt = kt;
+        long long sks = ks;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            if (KL) skl += __shfl_xor_sync(0xffffffffu, skl, o);
+            if (TV) stv += __shfl_xor_sync(0xffffffffu, stv, o);
+            if (KLT) skt += __shfl_xor_sync(0xffffffffu, skt, o);
+            sks += __shfl_xor_sync(0xffffffffu, sks, o);
+        }
+        const long long Mx_q = rsb[s] - sks;
+        const float Mx = unfix62(Mx_q);
+        if (KL) {
+            const float merged = Mx > 0.f ? Mx * logf(Mx / fmaxf(Mt, FLT_MIN)) : 0.f;
+            skl = __fmaf_rn(skl, kLn2s, merged);
+            if (skl < kExactBelowS)                      // warp-uniform
+                skl = kept_kl_exact<false>(P, x, k_pad, lst, nl, tP4, tL, tE, tab, lane) + merged;
+        }
+        if (KLT) {
+            const float merged = Mt > 0.f ? Mt * logf(Mt / fmaxf(Mx, FLT_MIN)) : 0.f;
+            skt = __fmaf_rn(skt, kLn2s, merged);
+            if (skt < kExactBelowS)
+                skt = kept_kl_exact<true>(P, x, k_pad, lst, nl, tP4, tL, tE, tab, lane) + merged;
+        }
+        if (lane == 0) {
+            if (KL) okl[x] = skl;
+            if (TV) otv[x] = stv + unfix62(Mx_q >= Mt_q ? Mx_q - Mt_q : Mt_q - Mx_q);
+            if (KLT) okt[x] = skt;
+        }
+        kl = tv = kt = 0.f;
+        ks = 0;
+    };
+
+    using B0 = std::integral_constant<int, 0>;
+    using B1 = std::integral_constant<int, 1>;
+    auto advance = [&](int64_t &xx, int &gg) {
+        if (++gg == ngroups) {
+            gg = 0;
+            xx += nwarps;
+        }
+    };
+    int64_t x = warp;
+    int g = 0;
+    if (x >= n_v) return;
+    fetch(B0{}, x, g);
+    for (;;) {
+        int64_t xn = x;
+        int gn = g;
+        advance(xn, gn);
+        if (xn < n_v) fetch(B1{}, xn, gn);
+        compute(B0{}, g);
+        if (xn != x) finish(B0{}, x);
+        if (xn >= n_v) break;
+        x = xn;
+        g = gn;
+        advance(xn, gn);
+        if (xn < n_v) fetch(B0{}, xn, gn);
+        compute(B1{}, g);
+        if (xn != x) finish(B1{}, x);
+        if (xn >= n_v) break;
+        x = xn;
+        g = gn;
+    }
+}
+
+int sms_now() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+int64_t sparse_list_pitch(int64_t k_pad) { return (((k_pad >> 2) + 7) / 8) * 8; }
+
+size_t sparse_field_smem(int64_t k_pad) {
+    return 4 * (size_t)k_pad * sizeof(float) + (size_t)sparse_list_pitch(k_pad) * sizeof(uint16_t);
+}
+
+size_t sparse_stage_bytes(int64_t k_pad, int32_t T) {
+    return 4 * (size_t)T * k_pad * sizeof(float) + (size_t)T * sparse_list_pitch(k_pad) * sizeof(uint16_t) +
+           (size_t)T * sizeof(int32_t);
+}
+
+dd_status build_sparse_rows(DevMesh &m, double theta, cudaStream_t s, int64_t *kept_out, int64_t *blocks_out,
+                            std::string &err) {
+    if ((m.k_pad >> 2) > 65536) {
+        err = "sparse fields: more than 65,536 blocks of four boundary columns";
+        return DD_EINVAL;
+    }
+    long long *rowsum = nullptr;
+    unsigned long long *counts = nullptr;
+    cudaError_t e = cudaMalloc((void **)&rowsum, (size_t)m.n_v * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&counts, 2 * sizeof(unsigned long long));
+    unsigned long long hc[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        sparse_rows_kernel<<<(unsigned)((m.n_v + 7) / 8), 256, 0, s>>>(m.P, m.n_v, m.k_pad, (float)theta, rowsum,
+                                                                        counts);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (counts) cudaFree(counts);
+    if (e != cudaSuccess) {
+        if (rowsum) cudaFree(rowsum);
+        cudaGetLastError();
+        err = std::string("sparse fields: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA;
+    }
+    m.sp_rowsum = rowsum;
+    m.sp_theta = (float)theta;
+    m.sp_kept = (int64_t)hc[0];
+    m.sp_blocks = (int64_t)hc[1];
+    m.owned.push_back(rowsum);
+    m.bytes += m.n_v * (int64_t)sizeof(long long);
+    if (kept_out) *kept_out = m.sp_kept;
+    if (blocks_out) *blocks_out = m.sp_blocks;
+    return DD_OK;
+}
+
+void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *stage, int32_t T, float *out_kl,
+                          float *out_tv, float *out_klt, int *err_flag, cudaStream_t s) {
+    float *sP = reinterpret_cast<float *>(stage);
+    const float *sL = sP + (int64_t)T * m.k_pad;
+    const float *sE = sL + (int64_t)T * m.k_pad;
+    const float *sF = sE + (int64_t)T * m.k_pad;
+    const int64_t lp = sparse_list_pitch(m.k_pad);
+    uint16_t *sList = reinterpret_cast<uint16_t *>(const_cast<float *>(sF) + (int64_t)T * m.k_pad);
+    int32_t *sCount = reinterpret_cast<int32_t *>(sList + (int64_t)T * lp);
+    sparse_stage_kernel<<<(unsigned)T, 256, 0, s>>>(sP, m.k_pad, m.sp_theta, sList, lp, sCount);
+    const size_t smem = sparse_field_smem(m.k_pad);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+        if (per_sm < 1) per_sm = 1;
+        int64_t gx = (int64_t)sms_now() * per_sm / T;
+        const int64_t row_blocks = (m.n_v + 7) / 8;
+        if (gx < 1) gx = 1;
+        if (gx > row_blocks) gx = row_blocks;
+        kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(m.P, m.n_v, m.k_pad, sP, sL, sE, sF, sList, lp,
+                                                               sCount, m.sp_rowsum, d_targets, out_kl, out_tv,
+                                                               out_klt, err_flag);
+    };
+    // two blocks per lane and item, three CTAs per SM (measured: U = 4 or 8 with
+    // two CTAs per SM were slower; the pass is issue- and latency-bound)
+    const int mask = (out_kl ? 1 : 0) | (out_tv ? 2 : 0) | (out_klt ? 4 : 0);
+    switch (mask) {
+        case 1: go(sparse_field_kernel<2, true, false, false>); break;
+        case 2: go(sparse_field_kernel<2, false, true, false>); break;
+        case 3: go(sparse_field_kernel<2, true, true, false>); break;
+        case 4: go(sparse_field_kernel<2, false, false, true>); break;
+        case 5: go(sparse_field_kernel<2, true, false, true>); break;
+        case 6: go(sparse_field_kernel<2, false, true, true>); break;
+        default: go(sparse_field_kernel<2, true, true, true>); break;
+    }
+}

@@ -60,4 +60,13 @@ __device__ __forceinline__ void split_log(float p, const float *tab, float &lm, 
     lm = split_log_tail(mb, tab[j], tab[kLogTab + j]);
 }
 
+// Hardware base-2 logarithm (lg2.approx) of the mantissa m in [1, 2) of a
+// float bit pattern i; the result lies in [0, 1].  Its error over all 2^23
+// mantissas spans at most DD_FAST_LOG_SPREAD (measured by dd_check_fast_log).
+__device__ __forceinline__ float lg2_mant(int i) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__int_as_float((i & 0x007FFFFF) | 0x3F800000)));
+    return y;
+}
+
 }  // namespace

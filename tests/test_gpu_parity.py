@@ -219,7 +219,7 @@ def test_errors(env):
         dd.dd_distance(ctx, mid, [int(po.B[0])], dd.DD_F_KL, 0, out)
     assert e.value.status == dd.DD_EINVAL
     with pytest.raises(dd.DDError) as e:
-        dd.dd_distance(ctx, mid, [int(wl.targets[0])], 4, 0, out)
+        dd.dd_distance(ctx, mid, [int(wl.targets[0])], 8, 0, out)      # no such field bit
     assert e.value.status == dd.DD_EINVAL
     with pytest.raises(dd.DDError) as e:
         dd.dd_distance(ctx, 99, [int(wl.targets[0])], 1, 0, out)
