@@ -228,3 +228,29 @@ def test_errors(env):
         dd.dd_poisson_kernel(ctx, mid, 1e-30, 3)
     assert e.value.status == dd.DD_ENOTCONV
     dd.dd_unload_mesh(ctx, mid)
+
+
+def test_every_tile_shape_bit_identical(env, monkeypatch):
+    """The three tile shapes sum every (row, target) in the same order (32-term
+    chunks, compensated across chunks), so their fields are bit-identical; they
+    match the oracle."""
+    dd, ctx = env
+    wl, po, P = case("grid37")
+    mid = load(dd, ctx, wl.mesh)
+    dd.dd_set_poisson_kernel(ctx, mid, P)
+    targets = [int(t) for t in wl.targets]
+    outs = []
+    for shape in range(3):
+        monkeypatch.setenv("DD_TILE_SHAPE", str(shape))
+        out = torch.empty((2, len(targets), wl.mesh.n_v), dtype=torch.float32, device="cuda")
+        dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, out)
+        dd.dd_sync(ctx)
+        outs.append(out.cpu().numpy())
+    monkeypatch.delenv("DD_TILE_SHAPE")
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    for a, t in enumerate(targets):
+        assert field_error(outs[2][0, a], kl_field_fast(P, P[t])) <= TOL_FP32
+        assert field_error(outs[2][1, a], tv_field(P, P[t])) <= TOL_FP32
+        assert outs[2][0, a, t] == 0.0 and outs[2][1, a, t] == 0.0
+    dd.dd_unload_mesh(ctx, mid)
