@@ -35,6 +35,9 @@ T_BATCH, S_PER_TARGET, MAX_PTS = 64, 256, 1024
 # kernels one dd_query step launches: target staging, field tile, triangle rates,
 # vertex decisions, path walk
 STEP_LAUNCHES = 5
+# DRAM bytes (read + write) of one field_tile_kernel launch of this step, from an
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); P is read once
+TILE_TRAFFIC_BYTES = 78423296        # 75,715,328 read + 2,707,968 written (4 n k_pad = 74.7 MB of P)
 N_BATCHES = 8
 
 
@@ -197,6 +200,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
+    dd.dd_kernel_timing(ctx, 1)          # per-kernel CUDA events on this stream, live over the timed steps
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))
@@ -205,6 +209,7 @@ def run_ours(args, rank, world, local_rank):
         ends[i].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    kernel_ms = dd.dd_kernel_timing(ctx, 0)
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_ms = float(sum(step_ms))
@@ -240,19 +245,26 @@ def run_ours(args, rank, world, local_rank):
     fields_per_step = 2 * T
     value = world * fields_per_step * args.steps / (dev_ms / 1e3)
     pk, pk_kind = peaks()
-    # dominant kernel and its roofline
+    # dominant kernel (largest device time over the timed steps) and its roofline
     sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    if field_ms >= trace_ms:
+    tot = sum(ms for _, ms in kernel_ms.values()) or 1.0
+    kernels = {name: {"launches": n, "ms_per_launch": round(ms / max(n, 1), 4), "share": round(ms / tot, 4)}
+               for name, (n, ms) in sorted(kernel_ms.items(), key=lambda kv: -kv[1][1])}
+    dom = max(kernel_ms, key=lambda k: kernel_ms[k][1]) if kernel_ms else "field_tile_kernel"
+    dom_ms = kernel_ms[dom][1] / max(kernel_ms[dom][0], 1) if kernel_ms else field_ms
+    if dom == "field_tile_kernel":
         flops = 8.0 * n_v * k * T            # KL: 2 FADD + 2 FFMA(=4 flop), TV: 2 FADD, per (x, b, t)
-        achieved = flops / (field_ms / 1e3) / 1e12
+        achieved = flops / (dom_ms / 1e3) / 1e12
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": "field_tile_kernel", "bound": "alu", "achieved": round(achieved, 3),
-                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock sampled)"}
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": TILE_TRAFFIC_BYTES,
+                "algorithmic_flop": flops, "ms_per_launch": round(dom_ms, 4),
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock sampled)",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, this workload"}
     else:
         paths = T * S
-        roof = {"kernel": "trace_kernel", "bound": "latency", "achieved": round(paths / (trace_ms / 1e3), 1),
-                "peak": None, "unit": "paths/s", "frac": None, "traffic": None}
+        roof = {"kernel": dom, "bound": "latency", "achieved": round(paths / (dom_ms / 1e3), 1),
+                "peak": None, "unit": "paths/s", "frac": None, "traffic": None, "ms_per_launch": round(dom_ms, 4)}
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
@@ -270,7 +282,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "peaks": pk_kind,
         "e2e": {"value": round(world * fields_per_step * e2e_steps / e2e_s, 1), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": STEP_LAUNCHES * args.steps,
+        "gpu_launches": int(sum(n for n, _ in kernel_ms.values())) or STEP_LAUNCHES * args.steps,
+        "kernels": kernels,
         "clocks": clocks,
     }
     if args.stream and args.section == "all":

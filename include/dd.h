@@ -343,6 +343,17 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
  * terminated) into buf (may be NULL) and returns the full length. */
 int32_t dd_tuning_table(char *buf, int32_t len);
 
+/* Per-kernel device time on the context's stream (an observability hook; the
+ * paper has no counterpart).  While enabled, every kernel the library
+ * launches on that stream is bracketed by two CUDA events; the totals per
+ * kernel name are folded in when read.
+ *   mode  1: enable (or reset the totals); 2: read; 0: read, then disable
+ *   buf   NULL or host text, one line per kernel: "name launches total_ms"
+ * Returns the text length + 1 (the size buf needs), DD_EINVAL for a bad mode.
+ * Reading synchronizes with the recorded events.  Keyed by the stream the
+ * context had when timing was enabled. */
+int32_t dd_kernel_timing(dd_ctx *ctx, int32_t mode, char *buf, int32_t len);
+
 /* ---- query server: continuous batching of path queries ------------------
  * A query asks for the paths from S sources to one interior target of a
  * loaded mesh, traced on the target's KL field (Section IV).  A server runs a

@@ -3,6 +3,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -222,6 +226,87 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
 int popcount2(uint32_t f) { return ((f & DD_F_KL) ? 1 : 0) + ((f & DD_F_TV) ? 1 : 0) + ((f & DD_F_KLT) ? 1 : 0); }
 
 }  // namespace
+
+namespace {
+
+struct KTimer {
+    std::vector<std::tuple<const char *, cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<cudaEvent_t> pool;
+    std::map<std::string, std::pair<int64_t, double>> totals;   // launches, total ms
+};
+
+std::mutex g_kt_mutex;
+std::map<cudaStream_t, KTimer> g_kt;
+std::atomic<int> g_kt_on{0};
+
+cudaEvent_t kt_event(KTimer &t) {
+    if (!t.pool.empty()) {
+        cudaEvent_t e = t.pool.back();
+        t.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void kt_fold(KTimer &t) {
+    for (auto &m : t.pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(std::get<2>(m)) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, std::get<1>(m), std::get<2>(m)) == cudaSuccess) {
+            auto &tot = t.totals[std::get<0>(m)];
+            tot.first += 1;
+            tot.second += ms;
+        } else {
+            cudaGetLastError();
+        }
+        t.pool.push_back(std::get<1>(m));
+        t.pool.push_back(std::get<2>(m));
+    }
+    t.pending.clear();
+}
+
+}  // namespace
+
+KMark::KMark(const char *n, cudaStream_t s) {
+    if (!g_kt_on.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lock(g_kt_mutex);
+    auto it = g_kt.find(s);
+    if (it == g_kt.end()) return;
+    cudaEvent_t e = kt_event(it->second);
+    if (!e) return;
+    if (cudaEventRecord(e, s) != cudaSuccess) {
+        cudaGetLastError();
+        it->second.pool.push_back(e);
+        return;
+    }
+    name = n;
+    stream = s;
+    a = e;
+}
+
+KMark::~KMark() {
+    if (!a) return;
+    std::lock_guard<std::mutex> lock(g_kt_mutex);
+    auto it = g_kt.find(stream);
+    if (it == g_kt.end()) {
+        cudaEventDestroy(a);
+        return;
+    }
+    cudaEvent_t b = kt_event(it->second);
+    if (!b || cudaEventRecord(b, stream) != cudaSuccess) {
+        cudaGetLastError();
+        it->second.pool.push_back(a);
+        if (b) it->second.pool.push_back(b);
+        return;
+    }
+    it->second.pending.emplace_back(name, a, b);
+    if (it->second.pending.size() > 4096) kt_fold(it->second);
+}
 
 extern "C" {
 
@@ -1033,6 +1118,43 @@ dd_status dd_check_fast_log(double *spread) {
     } catch (...) {
         return DD_ENOMEM;
     }
+}
+
+int32_t dd_kernel_timing(dd_ctx *ctx, int32_t mode, char *buf, int32_t len) {
+    if (!ctx || mode < 0 || mode > 2) return DD_EINVAL;
+    std::lock_guard<std::mutex> lock(g_kt_mutex);
+    auto it = g_kt.find(ctx->stream);
+    if (mode == 1) {
+        if (it == g_kt.end()) {
+            g_kt[ctx->stream];
+            g_kt_on.fetch_add(1);
+        } else {
+            kt_fold(it->second);
+            it->second.totals.clear();
+        }
+        return 0;
+    }
+    std::string out;
+    if (it != g_kt.end()) {
+        kt_fold(it->second);
+        for (auto &kv : it->second.totals) {
+            char line[160];
+            std::snprintf(line, sizeof line, "%s %lld %.6f\n", kv.first.c_str(), (long long)kv.second.first,
+                          kv.second.second);
+            out += line;
+        }
+        if (mode == 0) {
+            for (cudaEvent_t e : it->second.pool) cudaEventDestroy(e);
+            g_kt.erase(it);
+            g_kt_on.fetch_sub(1);
+        }
+    }
+    if (buf && len > 0) {
+        const size_t n = std::min<size_t>(out.size(), (size_t)len - 1);
+        std::memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return (int32_t)out.size() + 1;
 }
 
 int32_t dd_tuning_table(char *buf, int32_t len) {

@@ -173,7 +173,10 @@ dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *
         const int64_t rows_blocks = (n_v + 7) / 8;
         if (gx < 1) gx = 1;
         if (gx > rows_blocks) gx = rows_blocks;
-        kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, q, out);
+        {
+            KMark km_("fdiv_kernel", s);
+            kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, q, out);
+        }
     };
     switch (family) {
         case DD_DIV_CHI2: go(fdiv_kernel<kChi2>); break;

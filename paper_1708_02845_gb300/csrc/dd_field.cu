@@ -456,7 +456,10 @@ void launch_tile(const float *P, int64_t n_v, int64_t k_pad, const float *sP, co
     dim3 g((unsigned)((n_v + TM - 1) / TM), (unsigned)((T + TN - 1) / TN));
     auto kern = field_tile_kernel<TM, TN, RM, CN>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
-    kern<<<g, 256, S::smem_bytes, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv);
+    {
+        KMark km_("field_tile_kernel", s);
+        kern<<<g, 256, S::smem_bytes, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv);
+    }
 }
 
 int g_num_sms = 0;
@@ -612,7 +615,10 @@ void launch_stage_targets(const float *P, int64_t k_pad, int64_t /*k*/, const in
     float *sE = sL + (int64_t)T * k_pad;
     float *sF = sE + (int64_t)T * k_pad;
     dim3 g((unsigned)((k_pad + 255) / 256), (unsigned)T);
-    stage_targets_kernel<<<g, 256, 0, s>>>(P, k_pad, targets, T, sP, sL, sE, sF);
+    {
+        KMark km_("stage_targets_kernel", s);
+        stage_targets_kernel<<<g, 256, 0, s>>>(P, k_pad, targets, T, sP, sL, sE, sF);
+    }
 }
 
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, float *out_kl,
@@ -633,8 +639,11 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
         int64_t grid_x = (int64_t)num_sms() * per_sm / T;
         if (grid_x < 1) grid_x = 1;
         if (grid_x > row_blocks) grid_x = row_blocks;
-        kern<<<dim3((unsigned)grid_x, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv,
-                                                                   err_flag);
+        {
+            KMark km_("field_stream_kernel", s);
+            kern<<<dim3((unsigned)grid_x, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv,
+                                                                       err_flag);
+        }
         return;
     }
     const int v = tune_variant(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
@@ -654,7 +663,10 @@ void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, con
                         const int32_t *d_targets, int32_t n_targets, int64_t k_max, cudaStream_t s) {
     if (n_targets <= 0) return;
     dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(8, (k_max + 255) / 256)), (unsigned)n_targets);
-    batch_stage_kernel<<<g, 256, 0, s>>>(d_probs, d_tprob, d_tlocal, d_targets, k_max);
+    {
+        KMark km_("batch_stage_kernel", s);
+        batch_stage_kernel<<<g, 256, 0, s>>>(d_probs, d_tprob, d_tlocal, d_targets, k_max);
+    }
 }
 
 void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, int32_t n_items, int32_t *d_counter,
@@ -668,7 +680,10 @@ void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, 
     int64_t grid = (int64_t)num_sms() * per_sm;
     if (grid > n_items) grid = n_items;
     cudaMemsetAsync(d_counter, 0, sizeof(int32_t), s);
-    batch_tile_kernel<<<(unsigned)grid, 256, smem, s>>>(d_probs, d_items, n_items, d_counter);
+    {
+        KMark km_("batch_tile_kernel", s);
+        batch_tile_kernel<<<(unsigned)grid, 256, smem, s>>>(d_probs, d_items, n_items, d_counter);
+    }
 }
 
 std::string tuning_table() {

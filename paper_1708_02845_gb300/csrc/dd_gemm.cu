@@ -342,7 +342,10 @@ dd_status launch_kl_gemm(const DevMesh &m, const int32_t *d_targets, int32_t T, 
     __nv_bfloat16 *bhi = reinterpret_cast<__nv_bfloat16 *>(scratch);
     __nv_bfloat16 *blo = bhi + (size_t)T * kb;
     dim3 gs((unsigned)((kb + 255) / 256), (unsigned)T);
-    split_targets_kernel<<<gs, 256, 0, s>>>(m.P, m.k, m.k_pad, kb, d_targets, T, bhi, blo);
+    {
+        KMark km_("split_targets_kernel", s);
+        split_targets_kernel<<<gs, 256, 0, s>>>(m.P, m.k, m.k_pad, kb, d_targets, T, bhi, blo);
+    }
     CUtensorMap tAhi, tAlo, tBhi, tBlo;
     if (!make_map(&tAhi, m.p_hi, m.n_v, kb, BM) || !make_map(&tAlo, m.p_lo, m.n_v, kb, BM) ||
         !make_map(&tBhi, bhi, T, kb, BN) || !make_map(&tBlo, blo, T, kb, BN)) {
@@ -360,7 +363,10 @@ dd_status launch_kl_gemm(const DevMesh &m, const int32_t *d_targets, int32_t T, 
     g.kblocks = (int32_t)(kb / BK);
     g.err = err_flag;
     dim3 grid((unsigned)((T + BN - 1) / BN), (unsigned)((m.n_v + BM - 1) / BM));
-    kl_gemm_kernel<<<grid, 192, SMEM_BYTES, s>>>(tAhi, tAlo, tBhi, tBlo, g);
+    {
+        KMark km_("kl_gemm_kernel", s);
+        kl_gemm_kernel<<<grid, 192, SMEM_BYTES, s>>>(tAhi, tAlo, tBhi, tBlo, g);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("KL GEMM launch failed: ") + cudaGetErrorString(e);

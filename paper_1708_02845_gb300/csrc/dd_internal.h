@@ -188,6 +188,20 @@ struct dd_ctx {
     cudaEvent_t pinned_free[S_COUNT] = {};    // recorded after the last upload from pinned[id]
 };
 
+// Per-kernel device time (dd_kernel_timing): while timing is enabled for a
+// stream, a KMark around a launch on that stream records a CUDA event before
+// and after it; totals per kernel name are folded in when read.  Without
+// timing enabled a KMark costs one relaxed atomic load.
+struct KMark {
+    KMark(const char *name, cudaStream_t s);
+    ~KMark();
+    KMark(const KMark &) = delete;
+    KMark &operator=(const KMark &) = delete;
+    const char *name = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t a = nullptr;
+};
+
 #define DD_CUDA_TRY(expr, errstr)                                                   \
     do {                                                                            \
         cudaError_t e__ = (expr);                                                   \

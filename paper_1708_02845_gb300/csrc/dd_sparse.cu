@@ -450,7 +450,10 @@ void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *st
     const int64_t lp = sparse_list_pitch(m.k_pad);
     uint16_t *sList = reinterpret_cast<uint16_t *>(const_cast<float *>(sF) + (int64_t)T * m.k_pad);
     int32_t *sCount = reinterpret_cast<int32_t *>(sList + (int64_t)T * lp);
-    sparse_stage_kernel<<<(unsigned)T, 256, 0, s>>>(sP, m.k_pad, m.sp_theta, sList, lp, sCount);
+    {
+        KMark km_("sparse_stage_kernel", s);
+        sparse_stage_kernel<<<(unsigned)T, 256, 0, s>>>(sP, m.k_pad, m.sp_theta, sList, lp, sCount);
+    }
     const size_t smem = sparse_field_smem(m.k_pad);
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -461,9 +464,12 @@ void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *st
         const int64_t row_blocks = (m.n_v + 7) / 8;
         if (gx < 1) gx = 1;
         if (gx > row_blocks) gx = row_blocks;
-        kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(m.P, m.n_v, m.k_pad, sP, sL, sE, sF, sList, lp,
-                                                               sCount, m.sp_rowsum, d_targets, out_kl, out_tv,
-                                                               out_klt, err_flag);
+        {
+            KMark km_("sparse_field_kernel", s);
+            kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(m.P, m.n_v, m.k_pad, sP, sL, sE, sF, sList, lp,
+                                                                   sCount, m.sp_rowsum, d_targets, out_kl, out_tv,
+                                                                   out_klt, err_flag);
+        }
     };
     // two blocks per lane and item, three CTAs per SM (measured: U = 4 or 8 with
     // two CTAs per SM were slower; the pass is issue- and latency-bound)

@@ -466,7 +466,7 @@ struct TraceParams {
     int32_t *out_len, *out_status;
 };
 
-__global__ void __launch_bounds__(64) trace_kernel(const TraceParams p) {
+__global__ void __launch_bounds__(128) trace_kernel(const TraceParams p) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = gid < p.total;       // padding lanes stay in the warp's walk loop, idle
     const int64_t id = active ? gid : 0;
@@ -577,14 +577,23 @@ void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, c
     p.out_len = out_len;
     p.out_status = out_status;
     if (p.total == 0) return;
-    rates_kernel<<<(unsigned)((m.n_t * T + 255) / 256), 256, 0, s>>>(m.gphi, m.trec, m.n_t, T, fields, field_stride,
-                                                                      rates);
+    {
+        KMark km_("rates_kernel", s);
+        rates_kernel<<<(unsigned)((m.n_t * T + 255) / 256), 256, 0, s>>>(m.gphi, m.trec, m.n_t, T, fields, field_stride,
+                                                                          rates);
+    }
     if (dense) {
         const int64_t warps = m.n_v * ((T + 31) / 32);
-        vertex_decision_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(p.d, T, fields, field_stride, rates,
-                                                                            targets, dec);
+        {
+            KMark km_("vertex_decision_kernel", s);
+            vertex_decision_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(p.d, T, fields, field_stride, rates,
+                                                                                targets, dec);
+        }
     }
-    trace_kernel<<<(unsigned)((p.total + 63) / 64), 64, 0, s>>>(p);
+    {
+        KMark km_("trace_kernel", s);
+        trace_kernel<<<(unsigned)((p.total + 127) / 128), 128, 0, s>>>(p);   // 128: measured best of 64/128/256
+    }
 }
 
 size_t batch_trace_dom_bytes() { return sizeof(BatchTraceDom); }
@@ -610,9 +619,15 @@ void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t
     const int64_t total = d_path_target ? n_paths : (int64_t)n_targets * S;
     if (total == 0) return;
     dim3 gr((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_nt + 255) / 256)), (unsigned)n_targets);
-    batch_rates_kernel<<<gr, 256, 0, s>>>(doms, d_tdom, d_tloc);
+    {
+        KMark km_("batch_rates_kernel", s);
+        batch_rates_kernel<<<gr, 256, 0, s>>>(doms, d_tdom, d_tloc);
+    }
     (void)max_nv;
-    batch_trace_kernel<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(doms, d_tdom, d_tloc, d_targets, d_sources,
-                                                                    d_path_target, total, S, max_pts, out_xy, out_len,
-                                                                    out_status);
+    {
+        KMark km_("batch_trace_kernel", s);
+        batch_trace_kernel<<<(unsigned)((total + 63) / 64), 64, 0, s>>>(doms, d_tdom, d_tloc, d_targets, d_sources,
+                                                                        d_path_target, total, S, max_pts, out_xy, out_len,
+                                                                        out_status);
+    }
 }

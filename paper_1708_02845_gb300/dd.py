@@ -60,6 +60,7 @@ _SIGS = {
     "dd_distance_noalloc": (_i32, [_p, _i64, _i64, _p, _i32, _u32, _p, _p]),
     "dd_query_batch": (_i32, [_p, _i32, _p, _p, _p, _p, _i32, _u32, _u32, _i32, _p, _p, _p, _p]),
     "dd_tuning_table": (_i32, [ctypes.c_char_p, _i32]),
+    "dd_kernel_timing": (_i32, [_p, _i32, ctypes.c_char_p, _i32]),
     "dd_check_fast_log": (_i32, [ctypes.POINTER(ctypes.c_double)]),
     "dd_multigrid_check": (_i32, [_p, _p, _p, _i64, _p, _p, _f64, _i32, _p, _p]),
     "dd_server_create": (_i32, [_p, _i64, _i32, _i32, _i32, ctypes.POINTER(_p)]),
@@ -346,3 +347,25 @@ def dd_server_wait_idle(sv, timeout_s: float = 60.0):
 
 def dd_server_destroy(sv):
     lib.dd_server_destroy(sv)
+
+
+def dd_kernel_timing(ctx, mode: int) -> dict:
+    """mode 1: enable/reset, 2: read, 0: read and disable; returns
+    {kernel name: (launches, total ms)} of what was read."""
+    if mode == 1:
+        st = lib.dd_kernel_timing(ctx, 1, None, 0)
+        if st < 0:
+            raise DDError(st, "dd_kernel_timing")
+        return {}
+    n = lib.dd_kernel_timing(ctx, 2, None, 0)
+    if n < 0:
+        raise DDError(n, "dd_kernel_timing")
+    buf = ctypes.create_string_buffer(n + 1)
+    lib.dd_kernel_timing(ctx, 2, buf, len(buf))
+    if mode == 0:
+        lib.dd_kernel_timing(ctx, 0, None, 0)
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.rsplit(" ", 2)
+        out[name] = (int(cnt), float(ms))
+    return out

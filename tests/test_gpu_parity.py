@@ -254,3 +254,29 @@ def test_every_tile_shape_bit_identical(env, monkeypatch):
         assert field_error(outs[2][1, a], tv_field(P, P[t])) <= TOL_FP32
         assert outs[2][0, a, t] == 0.0 and outs[2][1, a, t] == 0.0
     dd.dd_unload_mesh(ctx, mid)
+
+
+def test_kernel_timing_hook(env):
+    """dd_kernel_timing: per-kernel CUDA-event totals of the launches on the
+    context's stream, one entry per kernel of a dd_query, none once disabled."""
+    dd, ctx = env
+    wl, po, P = case("grid37")
+    mid = load(dd, ctx, wl.mesh)
+    dd.dd_set_poisson_kernel(ctx, mid, P)
+    targets = [int(t) for t in wl.targets[:8]]
+    src = np.asarray(wl.sources)[:8]
+    n = wl.mesh.n_v
+    f = torch.empty((2, 8, n), dtype=torch.float32, device="cuda")
+    xy = torch.empty((8 * src.shape[1], 512, 2), dtype=torch.float32, device="cuda")
+    ln = torch.empty(8 * src.shape[1], dtype=torch.int32, device="cuda")
+    st = torch.empty(8 * src.shape[1], dtype=torch.int32, device="cuda")
+    dd.dd_query(ctx, mid, targets, src, 3, dd.DD_PREC_FP32, dd.DD_F_KL, 512, f, xy, ln, st)   # tunes once
+    dd.dd_kernel_timing(ctx, 1)
+    for _ in range(3):
+        dd.dd_query(ctx, mid, targets, src, 3, dd.DD_PREC_FP32, dd.DD_F_KL, 512, f, xy, ln, st)
+    got = dd.dd_kernel_timing(ctx, 0)
+    for name in ("stage_targets_kernel", "field_tile_kernel", "rates_kernel", "trace_kernel"):
+        assert got[name][0] == 3 and got[name][1] > 0.0, (name, got)
+    dd.dd_query(ctx, mid, targets, src, 3, dd.DD_PREC_FP32, dd.DD_F_KL, 512, f, xy, ln, st)
+    assert dd.dd_kernel_timing(ctx, 2) == {}
+    dd.dd_unload_mesh(ctx, mid)
