@@ -235,10 +235,11 @@ def run_ours(args, rank, world, local_rank):
         tg, sr = batches[i % len(batches)]
         dd.dd_query(ctx, mid, tg, sr, 3, 0, 1, MAX_PTS, hf, hxy, hl, hs)
     e2e_s = time.perf_counter() - e0
-    # the library copies, per chunk of 512 paths, the rows up to the chunk's longest
-    # path (counted on the last step's lengths)
+    # into pinned host buffers the library moves exactly each path's defined
+    # prefix (len points), plus the lengths and statuses (counted on the last
+    # step's lengths)
     ln = hl.numpy()
-    path_bytes = sum(int(ln[c:c + 512].max()) * 8 * len(ln[c:c + 512]) for c in range(0, len(ln), 512))
+    path_bytes = int(ln.astype(np.int64).sum()) * 8
     h2d = T * 4 + T * S * 4
     d2h = 2 * T * n_v * 4 + T * S * 8 + path_bytes
 

@@ -91,6 +91,28 @@ int pointer_space(const dd_ctx *ctx, const void *p) {
     return 0;
 }
 
+// The device address of page-locked (pinned) host memory, which kernels can
+// write directly (over NVLink-C2C on Grace), or nullptr for other memory.
+void *mapped_alias(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+dd_status ensure_side(dd_ctx *ctx) {
+    if (ctx->side) return DD_OK;
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->side_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->side_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, DD_ECUDA, "side stream creation failed");
+    }
+    return DD_OK;
+}
+
 dd_status get_mesh(dd_ctx *ctx, int32_t mesh, DevMesh **out) {
     if (!ctx) return DD_EINVAL;
     if (mesh < 0 || mesh >= (int32_t)ctx->meshes.size() || !ctx->meshes[mesh].live)
@@ -352,6 +374,9 @@ void dd_destroy(dd_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto &s : ctx->meshes)
         if (s.live) free_mesh(s.dev);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (cudaEvent_t e : ctx->side_ev)
+        if (e) cudaEventDestroy(e);
     for (int i = 0; i < S_COUNT; ++i)
         if (ctx->scratch[i]) cudaFree(ctx->scratch[i]);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -670,17 +695,38 @@ dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32
     const size_t n = (size_t)T * S;
     float2 *dxy = reinterpret_cast<float2 *>(out_xy);
     int32_t *dlen = out_len, *dst = out_status;
+    // Host outputs.  Pinned (page-locked) memory has a device address: the
+    // walk writes lengths and statuses there itself, and one copy kernel
+    // moves each path's defined prefix from device scratch into it with
+    // coalesced 16-byte stores (over NVLink-C2C on Grace; measured 0.99 ms
+    // per grid140 step against 1.26 ms for the copy-engine path below, while
+    // the walk storing points straight into host memory took 1.93 ms).
+    // Pageable memory goes through device scratch and the copy engine.
+    float2 *xy_alias = nullptr;
     if (sx == 0) {
+        xy_alias = reinterpret_cast<float2 *>(mapped_alias(out_xy));
         if ((st = ensure_scratch(ctx, S_XY, n * max_pts * sizeof(float2))) != DD_OK) return st;
         dxy = reinterpret_cast<float2 *>(ctx->scratch[S_XY]);
     }
+    const bool xy_copy = sx == 0 && !xy_alias;
+    bool len_direct = false, st_direct = false;
     if (sl == 0) {
-        if ((st = ensure_scratch(ctx, S_LEN, n * sizeof(int32_t))) != DD_OK) return st;
-        dlen = reinterpret_cast<int32_t *>(ctx->scratch[S_LEN]);
+        if (void *a = mapped_alias(out_len)) {
+            dlen = reinterpret_cast<int32_t *>(a);
+            len_direct = true;
+        } else {
+            if ((st = ensure_scratch(ctx, S_LEN, n * sizeof(int32_t))) != DD_OK) return st;
+            dlen = reinterpret_cast<int32_t *>(ctx->scratch[S_LEN]);
+        }
     }
     if (ss == 0) {
-        if ((st = ensure_scratch(ctx, S_STATUS, n * sizeof(int32_t))) != DD_OK) return st;
-        dst = reinterpret_cast<int32_t *>(ctx->scratch[S_STATUS]);
+        if (void *a = mapped_alias(out_status)) {
+            dst = reinterpret_cast<int32_t *>(a);
+            st_direct = true;
+        } else {
+            if ((st = ensure_scratch(ctx, S_STATUS, n * sizeof(int32_t))) != DD_OK) return st;
+            dst = reinterpret_cast<int32_t *>(ctx->scratch[S_STATUS]);
+        }
     }
     if (edges) {
         launch_edge_paths(m, d_fields, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
@@ -694,13 +740,17 @@ dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32
                      ctx->scratch[S_GRAD], ctx->stream);
     }
     CK(cudaGetLastError(), "trace kernel launch");
-    bool host = false;
-    if (sx == 0) {
+    if (xy_alias) {
+        launch_copy_paths(dxy, dlen, (int64_t)n, max_pts, xy_alias, ctx->stream);
+        CK(cudaGetLastError(), "path copy kernel launch");
+    }
+    bool host = xy_alias || len_direct || st_direct;
+    if (xy_copy) {
         // Only each path's prefix of len points is defined: copy, per chunk of
         // paths, the rows up to the chunk's longest path (one strided copy
         // each) instead of all max_pts points of every path.
         std::vector<int32_t> lens(n);
-        int32_t *hl = sl == 0 ? out_len : lens.data();
+        int32_t *hl = (sl == 0 && !len_direct) ? out_len : lens.data();
         CK(cudaMemcpyAsync(hl, dlen, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "copy lengths");
         CK(cudaStreamSynchronize(ctx->stream), "path lengths");
         const size_t chunk = 512, pitch = (size_t)max_pts * sizeof(float2);
@@ -715,11 +765,11 @@ dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32
                "copy paths");
         }
         host = true;
-    } else if (sl == 0) {
+    } else if (sl == 0 && !len_direct) {
         CK(cudaMemcpyAsync(out_len, dlen, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "copy lengths");
         host = true;
     }
-    if (ss == 0) {
+    if (ss == 0 && !st_direct) {
         CK(cudaMemcpyAsync(out_status, dst, n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
            "copy statuses");
         host = true;
@@ -872,15 +922,23 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
         st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst);
         if (st != DD_OK) return st;
         const float *trace_field = field_slot(dst, f_mask, trace_f, (int64_t)T * m->n_v);
-        if (sf == 0)
-            CK(cudaMemcpyAsync(out_fields, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy fields");
-        st = trace_into(ctx, *m, trace_field, targets, T, sources, S, max_pts, out_xy, out_len, out_status, true);
-        if (st != DD_OK) return st;
         if (sf == 0) {
+            // the fields go back on a side stream while the paths are traced
+            if ((st = ensure_side(ctx)) != DD_OK) return st;
+            CK(cudaEventRecord(ctx->side_ev[0], ctx->stream), "fields ready");
+            CK(cudaStreamWaitEvent(ctx->side, ctx->side_ev[0], 0), "side wait");
+            CK(cudaMemcpyAsync(out_fields, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->side), "copy fields");
+            CK(cudaEventRecord(ctx->side_ev[1], ctx->side), "fields copied");
+        }
+        st = trace_into(ctx, *m, trace_field, targets, T, sources, S, max_pts, out_xy, out_len, out_status, true);
+        if (sf == 0) {
+            // the next call may reuse the field scratch: the copy must be done
+            CK(cudaEventSynchronize(ctx->side_ev[1]), "query fields");
+            if (st != DD_OK) return st;
             CK(cudaStreamSynchronize(ctx->stream), "query");
             return check_kernel_flag(ctx);
         }
-        return DD_OK;
+        return st;
     } catch (...) {
         return set_err(ctx, DD_ENOMEM, "host allocation failed");
     }

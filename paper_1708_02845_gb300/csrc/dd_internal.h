@@ -124,6 +124,12 @@ void launch_edge_paths(const DevMesh &m, const float *fields, const int32_t *tar
 dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, int32_t family,
                       double param, float *out, cudaStream_t s, std::string &err);
 
+// Copy the defined prefix of every path (len[i] points of row i, pitch max_pts)
+// from device memory to another buffer (e.g. pinned host memory seen through its
+// device address), one warp per path, 16-byte stores (dd_trace.cu).
+void launch_copy_paths(const float2 *src, const int32_t *len, int64_t n, int32_t max_pts, float2 *dst,
+                       cudaStream_t s);
+
 // Sparse fields (dd_sparse.cu, Section V).  build_sparse_rows fills the sp_*
 // members of m from m.P (the caller frees earlier ones).  The sparse stage is
 // the dense stage (4 x T x k_pad floats, filled by launch_stage_targets)
@@ -186,6 +192,8 @@ struct dd_ctx {
     void *pinned[S_COUNT] = {};               // host staging for index uploads, one per scratch id
     size_t pinned_cap[S_COUNT] = {};
     cudaEvent_t pinned_free[S_COUNT] = {};    // recorded after the last upload from pinned[id]
+    cudaStream_t side = nullptr;              // copies that overlap the main stream's kernels
+    cudaEvent_t side_ev[2] = {};
 };
 
 // Per-kernel device time (dd_kernel_timing): while timing is enabled for a

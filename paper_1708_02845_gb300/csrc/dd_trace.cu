@@ -631,3 +631,45 @@ void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t
                                                                         out_status);
     }
 }
+
+namespace {
+// one warp per path: its first len points.  MODE 2: point pairs as 16-byte
+// stores (rows 16-byte aligned at both ends); 1: one point (8 bytes) per
+// store; 0: one float per store (any 4-byte aligned buffer).
+template <int MODE>
+__global__ void copy_paths_kernel(const float2 *__restrict__ src, const int32_t *__restrict__ len, int64_t n,
+                                  int32_t max_pts, float2 *__restrict__ dst) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const int L = min(max(len[w], 0), max_pts);
+    const float2 *a = src + w * (int64_t)max_pts;
+    float2 *b = dst + w * (int64_t)max_pts;
+    if (MODE == 2) {
+        const float4 *a4 = reinterpret_cast<const float4 *>(a);
+        float4 *b4 = reinterpret_cast<float4 *>(b);
+        for (int i = lane; 2 * i + 1 < L; i += 32) b4[i] = __ldcs(a4 + i);
+        if ((L & 1) && lane == 0) b[L - 1] = a[L - 1];
+    } else if (MODE == 1) {
+        for (int i = lane; i < L; i += 32) b[i] = a[i];
+    } else {
+        const float *af = reinterpret_cast<const float *>(a);
+        float *bf = reinterpret_cast<float *>(b);
+        for (int i = lane; i < 2 * L; i += 32) bf[i] = af[i];
+    }
+}
+}  // namespace
+
+void launch_copy_paths(const float2 *src, const int32_t *len, int64_t n, int32_t max_pts, float2 *dst,
+                       cudaStream_t s) {
+    if (n <= 0) return;
+    const uintptr_t d = reinterpret_cast<uintptr_t>(dst);
+    const unsigned grid = (unsigned)((n + 7) / 8);
+    KMark km_("copy_paths_kernel", s);
+    if ((max_pts & 1) == 0 && (d & 15) == 0)
+        copy_paths_kernel<2><<<grid, 256, 0, s>>>(src, len, n, max_pts, dst);
+    else if ((d & 7) == 0)
+        copy_paths_kernel<1><<<grid, 256, 0, s>>>(src, len, n, max_pts, dst);
+    else
+        copy_paths_kernel<0><<<grid, 256, 0, s>>>(src, len, n, max_pts, dst);
+}

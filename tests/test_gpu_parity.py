@@ -280,3 +280,41 @@ def test_kernel_timing_hook(env):
     dd.dd_query(ctx, mid, targets, src, 3, dd.DD_PREC_FP32, dd.DD_F_KL, 512, f, xy, ln, st)
     assert dd.dd_kernel_timing(ctx, 2) == {}
     dd.dd_unload_mesh(ctx, mid)
+
+
+def test_query_host_output_kinds(env):
+    """dd_query into device memory, pinned host memory (paths moved by the copy
+    kernel, also at a 4-byte-aligned offset) and pageable host memory: the
+    same fields, lengths, statuses and path prefixes."""
+    dd, ctx = env
+    wl, po, P = case("grid37")
+    mid = load(dd, ctx, wl.mesh)
+    dd.dd_set_poisson_kernel(ctx, mid, P)
+    targets = [int(t) for t in wl.targets[:6]]
+    src = np.asarray(wl.sources)[:6]
+    n, S, mp = wl.mesh.n_v, src.shape[1], 301            # odd max_pts: rows not 16-byte aligned
+
+    def run(kind):
+        if kind == "device":
+            mk = lambda shape, dt: torch.empty(shape, dtype=dt, device="cuda")
+        elif kind == "pageable":
+            mk = lambda shape, dt: torch.empty(shape, dtype=dt)
+        else:
+            def mk(shape, dt, off=(kind == "pinned_offset")):
+                flat = torch.empty(int(np.prod(shape)) + 1, dtype=dt).pin_memory()
+                return flat[1:].view(shape) if off else flat[:-1].view(shape)
+        f = mk((2, 6, n), torch.float32)
+        xy = mk((6 * S, mp, 2), torch.float32)
+        ln = mk((6 * S,), torch.int32)
+        st = mk((6 * S,), torch.int32)
+        dd.dd_query(ctx, mid, targets, src, 3, dd.DD_PREC_FP32, dd.DD_F_KL, mp, f, xy, ln, st)
+        dd.dd_sync(ctx)
+        return f.cpu().numpy(), xy.cpu().numpy(), ln.cpu().numpy(), st.cpu().numpy()
+
+    ref = run("device")
+    for kind in ("pinned", "pinned_offset", "pageable"):
+        f, xy, ln, st = run(kind)
+        assert np.array_equal(f, ref[0]) and np.array_equal(ln, ref[2]) and np.array_equal(st, ref[3]), kind
+        for i in range(len(ln)):
+            assert np.array_equal(xy[i, :ln[i]], ref[1][i, :ln[i]]), (kind, i)
+    dd.dd_unload_mesh(ctx, mid)
