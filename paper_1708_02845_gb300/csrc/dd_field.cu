@@ -42,31 +42,12 @@
 
 #include "dd_internal.h"
 #include "dd_bulk.cuh"
+#include "dd_f32x2.cuh"
 #include "dd_splitlog.cuh"
 
 namespace {
 
 constexpr float kLn2 = 0.693147180559945309f;
-
-// ---- packed FP32x2 helpers (two IEEE round-to-nearest operations per instruction)
-typedef unsigned long long f2_t;
-
-__device__ __forceinline__ f2_t pk(float a, float b) {
-    f2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(f2_t r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
-__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
-    f2_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
-    f2_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
 
 // one term of each sum; accumulators updated in place
 __device__ __forceinline__ void accumulate(float px, float lmx, float ex, float pt, float lmt, float et,

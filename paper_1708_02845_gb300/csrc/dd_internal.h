@@ -133,9 +133,10 @@ void launch_copy_paths(const float2 *src, const int32_t *len, int64_t n, int32_t
 // Sparse fields (dd_sparse.cu, Section V).  build_sparse_rows fills the sp_*
 // members of m from m.P (the caller frees earlier ones).  The sparse stage is
 // the dense stage (4 x T x k_pad floats, filled by launch_stage_targets)
-// followed by T block lists of sparse_list_pitch(k_pad) uint16 and T int32
-// counts; launch_sparse_fields thresholds the staged rows in place, lists
-// their blocks and launches the field kernel (one target per grid row).
+// followed by T block lists of sparse_list_pitch(k_pad) uint16, T int32
+// counts (padded to 16 bytes) and T doubles M_t; launch_sparse_fields
+// thresholds the staged rows in place, lists their blocks, computes M_t and
+// launches the field kernel (one target per grid row).
 int64_t sparse_list_pitch(int64_t k_pad);
 size_t sparse_stage_bytes(int64_t k_pad, int32_t T);
 size_t sparse_field_smem(int64_t k_pad);

@@ -18,15 +18,18 @@
 // of the boundary, so the list is a few runs of consecutive blocks).  The
 // field kernel reads, for every row, only those blocks of the dense FP32 P
 // (16-byte loads, consecutive within a run), one warp per row, the next
-// item's loads in flight while the current one is summed.  Masses are kept
-// in 2^-62 fixed point (int64, exact for every entry above 2^-39): M_x is
-// the row's total (per mesh, dd_sparsify) minus its S_t part, exact and
-// independent of the order of the additions, so M_t from row t equals M_x at
-// x = t bit for bit and the fields are exactly 0 there.  (FP64 would serve
-// too, but its rate on this GPU is a small fraction of the integer pipes'.)
-// KL and KLT over S_t take the same two passes as the dense streaming kernel
-// (exponents exact, hardware log2 of the mantissas, rows below DD_EXACT_BELOW
-// recomputed with the table logarithm).
+// item's loads in flight while the current one is summed.  Per block, one
+// routine (block_terms) does the arithmetic in packed FP32x2 on the block's
+// two pairs of entries; a dropped column enters with weight 0 (its target
+// entry is 0 already), so KL, KLT, TV and the mass need one select per
+// entry.  M_x is the row's total (per mesh, exact 2^-62 fixed point) minus
+// its S_t part, summed with compensation (Kahan) per lane and in FP64 across
+// the warp once per row; M_t comes from the same routine in the same order on
+// row t, so M_x = M_t bit for bit at x = t and the fields are exactly 0 there.
+// (Per-entry FP64 would be simpler, but its rate on this GPU is a small
+// fraction of the FP32 pipes'.)  KL and KLT over S_t take the same two passes
+// as the dense streaming kernel (exponents exact, hardware log2 of the
+// mantissas, rows below DD_EXACT_BELOW recomputed with the table logarithm).
 #include <cfloat>
 #include <cmath>
 #include <string>
@@ -34,6 +37,7 @@
 #include <vector>
 
 #include "dd_bulk.cuh"
+#include "dd_f32x2.cuh"
 #include "dd_internal.h"
 #include "dd_splitlog.cuh"
 
@@ -55,7 +59,7 @@ __device__ __forceinline__ long long fix62(float p) {
     return sh >= 0 ? (m << sh) : (sh > -24 ? (m >> -sh) : 0LL);
 }
 
-__device__ __forceinline__ float unfix62(long long q) { return __ll2float_rn(q) * 0x1p-62f; }
+__device__ __forceinline__ double total62(long long q) { return __ll2double_rn(q) * 0x1p-62; }
 
 // per row: fixed-point total of the stored FP32 row, and how many entries /
 // 4-column blocks the row's own threshold keeps (the sparsity figure).  One
@@ -100,12 +104,82 @@ __global__ void sparse_rows_kernel(const float *__restrict__ P, int64_t n_v, int
     }
 }
 
+// One listed block of a row against the staged target block: p4 (target
+// entries, dropped ones 0), f4 / e4 (the dense target row's hardware mantissa
+// log2 and biased exponent).  Accumulates, per pair of entries (0,1) and
+// (2,3) in the halves of packed registers: kl += w d, kt += p_t d (KLT with
+// the sign flipped), tv += |w - p_t|, and the mass w into the Kahan pair
+// (s, c), where w = P[x,b] on kept columns and 0 on dropped ones and
+// d = log2(P[x,b]/P[t,b]) from exact exponents and hardware mantissa logs.
+template <bool KL, bool TV, bool KLT>
+__device__ __forceinline__ void block_terms(const float4 &v, const float4 &p4, const float4 &f4, const float4 &e4,
+                                            f2_t &kl, f2_t &tv, f2_t &kt, f2_t &s, f2_t &c) {
+    const f2_t mone = pk(-1.0f, -1.0f);
+    const float px[4] = {v.x, v.y, v.z, v.w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
+    float w[4], lf[4], eb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        w[q] = pt[q] > 0.f ? px[q] : 0.f;
+        if (KL || KLT) {
+            const int bits = __float_as_int(fmaxf(px[q], FLT_MIN));
+            lf[q] = lg2_mant(bits);
+            eb[q] = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const f2_t w2 = pk(w[2 * h], w[2 * h + 1]);
+        const f2_t pt2 = h ? pk(p4.z, p4.w) : pk(p4.x, p4.y);
+        if (KL || KLT) {
+            const f2_t ft2 = h ? pk(f4.z, f4.w) : pk(f4.x, f4.y);
+            const f2_t et2 = h ? pk(e4.z, e4.w) : pk(e4.x, e4.y);
+            const f2_t d = add2(fma2(ft2, mone, pk(lf[2 * h], lf[2 * h + 1])),
+                                fma2(et2, mone, pk(eb[2 * h], eb[2 * h + 1])));
+            if (KL) kl = fma2(w2, d, kl);
+            if (KLT) kt = fma2(pt2, d, kt);
+        }
+        if (TV) tv = add2(tv, fma2(pt2, mone, w2) & 0x7fffffff7fffffffULL);
+        const f2_t y = fma2(c, mone, w2);                 // Kahan: y = w - c
+        const f2_t t = add2(s, y);
+        c = fma2(y, mone, fma2(s, mone, t));              // c = (t - s) - y
+        s = t;
+    }
+}
+
+// the lane's Kahan pair as one FP64 value, reduced over the warp (fixed order)
+__device__ __forceinline__ double lane_mass_sum(f2_t s, f2_t c) {
+    float s0, s1, c0, c1;
+    upk(s, s0, s1);
+    upk(c, c0, c1);
+    double m = ((double)s0 - (double)c0) + ((double)s1 - (double)c1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+    return m;
+}
+
+// S_t part of row x's mass for one warp: block_terms' additions in the field
+// kernel's order (lane l takes list entries l, l + 32, ...)
+__device__ __forceinline__ double kept_mass(const float *__restrict__ P, int64_t x, int64_t k_pad,
+                                            const uint16_t *lst, int nl, const float4 *tP4, const float4 *tF4,
+                                            const float4 *tE4, int lane) {
+    const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+    f2_t kl = 0ULL, tv = 0ULL, kt = 0ULL, s = 0ULL, c = 0ULL;
+    for (int i = lane; i < nl; i += 32) {
+        const int j = lst[i];
+        block_terms<false, false, false>(__ldcg(row + j), tP4[j], tF4[j], tE4[j], kl, tv, kt, s, c);
+    }
+    return lane_mass_sum(s, c);
+}
+
 // Per target (one CTA each), after stage_targets_kernel: zero the staged
 // row's entries below theta x its maximum (the logs stay those of the dense
-// row) and list, in column order, the blocks holding a kept entry:
-// list[a][0 .. count[a]), pitch lp.
-__global__ void sparse_stage_kernel(float *__restrict__ sP, int64_t k_pad, float theta, uint16_t *__restrict__ list,
-                                    int64_t lp, int32_t *__restrict__ count) {
+// row), list, in column order, the blocks holding a kept entry
+// (list[a][0 .. count[a]), pitch lp), and compute M_t (mt_out[a]).
+__global__ void sparse_stage_kernel(const float *__restrict__ P, float *__restrict__ sP, const float *__restrict__ sE,
+                                    const float *__restrict__ sF, int64_t k_pad, float theta,
+                                    uint16_t *__restrict__ list, int64_t lp, int32_t *__restrict__ count,
+                                    const long long *__restrict__ rowsum, const int32_t *__restrict__ targets,
+                                    double *__restrict__ mt_out) {
     __shared__ float red[32];
     __shared__ int wsum[32];
     const int a = blockIdx.x;
@@ -155,23 +229,15 @@ __global__ void sparse_stage_kernel(float *__restrict__ sP, int64_t k_pad, float
         __syncthreads();
     }
     if (threadIdx.x == 0) count[a] = base;
-}
-
-// S_t part of one row's mass for one warp, fixed point (exact in any order)
-__device__ __forceinline__ long long kept_mass(const float *__restrict__ P, int64_t x, int64_t k_pad,
-                                               const uint16_t *lst, int nl, const float4 *tP4, int lane) {
-    const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
-    long long s = 0;
-    for (int i = lane; i < nl; i += 32) {
-        const int j = lst[i];
-        const float4 v = __ldcg(row + j);
-        const float4 p = tP4[j];
-        s += (p.x > 0.f ? fix62(v.x) : 0LL) + (p.y > 0.f ? fix62(v.y) : 0LL) + (p.z > 0.f ? fix62(v.z) : 0LL) +
-             (p.w > 0.f ? fix62(v.w) : 0LL);
+    // the target's mass outside S_t, by the routine and lane order the field
+    // kernel uses for every row (so that it reproduces this value at x = t)
+    if (threadIdx.x < 32) {
+        const double mt = total62(rowsum[targets[a]]) -
+                          kept_mass(P, targets[a], k_pad, L, base, reinterpret_cast<const float4 *>(row),
+                                    reinterpret_cast<const float4 *>(sF + (int64_t)a * k_pad),
+                                    reinterpret_cast<const float4 *>(sE + (int64_t)a * k_pad), lane);
+        if (lane == 0) mt_out[a] = mt;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
 }
 
 // exact (table) KL over the kept columns of one row, for one warp: the row
@@ -221,12 +287,11 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
     const float *__restrict__ P, int64_t n_v, int64_t k_pad, const float *__restrict__ sP,
     const float *__restrict__ sL, const float *__restrict__ sE, const float *__restrict__ sF,
     const uint16_t *__restrict__ sList, int64_t lp, const int32_t *__restrict__ sCount,
-    const long long *__restrict__ rowsum, const int32_t *__restrict__ targets, float *__restrict__ out_kl,
+    const double *__restrict__ sMt, const long long *__restrict__ rowsum, float *__restrict__ out_kl,
     float *__restrict__ out_tv, float *__restrict__ out_klt, int *__restrict__ err_flag) {
     extern __shared__ __align__(16) float smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ float tab[2 * kLogTab];
-    __shared__ long long sh_mt;
     float *tP = smem;
     float *tL = tP + k_pad;
     float *tE = tL + k_pad;
@@ -259,14 +324,8 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
     const float4 *tP4 = reinterpret_cast<const float4 *>(tP);
     const float4 *tF4 = reinterpret_cast<const float4 *>(tF);
     const float4 *tE4 = reinterpret_cast<const float4 *>(tE);
-    if (threadIdx.x < 32) {
-        const int64_t t_row = targets[a];
-        const long long mt = rowsum[t_row] - kept_mass(P, t_row, k_pad, lst, nl, tP4, lane);
-        if (lane == 0) sh_mt = mt;
-    }
-    __syncthreads();
-    const long long Mt_q = sh_mt;
-    const float Mt = unfix62(Mt_q);
+    const double Mt_d = sMt[a];
+    const float Mt = (float)Mt_d;
 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -276,9 +335,9 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
     float *okt = KLT ? out_klt + (int64_t)a * n_v : nullptr;
 
     float4 buf[2][U];
+    int jb[2][U];                      // block index of each fetched block (-1: none)
     long long rsb[2];                  // the fetched row's total, loaded with its blocks
-    float kl = 0.f, tv = 0.f, kt = 0.f;
-    long long ks = 0;
+    f2_t kl = 0ULL, tv = 0ULL, kt = 0ULL, ms = 0ULL, mc = 0ULL;
 
     // S: which register buffer (a compile-time index, so the buffers stay in registers)
     auto fetch = [&](auto S_, int64_t x, int g) {
@@ -288,49 +347,34 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = g * 32 * U + u * 32 + lane;
-            buf[s][u] = i < nl ? __ldcs(row + lst[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            jb[s][u] = i < nl ? (int)lst[i] : -1;
+            buf[s][u] = jb[s][u] >= 0 ? __ldcs(row + jb[s][u]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
-    auto compute = [&](auto S_, int g) {
+    auto compute = [&](auto S_) {
         constexpr int s = decltype(S_)::value;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int i = g * 32 * U + u * 32 + lane;
-            if (i >= nl) break;
-            const int j = lst[i];
-            const float4 p4 = tP4[j], f4 = tF4[j], e4 = tE4[j];
-            const float px[4] = {buf[s][u].x, buf[s][u].y, buf[s][u].z, buf[s][u].w};
-            const float pt[4] = {p4.x, p4.y, p4.z, p4.w}, ft[4] = {f4.x, f4.y, f4.z, f4.w};
-            const float et[4] = {e4.x, e4.y, e4.z, e4.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (!(pt[q] > 0.f)) continue;          // a dropped column of a listed block: merged bin
-                ks += fix62(px[q]);
-                if (TV) tv = __fadd_rn(tv, fabsf(__fadd_rn(px[q], -pt[q])));
-                if (KL || KLT) {
-                    const int bits = __float_as_int(fmaxf(px[q], FLT_MIN));
-                    const float lf = lg2_mant(bits);
-                    const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
-                    const float d = __fadd_rn(__fadd_rn(lf, -ft[q]), __fadd_rn(eb, -et[q]));   // log2(P_x/P_t)
-                    if (KL) kl = __fmaf_rn(px[q], d, kl);
-                    if (KLT) kt = __fmaf_rn(-pt[q], d, kt);
-                }
-            }
+            const int j = jb[s][u];
+            if (j < 0) break;
+            block_terms<KL, TV, KLT>(buf[s][u], tP4[j], tF4[j], tE4[j], kl, tv, kt, ms, mc);
         }
     };
     auto finish = [&](auto S_, int64_t x) {
         constexpr int s = decltype(S_)::value;
-        float skl = kl, stv = tv, skt = kt;
-        long long sks = ks;
+        float k0, k1, v0, v1, t0, t1;
+        upk(kl, k0, k1);
+        upk(tv, v0, v1);
+        upk(kt, t0, t1);
+        float skl = k0 + k1, stv = v0 + v1, skt = t0 + t1;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             if (KL) skl += __shfl_xor_sync(0xffffffffu, skl, o);
             if (TV) stv += __shfl_xor_sync(0xffffffffu, stv, o);
             if (KLT) skt += __shfl_xor_sync(0xffffffffu, skt, o);
-            sks += __shfl_xor_sync(0xffffffffu, sks, o);
         }
-        const long long Mx_q = rsb[s] - sks;
-        const float Mx = unfix62(Mx_q);
+        const double Mx_d = total62(rsb[s]) - lane_mass_sum(ms, mc);
+        const float Mx = (float)Mx_d;
         if (KL) {
             const float merged = Mx > 0.f ? Mx * logf(Mx / fmaxf(Mt, FLT_MIN)) : 0.f;
             skl = __fmaf_rn(skl, kLn2s, merged);
@@ -339,17 +383,16 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
         }
         if (KLT) {
             const float merged = Mt > 0.f ? Mt * logf(Mt / fmaxf(Mx, FLT_MIN)) : 0.f;
-            skt = __fmaf_rn(skt, kLn2s, merged);
+            skt = __fmaf_rn(-skt, kLn2s, merged);
             if (skt < kExactBelowS)
                 skt = kept_kl_exact<true>(P, x, k_pad, lst, nl, tP4, tL, tE, tab, lane) + merged;
         }
         if (lane == 0) {
             if (KL) okl[x] = skl;
-            if (TV) otv[x] = stv + unfix62(Mx_q >= Mt_q ? Mx_q - Mt_q : Mt_q - Mx_q);
+            if (TV) otv[x] = stv + (float)fabs(Mx_d - Mt_d);
             if (KLT) okt[x] = skt;
         }
-        kl = tv = kt = 0.f;
-        ks = 0;
+        kl = tv = kt = ms = mc = 0ULL;
     };
 
     using B0 = std::integral_constant<int, 0>;
@@ -369,14 +412,14 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
         int gn = g;
         advance(xn, gn);
         if (xn < n_v) fetch(B1{}, xn, gn);
-        compute(B0{}, g);
+        compute(B0{});
         if (xn != x) finish(B0{}, x);
         if (xn >= n_v) break;
         x = xn;
         g = gn;
         advance(xn, gn);
         if (xn < n_v) fetch(B0{}, xn, gn);
-        compute(B1{}, g);
+        compute(B1{});
         if (xn != x) finish(B1{}, x);
         if (xn >= n_v) break;
         x = xn;
@@ -399,9 +442,11 @@ size_t sparse_field_smem(int64_t k_pad) {
     return 4 * (size_t)k_pad * sizeof(float) + (size_t)sparse_list_pitch(k_pad) * sizeof(uint16_t);
 }
 
+size_t sparse_count_bytes(int32_t T) { return ((size_t)T * sizeof(int32_t) + 15) / 16 * 16; }
+
 size_t sparse_stage_bytes(int64_t k_pad, int32_t T) {
     return 4 * (size_t)T * k_pad * sizeof(float) + (size_t)T * sparse_list_pitch(k_pad) * sizeof(uint16_t) +
-           (size_t)T * sizeof(int32_t);
+           sparse_count_bytes(T) + (size_t)T * sizeof(double);
 }
 
 dd_status build_sparse_rows(DevMesh &m, double theta, cudaStream_t s, int64_t *kept_out, int64_t *blocks_out,
@@ -450,9 +495,11 @@ void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *st
     const int64_t lp = sparse_list_pitch(m.k_pad);
     uint16_t *sList = reinterpret_cast<uint16_t *>(const_cast<float *>(sF) + (int64_t)T * m.k_pad);
     int32_t *sCount = reinterpret_cast<int32_t *>(sList + (int64_t)T * lp);
+    double *sMt = reinterpret_cast<double *>(reinterpret_cast<char *>(sCount) + sparse_count_bytes(T));
     {
         KMark km_("sparse_stage_kernel", s);
-        sparse_stage_kernel<<<(unsigned)T, 256, 0, s>>>(sP, m.k_pad, m.sp_theta, sList, lp, sCount);
+        sparse_stage_kernel<<<(unsigned)T, 256, 0, s>>>(m.P, sP, sE, sF, m.k_pad, m.sp_theta, sList, lp, sCount,
+                                                         m.sp_rowsum, d_targets, sMt);
     }
     const size_t smem = sparse_field_smem(m.k_pad);
     auto go = [&](auto kern) {
@@ -467,8 +514,8 @@ void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *st
         {
             KMark km_("sparse_field_kernel", s);
             kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(m.P, m.n_v, m.k_pad, sP, sL, sE, sF, sList, lp,
-                                                                   sCount, m.sp_rowsum, d_targets, out_kl, out_tv,
-                                                                   out_klt, err_flag);
+                                                                   sCount, sMt, m.sp_rowsum, out_kl, out_tv, out_klt,
+                                                                   err_flag);
         }
     };
     // two blocks per lane and item, three CTAs per SM (measured: U = 4 or 8 with
