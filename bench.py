@@ -697,9 +697,20 @@ def _oracle_task(args):
 def oracle_pool(cores: int):
     import multiprocessing
     from concurrent.futures import ProcessPoolExecutor
-    pool = ProcessPoolExecutor(max_workers=cores, mp_context=multiprocessing.get_context("spawn"),
-                               initializer=_oracle_init)
-    list(pool.map(_oracle_task, [(w, 1) for w in range(cores)]))      # every worker built its kernel
+    # one thread per worker: the workers inherit this environment when spawned
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        pool = ProcessPoolExecutor(max_workers=cores, mp_context=multiprocessing.get_context("spawn"),
+                                   initializer=_oracle_init)
+        list(pool.map(_oracle_task, [(w, 1) for w in range(cores)]))      # every worker built its kernel
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     return pool
 
 
