@@ -9,17 +9,23 @@
 // about 2^-16 relative, is dropped), so the error is about 2^-15 of
 // S_x = sum_b P[x,b] |log P[t,b]|.  e_x is computed once per mesh in FP64.
 //
-// sm_103a kernel: one CTA per 128-row x 256-target output tile; warp 0
-// loads A (P hi/lo) and B (log P_t hi/lo) tiles with TMA (128-byte swizzle,
-// K-major, two pipeline stages completing on mbarriers), warp 1 issues
-// tcgen05.mma (kind::f16, BF16 in, FP32 accumulator in TMEM, 128 x 256 x 16
-// per instruction) and commits stage releases, warps 2-5 read the
-// accumulator with tcgen05.ld and write KL = e_x - C.  Every mbarrier wait is
-// bounded; on expiry the kernel sets an error flag, drains its own copies
-// and MMAs, frees TMEM and returns.
+// sm_103a kernel, persistent: one CTA per SM walks the 128-row x 256-target
+// output tiles (tile i of a CTA = blockIdx.x + i gridDim.x; consecutive tiles
+// share their row tile, so the CTAs working at one time read each A tile once
+// from HBM).  Warp 0 loads A (P hi/lo) and B (log P_t hi/lo) tiles with TMA
+// (128-byte swizzle, K-major, two stages on mbarriers, one ring across all
+// tiles, so the next tile's loads start while the current one finishes);
+// warp 1 issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulator in TMEM,
+// 128 x 256 x 16 per instruction) into one of two 256-column TMEM
+// accumulators; warps 2-5 read the other accumulator with tcgen05.ld and
+// write KL = e_x - C, then hand it back, so the epilogue of one tile overlaps
+// the main loop of the next.  Every mbarrier wait is bounded and also gives up
+// when another role has given up (a flag in shared memory); the kernel then
+// sets an error flag, drains its own copies, frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 #include <cstring>
@@ -33,8 +39,8 @@ constexpr int BM = 128, BN = 256, BK = 64, STAGES = 2;
 constexpr int A_BYTES = BM * BK * 2;                         // 16 KB
 constexpr int B_BYTES = BN * BK * 2;                         // 32 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;       // 96 KB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;   // + alignment slack, barriers, TMEM slot, abort flag
+constexpr uint32_t TMEM_COLS = 512;                          // two 256-column accumulators
 constexpr uint32_t kWaitLimit = 1u << 25;                    // bounded spins (non-suspending test_wait)
 
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N = 256, M = 128
@@ -57,12 +63,19 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait: true when the phase completed, false (error flag set) when the limit expired
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
+// bounded wait: true when the phase completed; false (error flag set, abort
+// raised for the other roles) when the limit expired or another role aborted
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, volatile int *abort) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
         if (mbar_test(bar, parity)) return true;
+        if (*abort) return false;
+    }
     atomicExch(err, 2);
+    *abort = 1;
     return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
@@ -114,18 +127,24 @@ __global__ void __launch_bounds__(192, 1) kl_gemm_kernel(const __grid_constant__
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *accf = empty + STAGES;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accf + 1);
+    uint64_t *accf = empty + STAGES;     // [2] accumulator written (MMA commit)
+    uint64_t *acce = accf + 2;           // [2] accumulator read out (4 epilogue warps)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acce + 2);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * BN;     // target tile (fast grid axis: CTAs of one row tile run together)
-    const int m0 = blockIdx.y * BM;     // row tile
+    const int ntn = (g.T + BN - 1) / BN;
+    const int ntiles = ntn * (int)((g.n_v + BM - 1) / BM);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -141,56 +160,80 @@ __global__ void __launch_bounds__(192, 1) kl_gemm_kernel(const __grid_constant__
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer
+            // ---------------- TMA producer: one ring of stages across all of this CTA's tiles
             int issued = 0;
-            for (int kb = 0; kb < g.kblocks; ++kb) {
-                const int s = kb % STAGES, round = kb / STAGES;
-                if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, g.err)) break;
-                uint8_t *st = smem + s * STAGE_BYTES;
-                mbar_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(st, &tAhi, &full[s], kb * BK, m0);
-                tma_load_2d(st + A_BYTES, &tAlo, &full[s], kb * BK, m0);
-                tma_load_2d(st + 2 * A_BYTES, &tBhi, &full[s], kb * BK, n0);
-                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tBlo, &full[s], kb * BK, n0);
-                ++issued;
+            for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+                const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+                for (int kb = 0; kb < g.kblocks; ++kb, ++issued) {
+                    const int s = issued % STAGES, round = issued / STAGES;
+                    if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, g.err, abort)) break;
+                    uint8_t *st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(st, &tAhi, &full[s], kb * BK, m0);
+                    tma_load_2d(st + A_BYTES, &tAlo, &full[s], kb * BK, m0);
+                    tma_load_2d(st + 2 * A_BYTES, &tBhi, &full[s], kb * BK, n0);
+                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &tBlo, &full[s], kb * BK, n0);
+                }
             }
             // drain: every issued stage must have landed before the CTA may exit
-            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
-                mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, g.err);
+            volatile int never = 0;
+            for (int q = issued - STAGES < 0 ? 0 : issued - STAGES; q < issued; ++q)
+                mbar_wait(&full[q % STAGES], (q / STAGES) & 1, g.err, &never);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer
-            for (int kb = 0; kb < g.kblocks; ++kb) {
-                const int s = kb % STAGES, round = kb / STAGES;
-                if (!mbar_wait(&full[s], round & 1, g.err)) break;
+            // ---------------- MMA issuer: tile i into accumulator i & 1
+            int consumed = 0, i = 0, last_buf = -1, last_par = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++i) {
+                const int buf = i & 1, use = i >> 1;
+                if (use > 0 && !mbar_wait(&acce[buf], (use - 1) & 1, g.err, abort)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t st = saddr(smem + s * STAGE_BYTES);
-                const uint64_t ahi = smem_desc(st), alo = smem_desc(st + A_BYTES);
-                const uint64_t bhi = smem_desc(st + 2 * A_BYTES), blo = smem_desc(st + 2 * A_BYTES + B_BYTES);
+                const uint32_t acc = tmem + (uint32_t)(buf * BN);
+                bool ok = true;
+                for (int kb = 0; kb < g.kblocks; ++kb, ++consumed) {
+                    const int s = consumed % STAGES, round = consumed / STAGES;
+                    if (!mbar_wait(&full[s], round & 1, g.err, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t st = saddr(smem + s * STAGE_BYTES);
+                    const uint64_t ahi = smem_desc(st), alo = smem_desc(st + A_BYTES);
+                    const uint64_t bhi = smem_desc(st + 2 * A_BYTES), blo = smem_desc(st + 2 * A_BYTES + B_BYTES);
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    const uint64_t off = (uint64_t)((kk * 32) >> 4);   // 16 BF16 = 32 bytes along K
-                    mma_bf16(tmem, ahi + off, bhi + off, (kb > 0 || kk > 0) ? 1u : 0u);
-                    mma_bf16(tmem, ahi + off, blo + off, 1u);
-                    mma_bf16(tmem, alo + off, bhi + off, 1u);
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t off = (uint64_t)((kk * 32) >> 4);   // 16 BF16 = 32 bytes along K
+                        mma_bf16(acc, ahi + off, bhi + off, (kb > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(acc, ahi + off, blo + off, 1u);
+                        mma_bf16(acc, alo + off, bhi + off, 1u);
+                    }
+                    mma_commit(&empty[s]);      // the stage is free once these MMAs complete
                 }
-                mma_commit(&empty[s]);      // the stage is free once these MMAs complete
+                mma_commit(&accf[buf]);         // accumulator ready (also after an early stop)
+                last_buf = buf;
+                last_par = use & 1;
+                if (!ok) break;
             }
-            mma_commit(accf);               // accumulator ready (also after an early stop)
+            // every MMA issued here has completed before TMEM may be freed
+            volatile int never = 0;
+            if (last_buf >= 0) mbar_wait(&accf[last_buf], (uint32_t)last_par, g.err, &never);
         }
     } else {
         // ---------------- epilogue: warps 2..5 read TMEM lanes 32*(warp % 4) .. +31
         const int q = warp & 3;
-        const int64_t row = (int64_t)m0 + q * 32 + lane;
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(accf, 0, g.err));   // warp-uniform for tcgen05.ld
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) {
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int buf = i & 1, use = i >> 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&accf[buf], use & 1, g.err, abort));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+            const int64_t row = (int64_t)m0 + q * 32 + lane;
             const float e = row < g.n_v ? g.ex[row] : 0.0f;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c0);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -209,6 +252,10 @@ __global__ void __launch_bounds__(192, 1) kl_gemm_kernel(const __grid_constant__
                     }
                 }
             }
+            // hand the accumulator back to the MMA warp
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[buf]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -362,7 +409,11 @@ dd_status launch_kl_gemm(const DevMesh &m, const int32_t *d_targets, int32_t T, 
     g.T = T;
     g.kblocks = (int32_t)(kb / BK);
     g.err = err_flag;
-    dim3 grid((unsigned)((T + BN - 1) / BN), (unsigned)((m.n_v + BM - 1) / BM));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = (int64_t)((T + BN - 1) / BN) * ((m.n_v + BM - 1) / BM);
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, sms > 0 ? sms : 1)));   // one CTA per SM
     {
         KMark km_("kl_gemm_kernel", s);
         kl_gemm_kernel<<<grid, 192, SMEM_BYTES, s>>>(tAhi, tAlo, tBhi, tBlo, g);
