@@ -131,7 +131,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
     ctx = dd.dd_create(local_rank, stream.cuda_stream)
-    if args.section in ("grid450", "batch", "serve", "census"):
+    if args.section in ("grid450", "batch", "serve", "census", "mid"):
         pk, pk_kind = peaks()
         flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev)
         if args.section == "grid450":
@@ -141,6 +141,8 @@ def run_ours(args, rank, world, local_rank):
             out = {"metric": "batch64 section only", "batch": batch_section(dd, ctx, dev, stream, flush, args)}
         elif args.section == "census":
             out = {"metric": "census section only", "census": census_section(dd, ctx, dev)}
+        elif args.section == "mid":
+            out = {"metric": "grid300 section only", "mid": mid_section(dd, ctx, dev, stream, flush, pk, pk_kind)}
         else:
             out = {"metric": "serving section only", "serve": serve_section(dd, ctx, args, n_domains=8, seconds=10.0)}
         dd.dd_destroy(ctx)
@@ -439,6 +441,53 @@ def sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, p
                               "klt_max_rel": float(np.max(rel[2][interior])),
                               "klt_median_rel": float(np.median(rel[2][interior]))},
             "traffic": None}
+
+
+def mid_section(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 8):
+    """A mid-size grid for full ncu captures (a few GB on the device): N = 300
+    with 12 obstacles (n = 86,449, k = 2,122, P = 0.73 GB, larger than L2).
+    The single-target dense stream (KL+TV), the sparse pass (KL+TV, Section V)
+    and the split-BF16 KL GEMM for 512 targets, each timed with CUDA events
+    (L2 flushed before every launch)."""
+    import torch
+    from synthetic import workloads
+    T = 512
+    wl = workloads.grid(300, 12, 8, 30, False, T, 0, 170802845 + 400, "grid300")
+    idx, off = wl.mesh.loop_arrays()
+    mid = dd.dd_load_mesh(ctx, wl.mesh.xy, wl.mesh.tri, idx, off)
+    dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+    info = dd.dd_mesh_info(ctx, mid)
+    n_v, k, k_pad = info["n_v"], info["k"], info["k_pad"]
+    tl = [int(t) for t in wl.targets]
+
+    def timed(fn, n_rep):
+        ms = []
+        for i in range(n_rep):
+            flush.fill_(0.5)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    out1 = torch.empty((2, 1, n_v), dtype=torch.float32, device=dev)
+    dd.dd_sparsify(ctx, mid)
+    for prec in (dd.DD_PREC_FP32, dd.DD_PREC_SPARSE):
+        dd.dd_distance(ctx, mid, [tl[0]], 3, prec, out1)
+    dense_ms = timed(lambda i: dd.dd_distance(ctx, mid, [tl[i]], 3, dd.DD_PREC_FP32, out1), reps)
+    sparse_ms = timed(lambda i: dd.dd_distance(ctx, mid, [tl[i]], 3, dd.DD_PREC_SPARSE, out1), reps)
+    outk = torch.empty((1, T, n_v), dtype=torch.float32, device=dev)
+    dd.dd_distance(ctx, mid, tl, 1, dd.DD_PREC_BF16X3, outk)
+    gemm_ms = timed(lambda i: dd.dd_distance(ctx, mid, tl, 1, dd.DD_PREC_BF16X3, outk), 4)
+    dd.dd_unload_mesh(ctx, mid)
+    issued = 3 * 2.0 * n_v * k * T / (gemm_ms / 1e3) / 1e12
+    return {"workload": "grid300: n=%d, k=%d, P=%.2f GB FP32" % (n_v, k, 4.0 * n_v * k_pad / 1e9),
+            "dense_stream_ms": round(dense_ms, 4),
+            "dense_stream_gbs": round(4.0 * n_v * k_pad / (dense_ms / 1e3) / 1e9, 1),
+            "sparse_ms": round(sparse_ms, 4), "gemm_T": T, "gemm_ms": round(gemm_ms, 4),
+            "gemm_tflops_issued": round(issued, 1), "peak_bf16": pk.get("bf16_tflops"), "peak_source": pk_kind}
 
 
 def batch_section(dd, ctx, dev, stream, flush, args, S: int = 64, max_pts: int = 1536):
@@ -746,8 +795,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", dest="stream", action="store_false",
                     help="skip the grid450 measurements (single-target HBM stream, BF16 tensor-core KL)")
-    ap.add_argument("--section", choices=["all", "step", "grid450", "batch", "serve", "census"], default="all",
-                    help="step: only the grid140 query step; grid450 / batch / serve / census: only that part")
+    ap.add_argument("--section", choices=["all", "step", "grid450", "batch", "serve", "census", "mid"], default="all",
+                    help="step: only the grid140 query step; grid450 / batch / serve / census / mid: only that part "
+                         "(mid: a grid300 case small enough for full ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
