@@ -38,6 +38,8 @@ STEP_LAUNCHES = 5
 # DRAM bytes (read + write) of one field_tile_kernel launch of this step, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); P is read once
 TILE_TRAFFIC_BYTES = 78423296        # 75,715,328 read + 2,707,968 written (4 n k_pad = 74.7 MB of P)
+# the same for one field_stream_kernel launch of the grid450 single-target pass
+STREAM_TRAFFIC_BYTES = 3035740160    # 3,032,217,088 read + 3,523,072 written (4 n k_pad = 3.03 GB of P)
 N_BATCHES = 8
 
 
@@ -342,7 +344,9 @@ def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10):
                   "kernel": "field_stream_kernel (+ stage_targets_kernel)", "bound": "hbm",
                   "achieved": round(achieved, 1), "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                   "frac": round(achieved / pk.get("hbm_gbs", 6672.5), 4), "peak_source": pk_kind,
-                  "ms_per_field_pair": round(med, 4), "fields_per_s": round(2 / (med / 1e3), 1), "traffic": None,
+                  "ms_per_field_pair": round(med, 4), "fields_per_s": round(2 / (med / 1e3), 1),
+                  "traffic": STREAM_TRAFFIC_BYTES, "algorithmic_bytes": int(nbytes),
+                  "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, this workload",
                   "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(pre, 2)}}
 
     outk = torch.empty((1, T_big, n_v), dtype=torch.float32, device=dev)
