@@ -28,6 +28,8 @@ def test_hand_example():
                   [0.25, 0.25, 0.25, 0.25],
                   [0.9, 0.0089, 0.0911, 0.0]])
     assert sparse.support(P, 0, 0.01).tolist() == [True, False, True, False]
+    # rows keep 2, 4 and 2 of their 4 entries (zeros are never kept)
+    assert sparse.sparsity(P, 0.01) == pytest.approx(1.0 / 3.0, abs=1e-15)
     assert sparse.merged_mass(P, 0, 0.01) == pytest.approx(0.004, abs=1e-18)
     kl = sparse.sparse_kl_field(P, 0, 0.01)
     # row 1: 0.25 log(0.25/0.5) + 0.25 log(0.25/0.496) + (0.5) log(0.5/0.004)
