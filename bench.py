@@ -610,7 +610,42 @@ def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1,
         rows.append(agg)
     return {"workload": "convex_holes(n, seed 1..4): unit disk minus 4 convex polygons, Delaunay; "
                         "all interior targets up to %d per mesh" % max_targets,
-            "rows": rows, "seconds": round(time.perf_counter() - t0, 2)}
+            "rows": rows, "paths": path_shapes(dd, ctx, dev), "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def path_shapes(dd, ctx, dev, n_goal: int = 10000, T: int = 32, S: int = 32, max_pts: int = 4096):
+    """Fig. 2: paths that cut through triangles against paths along edges, on
+    the same target-weighted KL fields of one convex-holes mesh: the share of
+    paths that reach the target and the mean length of those that do."""
+    import torch
+    from synthetic.meshes import convex_holes
+    from synthetic.rng import SplitMix64
+    mesh = convex_holes(n_goal, seed=1)
+    idx, off = mesh.loop_arrays()
+    mid = dd.dd_load_mesh(ctx, mesh.xy, mesh.tri, idx, off)
+    dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+    interior = np.nonzero(~mesh.boundary_flags())[0]
+    rng = SplitMix64(170802845 + 7)
+    targets = [int(interior[rng.choice(len(interior))]) for _ in range(T)]
+    sources = np.array([[int(interior[rng.choice(len(interior))]) for _ in range(S)] for _ in range(T)], np.int32)
+    f = torch.empty((1, T, mesh.n_v), dtype=torch.float32, device=dev)
+    dd.dd_distance(ctx, mid, targets, dd.DD_F_KLT, dd.DD_PREC_FP32, f)
+    out = {}
+    for name, fn in (("triangles", dd.dd_trace_fields), ("edges", dd.dd_trace_edges)):
+        xy = torch.empty((T * S, max_pts, 2), dtype=torch.float32, device=dev)
+        ln = torch.empty(T * S, dtype=torch.int32, device=dev)
+        st = torch.empty(T * S, dtype=torch.int32, device=dev)
+        fn(ctx, mid, f[0].contiguous(), targets, sources, max_pts, xy, ln, st)
+        torch.cuda.synchronize()
+        xy, ln, st = xy.cpu().numpy(), ln.cpu().numpy(), st.cpu().numpy()
+        lens = [float(np.sum(np.hypot(*np.diff(xy[i, :ln[i]], axis=0).T))) for i in range(T * S) if st[i] == 0]
+        out[name] = {"ok_share": round(float(np.mean(st == 0)), 4), "mean_length": round(float(np.mean(lens)), 4),
+                     "mean_points": round(float(np.mean(ln[st == 0])), 1)}
+    out["edge_over_triangle_length"] = round(out["edges"]["mean_length"] / out["triangles"]["mean_length"], 4)
+    out["workload"] = "convex_holes(%d, seed 1): n=%d; %d targets x %d sources on the target-weighted KL field" % (
+        n_goal, mesh.n_v, T, S)
+    dd.dd_unload_mesh(ctx, mid)
+    return out
 
 
 def serve_section(dd, ctx, args, n_domains: int, seconds: float, rate: float = 2000.0, max_pts: int = 2048):
