@@ -272,7 +272,11 @@ def run_ours(args, rank, world, local_rank):
     else:
         paths = T * S
         roof = {"kernel": dom, "bound": "latency", "achieved": round(paths / (dom_ms / 1e3), 1),
-                "peak": None, "unit": "paths/s", "frac": None, "traffic": None, "ms_per_launch": round(dom_ms, 4)}
+                "peak": None, "unit": "paths/s", "frac": None, "traffic": None, "ms_per_launch": round(dom_ms, 4),
+                "note": "one dependent L2 round trip per walk step along the longest path"}
+    # walk steps (points appended) per second of the walk kernel, from the last timed step's paths
+    walk_ms = kernel_ms["trace_kernel"][1] / max(kernel_ms["trace_kernel"][0], 1) if "trace_kernel" in kernel_ms else None
+    walk_steps = int(np.clip(lens, 0, None).sum())
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
@@ -283,6 +287,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed between steps (256 MB write outside the step events)",
                    "parallelism": f"replicas x{world}"},
         "paths_per_s": round(world * T * S * args.steps / (dev_ms / 1e3), 1),
+        "walk_steps_per_s": round(walk_steps / (walk_ms / 1e3), 1) if walk_ms else None,
         "kernel_split_ms": {"fields": round(field_ms, 4), "trace": round(trace_ms, 4)},
         "paths_ok_frac": float(np.mean(status == 0)), "max_path_pts": int(lens.max()),
         "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(preproc_s, 3)},
