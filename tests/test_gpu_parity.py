@@ -318,3 +318,43 @@ def test_query_host_output_kinds(env):
         for i in range(len(ln)):
             assert np.array_equal(xy[i, :ln[i]], ref[1][i, :ln[i]]), (kind, i)
     dd.dd_unload_mesh(ctx, mid)
+
+
+def test_degenerate_inputs(env):
+    """Empty and degenerate calls: no targets, no sources, ids out of range and
+    max_pts < 2 are DD_EINVAL; a source equal to its target is a one-point OK
+    path; max_pts = 2 truncates a long path to its first two points; a source
+    on the boundary traces without error from the source's position."""
+    dd, ctx = env
+    wl, po, P = case("grid24")
+    mesh = wl.mesh
+    mid = load(dd, ctx, mesh)
+    dd.dd_set_poisson_kernel(ctx, mid, P)
+    t = int(wl.targets[0])
+    out = torch.empty((2, 1, mesh.n_v), dtype=torch.float32, device="cuda")
+    xy = torch.empty((4, 1024, 2), dtype=torch.float32, device="cuda")
+    ln = torch.empty(4, dtype=torch.int32, device="cuda")
+    st = torch.empty(4, dtype=torch.int32, device="cuda")
+    for call in (lambda: dd.dd_distance(ctx, mid, [], 3, 0, out),
+                 lambda: dd.dd_distance(ctx, mid, [mesh.n_v], 3, 0, out),
+                 lambda: dd.dd_trace(ctx, mid, t, dd.DD_F_KL, [], 64, xy, ln, st),
+                 lambda: dd.dd_trace(ctx, mid, t, dd.DD_F_KL, [mesh.n_v], 64, xy, ln, st),
+                 lambda: dd.dd_trace(ctx, mid, t, dd.DD_F_KL, [t], 1, xy, ln, st),
+                 lambda: dd.dd_query(ctx, mid, [t], np.zeros((1, 0), np.int32), 3, 0, 1, 64, out, xy, ln, st)):
+        with pytest.raises(dd.DDError) as e:
+            call()
+        assert e.value.status == dd.DD_EINVAL
+    far = int(po.I[np.argmax(np.hypot(*(mesh.xy[po.I] - mesh.xy[t]).T))])
+    boundary = int(po.B[len(po.B) // 2])
+    dd.dd_trace(ctx, mid, t, dd.DD_F_KL, [t, far, far, boundary], 1024, xy, ln, st)
+    dd.dd_sync(ctx)
+    L, S_ = ln.cpu().numpy(), st.cpu().numpy()
+    X = xy.cpu().numpy()
+    assert L[0] == 1 and S_[0] == dd.DD_TRACE_OK and np.allclose(X[0, 0], mesh.xy[t])
+    assert S_[1] == dd.DD_TRACE_OK and L[1] > 2
+    assert np.allclose(X[1, 0], mesh.xy[far]) and np.allclose(X[1, L[1] - 1], mesh.xy[t])
+    assert np.allclose(X[3, 0], mesh.xy[boundary]) and S_[3] in (dd.DD_TRACE_OK, dd.DD_TRACE_STUCK)
+    dd.dd_trace(ctx, mid, t, dd.DD_F_KL, [far], 2, xy, ln, st)
+    dd.dd_sync(ctx)
+    assert ln.cpu().numpy()[0] == 2 and st.cpu().numpy()[0] == dd.DD_TRACE_TRUNCATED
+    dd.dd_unload_mesh(ctx, mid)
