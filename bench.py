@@ -299,6 +299,7 @@ def run_ours(args, rank, world, local_rank):
         "kernels": kernels,
         "clocks": clocks,
     }
+    line["step_bf16x3"] = bf16x3_step(dd, ctx, mid, batches, fields, pxy, plen, pst, flush, stream, args, T, S, n_v)
     if args.stream and args.section == "all":
         line["stream"], line["gemm"] = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
         line["batch"] = batch_section(dd, ctx, dev, stream, flush, args)
@@ -306,6 +307,49 @@ def run_ours(args, rank, world, local_rank):
         line["census"] = census_section(dd, ctx, dev)
     dd.dd_destroy(ctx)
     return line
+
+
+def bf16x3_step(dd, ctx, mid, batches, fields, pxy, plen, pst, flush, stream, args, T, S, n_v):
+    """The same query step with DD_PREC_BF16X3: the KL fields from the split-BF16
+    tensor-core GEMM (error bound 1e-4 of S_x, not the FP32 path's 1e-5: not
+    the headline), TV from a TV-only FP32 tile pass, the paths traced on the
+    GEMM's KL fields.  Reports its time and the KL fields' largest deviation
+    from the FP32 path's relative to max(|KL|, 1)."""
+    import torch
+
+    def step(i):
+        tg, sr = batches[i % len(batches)]
+        dd.dd_query(ctx, mid, tg, sr, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_BF16X3, dd.DD_F_KL, MAX_PTS,
+                    fields, pxy, plen, pst)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    dd.dd_kernel_timing(ctx, 1)
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(args.warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    kt = dd.dd_kernel_timing(ctx, 0)
+    tg, sr = batches[0]
+    ref = torch.empty_like(fields)
+    dd.dd_distance(ctx, mid, tg, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, ref)
+    got = torch.empty_like(fields)
+    dd.dd_distance(ctx, mid, tg, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_BF16X3, got)
+    torch.cuda.synchronize()
+    r, g = ref.cpu().numpy().astype(np.float64), got.cpu().numpy().astype(np.float64)
+    fin = r[0] < 80.0
+    dev_ms = float(sum(ms))
+    return {"ms_per_step": round(dev_ms / args.steps, 4), "fields_per_s": round(2 * T * args.steps / (dev_ms / 1e3), 1),
+            "kl_max_dev_vs_fp32": float(np.max(np.abs(g[0][fin] - r[0][fin]) / np.maximum(np.abs(r[0][fin]), 1.0))),
+            "tv_identical": bool(np.array_equal(g[1], r[1])),
+            "kernels": {n: {"launches": c, "ms_per_launch": round(v / max(c, 1), 4)} for n, (c, v) in kt.items()},
+            "note": "KL through the tensor-core GEMM (split BF16, 1e-4 bound), TV through a TV-only FP32 pass"}
 
 
 def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10):
@@ -542,6 +586,7 @@ def batch_section(dd, ctx, dev, stream, flush, args, S: int = 64, max_pts: int =
         q()
     torch.cuda.synchronize()
     ms = []
+    dd.dd_kernel_timing(ctx, 1)
     for _ in range(max(3, min(args.steps, 10))):
         flush.fill_(0.25)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -550,6 +595,10 @@ def batch_section(dd, ctx, dev, stream, flush, args, S: int = 64, max_pts: int =
         e1.record(stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
+    kt = dd.dd_kernel_timing(ctx, 0)
+    ktot = sum(v for _, v in kt.values()) or 1.0
+    kernels = {n: {"launches": c, "ms_per_launch": round(v / max(c, 1), 4), "share": round(v / ktot, 4)}
+               for n, (c, v) in sorted(kt.items(), key=lambda kv: -kv[1][1])}
     med = statistics.median(ms)
     stn = st.cpu().numpy()
     elem_targets = float(sum(T * n * k for T, n, k in zip(Ts, n_vs, ks)))
@@ -560,7 +609,7 @@ def batch_section(dd, ctx, dev, stream, flush, args, S: int = 64, max_pts: int =
             "ms_per_batch": round(med, 3), "fields_per_s": round(2 * nT / (med / 1e3), 1),
             "paths_per_s": round(nT * S / (med / 1e3), 1),
             "field_flop_per_batch": 8.0 * elem_targets, "paths_ok_frac": float(np.mean(stn == 0)),
-            "tile_shapes": dd.dd_tuning_table().strip().splitlines(),
+            "tile_shapes": dd.dd_tuning_table().strip().splitlines(), "kernels": kernels,
             "preproc": {"pcg_iters_total": pcg_iters, "seconds": round(pre, 2)}, "launches_per_batch": 5}
 
 

@@ -59,6 +59,13 @@ __device__ __forceinline__ void accumulate(float px, float lmx, float ex, float 
     tv = __fadd_rn(tv, fabsf(__fadd_rn(px, -pt)));
 }
 
+// the KL term alone (the same operations as in accumulate)
+__device__ __forceinline__ void accumulate_kl(float px, float lmx, float ex, float lmt, float et, float &kl) {
+    const float d = __fadd_rn(lmx, -lmt);
+    const float de = __fadd_rn(ex, -et);
+    kl = __fmaf_rn(px, __fmaf_rn(de, kLn2, d), kl);
+}
+
 // stage_P / stage_L / stage_E / stage_F: [T][k_pad] target row, its mantissa
 // log (table), biased exponent and mantissa log2 (hardware), the target-side
 // arguments clamped at FLT_MIN
@@ -292,8 +299,9 @@ struct TileShape {
 };
 
 // one output tile (rows x0.., targets a0..) of one problem; tsm holds the
-// staging arrays followed by the log table (built by the caller).
-template <int TM, int TN, int RM, int CN>
+// staging arrays followed by the log table (built by the caller).  KL / TV:
+// which sums to form (a TV-only tile skips the logarithms and the KL terms).
+template <int TM, int TN, int RM, int CN, bool KL = true, bool TV = true>
 __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
                                           const float *__restrict__ sP, const float *__restrict__ sL,
                                           const float *__restrict__ sE, int32_t T, float *__restrict__ out_kl,
@@ -337,11 +345,13 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
                 const float vals[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    float lm, E;
-                    split_log<false>(vals[q], tab, lm, E);
                     xP[cb + e + q][r] = vals[q];
-                    xL[cb + e + q][r] = lm;
-                    xE[cb + e + q][r] = E;
+                    if (KL) {
+                        float lm, E;
+                        split_log<false>(vals[q], tab, lm, E);
+                        xL[cb + e + q][r] = lm;
+                        xE[cb + e + q][r] = E;
+                    }
                 }
             }
         }
@@ -353,16 +363,20 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
                 float2 p2 = make_float2(0.f, 0.f), l2 = p2, e2 = p2;
                 if (ag < T && b0 + cb + e < k_pad) {
                     const int64_t off = (int64_t)ag * k_pad + b0 + cb + e;
-                    p2 = __ldg(reinterpret_cast<const float2 *>(sP + off));
-                    l2 = __ldg(reinterpret_cast<const float2 *>(sL + off));
-                    e2 = __ldg(reinterpret_cast<const float2 *>(sE + off));
+                    if (TV || KL) p2 = __ldg(reinterpret_cast<const float2 *>(sP + off));
+                    if (KL) {
+                        l2 = __ldg(reinterpret_cast<const float2 *>(sL + off));
+                        e2 = __ldg(reinterpret_cast<const float2 *>(sE + off));
+                    }
                 }
                 yP[cb + e][a] = p2.x;
                 yP[cb + e + 1][a] = p2.y;
-                yL[cb + e][a] = l2.x;
-                yL[cb + e + 1][a] = l2.y;
-                yE[cb + e][a] = e2.x;
-                yE[cb + e + 1][a] = e2.y;
+                if (KL) {
+                    yL[cb + e][a] = l2.x;
+                    yL[cb + e + 1][a] = l2.y;
+                    yE[cb + e][a] = e2.x;
+                    yE[cb + e + 1][a] = e2.y;
+                }
             }
         }
         __syncthreads();
@@ -372,20 +386,30 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
 #pragma unroll
             for (int r = 0; r < RM; ++r) {
                 rP[r] = xP[b][ty * RM + r];
-                rL[r] = xL[b][ty * RM + r];
-                rE[r] = xE[b][ty * RM + r];
+                if (KL) {
+                    rL[r] = xL[b][ty * RM + r];
+                    rE[r] = xE[b][ty * RM + r];
+                }
             }
 #pragma unroll
             for (int c = 0; c < CN; ++c) {
-                cP[c] = yP[b][tx * CN + c];
-                cL[c] = yL[b][tx * CN + c];
-                cE[c] = yE[b][tx * CN + c];
+                if (TV) cP[c] = yP[b][tx * CN + c];
+                if (KL) {
+                    cL[c] = yL[b][tx * CN + c];
+                    cE[c] = yE[b][tx * CN + c];
+                }
             }
 #pragma unroll
             for (int r = 0; r < RM; ++r)
 #pragma unroll
-                for (int c = 0; c < CN; ++c)
-                    accumulate(rP[r], rL[r], rE[r], cP[c], cL[c], cE[c], ckl[r][c], ctv[r][c]);
+                for (int c = 0; c < CN; ++c) {
+                    if (KL && TV)
+                        accumulate(rP[r], rL[r], rE[r], cP[c], cL[c], cE[c], ckl[r][c], ctv[r][c]);
+                    else if (KL)
+                        accumulate_kl(rP[r], rL[r], rE[r], cL[c], cE[c], ckl[r][c]);
+                    else
+                        ctv[r][c] = __fadd_rn(ctv[r][c], fabsf(__fadd_rn(rP[r], -cP[c])));
+                }
         }
 #pragma unroll
         for (int r = 0; r < RM; ++r)
@@ -418,7 +442,7 @@ typedef TileShape<64, 64, 4, 4> TileA;
 typedef TileShape<128, 32, 4, 4> TileB;
 typedef TileShape<256, 16, 8, 2> TileC;
 
-template <int TM, int TN, int RM, int CN>
+template <int TM, int TN, int RM, int CN, bool KL, bool TV>
 __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
                                                          const float *__restrict__ sP, const float *__restrict__ sL,
                                                          const float *__restrict__ sE, int32_t T,
@@ -427,20 +451,25 @@ __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restr
     float *tab = tsm + 3 * kTileB * (TM + TN);
     build_log_table(tab);
     __syncthreads();
-    tile_body<TM, TN, RM, CN>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, (int64_t)blockIdx.x * TM,
-                              blockIdx.y * TN, tsm, tab);
+    tile_body<TM, TN, RM, CN, KL, TV>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, (int64_t)blockIdx.x * TM,
+                                      blockIdx.y * TN, tsm, tab);
 }
 
 template <class S, int TM, int TN, int RM, int CN>
 void launch_tile(const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL, const float *sE,
                  int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
     dim3 g((unsigned)((n_v + TM - 1) / TM), (unsigned)((T + TN - 1) / TN));
-    auto kern = field_tile_kernel<TM, TN, RM, CN>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
-    {
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
         KMark km_("field_tile_kernel", s);
         kern<<<g, 256, S::smem_bytes, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv);
-    }
+    };
+    if (out_kl && out_tv)
+        go(field_tile_kernel<TM, TN, RM, CN, true, true>);
+    else if (out_kl)
+        go(field_tile_kernel<TM, TN, RM, CN, true, false>);
+    else
+        go(field_tile_kernel<TM, TN, RM, CN, false, true>);
 }
 
 int g_num_sms = 0;
