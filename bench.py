@@ -32,12 +32,16 @@ if ROOT not in sys.path:
 METRIC = "distance fields/s (KL+TV, one target over all vertices) with traced paths"
 UNIT = "fields/s"
 T_BATCH, S_PER_TARGET, MAX_PTS = 64, 256, 1024
-# kernels one dd_query step launches: target staging, field tile, triangle rates,
-# vertex decisions, path walk
-STEP_LAUNCHES = 5
+# kernels one dd_query step launches: target staging, field tile, exact KL
+# recompute near the targets, triangle rates, vertex decisions, path walk
+STEP_LAUNCHES = 6
+# bytes the walk gathers and stores per point it appends: one 64-B triangle
+# record, one 16-B rate vector, one 8-B point
+WALK_BYTES_PER_POINT = 88
 # DRAM bytes (read + write) of one field_tile_kernel launch of this step, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); P is read once
-TILE_TRAFFIC_BYTES = 78423296        # 75,715,328 read + 2,707,968 written (4 n k_pad = 74.7 MB of P)
+TILE_TRAFFIC_BYTES = None            # to be re-taken after the kernel's change (P is 4 n k_pad = 74.7 MB)
+WALK_TRAFFIC_BYTES = None
 # the same for one field_stream_kernel launch of the grid450 single-target pass
 STREAM_TRAFFIC_BYTES = 3035740160    # 3,032,217,088 read + 3,523,072 written (4 n k_pad = 3.03 GB of P)
 N_BATCHES = 8
@@ -257,26 +261,35 @@ def run_ours(args, rank, world, local_rank):
                for name, (n, ms) in sorted(kernel_ms.items(), key=lambda kv: -kv[1][1])}
     dom = max(kernel_ms, key=lambda k: kernel_ms[k][1]) if kernel_ms else "field_tile_kernel"
     dom_ms = kernel_ms[dom][1] / max(kernel_ms[dom][0], 1) if kernel_ms else field_ms
-    if dom == "field_tile_kernel":
-        # per (x, b, t): KL 2 FADD + 2 FFMA, TV 2 FADD = 6 FP32 instructions (8 flop)
-        ops = 6.0 * n_v * k * T
-        achieved = ops / (dom_ms / 1e3) / 1e12
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": "T FP32 instructions/s", "frac": round(achieved / peak, 4), "traffic": TILE_TRAFFIC_BYTES,
-                "algorithmic_fp32_ops": ops, "tflops_8_per_triple": round(8.0 * n_v * k * T / (dom_ms / 1e3) / 1e12, 3),
-                "ms_per_launch": round(dom_ms, 4),
-                "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled), one "
-                               "FP32 instruction per lane per clock",
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, this workload"}
-    else:
-        paths = T * S
-        roof = {"kernel": dom, "bound": "latency", "achieved": round(paths / (dom_ms / 1e3), 1),
-                "peak": None, "unit": "paths/s", "frac": None, "traffic": None, "ms_per_launch": round(dom_ms, 4),
-                "note": "one dependent L2 round trip per walk step along the longest path"}
-    # walk steps (points appended) per second of the walk kernel, from the last timed step's paths
     walk_ms = kernel_ms["trace_kernel"][1] / max(kernel_ms["trace_kernel"][0], 1) if "trace_kernel" in kernel_ms else None
     walk_steps = int(np.clip(lens, 0, None).sum())
+    tile_ms = kernel_ms["field_tile_kernel"][1] / max(kernel_ms["field_tile_kernel"][0], 1) \
+        if "field_tile_kernel" in kernel_ms else field_ms
+    # field tile: per (x, b, t) KL one FADD (log2 ratio) + one FFMA, TV two FADD = 4 FP32 instructions
+    ops = 4.0 * n_v * k * T
+    hbm_peak = float(pk["hbm_gbs"])
+    peak_alu = 152 * 128 * sm_mhz * 1e6 / 1e12
+    roof_tile = {"kernel": "field_tile_kernel", "bound": "alu", "achieved": round(ops / (tile_ms / 1e3) / 1e12, 3),
+                 "peak": round(peak_alu, 3), "unit": "T FP32 instructions/s",
+                 "frac": round(ops / (tile_ms / 1e3) / 1e12 / peak_alu, 4), "traffic": TILE_TRAFFIC_BYTES,
+                 "algorithmic_fp32_ops": ops, "ms_per_launch": round(tile_ms, 4),
+                 "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled), one "
+                                "FP32 instruction per lane per clock",
+                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, this workload"}
+    if walk_ms is not None:
+        # walk: per point appended, one 64-B triangle record and one 16-B rate gathered, one 8-B point stored
+        wbytes = WALK_BYTES_PER_POINT * walk_steps
+        roof_walk = {"kernel": "trace_kernel", "bound": "hbm", "achieved": round(wbytes / (walk_ms / 1e3) / 1e9, 1),
+                     "peak": hbm_peak, "unit": "GB/s", "frac": round(wbytes / (walk_ms / 1e3) / 1e9 / hbm_peak, 4),
+                     "traffic": WALK_TRAFFIC_BYTES, "algorithmic_bytes": wbytes, "ms_per_launch": round(walk_ms, 4),
+                     "peak_source": "measured HBM copy bandwidth, burst",
+                     "note": "a chain of dependent gathers (latency-bound): the records and rates (39 MB) are "
+                             "L2-resident, so the DRAM traffic is far below the gathered bytes and the frac "
+                             "against HBM shows the distance from any bandwidth roofline"}
+    else:
+        roof_walk = None
+    dom = max(kernel_ms, key=lambda k: kernel_ms[k][1]) if kernel_ms else "field_tile_kernel"
+    roof = roof_walk if (dom == "trace_kernel" and roof_walk is not None) else roof_tile
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
@@ -292,7 +305,8 @@ def run_ours(args, rank, world, local_rank):
         "paths_ok_frac": float(np.mean(status == 0)), "max_path_pts": int(lens.max()),
         "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(preproc_s, 3)},
         "wall_s_timed_region": round(wall, 4),
-        "roofline": roof, "peaks": pk_kind,
+        "roofline": roof, "roofline_fields": roof_tile if roof is not roof_tile else None,
+        "roofline_walk": roof_walk if roof is not roof_walk else None, "peaks": pk_kind,
         "e2e": {"value": round(world * fields_per_step * e2e_steps / e2e_s, 1), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(n for n, _ in kernel_ms.values())) or STEP_LAUNCHES * args.steps,

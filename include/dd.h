@@ -61,15 +61,22 @@ typedef enum {
 enum { DD_F_KL = 1, DD_F_TV = 2, DD_F_KLT = 4 };
 
 /* arithmetic of the field evaluation:
- *  DD_PREC_FP32   FP32 CUDA-core evaluation of Eq. 34-35 term by term, each
- *                 log split into an exact exponent and a mantissa log.  For
- *                 one or two targets the mantissa logs of a first pass come
- *                 from the hardware base-2 logarithm; every row whose KL there
- *                 is below DD_EXACT_BELOW (the rows near the target, x = t
- *                 among them) is recomputed with the table-driven logarithm
- *                 used for more targets.  The first pass's KL is within
- *                 ln2 * DD_FAST_LOG_SPREAD of the table form (see
- *                 dd_check_fast_log), so both keep 1e-5 relative accuracy.
+ *  DD_PREC_FP32   FP32 CUDA-core evaluation of Eq. 34-35 term by term in
+ *                 two passes.  The exact form splits each log into an exact
+ *                 exponent and a table-driven mantissa log.  For one or two
+ *                 targets a first pass takes the mantissa logs from the
+ *                 hardware base-2 logarithm and is within ln2 *
+ *                 DD_FAST_LOG_SPREAD of the exact form (see
+ *                 dd_check_fast_log); rows whose KL there is below
+ *                 DD_EXACT_BELOW are recomputed in the exact form.  For more
+ *                 targets the first pass forms each log2 as one FP32 number
+ *                 (exponent plus hardware mantissa log) and is within ln2 *
+ *                 DD_FAST_LOG_SPREAD + 2^-24 (2 ln k + 2 KL + 2) of the exact
+ *                 form; every (row, target) pair whose KL there is below
+ *                 DD_TILE_EXACT_BELOW is recomputed in the exact form.  In
+ *                 both cases the rows near the target (x = t among them) come
+ *                 from the exact form and every value keeps 1e-5 relative
+ *                 accuracy.
  *  DD_PREC_BF16X3 KL cross term sum_b P[x,b] log P[t,b] as a tensor-core GEMM
  *                 of split BF16 hi/lo operands (hi*hi + hi*lo + lo*hi, FP32
  *                 accumulation); TV and KLT are always FP32
@@ -87,6 +94,7 @@ enum { DD_F_KL = 1, DD_F_TV = 2, DD_F_KLT = 4 };
 enum { DD_PREC_FP32 = 0, DD_PREC_BF16X3 = 1, DD_PREC_SPARSE = 2 };
 #define DD_FAST_LOG_SPREAD 5.0e-7
 #define DD_EXACT_BELOW 0.05
+#define DD_TILE_EXACT_BELOW 0.25
 
 /* Measures, on the current device, the spread (maximum minus minimum) of the
  * error of the hardware base-2 logarithm used by the FP32 first pass, over

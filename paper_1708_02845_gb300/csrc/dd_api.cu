@@ -1083,7 +1083,7 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
             std::memcpy(meta.data() + o_items + j * sizeof(BatchItem), &order[j].second, sizeof(BatchItem));
         if ((st = upload(ctx, S_META, meta.data(), meta.size())) != DD_OK) return st;
         dmeta = reinterpret_cast<uint8_t *>(ctx->scratch[S_META]);
-        launch_batch_fields(reinterpret_cast<const BatchProblem *>(dmeta + o_probs),
+        launch_batch_fields(reinterpret_cast<const BatchProblem *>(dmeta + o_probs), (int32_t)n_items,
                             reinterpret_cast<const BatchItem *>(dmeta + o_items), (int32_t)order.size(),
                             reinterpret_cast<int32_t *>(dmeta + o_counter), ctx->stream);
         CK(cudaGetLastError(), "batch field launch");

@@ -25,9 +25,12 @@
 //    of the arithmetic, the target row and its logs staged in shared memory
 //    by a bulk async copy completing on an mbarrier, a lane-replicated copy
 //    of the log table (no bank conflicts), warp-shuffle reductions.
-//  * field_tile (many targets): 64 rows x 64 targets per CTA, b in chunks of
-//    32 staged through shared memory, 4 x 4 register micro-tiles.  Each P
-//    element's logarithm is computed once per CTA and reused for 64 targets.
+//  * field_tile (many targets): TM rows x TN targets per CTA, b in chunks of
+//    32 staged through shared memory, register micro-tiles.  Each P element's
+//    base-2 logarithm is formed once per CTA as one FP32 number and reused for
+//    TN targets (one subtraction and one multiply-add per KL term); the
+//    (row, target) pairs whose KL lands below DD_TILE_EXACT_BELOW are then
+//    recomputed in the exact split form by the same CTA.
 #include <algorithm>
 #include <vector>
 #include <type_traits>
@@ -107,6 +110,7 @@ __device__ __forceinline__ float4 ld_stream(const float4 *p) {
 // whose fast KL lies below DD_EXACT_BELOW are recomputed with the table
 // logarithm, so every row meets 1e-5 relative: ln2 * 5e-7 / 0.05 = 7e-6.
 constexpr float kExactBelow = (float)DD_EXACT_BELOW;
+constexpr float kTileExactBelow = (float)DD_TILE_EXACT_BELOW;
 
 // exact (table) KL of row x for one warp, from the staged target arrays
 __device__ __forceinline__ float kl_row_exact(const float *__restrict__ P, int64_t x, int64_t k_pad, int nvec,
@@ -114,6 +118,7 @@ __device__ __forceinline__ float kl_row_exact(const float *__restrict__ P, int64
                                               int lane) {
     const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
     float k0 = 0.0f, k1 = 0.0f;
+#pragma unroll 3
     for (int c = lane; c < nvec; c += 32) {
         const float4 v = __ldcg(row + c);
         const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
@@ -295,12 +300,47 @@ template <int TM, int TN, int RM, int CN>
 struct TileShape {
     static constexpr int ROWG = TM / RM, COLG = TN / CN;
     static_assert(ROWG * COLG == 256, "256 threads");
-    static constexpr size_t smem_bytes = (3 * kTileB * (TM + TN) + 2 * kLogTab) * sizeof(float);
+    static constexpr size_t smem_bytes = (2 * kTileB * (TM + TN) + 2 * kLogTab) * sizeof(float);
 };
 
+// N consecutive floats from shared memory in 16-byte (or 8-byte) loads; src
+// is aligned to 4 N bytes (N a multiple of 4) or 8 bytes (N = 2)
+template <int N>
+__device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src) {
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const float4 v = reinterpret_cast<const float4 *>(src)[i];
+            dst[4 * i] = v.x;
+            dst[4 * i + 1] = v.y;
+            dst[4 * i + 2] = v.z;
+            dst[4 * i + 3] = v.w;
+        }
+    } else {
+        static_assert(N == 2, "micro-tile widths 2, 4, 8");
+        const float2 v = *reinterpret_cast<const float2 *>(src);
+        dst[0] = v.x;
+        dst[1] = v.y;
+    }
+}
+
 // one output tile (rows x0.., targets a0..) of one problem; tsm holds the
-// staging arrays followed by the log table (built by the caller).  KL / TV:
-// which sums to form (a TV-only tile skips the logarithms and the KL terms).
+// staging arrays.  KL / TV: which sums to form (a TV-only tile skips the
+// logarithms).
+//
+// KL first pass: each P element's base-2 logarithm is formed once as one FP32
+// number, fast_l2 = E + lg2 m (hardware mantissa log), so a term costs one
+// subtraction and one multiply-add.  Against the exact split form a row's
+// first-pass KL (in nats) errs by at most ln2 * DD_FAST_LOG_SPREAD (the
+// varying part of the mantissa log's error; its constant part cancels) plus
+// 2^-24 (2 ln k + 2 KL + 2): each logarithm rounds to half an ulp of its
+// magnitude, sum_b P[x,b] |log P[x,b]| <= ln k, sum_b P[x,b] |log P[t,b]| =
+// that entropy + KL, and the subtraction rounds relative to |log ratio|,
+// whose P[x,b]-weighted sum is at most KL + 2.  Every (row, target) pair
+// whose first-pass KL lies below kTileExactBelow -- the rows around each
+// target, x = t among them -- is then recomputed by one warp with the table
+// logarithm (fix_kl_kernel, kl_row_exact), so every value keeps 1e-5
+// relative accuracy.
 template <int TM, int TN, int RM, int CN, bool KL = true, bool TV = true>
 __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
                                           const float *__restrict__ sP, const float *__restrict__ sL,
@@ -310,10 +350,8 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
     constexpr int COLG = TN / CN;
     float (*xP)[TM] = reinterpret_cast<float (*)[TM]>(tsm);
     float (*xL)[TM] = reinterpret_cast<float (*)[TM]>(tsm + 1 * kTileB * TM);
-    float (*xE)[TM] = reinterpret_cast<float (*)[TM]>(tsm + 2 * kTileB * TM);
-    float (*yP)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 3 * kTileB * TM);
-    float (*yL)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 3 * kTileB * TM + 1 * kTileB * TN);
-    float (*yE)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 3 * kTileB * TM + 2 * kTileB * TN);
+    float (*yP)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 2 * kTileB * TM);
+    float (*yL)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 2 * kTileB * TM + 1 * kTileB * TN);
     const int tid = threadIdx.x;
     const int tx = tid % COLG;        // target group: targets tx*CN ..
     const int ty = tid / COLG;        // row group: rows ty*RM ..
@@ -346,12 +384,7 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     xP[cb + e + q][r] = vals[q];
-                    if (KL) {
-                        float lm, E;
-                        split_log<false>(vals[q], tab, lm, E);
-                        xL[cb + e + q][r] = lm;
-                        xE[cb + e + q][r] = E;
-                    }
+                    if (KL) xL[cb + e + q][r] = fast_l2(vals[q]);
                 }
             }
         }
@@ -360,55 +393,31 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
             const int ag = a0 + a;
 #pragma unroll
             for (int e = 0; e < FT; e += 2) {
-                float2 p2 = make_float2(0.f, 0.f), l2 = p2, e2 = p2;
-                if (ag < T && b0 + cb + e < k_pad) {
-                    const int64_t off = (int64_t)ag * k_pad + b0 + cb + e;
-                    if (TV || KL) p2 = __ldg(reinterpret_cast<const float2 *>(sP + off));
-                    if (KL) {
-                        l2 = __ldg(reinterpret_cast<const float2 *>(sL + off));
-                        e2 = __ldg(reinterpret_cast<const float2 *>(sE + off));
-                    }
-                }
+                float2 p2 = make_float2(0.f, 0.f);
+                if (ag < T && b0 + cb + e < k_pad)
+                    p2 = __ldg(reinterpret_cast<const float2 *>(sP + (int64_t)ag * k_pad + b0 + cb + e));
                 yP[cb + e][a] = p2.x;
                 yP[cb + e + 1][a] = p2.y;
                 if (KL) {
-                    yL[cb + e][a] = l2.x;
-                    yL[cb + e + 1][a] = l2.y;
-                    yE[cb + e][a] = e2.x;
-                    yE[cb + e + 1][a] = e2.y;
+                    yL[cb + e][a] = fast_l2(fmaxf(p2.x, FLT_MIN));
+                    yL[cb + e + 1][a] = fast_l2(fmaxf(p2.y, FLT_MIN));
                 }
             }
         }
         __syncthreads();
 #pragma unroll 4
         for (int b = 0; b < kTileB; ++b) {
-            float rP[RM], rL[RM], rE[RM], cP[CN], cL[CN], cE[CN];
-#pragma unroll
-            for (int r = 0; r < RM; ++r) {
-                rP[r] = xP[b][ty * RM + r];
-                if (KL) {
-                    rL[r] = xL[b][ty * RM + r];
-                    rE[r] = xE[b][ty * RM + r];
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CN; ++c) {
-                if (TV) cP[c] = yP[b][tx * CN + c];
-                if (KL) {
-                    cL[c] = yL[b][tx * CN + c];
-                    cE[c] = yE[b][tx * CN + c];
-                }
-            }
+            float rP[RM], rL[RM], cP[CN], cL[CN];
+            lds_vec(rP, &xP[b][ty * RM]);
+            if (KL) lds_vec(rL, &xL[b][ty * RM]);
+            if (TV) lds_vec(cP, &yP[b][tx * CN]);
+            if (KL) lds_vec(cL, &yL[b][tx * CN]);
 #pragma unroll
             for (int r = 0; r < RM; ++r)
 #pragma unroll
                 for (int c = 0; c < CN; ++c) {
-                    if (KL && TV)
-                        accumulate(rP[r], rL[r], rE[r], cP[c], cL[c], cE[c], ckl[r][c], ctv[r][c]);
-                    else if (KL)
-                        accumulate_kl(rP[r], rL[r], rE[r], cL[c], cE[c], ckl[r][c]);
-                    else
-                        ctv[r][c] = __fadd_rn(ctv[r][c], fabsf(__fadd_rn(rP[r], -cP[c])));
+                    if (KL) ckl[r][c] = __fmaf_rn(rP[r], __fadd_rn(rL[r], -cL[c]), ckl[r][c]);
+                    if (TV) ctv[r][c] = __fadd_rn(ctv[r][c], fabsf(__fadd_rn(rP[r], -cP[c])));
                 }
         }
 #pragma unroll
@@ -431,9 +440,60 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
         for (int c = 0; c < CN; ++c) {
             const int a = a0 + tx * CN + c;
             if (a >= T) continue;
-            if (out_kl) out_kl[(int64_t)a * n_v + x] = kl[r][c];
-            if (out_tv) out_tv[(int64_t)a * n_v + x] = tv[r][c];
+            if (KL && out_kl) out_kl[(int64_t)a * n_v + x] = __fmul_rn(kl[r][c], kLn2);
+            if (TV && out_tv) out_tv[(int64_t)a * n_v + x] = tv[r][c];
         }
+    }
+}
+
+// Exact recompute after the tile pass: one warp reads the first-pass KL of 32
+// rows of one target, rows g, g + G, g + 2G, ... (G = ceil(n_v / 32) groups
+// per target), and every row below kTileExactBelow among them is recomputed
+// in the exact split form by the whole warp.  The rows around a target are
+// neighbours in vertex order, so the stride spreads them over many groups;
+// groups are dealt round-robin over the warps of the grid, consecutive groups
+// to different CTAs.
+__device__ __forceinline__ void fix_problem(const BatchProblem &q, int64_t wid, int64_t nw, int64_t &base,
+                                            const float *tab, int lane) {
+    if (!q.out_kl || q.T <= 0 || q.n_v <= 0) return;
+    const int64_t groups = (q.n_v + 31) / 32, total = groups * q.T;
+    const int nvec = (int)(q.k_pad >> 2);
+    for (int64_t g = (wid + nw - base % nw) % nw; g < total; g += nw) {
+        const int a = (int)(g / groups);
+        const int64_t g0 = g % groups, x = g0 + lane * groups;
+        float *row = q.out_kl + (int64_t)a * q.n_v;
+        const bool low = x < q.n_v && row[x] < kTileExactBelow;
+        unsigned m = __ballot_sync(0xffffffffu, low);
+        const int64_t o = (int64_t)a * q.k_pad;
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const int64_t xl = g0 + l * groups;
+            const float v = kl_row_exact(q.P, xl, q.k_pad, nvec, q.sP + o, q.sL + o, q.sE + o, tab, lane);
+            if (lane == 0) row[xl] = v;
+        }
+    }
+    base += total;
+}
+
+__global__ void __launch_bounds__(256) fix_kl_kernel(BatchProblem q) {
+    __shared__ float tab[2 * kLogTab];
+    build_log_table(tab);
+    __syncthreads();
+    const int64_t wid = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x, nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int64_t base = 0;
+    fix_problem(q, wid, nw, base, tab, threadIdx.x & 31);
+}
+
+__global__ void __launch_bounds__(256) fix_kl_batch_kernel(const BatchProblem *__restrict__ probs, int32_t n_probs) {
+    __shared__ float tab[2 * kLogTab];
+    build_log_table(tab);
+    __syncthreads();
+    const int64_t wid = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x, nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int64_t base = 0;
+    for (int p = 0; p < n_probs; ++p) {
+        const BatchProblem q = probs[p];
+        fix_problem(q, wid, nw, base, tab, threadIdx.x & 31);
     }
 }
 
@@ -448,7 +508,7 @@ __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restr
                                                          const float *__restrict__ sE, int32_t T,
                                                          float *__restrict__ out_kl, float *__restrict__ out_tv) {
     extern __shared__ __align__(16) float tsm[];
-    float *tab = tsm + 3 * kTileB * (TM + TN);
+    float *tab = tsm + 2 * kTileB * (TM + TN);
     build_log_table(tab);
     __syncthreads();
     tile_body<TM, TN, RM, CN, KL, TV>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, (int64_t)blockIdx.x * TM,
@@ -658,6 +718,11 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
     }
     const int v = tune_variant(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
     launch_variant(v, P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+    if (out_kl) {
+        const BatchProblem q{P, n_v, k_pad, sP, sL, sE, T, v, out_kl, nullptr};
+        KMark km_("fix_kl_kernel", s);
+        fix_kl_kernel<<<(unsigned)(num_sms() * 4), 256, 0, s>>>(q);
+    }
 }
 
 
@@ -679,10 +744,10 @@ void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, con
     }
 }
 
-void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, int32_t n_items, int32_t *d_counter,
-                         cudaStream_t s) {
+void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const BatchItem *d_items, int32_t n_items,
+                         int32_t *d_counter, cudaStream_t s) {
     if (n_items <= 0) return;
-    const size_t smem = (size_t)3 * kTileB * (256 + 16) * sizeof(float);
+    const size_t smem = (size_t)2 * kTileB * (256 + 16) * sizeof(float);
     cudaFuncSetAttribute(batch_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tile_kernel, 256, smem);
@@ -693,6 +758,10 @@ void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, 
     {
         KMark km_("batch_tile_kernel", s);
         batch_tile_kernel<<<(unsigned)grid, 256, smem, s>>>(d_probs, d_items, n_items, d_counter);
+    }
+    {
+        KMark km_("fix_kl_batch_kernel", s);
+        fix_kl_batch_kernel<<<(unsigned)(num_sms() * 4), 256, 0, s>>>(d_probs, n_probs);
     }
 }
 

@@ -110,8 +110,8 @@ int tile_rows(int variant);
 int tile_targets(int variant);
 void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, const int32_t *d_tlocal,
                         const int32_t *d_targets, int32_t n_targets, int64_t k_max, cudaStream_t s);
-void launch_batch_fields(const BatchProblem *d_probs, const BatchItem *d_items, int32_t n_items, int32_t *d_counter,
-                         cudaStream_t s);
+void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const BatchItem *d_items, int32_t n_items,
+                         int32_t *d_counter, cudaStream_t s);
 std::string tuning_table();
 // spurious local minima of T fields [T][n_v] (counts host [T], flags optional [T][n_v])
 void launch_local_minima(const DevMesh &m, const float *fields, const int32_t *targets, int32_t T, int32_t *counts,

@@ -69,4 +69,15 @@ __device__ __forceinline__ float lg2_mant(int i) {
     return y;
 }
 
+// Base-2 logarithm as one FP32 number: the exponent E (exact, from the bit
+// pattern: 2^23 + biased E as a float, minus 2^23 + 127) plus the hardware
+// mantissa log, rounded once to half an ulp of the result.  Positive normal
+// arguments only; +0 gives -127 (finite), harmless where the argument is
+// also the term's weight.
+__device__ __forceinline__ float fast_l2(float p) {
+    const int i = __float_as_int(p);
+    const float E = __fsub_rn(__int_as_float(0x4B000000 | (int)((unsigned)i >> 23)), 8388735.0f);
+    return __fadd_rn(E, lg2_mant(i));
+}
+
 }  // namespace

@@ -113,8 +113,10 @@ def test_fast_log_spread(env):
 def test_stream_pass_against_table_path(env, name):
     """One target (streaming kernel, hardware mantissa log with exact recompute
     of rows below DD_EXACT_BELOW) against the same target among three (tile
-    kernel, table log): rows below the threshold agree to FP32 summation
-    rounding, the others within ln2 * DD_FAST_LOG_SPREAD plus rounding."""
+    kernel, one-number log2 first pass with exact recompute of pairs below
+    DD_TILE_EXACT_BELOW): rows where both are exact agree to FP32 summation
+    rounding, rows where one is exact within ln2 * DD_FAST_LOG_SPREAD plus
+    rounding, the rest within the sum of both first passes' bounds."""
     dd, ctx = env
     wl, po, P = case(name)
     mid = load(dd, ctx, wl.mesh)
@@ -128,8 +130,13 @@ def test_stream_pass_against_table_path(env, name):
         assert np.all(np.abs(one[1, 0] - three[1, 0]) <= 2e-6 * np.maximum(three[1, 0], 1.0))   # TV: summation order
         near = kl3 < dd.DD_EXACT_BELOW
         assert np.all(np.abs(kl1 - kl3)[near] <= 2e-6 * np.maximum(kl3[near], 1e-2))
-        far = ~near & np.isfinite(kl3)
-        bound = math.log(2.0) * dd.DD_FAST_LOG_SPREAD + 1e-6 * kl3[far]
+        between = ~near & (kl3 < dd.DD_TILE_EXACT_BELOW)
+        bound = math.log(2.0) * dd.DD_FAST_LOG_SPREAD + 1e-6 * kl3[between]
+        assert np.all(np.abs(kl1 - kl3)[between] <= bound)
+        far = (kl3 >= dd.DD_TILE_EXACT_BELOW) & np.isfinite(kl3)
+        k = P.shape[1]
+        bound = (2 * math.log(2.0) * dd.DD_FAST_LOG_SPREAD + 2.0 ** -24 * (2 * math.log(k) + 2 * kl3[far] + 2)
+                 + 1e-6 * kl3[far])
         assert np.all(np.abs(kl1 - kl3)[far] <= bound)
         assert one[0, 0, t] == 0.0
     dd.dd_unload_mesh(ctx, mid)
@@ -275,7 +282,7 @@ def test_kernel_timing_hook(env):
     for _ in range(3):
         dd.dd_query(ctx, mid, targets, src, 3, dd.DD_PREC_FP32, dd.DD_F_KL, 512, f, xy, ln, st)
     got = dd.dd_kernel_timing(ctx, 0)
-    for name in ("stage_targets_kernel", "field_tile_kernel", "rates_kernel", "trace_kernel"):
+    for name in ("stage_targets_kernel", "field_tile_kernel", "fix_kl_kernel", "rates_kernel", "trace_kernel"):
         assert got[name][0] == 3 and got[name][1] > 0.0, (name, got)
     dd.dd_query(ctx, mid, targets, src, 3, dd.DD_PREC_FP32, dd.DD_F_KL, 512, f, xy, ln, st)
     assert dd.dd_kernel_timing(ctx, 2) == {}
