@@ -40,8 +40,9 @@ STEP_LAUNCHES = 6
 WALK_BYTES_PER_POINT = 88
 # DRAM bytes (read + write) of one field_tile_kernel launch of this step, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); P is read once
-TILE_TRAFFIC_BYTES = None            # to be re-taken after the kernel's change (P is 4 n k_pad = 74.7 MB)
-WALK_TRAFFIC_BYTES = None
+TILE_TRAFFIC_BYTES = 77092352        # 75,064,576 read + 2,027,776 written (P is 4 n k_pad = 74.7 MB; 64x64 shape)
+# the same for one trace_kernel launch (records and rates mostly served by L2)
+WALK_TRAFFIC_BYTES = 31522560        # 31,330,816 read + 191,744 written
 # the same for one field_stream_kernel launch of the grid450 single-target pass
 STREAM_TRAFFIC_BYTES = 3035740160    # 3,032,217,088 read + 3,523,072 written (4 n k_pad = 3.03 GB of P)
 N_BATCHES = 8
@@ -283,6 +284,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak": hbm_peak, "unit": "GB/s", "frac": round(wbytes / (walk_ms / 1e3) / 1e9 / hbm_peak, 4),
                      "traffic": WALK_TRAFFIC_BYTES, "algorithmic_bytes": wbytes, "ms_per_launch": round(walk_ms, 4),
                      "peak_source": "measured HBM copy bandwidth, burst",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, this workload",
                      "note": "a chain of dependent gathers (latency-bound): the records and rates (39 MB) are "
                              "L2-resident, so the DRAM traffic is far below the gathered bytes and the frac "
                              "against HBM shows the distance from any bandwidth roofline"}
