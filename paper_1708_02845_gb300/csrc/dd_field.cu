@@ -71,23 +71,27 @@ __device__ __forceinline__ void accumulate_kl(float px, float lmx, float ex, flo
 
 // stage_P / stage_L / stage_E / stage_F: [T][k_pad] target row, its mantissa
 // log (table), biased exponent and mantissa log2 (hardware), the target-side
-// arguments clamped at FLT_MIN
+// arguments clamped at FLT_MIN.  One CTA per target, so that the log table
+// (FP64, slow on this part) is built once per target row.
 __global__ void stage_targets_kernel(const float *__restrict__ P, int64_t k_pad, const int32_t *__restrict__ targets,
                                      int32_t T, float *__restrict__ sP, float *__restrict__ sL,
                                      float *__restrict__ sE, float *__restrict__ sF) {
     __shared__ float tab[2 * kLogTab];
     build_log_table(tab);
     __syncthreads();
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int a = blockIdx.y;
-    if (b >= k_pad || a >= T) return;
-    const float p = P[(int64_t)targets[a] * k_pad + b];
-    float lm, E;
-    split_log<true>(p, tab, lm, E);
-    sP[(int64_t)a * k_pad + b] = p;
-    sL[(int64_t)a * k_pad + b] = lm;
-    sE[(int64_t)a * k_pad + b] = E;
-    sF[(int64_t)a * k_pad + b] = lg2_mant(__float_as_int(fmaxf(p, FLT_MIN)));
+    const int a = blockIdx.x;
+    if (a >= T) return;
+    const float *row = P + (int64_t)targets[a] * k_pad;
+    const int64_t o = (int64_t)a * k_pad;
+    for (int64_t b = threadIdx.x; b < k_pad; b += blockDim.x) {
+        const float p = row[b];
+        float lm, E;
+        split_log<true>(p, tab, lm, E);
+        sP[o + b] = p;
+        sL[o + b] = lm;
+        sE[o + b] = E;
+        sF[o + b] = lg2_mant(__float_as_int(fmaxf(p, FLT_MIN)));
+    }
 }
 
 // ------------------------------------------------------------------ few targets
@@ -684,10 +688,10 @@ void launch_stage_targets(const float *P, int64_t k_pad, int64_t /*k*/, const in
     float *sL = sP + (int64_t)T * k_pad;
     float *sE = sL + (int64_t)T * k_pad;
     float *sF = sE + (int64_t)T * k_pad;
-    dim3 g((unsigned)((k_pad + 255) / 256), (unsigned)T);
+    if (T <= 0) return;
     {
         KMark km_("stage_targets_kernel", s);
-        stage_targets_kernel<<<g, 256, 0, s>>>(P, k_pad, targets, T, sP, sL, sE, sF);
+        stage_targets_kernel<<<(unsigned)T, 256, 0, s>>>(P, k_pad, targets, T, sP, sL, sE, sF);
     }
 }
 
