@@ -624,9 +624,10 @@ def batch_section(dd, ctx, dev, stream, flush, args, S: int = 64, max_pts: int =
                         % (len(wls), min(n_vs), max(n_vs), min(ks), max(ks), nT, nT * S),
             "ms_per_batch": round(med, 3), "fields_per_s": round(2 * nT / (med / 1e3), 1),
             "paths_per_s": round(nT * S / (med / 1e3), 1),
-            "field_flop_per_batch": 8.0 * elem_targets, "paths_ok_frac": float(np.mean(stn == 0)),
+            "field_fp32_instructions_per_batch": 4.0 * elem_targets, "paths_ok_frac": float(np.mean(stn == 0)),
             "tile_shapes": dd.dd_tuning_table().strip().splitlines(), "kernels": kernels,
-            "preproc": {"pcg_iters_total": pcg_iters, "seconds": round(pre, 2)}, "launches_per_batch": 5}
+            "preproc": {"pcg_iters_total": pcg_iters, "seconds": round(pre, 2)},
+            "launches_per_batch": round(sum(c for c, _ in kt.values()) / max(len(ms), 1), 2)}
 
 
 def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1, 2, 3, 4),
