@@ -38,3 +38,25 @@ def test_binding_covers_header():
     for n in declared_functions():
         assert hasattr(dd, n), n
     assert dd.dd_version() == 100
+
+
+def header_constants():
+    """Every DD_ name given a value in dd.h: enum members and numeric #defines."""
+    src = open(os.path.join(ROOT, "include", "dd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    vals = {}
+    for name, v in re.findall(r"#define\s+(DD_[A-Z0-9_]+)\s+([-+0-9.eE]+)\s*$", src, flags=re.M):
+        vals[name] = float(v)
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, v in re.findall(r"(DD_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            vals[name] = int(v)
+    return vals
+
+
+def test_binding_constants_match_header():
+    from paper_1708_02845_gb300 import dd
+    vals = header_constants()
+    assert len(vals) >= 26 and vals["DD_TILE_EXACT_BELOW"] == 0.25 and vals["DD_EBUDGET"] == -7
+    for name, v in vals.items():
+        assert hasattr(dd, name), name
+        assert getattr(dd, name) == v, (name, getattr(dd, name), v)
