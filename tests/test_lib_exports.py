@@ -60,3 +60,15 @@ def test_binding_constants_match_header():
     for name, v in vals.items():
         assert hasattr(dd, name), name
         assert getattr(dd, name) == v, (name, getattr(dd, name), v)
+
+
+def test_no_device_is_an_error_not_a_fallback():
+    """Without a usable GPU the context cannot be created: dd_create reports
+    an error status (no CPU path exists behind the boundary)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1708_02845_gb300 import dd
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_create(0)
+    assert e.value.status in (dd.DD_ECUDA, dd.DD_EINVAL)
