@@ -30,7 +30,7 @@
 //    base-2 logarithm is formed once per CTA as one FP32 number and reused for
 //    TN targets (one subtraction and one multiply-add per KL term); the
 //    (row, target) pairs whose KL lands below DD_TILE_EXACT_BELOW are then
-//    recomputed in the exact split form by the same CTA.
+//    recomputed in the exact split form by a second kernel (fix_kl_kernel).
 #include <algorithm>
 #include <vector>
 #include <type_traits>
@@ -361,7 +361,7 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
     const int ty = tid / COLG;        // row group: rows ty*RM ..
 
     // two-level summation: 32-term chunk sums, added into the totals with a
-    // compensated (Kahan) sum for KL, whose terms cancel near the target
+    // compensated (Kahan) sum for KL, whose terms partly cancel
     float kl[RM][CN], tv[RM][CN], klc[RM][CN];
 #pragma unroll
     for (int r = 0; r < RM; ++r)
