@@ -5,7 +5,7 @@ import pytest
 
 from oracle.topology import split_boundary, edge_triangle_counts
 from synthetic import workloads
-from synthetic.meshes import disk_rings, grid_obstacles
+from synthetic.meshes import convex_holes, disk_rings, grid_obstacles
 
 
 @pytest.fixture(scope="module")
@@ -17,7 +17,8 @@ def dd():
 
 
 @pytest.mark.parametrize("mesh", [disk_rings(16, 128), workloads.grid140(T=1, S=0).mesh,
-                                  grid_obstacles(7, [(2, 2, 2, 3)])])
+                                  grid_obstacles(7, [(2, 2, 2, 3)]), convex_holes(500, 4, 2),
+                                  convex_holes(2000, 2, 3)])
 def test_counts_match_oracle(dd, mesh):
     idx, off = mesh.loop_arrays()
     n_v, k, m, ne = dd.dd_check_mesh(mesh.xy, mesh.tri, idx, off)
