@@ -12,7 +12,7 @@ import scipy.sparse.linalg as spla
 from oracle.laplacian import cotan_laplacian
 from oracle.topology import split_boundary
 from synthetic import workloads
-from synthetic.meshes import disk_rings, grid_obstacles
+from synthetic.meshes import convex_holes, disk_rings, grid_obstacles
 
 
 @pytest.fixture(scope="module")
@@ -36,6 +36,7 @@ MESHES = {
     "disk16": lambda: disk_rings(16, 128),
     "grid37": lambda: workloads.small_grid(37, 3, T=1, S=0).mesh,
     "grid140": lambda: workloads.grid140(T=1, S=0).mesh,
+    "holes10k": lambda: convex_holes(10000, 4, 1),          # unstructured Delaunay, five boundary loops
 }
 
 
