@@ -12,6 +12,16 @@ N > 1 runs one process per GPU under torch.distributed.run; every rank
 processes its own target batches (weak scaling, no data-path collective).
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the
 same workload (rank 0 only).
+
+The JSON line: `value` from CUDA events around each step (inputs resident,
+L2 flushed between steps outside the events), `e2e` through the same call
+with pinned host buffers, `kernels` (live per-kernel times from the
+library's own events), `roofline` for the dominant kernel with
+`roofline_fields` / `roofline_walk` for the other of the two, `clocks`
+sampled during the timed region (measured once more, with `remeasured`, if
+they show a slowdown or a clock lock), `cpu_baseline` (the oracle on every
+host core), `step_bf16x3` (the same step on the split-BF16 path), and with
+no `--section` the grid450, batch, serving and census measurements.
 """
 
 import argparse
