@@ -1,0 +1,155 @@
+"""bench.py's step measurement on the CPU with a stand-in library and
+stand-in CUDA events: the JSON line carries the contract's keys with
+consistent values, the dominant kernel's roofline is chosen from the live
+per-kernel times, and a timed region whose clocks show a slowdown is
+measured once more.  (The numbers are the stand-ins'; the GPU run gives the
+real ones.)"""
+import json
+import os
+import sys
+import time
+import types
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import bench  # noqa: E402
+
+
+class _Event:
+    def __init__(self, enable_timing=True):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = time.perf_counter()
+
+    def elapsed_time(self, other):
+        return max((other.t - self.t) * 1e3, 1e-3)
+
+
+def _fake_dd(n_v, k, kernel_ms):
+    m = types.ModuleType("paper_1708_02845_gb300.dd")
+    m.DD_F_KL, m.DD_F_TV, m.DD_F_KLT = 1, 2, 4
+    m.DD_PREC_FP32, m.DD_PREC_BF16X3, m.DD_PREC_SPARSE = 0, 1, 2
+    m.dd_create = lambda dev, stream=0: object()
+    m.dd_destroy = lambda ctx: None
+    m.dd_sync = lambda ctx: None
+    m.dd_load_mesh = lambda ctx, xy, tri, idx, off: 0
+    m.dd_mesh_info = lambda ctx, mid: {"n_v": n_v, "k": k, "k_pad": (k + 3) // 4 * 4}
+    m.dd_poisson_kernel = lambda ctx, mid, rtol, it: (24, 2e-16)
+    m.timing = {"on": False}
+
+    def query(ctx, mid, tg, sr, f, prec, tf, max_pts, fields, xy, ln, st):
+        fields.fill_(0.5)
+        ln.fill_(12)
+        st.zero_()
+
+    def distance(ctx, mid, tg, f, prec, out):
+        out.fill_(0.5)
+
+    def kernel_timing(ctx, mode):
+        if mode == 1:
+            m.timing["on"] = True
+            return {}
+        on, m.timing["on"] = m.timing["on"], False
+        return dict(kernel_ms) if on else {}
+
+    m.dd_query = query
+    m.dd_distance = distance
+    m.dd_trace_fields = lambda ctx, mid, f, tg, sr, max_pts, xy, ln, st: None
+    m.dd_kernel_timing = kernel_timing
+    return m
+
+
+@pytest.fixture
+def stand_ins(monkeypatch):
+    def install(n_v, k, kernel_ms, clock_records):
+        import paper_1708_02845_gb300 as pkg
+        import paper_1708_02845_gb300.build as b
+        fake = _fake_dd(n_v, k, kernel_ms)
+        monkeypatch.setitem(sys.modules, "paper_1708_02845_gb300.dd", fake)
+        monkeypatch.setattr(pkg, "dd", fake, raising=False)
+        monkeypatch.setattr(b, "build", lambda *a, **kw: "")
+        real_empty = torch.empty
+
+        def empty(*a, device=None, **kw):
+            return real_empty(*a, **kw)
+
+        monkeypatch.setattr(torch, "empty", empty)
+        monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
+        monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+        monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+        monkeypatch.setattr(torch.cuda, "Event", _Event)
+        monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: types.SimpleNamespace(cuda_stream=0))
+        records = list(clock_records)
+        monkeypatch.setattr(bench.ClockSampler, "start", lambda self: None)
+        monkeypatch.setattr(bench.ClockSampler, "stop", lambda self: records.pop(0) if records else
+                            {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3})
+        monkeypatch.setattr(bench, "workload_batches", _small_batches)
+        return fake
+    return install
+
+
+def _small_batches(rank):
+    from synthetic import workloads
+    wl = workloads.grid140(T=bench.T_BATCH, S=bench.S_PER_TARGET)
+    return wl, [(wl.targets, wl.sources)] * 2
+
+
+def _args(steps=3):
+    return types.SimpleNamespace(steps=steps, warmup=3, section="step", stream=False, no_cpu_baseline=True,
+                                 gpus=1, impl="ours")
+
+
+KERNELS = {"stage_targets_kernel": (3, 0.04), "field_tile_kernel": (3, 0.67), "fix_kl_kernel": (3, 0.2),
+           "rates_kernel": (3, 0.075), "vertex_decision_kernel": (3, 0.17), "trace_kernel": (3, 1.0)}
+GOOD = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+
+
+def test_step_line_keeps_the_contract(stand_ins):
+    stand_ins(18174, 1028, KERNELS, [GOOD])
+    line = bench.run_ours(_args(), 0, 1, 0)
+    json.dumps(line)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks",
+                "kernels"):
+        assert key in line, key
+    assert line["metric"] == bench.METRIC and line["unit"] == "fields/s" and line["n_gpus"] == 1
+    assert line["steps"] == 3 and line["warmup"] == 3 and line["higher_is_better"] is True
+    assert "workload" in line["config"] and line["vs_baseline"] is None
+    assert abs(line["value"] - 2 * 64 / (line["ms_per_step"] / 1e3)) <= 1e-3 * line["value"] + 1.0
+    r = line["roofline"]
+    assert r["kernel"] == "trace_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["peak"] == bench.peaks()[0]["hbm_gbs"] and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
+    assert r["traffic"] == bench.WALK_TRAFFIC_BYTES
+    assert r["algorithmic_bytes"] == bench.WALK_BYTES_PER_POINT * 64 * 256 * 12
+    f = line["roofline_fields"]
+    assert f["kernel"] == "field_tile_kernel" and f["bound"] == "alu" and f["traffic"] == bench.TILE_TRAFFIC_BYTES
+    assert f["algorithmic_fp32_ops"] == 4.0 * 18174 * 1028 * 64
+    assert abs(f["ms_per_launch"] - 0.67 / 3) < 1e-4
+    assert line["gpu_launches"] == 18 and line["roofline_walk"] is None
+    e = line["e2e"]
+    assert e["unit"] == "fields/s" and e["h2d_bytes_per_step"] == 64 * 4 + 64 * 256 * 4
+    assert e["d2h_bytes_per_step"] == 2 * 64 * 18174 * 4 + 64 * 256 * 8 + 64 * 256 * 12 * 8
+    assert "remeasured" not in line and line["clocks"] == GOOD
+    assert line["step_bf16x3"]["tv_identical"] is True
+
+
+def test_tile_named_when_it_dominates(stand_ins):
+    k = dict(KERNELS, field_tile_kernel=(3, 1.5))
+    stand_ins(18174, 1028, k, [GOOD])
+    line = bench.run_ours(_args(), 0, 1, 0)
+    assert line["roofline"]["kernel"] == "field_tile_kernel" and line["roofline"]["bound"] == "alu"
+    assert line["roofline_walk"]["kernel"] == "trace_kernel" and line["roofline_fields"] is None
+
+
+def test_throttled_region_is_measured_again(stand_ins):
+    hot = {"sm_mhz": 1500.0, "sm_max_mhz": 2070.0, "reasons": ["hw_thermal_slowdown"], "samples": 3}
+    stand_ins(18174, 1028, KERNELS, [hot, GOOD])
+    line = bench.run_ours(_args(), 0, 1, 0)
+    assert line["remeasured"]["first"]["reasons"] == ["hw_thermal_slowdown"]
+    assert line["clocks"] == GOOD
+    assert np.isfinite(line["value"])
