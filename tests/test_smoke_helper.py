@@ -42,8 +42,8 @@ def _case():
     P = po.full()
     t = int(wl.targets[0])
     src = np.asarray(wl.sources[0], dtype=np.int32)
-    others = [int(v) for v in po.I if int(v) != t and int(v) not in set(src.tolist())]
-    targets = [t] + [others[len(others) * j // 4] for j in (1, 2, 3)]
+    targets = entry._query_targets(po.I, t, src)
+    assert all(bool(~wl.mesh.boundary_flags()[v]) for v in targets)
     return P, targets, np.tile(src, (4, 1))
 
 
