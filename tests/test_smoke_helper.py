@@ -56,3 +56,61 @@ def test_query_check_accepts_the_oracle_and_rejects_a_planted_error():
     assert fake.calls == [(targets, (4, 8), 3, 0, 1, 256)]
     with pytest.raises(AssertionError):
         entry._query_check(_FakeDD(P, scale=1.0 + 1e-4), None, 0, P, targets, sources, "cpu")
+
+
+def _fake_library(P, mesh):
+    from oracle.trace import Tracer
+    import types
+    m = types.ModuleType("paper_1708_02845_gb300.dd")
+    m.DD_F_KL, m.DD_F_TV, m.DD_PREC_FP32, m.DD_TRACE_OK = 1, 2, 0, 0
+    m.dd_create = lambda dev, stream=0: object()
+    m.dd_destroy = lambda ctx: None
+    m.dd_sync = lambda ctx: None
+    m.dd_load_mesh = lambda ctx, xy, tri, idx, off: 0
+    m.dd_poisson_kernel = lambda ctx, mid, rtol, it: (30, 1e-16)
+    tracer = Tracer(mesh.xy, mesh.tri)
+
+    def fields(targets, out):
+        for a, t in enumerate(targets):
+            kl = kl_field_fast(P, P[t])
+            out[0, a] = torch.from_numpy(np.where(np.isfinite(kl), kl, 87.0).astype(np.float32))
+            out[1, a] = torch.from_numpy(tv_field(P, P[t]).astype(np.float32))
+
+    def paths(t, sources, max_pts, xy, ln, st, base=0):
+        kl = kl_field_fast(P, P[t])
+        for s, q in enumerate(sources):
+            path, status = tracer.trace(kl, int(q), int(t), max_pts=max_pts)
+            xy[base + s, :len(path)] = torch.from_numpy(np.asarray(path, dtype=np.float32))
+            ln[base + s] = len(path)
+            st[base + s] = status
+
+    m.dd_distance = lambda ctx, mid, targets, f, prec, out: fields(targets, out)
+    m.dd_trace = lambda ctx, mid, t, f, sources, max_pts, xy, ln, st: paths(t, sources, max_pts, xy, ln, st)
+
+    def query(ctx, mid, targets, sources, f, prec, tf, max_pts, out, xy, ln, st):
+        fields(targets, out)
+        S = np.asarray(sources).shape[1]
+        for a, t in enumerate(targets):
+            paths(t, np.asarray(sources)[a], max_pts, xy, ln, st, base=a * S)
+
+    m.dd_query = query
+    return m
+
+
+def test_smoke_runs_end_to_end_with_a_stand_in_library(monkeypatch, capsys):
+    """The whole of smoke() on the CPU: the stand-in returns the oracle's own
+    fields and paths, so every check in smoke() must pass and it must report
+    both the one-target and the four-target errors."""
+    import paper_1708_02845_gb300 as pkg
+    wl = workloads.disk(n_rings=8, n_seg=64, n_sources=8)
+    po = PoissonOracle(wl.mesh.xy, wl.mesh.tri, wl.mesh.loops)
+    fake = _fake_library(po.full(), wl.mesh)
+    monkeypatch.setitem(sys.modules, "paper_1708_02845_gb300.dd", fake)
+    monkeypatch.setattr(pkg, "dd", fake, raising=False)
+    real_empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, device=None, **kw: real_empty(*a, **kw))
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: True)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: type("S", (), {"cuda_stream": 0})())
+    entry.smoke()
+    out = capsys.readouterr().out
+    assert "smoke ok" in out and "query4=" in out
