@@ -153,3 +153,21 @@ def test_throttled_region_is_measured_again(stand_ins):
     assert line["remeasured"]["first"]["reasons"] == ["hw_thermal_slowdown"]
     assert line["clocks"] == GOOD
     assert np.isfinite(line["value"])
+
+
+def test_reference_arm_line():
+    """`--impl reference` times the oracle on the host cores and prints the
+    same metric, unit and direction as the library's line, with its own
+    cpu_baseline and an e2e that moves no bytes."""
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["higher_is_better"] is True and line["value"] > 0 and line["steps"] == 1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
