@@ -179,8 +179,10 @@ dd_status dd_unload_mesh(dd_ctx *ctx, int32_t mesh);
 dd_status dd_mesh_info(dd_ctx *ctx, int32_t mesh, int64_t *info);
 
 /* Solve for the Poisson kernel, Eq. (32)-(33): (-L_II) X = L_IB for all k
- * right-hand sides at once by Jacobi-preconditioned conjugate gradients in
- * FP64 on the device, iterating until every column's residual satisfies
+ * right-hand sides at once by conjugate gradients in FP64 on the device,
+ * preconditioned by a smoothed-aggregation multigrid V-cycle (the diagonal of
+ * -L_II on meshes under 256 interior vertices or where no hierarchy can be
+ * built), iterating until every column's residual satisfies
  * ||r_b|| <= rtol * ||L_IB e_b|| or max_iter iterations have run.  The result
  * is stored as FP32 P (row pitch k_pad, boundary rows the identity, negative
  * round-off clamped to 0, values below FLT_MIN flushed to 0).  All columns
@@ -416,10 +418,17 @@ void dd_server_destroy(dd_server *sv);
  *   P        device float32 [n_v][k_pad] Poisson kernel (e.g. copied from
  *            dd_get_poisson_kernel and padded), k_pad a multiple of 4 with
  *            zero padding columns, 16-byte aligned
- *   targets  device int32 [T] interior vertex ids (not checked)
+ *   targets  device int32 [T] interior vertex ids, 4-byte aligned.  An id
+ *            outside [0, n_v) is detected on the device: it is never used
+ *            as a row index, and the call returns DD_EINVAL (the output is
+ *            then unspecified)
  *   f_mask   DD_F_KL | DD_F_TV as in dd_distance
- *   out      device float32 [nf][T][n_v], layout as in dd_distance
+ *   out      device float32 [nf][T][n_v], layout as in dd_distance, 4-byte
+ *            aligned
  *   cuda_stream  stream for the work (NULL = legacy default stream)
+ * The fields equal dd_distance's bit for bit.  Nothing is timed or tuned:
+ * for T > 2 the tile shape is a fixed function of T (dd_distance's autotuner
+ * would run timed launches the first time it meets a size class).
  * Scratch: one fixed device array per GPU (16 MiB, held until the process
  * exits) holds the staged target rows, so T * k_pad must not exceed 1,048,576
  * (DD_EINVAL otherwise).  Every call shares that array: calls whose work
@@ -427,7 +436,8 @@ void dd_server_destroy(dd_server *sv);
  * serialised by the caller.  The first call on a device looks up the array's
  * device address; make that first call before any stream capture.  The call
  * returns after the work finished (it synchronises the stream).
- * Errors: DD_EINVAL, DD_ECUDA, DD_ETIMEOUT (a bounded device wait gave up). */
+ * Errors: DD_EINVAL (sizes, alignment, an id out of range), DD_ECUDA,
+ * DD_ETIMEOUT (a bounded device wait gave up). */
 dd_status dd_distance_noalloc(const float *P, int64_t n_v, int64_t k_pad, const int32_t *targets,
                               int32_t T, uint32_t f_mask, float *out, void *cuda_stream);
 

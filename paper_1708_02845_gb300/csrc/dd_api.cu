@@ -225,7 +225,7 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
         if (T > 65535) return set_err(ctx, DD_EINVAL, "DD_PREC_SPARSE: at most 65,535 targets per call");
         if ((st = ensure_scratch(ctx, S_STAGE, sparse_stage_bytes(m.k_pad, T))) != DD_OK) return st;
         float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
-        launch_stage_targets(m.P, m.k_pad, m.k, d_targets, T, stage, ctx->stream);
+        launch_stage_targets(m.P, m.n_v, m.k_pad, d_targets, T, stage, ctx->stream);
         launch_sparse_fields(m, d_targets, stage, T, kl, tv, klt, ctx->d_err, ctx->stream);
         CK(cudaGetLastError(), "sparse field kernel launch");
         return DD_OK;
@@ -233,7 +233,7 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
     st = ensure_scratch(ctx, S_STAGE, 4 * (size_t)T * m.k_pad * sizeof(float));
     if (st != DD_OK) return st;
     float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
-    launch_stage_targets(m.P, m.k_pad, m.k, d_targets, T, stage, ctx->stream);
+    launch_stage_targets(m.P, m.n_v, m.k_pad, d_targets, T, stage, ctx->stream);
     if (kl || tv) launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream);
     if (klt) {
         // the target-weighted KL is the reverse-KL member of the f-divergence kernels
@@ -665,7 +665,7 @@ dd_status dd_divergence(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32
         }
         if ((st = ensure_scratch(ctx, S_STAGE, 4 * (size_t)T * m->k_pad * sizeof(float))) != DD_OK) return st;
         float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
-        launch_stage_targets(m->P, m->k_pad, m->k, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T,
+        launch_stage_targets(m->P, m->n_v, m->k_pad, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T,
                              stage, ctx->stream);
         std::string err;
         if ((st = launch_fdiv(m->P, m->n_v, m->k_pad, stage, T, family, param, dst, ctx->stream, err)) != DD_OK)

@@ -72,17 +72,26 @@ __device__ __forceinline__ void accumulate_kl(float px, float lmx, float ex, flo
 // stage_P / stage_L / stage_E / stage_F: [T][k_pad] target row, its mantissa
 // log (table), biased exponent and mantissa log2 (hardware), the target-side
 // arguments clamped at FLT_MIN.  One CTA per target, so that the log table
-// (FP64, slow on this part) is built once per target row.
-__global__ void stage_targets_kernel(const float *__restrict__ P, int64_t k_pad, const int32_t *__restrict__ targets,
-                                     int32_t T, float *__restrict__ sP, float *__restrict__ sL,
-                                     float *__restrict__ sE, float *__restrict__ sF) {
+// (FP64, slow on this part) is built once per target row.  A target id
+// outside [0, n_v) reads nothing: its staged rows are zero-filled and
+// *bad_id (when given) is set to 1.
+__global__ void stage_targets_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
+                                     const int32_t *__restrict__ targets, int32_t T, float *__restrict__ sP,
+                                     float *__restrict__ sL, float *__restrict__ sE, float *__restrict__ sF,
+                                     int *__restrict__ bad_id) {
     __shared__ float tab[2 * kLogTab];
     build_log_table(tab);
     __syncthreads();
     const int a = blockIdx.x;
     if (a >= T) return;
-    const float *row = P + (int64_t)targets[a] * k_pad;
     const int64_t o = (int64_t)a * k_pad;
+    const int32_t t = targets[a];
+    if (t < 0 || (int64_t)t >= n_v) {
+        if (threadIdx.x == 0 && bad_id) atomicExch(bad_id, 1);
+        for (int64_t b = threadIdx.x; b < k_pad; b += blockDim.x) sP[o + b] = sL[o + b] = sE[o + b] = sF[o + b] = 0.0f;
+        return;
+    }
+    const float *row = P + (int64_t)t * k_pad;
     for (int64_t b = threadIdx.x; b < k_pad; b += blockDim.x) {
         const float p = row[b];
         float lm, E;
@@ -682,8 +691,8 @@ int tune_variant(const float *P, int64_t n_v, int64_t k_pad, const float *sP, co
 
 }  // namespace
 
-void launch_stage_targets(const float *P, int64_t k_pad, int64_t /*k*/, const int32_t *targets, int32_t T,
-                          float4 *stage, cudaStream_t s) {
+void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int32_t *targets, int32_t T,
+                          float4 *stage, cudaStream_t s, int *bad_id) {
     float *sP = reinterpret_cast<float *>(stage);
     float *sL = sP + (int64_t)T * k_pad;
     float *sE = sL + (int64_t)T * k_pad;
@@ -691,12 +700,12 @@ void launch_stage_targets(const float *P, int64_t k_pad, int64_t /*k*/, const in
     if (T <= 0) return;
     {
         KMark km_("stage_targets_kernel", s);
-        stage_targets_kernel<<<(unsigned)T, 256, 0, s>>>(P, k_pad, targets, T, sP, sL, sE, sF);
+        stage_targets_kernel<<<(unsigned)T, 256, 0, s>>>(P, n_v, k_pad, targets, T, sP, sL, sE, sF, bad_id);
     }
 }
 
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, float *out_kl,
-                        float *out_tv, int *err_flag, cudaStream_t s) {
+                        float *out_tv, int *err_flag, cudaStream_t s, int variant) {
     const float *sP = reinterpret_cast<const float *>(stage);
     const float *sL = sP + (int64_t)T * k_pad;
     const float *sE = sL + (int64_t)T * k_pad;
@@ -720,7 +729,8 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
         }
         return;
     }
-    const int v = tune_variant(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+    const int v = (variant >= 0 && variant < kNumShapes) ? variant
+                                                         : tune_variant(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
     launch_variant(v, P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
     if (out_kl) {
         const BatchProblem q{P, n_v, k_pad, sP, sL, sE, T, v, out_kl, nullptr};

@@ -87,11 +87,15 @@ dd_status store_poisson(DevMesh &m, const double *P, cudaStream_t s, std::string
 // arrays back to back -- P[t_a,b], the log-mantissa lm (table), the exponent E
 // as the biased float 12582912 + 127 + E (exact; only differences of two are
 // used), and the hardware base-2 log of the mantissa (streaming kernel).
-void launch_stage_targets(const float *P, int64_t k_pad, int64_t k, const int32_t *targets, int32_t T,
-                          float4 *stage, cudaStream_t s);
-// FP32 fields.  out_kl / out_tv: [T][n_v] (either may be null).
+// Target ids outside [0, n_v) are not read: their rows are zero-filled and
+// *bad_id (if not null) is set to 1.
+void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int32_t *targets, int32_t T,
+                          float4 *stage, cudaStream_t s, int *bad_id = nullptr);
+// FP32 fields.  out_kl / out_tv: [T][n_v] (either may be null).  variant: the
+// tile shape for T > 2 (0, 1, 2), or -1 for the autotuner's choice (which may
+// run timed launches the first time a size class is seen).
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T,
-                        float *out_kl, float *out_tv, int *err_flag, cudaStream_t s);
+                        float *out_kl, float *out_tv, int *err_flag, cudaStream_t s, int variant = -1);
 // One problem of a multi-domain field launch, and one output tile of it.
 struct BatchProblem {
     const float *P;

@@ -14,8 +14,14 @@
 // a device and kept until the process exits.  Its device address is looked
 // up once per device (cudaGetSymbolAddress, with that device current) on the
 // first call there; host code never passes the symbol itself to a kernel.
+//
+// Nothing here times or tunes: for more than two targets the tile shape is a
+// fixed function of T (the autotuner behind dd_distance would run timed
+// launches and synchronise the first time it meets a size class), and every
+// tile shape gives bit-identical fields, so the result equals dd_distance's.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "dd_internal.h"
@@ -26,7 +32,7 @@ constexpr int64_t kNoallocStageFloats = 4LL * (1LL << 20);   // 4 arrays x T*k_p
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) float g_noalloc_stage[kNoallocStageFloats];
-__device__ __align__(256) int g_noalloc_flag[64];
+__device__ __align__(256) int g_noalloc_flag[64];    // [0]: a bounded wait gave up, [1]: a target id out of range
 
 std::mutex g_noalloc_mutex;
 float *g_stage_ptr[kMaxDevices] = {};
@@ -51,12 +57,19 @@ dd_status noalloc_setup(int dev, float **stage, int **flag) {
     return DD_OK;
 }
 
+// the tile shape for T targets: narrow target tiles for few targets, wide for many
+int fixed_tile_shape(int32_t T) { return T <= 16 ? 2 : (T <= 32 ? 1 : 0); }
+
 }  // namespace
 
 extern "C" dd_status dd_distance_noalloc(const float *P, int64_t n_v, int64_t k_pad, const int32_t *targets,
                                          int32_t T, uint32_t f_mask, float *out, void *cuda_stream) {
     if (!P || !targets || !out) return DD_EINVAL;
     if (n_v < 1 || T < 1 || k_pad < 4 || (k_pad % 4) != 0) return DD_EINVAL;
+    // 16-byte loads of P, 4-byte accesses of the ids and the output
+    if ((reinterpret_cast<uintptr_t>(P) & 15) || (reinterpret_cast<uintptr_t>(targets) & 3) ||
+        (reinterpret_cast<uintptr_t>(out) & 3))
+        return DD_EINVAL;
     if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV))) return DD_EINVAL;
     if ((int64_t)T * k_pad > kNoallocStageFloats / 4) return DD_EINVAL;   // beyond the fixed scratch
     int dev = 0;
@@ -69,21 +82,25 @@ extern "C" dd_status dd_distance_noalloc(const float *P, int64_t n_v, int64_t k_
     dd_status st = noalloc_setup(dev, &stage, &flag);
     if (st != DD_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // the error flag keeps the previous call's value: clear it first
-    if (cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) {
+    // the flags keep the previous call's values: clear them first
+    if (cudaMemsetAsync(flag, 0, 2 * sizeof(int), s) != cudaSuccess) {
         cudaGetLastError();
         return DD_ECUDA;
     }
     float *kl = (f_mask & DD_F_KL) ? out : nullptr;
     float *tv = (f_mask & DD_F_TV) ? out + ((f_mask & DD_F_KL) ? (int64_t)T * n_v : 0) : nullptr;
-    launch_stage_targets(P, k_pad, k_pad, targets, T, reinterpret_cast<float4 *>(stage), s);
-    launch_fields_fp32(P, n_v, k_pad, reinterpret_cast<const float4 *>(stage), T, kl, tv, flag, s);
+    // an id outside [0, n_v) is never used as a row index: the staging kernel
+    // zero-fills its rows and raises flag[1]
+    launch_stage_targets(P, n_v, k_pad, targets, T, reinterpret_cast<float4 *>(stage), s, flag + 1);
+    launch_fields_fp32(P, n_v, k_pad, reinterpret_cast<const float4 *>(stage), T, kl, tv, flag, s,
+                       fixed_tile_shape(T));
     if (cudaGetLastError() != cudaSuccess) return DD_ECUDA;
-    int h = 0;
-    if (cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    int h[2] = {0, 0};
+    if (cudaMemcpyAsync(h, flag, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return DD_ECUDA;
     }
-    return h ? DD_ETIMEOUT : DD_OK;
+    if (h[1]) return DD_EINVAL;
+    return h[0] ? DD_ETIMEOUT : DD_OK;
 }
