@@ -672,10 +672,12 @@ def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1,
     """Spurious-local-minimum census (Section V): on convex-holes Delaunay
     meshes of growing resolution (the same four domains at every size), the
     share of targets whose TV field, KL field and target-weighted KL field
-    (the reverse direction, Sum_b P[t,b] log(P[t,b]/P[x,b])), and the sparse
-    KL, TV and target-weighted KL fields (the target row's entries below
-    1/sqrt(n) of its maximum merged into one bin), have
-    an interior vertex other than the target with no lower neighbour.  All interior
+    (the reverse direction, Sum_b P[t,b] log(P[t,b]/P[x,b])), the sparse KL,
+    TV and target-weighted KL fields of Section V (each row's entries below
+    1/sqrt(n) of its maximum eliminated, the weight row deciding the terms),
+    and the merged-bin target-weighted KL (an extension: the target row's
+    small entries merged into one bin), have an interior vertex other than
+    the target with no lower neighbour.  All interior
     targets up to max_targets, else max_targets spread evenly over them.
     Everything runs through the library: the FP64 kernel solve, the FP32
     fields, the minimum test."""
@@ -686,7 +688,7 @@ def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1,
     for n_goal in sizes:
         agg = {"n_goal": n_goal, "meshes": 0, "n_v": [], "k": [], "targets": 0,
                "tv": [0, 0], "kl": [0, 0], "kl_target_weighted": [0, 0], "kl_sparse": [0, 0], "tv_sparse": [0, 0],
-               "kl_target_weighted_sparse": [0, 0]}
+               "kl_target_weighted_sparse": [0, 0], "kl_target_weighted_merged": [0, 0]}
         for seed in seeds:
             mesh = convex_holes(n_goal, seed=seed)
             idx, off = mesh.loop_arrays()
@@ -704,9 +706,11 @@ def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1,
             dd.dd_sparsify(ctx, mid)
             sparse_f = torch.empty((3, T, mesh.n_v), dtype=torch.float32, device=dev)
             dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV | dd.DD_F_KLT, dd.DD_PREC_SPARSE, sparse_f)
+            merged_f = torch.empty((1, T, mesh.n_v), dtype=torch.float32, device=dev)
+            dd.dd_distance(ctx, mid, targets, dd.DD_F_KLT, dd.DD_PREC_SPARSE_MERGED, merged_f)
             for name, f in (("kl", fields[0]), ("tv", fields[1]), ("kl_target_weighted", rev),
                             ("kl_sparse", sparse_f[0]), ("tv_sparse", sparse_f[1]),
-                            ("kl_target_weighted_sparse", sparse_f[2])):
+                            ("kl_target_weighted_sparse", sparse_f[2]), ("kl_target_weighted_merged", merged_f[0])):
                 c = dd.dd_local_minima(ctx, mid, f.contiguous(), targets, None)
                 agg[name][0] += int(np.count_nonzero(c))
                 agg[name][1] += int(c.sum())
@@ -715,7 +719,8 @@ def census_section(dd, ctx, dev, sizes=(175, 500, 2000, 10000, 40000), seeds=(1,
             agg["k"].append(dd.dd_mesh_info(ctx, mid)["k"])
             agg["targets"] += T
             dd.dd_unload_mesh(ctx, mid)
-        for name in ("tv", "kl", "kl_target_weighted", "kl_sparse", "tv_sparse", "kl_target_weighted_sparse"):
+        for name in ("tv", "kl", "kl_target_weighted", "kl_sparse", "tv_sparse", "kl_target_weighted_sparse",
+                     "kl_target_weighted_merged"):
             agg[name] = {"targets_with_minima": agg[name][0], "minima": agg[name][1],
                          "share": round(agg[name][0] / agg["targets"], 4)}
         rows.append(agg)

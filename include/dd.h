@@ -80,18 +80,32 @@ enum { DD_F_KL = 1, DD_F_TV = 2, DD_F_KLT = 4 };
  *  DD_PREC_BF16X3 KL cross term sum_b P[x,b] log P[t,b] as a tensor-core GEMM
  *                 of split BF16 hi/lo operands (hi*hi + hi*lo + lo*hi, FP32
  *                 accumulation); TV and KLT are always FP32
- *  DD_PREC_SPARSE the sparse fields of Section V (small entries of P
- *                 eliminated, see dd_sparsify), FP32 as DD_PREC_FP32.  The
- *                 target row keeps S_t = {b : P[t,b] >= theta max_b' P[t,b']}
- *                 (FP32 product); the other columns merge into one bin of
- *                 mass M_y = sum_{b not in S_t} P[y,b]:
- *                   KL~_t(x) = sum_{b in S_t} P[x,b] log(P[x,b]/P[t,b])
+ *  DD_PREC_SPARSE the sparse fields of Section V: P sparsified by
+ *                 eliminating the entries below a threshold (see
+ *                 dd_sparsify), FP32 as DD_PREC_FP32.  Row y keeps
+ *                 S_y = {b : P[y,b] >= theta max_b' P[y,b'], P[y,b] > 0}
+ *                 (FP32 product), P~ is P with the other entries set to 0.
+ *                 In Eq. 35 the weight row's eliminated entries drop their
+ *                 terms and the other row enters through its logarithm from
+ *                 the full P:
+ *                   KLT~_t(x) = sum_{b in S_t} P[t,b] log(P[t,b]/P[x,b])
+ *                   KL~_t(x)  = sum_{b in S_x} P[x,b] log(P[x,b]/P[t,b])
+ *                   TV~_t(x)  = sum_b |P~[x,b] - P~[t,b]|
+ *                 (approximations, not divergences: KL~ and KLT~ can be
+ *                 negative; all three are 0 at x = t).  KL~ and TV~ read
+ *                 only the sparse copy of P; KLT~ reads the dense P at the
+ *                 4-column blocks holding S_t
+ *  DD_PREC_SPARSE_MERGED  an extension, not in the paper: S_t decides for
+ *                 both rows and the other columns merge into one bin of mass
+ *                 M_y = sum_{b not in S_t} P[y,b]:
+ *                   KL^_t(x) = sum_{b in S_t} P[x,b] log(P[x,b]/P[t,b])
  *                              + M_x log(M_x / M_t)
- *                   TV~_t(x) = sum_{b in S_t} |P[x,b] - P[t,b]| + |M_x - M_t|
+ *                   KLT^_t(x) likewise with the roles of x and t swapped
+ *                   TV^_t(x) = sum_{b in S_t} |P[x,b] - P[t,b]| + |M_x - M_t|
  *                 (divergences of the coarse-grained harmonic measures:
- *                 0 <= KL~ <= KL, 0 <= TV~ <= TV, both 0 at x = t); each row
+ *                 0 <= KL^ <= KL, 0 <= TV^ <= TV, all 0 at x = t); each row
  *                 is read only at the 4-column blocks holding S_t */
-enum { DD_PREC_FP32 = 0, DD_PREC_BF16X3 = 1, DD_PREC_SPARSE = 2 };
+enum { DD_PREC_FP32 = 0, DD_PREC_BF16X3 = 1, DD_PREC_SPARSE = 2, DD_PREC_SPARSE_MERGED = 3 };
 #define DD_FAST_LOG_SPREAD 5.0e-7
 #define DD_EXACT_BELOW 0.05
 #define DD_TILE_EXACT_BELOW 0.25
@@ -207,20 +221,21 @@ dd_status dd_set_poisson_kernel(dd_ctx *ctx, int32_t mesh, const double *P);
  * out: device or host.  Errors: DD_ESTATE if none is stored. */
 dd_status dd_get_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out);
 
-/* Prepare DD_PREC_SPARSE on this mesh (Section V: entries below a threshold
- * of 1/sqrt(n) are eliminated before the KL sum, about 90 % of them; the
- * paper does not say relative to what -- here, relative to the row's
- * largest entry, applied to the target's row, see DD_PREC_SPARSE).  Stores
- * theta and the FP64 total of every row of the stored P (8 bytes per vertex)
- * and reports the sparsity: over all rows, how many entries the threshold
- * keeps, each row against its own maximum.  Recomputing or replacing P
- * (dd_poisson_kernel, dd_set_poisson_kernel) discards it.
+/* Prepare DD_PREC_SPARSE and DD_PREC_SPARSE_MERGED on this mesh (Section V:
+ * the entries of P below a threshold of 1/sqrt(n) are eliminated before the
+ * KL sum, about 90 % of them; the paper does not say relative to what --
+ * here, relative to each row's largest entry).  Stores theta, the sparsified
+ * P as CSR (each row's kept entries in column order: FP32 values, 16-bit
+ * column ids, 64-bit row offsets) and the exact total of every stored row
+ * (8 bytes per vertex, for the merged-bin extension).  Recomputing or
+ * replacing P (dd_poisson_kernel, dd_set_poisson_kernel) discards it.
  *   theta   threshold relative to the row maximum, < 1; negative: 1/sqrt(n_v)
- *   kept    NULL or out: kept entries over all rows
- *   blocks  NULL or out: 4-column blocks holding a kept entry, over all rows
+ *   kept    NULL or out: kept entries over all rows (the sparsity is
+ *           1 - kept / (n_v k))
+ *   bytes   NULL or out: device bytes of the CSR copy
  * Errors: DD_ESTATE before a Poisson kernel exists, DD_EINVAL (theta >= 1 or
- * NaN, k beyond 262,144 columns), DD_ENOMEM, DD_ECUDA. */
-dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, int64_t *blocks);
+ * NaN, k beyond 65,536 columns), DD_ENOMEM, DD_ECUDA. */
+dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, int64_t *bytes);
 
 /* Divergence fields of T target vertices, Eq. (34)-(35):
  *   TV_t(x)  = sum_b |P[x,b] - P[t,b]|
@@ -230,8 +245,9 @@ dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, in
  *   targets  host [T] interior vertex ids (a boundary target is DD_EINVAL:
  *            its KL row is infinite)
  *   f_mask   any non-empty combination of DD_F_KL, DD_F_TV, DD_F_KLT
- *   prec     DD_PREC_FP32, DD_PREC_BF16X3 or DD_PREC_SPARSE (after dd_sparsify;
- *            DD_ESTATE before)
+ *   prec     DD_PREC_FP32, DD_PREC_BF16X3, DD_PREC_SPARSE or
+ *            DD_PREC_SPARSE_MERGED (the last two after dd_sparsify; DD_ESTATE
+ *            before)
  *   out      device or host float32 [nf][T][n_v], nf = number of bits set,
  *            blocks in bit order (KL, TV, KLT)
  * In FP32 a log argument below FLT_MIN is taken as FLT_MIN: where P[t,b] = 0

@@ -152,7 +152,10 @@ void release(DevMesh &m, T *&p, int64_t bytes) {
 
 void drop_sparse(DevMesh &m) {
     release(m, m.sp_rowsum, m.n_v * (int64_t)sizeof(long long));
-    m.sp_kept = m.sp_blocks = 0;
+    release(m, m.sp_off, (m.n_v + 1) * (int64_t)sizeof(int64_t));
+    release(m, m.sp_val, m.sp_kept * (int64_t)sizeof(float));
+    release(m, m.sp_col, m.sp_kept * (int64_t)sizeof(uint16_t));
+    m.sp_kept = m.sp_bytes = 0;
     m.sp_theta = 0.f;
 }
 
@@ -218,7 +221,7 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
         kl = nullptr;
         if (!tv && !klt) return DD_OK;
     }
-    if (prec == DD_PREC_SPARSE) {
+    if (prec == DD_PREC_SPARSE || prec == DD_PREC_SPARSE_MERGED) {
         if (!m.sp_rowsum) return set_err(ctx, DD_ESTATE, "DD_PREC_SPARSE before dd_sparsify");
         if (sparse_field_smem(m.k_pad) > 200 * 1024)
             return set_err(ctx, DD_EINVAL, "DD_PREC_SPARSE: k too large for the staged target row");
@@ -226,7 +229,8 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
         if ((st = ensure_scratch(ctx, S_STAGE, sparse_stage_bytes(m.k_pad, T))) != DD_OK) return st;
         float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
         launch_stage_targets(m.P, m.n_v, m.k_pad, d_targets, T, stage, ctx->stream);
-        launch_sparse_fields(m, d_targets, stage, T, kl, tv, klt, ctx->d_err, ctx->stream);
+        launch_sparse_fields(m, d_targets, stage, T, kl, tv, klt, prec == DD_PREC_SPARSE_MERGED, ctx->d_err,
+                             ctx->stream);
         CK(cudaGetLastError(), "sparse field kernel launch");
         return DD_OK;
     }
@@ -580,7 +584,7 @@ dd_status dd_get_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out) {
     return DD_OK;
 }
 
-dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, int64_t *blocks) {
+dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, int64_t *bytes) {
     DevMesh *m = nullptr;
     dd_status st = get_mesh(ctx, mesh, &m);
     if (st != DD_OK) return st;
@@ -591,7 +595,7 @@ dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, in
         if (theta < 0.0) theta = 1.0 / std::sqrt((double)m->n_v);
         drop_sparse(*m);
         std::string err;
-        if ((st = build_sparse_rows(*m, theta, ctx->stream, kept, blocks, err)) != DD_OK) return set_err(ctx, st, err);
+        if ((st = build_sparse_rows(*m, theta, ctx->stream, kept, bytes, err)) != DD_OK) return set_err(ctx, st, err);
         return DD_OK;
     } catch (...) {
         return set_err(ctx, DD_ENOMEM, "host allocation failed");
@@ -608,7 +612,8 @@ dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t
         if (T < 1) return set_err(ctx, DD_EINVAL, "T must be >= 1");
         if (f_mask == 0 || (f_mask & ~(uint32_t)(DD_F_KL | DD_F_TV | DD_F_KLT)))
             return set_err(ctx, DD_EINVAL, "f_mask must be a non-empty combination of DD_F_KL, DD_F_TV, DD_F_KLT");
-        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3 && prec != DD_PREC_SPARSE)
+        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3 && prec != DD_PREC_SPARSE &&
+            prec != DD_PREC_SPARSE_MERGED)
             return set_err(ctx, DD_EINVAL, "unsupported precision");
         if (!out) return set_err(ctx, DD_EINVAL, "out is null");
         if ((st = check_targets(ctx, *m, targets, T, true, "targets")) != DD_OK) return st;
@@ -903,7 +908,8 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
             return set_err(ctx, DD_EINVAL, "bad f_mask");
         if ((trace_f != DD_F_KL && trace_f != DD_F_TV && trace_f != DD_F_KLT) || !(f_mask & trace_f))
             return set_err(ctx, DD_EINVAL, "trace_f must be one bit of f_mask");
-        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3 && prec != DD_PREC_SPARSE)
+        if (prec != DD_PREC_FP32 && prec != DD_PREC_BF16X3 && prec != DD_PREC_SPARSE &&
+            prec != DD_PREC_SPARSE_MERGED)
             return set_err(ctx, DD_EINVAL, "unsupported precision");
         if (!out_fields) return set_err(ctx, DD_EINVAL, "out_fields is null");
         if ((st = check_path_args(ctx, S, max_pts, out_xy, out_len, out_status)) != DD_OK) return st;

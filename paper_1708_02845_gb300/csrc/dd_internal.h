@@ -64,11 +64,14 @@ struct DevMesh {
     void *p_hi = nullptr, *p_lo = nullptr;   // BF16 split of P, [n_v][kb] (built on first BF16 request)
     float *ex = nullptr;                     // [n_v] sum_b P log P (FP64-accumulated)
     int64_t kb = 0;                          // BF16 row pitch: k rounded up to 64
-    // sparse fields (dd_sparsify): exact total of every stored row, the threshold
-    // relative to the row maximum, and the kept entries / 4-column blocks over
-    // all rows at that threshold
+    // sparse fields (dd_sparsify): the threshold relative to the row maximum,
+    // the sparsified P as CSR (each row's kept entries in column order), and
+    // the exact total of every stored row (for the merged-bin extension)
+    int64_t *sp_off = nullptr;               // [n_v + 1] row offsets into sp_val / sp_col
+    float *sp_val = nullptr;                 // [sp_kept] kept entries
+    uint16_t *sp_col = nullptr;              // [sp_kept] their columns
     long long *sp_rowsum = nullptr;          // [n_v] row totals in 2^-62 fixed point
-    int64_t sp_kept = 0, sp_blocks = 0;
+    int64_t sp_kept = 0, sp_bytes = 0;
     float sp_theta = 0.f;
     int64_t bytes = 0;
     std::vector<void *> owned;
@@ -135,19 +138,21 @@ void launch_copy_paths(const float2 *src, const int32_t *len, int64_t n, int32_t
                        cudaStream_t s);
 
 // Sparse fields (dd_sparse.cu, Section V).  build_sparse_rows fills the sp_*
-// members of m from m.P (the caller frees earlier ones).  The sparse stage is
-// the dense stage (4 x T x k_pad floats, filled by launch_stage_targets)
-// followed by T block lists of sparse_list_pitch(k_pad) uint16, T int32
-// counts (padded to 16 bytes) and T doubles M_t; launch_sparse_fields
-// thresholds the staged rows in place, lists their blocks, computes M_t and
-// launches the field kernel (one target per grid row).
+// members of m from m.P (the caller frees earlier ones; every array it
+// allocates is pushed to m.owned).  The sparse stage is the dense stage
+// (4 x T x k_pad floats, filled by launch_stage_targets) followed by T block
+// lists of sparse_list_pitch(k_pad) uint16, T int32 counts (padded to 16
+// bytes) and T doubles M_t; launch_sparse_fields thresholds the staged rows in
+// place, lists their blocks, computes M_t and launches the field kernels (one
+// target per grid row): KL~ and TV~ from the CSR rows, KLT~ from the dense
+// rows at the target's blocks; merged: the merged-bin extension instead.
 int64_t sparse_list_pitch(int64_t k_pad);
 size_t sparse_stage_bytes(int64_t k_pad, int32_t T);
 size_t sparse_field_smem(int64_t k_pad);
-dd_status build_sparse_rows(DevMesh &m, double theta, cudaStream_t s, int64_t *kept_out, int64_t *blocks_out,
+dd_status build_sparse_rows(DevMesh &m, double theta, cudaStream_t s, int64_t *kept_out, int64_t *bytes_out,
                             std::string &err);
 void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *stage, int32_t T, float *out_kl,
-                          float *out_tv, float *out_klt, int *err_flag, cudaStream_t s);
+                          float *out_tv, float *out_klt, bool merged, int *err_flag, cudaStream_t s);
 // spread (max - min) of the hardware mantissa log's error over [1, 2), in base-2 units
 dd_status fast_log_spread(double *spread, std::string &err);
 

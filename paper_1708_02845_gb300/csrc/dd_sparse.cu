@@ -1,35 +1,46 @@
 // Sparse KL and TV fields, Section V: the Poisson kernel's small entries
-// eliminated before the sums (threshold 1/sqrt(n), about 90 % of the
-// entries).  The target row decides: S_t = {b : P[t,b] >= theta max_b' P[t,b']}
-// (FP32 product), and every other column is merged into one bin, so the
-// fields are the divergences between the coarse-grained harmonic measures
-// (P[y,b] for b in S_t, and M_y = sum_{b not in S_t} P[y,b]):
+// eliminated before the sums (threshold 1/sqrt(n) of each row's largest
+// entry, about 90 % of the entries).  In Eq. (35) the weight row decides
+// which terms remain (an eliminated weight drops its term) and the other row
+// enters through its logarithm, taken from the full kernel:
 //
-//   KL~_t(x)  = sum_{b in S_t} P[x,b] log(P[x,b] / P[t,b]) + M_x log(M_x / M_t)
-//   KLT~_t(x) = sum_{b in S_t} P[t,b] log(P[t,b] / P[x,b]) + M_t log(M_t / M_x)
-//   TV~_t(x)  = sum_{b in S_t} |P[x,b] - P[t,b]| + |M_x - M_t|
+//   KLT~_t(x) = sum_{b in S_t} P[t,b] log(P[t,b] / P[x,b])     target-weighted
+//   KL~_t(x)  = sum_{b in S_x} P[x,b] log(P[x,b] / P[t,b])     field-weighted
+//   TV~_t(x)  = sum_b |P~[x,b] - P~[t,b]|                      sparsified rows
 //
-// Every row meets the same columns, so the field is as smooth as the dense
-// one, and merging can only lose information: 0 <= KL~ <= KL, 0 <= KLT~ <=
-// KLT, 0 <= TV~ <= TV.
+// with S_y = {b : P[y,b] >= theta max_b' P[y,b'], P[y,b] > 0} (FP32 product)
+// and P~ = P with the other entries set to 0.
 //
-// Work: per target, the 4-column blocks of P holding a column of S_t are
-// listed once (sparse_stage_kernel, in column order; S_t lies on a few arcs
-// of the boundary, so the list is a few runs of consecutive blocks).  The
-// field kernel reads, for every row, only those blocks of the dense FP32 P
-// (16-byte loads, consecutive within a run), one warp per row, the next
-// item's loads in flight while the current one is summed.  Per block, one
-// routine (block_terms) does the arithmetic in packed FP32x2 on the block's
-// two pairs of entries; a dropped column enters with weight 0 (its target
-// entry is 0 already), so KL, KLT, TV and the mass need one select per
-// entry.  M_x is the row's total (per mesh, exact 2^-62 fixed point) minus
-// its S_t part, summed with compensation (Kahan) per lane and in FP64 across
-// the warp once per row; M_t comes from the same routine in the same order on
-// row t, so M_x = M_t bit for bit at x = t and the fields are exactly 0 there.
-// (Per-entry FP64 would be simpler, but its rate on this GPU is a small
-// fraction of the FP32 pipes'.)  KL and KLT over S_t take the same two passes
-// as the dense streaming kernel (exponents exact, hardware log2 of the
-// mantissas, rows below DD_EXACT_BELOW recomputed with the table logarithm).
+// Layouts.  dd_sparsify stores the sparsified P as CSR (each row's kept
+// entries in column order: FP32 values, 16-bit columns, 64-bit row offsets),
+// about a sixth of the dense P at 84 % sparsity.  KL~ and TV~ read only that
+// (csr_field_kernel: one warp per row, the target row's thresholded values
+// and logarithms staged in shared memory by bulk async copies and gathered
+// by column).  KLT~ needs the field row at the target's kept columns, which
+// the CSR row may not hold (an entry below the field row's own threshold is
+// still non-zero), so it reads the dense P at the 4-column blocks holding
+// S_t (sparse_field_kernel, the list built once per target by
+// sparse_stage_kernel; S_t lies on a few arcs of the boundary, so the list
+// is a few runs of consecutive blocks).
+//
+// Extension (not in the paper; DD_PREC_SPARSE_MERGED): S_t decides for both
+// rows and every other column merges into one bin of mass
+// M_y = sum_{b not in S_t} P[y,b]:
+//
+//   KL^_t(x)  = sum_{b in S_t} P[x,b] log(P[x,b] / P[t,b]) + M_x log(M_x / M_t)
+//   KLT^_t(x) = sum_{b in S_t} P[t,b] log(P[t,b] / P[x,b]) + M_t log(M_t / M_x)
+//   TV^_t(x)  = sum_{b in S_t} |P[x,b] - P[t,b]| + |M_x - M_t|
+//
+// M_x is the row's total (per mesh, exact 2^-62 fixed point) minus its S_t
+// part, summed with compensation (Kahan) per lane and in FP64 across the warp
+// once per row; M_t comes from the same routine in the same order on row t,
+// so M_x = M_t bit for bit at x = t and the fields are exactly 0 there.
+//
+// Every KL sum takes the same two passes as the dense streaming kernel
+// (exponents exact, hardware log2 of the mantissas, rows below
+// DD_EXACT_BELOW recomputed with the table logarithm), and every field is
+// exactly 0 at x = t.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <string>
@@ -65,7 +76,8 @@ __device__ __forceinline__ double total62(long long q) { return __ll2double_rn(q
 // 4-column blocks the row's own threshold keeps (the sparsity figure).  One
 // warp per row.
 __global__ void sparse_rows_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad, float theta,
-                                   long long *__restrict__ rowsum, unsigned long long *__restrict__ counts) {
+                                   long long *__restrict__ rowsum, unsigned long long *__restrict__ counts,
+                                   int32_t *__restrict__ row_kept, float *__restrict__ row_thr) {
     const int lane = threadIdx.x & 31;
     const int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (x >= n_v) return;
@@ -99,8 +111,36 @@ __global__ void sparse_rows_kernel(const float *__restrict__ P, int64_t n_v, int
     }
     if (lane == 0) {
         rowsum[x] = s;
+        row_kept[x] = (int32_t)ne;
+        row_thr[x] = t;
         atomicAdd(counts, ne);
         atomicAdd(counts + 1, nbk);
+    }
+}
+
+// CSR of the sparsified P: one warp per row writes the row's kept entries in
+// column order from off[x] (a ballot compaction per 32 columns), the same
+// decision as sparse_rows_kernel (P[x,b] >= row_thr[x] and P[x,b] > 0).
+__global__ void csr_fill_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
+                                const float *__restrict__ row_thr, const int64_t *__restrict__ off,
+                                float *__restrict__ val, uint16_t *__restrict__ col) {
+    const int lane = threadIdx.x & 31;
+    const int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (x >= n_v) return;
+    const float *row = P + x * k_pad;
+    const float t = row_thr[x];
+    int64_t pos = off[x];
+    for (int64_t b0 = 0; b0 < k_pad; b0 += 32) {
+        const int64_t b = b0 + lane;
+        const float v = b < k_pad ? __ldg(row + b) : 0.0f;
+        const bool keep = v >= t && v > 0.0f;
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int64_t i = pos + __popc(ball & ((1u << lane) - 1u));
+            val[i] = v;
+            col[i] = (uint16_t)b;
+        }
+        pos += __popc(ball);
     }
 }
 
@@ -111,7 +151,7 @@ __global__ void sparse_rows_kernel(const float *__restrict__ P, int64_t n_v, int
 // the sign flipped), tv += |w - p_t|, and the mass w into the Kahan pair
 // (s, c), where w = P[x,b] on kept columns and 0 on dropped ones and
 // d = log2(P[x,b]/P[t,b]) from exact exponents and hardware mantissa logs.
-template <bool KL, bool TV, bool KLT>
+template <bool KL, bool TV, bool KLT, bool MASS = true>
 __device__ __forceinline__ void block_terms(const float4 &v, const float4 &p4, const float4 &f4, const float4 &e4,
                                             f2_t &kl, f2_t &tv, f2_t &kt, f2_t &s, f2_t &c) {
     const f2_t mone = pk(-1.0f, -1.0f);
@@ -139,10 +179,12 @@ __device__ __forceinline__ void block_terms(const float4 &v, const float4 &p4, c
             if (KLT) kt = fma2(pt2, d, kt);
         }
         if (TV) tv = add2(tv, fma2(pt2, mone, w2) & 0x7fffffff7fffffffULL);
-        const f2_t y = fma2(c, mone, w2);                 // Kahan: y = w - c
-        const f2_t t = add2(s, y);
-        c = fma2(y, mone, fma2(s, mone, t));              // c = (t - s) - y
-        s = t;
+        if (MASS) {
+            const f2_t y = fma2(c, mone, w2);             // Kahan: y = w - c
+            const f2_t t = add2(s, y);
+            c = fma2(y, mone, fma2(s, mone, t));          // c = (t - s) - y
+            s = t;
+        }
     }
 }
 
@@ -282,7 +324,7 @@ __device__ __forceinline__ float kept_kl_exact(const float *__restrict__ P, int6
 // copy each.  Items are (row, group of 32 U listed blocks).  The row-side
 // logarithms are taken at max(P[x,b], FLT_MIN): a zero entry contributes 0 to
 // KL (weight 0) and a large finite term to KLT (the exact value is +inf).
-template <int U, bool KL, bool TV, bool KLT>
+template <int U, bool KL, bool TV, bool KLT, bool MERGED>
 __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
     const float *__restrict__ P, int64_t n_v, int64_t k_pad, const float *__restrict__ sP,
     const float *__restrict__ sL, const float *__restrict__ sE, const float *__restrict__ sF,
@@ -343,7 +385,7 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
     auto fetch = [&](auto S_, int64_t x, int g) {
         constexpr int s = decltype(S_)::value;
         const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
-        rsb[s] = rowsum[x];
+        rsb[s] = MERGED ? rowsum[x] : 0LL;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = g * 32 * U + u * 32 + lane;
@@ -357,7 +399,7 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
         for (int u = 0; u < U; ++u) {
             const int j = jb[s][u];
             if (j < 0) break;
-            block_terms<KL, TV, KLT>(buf[s][u], tP4[j], tF4[j], tE4[j], kl, tv, kt, ms, mc);
+            block_terms<KL, TV, KLT, MERGED>(buf[s][u], tP4[j], tF4[j], tE4[j], kl, tv, kt, ms, mc);
         }
     };
     auto finish = [&](auto S_, int64_t x) {
@@ -373,23 +415,23 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
             if (TV) stv += __shfl_xor_sync(0xffffffffu, stv, o);
             if (KLT) skt += __shfl_xor_sync(0xffffffffu, skt, o);
         }
-        const double Mx_d = total62(rsb[s]) - lane_mass_sum(ms, mc);
+        const double Mx_d = MERGED ? total62(rsb[s]) - lane_mass_sum(ms, mc) : 0.0;
         const float Mx = (float)Mx_d;
         if (KL) {
-            const float merged = Mx > 0.f ? Mx * logf(Mx / fmaxf(Mt, FLT_MIN)) : 0.f;
+            const float merged = (MERGED && Mx > 0.f) ? Mx * logf(Mx / fmaxf(Mt, FLT_MIN)) : 0.f;
             skl = __fmaf_rn(skl, kLn2s, merged);
             if (skl < kExactBelowS)                      // warp-uniform
                 skl = kept_kl_exact<false>(P, x, k_pad, lst, nl, tP4, tL, tE, tab, lane) + merged;
         }
         if (KLT) {
-            const float merged = Mt > 0.f ? Mt * logf(Mt / fmaxf(Mx, FLT_MIN)) : 0.f;
+            const float merged = (MERGED && Mt > 0.f) ? Mt * logf(Mt / fmaxf(Mx, FLT_MIN)) : 0.f;
             skt = __fmaf_rn(-skt, kLn2s, merged);
             if (skt < kExactBelowS)
                 skt = kept_kl_exact<true>(P, x, k_pad, lst, nl, tP4, tL, tE, tab, lane) + merged;
         }
         if (lane == 0) {
             if (KL) okl[x] = skl;
-            if (TV) otv[x] = stv + (float)fabs(Mx_d - Mt_d);
+            if (TV) otv[x] = MERGED ? stv + (float)fabs(Mx_d - Mt_d) : stv;
             if (KLT) okt[x] = skt;
         }
         kl = tv = kt = ms = mc = 0ULL;
@@ -427,6 +469,196 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
     }
 }
 
+// exact (table) KL~ of one CSR row for one warp: sum over the row's entries
+// of P[x,b] log(P[x,b] / P[t,b]), the target's logs from the staged arrays
+__device__ __forceinline__ float csr_kl_exact(const float *__restrict__ val, const uint16_t *__restrict__ col,
+                                              int64_t o0, int64_t o1, const float *tL, const float *tE,
+                                              const float *tab, int lane) {
+    float k0 = 0.0f, k1 = 0.0f;
+    int q = 0;
+    for (int64_t i = o0 + lane; i < o1; i += 32, ++q) {
+        const float v = __ldcg(val + i);
+        const int c = col[i];
+        float lm, Eb;
+        split_log<false>(v, tab, lm, Eb);
+        const float lr = __fmaf_rn(__fadd_rn(Eb, -tE[c]), kLn2s, __fadd_rn(lm, -tL[c]));
+        if (q & 1)
+            k1 = __fmaf_rn(v, lr, k1);
+        else
+            k0 = __fmaf_rn(v, lr, k0);
+    }
+    float s = k0 + k1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// the staged target mass over one CSR row's columns, sum_{b in S_x} P~[t,b]:
+// lane l adds the row's entries l, l + 32, ... in order, then the fixed
+// shuffle tree -- the same additions the field kernel makes, so that on row
+// x = t it reproduces the target's total bit for bit
+__device__ __forceinline__ float csr_target_mass(const uint16_t *__restrict__ col, int64_t o0, int64_t o1,
+                                                 const float *tP, int lane) {
+    float a = 0.0f;
+    for (int64_t i = o0 + lane; i < o1; i += 32) a = __fadd_rn(a, tP[col[i]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = __fadd_rn(a, __shfl_xor_sync(0xffffffffu, a, o));
+    return a;
+}
+
+// KL~ and TV~ from the CSR rows, one target per grid row (blockIdx.y).
+// Dynamic smem: the target's thresholded row P~[t,:], its table mantissa log,
+// biased exponent and hardware mantissa log2 (the logs of the dense row),
+// one bulk copy each.  One warp per row; items are (row, chunk of 32 U
+// entries), each lane loading U values and columns of the next item while the
+// current one is summed.  Per entry v = P[x,b] at column c:
+//   KL: v ((lg2 m_v - lg2 m_t[c]) + (E_v - E_t[c])), times ln2 at the end
+//   TV: |v - P~[t,c]|, and the target mass the row covers, P~[t,c]
+// so that TV~ = sum |v - P~[t,c]| + (M~_t - covered), M~_t the target's own
+// total by the same additions (csr_target_mass on row t).
+template <int U, bool KL, bool TV>
+__global__ void __launch_bounds__(256, 2) csr_field_kernel(
+    const float *__restrict__ val, const uint16_t *__restrict__ col, const int64_t *__restrict__ off, int64_t n_v,
+    int64_t k_pad, const float *__restrict__ sP, const float *__restrict__ sL, const float *__restrict__ sE,
+    const float *__restrict__ sF, const int32_t *__restrict__ targets, float *__restrict__ out_kl,
+    float *__restrict__ out_tv, int *__restrict__ err_flag) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float tab[2 * kLogTab];
+    __shared__ float mt_sh;
+    float *tP = smem;
+    float *tL = tP + k_pad;
+    float *tE = tL + k_pad;
+    float *tF = tE + k_pad;
+    const int a = blockIdx.y;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t row_bytes = (uint32_t)(k_pad * sizeof(float));
+        mbar_expect_tx(&bar, 4u * row_bytes);
+        bulk_g2s(tP, sP + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(tL, sL + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(tE, sE + (int64_t)a * k_pad, row_bytes, &bar);
+        bulk_g2s(tF, sF + (int64_t)a * k_pad, row_bytes, &bar);
+    }
+    build_log_table(tab);
+    __syncthreads();
+    // every thread waits (bounded); a CTA whose wait gave up waits once more
+    // (also bounded) so that it does not exit while its copies may still land
+    const bool ok = mbar_wait(&bar, 0, err_flag);
+    if (!ok) mbar_wait(&bar, 0, err_flag);
+    const int lane = threadIdx.x & 31;
+    if (TV && threadIdx.x < 32) {
+        const int64_t t = targets[a];
+        const float m = ok ? csr_target_mass(col, off[t], off[t + 1], tP, lane) : 0.0f;
+        if (lane == 0) mt_sh = m;
+    }
+    __syncthreads();
+    if (!ok) return;
+    const float Mt = TV ? mt_sh : 0.0f;
+
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float *okl = KL ? out_kl + (int64_t)a * n_v : nullptr;
+    float *otv = TV ? out_tv + (int64_t)a * n_v : nullptr;
+
+    float vb[2][U];
+    int cb[2][U];
+    float kl = 0.0f, tv = 0.0f, cov = 0.0f;
+
+    // an item: row x, its entries [o0, o1), chunk start i0
+    struct Item {
+        int64_t x, o0, o1, i0;
+    };
+    auto first = [&](int64_t x) {
+        Item it{x, 0, 0, 0};
+        if (x < n_v) {
+            it.o0 = off[x];
+            it.o1 = off[x + 1];
+            it.i0 = it.o0;
+        }
+        return it;
+    };
+    auto next = [&](const Item &it) {
+        if (it.i0 + 32 * U < it.o1) return Item{it.x, it.o0, it.o1, it.i0 + 32 * U};
+        return first(it.x + nwarps);
+    };
+    auto fetch = [&](auto S_, const Item &it) {
+        constexpr int s = decltype(S_)::value;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = it.i0 + u * 32 + lane;
+            const bool in = i < it.o1;
+            vb[s][u] = in ? __ldcs(val + i) : 0.0f;
+            cb[s][u] = in ? (int)__ldcs(col + i) : -1;
+        }
+    };
+    auto compute = [&](auto S_) {
+        constexpr int s = decltype(S_)::value;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = cb[s][u];
+            if (c < 0) break;
+            const float v = vb[s][u];
+            if (KL) {
+                const int bits = __float_as_int(v);
+                const float lf = lg2_mant(bits);
+                const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
+                const float d = __fadd_rn(__fadd_rn(lf, -tF[c]), __fadd_rn(eb, -tE[c]));
+                kl = __fmaf_rn(v, d, kl);
+            }
+            if (TV) {
+                const float pt = tP[c];
+                tv = __fadd_rn(tv, fabsf(__fadd_rn(v, -pt)));
+                cov = __fadd_rn(cov, pt);
+            }
+        }
+    };
+    auto finish = [&](const Item &it) {
+        float skl = kl, stv = tv, sc = cov;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            if (KL) skl += __shfl_xor_sync(0xffffffffu, skl, o);
+            if (TV) {
+                stv += __shfl_xor_sync(0xffffffffu, stv, o);
+                sc = __fadd_rn(sc, __shfl_xor_sync(0xffffffffu, sc, o));
+            }
+        }
+        if (KL) {
+            skl *= kLn2s;
+            if (skl < kExactBelowS)                  // warp-uniform
+                skl = csr_kl_exact(val, col, it.o0, it.o1, tL, tE, tab, lane);
+        }
+        if (lane == 0) {
+            if (KL) okl[it.x] = skl;
+            if (TV) otv[it.x] = __fadd_rn(stv, __fadd_rn(Mt, -sc));
+        }
+        kl = tv = cov = 0.0f;
+    };
+    using B0 = std::integral_constant<int, 0>;
+    using B1 = std::integral_constant<int, 1>;
+    Item cur = first(warp);
+    if (cur.x >= n_v) return;
+    fetch(B0{}, cur);
+    for (;;) {
+        Item nx = next(cur);
+        if (nx.x < n_v) fetch(B1{}, nx);
+        compute(B0{});
+        if (nx.x != cur.x) finish(cur);
+        if (nx.x >= n_v) break;
+        cur = nx;
+        nx = next(cur);
+        if (nx.x < n_v) fetch(B0{}, nx);
+        compute(B1{});
+        if (nx.x != cur.x) finish(cur);
+        if (nx.x >= n_v) break;
+        cur = nx;
+    }
+}
+
 int sms_now() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -449,45 +681,78 @@ size_t sparse_stage_bytes(int64_t k_pad, int32_t T) {
            sparse_count_bytes(T) + (size_t)T * sizeof(double);
 }
 
-dd_status build_sparse_rows(DevMesh &m, double theta, cudaStream_t s, int64_t *kept_out, int64_t *blocks_out,
+dd_status build_sparse_rows(DevMesh &m, double theta, cudaStream_t s, int64_t *kept_out, int64_t *bytes_out,
                             std::string &err) {
-    if ((m.k_pad >> 2) > 65536) {
-        err = "sparse fields: more than 65,536 blocks of four boundary columns";
+    if (m.k > 65536) {
+        err = "sparse fields: more than 65,536 boundary columns (16-bit column ids)";
         return DD_EINVAL;
     }
     long long *rowsum = nullptr;
     unsigned long long *counts = nullptr;
-    cudaError_t e = cudaMalloc((void **)&rowsum, (size_t)m.n_v * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&counts, 2 * sizeof(unsigned long long));
-    unsigned long long hc[2] = {0, 0};
-    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
-    if (e == cudaSuccess) {
-        sparse_rows_kernel<<<(unsigned)((m.n_v + 7) / 8), 256, 0, s>>>(m.P, m.n_v, m.k_pad, (float)theta, rowsum,
-                                                                        counts);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (counts) cudaFree(counts);
-    if (e != cudaSuccess) {
-        if (rowsum) cudaFree(rowsum);
+    int32_t *row_kept = nullptr;
+    float *row_thr = nullptr;
+    int64_t *off = nullptr;
+    float *val = nullptr;
+    uint16_t *col = nullptr;
+    auto fail = [&](cudaError_t e) {
+        for (void *p : {(void *)rowsum, (void *)counts, (void *)row_kept, (void *)row_thr, (void *)off, (void *)val,
+                        (void *)col})
+            if (p) cudaFree(p);
         cudaGetLastError();
         err = std::string("sparse fields: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA;
+    };
+    const int64_t n = m.n_v;
+    cudaError_t e = cudaMalloc((void **)&rowsum, (size_t)n * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&counts, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&row_kept, (size_t)n * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&row_thr, (size_t)n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&off, (size_t)(n + 1) * sizeof(int64_t));
+    unsigned long long hc[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        sparse_rows_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(m.P, n, m.k_pad, (float)theta, rowsum, counts,
+                                                                   row_kept, row_thr);
+        e = cudaGetLastError();
     }
+    // row offsets: an exclusive scan of the per-row counts on the host (a one-off step)
+    std::vector<int32_t> hk((size_t)n);
+    std::vector<int64_t> ho((size_t)n + 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hk.data(), row_kept, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e);
+    ho[0] = 0;
+    for (int64_t x = 0; x < n; ++x) ho[x + 1] = ho[x] + hk[x];
+    const int64_t nnz = ho[n];
+    e = cudaMemcpyAsync(off, ho.data(), (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&val, (size_t)std::max<int64_t>(nnz, 1) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&col, (size_t)std::max<int64_t>(nnz, 1) * sizeof(uint16_t));
+    if (e == cudaSuccess) {
+        csr_fill_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(m.P, n, m.k_pad, row_thr, off, val, col);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e);
+    cudaFree(counts);
+    cudaFree(row_kept);
+    cudaFree(row_thr);
     m.sp_rowsum = rowsum;
+    m.sp_off = off;
+    m.sp_val = val;
+    m.sp_col = col;
     m.sp_theta = (float)theta;
     m.sp_kept = (int64_t)hc[0];
-    m.sp_blocks = (int64_t)hc[1];
-    m.owned.push_back(rowsum);
-    m.bytes += m.n_v * (int64_t)sizeof(long long);
+    m.sp_bytes = (n + 1) * (int64_t)sizeof(int64_t) + nnz * (int64_t)(sizeof(float) + sizeof(uint16_t));
+    for (void *p : {(void *)rowsum, (void *)off, (void *)val, (void *)col}) m.owned.push_back(p);
+    m.bytes += n * (int64_t)sizeof(long long) + m.sp_bytes;
     if (kept_out) *kept_out = m.sp_kept;
-    if (blocks_out) *blocks_out = m.sp_blocks;
+    if (bytes_out) *bytes_out = m.sp_bytes;
     return DD_OK;
 }
 
 void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *stage, int32_t T, float *out_kl,
-                          float *out_tv, float *out_klt, int *err_flag, cudaStream_t s) {
+                          float *out_tv, float *out_klt, bool merged, int *err_flag, cudaStream_t s) {
     float *sP = reinterpret_cast<float *>(stage);
     const float *sL = sP + (int64_t)T * m.k_pad;
     const float *sE = sL + (int64_t)T * m.k_pad;
@@ -501,33 +766,53 @@ void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *st
         sparse_stage_kernel<<<(unsigned)T, 256, 0, s>>>(m.P, sP, sE, sF, m.k_pad, m.sp_theta, sList, lp, sCount,
                                                          m.sp_rowsum, d_targets, sMt);
     }
-    const size_t smem = sparse_field_smem(m.k_pad);
-    auto go = [&](auto kern) {
+    const int64_t row_blocks = (m.n_v + 7) / 8;
+    auto grid_x = [&](auto kern, size_t smem) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
         if (per_sm < 1) per_sm = 1;
         int64_t gx = (int64_t)sms_now() * per_sm / T;
-        const int64_t row_blocks = (m.n_v + 7) / 8;
         if (gx < 1) gx = 1;
         if (gx > row_blocks) gx = row_blocks;
-        {
-            KMark km_("sparse_field_kernel", s);
-            kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(m.P, m.n_v, m.k_pad, sP, sL, sE, sF, sList, lp,
-                                                                   sCount, sMt, m.sp_rowsum, out_kl, out_tv, out_klt,
-                                                                   err_flag);
-        }
+        return (unsigned)gx;
     };
-    // two blocks per lane and item, three CTAs per SM (measured: U = 4 or 8 with
-    // two CTAs per SM were slower; the pass is issue- and latency-bound)
-    const int mask = (out_kl ? 1 : 0) | (out_tv ? 2 : 0) | (out_klt ? 4 : 0);
-    switch (mask) {
-        case 1: go(sparse_field_kernel<2, true, false, false>); break;
-        case 2: go(sparse_field_kernel<2, false, true, false>); break;
-        case 3: go(sparse_field_kernel<2, true, true, false>); break;
-        case 4: go(sparse_field_kernel<2, false, false, true>); break;
-        case 5: go(sparse_field_kernel<2, true, false, true>); break;
-        case 6: go(sparse_field_kernel<2, false, true, true>); break;
-        default: go(sparse_field_kernel<2, true, true, true>); break;
+    // the dense rows at the target's blocks: KLT~ (or the merged-bin fields)
+    auto go = [&](auto kern) {
+        const size_t smem = sparse_field_smem(m.k_pad);
+        const unsigned gx = grid_x(kern, smem);
+        KMark km_("sparse_field_kernel", s);
+        kern<<<dim3(gx, (unsigned)T), 256, smem, s>>>(m.P, m.n_v, m.k_pad, sP, sL, sE, sF, sList, lp, sCount, sMt,
+                                                       m.sp_rowsum, out_kl, out_tv, out_klt, err_flag);
+    };
+    // the CSR rows: KL~ and TV~
+    auto go_csr = [&](auto kern) {
+        const size_t smem = 4 * (size_t)m.k_pad * sizeof(float);
+        const unsigned gx = grid_x(kern, smem);
+        KMark km_("csr_field_kernel", s);
+        kern<<<dim3(gx, (unsigned)T), 256, smem, s>>>(m.sp_val, m.sp_col, m.sp_off, m.n_v, m.k_pad, sP, sL, sE, sF,
+                                                       d_targets, out_kl, out_tv, err_flag);
+    };
+    if (merged) {
+        // two blocks per lane and item, three CTAs per SM (measured: U = 4 or 8 with
+        // two CTAs per SM were slower; the pass is issue- and latency-bound)
+        const int mask = (out_kl ? 1 : 0) | (out_tv ? 2 : 0) | (out_klt ? 4 : 0);
+        switch (mask) {
+            case 1: go(sparse_field_kernel<2, true, false, false, true>); break;
+            case 2: go(sparse_field_kernel<2, false, true, false, true>); break;
+            case 3: go(sparse_field_kernel<2, true, true, false, true>); break;
+            case 4: go(sparse_field_kernel<2, false, false, true, true>); break;
+            case 5: go(sparse_field_kernel<2, true, false, true, true>); break;
+            case 6: go(sparse_field_kernel<2, false, true, true, true>); break;
+            default: go(sparse_field_kernel<2, true, true, true, true>); break;
+        }
+        return;
     }
+    if (out_kl && out_tv)
+        go_csr(csr_field_kernel<8, true, true>);
+    else if (out_kl)
+        go_csr(csr_field_kernel<8, true, false>);
+    else if (out_tv)
+        go_csr(csr_field_kernel<8, false, true>);
+    if (out_klt) go(sparse_field_kernel<2, false, false, true, false>);
 }

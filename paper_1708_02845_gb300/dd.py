@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libdd.so")
 
 DD_OK, DD_EINVAL, DD_ENOMEM, DD_ECUDA, DD_ESTATE, DD_ENOTCONV, DD_ETIMEOUT, DD_EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7
 DD_F_KL, DD_F_TV, DD_F_KLT = 1, 2, 4
-DD_PREC_FP32, DD_PREC_BF16X3, DD_PREC_SPARSE = 0, 1, 2
+DD_PREC_FP32, DD_PREC_BF16X3, DD_PREC_SPARSE, DD_PREC_SPARSE_MERGED = 0, 1, 2, 3
 DD_FAST_LOG_SPREAD, DD_EXACT_BELOW, DD_TILE_EXACT_BELOW = 5.0e-7, 0.05, 0.25
 DD_DIV_CHI2, DD_DIV_HELLINGER, DD_DIV_POWER, DD_DIV_ALPHA, DD_DIV_KL_REVERSE = 1, 2, 3, 4, 5
 DD_TRACE_OK, DD_TRACE_STUCK, DD_TRACE_STEP_LIMIT, DD_TRACE_TRUNCATED = 0, 1, 2, 3
@@ -195,10 +195,10 @@ def dd_get_poisson_kernel(ctx, mesh: int, out):
 
 
 def dd_sparsify(ctx, mesh: int, theta: float = -1.0):
-    """Sparse rows for DD_PREC_SPARSE; returns (kept entries, stored blocks)."""
-    kept, blocks = _i64(0), _i64(0)
-    _check(ctx, lib.dd_sparsify(ctx, mesh, float(theta), ctypes.byref(kept), ctypes.byref(blocks)))
-    return kept.value, blocks.value
+    """Sparse copy of P for DD_PREC_SPARSE(_MERGED); returns (kept entries, bytes of the CSR copy)."""
+    kept, nbytes = _i64(0), _i64(0)
+    _check(ctx, lib.dd_sparsify(ctx, mesh, float(theta), ctypes.byref(kept), ctypes.byref(nbytes)))
+    return kept.value, nbytes.value
 
 
 def dd_distance(ctx, mesh: int, targets, f_mask: int, prec: int, out):

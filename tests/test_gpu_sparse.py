@@ -1,10 +1,17 @@
-"""GPU parity of the sparse KL/TV fields (Section V, DD_PREC_SPARSE after
-dd_sparsify: the target row's small entries merged into one bin) against the
-FP64 oracle, through the C ABI.
+"""GPU parity of the sparse fields (Section V: P sparsified by eliminating
+the entries below a threshold relative to their row's maximum; DD_PREC_SPARSE
+after dd_sparsify) and of the merged-bin extension (DD_PREC_SPARSE_MERGED)
+against the FP64 oracle, through the C ABI.
 
-Which entries a row keeps is decided in FP32 on both sides, so the kept
-counts must agree exactly; the fields to the FP32 tolerance
-|g - r| / max(|r|, 1e-2) <= 1e-5, and exactly 0 at the target.
+The oracle decides which entries a row keeps in FP64 on the FP64 kernel, the
+device in FP32 on its FP32 copy; the two can differ only on entries whose
+FP64 value lies within FP32 rounding of theta x (row max): relative
+BORDER = 8 x 2^-24 (the rounding of the stored entry, of theta, of the
+row maximum and of their product, each at most 2^-24, with margin).  Rows
+holding such an entry are left out of the comparison (a target holding one
+is not used), and the kept counts agree up to the number of such entries.
+Everything else: the fields to the FP32 tolerance |g - r| / max(|r|, 1e-2)
+<= 1e-5, and exactly 0 at the target.
 """
 import numpy as np
 import pytest
@@ -18,6 +25,8 @@ from tests._gpu import TOL_FP32, ctx_and_lib, field_error, load
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+BORDER = 8.0 * 2.0 ** -24
 
 CASES = {
     "disk": lambda: workloads.disk(),
@@ -50,12 +59,39 @@ def _targets(po, count):
     return [int(ids[i]) for i in np.linspace(0, len(ids) - 1, count + 2).astype(int)[1:-1]]
 
 
-def _blocks(mask):
-    k = mask.shape[1]
-    kp = (k + 3) // 4 * 4
-    m = np.zeros((mask.shape[0], kp), bool)
-    m[:, :k] = mask
-    return int(m.reshape(mask.shape[0], kp // 4, 4).any(axis=2).sum())
+def _border(P, theta):
+    """[rows][k]: entries within FP32 rounding of their row's threshold (the
+    FP64 and FP32 decisions may differ there)."""
+    P = np.asarray(P, dtype=np.float64)
+    thr = theta * P.max(axis=1, keepdims=True)
+    return np.abs(P - thr) <= BORDER * thr
+
+
+def _check_sparse(dd, got, P, th, targets, merged=False):
+    """Compare [3][T][n] fields (KL, TV, KLT) with the oracle on the rows no
+    borderline entry can change; returns the share of rows left out."""
+    bad_rows = _border(P, th).any(axis=1)
+    used = 0
+    for a, t in enumerate(targets):
+        assert not bad_rows[t], "a target holds a borderline entry: choose another"
+        if merged:
+            refs = (sparse.merged_kl_field(P, t, th), sparse.merged_tv_field(P, t, th),
+                    sparse.merged_klt_field(P, t, th))
+            rows = np.ones(P.shape[0], bool)                  # only the target's decision matters
+        else:
+            refs = (sparse.sparse_kl_field(P, t, th), sparse.sparse_tv_field(P, t, th),
+                    sparse.sparse_klt_field(P, t, th))
+            rows = ~bad_rows
+        used += 1
+        for f, (r, lo) in enumerate(zip(refs, (80.0, None, 50.0))):
+            g = got[f, a]
+            assert field_error(g[rows], r[rows]) <= TOL_FP32, (f, field_error(g[rows], r[rows]))
+            assert g[t] == 0.0
+            inf = ~np.isfinite(r) & rows
+            if inf.any():
+                assert np.all(g[inf] >= lo)
+    assert used == len(targets)
+    return float(np.mean(bad_rows))
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -66,26 +102,26 @@ def test_sparse_fields_on_oracle_kernel(env, name, theta):
     th = sparse.default_theta(wl.mesh.n_v) if theta is None else theta
     mid = load(dd, ctx, wl.mesh)
     dd.dd_set_poisson_kernel(ctx, mid, P)
-    kept, blocks = dd.dd_sparsify(ctx, mid, -1.0 if theta is None else theta)
+    kept, nbytes = dd.dd_sparsify(ctx, mid, -1.0 if theta is None else theta)
     mask = sparse.keep_mask(P, th)
-    assert kept == int(mask.sum())
-    assert blocks == _blocks(mask)
+    assert abs(kept - int(mask.sum())) <= int(_border(P, th).sum())
+    assert nbytes == (wl.mesh.n_v + 1) * 8 + kept * 6
     targets = _targets(po, 5)
-    out = torch.empty((3, len(targets), wl.mesh.n_v), dtype=torch.float32, device="cuda")
+    T, n = len(targets), wl.mesh.n_v
+    out = torch.empty((3, T, n), dtype=torch.float32, device="cuda")
     dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV | dd.DD_F_KLT, dd.DD_PREC_SPARSE, out)
-    one = torch.empty((1, len(targets), wl.mesh.n_v), dtype=torch.float32, device="cuda")
+    one = torch.empty((1, T, n), dtype=torch.float32, device="cuda")
+    two = torch.empty((1, T, n), dtype=torch.float32, device="cuda")
     dd.dd_distance(ctx, mid, targets, dd.DD_F_KLT, dd.DD_PREC_SPARSE, one)
+    dd.dd_distance(ctx, mid, targets, dd.DD_F_TV, dd.DD_PREC_SPARSE, two)
+    mrg = torch.empty((3, T, n), dtype=torch.float32, device="cuda")
+    dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV | dd.DD_F_KLT, dd.DD_PREC_SPARSE_MERGED, mrg)
     dd.dd_sync(ctx)
     got = out.cpu().numpy()
-    assert np.array_equal(one.cpu().numpy()[0], got[2])      # the same kernel arithmetic alone or together
-    for a, t in enumerate(targets):
-        refs = (sparse.sparse_kl_field(P, t, th), sparse.sparse_tv_field(P, t, th), sparse.sparse_klt_field(P, t, th))
-        for f, (r, lo) in enumerate(zip(refs, (80.0, None, 50.0))):
-            assert field_error(got[f, a], r) <= TOL_FP32, (f, field_error(got[f, a], r))
-            assert got[f, a, t] == 0.0
-            inf = ~np.isfinite(r)
-            if inf.any():
-                assert np.all(got[f, a][inf] >= lo)
+    # the same kernel arithmetic alone or together
+    assert np.array_equal(one.cpu().numpy()[0], got[2]) and np.array_equal(two.cpu().numpy()[0], got[1])
+    assert _check_sparse(dd, got, P, th, targets) < 0.01
+    _check_sparse(dd, mrg.cpu().numpy(), P, th, targets, merged=True)
     dd.dd_unload_mesh(ctx, mid)
 
 
@@ -176,21 +212,18 @@ def test_sparse_states_and_errors(env):
 
 
 def test_sparse_end_to_end_grid140(env):
-    """Device PCG, dd_sparsify, sparse fields and a traced query; the oracle
-    runs on the kernel the device stored (exported), so the kept sets agree."""
+    """Device PCG, dd_sparsify, sparse fields and a traced query against the
+    oracle's own FP64 kernel of the same mesh."""
     dd, ctx = env
     wl = workloads.grid140(T=3, S=8)
     mesh = wl.mesh
+    P = PoissonOracle(mesh.xy, mesh.tri, mesh.loops).full()
     mid = load(dd, ctx, mesh)
     dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
-    info = dd.dd_mesh_info(ctx, mid)
-    P32 = np.empty((mesh.n_v, info["k"]), dtype=np.float32)
-    dd.dd_get_poisson_kernel(ctx, mid, P32)
-    P = P32.astype(np.float64)
     th = sparse.default_theta(mesh.n_v)
-    kept, blocks = dd.dd_sparsify(ctx, mid)
+    kept, _ = dd.dd_sparsify(ctx, mid)
     mask = sparse.keep_mask(P, th)
-    assert kept == int(mask.sum()) and blocks == _blocks(mask)
+    assert abs(kept - int(mask.sum())) <= int(_border(P, th).sum())
     assert 0.5 < 1.0 - kept / P.size < 0.99
     targets = [int(t) for t in wl.targets]
     S = wl.sources.shape[1]
@@ -201,11 +234,7 @@ def test_sparse_end_to_end_grid140(env):
     dd.dd_query(ctx, mid, targets, wl.sources, dd.DD_F_KL | dd.DD_F_TV | dd.DD_F_KLT, dd.DD_PREC_SPARSE,
                 dd.DD_F_KLT, 1024, f, xy, ln, st)
     dd.dd_sync(ctx)
-    g = f.cpu().numpy()
-    for a, t in enumerate(targets):
-        assert field_error(g[0, a], sparse.sparse_kl_field(P, t, th)) <= TOL_FP32
-        assert field_error(g[1, a], sparse.sparse_tv_field(P, t, th)) <= TOL_FP32
-        assert field_error(g[2, a], sparse.sparse_klt_field(P, t, th)) <= TOL_FP32
+    assert _check_sparse(dd, f.cpu().numpy(), P, th, targets) < 0.01
     # the query traced exactly what dd_trace_fields traces on the same sparse field
     xy2, ln2, st2 = torch.empty_like(xy), torch.empty_like(ln), torch.empty_like(st)
     dd.dd_trace_fields(ctx, mid, f[2].contiguous(), targets, wl.sources, 1024, xy2, ln2, st2)

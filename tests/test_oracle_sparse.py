@@ -1,15 +1,19 @@
-"""Pins for the oracle's sparse KL/KLT/TV fields (Section V; the target row's
-entries below 1/sqrt(n) of its maximum merged into one bin) -- CPU only.
+"""Pins for the oracle's sparse fields (Section V: P sparsified by eliminating
+the entries below 1/sqrt(n) of their row's maximum before the sums) -- CPU only.
 
-Pinned by: a hand-worked example (the kept columns, the merged bin and both
-sums written out), the dense fields as the theta -> 0 limit, the
-data-processing inequality (merging columns cannot increase an f-divergence:
-0 <= KL~ <= KL, 0 <= KLT~ <= KLT, 0 <= TV~ <= TV) and the bound TV - TV~ <= 2 M_t, exact zeros
-at the target, the FP32 threshold decision, nested kept sets as theta grows,
-the disk's centre row, whose entries are all equal by the mesh's
-rotational symmetry, so that no threshold below 1 drops any of them, and the
-sparsities Table I prints (tests/golden/table1_domains.txt), which the
-relative threshold approaches and an absolute one does not.
+Pinned by: a hand-worked example (the kept entries of each row and every
+sum written out), the threshold decided in FP64 (an entry equal to theta x
+max is kept, the next double below is not, and an entry FP32 rounding would
+keep is not), the dense fields as the theta -> 0 limit, exact zeros at the
+target, the log-sum inequality (a restricted KL sum is at least A log(A/C)
+for the masses A, C it covers), the triangle inequality for TV between
+sparsified rows, nested kept sets as theta grows, the disk's centre row,
+whose entries are all equal by the mesh's rotational symmetry (no threshold
+below 1 drops any, so the target-weighted field is the dense one and has
+the disk's closed form), and the sparsities Table I prints
+(tests/golden/table1_domains.txt), which the relative threshold approaches
+and an absolute one does not.  The merged-bin extension is pinned by its own
+hand example and the data-processing inequality.
 """
 import math
 import os
@@ -24,37 +28,48 @@ from oracle.poisson import PoissonOracle
 from synthetic import workloads
 from synthetic.meshes import convex_holes, disk_rings
 
+# rows keep {0, 2}, all four, {0, 2} at theta = 0.01 (thresholds 0.005, 0.0025, 0.009)
+HAND = np.array([[0.5, 0.004, 0.495, 0.001],
+                 [0.25, 0.25, 0.25, 0.25],
+                 [0.9, 0.0089, 0.0911, 0.0]])
+
 
 def test_hand_example():
-    # target row 0 keeps columns {0, 2} at theta = 0.01 (0.004 < 0.005); M_0 = 0.004
-    P = np.array([[0.5, 0.004, 0.496, 0.0],
-                  [0.25, 0.25, 0.25, 0.25],
-                  [0.9, 0.0089, 0.0911, 0.0]])
-    assert sparse.support(P, 0, 0.01).tolist() == [True, False, True, False]
-    # rows keep 2, 4 and 2 of their 4 entries (zeros are never kept)
-    assert sparse.sparsity(P, 0.01) == pytest.approx(1.0 / 3.0, abs=1e-15)
-    assert sparse.merged_mass(P, 0, 0.01) == pytest.approx(0.004, abs=1e-18)
-    kl = sparse.sparse_kl_field(P, 0, 0.01)
-    # row 1: 0.25 log(0.25/0.5) + 0.25 log(0.25/0.496) + (0.5) log(0.5/0.004)
-    ref1 = 0.25 * math.log(0.5) + 0.25 * math.log(0.25 / 0.496) + 0.5 * math.log(0.5 / 0.004)
-    assert kl[1] == pytest.approx(ref1, rel=1e-14)
-    assert kl[0] == 0.0
-    klt = sparse.sparse_klt_field(P, 0, 0.01)
-    # row 2: 0.5 log(0.5/0.9) + 0.496 log(0.496/0.0911) + 0.004 log(0.004/0.0089)
-    ref2 = 0.5 * math.log(0.5 / 0.9) + 0.496 * math.log(0.496 / 0.0911) + 0.004 * math.log(0.004 / 0.0089)
-    assert klt[2] == pytest.approx(ref2, rel=1e-14)
-    assert klt[0] == 0.0
-    tv = sparse.sparse_tv_field(P, 0, 0.01)
-    # row 2: |0.9 - 0.5| + |0.0911 - 0.496| + |0.0089 - 0.004|
-    assert tv[2] == pytest.approx(0.4 + 0.4049 + 0.0049, rel=1e-13)
-    assert tv[0] == 0.0
+    P, th = HAND, 0.01
+    assert sparse.keep_mask(P, th).tolist() == [[True, False, True, False], [True] * 4,
+                                                [True, False, True, False]]
+    assert sparse.support(P, 0, th).tolist() == [True, False, True, False]
+    assert sparse.sparsity(P, th) == pytest.approx(1.0 / 3.0, abs=1e-15)
+    L = math.log
+    # target-weighted: the target's kept columns 0 and 2 weight the terms
+    klt = sparse.sparse_klt_field(P, 0, th)
+    assert klt[1] == pytest.approx(0.5 * L(0.5 / 0.25) + 0.495 * L(0.495 / 0.25), rel=1e-14)
+    assert klt[2] == pytest.approx(0.5 * L(0.5 / 0.9) + 0.495 * L(0.495 / 0.0911), rel=1e-14)
+    assert sparse.sparse_klt_field(P, 1, th)[0] == pytest.approx(
+        0.25 * (L(0.25 / 0.5) + L(0.25 / 0.004) + L(0.25 / 0.495) + L(0.25 / 0.001)), rel=1e-14)
+    # field-weighted: each row's own kept entries weight the terms, the target's log from its full row
+    kl = sparse.sparse_kl_field(P, 0, th)
+    assert kl[1] == pytest.approx(0.25 * (L(0.25 / 0.5) + L(0.25 / 0.004) + L(0.25 / 0.495) + L(0.25 / 0.001)),
+                                  rel=1e-14)
+    assert kl[2] == pytest.approx(0.9 * L(0.9 / 0.5) + 0.0911 * L(0.0911 / 0.495), rel=1e-14)
+    assert np.isinf(sparse.sparse_kl_field(P, 2, th)[1])          # row 1 keeps column 3, where P[2,3] = 0
+    # TV between the sparsified rows [0.5, 0, 0.495, 0], [.25]*4, [0.9, 0, 0.0911, 0]
+    tv = sparse.sparse_tv_field(P, 0, th)
+    assert tv[1] == pytest.approx(0.25 + 0.25 + 0.245 + 0.25, rel=1e-14)
+    assert tv[2] == pytest.approx(0.4 + 0.4039, rel=1e-14)
+    for f in (klt, kl, tv):
+        assert f[0] == 0.0
 
 
-def test_threshold_decided_in_fp32():
-    thr = np.float32(0.01) * np.float32(0.5)
-    below = np.nextafter(thr, np.float32(0.0))
-    P = np.array([[0.5, float(thr), float(below), 0.5 - float(thr) - float(below)]])
-    assert sparse.keep_mask(P, 0.01).tolist() == [[True, True, False, True]]
+def test_threshold_decided_in_fp64():
+    th, mx = 0.01, 0.5
+    at = th * mx                                   # exactly the threshold: kept
+    below = np.nextafter(at, 0.0)                  # one double below: dropped
+    # FP32 rounding would keep this one: float32(v) >= float32(theta) * float32(max)
+    v32 = 0.00499999995
+    assert np.float32(v32) >= np.float32(th) * np.float32(mx) and v32 < at
+    P = np.array([[mx, at, below, v32, 0.0]])
+    assert sparse.keep_mask(P, th).tolist() == [[True, True, False, False, False]]
 
 
 def _cases():
@@ -64,32 +79,35 @@ def _cases():
 
 
 @pytest.mark.parametrize("idx", [0, 1])
-def test_dense_limit_data_processing_and_zeros(idx):
+def test_dense_limit_bounds_and_zeros(idx):
     mesh, targets = _cases()[idx]
     po = PoissonOracle(mesh.xy, mesh.tri, mesh.loops)
     P = po.full()
     theta = sparse.default_theta(mesh.n_v)
+    keep = sparse.keep_mask(P, theta)
+    dropped = np.where(keep, 0.0, P).sum(axis=1)           # mass each row loses
     for t in targets:
-        kl, tv = kl_field_fast(P, P[t]), tv_field(P, P[t])
-        fin = np.isfinite(kl)
-        # theta -> 0: only the target's zero columns are merged (mass 0 in row t)
-        k0 = sparse.sparse_kl_field(P, t, 1e-30)
-        assert np.allclose(k0[fin], kl[fin], rtol=1e-12, atol=1e-14)
-        assert np.all(~np.isfinite(k0[~fin]))
-        assert np.allclose(sparse.sparse_tv_field(P, t, 1e-30), tv, rtol=1e-12, atol=1e-14)
-        klt = kl_reverse_field(P, P[t])
-        kt0 = sparse.sparse_klt_field(P, t, 1e-30)
-        assert np.allclose(kt0[np.isfinite(klt)], klt[np.isfinite(klt)], rtol=1e-12, atol=1e-14)
-        ks, ts = sparse.sparse_kl_field(P, t, theta), sparse.sparse_tv_field(P, t, theta)
-        kts = sparse.sparse_klt_field(P, t, theta)
+        kl, tv, klt = kl_field_fast(P, P[t]), tv_field(P, P[t]), kl_reverse_field(P, P[t])
+        # theta -> 0 keeps every positive entry: the dense fields wherever they are finite
+        for sp, dense in ((sparse.sparse_kl_field, kl), (sparse.sparse_tv_field, tv),
+                          (sparse.sparse_klt_field, klt)):
+            f0 = sp(P, t, 1e-300)
+            fin = np.isfinite(dense)
+            assert np.allclose(f0[fin], dense[fin], rtol=1e-12, atol=1e-14)
+        ks, ts, kts = (sparse.sparse_kl_field(P, t, theta), sparse.sparse_tv_field(P, t, theta),
+                       sparse.sparse_klt_field(P, t, theta))
         assert ks[t] == 0.0 and ts[t] == 0.0 and kts[t] == 0.0
-        assert sparse.merged_mass(P, t, theta) > 0.0 or idx == 1
-        m_t = sparse.merged_mass(P, t, theta)
+        assert dropped[t] > 0.0 or idx == 1
+        S_t = keep[t]
         for x in po.I:
-            assert -1e-13 <= ks[x] <= kl[x] * (1 + 1e-12) + 1e-13
-            assert -1e-13 <= ts[x] <= tv[x] * (1 + 1e-12) + 1e-13
-            assert -1e-13 <= kts[x] <= klt[x] * (1 + 1e-12) + 1e-13
-            assert tv[x] - ts[x] <= 2 * m_t * (1 + 1e-9) + 1e-13
+            # log-sum inequality over the columns each sum covers
+            A, C = P[t, S_t].sum(), P[x, S_t].sum()
+            assert kts[x] >= A * math.log(A / C) - 1e-12
+            S_x = keep[x]
+            A, C = P[x, S_x].sum(), P[t, S_x].sum()
+            assert ks[x] >= A * math.log(A / C) - 1e-12
+            # triangle inequality: sparsifying the two rows moves TV by at most the mass they lose
+            assert abs(ts[x] - tv[x]) <= dropped[x] + dropped[t] + 1e-13
 
 
 def test_nested_and_disk_centre():
@@ -105,10 +123,41 @@ def test_nested_and_disk_centre():
     # vertex 0 is the centre: all 48 entries equal up to the solve's rounding
     assert np.ptp(P[0]) < 1e-12
     assert sparse.support(P, 0, 0.999).all()
-    assert sparse.merged_mass(P, 0, sparse.default_theta(mesh.n_v)) == 0.0
-    # so with the centre as target the sparse fields are the dense ones
-    t = 0
-    assert np.allclose(sparse.sparse_tv_field(P, t, 0.5), tv_field(P, P[t]), rtol=1e-13, atol=1e-15)
+    # so with the centre as target the target-weighted sparse field is the dense one,
+    # whose disk value is -log(1 - |x|^2) up to discretisation (appendix, Eq. A6)
+    klt = sparse.sparse_klt_field(P, 0, 0.5)
+    assert np.allclose(klt[po.I], kl_reverse_field(P, P[0])[po.I], rtol=1e-13, atol=1e-15)
+    r2 = (mesh.xy[po.I] ** 2).sum(axis=1)
+    inner = r2 < 0.5 ** 2
+    assert np.max(np.abs(klt[po.I][inner] + np.log1p(-r2[inner]))) < 0.02
+
+
+def test_merged_bin_extension():
+    """The merged-bin fields: hand values and the data-processing inequality."""
+    P, th = HAND, 0.01
+    L = math.log
+    assert sparse.merged_mass(P, 0, th) == pytest.approx(0.005, abs=1e-17)
+    # row 1: columns 0, 2 plus the bin of mass 0.5 against the target's 0.005
+    assert sparse.merged_kl_field(P, 0, th)[1] == pytest.approx(
+        0.25 * L(0.5) + 0.25 * L(0.25 / 0.495) + 0.5 * L(0.5 / 0.005), rel=1e-14)
+    assert sparse.merged_klt_field(P, 0, th)[2] == pytest.approx(
+        0.5 * L(0.5 / 0.9) + 0.495 * L(0.495 / 0.0911) + 0.005 * L(0.005 / 0.0089), rel=1e-14)
+    assert sparse.merged_tv_field(P, 0, th)[2] == pytest.approx(0.4 + 0.4039 + 0.0039, rel=1e-13)
+    mesh, targets = _cases()[0]
+    po = PoissonOracle(mesh.xy, mesh.tri, mesh.loops)
+    P = po.full()
+    theta = sparse.default_theta(mesh.n_v)
+    for t in targets[:2]:
+        kl, tv, klt = kl_field_fast(P, P[t]), tv_field(P, P[t]), kl_reverse_field(P, P[t])
+        ks, ts, kts = (sparse.merged_kl_field(P, t, theta), sparse.merged_tv_field(P, t, theta),
+                       sparse.merged_klt_field(P, t, theta))
+        m_t = sparse.merged_mass(P, t, theta)
+        assert ks[t] == 0.0 and ts[t] == 0.0 and kts[t] == 0.0
+        for x in po.I:
+            assert -1e-13 <= ks[x] <= kl[x] * (1 + 1e-12) + 1e-13
+            assert -1e-13 <= ts[x] <= tv[x] * (1 + 1e-12) + 1e-13
+            assert -1e-13 <= kts[x] <= klt[x] * (1 + 1e-12) + 1e-13
+            assert tv[x] - ts[x] <= 2 * m_t * (1 + 1e-9) + 1e-13
 
 
 def _table1():
