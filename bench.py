@@ -1,10 +1,11 @@
 """Benchmark of the online divergence-distance path (fields + traced paths).
 
-One step = one dd_query over a batch of the grid140 workload: KL and TV
-fields of 64 interior targets over all n = 18,174 vertices (k = 1,028
-boundary columns) and 64 x 256 paths traced on the KL fields.  The Poisson
-kernel is computed once per domain before timing (the paper's
-preprocessing) and reported separately.
+One step = one dd_query over a batch of the grid450 workload (the largest
+configuration that fits one GPU): KL and TV fields of 1,024 interior targets
+over all n = 192,360 vertices (k = 3,936 boundary columns, P = 3.0 GB FP32)
+on the FP32 path, and 1,024 x 16 paths traced on the KL fields.  The Poisson
+kernel is computed once per domain before timing (the paper's preprocessing)
+and reported separately.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -14,14 +15,17 @@ processes its own target batches (weak scaling, no data-path collective).
 same workload (rank 0 only).
 
 The JSON line: `value` from CUDA events around each step (inputs resident,
-L2 flushed between steps outside the events), `e2e` through the same call
-with pinned host buffers, `kernels` (live per-kernel times from the
-library's own events), `roofline` for the dominant kernel with
-`roofline_fields` / `roofline_walk` for the other of the two, `clocks`
-sampled during the timed region (measured once more, with `remeasured`, if
-they show a slowdown or a clock lock), `cpu_baseline` (the oracle on every
-host core), `step_bf16x3` (the same step on the split-BF16 path), and with
-no `--section` the grid450, batch, serving and census measurements.
+P far larger than L2, L2 also flushed between steps outside the events),
+`e2e` through the same call with pinned host buffers, `kernels` (live
+per-kernel times from the library's own events), `roofline` for the
+dominant kernel, `clocks` sampled during the timed region (measured once
+more, with `remeasured`, if they show a slowdown or a clock lock),
+`error_vs_oracle` (every result of the step against the FP64 oracle on
+sampled rows), `step_bf16x3` (the same step with the KL fields from the
+split-BF16 tensor-core GEMM), `cpu_baseline` (the oracle on every host core,
+full fields and the paper's path-only scheme), and with no `--section` the
+grid140 step, the grid450 single-target, sparse and other-divergence
+passes, the batch, serving and census measurements.
 """
 
 import argparse
@@ -41,21 +45,31 @@ if ROOT not in sys.path:
 
 METRIC = "distance fields/s (KL+TV, one target over all vertices) with traced paths"
 UNIT = "fields/s"
-T_BATCH, S_PER_TARGET, MAX_PTS = 64, 256, 1024
+# the query-step workloads: targets per step, sources per target, polyline capacity
+WORKLOADS = {
+    "grid450": {"T": 1024, "S": 16, "max_pts": 4096,
+                "desc": "grid450: unit square h=1/450, 24 rectangular obstacles, n=%d, k=%d; %d targets x (KL+TV) "
+                        "+ %dx%d KL paths per step"},
+    "grid140": {"T": 64, "S": 256, "max_pts": 1024,
+                "desc": "grid140: unit square h=1/140, 8 square obstacles, n=%d, k=%d; %d targets x (KL+TV) "
+                        "+ %dx%d KL paths per step"},
+}
+HEADLINE = "grid450"
 # kernels one dd_query step launches: target staging, field tile, exact KL
 # recompute near the targets, triangle rates, vertex decisions, path walk
 STEP_LAUNCHES = 6
-# bytes the walk gathers and stores per point it appends: one 64-B triangle
-# record, one 16-B rate vector, one 8-B point
-WALK_BYTES_PER_POINT = 88
-# DRAM bytes (read + write) of one field_tile_kernel launch of this step, from an
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); P is read once
-TILE_TRAFFIC_BYTES = 77092352        # 75,064,576 read + 2,027,776 written (P is 4 n k_pad = 74.7 MB; 64x64 shape)
-# the same for one trace_kernel launch (records and rates mostly served by L2)
-WALK_TRAFFIC_BYTES = 31522560        # 31,330,816 read + 191,744 written
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from
+# ncu captures of the step's kernels; None where no capture of the current
+# kernel exists
+TRAFFIC = {
+    "grid140": {"field_tile_kernel": 77092352, "trace_kernel": 31522560},
+    "grid450": {},
+}
 # the same for one field_stream_kernel launch of the grid450 single-target pass
 STREAM_TRAFFIC_BYTES = 3035740160    # 3,032,217,088 read + 3,523,072 written (4 n k_pad = 3.03 GB of P)
-N_BATCHES = 8
+N_BATCHES = 4
+# sampled rows and targets for the error against the FP64 oracle (Green's rows)
+ERR_ROWS, ERR_TARGETS = 256, 128
 
 
 def peaks():
@@ -77,19 +91,33 @@ def max_over_ranks(value: float, device=None) -> float:
     return float(t.item())
 
 
-def workload_batches(rank: int):
+def make_workload(name: str, T: int, S: int):
+    from synthetic import workloads
+    return getattr(workloads, name)(T=T, S=S)
+
+
+def workload_batches(rank: int, name: str = HEADLINE):
     from synthetic import workloads
     from synthetic.rng import SplitMix64
-    wl = workloads.grid140(T=T_BATCH, S=S_PER_TARGET)
+    w = WORKLOADS[name]
+    wl = make_workload(name, w["T"], w["S"])
     # rank 0 starts with the workload's own batch; every other batch (and all of
     # another rank's) is drawn from a rank-seeded stream, so ranks share no work
     batches = [(wl.targets, wl.sources)] if rank == 0 else []
     rng = SplitMix64(workloads.BASE_SEED + 1000 + rank)
     while len(batches) < N_BATCHES:
-        t = workloads.draw_targets(rng, wl.mesh, T_BATCH)
-        s = workloads.draw_sources(rng, wl.mesh, t, S_PER_TARGET)
+        t = workloads.draw_targets(rng, wl.mesh, w["T"])
+        s = workloads.draw_sources(rng, wl.mesh, t, w["S"])
         batches.append((t, s))
     return wl, batches
+
+
+def sm_count(device_index: int) -> int:
+    import torch
+    try:
+        return int(torch.cuda.get_device_properties(device_index).multi_processor_count)
+    except Exception:
+        return 0
 
 
 class ClockSampler:
@@ -147,57 +175,57 @@ def clocks_rejected(clocks) -> bool:
     return bool(sm and mx and sm < 0.8 * mx and not reasons)
 
 
-def run_ours(args, rank, world, local_rank):
-    import torch
-    from paper_1708_02845_gb300.build import build
-    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1708_02845_gb300", "_lib", "libdd.so")):
-        build()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    from paper_1708_02845_gb300 import dd
+def roof_tile(n_v, k, T, tile_ms, sms, sm_mhz, traffic):
+    """The field tile kernel against the FP32 instruction issue rate: per
+    (row, column, target) KL one FADD (log2 ratio) + one FFMA, TV two FADD."""
+    ops = 4.0 * n_v * k * T
+    peak_alu = sms * 128 * sm_mhz * 1e6 / 1e12
+    achieved = ops / (tile_ms / 1e3) / 1e12
+    return {"kernel": "field_tile_kernel", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 3),
+            "unit": "T FP32 instructions/s", "frac": round(achieved / peak_alu, 4), "traffic": traffic,
+            "algorithmic_fp32_ops": ops, "ms_per_launch": round(tile_ms, 4),
+            "peak_source": f"{sms} SMs (read from the device) x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock "
+                           "sampled in the timed region), one FP32 instruction per lane per clock",
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch" if traffic else
+                              "no ncu capture of this kernel on this workload"}
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.current_stream()
-    ctx = dd.dd_create(local_rank, stream.cuda_stream)
-    if args.section in ("grid450", "batch", "serve", "census", "mid"):
-        pk, pk_kind = peaks()
-        flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev)
-        if args.section == "grid450":
-            st_sec, gm_sec = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
-            out = {"metric": "grid450 sections only", "stream": st_sec, "gemm": gm_sec}
-        elif args.section == "batch":
-            out = {"metric": "batch64 section only", "batch": batch_section(dd, ctx, dev, stream, flush, args)}
-        elif args.section == "census":
-            out = {"metric": "census section only", "census": census_section(dd, ctx, dev)}
-        elif args.section == "mid":
-            out = {"metric": "grid300 section only", "mid": mid_section(dd, ctx, dev, stream, flush, pk, pk_kind)}
-        else:
-            out = {"metric": "serving section only", "serve": serve_section(dd, ctx, args, n_domains=8, seconds=10.0)}
-        dd.dd_destroy(ctx)
-        return out
-    wl, batches = workload_batches(rank)
+
+def roof_walk(walk_ms, walk_points, max_points, traffic):
+    """The walk: a chain of dependent gathers per path (one triangle record and
+    one rate vector per crossing), bounded by the longest path's chain of
+    dependent L2 round trips, not by a bandwidth."""
+    return {"kernel": "trace_kernel", "bound": "latency", "ms_per_launch": round(walk_ms, 4),
+            "points_per_s": round(walk_points / (walk_ms / 1e3), 1), "longest_path_points": int(max_points),
+            "us_per_point_of_longest_path": round(walk_ms * 1e3 / max(max_points, 1), 4), "traffic": traffic,
+            "note": "one dependent record + rate gather per crossing; the launch lasts as long as its longest path"}
+
+
+def query_step(dd, ctx, dev, stream, flush, args, rank, world, local_rank, name, pk, pk_kind):
+    """Load the workload, compute its Poisson kernel, then time K dd_query steps
+    (T targets x KL+TV fields + T x S KL paths) with CUDA events on the
+    context stream, per-kernel times from the library's events, clocks
+    sampled meanwhile; then the same call end to end with pinned host buffers."""
+    import torch
+    w = WORKLOADS[name]
+    T, S, max_pts = w["T"], w["S"], w["max_pts"]
+    wl, batches = workload_batches(rank, name)
     mesh = wl.mesh
     idx, off = mesh.loop_arrays()
     mid = dd.dd_load_mesh(ctx, mesh.xy, mesh.tri, idx, off)
     info = dd.dd_mesh_info(ctx, mid)
     t0 = time.perf_counter()
-    iters, resid = dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
+    iters, resid = dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
     preproc_s = time.perf_counter() - t0
-    n_v, k, k_pad = info["n_v"], info["k"], info["k_pad"]
+    n_v, k = info["n_v"], info["k"]
 
-    T, S = T_BATCH, S_PER_TARGET
     fields = torch.empty((2, T, n_v), dtype=torch.float32, device=dev)
-    pxy = torch.empty((T * S, MAX_PTS, 2), dtype=torch.float32, device=dev)
+    pxy = torch.empty((T * S, max_pts, 2), dtype=torch.float32, device=dev)
     plen = torch.empty(T * S, dtype=torch.int32, device=dev)
     pst = torch.empty(T * S, dtype=torch.int32, device=dev)
-    l2_bytes = 256 << 20
-    flush = torch.empty(l2_bytes // 4, dtype=torch.float32, device=dev)
 
     def step(i):
         tg, sr = batches[i % len(batches)]
-        dd.dd_query(ctx, mid, tg, sr, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, dd.DD_F_KL, MAX_PTS,
+        dd.dd_query(ctx, mid, tg, sr, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, dd.DD_F_KL, max_pts,
                     fields, pxy, plen, pst)
 
     for i in range(args.warmup):
@@ -206,16 +234,16 @@ def run_ours(args, rank, world, local_rank):
     dd.dd_sync(ctx)
     torch.cuda.synchronize()
 
-    # per-kernel split on the same stream (untimed for the metric): fields vs tracing
+    # fields vs tracing on the same stream (untimed for the metric)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     tg, sr = batches[0]
     split_f, split_t = [], []
-    for r in range(3):
+    for r in range(2):
         flush.fill_(1.0)
         ev[0].record(stream)
         dd.dd_distance(ctx, mid, tg, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, fields)
         ev[1].record(stream)
-        dd.dd_trace_fields(ctx, mid, fields[0], tg, sr, MAX_PTS, pxy, plen, pst)
+        dd.dd_trace_fields(ctx, mid, fields[0], tg, sr, max_pts, pxy, plen, pst)
         ev[2].record(stream)
         torch.cuda.synchronize()
         split_f.append(ev[0].elapsed_time(ev[1]))
@@ -266,18 +294,18 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the same C-ABI call with host buffers
     hf = torch.empty((2, T, n_v), dtype=torch.float32).pin_memory()
-    hxy = torch.empty((T * S, MAX_PTS, 2), dtype=torch.float32).pin_memory()
+    hxy = torch.empty((T * S, max_pts, 2), dtype=torch.float32).pin_memory()
     hl = torch.empty(T * S, dtype=torch.int32).pin_memory()
     hs = torch.empty(T * S, dtype=torch.int32).pin_memory()
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = max(3, min(args.steps, 10))
     for i in range(2):
-        tg, sr = batches[i]
-        dd.dd_query(ctx, mid, tg, sr, 3, 0, 1, MAX_PTS, hf, hxy, hl, hs)
+        tg, sr = batches[i % len(batches)]
+        dd.dd_query(ctx, mid, tg, sr, 3, 0, 1, max_pts, hf, hxy, hl, hs)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     for i in range(e2e_steps):
         tg, sr = batches[i % len(batches)]
-        dd.dd_query(ctx, mid, tg, sr, 3, 0, 1, MAX_PTS, hf, hxy, hl, hs)
+        dd.dd_query(ctx, mid, tg, sr, 3, 0, 1, max_pts, hf, hxy, hl, hs)
     e2e_s = time.perf_counter() - e0
     # into pinned host buffers the library moves exactly each path's defined
     # prefix (len points), plus the lengths and statuses (counted on the last
@@ -286,94 +314,67 @@ def run_ours(args, rank, world, local_rank):
     path_bytes = int(ln.astype(np.int64).sum()) * 8
     h2d = T * 4 + T * S * 4
     d2h = 2 * T * n_v * 4 + T * S * 8 + path_bytes
+    del hf, hxy, hl, hs
 
     fields_per_step = 2 * T
     value = world * fields_per_step * args.steps / (dev_ms / 1e3)
-    pk, pk_kind = peaks()
-    # dominant kernel (largest device time over the timed steps) and its roofline
     sm_mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    sms = sm_count(local_rank) or 152
     tot = sum(ms for _, ms in kernel_ms.values()) or 1.0
-    kernels = {name: {"launches": n, "ms_per_launch": round(ms / max(n, 1), 4), "share": round(ms / tot, 4)}
-               for name, (n, ms) in sorted(kernel_ms.items(), key=lambda kv: -kv[1][1])}
-    dom = max(kernel_ms, key=lambda k: kernel_ms[k][1]) if kernel_ms else "field_tile_kernel"
-    dom_ms = kernel_ms[dom][1] / max(kernel_ms[dom][0], 1) if kernel_ms else field_ms
-    walk_ms = kernel_ms["trace_kernel"][1] / max(kernel_ms["trace_kernel"][0], 1) if "trace_kernel" in kernel_ms else None
-    walk_steps = int(np.clip(lens, 0, None).sum())
-    tile_ms = kernel_ms["field_tile_kernel"][1] / max(kernel_ms["field_tile_kernel"][0], 1) \
-        if "field_tile_kernel" in kernel_ms else field_ms
-    # field tile: per (x, b, t) KL one FADD (log2 ratio) + one FFMA, TV two FADD = 4 FP32 instructions
-    ops = 4.0 * n_v * k * T
-    hbm_peak = float(pk["hbm_gbs"])
-    peak_alu = 152 * 128 * sm_mhz * 1e6 / 1e12
-    roof_tile = {"kernel": "field_tile_kernel", "bound": "alu", "achieved": round(ops / (tile_ms / 1e3) / 1e12, 3),
-                 "peak": round(peak_alu, 3), "unit": "T FP32 instructions/s",
-                 "frac": round(ops / (tile_ms / 1e3) / 1e12 / peak_alu, 4), "traffic": TILE_TRAFFIC_BYTES,
-                 "algorithmic_fp32_ops": ops, "ms_per_launch": round(tile_ms, 4),
-                 "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled), one "
-                                "FP32 instruction per lane per clock",
-                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, this workload"}
-    if walk_ms is not None:
-        # walk: per point appended, one 64-B triangle record and one 16-B rate gathered, one 8-B point stored
-        wbytes = WALK_BYTES_PER_POINT * walk_steps
-        roof_walk = {"kernel": "trace_kernel", "bound": "hbm", "achieved": round(wbytes / (walk_ms / 1e3) / 1e9, 1),
-                     "peak": hbm_peak, "unit": "GB/s", "frac": round(wbytes / (walk_ms / 1e3) / 1e9 / hbm_peak, 4),
-                     "traffic": WALK_TRAFFIC_BYTES, "algorithmic_bytes": wbytes, "ms_per_launch": round(walk_ms, 4),
-                     "peak_source": "measured HBM copy bandwidth, burst",
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, this workload",
-                     "note": "a chain of dependent gathers (latency-bound): the records and rates (39 MB) are "
-                             "L2-resident, so the DRAM traffic is far below the gathered bytes and the frac "
-                             "against HBM shows the distance from any bandwidth roofline"}
-    else:
-        roof_walk = None
-    dom = max(kernel_ms, key=lambda k: kernel_ms[k][1]) if kernel_ms else "field_tile_kernel"
-    roof = roof_walk if (dom == "trace_kernel" and roof_walk is not None) else roof_tile
+    kernels = {kn: {"launches": c, "ms_per_launch": round(ms / max(c, 1), 4), "share": round(ms / tot, 4)}
+               for kn, (c, ms) in sorted(kernel_ms.items(), key=lambda kv: -kv[1][1])}
+    per_launch = {kn: ms / max(c, 1) for kn, (c, ms) in kernel_ms.items()}
+    traffic = TRAFFIC.get(name, {})
+    tile_ms = per_launch.get("field_tile_kernel", field_ms)
+    roof_t = roof_tile(n_v, k, T, tile_ms, sms, sm_mhz, traffic.get("field_tile_kernel"))
+    walk_ms = per_launch.get("trace_kernel")
+    walk_points = int(np.clip(lens, 0, None).sum())
+    roof_w = roof_walk(walk_ms, walk_points, int(lens.max()), traffic.get("trace_kernel")) if walk_ms else None
+    dom = max(kernel_ms, key=lambda kn: kernel_ms[kn][1]) if kernel_ms else "field_tile_kernel"
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "grid140: unit square h=1/140, 8 square obstacles, n=%d, k=%d; 64 targets x "
-                               "(KL+TV) + 64x256 KL paths per step" % (n_v, k),
-                   "n_v": n_v, "k": k, "targets_per_step": T, "sources_per_target": S, "max_pts": MAX_PTS,
-                   "l2": "flushed between steps (256 MB write outside the step events)",
+        "config": {"workload": w["desc"] % (n_v, k, T, T, S), "n_v": n_v, "k": k, "targets_per_step": T,
+                   "sources_per_target": S, "max_pts": max_pts, "precision": "FP32 fields (DD_PREC_FP32)",
+                   "l2": "inputs larger than L2 (P = %.2f GB); L2 also flushed between steps (256 MB write outside "
+                         "the step events)" % (4.0 * n_v * info["k_pad"] / 1e9),
                    "parallelism": f"replicas x{world}"},
         "paths_per_s": round(world * T * S * args.steps / (dev_ms / 1e3), 1),
-        "walk_steps_per_s": round(walk_steps / (walk_ms / 1e3), 1) if walk_ms else None,
         "kernel_split_ms": {"fields": round(field_ms, 4), "trace": round(trace_ms, 4)},
         "paths_ok_frac": float(np.mean(status == 0)), "max_path_pts": int(lens.max()),
         "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(preproc_s, 3)},
         "wall_s_timed_region": round(wall, 4),
-        "roofline": roof, "roofline_fields": roof_tile if roof is not roof_tile else None,
-        "roofline_walk": roof_walk if roof is not roof_walk else None, "peaks": pk_kind,
+        "roofline": roof_t if dom != "trace_kernel" or roof_w is None else roof_w,
+        "roofline_walk": roof_w if dom != "trace_kernel" else None,
+        "roofline_fields": roof_t if dom == "trace_kernel" else None, "peaks": pk_kind,
         "e2e": {"value": round(world * fields_per_step * e2e_steps / e2e_s, 1), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(sum(n for n, _ in kernel_ms.values())) or STEP_LAUNCHES * args.steps,
+        "gpu_launches": int(sum(c for c, _ in kernel_ms.values())) or STEP_LAUNCHES * args.steps,
         "kernels": kernels,
         "clocks": clocks,
     }
+    if "fix_kl_kernel" in per_launch:
+        line["recompute_over_tile"] = round(per_launch["fix_kl_kernel"] / tile_ms, 4)
     if remeasured is not None:
         line["remeasured"] = remeasured
-    line["step_bf16x3"] = bf16x3_step(dd, ctx, mid, batches, fields, pxy, plen, pst, flush, stream, args, T, S, n_v)
-    if args.stream and args.section == "all":
-        line["stream"], line["gemm"] = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
-        line["batch"] = batch_section(dd, ctx, dev, stream, flush, args)
-        line["serve"] = serve_section(dd, ctx, args, n_domains=5, seconds=3.0)
-        line["census"] = census_section(dd, ctx, dev)
-    dd.dd_destroy(ctx)
-    return line
+    return {"line": line, "mid": mid, "wl": wl, "batches": batches, "fields": fields, "pxy": pxy, "plen": plen,
+            "pst": pst, "T": T, "S": S, "max_pts": max_pts, "n_v": n_v, "k": k, "k_pad": info["k_pad"]}
 
 
-def bf16x3_step(dd, ctx, mid, batches, fields, pxy, plen, pst, flush, stream, args, T, S, n_v):
+def bf16x3_step(dd, ctx, q, flush, stream, args):
     """The same query step with DD_PREC_BF16X3: the KL fields from the split-BF16
     tensor-core GEMM (error bound 1e-4 of S_x, not the FP32 path's 1e-5: not
     the headline), TV from a TV-only FP32 tile pass, the paths traced on the
-    GEMM's KL fields.  Reports its time and the KL fields' largest deviation
-    from the FP32 path's relative to max(|KL|, 1)."""
+    GEMM's KL fields.  Reports its time, its kernels and the KL fields'
+    largest deviation from the FP32 path's relative to max(|KL|, 1)."""
     import torch
+    mid, batches, fields, T = q["mid"], q["batches"], q["fields"], q["T"]
 
     def step(i):
         tg, sr = batches[i % len(batches)]
-        dd.dd_query(ctx, mid, tg, sr, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_BF16X3, dd.DD_F_KL, MAX_PTS,
-                    fields, pxy, plen, pst)
+        dd.dd_query(ctx, mid, tg, sr, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_BF16X3, dd.DD_F_KL, q["max_pts"],
+                    fields, q["pxy"], q["plen"], q["pst"])
 
     for i in range(args.warmup):
         step(i)
@@ -395,33 +396,170 @@ def bf16x3_step(dd, ctx, mid, batches, fields, pxy, plen, pst, flush, stream, ar
     got = torch.empty_like(fields)
     dd.dd_distance(ctx, mid, tg, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_BF16X3, got)
     torch.cuda.synchronize()
-    r, g = ref.cpu().numpy().astype(np.float64), got.cpu().numpy().astype(np.float64)
-    fin = r[0] < 80.0
+    fin = ref[0] < 80.0
+    dev = (got[0] - ref[0]).abs() / ref[0].abs().clamp(min=1.0)
+    kl_dev = float(dev[fin].max().item())
+    tv_same = bool(torch.equal(got[1], ref[1]))
+    del ref, got
     dev_ms = float(sum(ms))
     return {"ms_per_step": round(dev_ms / args.steps, 4), "fields_per_s": round(2 * T * args.steps / (dev_ms / 1e3), 1),
-            "kl_max_dev_vs_fp32": float(np.max(np.abs(g[0][fin] - r[0][fin]) / np.maximum(np.abs(r[0][fin]), 1.0))),
-            "tv_identical": bool(np.array_equal(g[1], r[1])),
+            "kl_max_dev_vs_fp32": kl_dev, "tv_identical": tv_same,
             "kernels": {n: {"launches": c, "ms_per_launch": round(v / max(c, 1), 4)} for n, (c, v) in kt.items()},
             "note": "KL through the tensor-core GEMM (split BF16, 1e-4 bound), TV through a TV-only FP32 pass"}
 
 
-def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10):
-    """grid450 (n = 192,360, k = 3,936; P = 3.0 GB FP32, far above L2).
+class OracleRows:
+    """FP64 oracle rows of P for sampled vertices and targets of one workload
+    (Green's-row solves), and the dense fields between them."""
+
+    def __init__(self, wl, targets, n_rows: int, seed: int):
+        from oracle.poisson import PoissonOracle
+        from synthetic.rng import SplitMix64
+        t0 = time.perf_counter()
+        po = PoissonOracle(wl.mesh.xy, wl.mesh.tri, wl.mesh.loops)
+        rng = SplitMix64(seed)
+        interior = np.asarray(po.I)
+        self.rows = np.array(sorted({int(interior[rng.choice(len(interior))]) for _ in range(n_rows)}), np.int64)
+        self.targets = np.asarray(targets, np.int64)
+        both = np.concatenate([self.rows, self.targets])
+        R = po.rows(both)
+        self.Px, self.Pt = R[:len(self.rows)], R[len(self.rows):]
+        self.seconds = time.perf_counter() - t0
+        self.n_v = wl.mesh.n_v
+
+    def dense(self):
+        """KL [T][R], TV [T][R], KLT [T][R] and S_x [T][R] = sum_b P[x,b] |log P[t,b]|."""
+        from oracle.divergence import kl_field_fast, tv_field
+        from oracle.fdiv import kl_reverse_field
+        kl = np.stack([kl_field_fast(self.Px, pt) for pt in self.Pt])
+        tv = np.stack([tv_field(self.Px, pt) for pt in self.Pt])
+        klt = np.stack([kl_reverse_field(self.Px, pt) for pt in self.Pt])
+        with np.errstate(divide="ignore"):
+            sx = np.stack([(self.Px * np.abs(np.log(pt))[None, :]).sum(axis=1) for pt in self.Pt])
+        return kl, tv, klt, sx
+
+
+def rel_err(g, r, floor):
+    """max and median of |g - r| / max(|r|, floor) over the finite reference entries."""
+    g = np.asarray(g, np.float64)
+    r = np.asarray(r, np.float64)
+    fl = np.broadcast_to(np.asarray(floor, np.float64), r.shape)
+    fin = np.isfinite(r) & np.isfinite(fl)
+    e = np.abs(g[fin] - r[fin]) / np.maximum(np.abs(r[fin]), fl[fin])
+    return {"max": float(e.max()), "median": float(np.median(e)), "n": int(e.size)}
+
+
+def error_vs_oracle(dd, ctx, dev, q, orows):
+    """Every field result of the step against the FP64 oracle on sampled rows:
+    FP32 KL and TV (tolerance 1e-5 relative, floor 1e-2), split-BF16 KL
+    (1e-4 relative, floor S_x = sum_b P[x,b] |log P[t,b]|)."""
+    import torch
+    mid, n_v = q["mid"], q["n_v"]
+    tg = [int(t) for t in orows.targets]
+    T = len(tg)
+    out = torch.empty((2, T, n_v), dtype=torch.float32, device=dev)
+    dd.dd_distance(ctx, mid, tg, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, out)
+    g32 = out[:, :, torch.as_tensor(orows.rows, device=dev)].cpu().numpy()
+    dd.dd_distance(ctx, mid, tg, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_BF16X3, out)
+    gbf = out[:, :, torch.as_tensor(orows.rows, device=dev)].cpu().numpy()
+    del out
+    kl, tv, _, sx = orows.dense()
+    res = {"sample": "%d sampled interior rows x %d targets of the step's first batch; oracle rows by Green's-row "
+                     "solves (%.1f s)" % (len(orows.rows), T, orows.seconds),
+           "fp32_kl": dict(rel_err(g32[0], kl, 1e-2), tol=1e-5, floor="1e-2"),
+           "fp32_tv": dict(rel_err(g32[1], tv, 1e-2), tol=1e-5, floor="1e-2"),
+           "bf16x3_kl": dict(rel_err(gbf[0], kl, sx), tol=1e-4, floor="S_x"),
+           "bf16x3_tv": dict(rel_err(gbf[1], tv, 1e-2), tol=1e-5, floor="1e-2")}
+    for key in ("fp32_kl", "fp32_tv", "bf16x3_kl", "bf16x3_tv"):
+        res[key]["ok"] = bool(res[key]["max"] <= res[key]["tol"])
+    return res
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1708_02845_gb300.build import build
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1708_02845_gb300", "_lib", "libdd.so")):
+        build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    from paper_1708_02845_gb300 import dd
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    ctx = dd.dd_create(local_rank, stream.cuda_stream)
+    pk, pk_kind = peaks()
+    flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev)
+    if args.section in ("grid450", "batch", "serve", "census", "mid", "grid140"):
+        if args.section == "grid450":
+            st_sec, gm_sec = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
+            out = {"metric": "grid450 sections only", "stream": st_sec, "gemm": gm_sec}
+        elif args.section == "grid140":
+            out = query_step(dd, ctx, dev, stream, flush, args, rank, world, local_rank, "grid140", pk, pk_kind)["line"]
+            out["metric"] = "grid140 step only"
+        elif args.section == "batch":
+            out = {"metric": "batch64 section only", "batch": batch_section(dd, ctx, dev, stream, flush, args)}
+        elif args.section == "census":
+            out = {"metric": "census section only", "census": census_section(dd, ctx, dev)}
+        elif args.section == "mid":
+            out = {"metric": "grid300 section only", "mid": mid_section(dd, ctx, dev, stream, flush, pk, pk_kind)}
+        else:
+            out = {"metric": "serving section only", "serve": serve_section(dd, ctx, args, n_domains=8, seconds=10.0)}
+        dd.dd_destroy(ctx)
+        return out
+    q = query_step(dd, ctx, dev, stream, flush, args, rank, world, local_rank, HEADLINE, pk, pk_kind)
+    line = q["line"]
+    line["step_bf16x3"] = bf16x3_step(dd, ctx, q, flush, stream, args)
+    orows = None
+    if args.oracle_errors and world == 1:
+        orows = OracleRows(q["wl"], q["batches"][0][0][:ERR_TARGETS], ERR_ROWS, seed=170802845 + 77)
+        line["error_vs_oracle"] = error_vs_oracle(dd, ctx, dev, q, orows)
+    if args.section == "all" and world == 1:
+        mid = q["mid"]
+        for key in ("fields", "pxy"):
+            q[key] = None
+        torch.cuda.empty_cache()
+        line["stream"], line["gemm"] = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, mid=mid,
+                                                        wl=q["wl"], orows=orows)
+        dd.dd_unload_mesh(ctx, mid)
+        g140 = query_step(dd, ctx, dev, stream, flush, args, rank, world, local_rank, "grid140", pk, pk_kind)
+        dd.dd_unload_mesh(ctx, g140["mid"])
+        line["grid140"] = {kk: g140["line"][kk] for kk in ("value", "ms_per_step", "config", "paths_per_s",
+                                                           "paths_ok_frac", "max_path_pts", "roofline",
+                                                           "roofline_fields", "roofline_walk", "kernels", "e2e",
+                                                           "clocks", "recompute_over_tile") if kk in g140["line"]}
+        del g140
+        torch.cuda.empty_cache()
+        line["batch"] = batch_section(dd, ctx, dev, stream, flush, args)
+        line["serve"] = serve_section(dd, ctx, args, n_domains=5, seconds=3.0)
+        line["census"] = census_section(dd, ctx, dev)
+    dd.dd_destroy(ctx)
+    return line
+
+
+def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10, mid=None, wl=None, orows=None):
+    """grid450 (n = 192,360, k = 3,936; P = 3.0 GB FP32, far above L2); the
+    mesh of the headline step when given (mid, wl), else loaded and solved here.
 
     stream: single-target KL+TV sweeps; the streaming kernel reads P once per
       target, achieved GB/s = (4 n k_pad + 8 n) bytes / event-timed dd_distance.
     gemm: 1,024 targets, KL through the split-BF16 tcgen05 GEMM; algorithmic
       2 n k T flop (three BF16 products issued), against the FP32 CUDA-core
-      path for the same KL fields."""
+      path for the same KL fields.
+    other_f_divergences, sparse: one target per call, one pass each."""
     import torch
     from synthetic import workloads
     T_big = 1024
-    wl = workloads.grid450(T=T_big)
-    idx, off = wl.mesh.loop_arrays()
-    mid = dd.dd_load_mesh(ctx, wl.mesh.xy, wl.mesh.tri, idx, off)
-    t0 = time.perf_counter()
-    iters, resid = dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
-    pre = time.perf_counter() - t0
+    own = mid is None
+    iters = resid = pre = None
+    if own:
+        wl = workloads.grid450(T=T_big)
+        idx, off = wl.mesh.loop_arrays()
+        mid = dd.dd_load_mesh(ctx, wl.mesh.xy, wl.mesh.tri, idx, off)
+        t0 = time.perf_counter()
+        iters, resid = dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+        pre = time.perf_counter() - t0
     info = dd.dd_mesh_info(ctx, mid)
     n_v, k, k_pad = info["n_v"], info["k"], info["k_pad"]
 
@@ -452,7 +590,8 @@ def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10):
                   "ms_per_field_pair": round(med, 4), "fields_per_s": round(2 / (med / 1e3), 1),
                   "traffic": STREAM_TRAFFIC_BYTES, "algorithmic_bytes": int(nbytes),
                   "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch, this workload",
-                  "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(pre, 2)}}
+                  "preproc": {"pcg_iters": iters, "resid": resid, "seconds": round(pre, 2)} if own else
+                  "the headline step's kernel"}
 
     outk = torch.empty((1, T_big, n_v), dtype=torch.float32, device=dev)
     dd.dd_distance(ctx, mid, tl, dd.DD_F_KL, dd.DD_PREC_BF16X3, outk)   # builds the BF16 split of P once
@@ -484,72 +623,120 @@ def grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 10):
         fdiv_sec["families"][name] = {"ms": round(ms_f, 4), "achieved": round(gbs, 1),
                                       "frac": round(gbs / pk.get("hbm_gbs", 6672.5), 4)}
     stream_sec["other_f_divergences"] = fdiv_sec
-    stream_sec["sparse"] = sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, pk_kind, reps)
-    stream_sec["sparse"]["speedup_vs_dense"] = round(med / stream_sec["sparse"]["ms_per_field_pair"], 2)
-    dd.dd_unload_mesh(ctx, mid)
+    klt_ms = fdiv_sec["families"]["kl_reverse"]["ms"]
+    stream_sec["sparse"] = sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, pk_kind, reps,
+                                             dense_ms=med, dense_klt_ms=klt_ms, orows=orows)
+    if own:
+        dd.dd_unload_mesh(ctx, mid)
     return stream_sec, gemm_sec
 
 
-def sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, pk_kind, reps):
-    """Sparse KL+TV of one target (Section V): the target row's entries below
-    max/sqrt(n) merged into one bin; every row of P is read only at the
-    4-column blocks holding the target's kept columns.  Algorithmic bytes of a
-    launch = 16 B x n x (the target's listed blocks) + 8 B x n (row totals) +
-    the two output fields; the listed blocks are counted on the host from the
-    exported kernel.  Accuracy against the dense FP32 fields of the same
-    targets."""
+def sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, pk_kind, reps, dense_ms=None,
+                      dense_klt_ms=None, orows=None):
+    """Sparse fields of Section V (each row's entries below 1/sqrt(n) of its
+    maximum eliminated), one target per call.  KL~ and TV~ read only the CSR
+    copy of the sparsified P (csr_field_kernel): algorithmic bytes of a call =
+    6 B per kept entry (value + 16-bit column) + 8 B per row offset + the two
+    output fields.  KLT~ reads the dense rows at the target's kept 4-column
+    blocks (sparse_field_kernel): 16 B x n x listed blocks + the output.  With
+    oracle rows: the device's sparse fields against the oracle's sparse fields
+    (parity; rows with an entry within FP32 rounding of its threshold counted
+    apart) and against the oracle's dense fields (the approximation), FP64,
+    on the sampled rows."""
     import torch
+    from oracle import sparse as osp
     t0 = time.perf_counter()
-    kept, blocks = dd.dd_sparsify(ctx, mid)
+    kept, csr_bytes = dd.dd_sparsify(ctx, mid)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    P32 = np.empty((n_v, k), dtype=np.float32)
-    dd.dd_get_poisson_kernel(ctx, mid, P32)
-    theta = np.float32(1.0 / math.sqrt(n_v))
+    P = torch.empty((n_v, k), dtype=torch.float32, device=dev)
+    dd.dd_get_poisson_kernel(ctx, mid, P)
+    theta32 = torch.tensor(1.0 / math.sqrt(n_v), dtype=torch.float32, device=dev)
     use = tl[:reps]
 
     def listed_blocks(t):
-        row = np.zeros(k_pad, np.float32)
-        row[:k] = P32[t]
-        keep = (row >= theta * row.max()) & (row > 0)
-        return int(keep.reshape(-1, 4).any(axis=1).sum())
+        row = torch.zeros(k_pad, dtype=torch.float32, device=dev)
+        row[:k] = P[t]
+        keep = (row >= theta32 * row.max()) & (row > 0)
+        return int(keep.reshape(-1, 4).any(dim=1).sum().item())
 
-    out1 = torch.empty((2, 1, n_v), dtype=torch.float32, device=dev)
+    blocks = [listed_blocks(t) for t in use]
+    del P
+    out2 = torch.empty((2, 1, n_v), dtype=torch.float32, device=dev)
+    out1 = torch.empty((1, 1, n_v), dtype=torch.float32, device=dev)
     for t in use[:3]:
-        dd.dd_distance(ctx, mid, [t], 3, dd.DD_PREC_SPARSE, out1)
+        dd.dd_distance(ctx, mid, [t], 3, dd.DD_PREC_SPARSE, out2)
+        dd.dd_distance(ctx, mid, [t], dd.DD_F_KLT, dd.DD_PREC_SPARSE, out1)
     torch.cuda.synchronize()
-    ms, gbs = [], []
-    for t in use:
-        flush.fill_(0.5)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        dd.dd_distance(ctx, mid, [t], 3, dd.DD_PREC_SPARSE, out1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        m = e0.elapsed_time(e1)
-        ms.append(m)
-        gbs.append((16.0 * n_v * listed_blocks(t) + 8.0 * n_v + 8.0 * n_v) / (m / 1e3) / 1e9)
-    med, g = statistics.median(ms), statistics.median(gbs)
-    dense = torch.empty((3, 4, n_v), dtype=torch.float32, device=dev)
-    sp = torch.empty_like(dense)
-    dd.dd_distance(ctx, mid, tl[:4], 7, dd.DD_PREC_FP32, dense)
-    dd.dd_distance(ctx, mid, tl[:4], 7, dd.DD_PREC_SPARSE, sp)
-    torch.cuda.synchronize()
-    d, s_ = dense.cpu().numpy().astype(np.float64), sp.cpu().numpy().astype(np.float64)
-    rel = np.abs(s_ - d) / np.maximum(np.abs(d), 1e-2)
-    interior = d[2] < 40.0          # KLT is +inf (returned large) on boundary rows
-    return {"kernel": "sparse_field_kernel (+ stage_targets_kernel, sparse_stage_kernel)", "bound": "hbm",
-            "achieved": round(g, 1), "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-            "frac": round(g / pk.get("hbm_gbs", 6672.5), 4), "peak_source": pk_kind,
-            "ms_per_field_pair": round(med, 4), "fields_per_s": round(2 / (med / 1e3), 1),
-            "speedup_vs_dense": None, "sparsity": round(1.0 - kept / float(n_v * k), 4),
-            "listed_blocks_mean": round(float(np.mean([listed_blocks(t) for t in use])), 1),
-            "dense_blocks": int(k_pad // 4), "build_seconds": round(build_s, 3),
-            "vs_dense_fp32": {"kl_max_rel": float(np.max(rel[0])), "kl_median_rel": float(np.median(rel[0])),
-                              "tv_max_rel": float(np.max(rel[1])), "tv_median_rel": float(np.median(rel[1])),
-                              "klt_max_rel": float(np.max(rel[2][interior])),
-                              "klt_median_rel": float(np.median(rel[2][interior]))},
-            "traffic": None}
+
+    def timed(fn):
+        ms = []
+        for t in use:
+            flush.fill_(0.5)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(t)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    ms_csr = timed(lambda t: dd.dd_distance(ctx, mid, [t], 3, dd.DD_PREC_SPARSE, out2))
+    ms_klt = timed(lambda t: dd.dd_distance(ctx, mid, [t], dd.DD_F_KLT, dd.DD_PREC_SPARSE, out1))
+    csr_alg = 6.0 * kept + 8.0 * (n_v + 1) + 8.0 * n_v
+    g_csr = statistics.median([csr_alg / (m / 1e3) / 1e9 for m in ms_csr])
+    g_klt = statistics.median([(16.0 * n_v * b + 4.0 * n_v) / (m / 1e3) / 1e9 for m, b in zip(ms_klt, blocks)])
+    hbm = pk.get("hbm_gbs", 6672.5)
+    res = {"reading": "Section V: each row's entries below max/sqrt(n) eliminated; KL~ over the field row's kept "
+                      "entries, KLT~ over the target row's kept columns, TV~ between the sparsified rows",
+           "sparsity": round(1.0 - kept / float(n_v * k), 4), "csr_bytes": int(csr_bytes),
+           "dense_bytes": int(4 * n_v * k_pad), "build_seconds": round(build_s, 3),
+           "kl_tv": {"kernel": "csr_field_kernel (+ stage_targets_kernel, sparse_stage_kernel)", "bound": "hbm",
+                     "ms_per_field_pair": round(statistics.median(ms_csr), 4), "achieved": round(g_csr, 1),
+                     "peak": hbm, "unit": "GB/s", "frac": round(g_csr / hbm, 4), "peak_source": pk_kind,
+                     "algorithmic_bytes": int(csr_alg),
+                     "speedup_vs_dense": round(dense_ms / statistics.median(ms_csr), 2) if dense_ms else None},
+           "klt": {"kernel": "sparse_field_kernel (+ stage_targets_kernel, sparse_stage_kernel)", "bound": "hbm",
+                   "ms_per_field": round(statistics.median(ms_klt), 4), "achieved": round(g_klt, 1), "peak": hbm,
+                   "unit": "GB/s", "frac": round(g_klt / hbm, 4), "listed_blocks_mean": round(float(np.mean(blocks)), 1),
+                   "dense_blocks": int(k_pad // 4),
+                   "speedup_vs_dense_klt": round(dense_klt_ms / statistics.median(ms_klt), 2) if dense_klt_ms else None},
+           "traffic": None}
+    if orows is not None:
+        nt = 16
+        tg = [int(t) for t in orows.targets[:nt]]
+        out3 = torch.empty((3, nt, n_v), dtype=torch.float32, device=dev)
+        dd.dd_distance(ctx, mid, tg, dd.DD_F_KL | dd.DD_F_TV | dd.DD_F_KLT, dd.DD_PREC_SPARSE, out3)
+        g = out3[:, :, torch.as_tensor(orows.rows, device=dev)].cpu().numpy()
+        del out3
+        theta = osp.default_theta(n_v)
+        thr = theta * orows.Px.max(axis=1, keepdims=True)
+        border_rows = (np.abs(orows.Px - thr) <= 8.0 * 2.0 ** -24 * thr).any(axis=1)
+        par = {"kl": [], "tv": [], "klt": []}
+        apx = {"kl": [], "tv": [], "klt": []}
+        from oracle.divergence import kl_field_fast, tv_field
+        from oracle.fdiv import kl_reverse_field
+        R = len(orows.rows)
+        for a in range(nt):
+            Ps = np.vstack([orows.Px, orows.Pt[a][None, :]])
+            refs = {"kl": osp.sparse_kl_field(Ps, R, theta)[:R], "tv": osp.sparse_tv_field(Ps, R, theta)[:R],
+                    "klt": osp.sparse_klt_field(Ps, R, theta)[:R]}
+            dense = {"kl": kl_field_fast(orows.Px, orows.Pt[a]), "tv": tv_field(orows.Px, orows.Pt[a]),
+                     "klt": kl_reverse_field(orows.Px, orows.Pt[a])}
+            for f, i in (("kl", 0), ("tv", 1), ("klt", 2)):
+                ok = ~border_rows & np.isfinite(refs[f])
+                par[f].append(np.abs(g[i, a][ok] - refs[f][ok]) / np.maximum(np.abs(refs[f][ok]), 1e-2))
+                fin = np.isfinite(dense[f])
+                apx[f].append(np.abs(g[i, a][fin] - dense[f][fin]) / np.maximum(np.abs(dense[f][fin]), 1e-2))
+        res["parity_vs_oracle_sparse"] = {f: {"max": float(np.max(np.concatenate(v))),
+                                              "median": float(np.median(np.concatenate(v))), "tol": 1e-5}
+                                          for f, v in par.items()}
+        res["parity_vs_oracle_sparse"]["rows_left_out"] = int(border_rows.sum())
+        res["approximation_vs_oracle_dense"] = {f: {"max": float(np.max(np.concatenate(v))),
+                                                    "median": float(np.median(np.concatenate(v)))}
+                                                for f, v in apx.items()}
+        res["error_sample"] = "%d sampled rows x %d targets, FP64 oracle rows, relative with floor 1e-2" % (R, nt)
+    return res
 
 
 def mid_section(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 8):
@@ -852,70 +1039,136 @@ def serve_section(dd, ctx, args, n_domains: int, seconds: float, rate: float = 2
             "preproc_s": round(pre, 2)}
 
 
-class OracleStep:
-    """The FP64 oracle on a bounded sample of the grid140 step (fields/s)."""
-
-    def __init__(self):
-        from oracle.poisson import PoissonOracle
-        from oracle.trace import Tracer
-        from synthetic import workloads
-        self.wl = workloads.grid140(T=T_BATCH, S=S_PER_TARGET)
-        po = PoissonOracle(self.wl.mesh.xy, self.wl.mesh.tri, self.wl.mesh.loops)
-        self.P = po.full()
-        self.tracer = Tracer(self.wl.mesh.xy, self.wl.mesh.tri)
-
-    def run(self, a: int, sample_paths: int):
-        """KL+TV of target a over all vertices plus `sample_paths` of its 256 paths.
-
-        Returns the seconds one real step-target (2 fields + 256 paths) would take."""
-        from oracle.divergence import kl_field_fast, tv_field
-        P = self.P
-        a = a % len(self.wl.targets)
-        t = int(self.wl.targets[a])
-        c0 = time.perf_counter()
-        kl = kl_field_fast(P, P[t])
-        tv_field(P, P[t])
-        c1 = time.perf_counter()
-        for q in self.wl.sources[a][:sample_paths]:
-            self.tracer.trace(kl, int(q), t, max_pts=MAX_PTS)
-        c2 = time.perf_counter()
-        return (c1 - c0) + (c2 - c1) / sample_paths * S_PER_TARGET
+# ---------------------------------------------------------------- the oracle on the host cores
+# The oracle's FP64 Poisson kernel of the workload lives in shared memory,
+# filled by spawned workers (each factorises -L_II itself and solves a block of
+# columns, Eq. 33); the same workers then time the oracle's fields (Eq. 34-35
+# over every vertex) and paths, one task per core at a time.  Spawned, not
+# forked: the parent has used CUDA by then.
+_HOST = {}
 
 
-# The oracle on every host core: one process per core (spawned, so that a pool
-# started after CUDA work does not inherit the parent's GPU context), each with
-# its own OracleStep; a task is one target of the sample, timed in its worker.
-_ORACLE = None
+def _host_init(name, shm_name, n, k):
+    from multiprocessing import shared_memory
+    w = WORKLOADS[name]
+    wl = make_workload(name, w["T"], w["S"])
+    shm = shared_memory.SharedMemory(name=shm_name)
+    _HOST.update(wl=wl, shm=shm, P=np.ndarray((n, k), dtype=np.float64, buffer=shm.buf), po=None, tracer=None)
 
 
-def _oracle_init():
-    global _ORACLE
-    _ORACLE = OracleStep()
+def _host_columns(cols):
+    from oracle.poisson import PoissonOracle
+    if _HOST["po"] is None:
+        wl = _HOST["wl"]
+        _HOST["po"] = PoissonOracle(wl.mesh.xy, wl.mesh.tri, wl.mesh.loops)
+    po = _HOST["po"]
+    c0, c1 = int(cols[0]), int(cols[-1]) + 1
+    X = po.lu.solve(po.L_IB[:, c0:c1].toarray())       # -L_II X = L_IB
+    P = _HOST["P"]
+    P[po.I, c0:c1] = X
+    P[np.asarray(po.B)[c0:c1], np.arange(c0, c1)] = 1.0
+    return c1 - c0
 
 
-def _oracle_task(args):
-    a, sample_paths = args
-    return _ORACLE.run(a, sample_paths)
+def _host_tracer():
+    from oracle.trace import Tracer
+    if _HOST["tracer"] is None:
+        wl = _HOST["wl"]
+        _HOST["tracer"] = Tracer(wl.mesh.xy, wl.mesh.tri)
+    return _HOST["tracer"]
 
 
-def oracle_pool(cores: int):
-    import multiprocessing
-    from concurrent.futures import ProcessPoolExecutor
-    # one thread per worker: the workers inherit this environment when spawned
-    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for k in saved:
-        os.environ[k] = "1"
-    try:
-        pool = ProcessPoolExecutor(max_workers=cores, mp_context=multiprocessing.get_context("spawn"),
-                                   initializer=_oracle_init)
-        list(pool.map(_oracle_task, [(w, 1) for w in range(cores)]))      # every worker built its kernel
-    finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-    return pool
+def _host_fields(t, r0, r1, keep=False, chunk=4096):
+    """KL and TV of target t over rows [r0, r1), in row chunks (oracle.divergence)."""
+    from oracle.divergence import kl_field_fast, tv_field
+    P = _HOST["P"]
+    pt = np.array(P[t])
+    kl = np.empty(r1 - r0) if keep else None
+    for a in range(r0, r1, chunk):
+        b = min(r1, a + chunk)
+        f = kl_field_fast(P[a:b], pt)
+        tv_field(P[a:b], pt)
+        if keep:
+            kl[a - r0:b - r0] = f
+    return kl
+
+
+def _host_full(args):
+    """One target's KL+TV over every vertex and one path traced on the KL field."""
+    t, q = args
+    tr = _host_tracer()
+    n = _HOST["P"].shape[0]
+    c0 = time.perf_counter()
+    kl = _host_fields(int(t), 0, n, keep=True)
+    c1 = time.perf_counter()
+    path, st = tr.trace(kl, int(q), int(t), max_pts=WORKLOADS[_HOST["wl"].name]["max_pts"])
+    c2 = time.perf_counter()
+    return c1 - c0, c2 - c1, int(st), len(path)
+
+
+def _host_path_only(args):
+    """The paper's CPU scheme (Section V, Table I): one path, KL evaluated only
+    at the vertices the walk reads."""
+    from oracle.trace import PathOnlyField
+    t, q = args
+    tr = _host_tracer()
+    c0 = time.perf_counter()
+    f = PathOnlyField(_HOST["P"], int(t), "kl")
+    path, st = tr.trace(f, int(q), int(t), max_pts=WORKLOADS[_HOST["wl"].name]["max_pts"])
+    return time.perf_counter() - c0, f.evaluated, int(st), len(path)
+
+
+def _host_ref_task(args):
+    """One core's share of a reference-arm step: strip j of n_strips of one
+    target's KL+TV field, and one path by the path-only scheme."""
+    t, j, n_strips, q = args
+    n = _HOST["P"].shape[0]
+    c0 = time.perf_counter()
+    _host_fields(int(t), j * n // n_strips, (j + 1) * n // n_strips)
+    c1 = time.perf_counter()
+    s, ev, st, npts = _host_path_only((t, q))
+    return c1 - c0, s, ev, st
+
+
+class HostOracle:
+    """The oracle's FP64 P of a workload in shared memory plus a spawned pool
+    of one single-threaded worker per host core."""
+
+    def __init__(self, name: str, cores: int):
+        import multiprocessing
+        from concurrent.futures import ProcessPoolExecutor
+        from multiprocessing import shared_memory
+        from oracle.topology import split_boundary
+        w = WORKLOADS[name]
+        wl = make_workload(name, w["T"], w["S"])
+        n = wl.mesh.n_v
+        k = len(split_boundary(n, wl.mesh.tri, wl.mesh.loops)[0])
+        self.name, self.n, self.k, self.cores = name, n, k, cores
+        self.shm = shared_memory.SharedMemory(create=True, size=n * k * 8)
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = "1"
+        try:
+            self.pool = ProcessPoolExecutor(max_workers=cores, mp_context=multiprocessing.get_context("spawn"),
+                                            initializer=_host_init, initargs=(name, self.shm.name, n, k))
+            t0 = time.perf_counter()
+            blocks = [b for b in np.array_split(np.arange(k), 2 * cores) if len(b)]
+            list(self.pool.map(_host_columns, blocks))
+            self.kernel_s = time.perf_counter() - t0
+        finally:
+            for v, val in saved.items():
+                if val is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = val
+
+    def map(self, fn, tasks):
+        return list(self.pool.map(fn, tasks))
+
+    def close(self):
+        self.pool.shutdown()
+        self.shm.close()
+        self.shm.unlink()
 
 
 def host_cores() -> int:
@@ -925,20 +1178,81 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_baseline(sample_paths: int = 16):
+def cpu_baseline(name: str = HEADLINE):
     """fields/s of the oracle with every host core busy: each core takes one
-    grid140 target (KL+TV over all n plus sample_paths of its 256 paths,
-    scaled to the full per-target work)."""
+    target of the step's first batch and computes its KL+TV over every vertex
+    (then traces one path on the KL field); beside it the paper's CPU scheme,
+    one path per core with KL evaluated only at the vertices the walk reads."""
     t0 = time.perf_counter()
     cores = host_cores()
-    pool = oracle_pool(cores)
-    per_target = list(pool.map(_oracle_task, [(cores + w, sample_paths) for w in range(cores)]))
-    pool.shutdown()
-    return {"value": round(cores * 2.0 / statistics.mean(per_target), 4), "unit": UNIT, "cores": cores,
-            "kind": "oracle",
-            "sample": f"{cores} targets of grid140, one per core at once: KL+TV over all n plus {sample_paths} "
-                      f"of {S_PER_TARGET} paths each, scaled to 2 fields + {S_PER_TARGET} paths per target",
+    ho = HostOracle(name, cores)
+    try:
+        wl, batches = workload_batches(0, name)
+        tg, sr = batches[0]
+        full = ho.map(_host_full, [(int(tg[w]), int(sr[w][0])) for w in range(cores)])
+        po = ho.map(_host_path_only, [(int(tg[w]), int(sr[w][1])) for w in range(cores)])
+    finally:
+        ho.close()
+    field_s = statistics.mean(r[0] for r in full)
+    return {"value": round(cores * 2.0 / field_s, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} targets of {name}'s first batch, one per core at once: KL+TV over all n = {ho.n} "
+                      f"vertices each (FP64, from the oracle's P in shared memory, computed in "
+                      f"{ho.kernel_s:.1f} s and not timed), then one path traced on the KL field",
+            "full_field_trace_ms_per_path": round(1e3 * statistics.mean(r[1] for r in full), 2),
+            "path_only": {"scheme": "Section V, Table I: KL only at the vertices the walk reads",
+                          "ms_per_path": round(1e3 * statistics.mean(r[0] for r in po), 2),
+                          "vertices_evaluated_per_path": round(float(np.mean([r[1] for r in po])), 1),
+                          "points_per_path": round(float(np.mean([r[3] for r in po])), 1),
+                          "ok_share": round(float(np.mean([r[2] == 0 for r in po])), 4)},
             "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def reference_arm(args):
+    """The FP64 oracle as the reference arm, on every host core: per step each
+    core takes one target of the step's batch (the GPU arm's targets, in
+    order) and computes one eighth of its KL+TV field (rows j n/8 .. (j+1) n/8,
+    j = step mod 8) and one path by the paper's path-only scheme.  The step's
+    time is its wall time; fields/s counts each eighth as 1/8 field."""
+    t0 = time.perf_counter()
+    cores = host_cores()
+    name = args.workload
+    n_strips = 8
+    ho = HostOracle(name, cores)
+    try:
+        wl, batches = workload_batches(0, name)
+
+        def tasks(i):
+            tg, sr = batches[i % len(batches)]
+            base = (i // len(batches)) * cores
+            return [(int(tg[(base + w) % len(tg)]), i % n_strips, n_strips, int(sr[(base + w) % len(tg)][0]))
+                    for w in range(cores)]
+
+        for i in range(args.warmup):
+            ho.map(_host_ref_task, tasks(i))
+        walls, evals = [], []
+        for i in range(args.steps):
+            c0 = time.perf_counter()
+            res = ho.map(_host_ref_task, tasks(args.warmup + i))
+            walls.append(time.perf_counter() - c0)
+            evals.extend(r[2] for r in res)
+    finally:
+        ho.close()
+    fields_per_step = cores * 2.0 / n_strips
+    v = fields_per_step * args.steps / sum(walls)
+    w = WORKLOADS[name]
+    return {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * sum(walls) / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w["desc"] % (ho.n, ho.k, w["T"], w["T"], w["S"]),
+                       "sample": f"per step {cores} of the step's targets (one per core): 1/{n_strips} of the rows "
+                                 "of each KL+TV field and one path by the path-only scheme"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": round(v, 4),
+                             "sample": f"per step {cores} targets at once (one per core): KL+TV over 1/{n_strips} "
+                                       "of the vertices + one path-only trace each; ms_per_step is the step's wall "
+                                       "time",
+                             "vertices_evaluated_per_path": round(float(np.mean(evals)), 1)},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "preproc_s": round(ho.kernel_s, 1), "seconds": round(time.perf_counter() - t0, 1)}
 
 
 def main():
@@ -947,12 +1261,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=HEADLINE,
+                    help="query-step workload of the reference arm and the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-stream", dest="stream", action="store_false",
-                    help="skip the grid450 measurements (single-target HBM stream, BF16 tensor-core KL)")
-    ap.add_argument("--section", choices=["all", "step", "grid450", "batch", "serve", "census", "mid"], default="all",
-                    help="step: only the grid140 query step; grid450 / batch / serve / census / mid: only that part "
-                         "(mid: a grid300 case small enough for full ncu captures)")
+    ap.add_argument("--no-oracle-errors", dest="oracle_errors", action="store_false",
+                    help="skip the error of the step's results against the FP64 oracle")
+    ap.add_argument("--section", choices=["all", "step", "grid140", "grid450", "batch", "serve", "census", "mid"],
+                    default="all",
+                    help="step: only the grid450 query step (with its split-BF16 form and oracle errors); grid140, "
+                         "grid450 (single-target, sparse, other-divergence and GEMM passes), batch, serve, census, "
+                         "mid (a grid300 case small enough for full ncu captures): only that part")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -962,30 +1280,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        t0 = time.perf_counter()
-        cores = host_cores()
-        pool = oracle_pool(cores)
-        for i in range(args.warmup):
-            list(pool.map(_oracle_task, [(i * cores + w, 2) for w in range(cores)]))
-        # per step every core takes one target; a step's time = the mean scaled per-target time
-        step_s = []
-        for i in range(args.steps):
-            res = list(pool.map(_oracle_task, [((args.warmup + i) * cores + w, 4) for w in range(cores)]))
-            step_s.append(statistics.mean(res))
-        pool.shutdown()
-        v = cores * 2.0 * args.steps / sum(step_s)
-        line = {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": round(1e3 * sum(step_s) / args.steps, 1),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "impl": "reference",
-                "config": {"workload": "grid140 (as --impl ours); per step one target per host core: KL+TV over "
-                                       "all n and 4 of its 256 paths, scaled to the full per-target work"},
-                "cpu_baseline": {"kind": "oracle", "cores": cores, "value": round(v, 4),
-                                 "sample": f"per step {cores} targets at once (one per core): KL+TV over all n + "
-                                           "4 of 256 paths each, scaled"},
-                "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-                "seconds": round(time.perf_counter() - t0, 1)}
-        print(json.dumps(line))
+        print(json.dumps(reference_arm(args)))
         return
 
     if world > 1:
@@ -996,7 +1291,7 @@ def main():
     line = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1 and args.section in ("all", "step"):
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -64,7 +64,11 @@ class Tracer:
         return 0 if row[0] == v else (1 if row[1] == v else 2)
 
     def trace(self, f, q: int, target: int, max_pts: int = 1 << 30, max_steps: int = None):
-        f = np.asarray(f, dtype=np.float64)
+        """Path from q to target on the field f: an array over all vertices, or
+        an object indexed by vertex id (e.g. a PathOnlyField, which evaluates
+        the divergence only at the vertices the walk reads)."""
+        if not isinstance(f, PathOnlyField):
+            f = np.asarray(f, dtype=np.float64)
         if max_steps is None:
             max_steps = 4 * len(self.tri)
         eps = self.eps
@@ -208,3 +212,35 @@ class Tracer:
             if not push(l1 * xy[e1] + l2 * xy[e2]):
                 return np.asarray(path), TRUNCATED
             state = ("e", t2, exit_local, l1, l2)
+
+
+class PathOnlyField:
+    """The field of one target evaluated only where the walk reads it: the
+    paper's CPU scheme (Section V, Table I), which computes KL or TV only at
+    the vertices relevant to the path, from the precomputed Poisson kernel.
+    f[x] is Eq. 35 (KL, weighted by row x, 0 log 0 = 0) or Eq. 34 (TV) for
+    rows x and t of P, computed on first use and kept."""
+
+    def __init__(self, P, t: int, kind: str = "kl"):
+        self.P = P
+        self.Pt = np.asarray(P[t], dtype=np.float64)
+        self.kind = kind
+        self.cache = {}
+
+    def __getitem__(self, x):
+        x = int(x)
+        v = self.cache.get(x)
+        if v is None:
+            px = np.asarray(self.P[x], dtype=np.float64)
+            if self.kind == "kl":
+                nz = px > 0.0
+                with np.errstate(divide="ignore"):
+                    v = float(np.sum(px[nz] * np.log(px[nz] / self.Pt[nz])))
+            else:
+                v = float(np.sum(np.abs(px - self.Pt)))
+            self.cache[x] = v
+        return v
+
+    @property
+    def evaluated(self) -> int:
+        return len(self.cache)

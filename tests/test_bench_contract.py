@@ -1,8 +1,9 @@
 """bench.py's step measurement on the CPU with a stand-in library and
 stand-in CUDA events: the JSON line carries the contract's keys with
 consistent values, the dominant kernel's roofline is chosen from the live
-per-kernel times, and a timed region whose clocks show a slowdown is
-measured once more.  (The numbers are the stand-ins'; the GPU run gives the
+per-kernel times (the tile kernel against the FP32 issue rate of the
+device's SM count, the walk against its latency chain), and a timed region
+whose clocks show a slowdown is measured once more.  (The numbers are the stand-ins'; the GPU run gives the
 real ones.)"""
 import json
 import os
@@ -59,6 +60,7 @@ def _fake_dd(n_v, k, kernel_ms):
 
     m.dd_query = query
     m.dd_distance = distance
+    m.dd_unload_mesh = lambda ctx, mid: None
     m.dd_trace_fields = lambda ctx, mid, f, tg, sr, max_pts, xy, ln, st: None
     m.dd_kernel_timing = kernel_timing
     return m
@@ -88,67 +90,68 @@ def stand_ins(monkeypatch):
         monkeypatch.setattr(bench.ClockSampler, "start", lambda self: None)
         monkeypatch.setattr(bench.ClockSampler, "stop", lambda self: records.pop(0) if records else
                             {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3})
-        monkeypatch.setattr(bench, "workload_batches", _small_batches)
+        monkeypatch.setitem(bench.WORKLOADS, bench.HEADLINE, dict(bench.WORKLOADS[bench.HEADLINE], **SMALL))
+        monkeypatch.setattr(bench, "sm_count", lambda dev: 148)
         return fake
     return install
 
 
-def _small_batches(rank):
-    from synthetic import workloads
-    wl = workloads.grid140(T=bench.T_BATCH, S=bench.S_PER_TARGET)
-    return wl, [(wl.targets, wl.sources)] * 2
+# the headline workload's mesh with fewer targets and sources per step (host memory)
+SMALL = {"T": 64, "S": 4, "max_pts": 256}
 
 
 def _args(steps=3):
-    return types.SimpleNamespace(steps=steps, warmup=3, section="step", stream=False, no_cpu_baseline=True,
-                                 gpus=1, impl="ours")
+    return types.SimpleNamespace(steps=steps, warmup=3, section="step", oracle_errors=False, no_cpu_baseline=True,
+                                 gpus=1, impl="ours", workload=bench.HEADLINE)
 
 
-KERNELS = {"stage_targets_kernel": (3, 0.04), "field_tile_kernel": (3, 0.67), "fix_kl_kernel": (3, 0.2),
+KERNELS = {"stage_targets_kernel": (3, 0.04), "field_tile_kernel": (3, 6.7), "fix_kl_kernel": (3, 0.6),
            "rates_kernel": (3, 0.075), "vertex_decision_kernel": (3, 0.17), "trace_kernel": (3, 1.0)}
 GOOD = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+N_V, K = 192360, 3936
 
 
 def test_step_line_keeps_the_contract(stand_ins):
-    stand_ins(18174, 1028, KERNELS, [GOOD])
+    stand_ins(N_V, K, KERNELS, [GOOD])
     line = bench.run_ours(_args(), 0, 1, 0)
     json.dumps(line)
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks",
                 "kernels"):
         assert key in line, key
+    T, S = SMALL["T"], SMALL["S"]
     assert line["metric"] == bench.METRIC and line["unit"] == "fields/s" and line["n_gpus"] == 1
     assert line["steps"] == 3 and line["warmup"] == 3 and line["higher_is_better"] is True
-    assert "workload" in line["config"] and line["vs_baseline"] is None
-    assert abs(line["value"] - 2 * 64 / (line["ms_per_step"] / 1e3)) <= 1e-3 * line["value"] + 1.0
+    assert line["config"]["workload"].startswith("grid450") and line["vs_baseline"] is None
+    assert abs(line["value"] - 2 * T / (line["ms_per_step"] / 1e3)) <= 1e-3 * line["value"] + 1.0
     r = line["roofline"]
-    assert r["kernel"] == "trace_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert r["peak"] == bench.peaks()[0]["hbm_gbs"] and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
-    assert r["traffic"] == bench.WALK_TRAFFIC_BYTES
-    assert r["algorithmic_bytes"] == bench.WALK_BYTES_PER_POINT * 64 * 256 * 12
-    f = line["roofline_fields"]
-    assert f["kernel"] == "field_tile_kernel" and f["bound"] == "alu" and f["traffic"] == bench.TILE_TRAFFIC_BYTES
-    assert f["algorithmic_fp32_ops"] == 4.0 * 18174 * 1028 * 64
-    assert abs(f["ms_per_launch"] - 0.67 / 3) < 1e-4
-    assert line["gpu_launches"] == 18 and line["roofline_walk"] is None
+    assert r["kernel"] == "field_tile_kernel" and r["bound"] == "alu" and r["traffic"] is None
+    assert r["algorithmic_fp32_ops"] == 4.0 * N_V * K * T
+    assert abs(r["ms_per_launch"] - 6.7 / 3) < 1e-4
+    assert abs(r["peak"] - 148 * 128 * 2070e6 / 1e12) < 1e-3            # the device's SM count
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
+    w = line["roofline_walk"]
+    assert w["kernel"] == "trace_kernel" and w["bound"] == "latency" and w["longest_path_points"] == 12
+    assert line["roofline_fields"] is None and line["gpu_launches"] == 18
+    assert abs(line["recompute_over_tile"] - 0.6 / 6.7) < 1e-3
     e = line["e2e"]
-    assert e["unit"] == "fields/s" and e["h2d_bytes_per_step"] == 64 * 4 + 64 * 256 * 4
-    assert e["d2h_bytes_per_step"] == 2 * 64 * 18174 * 4 + 64 * 256 * 8 + 64 * 256 * 12 * 8
+    assert e["unit"] == "fields/s" and e["h2d_bytes_per_step"] == T * 4 + T * S * 4
+    assert e["d2h_bytes_per_step"] == 2 * T * N_V * 4 + T * S * 8 + T * S * 12 * 8
     assert "remeasured" not in line and line["clocks"] == GOOD
     assert line["step_bf16x3"]["tv_identical"] is True
 
 
-def test_tile_named_when_it_dominates(stand_ins):
-    k = dict(KERNELS, field_tile_kernel=(3, 1.5))
-    stand_ins(18174, 1028, k, [GOOD])
+def test_walk_named_when_it_dominates(stand_ins):
+    k = dict(KERNELS, trace_kernel=(3, 9.0))
+    stand_ins(N_V, K, k, [GOOD])
     line = bench.run_ours(_args(), 0, 1, 0)
-    assert line["roofline"]["kernel"] == "field_tile_kernel" and line["roofline"]["bound"] == "alu"
-    assert line["roofline_walk"]["kernel"] == "trace_kernel" and line["roofline_fields"] is None
+    assert line["roofline"]["kernel"] == "trace_kernel" and line["roofline"]["bound"] == "latency"
+    assert line["roofline_fields"]["kernel"] == "field_tile_kernel" and line["roofline_walk"] is None
 
 
 def test_throttled_region_is_measured_again(stand_ins):
     hot = {"sm_mhz": 1500.0, "sm_max_mhz": 2070.0, "reasons": ["hw_thermal_slowdown"], "samples": 3}
-    stand_ins(18174, 1028, KERNELS, [hot, GOOD])
+    stand_ins(N_V, K, KERNELS, [hot, GOOD])
     line = bench.run_ours(_args(), 0, 1, 0)
     assert line["remeasured"]["first"]["reasons"] == ["hw_thermal_slowdown"]
     assert line["clocks"] == GOOD
@@ -161,12 +164,14 @@ def test_reference_arm_line():
     cpu_baseline and an e2e that moves no bytes."""
     import subprocess
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=root)
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "3", "--workload", "grid140"], capture_output=True, text=True, timeout=600,
+                       cwd=root)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
-    assert line["higher_is_better"] is True and line["value"] > 0 and line["steps"] == 1
+    assert line["higher_is_better"] is True and line["value"] > 0 and line["steps"] == 2
+    assert line["config"]["workload"].startswith("grid140") and line["ms_per_step"] > 0
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,

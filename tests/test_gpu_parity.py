@@ -167,7 +167,7 @@ def test_trace_parity(env, name, f):
     tr = Tracer(mesh.xy, mesh.tri)
     h = mean_edge(mesh)
     fbit = dd.DD_F_KL if f == "kl" else dd.DD_F_TV
-    n_t = min(len(wl.targets), 2)
+    n_t = len(wl.targets)                     # every target of the case (grid140: 8 x 32 paths)
     for a in range(n_t):
         t = int(wl.targets[a])
         srcs = wl.sources[a]

@@ -5,6 +5,9 @@ path between q and t is the image under the inverse Moebius map of the radial
 segment), the Equivalence Theorem A6 (KL paths agree with paths of the
 Dirichlet Green's function on a simply-connected domain), radial lines for a
 centred target (Theorem A5), and hand-built fields that force each status.
+The paper's CPU scheme (Table I: divergences evaluated only at the vertices
+the path needs) traces the same paths as the full field, evaluating a small
+share of the vertices.
 """
 import math
 
@@ -15,7 +18,7 @@ from oracle.divergence import kl_field_fast, tv_field
 from oracle.greens import dirichlet_green_column
 from oracle.hausdorff import hausdorff
 from oracle.poisson import PoissonOracle
-from oracle.trace import OK, STEP_LIMIT, STUCK_LOCAL_MIN, TRUNCATED, Tracer
+from oracle.trace import OK, STEP_LIMIT, STUCK_LOCAL_MIN, TRUNCATED, PathOnlyField, Tracer
 from synthetic import workloads
 from synthetic.meshes import disk_rings, grid_obstacles
 
@@ -58,6 +61,21 @@ def test_disk_paths_are_hyperbolic_geodesics(disk_setup):
             assert st == OK
             assert np.allclose(path[0], wl.mesh.xy[q]) and np.allclose(path[-1], wl.mesh.xy[t])
             assert hausdorff(path, geodesic(wl.mesh.xy[q], wl.mesh.xy[t]), h / 20) <= 0.5 * h
+
+
+def test_path_only_scheme_traces_the_same_paths(disk_setup):
+    wl, po, P, t, tr, h = disk_setup
+    for kind, full in (("kl", kl_field_fast(P, P[t])), ("tv", tv_field(P, P[t]))):
+        for q in wl.sources[0][:8]:
+            lazy = PathOnlyField(P, t, kind)
+            p1, s1 = tr.trace(full, int(q), t)
+            p2, s2 = tr.trace(lazy, int(q), t)
+            assert s1 == s2 == OK
+            assert p1.shape == p2.shape and np.allclose(p1, p2, rtol=0, atol=1e-12)
+            ids = np.fromiter(lazy.cache.keys(), dtype=np.int64)
+            vals = np.fromiter(lazy.cache.values(), dtype=np.float64)
+            assert np.allclose(vals, full[ids], rtol=1e-12, atol=1e-14)
+            assert 0 < lazy.evaluated < wl.mesh.n_v // 4
 
 
 def test_equivalence_with_green_paths(disk_setup):
