@@ -434,8 +434,9 @@ class OracleRows:
         kl = np.stack([kl_field_fast(self.Px, pt) for pt in self.Pt])
         tv = np.stack([tv_field(self.Px, pt) for pt in self.Pt])
         klt = np.stack([kl_reverse_field(self.Px, pt) for pt in self.Pt])
-        with np.errstate(divide="ignore"):
-            sx = np.stack([(self.Px * np.abs(np.log(pt))[None, :]).sum(axis=1) for pt in self.Pt])
+        # a zero column (P[t,b] = 0) has P[x,b] = 0 on every interior row: its term is 0
+        lg = np.abs(np.log(np.maximum(self.Pt, 1e-300)))
+        sx = np.stack([(self.Px * lg[a][None, :]).sum(axis=1) for a in range(len(self.Pt))])
         return kl, tv, klt, sx
 
 
