@@ -11,6 +11,11 @@ domains are not available, so two seeded families stand in for them:
 * ``grid_obstacles``: the unit square cut into N x N cells of side h = 1/N,
   each cell split on its (i, j) -> (i+1, j+1) diagonal, with axis-aligned
   rectangular blocks of whole cells removed as obstacles (holes).
+* ``cell_domain``: any union of whole grid cells (a boolean cell mask), each
+  cell split on the same diagonal, its boundary loops traced along the cell
+  edges; ``serpentine`` builds a long winding corridor from it (a maze-like
+  domain whose harmonic measures decay by hundreds of orders of magnitude
+  along the corridor) and ``strip`` a single straight corridor.
 * ``convex_holes``: the unit disk minus a few convex regular polygons, meshed
   as the Delaunay triangulation of a jittered hexagonal point set plus points
   spaced along every boundary loop (a stand-in for the paper's "Convex Holes"
@@ -168,6 +173,88 @@ def grid_obstacles(N: int, blocks) -> Mesh:
         loops.append(np.asarray(l, dtype=np.int32))
     return Mesh(xy=xy, tri=tri, loops=loops, name=f"grid_N{N}_o{len(blocks)}",
                 meta={"N": N, "blocks": list(blocks), "ids": ids})
+
+
+def cell_domain(free: np.ndarray, h: float, name: str = "cells", meta=None) -> Mesh:
+    """Mesh of the union of the free cells free[j, i] (cell (i, j) spans
+    [i h, (i+1) h] x [j h, (j+1) h]), each split on its (i, j) -> (i+1, j+1)
+    diagonal.  Boundary loops follow the cell edges with the domain on their
+    left (outer loop counter-clockwise and first, holes clockwise).  Cells
+    that touch only at a corner would pinch the boundary and are rejected."""
+    free = np.asarray(free, dtype=bool)
+    H, W = free.shape
+    used = np.zeros((H + 1, W + 1), dtype=bool)
+    cj, ci = np.nonzero(free)
+    for dj in (0, 1):
+        for di in (0, 1):
+            used[cj + dj, ci + di] = True
+    ids = -np.ones((H + 1, W + 1), dtype=np.int64)
+    ids[used] = np.arange(int(used.sum()))
+    jj, ii = np.nonzero(used)
+    xy = np.stack([ii * h, jj * h], axis=1).astype(np.float64)
+    v00, v10, v11, v01 = ids[cj, ci], ids[cj, ci + 1], ids[cj + 1, ci + 1], ids[cj + 1, ci]
+    tri = np.empty((2 * len(cj), 3), dtype=np.int32)
+    tri[0::2] = np.stack([v00, v10, v11], axis=1)
+    tri[1::2] = np.stack([v00, v11, v01], axis=1)
+
+    def is_free(j, i):
+        return 0 <= j < H and 0 <= i < W and free[j, i]
+
+    nxt = {}                                     # directed boundary edges, domain on the left
+    for j, i in zip(cj.tolist(), ci.tolist()):
+        sides = (((j - 1, i), (j, i), (j, i + 1)),            # bottom: (i, j) -> (i+1, j)
+                 ((j, i + 1), (j, i + 1), (j + 1, i + 1)),    # right
+                 ((j + 1, i), (j + 1, i + 1), (j + 1, i)),    # top
+                 ((j, i - 1), (j + 1, i), (j, i)))            # left
+        for (nj, ni), a, b in sides:
+            if not is_free(nj, ni):
+                u, v = int(ids[a]), int(ids[b])
+                if u in nxt:
+                    raise ValueError("cells touching at a corner pinch the boundary")
+                nxt[u] = v
+    loops, seen = [], set()
+    for start in sorted(nxt):
+        if start in seen:
+            continue
+        loop, u = [], start
+        while u not in seen:
+            seen.add(u)
+            loop.append(u)
+            u = nxt[u]
+        loops.append(np.asarray(loop, dtype=np.int32))
+
+    def area2(l):
+        p = xy[l]
+        return float(np.sum(p[:, 0] * np.roll(p[:, 1], -1) - np.roll(p[:, 0], -1) * p[:, 1]))
+
+    loops.sort(key=lambda l: -area2(l))          # the one counter-clockwise loop first
+    return Mesh(xy=xy, tri=tri, loops=loops, name=name, meta=dict(meta or {}, ids=ids))
+
+
+def serpentine(n_corr: int, corr_w: int, corr_len: int) -> Mesh:
+    """A winding corridor: n_corr vertical corridors of corr_w x corr_len cells,
+    joined at alternate ends through corr_w-wide gaps in the one-cell walls
+    between them (each wall hangs from the bottom or the top edge).  The
+    path from one end to the other is about n_corr (corr_len + 1) cells long,
+    so harmonic measures across it fall by about exp(-pi L / w) for a path of
+    length L in corridors of width w."""
+    W = n_corr * corr_w + (n_corr - 1)
+    Hc = corr_len
+    free = np.ones((Hc, W), dtype=bool)
+    for c in range(n_corr - 1):
+        x = c * (corr_w + 1) + corr_w
+        if c % 2 == 0:
+            free[:Hc - corr_w, x] = False        # wall from the bottom, gap at the top
+        else:
+            free[corr_w:, x] = False             # wall from the top, gap at the bottom
+    return cell_domain(free, 1.0 / max(W, Hc), name=f"serpentine_{n_corr}x{corr_w}x{corr_len}",
+                       meta={"n_corr": n_corr, "corr_w": corr_w, "corr_len": corr_len, "N": max(W, Hc)})
+
+
+def strip(w: int, length: int) -> Mesh:
+    """A straight corridor of w x length cells (cell side 1 / length)."""
+    return cell_domain(np.ones((w, length), dtype=bool), 1.0 / length, name=f"strip_{w}x{length}",
+                       meta={"w": w, "length": length, "N": length})
 
 
 def snap_to_vertex(xy: np.ndarray, p) -> int:
