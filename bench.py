@@ -356,6 +356,7 @@ def query_step(dd, ctx, dev, stream, flush, args, rank, world, local_rank, name,
     }
     if "fix_kl_kernel" in per_launch:
         line["recompute_over_tile"] = round(per_launch["fix_kl_kernel"] / tile_ms, 4)
+    line["tile_shapes"] = dd.dd_tuning_table().strip().splitlines()
     if remeasured is not None:
         line["remeasured"] = remeasured
     return {"line": line, "mid": mid, "wl": wl, "batches": batches, "fields": fields, "pxy": pxy, "plen": plen,
@@ -743,9 +744,9 @@ def sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, p
 def mid_section(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 8):
     """A mid-size grid for full ncu captures (a few GB on the device): N = 300
     with 12 obstacles (n = 86,449, k = 2,122, P = 0.73 GB, larger than L2).
-    The single-target dense stream (KL+TV), the sparse pass (KL+TV, Section V)
-    and the split-BF16 KL GEMM for 512 targets, each timed with CUDA events
-    (L2 flushed before every launch)."""
+    The single-target dense stream (KL+TV), the sparse pass (KL+TV, Section V),
+    the split-BF16 KL GEMM and the FP32 KL+TV pass for 512 targets, each timed
+    with CUDA events (L2 flushed before every launch)."""
     import torch
     from synthetic import workloads
     T = 512
@@ -778,12 +779,17 @@ def mid_section(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 8):
     outk = torch.empty((1, T, n_v), dtype=torch.float32, device=dev)
     dd.dd_distance(ctx, mid, tl, 1, dd.DD_PREC_BF16X3, outk)
     gemm_ms = timed(lambda i: dd.dd_distance(ctx, mid, tl, 1, dd.DD_PREC_BF16X3, outk), 4)
+    # the FP32 many-target pass (field tile kernel + exact recompute), KL+TV
+    out2 = torch.empty((2, T, n_v), dtype=torch.float32, device=dev)
+    dd.dd_distance(ctx, mid, tl, 3, dd.DD_PREC_FP32, out2)      # the first call runs the tile autotuner
+    tile_ms = timed(lambda i: dd.dd_distance(ctx, mid, tl, 3, dd.DD_PREC_FP32, out2), 4)
     dd.dd_unload_mesh(ctx, mid)
     issued = 3 * 2.0 * n_v * k * T / (gemm_ms / 1e3) / 1e12
     return {"workload": "grid300: n=%d, k=%d, P=%.2f GB FP32" % (n_v, k, 4.0 * n_v * k_pad / 1e9),
             "dense_stream_ms": round(dense_ms, 4),
             "dense_stream_gbs": round(4.0 * n_v * k_pad / (dense_ms / 1e3) / 1e9, 1),
             "sparse_ms": round(sparse_ms, 4), "gemm_T": T, "gemm_ms": round(gemm_ms, 4),
+            "fp32_fields_ms": round(tile_ms, 4), "tile_shapes": dd.dd_tuning_table().strip().splitlines(),
             "gemm_tflops_issued": round(issued, 1), "peak_bf16": pk.get("bf16_tflops"), "peak_source": pk_kind}
 
 

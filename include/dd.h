@@ -221,6 +221,40 @@ dd_status dd_set_poisson_kernel(dd_ctx *ctx, int32_t mesh, const double *P);
  * out: device or host.  Errors: DD_ESTATE if none is stored. */
 dd_status dd_get_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out);
 
+/* The Poisson kernel to full relative precision in every entry, however
+ * small, and its logarithm (Section V, Precision: on maze-like domains the
+ * kernel spans hundreds of orders of magnitude; the paper computes the
+ * vectors log P and combines them in the KL sum).  Refines the stored P by
+ * FP64 sweeps of the fixed-point form of Eq. (32),
+ *   P[i,b] = (sum_{j interior} w_ij P[j,b] + w_ib) / sum_j w_ij,
+ * which add non-negative terms only (so each entry keeps its own relative
+ * precision), starting from the solver's values where they are at least
+ * 2^-30 and from 0 elsewhere, until the largest relative change of an entry
+ * over 32 sweeps is at most tol or max_sweeps have run.  Then stores the
+ * refined P as before (FP32, values below FLT_MIN flushed to 0) and log2 P
+ * in FP32 for every entry (-inf where P is exactly 0).  Afterwards
+ * dd_distance (DD_PREC_FP32), dd_query and dd_divergence (reverse KL) take
+ * log P[t,b] (KL) and log P[x,b] (KLT) from log2 P wherever the FP32 entry is
+ * 0, instead of evaluating the logarithm at FLT_MIN; the split-BF16, sparse,
+ * batch and served paths do not.  Needs non-negative edge weights (grids,
+ * Delaunay meshes); entries below about 1e-300 underflow FP64.  Holds one
+ * more n_v x k_pad FP32 array; recomputing or replacing P discards it, and
+ * it discards the split-BF16 and sparse copies of the old P.
+ *   tol         relative change at which the sweeps stop (> 0; 1e-14 is typical)
+ *   max_sweeps  sweep cap (>= 1)
+ *   sweeps, change  NULL or out: sweeps run (largest over column chunks) and
+ *               the last relative change
+ * Synchronous.  Errors: DD_ESTATE (no Poisson kernel), DD_EINVAL, DD_ENOMEM,
+ * DD_ECUDA, DD_ENOTCONV (not below tol within max_sweeps; the result is still
+ * stored). */
+dd_status dd_log_poisson_kernel(dd_ctx *ctx, int32_t mesh, double tol, int32_t max_sweeps, int32_t *sweeps,
+                                double *change);
+
+/* Copy log2 P out (after dd_log_poisson_kernel), as [n_v][k] FP32 (pitch k),
+ * -inf where P is exactly 0.  out: device or host.  Errors: DD_ESTATE if
+ * none is stored. */
+dd_status dd_get_log_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out);
+
 /* Prepare DD_PREC_SPARSE and DD_PREC_SPARSE_MERGED on this mesh (Section V:
  * the entries of P below a threshold of 1/sqrt(n) are eliminated before the
  * KL sum, about 90 % of them; the paper does not say relative to what --

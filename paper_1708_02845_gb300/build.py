@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libdd.so")
 
-SOURCES = ["dd_api.cu", "dd_mesh.cpp", "dd_amg.cpp", "dd_pcg.cu", "dd_field.cu", "dd_fdiv.cu", "dd_sparse.cu", "dd_census.cu", "dd_trace.cu", "dd_noalloc.cu", "dd_gemm.cu", "dd_serve.cu"]
+SOURCES = ["dd_api.cu", "dd_mesh.cpp", "dd_amg.cpp", "dd_pcg.cu", "dd_logp.cu", "dd_field.cu", "dd_fdiv.cu", "dd_sparse.cu", "dd_census.cu", "dd_trace.cu", "dd_noalloc.cu", "dd_gemm.cu", "dd_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

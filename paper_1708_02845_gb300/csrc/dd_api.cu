@@ -162,6 +162,7 @@ void drop_sparse(DevMesh &m) {
 // what was derived from the stored P (the BF16 split, the row entropies, the
 // sparse rows) goes when P is recomputed or replaced
 void drop_derived(DevMesh &m) {
+    release(m, m.LP, m.n_v * m.k_pad * (int64_t)sizeof(float));
     release(m, m.p_hi, m.n_v * m.kb * 2);
     release(m, m.p_lo, m.n_v * m.kb * 2);
     release(m, m.ex, m.n_v * (int64_t)sizeof(float));
@@ -237,12 +238,13 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
     st = ensure_scratch(ctx, S_STAGE, 4 * (size_t)T * m.k_pad * sizeof(float));
     if (st != DD_OK) return st;
     float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
-    launch_stage_targets(m.P, m.n_v, m.k_pad, d_targets, T, stage, ctx->stream);
-    if (kl || tv) launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream);
+    launch_stage_targets(m.P, m.n_v, m.k_pad, d_targets, T, stage, ctx->stream, nullptr, m.LP);
+    if (kl || tv) launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream, -1, m.LP != nullptr);
     if (klt) {
         // the target-weighted KL is the reverse-KL member of the f-divergence kernels
         std::string err;
-        if ((st = launch_fdiv(m.P, m.n_v, m.k_pad, stage, T, DD_DIV_KL_REVERSE, 0.0, klt, ctx->stream, err)) != DD_OK)
+        if ((st = launch_fdiv(m.P, m.n_v, m.k_pad, stage, T, DD_DIV_KL_REVERSE, 0.0, klt, ctx->stream, err,
+                              m.LP)) != DD_OK)
             return set_err(ctx, st, err);
     }
     CK(cudaGetLastError(), "field kernel launch");
@@ -584,6 +586,46 @@ dd_status dd_get_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out) {
     return DD_OK;
 }
 
+dd_status dd_log_poisson_kernel(dd_ctx *ctx, int32_t mesh, double tol, int32_t max_sweeps, int32_t *sweeps,
+                                double *change) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    if (!m->has_P) return set_err(ctx, DD_ESTATE, "dd_log_poisson_kernel before dd_poisson_kernel");
+    if (!(tol > 0.0) || max_sweeps < 1) return set_err(ctx, DD_EINVAL, "tol must be > 0 and max_sweeps >= 1");
+    try {
+        if ((st = select_device(ctx)) != DD_OK) return st;
+        // the refined P changes what was derived from the old one
+        release(*m, m->p_hi, m->n_v * m->kb * 2);
+        release(*m, m->p_lo, m->n_v * m->kb * 2);
+        release(*m, m->ex, m->n_v * (int64_t)sizeof(float));
+        m->kb = 0;
+        drop_sparse(*m);
+        std::string err;
+        st = refine_log_poisson(*m, tol, max_sweeps, ctx->stream, sweeps, change, err);
+        if (st != DD_OK) set_err(ctx, st, err);
+        return st;
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
+dd_status dd_get_log_poisson_kernel(dd_ctx *ctx, int32_t mesh, float *out) {
+    DevMesh *m = nullptr;
+    dd_status st = get_mesh(ctx, mesh, &m);
+    if (st != DD_OK) return st;
+    if (!m->LP) return set_err(ctx, DD_ESTATE, "no log P stored (dd_log_poisson_kernel)");
+    if (!out) return set_err(ctx, DD_EINVAL, "out is null");
+    int sp = pointer_space(ctx, out);
+    if (sp < 0) return set_err(ctx, DD_EINVAL, "out is on another device");
+    if ((st = select_device(ctx)) != DD_OK) return st;
+    CK(cudaMemcpy2DAsync(out, (size_t)m->k * sizeof(float), m->LP, (size_t)m->k_pad * sizeof(float),
+                         (size_t)m->k * sizeof(float), (size_t)m->n_v, cudaMemcpyDefault, ctx->stream),
+       "copy log P");
+    if (sp == 0) CK(cudaStreamSynchronize(ctx->stream), "copy log P");
+    return DD_OK;
+}
+
 dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, int64_t *bytes) {
     DevMesh *m = nullptr;
     dd_status st = get_mesh(ctx, mesh, &m);
@@ -671,9 +713,10 @@ dd_status dd_divergence(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32
         if ((st = ensure_scratch(ctx, S_STAGE, 4 * (size_t)T * m->k_pad * sizeof(float))) != DD_OK) return st;
         float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
         launch_stage_targets(m->P, m->n_v, m->k_pad, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T,
-                             stage, ctx->stream);
+                             stage, ctx->stream, nullptr, m->LP);
         std::string err;
-        if ((st = launch_fdiv(m->P, m->n_v, m->k_pad, stage, T, family, param, dst, ctx->stream, err)) != DD_OK)
+        if ((st = launch_fdiv(m->P, m->n_v, m->k_pad, stage, T, family, param, dst, ctx->stream, err, m->LP)) !=
+            DD_OK)
             return set_err(ctx, st, err);
         CK(cudaGetLastError(), "divergence kernel launch");
         if (sp == 0) {
@@ -738,8 +781,9 @@ dd_status trace_into(dd_ctx *ctx, DevMesh &m, const float *d_fields, const int32
                           reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), T, S, max_pts, dxy, dlen, dst,
                           ctx->stream);
     } else {
-        if ((st = ensure_scratch(ctx, S_GRAD, trace_scratch_bytes(m, T, trace_dense_decisions(S)))) != DD_OK)
-            return st;
+        // rates and vertex decisions of every field are stored only where many paths share a field
+        const bool dense = trace_dense_decisions(S);
+        if ((st = ensure_scratch(ctx, S_GRAD, dense ? trace_scratch_bytes(m, T, true) : 256)) != DD_OK) return st;
         launch_trace(m, d_fields, m.n_v, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]),
                      reinterpret_cast<const int32_t *>(ctx->scratch[S_SOURCES]), T, S, max_pts, dxy, dlen, dst,
                      ctx->scratch[S_GRAD], ctx->stream);

@@ -91,10 +91,20 @@ __device__ __forceinline__ float fterm(float px, float pt, float lmt, float Ebt,
     }
 }
 
+// reverse KL term where P[x,b] is below FLT_MIN but its log2 lx is known:
+// P_t (log P_t - log P_x) = P_t ((E_t - lx) ln2 + lm_t)
+__device__ __forceinline__ float klrev_logp_term(float pt, float lmt, float Ebt, float lx) {
+    if (pt == 0.0f) return 0.0f;
+    return pt * __fmaf_rn(__fadd_rn(__fsub_rn(Ebt, 12583039.0f), -lx), kLn2f, lmt);
+}
+
+// LP (reverse KL only, may be null): log2 P; an entry whose FP32 value is 0
+// takes log P[x,b] from it instead of the clamp at FLT_MIN
 template <int FAM>
 __global__ void __launch_bounds__(256) fdiv_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
                                                    const float *__restrict__ sP, const float *__restrict__ sL,
-                                                   const float *__restrict__ sE, FdParams q, float *__restrict__ out) {
+                                                   const float *__restrict__ sE, FdParams q, float *__restrict__ out,
+                                                   const float *__restrict__ LP) {
     extern __shared__ __align__(16) float fsm[];
     __shared__ float tab[2 * kLogTab];
     float *tP = fsm, *tL = fsm + k_pad, *tE = fsm + 2 * k_pad;
@@ -127,6 +137,25 @@ __global__ void __launch_bounds__(256) fdiv_kernel(const float *__restrict__ P, 
                 const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
                 const float4 l4 = reinterpret_cast<const float4 *>(tL)[c];
                 const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
+                if (FAM == kKlRev && LP &&
+                    ((v[u].x == 0.f && p4.x != 0.f) || (v[u].y == 0.f && p4.y != 0.f) ||
+                     (v[u].z == 0.f && p4.z != 0.f) || (v[u].w == 0.f && p4.w != 0.f))) {
+                    const float4 lx = reinterpret_cast<const float4 *>(LP + x * k_pad)[c];
+                    const float px[4] = {v[u].x, v[u].y, v[u].z, v[u].w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
+                    const float lt[4] = {l4.x, l4.y, l4.z, l4.w}, et[4] = {e4.x, e4.y, e4.z, e4.w};
+                    const float l2[4] = {lx.x, lx.y, lx.z, lx.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float t = (px[e] == 0.f && l2[e] > -INFINITY)
+                                            ? klrev_logp_term(pt[e], lt[e], et[e], l2[e])
+                                            : fterm<FAM>(px[e], pt[e], lt[e], et[e], q, tab);
+                        if (e & 1)
+                            s1 += t;
+                        else
+                            s0 += t;
+                    }
+                    continue;
+                }
                 s0 += fterm<FAM>(v[u].x, p4.x, l4.x, e4.x, q, tab);
                 s1 += fterm<FAM>(v[u].y, p4.y, l4.y, e4.y, q, tab);
                 s0 += fterm<FAM>(v[u].z, p4.z, l4.z, e4.z, q, tab);
@@ -143,7 +172,7 @@ __global__ void __launch_bounds__(256) fdiv_kernel(const float *__restrict__ P, 
 }  // namespace
 
 dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, int32_t family,
-                      double param, float *out, cudaStream_t s, std::string &err) {
+                      double param, float *out, cudaStream_t s, std::string &err, const float *LP) {
     const float *sP = reinterpret_cast<const float *>(stage);
     const float *sL = sP + (int64_t)T * k_pad;
     const float *sE = sL + (int64_t)T * k_pad;
@@ -175,7 +204,8 @@ dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *
         if (gx > rows_blocks) gx = rows_blocks;
         {
             KMark km_("fdiv_kernel", s);
-            kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, q, out);
+            kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, q, out,
+                                                                   family == DD_DIV_KL_REVERSE ? LP : nullptr);
         }
     };
     switch (family) {

@@ -78,7 +78,7 @@ __device__ __forceinline__ void accumulate_kl(float px, float lmx, float ex, flo
 __global__ void stage_targets_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
                                      const int32_t *__restrict__ targets, int32_t T, float *__restrict__ sP,
                                      float *__restrict__ sL, float *__restrict__ sE, float *__restrict__ sF,
-                                     int *__restrict__ bad_id) {
+                                     int *__restrict__ bad_id, const float *__restrict__ LP) {
     __shared__ float tab[2 * kLogTab];
     build_log_table(tab);
     __syncthreads();
@@ -92,14 +92,25 @@ __global__ void stage_targets_kernel(const float *__restrict__ P, int64_t n_v, i
         return;
     }
     const float *row = P + (int64_t)t * k_pad;
+    const float *lrow = LP ? LP + (int64_t)t * k_pad : nullptr;
     for (int64_t b = threadIdx.x; b < k_pad; b += blockDim.x) {
         const float p = row[b];
-        float lm, E;
-        split_log<true>(p, tab, lm, E);
+        float lm, E, F;
+        const float l2 = (lrow && p == 0.0f) ? lrow[b] : -INFINITY;
+        if (l2 > -INFINITY) {
+            // an entry below FLT_MIN with a known logarithm: log2 p = e + f, e integer, f in [0, 1)
+            const float e = floorf(l2);
+            F = __fsub_rn(l2, e);
+            lm = __fmul_rn(F, kLn2);
+            E = __fadd_rn(12583039.0f, e);        // the biased-float exponent of split_log (exact)
+        } else {
+            split_log<true>(p, tab, lm, E);
+            F = lg2_mant(__float_as_int(fmaxf(p, FLT_MIN)));
+        }
         sP[o + b] = p;
         sL[o + b] = lm;
         sE[o + b] = E;
-        sF[o + b] = lg2_mant(__float_as_int(fmaxf(p, FLT_MIN)));
+        sF[o + b] = F;
     }
 }
 
@@ -354,12 +365,18 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src) {
 // target, x = t among them -- is then recomputed by one warp with the table
 // logarithm (fix_kl_kernel, kl_row_exact), so every value keeps 1e-5
 // relative accuracy.
+//
+// The target side's one-number log2 comes from the staged exponent and
+// hardware mantissa log (sE, sF) when they are given -- bit for bit the value
+// fast_l2 forms from the entry, and for an entry below FLT_MIN with a known
+// logarithm (log2 P from dd_log_poisson_kernel) that logarithm instead of
+// the clamp -- else from the staged entry itself (the multi-domain launch).
 template <int TM, int TN, int RM, int CN, bool KL = true, bool TV = true>
 __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
                                           const float *__restrict__ sP, const float *__restrict__ sL,
-                                          const float *__restrict__ sE, int32_t T, float *__restrict__ out_kl,
-                                          float *__restrict__ out_tv, int64_t x0, int a0, float *tsm,
-                                          const float *tab) {
+                                          const float *__restrict__ sE, const float *__restrict__ sF, int32_t T,
+                                          float *__restrict__ out_kl, float *__restrict__ out_tv, int64_t x0, int a0,
+                                          float *tsm, const float *tab) {
     constexpr int COLG = TN / CN;
     float (*xP)[TM] = reinterpret_cast<float (*)[TM]>(tsm);
     float (*xL)[TM] = reinterpret_cast<float (*)[TM]>(tsm + 1 * kTileB * TM);
@@ -412,8 +429,18 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
                 yP[cb + e][a] = p2.x;
                 yP[cb + e + 1][a] = p2.y;
                 if (KL) {
-                    yL[cb + e][a] = fast_l2(fmaxf(p2.x, FLT_MIN));
-                    yL[cb + e + 1][a] = fast_l2(fmaxf(p2.y, FLT_MIN));
+                    if (sF) {
+                        float2 e2 = make_float2(12583039.0f, 12583039.0f), f2 = make_float2(0.f, 0.f);
+                        if (ag < T && b0 + cb + e < k_pad) {
+                            e2 = __ldg(reinterpret_cast<const float2 *>(sE + (int64_t)ag * k_pad + b0 + cb + e));
+                            f2 = __ldg(reinterpret_cast<const float2 *>(sF + (int64_t)ag * k_pad + b0 + cb + e));
+                        }
+                        yL[cb + e][a] = __fadd_rn(__fsub_rn(e2.x, 12583039.0f), f2.x);
+                        yL[cb + e + 1][a] = __fadd_rn(__fsub_rn(e2.y, 12583039.0f), f2.y);
+                    } else {
+                        yL[cb + e][a] = fast_l2(fmaxf(p2.x, FLT_MIN));
+                        yL[cb + e + 1][a] = fast_l2(fmaxf(p2.y, FLT_MIN));
+                    }
                 }
             }
         }
@@ -518,24 +545,25 @@ typedef TileShape<256, 16, 8, 2> TileC;
 template <int TM, int TN, int RM, int CN, bool KL, bool TV>
 __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
                                                          const float *__restrict__ sP, const float *__restrict__ sL,
-                                                         const float *__restrict__ sE, int32_t T,
-                                                         float *__restrict__ out_kl, float *__restrict__ out_tv) {
+                                                         const float *__restrict__ sE, const float *__restrict__ sF,
+                                                         int32_t T, float *__restrict__ out_kl,
+                                                         float *__restrict__ out_tv) {
     extern __shared__ __align__(16) float tsm[];
     float *tab = tsm + 2 * kTileB * (TM + TN);
     build_log_table(tab);
     __syncthreads();
-    tile_body<TM, TN, RM, CN, KL, TV>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, (int64_t)blockIdx.x * TM,
+    tile_body<TM, TN, RM, CN, KL, TV>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, (int64_t)blockIdx.x * TM,
                                       blockIdx.y * TN, tsm, tab);
 }
 
 template <class S, int TM, int TN, int RM, int CN>
 void launch_tile(const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL, const float *sE,
-                 int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
-    dim3 g((unsigned)((n_v + TM - 1) / TM), (unsigned)((T + TN - 1) / TN));
+                 const float *sF, int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
+    const dim3 g((unsigned)((n_v + TM - 1) / TM), (unsigned)((T + TN - 1) / TN));
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_bytes);
         KMark km_("field_tile_kernel", s);
-        kern<<<g, 256, S::smem_bytes, s>>>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv);
+        kern<<<g, 256, S::smem_bytes, s>>>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv);
     };
     if (out_kl && out_tv)
         go(field_tile_kernel<TM, TN, RM, CN, true, true>);
@@ -579,15 +607,15 @@ __global__ void __launch_bounds__(256, 2) batch_tile_kernel(const BatchProblem *
         const BatchProblem q = probs[w.prob];
         switch (q.variant) {
             case 0:
-                tile_body<64, 64, 4, 4>(q.P, q.n_v, q.k_pad, q.sP, q.sL, q.sE, q.T, q.out_kl, q.out_tv,
+                tile_body<64, 64, 4, 4>(q.P, q.n_v, q.k_pad, q.sP, q.sL, q.sE, nullptr, q.T, q.out_kl, q.out_tv,
                                         (int64_t)w.x_tile * 64, w.a_tile * 64, tsm, tab);
                 break;
             case 1:
-                tile_body<128, 32, 4, 4>(q.P, q.n_v, q.k_pad, q.sP, q.sL, q.sE, q.T, q.out_kl, q.out_tv,
+                tile_body<128, 32, 4, 4>(q.P, q.n_v, q.k_pad, q.sP, q.sL, q.sE, nullptr, q.T, q.out_kl, q.out_tv,
                                          (int64_t)w.x_tile * 128, w.a_tile * 32, tsm, tab);
                 break;
             default:
-                tile_body<256, 16, 8, 2>(q.P, q.n_v, q.k_pad, q.sP, q.sL, q.sE, q.T, q.out_kl, q.out_tv,
+                tile_body<256, 16, 8, 2>(q.P, q.n_v, q.k_pad, q.sP, q.sL, q.sE, nullptr, q.T, q.out_kl, q.out_tv,
                                          (int64_t)w.x_tile * 256, w.a_tile * 16, tsm, tab);
                 break;
         }
@@ -624,13 +652,13 @@ constexpr int kNumShapes = 3;
 const int kShapeRows[kNumShapes] = {64, 128, 256}, kShapeTargets[kNumShapes] = {64, 32, 16};
 
 void launch_variant(int v, const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL,
-                    const float *sE, int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
+                    const float *sE, const float *sF, int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
     if (v == 0)
-        launch_tile<TileA, 64, 64, 4, 4>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+        launch_tile<TileA, 64, 64, 4, 4>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s);
     else if (v == 1)
-        launch_tile<TileB, 128, 32, 4, 4>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+        launch_tile<TileB, 128, 32, 4, 4>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s);
     else
-        launch_tile<TileC, 256, 16, 8, 2>(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+        launch_tile<TileC, 256, 16, 8, 2>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s);
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -652,7 +680,7 @@ std::tuple<int, int, int> tune_key(int64_t n_v, int64_t k_pad, int32_t T) {
 }
 
 int tune_variant(const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL, const float *sE,
-                 int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
+                 const float *sF, int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
     // DD_TILE_SHAPE=0..2 pins the shape (tests run every shape through it)
     if (const char *pin = std::getenv("DD_TILE_SHAPE")) {
         const int v = std::atoi(pin);
@@ -670,9 +698,9 @@ int tune_variant(const float *P, int64_t n_v, int64_t k_pad, const float *sP, co
     int best = 0;
     float best_ms = 1e30f;
     for (int v = 0; v < kNumShapes; ++v) {
-        launch_variant(v, P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);   // warm-up
+        launch_variant(v, P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s);   // warm-up
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; ++r) launch_variant(v, P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+        for (int r = 0; r < 3; ++r) launch_variant(v, P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -692,7 +720,7 @@ int tune_variant(const float *P, int64_t n_v, int64_t k_pad, const float *sP, co
 }  // namespace
 
 void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int32_t *targets, int32_t T,
-                          float4 *stage, cudaStream_t s, int *bad_id) {
+                          float4 *stage, cudaStream_t s, int *bad_id, const float *LP) {
     float *sP = reinterpret_cast<float *>(stage);
     float *sL = sP + (int64_t)T * k_pad;
     float *sE = sL + (int64_t)T * k_pad;
@@ -700,16 +728,19 @@ void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int3
     if (T <= 0) return;
     {
         KMark km_("stage_targets_kernel", s);
-        stage_targets_kernel<<<(unsigned)T, 256, 0, s>>>(P, n_v, k_pad, targets, T, sP, sL, sE, sF, bad_id);
+        stage_targets_kernel<<<(unsigned)T, 256, 0, s>>>(P, n_v, k_pad, targets, T, sP, sL, sE, sF, bad_id, LP);
     }
 }
 
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, float *out_kl,
-                        float *out_tv, int *err_flag, cudaStream_t s, int variant) {
+                        float *out_tv, int *err_flag, cudaStream_t s, int variant, bool staged_logs) {
     const float *sP = reinterpret_cast<const float *>(stage);
     const float *sL = sP + (int64_t)T * k_pad;
     const float *sE = sL + (int64_t)T * k_pad;
     const float *sF = sE + (int64_t)T * k_pad;
+    // the tile kernel forms the target side's log2 from the staged entry itself
+    // unless the staging holds logarithms of entries below FLT_MIN
+    const float *tF = staged_logs ? sF : nullptr;
     const size_t smem = 4 * (size_t)k_pad * sizeof(float);
     if (T <= 2 && smem <= 200 * 1024) {
         // one target per grid row; loads run 8 float4 per lane ahead of the arithmetic
@@ -729,9 +760,10 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
         }
         return;
     }
-    const int v = (variant >= 0 && variant < kNumShapes) ? variant
-                                                         : tune_variant(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
-    launch_variant(v, P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+    const int v = (variant >= 0 && variant < kNumShapes)
+                      ? variant
+                      : tune_variant(P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s);
+    launch_variant(v, P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s);
     if (out_kl) {
         const BatchProblem q{P, n_v, k_pad, sP, sL, sE, T, v, out_kl, nullptr};
         KMark km_("fix_kl_kernel", s);
@@ -742,7 +774,7 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
 
 int tile_variant_for(const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL, const float *sE,
                      int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
-    return tune_variant(P, n_v, k_pad, sP, sL, sE, T, out_kl, out_tv, s);
+    return tune_variant(P, n_v, k_pad, sP, sL, sE, nullptr, T, out_kl, out_tv, s);
 }
 
 int tile_rows(int variant) { return kShapeRows[variant]; }

@@ -60,6 +60,7 @@ struct DevMesh {
     int32_t *rb_row = nullptr, *rb_col = nullptr;
     double *rb_val = nullptr;
     float *P = nullptr;        // [n_v][k_pad] FP32 Poisson kernel
+    float *LP = nullptr;       // [n_v][k_pad] FP32 log2 P to full relative precision (dd_log_poisson_kernel), or null
     bool has_P = false;
     void *p_hi = nullptr, *p_lo = nullptr;   // BF16 split of P, [n_v][kb] (built on first BF16 request)
     float *ex = nullptr;                     // [n_v] sum_b P log P (FP64-accumulated)
@@ -85,20 +86,29 @@ dd_status run_pcg(DevMesh &m, double rtol, int32_t max_iter, cudaStream_t s, int
                   double *resid, std::string &err);
 // Store a host FP64 P [n_v][k] into m.P with the same clamp/flush as the solver.
 dd_status store_poisson(DevMesh &m, const double *P, cudaStream_t s, std::string &err);
+// Refine the stored P to full relative precision in every entry (FP64 sweeps of
+// the fixed-point form of Eq. 32, dd_logp.cu) and store log2 P in m.LP.
+dd_status refine_log_poisson(DevMesh &m, double tol, int32_t max_sweeps, cudaStream_t s, int32_t *sweeps,
+                             double *change, std::string &err);
 
 // Per-target staging of P[t,:] and its split logarithm: four [T][k_pad] float
 // arrays back to back -- P[t_a,b], the log-mantissa lm (table), the exponent E
 // as the biased float 12582912 + 127 + E (exact; only differences of two are
 // used), and the hardware base-2 log of the mantissa (streaming kernel).
 // Target ids outside [0, n_v) are not read: their rows are zero-filled and
-// *bad_id (if not null) is set to 1.
+// *bad_id (if not null) is set to 1.  With LP (log2 P, dd_log_poisson_kernel)
+// an entry whose FP32 value is 0 takes its logarithms from LP (finite there)
+// instead of the clamp at FLT_MIN.
 void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int32_t *targets, int32_t T,
-                          float4 *stage, cudaStream_t s, int *bad_id = nullptr);
+                          float4 *stage, cudaStream_t s, int *bad_id = nullptr, const float *LP = nullptr);
 // FP32 fields.  out_kl / out_tv: [T][n_v] (either may be null).  variant: the
 // tile shape for T > 2 (0, 1, 2), or -1 for the autotuner's choice (which may
-// run timed launches the first time a size class is seen).
+// run timed launches the first time a size class is seen).  staged_logs: the
+// staging took logarithms from log2 P (launch_stage_targets with LP), which
+// the tile kernel then reads instead of forming them from the staged entries.
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T,
-                        float *out_kl, float *out_tv, int *err_flag, cudaStream_t s, int variant = -1);
+                        float *out_kl, float *out_tv, int *err_flag, cudaStream_t s, int variant = -1,
+                        bool staged_logs = false);
 // One problem of a multi-domain field launch, and one output tile of it.
 struct BatchProblem {
     const float *P;
@@ -128,8 +138,9 @@ void launch_edge_paths(const DevMesh &m, const float *fields, const int32_t *tar
                        int32_t S, int32_t max_pts, float2 *out_xy, int32_t *out_len, int32_t *out_status,
                        cudaStream_t s);
 // other f-divergence fields [T][n_v] from staged targets (stage_targets_kernel's arrays)
+// With LP, the reverse KL takes log P[x,b] from LP where the FP32 entry is 0.
 dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, int32_t family,
-                      double param, float *out, cudaStream_t s, std::string &err);
+                      double param, float *out, cudaStream_t s, std::string &err, const float *LP = nullptr);
 
 // Copy the defined prefix of every path (len[i] points of row i, pitch max_pts)
 // from device memory to another buffer (e.g. pinned host memory seen through its
@@ -156,9 +167,10 @@ void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *st
 // spread (max - min) of the hardware mantissa log's error over [1, 2), in base-2 units
 dd_status fast_log_spread(double *spread, std::string &err);
 
-// Tracer: per-field triangle rates (and, when trace_dense_decisions(S), vertex
-// decisions) into `scratch` (trace_scratch_bytes(m, T, dense) bytes), then
-// T*S paths.
+// Tracer: when trace_dense_decisions(S), per-field triangle rates and vertex
+// decisions into `scratch` (trace_scratch_bytes(m, T, true) bytes), then T*S
+// paths; otherwise the walk forms the rates and decisions it needs itself and
+// `scratch` is unused.
 bool trace_dense_decisions(int32_t S);
 size_t trace_scratch_bytes(const DevMesh &m, int32_t T, bool decisions);
 void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, const int32_t *targets,

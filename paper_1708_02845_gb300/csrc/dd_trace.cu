@@ -255,7 +255,11 @@ __global__ void vertex_decision_kernel(const TraceDom p, int32_t T, const float 
 // (rates of this field start at `rates`, one entry per triangle every
 // `rstride`; its decisions at `dec`, one per vertex every `dstride`.  With
 // dec == nullptr a vertex state computes its decision itself -- the same
-// function, so the same result -- which pays when few paths share a field.)
+// function, so the same result -- which pays when few paths share a field.
+// With rates == nullptr the walk computes each triangle's rates from the
+// field where it needs them, by the same function as rates_kernel, so again
+// with the same result: few paths per field touch a small share of the
+// triangles, and a pass over all of them would cost more than the walk.)
 __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__restrict__ f,
                                            const float4 *__restrict__ rates, int64_t rstride,
                                            const VDec *__restrict__ dec, int64_t dstride, int target, int source,
@@ -338,7 +342,8 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
             if (!dv) {
                 if (scan_q < scan_end) {
                     const int tl = p.vt[scan_q++];
-                    fs.add(v, target, tl, load_tri(p.rec, tl), __ldg(rates + (int64_t)tl * rstride));
+                    fs.add(v, target, tl, load_tri(p.rec, tl),
+                           rates ? __ldg(rates + (int64_t)tl * rstride) : tri_rates(p.gphi, p.rec, tl, f));
                     continue;
                 }
                 own = fs.finish(p, f, target, v);
@@ -382,7 +387,7 @@ __device__ __forceinline__ void trace_path(const TraceDom &p, const float *__res
         // eb is local vertex L, ea is X, and the opposite vertex is Y
         const int tl = t_next;
         const Tri T = load_tri(p.rec, tl);
-        const float4 Rt = __ldg(rates + (int64_t)tl * rstride);
+        const float4 Rt = rates ? __ldg(rates + (int64_t)tl * rstride) : tri_rates(p.gphi, p.rec, tl, f);
         const int L = local_of(T, eb), X = L == 2 ? 0 : L + 1, Y = L == 0 ? 2 : L - 1;
         const float ra = sel3f(X, Rt.x, Rt.y, Rt.z), rb = sel3f(L, Rt.x, Rt.y, Rt.z), rc = sel3f(Y, Rt.x, Rt.y, Rt.z);
         const float qY = sel3f(Y, T.q0, T.q1, T.q2);
@@ -471,7 +476,8 @@ __global__ void __launch_bounds__(128) trace_kernel(const TraceParams p) {
     const bool active = gid < p.total;       // padding lanes stay in the warp's walk loop, idle
     const int64_t id = active ? gid : 0;
     const int a = (int)(id / p.S);
-    trace_path(p.d, p.fields + (int64_t)a * p.field_stride, p.rates + a, p.T, p.dec ? p.dec + a : nullptr, p.T,
+    trace_path(p.d, p.fields + (int64_t)a * p.field_stride, p.rates ? p.rates + a : nullptr, p.T,
+               p.dec ? p.dec + a : nullptr, p.T,
                p.targets[a], p.sources[id], p.out_xy + id * p.max_pts, p.max_pts, p.max_steps, p.out_len + id,
                p.out_status + id, active);
 }
@@ -557,7 +563,9 @@ void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, c
                   int32_t *out_status, void *scratch, cudaStream_t s) {
     const bool dense = trace_dense_decisions(S);
     TraceParams p;
-    float4 *rates = reinterpret_cast<float4 *>(scratch);
+    // the rates of every triangle only where vertex decisions are precomputed (many
+    // paths per field); with few, the walk forms the rates it needs itself
+    float4 *rates = dense ? reinterpret_cast<float4 *>(scratch) : nullptr;
     VDec *dec = dense ? reinterpret_cast<VDec *>(reinterpret_cast<char *>(scratch) +
                                                  align256((size_t)T * m.n_t * sizeof(float4)))
                       : nullptr;
@@ -577,12 +585,12 @@ void launch_trace(const DevMesh &m, const float *fields, int64_t field_stride, c
     p.out_len = out_len;
     p.out_status = out_status;
     if (p.total == 0) return;
-    {
-        KMark km_("rates_kernel", s);
-        rates_kernel<<<(unsigned)((m.n_t * T + 255) / 256), 256, 0, s>>>(m.gphi, m.trec, m.n_t, T, fields, field_stride,
-                                                                          rates);
-    }
     if (dense) {
+        {
+            KMark km_("rates_kernel", s);
+            rates_kernel<<<(unsigned)((m.n_t * T + 255) / 256), 256, 0, s>>>(m.gphi, m.trec, m.n_t, T, fields,
+                                                                              field_stride, rates);
+        }
         const int64_t warps = m.n_v * ((T + 31) / 32);
         {
             KMark km_("vertex_decision_kernel", s);

@@ -49,6 +49,8 @@ _SIGS = {
     "dd_poisson_kernel": (_i32, [_p, _i32, _f64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f64)]),
     "dd_set_poisson_kernel": (_i32, [_p, _i32, _p]),
     "dd_get_poisson_kernel": (_i32, [_p, _i32, _p]),
+    "dd_log_poisson_kernel": (_i32, [_p, _i32, _f64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f64)]),
+    "dd_get_log_poisson_kernel": (_i32, [_p, _i32, _p]),
     "dd_sparsify": (_i32, [_p, _i32, _f64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "dd_distance": (_i32, [_p, _i32, _p, _i32, _u32, _i32, _p]),
     "dd_divergence": (_i32, [_p, _i32, _p, _i32, _i32, _f64, _p]),
@@ -191,6 +193,21 @@ def dd_set_poisson_kernel(ctx, mesh: int, P):
 
 def dd_get_poisson_kernel(ctx, mesh: int, out):
     _check(ctx, lib.dd_get_poisson_kernel(ctx, mesh, ptr(out)))
+    return out
+
+
+def dd_log_poisson_kernel(ctx, mesh: int, tol: float = 1e-14, max_sweeps: int = 200000, allow_notconv=False):
+    """Refine P to full relative precision in every entry and store log2 P; returns (sweeps, last change)."""
+    sweeps = _i32()
+    change = _f64()
+    st = lib.dd_log_poisson_kernel(ctx, mesh, tol, max_sweeps, ctypes.byref(sweeps), ctypes.byref(change))
+    if not (allow_notconv and st == DD_ENOTCONV):
+        _check(ctx, st)
+    return sweeps.value, change.value
+
+
+def dd_get_log_poisson_kernel(ctx, mesh: int, out):
+    _check(ctx, lib.dd_get_log_poisson_kernel(ctx, mesh, ptr(out)))
     return out
 
 

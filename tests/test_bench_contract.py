@@ -63,6 +63,7 @@ def _fake_dd(n_v, k, kernel_ms):
     m.dd_unload_mesh = lambda ctx, mid: None
     m.dd_trace_fields = lambda ctx, mid, f, tg, sr, max_pts, xy, ln, st: None
     m.dd_kernel_timing = kernel_timing
+    m.dd_tuning_table = lambda: "rows<=2^18 k_pad<=2^12 T<=2^8: 64x64\n"
     return m
 
 
