@@ -971,16 +971,21 @@ def serve_section(dd, ctx, args, n_domains: int, seconds: float, rate: float = 2
     order = sorted(range(len(doms)), key=lambda i: doms[i].mesh.n_v)[:n_domains]
     doms = [doms[i] for i in sorted(order)]
     t0 = time.perf_counter()
-    mids = []
+    mids, pre_dom = [], []
     for wl in doms:
+        t1 = time.perf_counter()
         idx, off = wl.mesh.loop_arrays()
         mid = dd.dd_load_mesh(ctx, wl.mesh.xy, wl.mesh.tri, idx, off)
-        dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+        t2 = time.perf_counter()
+        it, _ = dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+        info = dd.dd_mesh_info(ctx, mid)
+        pre_dom.append({"n_v": info["n_v"], "k": info["k"], "load_s": round(t2 - t1, 2), "pcg_iters": it,
+                        "pcg_s": round(time.perf_counter() - t2, 2)})
         mids.append(mid)
     pre = time.perf_counter() - t0
     qs = workloads.serving_queries(doms, rate_qps=rate, duration_s=seconds)
     # ---- served
-    sv = dd.dd_server_create(ctx, 24 << 30, n_slots=3, max_batch=64, max_pts=max_pts)
+    sv = dd.dd_server_create(ctx, 32 << 30, n_slots=4, max_batch=256, max_pts=max_pts)
     lat = {}
     refused = 0
     start = time.perf_counter()
@@ -1037,13 +1042,13 @@ def serve_section(dd, ctx, args, n_domains: int, seconds: float, rate: float = 2
                        "qps": round(L.size / served_wall, 1),
                        "p50_ms": round(float(np.percentile(L, 50)), 3), "p99_ms": round(float(np.percentile(L, 99)), 3),
                        "paths_ok_frac_sample": round(float(np.mean(paths_ok)), 4) if paths_ok else None,
-                       "slots": 3, "max_batch": 64},
+                       "slots": 4, "max_batch": 256},
             "plain": {"queries": n_plain, "p50_ms": round(float(np.percentile(PL, 50)), 3),
                       "p99_ms": round(float(np.percentile(PL, 99)), 3),
                       "qps": round(n_plain / (time.perf_counter() - start), 1),
                       "form": "one dd_query per query (T=1, host buffers), in arrival order, first %d queries"
                               % n_plain},
-            "preproc_s": round(pre, 2)}
+            "preproc_s": round(pre, 2), "preproc_domains": pre_dom}
 
 
 # ---------------------------------------------------------------- the oracle on the host cores

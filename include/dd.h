@@ -447,9 +447,10 @@ dd_status dd_server_submit(dd_server *sv, int64_t query_id, int32_t mesh, int32_
  * being in host memory.  Returns how many were written (0 if none). */
 int32_t dd_server_poll(dd_server *sv, int32_t max_n, int64_t *ids, int32_t *statuses, double *latency_ms);
 
-/* Copy out and release a completed query: xy host [S][max_pts][2], len and
- * status host [S] (any may be NULL).  Returns the query's status, or
- * DD_ESTATE if it is not complete (or already released). */
+/* Copy out and release a completed query: xy host [S][max_pts][2] (path s
+ * in the first len[s] points of its row; the points past len[s] are left
+ * untouched), len and status host [S] (any may be NULL).  Returns the query's
+ * status, or DD_ESTATE if it is not complete (or already released). */
 dd_status dd_server_take(dd_server *sv, int64_t query_id, float *xy, int32_t *len, int32_t *status);
 
 /* Block until no query is pending or in flight, or timeout_s passed

@@ -204,9 +204,43 @@ float *field_slot(float *dst, uint32_t f_mask, uint32_t bit, int64_t stride) {
     return dst + slot * stride;
 }
 
+// The order in which the exact KL recompute visits the targets: along a
+// Morton (Z-order) curve of their positions, 16 bits per axis over the
+// targets' bounding box, ties by index.
+std::vector<int32_t> morton_order(const DevMesh &m, const int32_t *targets, int32_t T) {
+    float x0 = 3.4e38f, y0 = 3.4e38f, x1 = -3.4e38f, y1 = -3.4e38f;
+    for (int32_t a = 0; a < T; ++a) {
+        const float x = m.xy_h[2 * (size_t)targets[a]], y = m.xy_h[2 * (size_t)targets[a] + 1];
+        x0 = std::min(x0, x);
+        x1 = std::max(x1, x);
+        y0 = std::min(y0, y);
+        y1 = std::max(y1, y);
+    }
+    const float sx = x1 > x0 ? 65535.0f / (x1 - x0) : 0.0f, sy = y1 > y0 ? 65535.0f / (y1 - y0) : 0.0f;
+    auto spread = [](uint32_t v) {   // bits of v at the even positions
+        v &= 0xFFFFu;
+        v = (v | (v << 8)) & 0x00FF00FFu;
+        v = (v | (v << 4)) & 0x0F0F0F0Fu;
+        v = (v | (v << 2)) & 0x33333333u;
+        v = (v | (v << 1)) & 0x55555555u;
+        return v;
+    };
+    std::vector<std::pair<uint32_t, int32_t>> key((size_t)T);
+    for (int32_t a = 0; a < T; ++a) {
+        const uint32_t qx = (uint32_t)((m.xy_h[2 * (size_t)targets[a]] - x0) * sx);
+        const uint32_t qy = (uint32_t)((m.xy_h[2 * (size_t)targets[a] + 1] - y0) * sy);
+        key[a] = {spread(qx) | (spread(qy) << 1), a};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int32_t> order((size_t)T);
+    for (int32_t a = 0; a < T; ++a) order[a] = key[a].second;
+    return order;
+}
+
 // fields of T targets into dst [nf][T][n_v] (device), targets already in scratch
+// (h_targets: the same ids on the host, or null)
 dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t T, uint32_t f_mask, int32_t prec,
-                      float *dst) {
+                      float *dst, const int32_t *h_targets = nullptr) {
     const int64_t stride = (int64_t)T * m.n_v;
     float *kl = field_slot(dst, f_mask, DD_F_KL, stride);
     float *tv = field_slot(dst, f_mask, DD_F_TV, stride);
@@ -239,7 +273,15 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
     if (st != DD_OK) return st;
     float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
     launch_stage_targets(m.P, m.n_v, m.k_pad, d_targets, T, stage, ctx->stream, nullptr, m.LP);
-    if (kl || tv) launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream, -1, m.LP != nullptr);
+    const int32_t *order = nullptr;
+    if (kl && h_targets && T > 2 && !m.xy_h.empty()) {
+        const std::vector<int32_t> o = morton_order(m, h_targets, T);
+        if ((st = upload(ctx, S_ORDER, o.data(), o.size() * sizeof(int32_t))) != DD_OK) return st;
+        order = reinterpret_cast<const int32_t *>(ctx->scratch[S_ORDER]);
+    }
+    if (kl || tv)
+        launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream, -1, m.LP != nullptr,
+                           order);
     if (klt) {
         // the target-weighted KL is the reverse-KL member of the f-divergence kernels
         std::string err;
@@ -501,6 +543,7 @@ dd_status dd_load_mesh(dd_ctx *ctx, const double *xy, int64_t n_v, const int32_t
         if ((st = dev_copy(ctx, m, &m.rb_val, h.rb_val.data(), h.rb_val.size())) != DD_OK) return undo(st);
         m.is_boundary.assign(h.n_v, 0);
         for (int32_t v : h.B) m.is_boundary[v] = 1;
+        m.xy_h.assign(h.xy.begin(), h.xy.end());
         if ((st = dev_copy(ctx, m, &m.isb, m.is_boundary.data(), m.is_boundary.size())) != DD_OK) return undo(st);
         slot.live = true;
         ctx->meshes.push_back(slot);
@@ -669,7 +712,8 @@ dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t
             if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
             dst = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
         }
-        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst);
+        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst,
+                         targets);
         if (st != DD_OK) return st;
         if (sp == 0) {
             CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy fields to host");
@@ -969,7 +1013,8 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
             if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
             dst = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
         }
-        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst);
+        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst,
+                         targets);
         if (st != DD_OK) return st;
         const float *trace_field = field_slot(dst, f_mask, trace_f, (int64_t)T * m->n_v);
         if (sf == 0) {

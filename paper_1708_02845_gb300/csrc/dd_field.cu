@@ -324,7 +324,9 @@ template <int TM, int TN, int RM, int CN>
 struct TileShape {
     static constexpr int ROWG = TM / RM, COLG = TN / CN;
     static_assert(ROWG * COLG == 256, "256 threads");
-    static constexpr size_t smem_bytes = (2 * kTileB * (TM + TN) + 2 * kLogTab) * sizeof(float);
+    // transposed chunk arrays, the raw chunk buffer and the log table
+    static constexpr size_t smem_bytes =
+        (2 * kTileB * (TM + TN) + (kTileB + 4) * (TM + TN) + 2 * kLogTab) * sizeof(float);
 };
 
 // N consecutive floats from shared memory in 16-byte (or 8-byte) loads; src
@@ -371,6 +373,35 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src) {
 // fast_l2 forms from the entry, and for an entry below FLT_MIN with a known
 // logarithm (log2 P from dd_log_poisson_kernel) that logarithm instead of
 // the clamp -- else from the staged entry itself (the multi-domain launch).
+// Data movement (the arithmetic and its order are those of a plain loop over
+// 32-column chunks).  Each chunk of the row tile and of the target tile is
+// fetched by cp.async into a raw buffer (rows of 32 floats at a pitch of 36,
+// so that the transposing reads below hit different banks) while the
+// previous chunk is being summed; after a barrier every thread transposes
+// its share into [column][row] and [column][target] arrays, forming the
+// logarithms on the way, and the tile is summed from there.  The transposed
+// arrays are stored with an XOR swizzle of 4-element groups by column
+// (group ^ (b / F) * (F / 4), F the elements per thread and chunk), so that
+// the threads sharing a row or target write to different banks, while every
+// 4-element group stays contiguous for the 16-byte reads of the sums.
+constexpr int kRawPitch = kTileB + 4;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// position of element e (row or target) at chunk column b in a transposed
+// array of N elements per column, F elements per thread and chunk
+template <int N, int F>
+__device__ __forceinline__ int swz(int e, int b) {
+    constexpr int S = F / 4;                         // 0 for F = 2: no swizzle
+    return ((((e >> 2) ^ ((b / F) * S)) & (N / 4 - 1)) << 2) | (e & 3);
+}
+
 template <int TM, int TN, int RM, int CN, bool KL = true, bool TV = true>
 __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
                                           const float *__restrict__ sP, const float *__restrict__ sL,
@@ -378,13 +409,37 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
                                           float *__restrict__ out_kl, float *__restrict__ out_tv, int64_t x0, int a0,
                                           float *tsm, const float *tab) {
     constexpr int COLG = TN / CN;
-    float (*xP)[TM] = reinterpret_cast<float (*)[TM]>(tsm);
-    float (*xL)[TM] = reinterpret_cast<float (*)[TM]>(tsm + 1 * kTileB * TM);
-    float (*yP)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 2 * kTileB * TM);
-    float (*yL)[TN] = reinterpret_cast<float (*)[TN]>(tsm + 2 * kTileB * TM + 1 * kTileB * TN);
+    constexpr int FR = TM * kTileB / 256;     // row floats per thread per chunk (multiple of 4)
+    constexpr int FT = TN * kTileB / 256;     // target floats per thread per chunk (2, 4 or 8)
+    static_assert(RM % 4 == 0 && FR % 4 == 0, "16-byte row groups");
+    float *xP = tsm;                          // [kTileB][TM], swizzled
+    float *xL = tsm + 1 * kTileB * TM;
+    float *yP = tsm + 2 * kTileB * TM;        // [kTileB][TN], swizzled
+    float *yL = tsm + 2 * kTileB * TM + 1 * kTileB * TN;
+    float *rX = tsm + 2 * kTileB * (TM + TN);   // raw [TM][kRawPitch]
+    float *rY = rX + TM * kRawPitch;            // raw [TN][kRawPitch]
     const int tid = threadIdx.x;
     const int tx = tid % COLG;        // target group: targets tx*CN ..
     const int ty = tid / COLG;        // row group: rows ty*RM ..
+    (void)sL;
+
+    // raw copies of the chunk at column b0: 8 threads per 128-byte row segment
+    auto fetch = [&](int64_t b0) {
+        for (int f = tid; f < TM * 8; f += 256) {
+            const int r = f >> 3, c4 = f & 7;
+            const int64_t x = x0 + r, b = b0 + 4 * c4;
+            const bool ok = x < n_v && b < k_pad;
+            cp_async16(rX + r * kRawPitch + 4 * c4, ok ? P + x * k_pad + b : P, ok);
+        }
+        for (int f = tid; f < TN * 8; f += 256) {
+            const int a = f >> 3, c4 = f & 7;
+            const int ag = a0 + a;
+            const int64_t b = b0 + 4 * c4;
+            const bool ok = ag < T && b < k_pad;
+            cp_async16(rY + a * kRawPitch + 4 * c4, ok ? sP + (int64_t)ag * k_pad + b : sP, ok);
+        }
+        cp_async_commit();
+    };
 
     // two-level summation: 32-term chunk sums, added into the totals with a
     // compensated (Kahan) sum for KL, whose terms partly cancel
@@ -394,71 +449,129 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
 #pragma unroll
         for (int c = 0; c < CN; ++c) kl[r][c] = tv[r][c] = klc[r][c] = 0.0f;
 
-    constexpr int FR = TM * kTileB / 256;     // row floats per thread per chunk (multiple of 4)
-    constexpr int FT = TN * kTileB / 256;     // target floats per thread per chunk (2, 4 or 8)
+    fetch(0);
     for (int64_t b0 = 0; b0 < k_pad; b0 += kTileB) {
+        cp_async_wait_all();
+        __syncthreads();        // the raw chunk has landed; the previous chunk's sums are done
+        {
+            // this thread's columns cb .. cb + FR - 1 share one swizzle: one base offset
+            constexpr int TPR = kTileB / FR;
+            const int r = tid / TPR, cb = (tid % TPR) * FR;
+            float *bx = xP + cb * TM + swz<TM, FR>(r, cb);
+            float *bl = xL + cb * TM + swz<TM, FR>(r, cb);
+#pragma unroll
+            for (int e = 0; e < FR; e += 4) {
+                const float4 v4 = *reinterpret_cast<const float4 *>(rX + r * kRawPitch + cb + e);
+                const float vals[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    bx[(e + q) * TM] = vals[q];
+                    if (KL) bl[(e + q) * TM] = fast_l2(vals[q]);
+                }
+            }
+        }
+        {
+            constexpr int TPT = kTileB / FT;
+            const int a = tid / TPT, cb = (tid % TPT) * FT;
+            const int ag = a0 + a;
+            const int ot = cb * TN + swz<TN, FT>(a, cb);
+#pragma unroll
+            for (int e = 0; e < FT; e += 2) {
+                const float2 p2 = *reinterpret_cast<const float2 *>(rY + a * kRawPitch + cb + e);
+                const float pv[2] = {p2.x, p2.y};
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int b = cb + e + q, o = ot + (e + q) * TN;
+                    yP[o] = pv[q];
+                    if (KL) {
+                        if (sF) {
+                            // staged exponent and mantissa log2 (entries below FLT_MIN with a known log)
+                            float ev = 12583039.0f, fv = 0.0f;
+                            if (ag < T && b0 + b < k_pad) {
+                                ev = __ldg(sE + (int64_t)ag * k_pad + b0 + b);
+                                fv = __ldg(sF + (int64_t)ag * k_pad + b0 + b);
+                            }
+                            yL[o] = __fadd_rn(__fsub_rn(ev, 12583039.0f), fv);
+                        } else {
+                            yL[o] = fast_l2(fmaxf(pv[q], FLT_MIN));
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();        // the chunk is transposed; the raw buffer is free
+        if (b0 + kTileB < k_pad) fetch(b0 + kTileB);
         float ckl[RM][CN], ctv[RM][CN];
 #pragma unroll
         for (int r = 0; r < RM; ++r)
 #pragma unroll
             for (int c = 0; c < CN; ++c) ckl[r][c] = ctv[r][c] = 0.0f;
-        {
-            const int r = tid / (kTileB / FR), cb = (tid % (kTileB / FR)) * FR;
-            const int64_t x = x0 + r;
+        // columns in groups of G, inside which both swizzles are constant: the
+        // swizzled offsets are formed once per group, the columns' addresses
+        // are then fixed offsets from them
+        constexpr int GR = FR >= kTileB ? kTileB : FR;                  // rows: constant over GR columns
+        constexpr int GT = (FT < 4 || FT >= kTileB) ? kTileB : FT;     // targets (FT = 2: no swizzle)
+        constexpr int G = GR < GT ? GR : GT;
+#pragma unroll 1
+        for (int bb = 0; bb < kTileB; bb += G) {
+            int ro[RM / 4], co[CN % 4 == 0 ? CN / 4 : 1];
 #pragma unroll
-            for (int e = 0; e < FR; e += 4) {
-                float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (x < n_v && b0 + cb + e < k_pad)
-                    v4 = __ldg(reinterpret_cast<const float4 *>(P + x * k_pad + b0 + cb + e));
-                const float vals[4] = {v4.x, v4.y, v4.z, v4.w};
+            for (int i = 0; i < RM / 4; ++i) ro[i] = bb * TM + swz<TM, FR>(ty * RM + 4 * i, bb);
+            if constexpr (CN % 4 == 0) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    xP[cb + e + q][r] = vals[q];
-                    if (KL) xL[cb + e + q][r] = fast_l2(vals[q]);
-                }
+                for (int i = 0; i < CN / 4; ++i) co[i] = bb * TN + swz<TN, FT>(tx * CN + 4 * i, bb);
+            } else {
+                static_assert(CN == 2 && FT == 2, "micro-tile widths 2 (unswizzled), 4, 8");
+                co[0] = bb * TN + tx * CN;
             }
-        }
-        {
-            const int a = tid / (kTileB / FT), cb = (tid % (kTileB / FT)) * FT;
-            const int ag = a0 + a;
 #pragma unroll
-            for (int e = 0; e < FT; e += 2) {
-                float2 p2 = make_float2(0.f, 0.f);
-                if (ag < T && b0 + cb + e < k_pad)
-                    p2 = __ldg(reinterpret_cast<const float2 *>(sP + (int64_t)ag * k_pad + b0 + cb + e));
-                yP[cb + e][a] = p2.x;
-                yP[cb + e + 1][a] = p2.y;
-                if (KL) {
-                    if (sF) {
-                        float2 e2 = make_float2(12583039.0f, 12583039.0f), f2 = make_float2(0.f, 0.f);
-                        if (ag < T && b0 + cb + e < k_pad) {
-                            e2 = __ldg(reinterpret_cast<const float2 *>(sE + (int64_t)ag * k_pad + b0 + cb + e));
-                            f2 = __ldg(reinterpret_cast<const float2 *>(sF + (int64_t)ag * k_pad + b0 + cb + e));
-                        }
-                        yL[cb + e][a] = __fadd_rn(__fsub_rn(e2.x, 12583039.0f), f2.x);
-                        yL[cb + e + 1][a] = __fadd_rn(__fsub_rn(e2.y, 12583039.0f), f2.y);
-                    } else {
-                        yL[cb + e][a] = fast_l2(fmaxf(p2.x, FLT_MIN));
-                        yL[cb + e + 1][a] = fast_l2(fmaxf(p2.y, FLT_MIN));
+            for (int j = 0; j < G; ++j) {
+                float rP[RM], rL[RM], cP[CN], cL[CN];
+#pragma unroll
+                for (int i = 0; i < RM / 4; ++i) {
+                    const float4 p4 = *reinterpret_cast<const float4 *>(xP + ro[i] + j * TM);
+                    rP[4 * i] = p4.x;
+                    rP[4 * i + 1] = p4.y;
+                    rP[4 * i + 2] = p4.z;
+                    rP[4 * i + 3] = p4.w;
+                    if (KL) {
+                        const float4 l4 = *reinterpret_cast<const float4 *>(xL + ro[i] + j * TM);
+                        rL[4 * i] = l4.x;
+                        rL[4 * i + 1] = l4.y;
+                        rL[4 * i + 2] = l4.z;
+                        rL[4 * i + 3] = l4.w;
                     }
                 }
-            }
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int b = 0; b < kTileB; ++b) {
-            float rP[RM], rL[RM], cP[CN], cL[CN];
-            lds_vec(rP, &xP[b][ty * RM]);
-            if (KL) lds_vec(rL, &xL[b][ty * RM]);
-            if (TV) lds_vec(cP, &yP[b][tx * CN]);
-            if (KL) lds_vec(cL, &yL[b][tx * CN]);
+                if constexpr (CN % 4 == 0) {
 #pragma unroll
-            for (int r = 0; r < RM; ++r)
-#pragma unroll
-                for (int c = 0; c < CN; ++c) {
-                    if (KL) ckl[r][c] = __fmaf_rn(rP[r], __fadd_rn(rL[r], -cL[c]), ckl[r][c]);
-                    if (TV) ctv[r][c] = __fadd_rn(ctv[r][c], fabsf(__fadd_rn(rP[r], -cP[c])));
+                    for (int i = 0; i < CN / 4; ++i) {
+                        if (TV) {
+                            const float4 p4 = *reinterpret_cast<const float4 *>(yP + co[i] + j * TN);
+                            cP[4 * i] = p4.x;
+                            cP[4 * i + 1] = p4.y;
+                            cP[4 * i + 2] = p4.z;
+                            cP[4 * i + 3] = p4.w;
+                        }
+                        if (KL) {
+                            const float4 l4 = *reinterpret_cast<const float4 *>(yL + co[i] + j * TN);
+                            cL[4 * i] = l4.x;
+                            cL[4 * i + 1] = l4.y;
+                            cL[4 * i + 2] = l4.z;
+                            cL[4 * i + 3] = l4.w;
+                        }
+                    }
+                } else {
+                    if (TV) lds_vec(cP, yP + co[0] + j * TN);
+                    if (KL) lds_vec(cL, yL + co[0] + j * TN);
                 }
+#pragma unroll
+                for (int r = 0; r < RM; ++r)
+#pragma unroll
+                    for (int c = 0; c < CN; ++c) {
+                        if (KL) ckl[r][c] = __fmaf_rn(rP[r], __fadd_rn(rL[r], -cL[c]), ckl[r][c]);
+                        if (TV) ctv[r][c] = __fadd_rn(ctv[r][c], fabsf(__fadd_rn(rP[r], -cP[c])));
+                    }
+            }
         }
 #pragma unroll
         for (int r = 0; r < RM; ++r)
@@ -470,8 +583,8 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
                 kl[r][c] = t;
                 tv[r][c] = __fadd_rn(tv[r][c], ctv[r][c]);
             }
-        __syncthreads();
     }
+    __syncthreads();            // the transposed arrays may be refilled by the next tile of this CTA
 #pragma unroll
     for (int r = 0; r < RM; ++r) {
         const int64_t x = x0 + ty * RM + r;
@@ -492,14 +605,16 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
 // in the exact split form by the whole warp.  The rows around a target are
 // neighbours in vertex order, so the stride spreads them over many groups;
 // groups are dealt round-robin over the warps of the grid, consecutive groups
-// to different CTAs.
+// to different CTAs.  Targets are visited in q.order when given: the warps in
+// flight then work on a few targets close to each other, whose flagged rows
+// largely coincide, so a row read from DRAM for one serves the next from L2.
 __device__ __forceinline__ void fix_problem(const BatchProblem &q, int64_t wid, int64_t nw, int64_t &base,
                                             const float *tab, int lane) {
     if (!q.out_kl || q.T <= 0 || q.n_v <= 0) return;
     const int64_t groups = (q.n_v + 31) / 32, total = groups * q.T;
     const int nvec = (int)(q.k_pad >> 2);
     for (int64_t g = (wid + nw - base % nw) % nw; g < total; g += nw) {
-        const int a = (int)(g / groups);
+        const int a = q.order ? q.order[g / groups] : (int)(g / groups);
         const int64_t g0 = g % groups, x = g0 + lane * groups;
         float *row = q.out_kl + (int64_t)a * q.n_v;
         const bool low = x < q.n_v && row[x] < kTileExactBelow;
@@ -549,7 +664,7 @@ __global__ void __launch_bounds__(256, 2) field_tile_kernel(const float *__restr
                                                          int32_t T, float *__restrict__ out_kl,
                                                          float *__restrict__ out_tv) {
     extern __shared__ __align__(16) float tsm[];
-    float *tab = tsm + 2 * kTileB * (TM + TN);
+    float *tab = tsm + 2 * kTileB * (TM + TN) + (kTileB + 4) * (TM + TN);
     build_log_table(tab);
     __syncthreads();
     tile_body<TM, TN, RM, CN, KL, TV>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, (int64_t)blockIdx.x * TM,
@@ -733,7 +848,8 @@ void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int3
 }
 
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, float *out_kl,
-                        float *out_tv, int *err_flag, cudaStream_t s, int variant, bool staged_logs) {
+                        float *out_tv, int *err_flag, cudaStream_t s, int variant, bool staged_logs,
+                        const int32_t *order) {
     const float *sP = reinterpret_cast<const float *>(stage);
     const float *sL = sP + (int64_t)T * k_pad;
     const float *sE = sL + (int64_t)T * k_pad;
@@ -765,7 +881,7 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
                       : tune_variant(P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s);
     launch_variant(v, P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s);
     if (out_kl) {
-        const BatchProblem q{P, n_v, k_pad, sP, sL, sE, T, v, out_kl, nullptr};
+        const BatchProblem q{P, n_v, k_pad, sP, sL, sE, T, v, out_kl, nullptr, order};
         KMark km_("fix_kl_kernel", s);
         fix_kl_kernel<<<(unsigned)(num_sms() * 4), 256, 0, s>>>(q);
     }
@@ -793,7 +909,7 @@ void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, con
 void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const BatchItem *d_items, int32_t n_items,
                          int32_t *d_counter, cudaStream_t s) {
     if (n_items <= 0) return;
-    const size_t smem = (size_t)2 * kTileB * (256 + 16) * sizeof(float);
+    const size_t smem = (size_t)(2 * kTileB + kTileB + 4) * (256 + 16) * sizeof(float);
     cudaFuncSetAttribute(batch_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tile_kernel, 256, smem);

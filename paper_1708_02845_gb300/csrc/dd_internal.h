@@ -77,6 +77,7 @@ struct DevMesh {
     int64_t bytes = 0;
     std::vector<void *> owned;
     std::vector<uint8_t> is_boundary;  // host copy: vertex flags
+    std::vector<float> xy_h;           // host copy: vertex positions [n_v][2]
     std::vector<int32_t> vn_off_h, vn_h;
 };
 
@@ -106,9 +107,12 @@ void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int3
 // run timed launches the first time a size class is seen).  staged_logs: the
 // staging took logarithms from log2 P (launch_stage_targets with LP), which
 // the tile kernel then reads instead of forming them from the staged entries.
+// order: null, or device [T], the order in which the exact recompute after the
+// tile pass visits the targets (spatially close targets one after the other
+// share the rows they recompute through L2).
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T,
                         float *out_kl, float *out_tv, int *err_flag, cudaStream_t s, int variant = -1,
-                        bool staged_logs = false);
+                        bool staged_logs = false, const int32_t *order = nullptr);
 // One problem of a multi-domain field launch, and one output tile of it.
 struct BatchProblem {
     const float *P;
@@ -116,6 +120,7 @@ struct BatchProblem {
     const float *sP, *sL, *sE;   // staged targets [T][k_pad] each
     int32_t T, variant;          // targets; tile shape (0: 64x64, 1: 128x32, 2: 256x16)
     float *out_kl, *out_tv;      // [T][n_v] each (either may be null)
+    const int32_t *order;        // null, or [T]: the order in which the exact recompute visits the targets
 };
 struct BatchItem {
     int32_t prob, x_tile, a_tile, pad;
@@ -196,7 +201,8 @@ void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t
                         const int32_t *d_path_target = nullptr, int64_t n_paths = 0);
 
 // ---------------------------------------------------------------- context
-enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_META, S_COUNT };
+enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_META, S_ORDER,
+                 S_COUNT };
 
 struct MeshSlot {
     bool live = false;

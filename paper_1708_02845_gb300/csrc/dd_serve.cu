@@ -6,8 +6,8 @@
 // forms a batch from the queries that have arrived (arrival order, as many as
 // fit the slot's device arena and max_batch), groups them by mesh and runs
 //   staging of all targets -> one persistent field launch over every mesh's
-//   tiles -> one tracer launch over all paths -> copy of the paths to pinned
-//   host memory,
+//   tiles -> one tracer launch over all paths -> copy of each path's
+//   defined prefix to pinned host memory,
 // all on the slot's stream, so a batch formed from later arrivals overlaps on
 // the device with batches already running.  Completion is detected with an
 // event; the query's latency is the time from submission to its paths being
@@ -44,7 +44,7 @@ struct Query {
     std::vector<int32_t> sources;
     double t_submit = 0, t_done = 0;
     int32_t err = 0;
-    std::vector<float> xy;                  // [S][max_pts][2]
+    std::vector<float> xy;                  // the paths' defined points, path after path (len[s] points each)
     std::vector<int32_t> len, status;       // [S]
     size_t need = 0;                        // device bytes in a batch
 };
@@ -59,6 +59,7 @@ struct Slot {
     uint8_t *pin_in = nullptr;
     size_t pin_in_cap = 0;
     uint8_t *pin_out = nullptr;
+    uint8_t *pin_out_dev = nullptr;         // pin_out's device address (the path copy kernel writes there)
     size_t pin_out_cap = 0;
     size_t out_xy_off = 0, out_len_off = 0, out_st_off = 0;   // within pin_out
 };
@@ -229,7 +230,13 @@ bool launch_batch(dd_server *sv, Slot &sl) {
     sl.out_len_off = al((size_t)n_paths * sv->max_pts * 8);
     sl.out_st_off = sl.out_len_off + al(n_paths * 4);
     if (e == cudaSuccess && sl.out_st_off + al(n_paths * 4) > sl.pin_out_cap) e = cudaErrorMemoryAllocation;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.pin_out, d + o_xy, (size_t)n_paths * sv->max_pts * 8, cudaMemcpyDeviceToHost, s);
+    // each path's defined prefix only (one warp per path writes it through the
+    // pinned buffer's device address), then the lengths and statuses
+    if (e == cudaSuccess) {
+        launch_copy_paths(reinterpret_cast<const float2 *>(d + o_xy), reinterpret_cast<const int32_t *>(d + o_len),
+                          n_paths, sv->max_pts, reinterpret_cast<float2 *>(sl.pin_out_dev), s);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.pin_out + sl.out_len_off, d + o_len, n_paths * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sl.pin_out + sl.out_st_off, d + o_st, n_paths * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, s);
@@ -250,7 +257,15 @@ void retire(dd_server *sv, Slot &sl) {
     const int32_t *ln = reinterpret_cast<const int32_t *>(sl.pin_out + sl.out_len_off);
     const int32_t *st = reinterpret_cast<const int32_t *>(sl.pin_out + sl.out_st_off);
     for (Query *q : sl.qs) {
-        q->xy.assign(xy + pth * sv->max_pts * 2, xy + (pth + q->S) * sv->max_pts * 2);
+        size_t pts = 0;
+        for (int32_t s = 0; s < q->S; ++s) pts += (size_t)std::max(0, std::min(ln[pth + s], sv->max_pts));
+        q->xy.resize(2 * pts);
+        float *o = q->xy.data();
+        for (int32_t s = 0; s < q->S; ++s) {
+            const size_t np = (size_t)std::max(0, std::min(ln[pth + s], sv->max_pts));
+            std::memcpy(o, xy + (pth + s) * (size_t)sv->max_pts * 2, np * 2 * sizeof(float));
+            o += 2 * np;
+        }
         q->len.assign(ln + pth, ln + pth + q->S);
         q->status.assign(st + pth, st + pth + q->S);
         pth += q->S;
@@ -366,7 +381,8 @@ dd_status dd_server_create(dd_ctx *ctx, int64_t budget_bytes, int32_t n_slots, i
             sl.pin_in_cap = std::min<size_t>(per, (size_t)64 << 20);
             sl.pin_out_cap = std::min<size_t>(per, (size_t)1 << 30);
             if (cudaMallocHost((void **)&sl.pin_in, sl.pin_in_cap) != cudaSuccess ||
-                cudaMallocHost((void **)&sl.pin_out, sl.pin_out_cap) != cudaSuccess)
+                cudaMallocHost((void **)&sl.pin_out, sl.pin_out_cap) != cudaSuccess ||
+                cudaHostGetDevicePointer((void **)&sl.pin_out_dev, sl.pin_out, 0) != cudaSuccess)
                 throw std::bad_alloc();
         }
         sv->worker = std::thread(worker_loop, sv);
@@ -451,7 +467,14 @@ dd_status dd_server_take(dd_server *sv, int64_t query_id, float *xy, int32_t *le
     }
     const dd_status st = (dd_status)q->err;
     if (st == DD_OK) {
-        if (xy) std::memcpy(xy, q->xy.data(), q->xy.size() * sizeof(float));
+        if (xy) {
+            const float *p = q->xy.data();
+            for (int32_t s = 0; s < q->S; ++s) {
+                const size_t np = (size_t)std::max(0, std::min(q->len[s], sv->max_pts));
+                std::memcpy(xy + (size_t)s * sv->max_pts * 2, p, np * 2 * sizeof(float));
+                p += 2 * np;
+            }
+        }
         if (len) std::memcpy(len, q->len.data(), q->len.size() * sizeof(int32_t));
         if (status) std::memcpy(status, q->status.data(), q->status.size() * sizeof(int32_t));
     }

@@ -282,8 +282,9 @@ def test_kernel_timing_hook(env):
     for _ in range(3):
         dd.dd_query(ctx, mid, targets, src, 3, dd.DD_PREC_FP32, dd.DD_F_KL, 512, f, xy, ln, st)
     got = dd.dd_kernel_timing(ctx, 0)
-    for name in ("stage_targets_kernel", "field_tile_kernel", "fix_kl_kernel", "rates_kernel", "trace_kernel"):
+    for name in ("stage_targets_kernel", "field_tile_kernel", "fix_kl_kernel", "trace_kernel"):
         assert got[name][0] == 3 and got[name][1] > 0.0, (name, got)
+    assert "rates_kernel" not in got        # few paths per field: the walk forms the rates it needs
     dd.dd_query(ctx, mid, targets, src, 3, dd.DD_PREC_FP32, dd.DD_F_KL, 512, f, xy, ln, st)
     assert dd.dd_kernel_timing(ctx, 2) == {}
     dd.dd_unload_mesh(ctx, mid)
