@@ -493,7 +493,7 @@ def run_ours(args, rank, world, local_rank):
     ctx = dd.dd_create(local_rank, stream.cuda_stream)
     pk, pk_kind = peaks()
     flush = torch.empty((256 << 20) // 4, dtype=torch.float32, device=dev)
-    if args.section in ("grid450", "batch", "serve", "census", "mid", "grid140"):
+    if args.section in ("grid450", "batch", "serve", "census", "mid", "grid140", "maze"):
         if args.section == "grid450":
             st_sec, gm_sec = grid450_sections(dd, ctx, dev, stream, flush, pk, pk_kind)
             out = {"metric": "grid450 sections only", "stream": st_sec, "gemm": gm_sec}
@@ -502,6 +502,8 @@ def run_ours(args, rank, world, local_rank):
             out["metric"] = "grid140 step only"
         elif args.section == "batch":
             out = {"metric": "batch64 section only", "batch": batch_section(dd, ctx, dev, stream, flush, args)}
+        elif args.section == "maze":
+            out = {"metric": "maze section only", "maze": maze_section(dd, ctx, dev)}
         elif args.section == "census":
             out = {"metric": "census section only", "census": census_section(dd, ctx, dev)}
         elif args.section == "mid":
@@ -533,6 +535,7 @@ def run_ours(args, rank, world, local_rank):
                                                            "clocks", "recompute_over_tile") if kk in g140["line"]}
         del g140
         torch.cuda.empty_cache()
+        line["maze"] = maze_section(dd, ctx, dev)
         line["batch"] = batch_section(dd, ctx, dev, stream, flush, args)
         line["serve"] = serve_section(dd, ctx, args, n_domains=5, seconds=3.0)
         line["census"] = census_section(dd, ctx, dev)
@@ -739,6 +742,58 @@ def sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, p
                                                 for f, v in apx.items()}
         res["error_sample"] = "%d sampled rows x %d targets, FP64 oracle rows, relative with floor 1e-2" % (R, nt)
     return res
+
+
+def maze_section(dd, ctx, dev, n_targets: int = 64):
+    """log P on a maze-like domain (Section V, Precision): a serpentine
+    corridor of 6 x 4 x 40 cells whose kernel reaches 1e-76.  The device
+    solve, the full-precision refinement (sweeps, seconds), and the FP32 KL
+    and TV fields of targets spread over the maze against the oracle's
+    subtraction-free kernel, before the refinement (log P[t,b] evaluated at
+    FLT_MIN where FP32 P is 0) and after it."""
+    import torch
+    from oracle.divergence import kl_field_fast, tv_field
+    from oracle.logpoisson import poisson_subtraction_free
+    from synthetic.meshes import serpentine
+    mesh = serpentine(6, 4, 40)
+    t0 = time.perf_counter()
+    P = poisson_subtraction_free(mesh.xy, mesh.tri, mesh.loops)
+    oracle_s = time.perf_counter() - t0
+    interior = np.nonzero(~mesh.boundary_flags())[0]
+    targets = [int(interior[i]) for i in np.linspace(0, len(interior) - 1, n_targets).astype(int)]
+    idx, off = mesh.loop_arrays()
+    mid = dd.dd_load_mesh(ctx, mesh.xy, mesh.tri, idx, off)
+    t0 = time.perf_counter()
+    dd.dd_poisson_kernel(ctx, mid, 1e-15, 40000)
+    pcg_s = time.perf_counter() - t0
+    out = torch.empty((2, len(targets), mesh.n_v), dtype=torch.float32, device=dev)
+
+    def errors():
+        dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, out)
+        g = out.cpu().numpy().astype(np.float64)
+        ek, et = [], []
+        for a, t in enumerate(targets):
+            rk, rt = kl_field_fast(P, P[t]), tv_field(P, P[t])
+            fin = np.isfinite(rk)
+            ek.append(np.max(np.abs(g[0, a][fin] - rk[fin]) / np.maximum(np.abs(rk[fin]), 1e-2)))
+            et.append(np.max(np.abs(g[1, a] - rt) / np.maximum(np.abs(rt), 1e-2)))
+        return {"kl_max": float(np.max(ek)), "kl_median": float(np.median(ek)), "tv_max": float(np.max(et))}
+
+    before = errors()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sweeps, change = dd.dd_log_poisson_kernel(ctx, mid, 1e-14, 200000)
+    refine_s = time.perf_counter() - t0
+    after = errors()
+    dd.dd_unload_mesh(ctx, mid)
+    pos = P[P > 0]
+    return {"workload": "serpentine maze 6 x 4 x 40 cells: n=%d, k=%d; %d targets spread over the interior"
+                        % (mesh.n_v, sum(len(l) for l in mesh.loops), len(targets)),
+            "kernel_min": float(pos.min()), "share_below_flt_min": round(float(np.mean(pos < 1.1754944e-38)), 4),
+            "pcg_seconds": round(pcg_s, 3), "refine": {"sweeps": sweeps, "last_change": change,
+                                                       "seconds": round(refine_s, 3)},
+            "fields_vs_oracle_before_refinement": before, "fields_vs_oracle_after_refinement": after,
+            "tolerance": "1e-5 relative, floor 1e-2", "oracle_seconds": round(oracle_s, 2)}
 
 
 def mid_section(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 8):
@@ -1278,11 +1333,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-errors", dest="oracle_errors", action="store_false",
                     help="skip the error of the step's results against the FP64 oracle")
-    ap.add_argument("--section", choices=["all", "step", "grid140", "grid450", "batch", "serve", "census", "mid"],
+    ap.add_argument("--section", choices=["all", "step", "grid140", "grid450", "batch", "serve", "census", "mid",
+                                          "maze"],
                     default="all",
                     help="step: only the grid450 query step (with its split-BF16 form and oracle errors); grid140, "
                          "grid450 (single-target, sparse, other-divergence and GEMM passes), batch, serve, census, "
-                         "mid (a grid300 case small enough for full ncu captures): only that part")
+                         "mid (a grid300 case small enough for full ncu captures), maze (log P): only that part")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
