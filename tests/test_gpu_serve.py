@@ -60,3 +60,60 @@ def test_served_equals_alone():
         if sv is not None:
             dd.dd_server_destroy(sv)
         dd.dd_destroy(ctx)
+
+
+def test_arrivals_join_while_batches_run():
+    """Queries submitted while earlier batches are on the device (some of the
+    first wave done, others not yet) are served, and each result equals the
+    query computed alone."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import time
+    dd, ctx = ctx_and_lib()
+    sv = None
+    try:
+        wl = workloads.grid140(T=1, S=1)
+        mid = load(dd, ctx, wl.mesh)
+        dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
+        dd.dd_sync(ctx)
+        mp = 2048
+        sv = dd.dd_server_create(ctx, 2 << 30, n_slots=2, max_batch=4, max_pts=mp)
+        interior = np.nonzero(~wl.mesh.boundary_flags())[0]
+        rng = SplitMix64(4096)
+
+        def draw(qid):
+            t = int(interior[rng.choice(len(interior))])
+            src = np.asarray([int(interior[rng.choice(len(interior))]) for _ in range(1 + rng.choice(32))], np.int32)
+            return qid, t, src
+
+        wave1 = [draw(q) for q in range(64)]
+        for qid, t, src in wave1:
+            assert dd.dd_server_submit(sv, qid, mid, t, src) == dd.DD_OK
+        done = {}
+        t0 = time.perf_counter()
+        while not done and time.perf_counter() - t0 < 60.0:
+            ids, sts, _ = dd.dd_server_poll(sv)
+            done.update(zip(ids.tolist(), sts.tolist()))
+        assert 0 < len(done) < len(wave1)          # the first wave is partly served, partly in flight
+        wave2 = [draw(q) for q in range(100, 124)]
+        for qid, t, src in wave2:
+            assert dd.dd_server_submit(sv, qid, mid, t, src) == dd.DD_OK
+        dd.dd_server_wait_idle(sv, 120.0)
+        ids, sts, _ = dd.dd_server_poll(sv)
+        done.update(zip(ids.tolist(), sts.tolist()))
+        assert sorted(done) == sorted(q for q, _, _ in wave1 + wave2) and all(v == 0 for v in done.values())
+        h = mean_edge(wl.mesh)
+        for qid, t, src in wave1 + wave2:
+            S = len(src)
+            xy, ln, st = dd.dd_server_take(sv, qid, S, mp)
+            axy = np.zeros((S, mp, 2), np.float32)
+            aln = np.zeros(S, np.int32)
+            ast = np.zeros(S, np.int32)
+            dd.dd_trace(ctx, mid, t, dd.DD_F_KL, src, mp, axy, aln, ast)
+            for s in range(S):
+                assert st[s] == ast[s]
+                assert hausdorff(xy[s, :ln[s]], axy[s, :aln[s]], h / 10) <= 0.5 * h
+    finally:
+        if sv is not None:
+            dd.dd_server_destroy(sv)
+        dd.dd_destroy(ctx)
