@@ -68,20 +68,46 @@ __device__ __forceinline__ float alpha_bracket(float L, float e) {
 enum { kChi2 = DD_DIV_CHI2, kHell = DD_DIV_HELLINGER, kPow = DD_DIV_POWER, kAlpha = DD_DIV_ALPHA,
        kKlRev = DD_DIV_KL_REVERSE };
 
+// Hardware approximations (one MUFU instruction each; relative errors of a
+// few 2^-23, absolute error of lg2 a few 1e-7).  The chi2, Hellinger and power
+// terms are non-negative, so the relative error of every term, and of the
+// row's sum, stays at that level -- far inside the 1e-5 of the FP32 path.
+__device__ __forceinline__ float rcp_hw(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_hw(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_hw(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_hw(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <int FAM>
 __device__ __forceinline__ float fterm(float px, float pt, float lmt, float Ebt, const FdParams &q, const float *tab) {
     if (FAM == kChi2) {
         const float d = pt - px;
-        return d * d / fmaxf(px, FLT_MIN);
+        return d * d * rcp_hw(fmaxf(px, FLT_MIN));
     } else if (FAM == kHell) {
-        const float d = pt - px, s = sqrtf(pt) + sqrtf(px);
+        const float d = pt - px, s = sqrt_hw(pt) + sqrt_hw(px);
         if (s == 0.0f) return 0.0f;
-        const float r = d / s;
+        const float r = d * rcp_hw(s);
         return r * r;
     } else if (FAM == kPow) {
+        // |d| (|d| / P_x)^(p-1) = |d| 2^((p-1) log2(|d| / P_x))
         const float ad = fabsf(pt - px);
-        if (ad == 0.0f) return 0.0f;
-        return ad * powf(ad / fmaxf(px, FLT_MIN), q.p - 1.0f);
+        if (ad == 0.0f || q.p == 1.0f) return ad;      // p = 1: TV's term, also where P_x = 0
+        return ad * ex2_hw((q.p - 1.0f) * lg2_hw(ad * rcp_hw(fmaxf(px, FLT_MIN))));
     } else if (FAM == kAlpha) {
         if (px == 0.0f) return pt == 0.0f ? 0.0f : (q.alpha_gt1 ? INFINITY : q.lin * pt);
         return px * q.lin * alpha_bracket(log_ratio(px, lmt, Ebt, tab), q.p);
@@ -169,6 +195,94 @@ __global__ void __launch_bounds__(256) fdiv_kernel(const float *__restrict__ P, 
     }
 }
 
+// The reverse KL (the target-weighted KL of dd_distance's DD_F_KLT) in two
+// passes, as the streaming KL kernel: a first pass per element
+//   P_t ((lg2 m_t - lg2 m_x) + (E_t - E_x))      (times ln2 at the end)
+// with exact exponents and hardware mantissa logs, within ln2 *
+// DD_FAST_LOG_SPREAD * sum_b P[t,b] = 3.5e-7 of the exact form (the constant
+// part of the mantissa log's error cancels between the two sides), then every
+// row whose first-pass value is below DD_EXACT_BELOW -- the rows around the
+// target, x = t among them -- recomputed by its warp with the table
+// logarithm (fterm), so every value keeps 1e-5 relative accuracy.  A row
+// entry P[x,b] = 0 is taken at FLT_MIN on both passes.  Shared memory: the
+// target's P, table mantissa log, biased exponent and hardware mantissa log2.
+__global__ void __launch_bounds__(256) klrev_two_pass_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
+                                                            const float *__restrict__ sP, const float *__restrict__ sL,
+                                                            const float *__restrict__ sE, const float *__restrict__ sF,
+                                                            float *__restrict__ out) {
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ float tab[2 * kLogTab];
+    float *tP = fsm, *tL = fsm + k_pad, *tE = fsm + 2 * k_pad, *tF = fsm + 3 * k_pad;
+    const int a = blockIdx.y;
+    for (int64_t b = threadIdx.x; b < k_pad; b += blockDim.x) {
+        tP[b] = sP[(int64_t)a * k_pad + b];
+        tL[b] = sL[(int64_t)a * k_pad + b];
+        tE[b] = sE[(int64_t)a * k_pad + b];
+        tF[b] = sF[(int64_t)a * k_pad + b];
+    }
+    build_log_table(tab);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nvec = (int)(k_pad >> 2);
+    const FdParams q{};
+    for (int64_t x = warp; x < n_v; x += nwarps) {
+        const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int c0 = 0; c0 < nvec; c0 += 128) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u * 32 + lane;
+                v[u] = c < nvec ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u * 32 + lane;
+                if (c >= nvec) break;
+                const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
+                const float4 f4 = reinterpret_cast<const float4 *>(tF)[c];
+                const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
+                const float px[4] = {v[u].x, v[u].y, v[u].z, v[u].w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
+                const float ft[4] = {f4.x, f4.y, f4.z, f4.w}, et[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int bits = __float_as_int(fmaxf(px[e], FLT_MIN));
+                    const float lf = lg2_mant(bits);
+                    const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
+                    const float t = pt[e] * __fadd_rn(__fadd_rn(ft[e], -lf), __fadd_rn(et[e], -eb));
+                    if (e & 1)
+                        s1 += t;
+                    else
+                        s0 += t;
+                }
+            }
+        }
+        float s = s0 + s1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        s *= kLn2f;
+        if (s < (float)DD_EXACT_BELOW) {        // warp-uniform: the exact (table) form
+            float r0 = 0.0f, r1 = 0.0f;
+            for (int c = lane; c < nvec; c += 32) {
+                const float4 vx = __ldcg(row + c);
+                const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
+                const float4 l4 = reinterpret_cast<const float4 *>(tL)[c];
+                const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
+                r0 += fterm<kKlRev>(vx.x, p4.x, l4.x, e4.x, q, tab);
+                r1 += fterm<kKlRev>(vx.y, p4.y, l4.y, e4.y, q, tab);
+                r0 += fterm<kKlRev>(vx.z, p4.z, l4.z, e4.z, q, tab);
+                r1 += fterm<kKlRev>(vx.w, p4.w, l4.w, e4.w, q, tab);
+            }
+            s = r0 + r1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        }
+        if (lane == 0) out[(int64_t)a * n_v + x] = s;
+    }
+}
+
 }  // namespace
 
 dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, int32_t family,
@@ -208,6 +322,25 @@ dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *
                                                                    family == DD_DIV_KL_REVERSE ? LP : nullptr);
         }
     };
+    if (family == DD_DIV_KL_REVERSE && !LP) {
+        // two passes (hardware mantissa logs, then the table form near the target)
+        const float *sF = sE + (int64_t)T * k_pad;
+        const size_t smem4 = 4 * (size_t)k_pad * sizeof(float);
+        if (smem4 <= 200 * 1024) {
+            auto kern = klrev_two_pass_kernel;
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem4);
+            if (per_sm < 1) per_sm = 1;
+            int64_t gx = (int64_t)sms * per_sm / (T > 0 ? T : 1);
+            const int64_t rows_blocks = (n_v + 7) / 8;
+            if (gx < 1) gx = 1;
+            if (gx > rows_blocks) gx = rows_blocks;
+            KMark km_("klrev_two_pass_kernel", s);
+            kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem4, s>>>(P, n_v, k_pad, sP, sL, sE, sF, out);
+            return DD_OK;
+        }
+    }
     switch (family) {
         case DD_DIV_CHI2: go(fdiv_kernel<kChi2>); break;
         case DD_DIV_HELLINGER: go(fdiv_kernel<kHell>); break;
