@@ -512,7 +512,7 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
         constexpr int GR = FR >= kTileB ? kTileB : FR;                  // rows: constant over GR columns
         constexpr int GT = (FT < 4 || FT >= kTileB) ? kTileB : FT;     // targets (FT = 2: no swizzle)
         constexpr int G = GR < GT ? GR : GT;
-#pragma unroll 1
+#pragma unroll
         for (int bb = 0; bb < kTileB; bb += G) {
             int ro[RM / 4], co[CN % 4 == 0 ? CN / 4 : 1];
 #pragma unroll
