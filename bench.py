@@ -55,15 +55,18 @@ WORKLOADS = {
                         "+ %dx%d KL paths per step"},
 }
 HEADLINE = "grid450"
-# kernels one dd_query step launches: target staging, field tile, exact KL
-# recompute near the targets, triangle rates, vertex decisions, path walk
+# kernels one dd_query step launches at most: target staging, field tile,
+# exact KL recompute near the targets, triangle rates and vertex decisions
+# (only when 128 or more paths share a field), path walk
 STEP_LAUNCHES = 6
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from
-# ncu captures of the step's kernels; None where no capture of the current
-# kernel exists
+# ncu captures of the step's kernels (means over the captured query steps);
+# absent where no capture of the current kernel exists; used only when the
+# step runs the captured (T, S).  grid450's tile launch reads P once per
+# 64-target column of tiles: 16 x 3.03 GB.
 TRAFFIC = {
-    "grid140": {"field_tile_kernel": 77092352, "trace_kernel": 31522560},
-    "grid450": {},
+    "grid140": {},
+    "grid450": {"T": 1024, "S": 16, "field_tile_kernel": 50092987319, "trace_kernel": 307350638},
 }
 # the same for one field_stream_kernel launch of the grid450 single-target pass
 STREAM_TRAFFIC_BYTES = 3035740160    # 3,032,217,088 read + 3,523,072 written (4 n k_pad = 3.03 GB of P)
@@ -325,6 +328,8 @@ def query_step(dd, ctx, dev, stream, flush, args, rank, world, local_rank, name,
                for kn, (c, ms) in sorted(kernel_ms.items(), key=lambda kv: -kv[1][1])}
     per_launch = {kn: ms / max(c, 1) for kn, (c, ms) in kernel_ms.items()}
     traffic = TRAFFIC.get(name, {})
+    if (traffic.get("T"), traffic.get("S")) != (T, S):
+        traffic = {}
     tile_ms = per_launch.get("field_tile_kernel", field_ms)
     roof_t = roof_tile(n_v, k, T, tile_ms, sms, sm_mhz, traffic.get("field_tile_kernel"))
     walk_ms = per_launch.get("trace_kernel")
