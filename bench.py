@@ -645,7 +645,7 @@ def sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, p
                       dense_klt_ms=None, orows=None):
     """Sparse fields of Section V (each row's entries below 1/sqrt(n) of its
     maximum eliminated), one target per call.  KL~ and TV~ read only the CSR
-    copy of the sparsified P (csr_field_kernel): algorithmic bytes of a call =
+    copy of the sparsified P (csr_stream_kernel): algorithmic bytes of a call =
     6 B per kept entry (value + 16-bit column) + 8 B per row offset + the two
     output fields.  KLT~ reads the dense rows at the target's kept 4-column
     blocks (sparse_field_kernel): 16 B x n x listed blocks + the output.  With
@@ -701,7 +701,7 @@ def sparse_subsection(dd, ctx, dev, stream, flush, mid, n_v, k, k_pad, tl, pk, p
                       "entries, KLT~ over the target row's kept columns, TV~ between the sparsified rows",
            "sparsity": round(1.0 - kept / float(n_v * k), 4), "csr_bytes": int(csr_bytes),
            "dense_bytes": int(4 * n_v * k_pad), "build_seconds": round(build_s, 3),
-           "kl_tv": {"kernel": "csr_field_kernel (+ stage_targets_kernel, sparse_stage_kernel)", "bound": "hbm",
+           "kl_tv": {"kernel": "csr_stream_kernel (+ stage_targets_kernel, sparse_stage_kernel)", "bound": "hbm",
                      "ms_per_field_pair": round(statistics.median(ms_csr), 4), "achieved": round(g_csr, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(g_csr / hbm, 4), "peak_source": pk_kind,
                      "algorithmic_bytes": int(csr_alg),

@@ -1180,7 +1180,9 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
         dmeta = reinterpret_cast<uint8_t *>(ctx->scratch[S_META]);
         launch_batch_fields(reinterpret_cast<const BatchProblem *>(dmeta + o_probs), (int32_t)n_items,
                             reinterpret_cast<const BatchItem *>(dmeta + o_items), (int32_t)order.size(),
-                            reinterpret_cast<int32_t *>(dmeta + o_counter), ctx->stream);
+                            reinterpret_cast<int32_t *>(dmeta + o_counter), ctx->stream,
+                            reinterpret_cast<const int32_t *>(dmeta + o_tprob),
+                            reinterpret_cast<const int32_t *>(dmeta + o_tloc), nT, max_k, max_nv);
         CK(cudaGetLastError(), "batch field launch");
         bool host = false;
         if (sf == 0) {

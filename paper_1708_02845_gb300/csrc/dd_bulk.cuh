@@ -40,7 +40,20 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// true when the phase completed; the thread may first be suspended for up
+// to hint_ns while it has not
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 constexpr uint32_t kWaitLimit = 1u << 25;   // bounded spins of a non-suspending test (about a second)
+constexpr uint32_t kSuspendLimit = 1u << 20;   // bounded suspending polls of at most 1 us each (about a second)
 
 // bounded wait: true when the phase completed; false (error flag set) when the limit expired
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
@@ -50,5 +63,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
     return false;
 }
 
+
+// bounded wait that lets the thread be suspended between polls (no issue
+// slots spent spinning): true when the phase completed; false (error flag
+// set) when the limit expired
+__device__ __forceinline__ bool mbar_wait_suspend(uint64_t *bar, uint32_t parity, int *err) {
+    for (uint32_t i = 0; i < kSuspendLimit; ++i)
+        if (mbar_try(bar, parity, 1000u)) return true;
+    atomicExch(err, 1);
+    return false;
+}
 
 }  // namespace

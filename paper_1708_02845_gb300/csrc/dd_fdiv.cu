@@ -25,6 +25,12 @@
 // One warp per row, lanes along b, 16-byte loads of P four float4 per lane
 // ahead; the target's P, log-mantissa and exponent rows staged in shared
 // memory (the arrays of stage_targets_kernel); one target per grid row.
+// The reverse KL and the alpha family with 0.1 <= |e| <= 2, |1 - e| >= 0.1
+// take a first pass with hardware logarithms (and exp2) and recompute in the
+// exact form above only the rows whose value is below DD_EXACT_BELOW
+// (two_pass_kernel); the other families and parameters take the exact form
+// throughout (fdiv_kernel).
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -39,6 +45,9 @@ struct FdParams {
     float p;         // power: p; alpha: e = (1 + a)/2
     float lin;       // alpha: 2 / (1 - a)
     int alpha_gt1;   // alpha: a > 1
+    float inv_e;     // alpha: 1 / e
+    float below;     // two-pass families: rows whose first-pass value is below this are recomputed
+    float c[6];      // alpha exact form: (1 - e^(n-1)) / n!, n = 2 .. 7
 };
 
 // log(P_t / P_x) from the split logarithms (target side staged)
@@ -48,21 +57,16 @@ __device__ __forceinline__ float log_ratio(float px, float lmt, float Ebt, const
     return __fmaf_rn(__fadd_rn(Ebt, -Eb), kLn2f, __fadd_rn(lmt, -lm));
 }
 
-// expm1(L) - expm1(e L) / e
-__device__ __forceinline__ float alpha_bracket(float L, float e) {
+// expm1(L) - expm1(e L) / e; for |L| < 1/8 its series sum_{n>=2} c_n L^n
+// with c_n = (1 - e^(n-1)) / n! (FP64 on the host), which does not cancel
+__device__ __forceinline__ float alpha_bracket(float L, const FdParams &q) {
     if (fabsf(L) < 0.125f) {
-        // sum_{n>=2} (1 - e^(n-1)) L^n / n!
-        float en = e, s = 0.0f, Ln = L, fact = 1.0f;
+        float s = q.c[5];
 #pragma unroll
-        for (int n = 2; n <= 7; ++n) {
-            Ln *= L;
-            fact *= (float)n;
-            s += (1.0f - en) * Ln / fact;
-            en *= e;
-        }
-        return s;
+        for (int i = 4; i >= 0; --i) s = __fmaf_rn(s, L, q.c[i]);
+        return L * L * s;
     }
-    return expm1f(L) - expm1f(e * L) / e;
+    return expm1f(L) - expm1f(q.p * L) * q.inv_e;
 }
 
 enum { kChi2 = DD_DIV_CHI2, kHell = DD_DIV_HELLINGER, kPow = DD_DIV_POWER, kAlpha = DD_DIV_ALPHA,
@@ -110,7 +114,7 @@ __device__ __forceinline__ float fterm(float px, float pt, float lmt, float Ebt,
         return ad * ex2_hw((q.p - 1.0f) * lg2_hw(ad * rcp_hw(fmaxf(px, FLT_MIN))));
     } else if (FAM == kAlpha) {
         if (px == 0.0f) return pt == 0.0f ? 0.0f : (q.alpha_gt1 ? INFINITY : q.lin * pt);
-        return px * q.lin * alpha_bracket(log_ratio(px, lmt, Ebt, tab), q.p);
+        return px * q.lin * alpha_bracket(log_ratio(px, lmt, Ebt, tab), q);
     } else {   // kKlRev
         if (pt == 0.0f) return 0.0f;
         return pt * log_ratio(px, lmt, Ebt, tab);
@@ -122,6 +126,93 @@ __device__ __forceinline__ float fterm(float px, float pt, float lmt, float Ebt,
 __device__ __forceinline__ float klrev_logp_term(float pt, float lmt, float Ebt, float lx) {
     if (pt == 0.0f) return 0.0f;
     return pt * __fmaf_rn(__fadd_rn(__fsub_rn(Ebt, 12583039.0f), -lx), kLn2f, lmt);
+}
+
+// First-pass alpha terms of four entries per lane, from L2 = log2(P_t / P_x)
+// formed from exact exponents and hardware mantissa logs:
+//   P_x lin [expm1(L) - expm1(e L)/e] = lin [(P_t - P_x) - P_x (2^(e L2) - 1)/e]
+// with the hardware exp2.  Its error is absolute, not relative to the term:
+// |lin| / |e| 2^-22 P_x 2^(e L2) from the exp2, whose sum over b is at most
+// |lin| / |e| 2^-22 (sum_b P_t^e P_x^(1-e) <= 1 for 0 < e < 1, Hoelder; for
+// e > 1 or e < 0 the value itself grows with that sum), plus the log's
+// DD_FAST_LOG_SPREAD, whose effect vanishes to first order at u = 1.  So the
+// rows whose first-pass value is below q.below = max(DD_EXACT_BELOW,
+// 2e5 |lin| / |e| 2^-22) are recomputed in the exact form, and every other
+// value is within 1e-5 / 2 of exact, relatively.  The entries with P_x = 0 or
+// P_t = 0 take their limits by selection, evaluated only when a lane of the
+// warp holds one; every lane of the warp must call it (padding entries pass
+// P_x = P_t = 0 and give 0).
+__device__ __forceinline__ void alpha_fast4(const float (&px)[4], const float (&pt)[4], const float (&ft)[4],
+                                            const float (&et)[4], const FdParams &q, float (&t)[4]) {
+    bool special = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int bits = __float_as_int(fmaxf(px[j], FLT_MIN));
+        const float lf = lg2_mant(bits);
+        const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
+        const float L2 = __fadd_rn(__fadd_rn(ft[j], -lf), __fadd_rn(et[j], -eb));
+        const float ue = ex2_hw(q.p * L2);
+        t[j] = q.lin * __fmaf_rn(-px[j] * q.inv_e, ue - 1.0f, pt[j] - px[j]);
+        special |= px[j] == 0.0f || pt[j] == 0.0f;
+    }
+    if (__any_sync(0xffffffffu, special)) {
+        const float at_px0 = q.alpha_gt1 ? INFINITY : q.lin;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float v = pt[j] == 0.0f ? px[j] * q.inv_e : t[j];                   // u = 0: lin P_x (1/e - 1) = P_x / e
+            v = px[j] == 0.0f ? (pt[j] == 0.0f ? 0.0f : at_px0 * pt[j]) : v;    // P_x = 0: lin P_t, or +inf for a > 1
+            t[j] = v;
+        }
+    }
+}
+
+// Rows x = warp, warp + nwarps, ... of P streamed by one warp in chunks of
+// 32 U float4 (U per lane), with two register buffers: the loads of the next
+// chunk (of this row or the next) are in flight while the current one is
+// computed.  chunk(b, x, c0): the lane's U float4 b of row x, float4 columns
+// c0 + u * 32 + lane (zero past the row's end); done(x): row x is complete.
+template <int U, typename Chunk, typename Done>
+__device__ __forceinline__ void stream_rows(const float *__restrict__ P, int64_t n_v, int64_t k_pad, int64_t warp,
+                                            int64_t nwarps, int lane, Chunk chunk, Done done) {
+    const int nvec = (int)(k_pad >> 2);
+    const int nch = (nvec + 32 * U - 1) / (32 * U);
+    float4 b0[U], b1[U];
+    auto fetch = [&](float4(&b)[U], int64_t x, int ch) {
+        const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = ch * 32 * U + u * 32 + lane;
+            b[u] = c < nvec ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto next = [&](int64_t &x, int &ch) {
+        if (++ch == nch) {
+            ch = 0;
+            x += nwarps;
+        }
+    };
+    int64_t x = warp;
+    int ch = 0;
+    if (x >= n_v) return;
+    fetch(b0, x, 0);
+    for (;;) {
+        int64_t xn = x;
+        int cn = ch;
+        next(xn, cn);
+        if (xn < n_v) fetch(b1, xn, cn);
+        chunk(b0, x, ch * 32 * U);
+        if (cn == 0) done(x);
+        if (xn >= n_v) return;
+        x = xn;
+        ch = cn;
+        next(xn, cn);
+        if (xn < n_v) fetch(b0, xn, cn);
+        chunk(b1, x, ch * 32 * U);
+        if (cn == 0) done(x);
+        if (xn >= n_v) return;
+        x = xn;
+        ch = cn;
+    }
 }
 
 // LP (reverse KL only, may be null): log2 P; an entry whose FP32 value is 0
@@ -146,70 +237,68 @@ __global__ void __launch_bounds__(256) fdiv_kernel(const float *__restrict__ P, 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nvec = (int)(k_pad >> 2);
-    for (int64_t x = warp; x < n_v; x += nwarps) {
-        const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
-        float s0 = 0.0f, s1 = 0.0f;
-        for (int c0 = 0; c0 < nvec; c0 += 128) {
-            float4 v[4];
+    float s0 = 0.0f, s1 = 0.0f;
+    auto chunk = [&](const float4(&v)[4], int64_t x, int c0) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = c0 + u * 32 + lane;
-                v[u] = c < nvec ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * 32 + lane;
+            if (c >= nvec) break;
+            const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
+            const float4 l4 = reinterpret_cast<const float4 *>(tL)[c];
+            const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
+            if (FAM == kKlRev && LP &&
+                ((v[u].x == 0.f && p4.x != 0.f) || (v[u].y == 0.f && p4.y != 0.f) ||
+                 (v[u].z == 0.f && p4.z != 0.f) || (v[u].w == 0.f && p4.w != 0.f))) {
+                const float4 lx = reinterpret_cast<const float4 *>(LP + x * k_pad)[c];
+                const float px[4] = {v[u].x, v[u].y, v[u].z, v[u].w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
+                const float lt[4] = {l4.x, l4.y, l4.z, l4.w}, et[4] = {e4.x, e4.y, e4.z, e4.w};
+                const float l2[4] = {lx.x, lx.y, lx.z, lx.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = c0 + u * 32 + lane;
-                if (c >= nvec) break;
-                const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
-                const float4 l4 = reinterpret_cast<const float4 *>(tL)[c];
-                const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
-                if (FAM == kKlRev && LP &&
-                    ((v[u].x == 0.f && p4.x != 0.f) || (v[u].y == 0.f && p4.y != 0.f) ||
-                     (v[u].z == 0.f && p4.z != 0.f) || (v[u].w == 0.f && p4.w != 0.f))) {
-                    const float4 lx = reinterpret_cast<const float4 *>(LP + x * k_pad)[c];
-                    const float px[4] = {v[u].x, v[u].y, v[u].z, v[u].w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
-                    const float lt[4] = {l4.x, l4.y, l4.z, l4.w}, et[4] = {e4.x, e4.y, e4.z, e4.w};
-                    const float l2[4] = {lx.x, lx.y, lx.z, lx.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float t = (px[e] == 0.f && l2[e] > -INFINITY)
-                                            ? klrev_logp_term(pt[e], lt[e], et[e], l2[e])
-                                            : fterm<FAM>(px[e], pt[e], lt[e], et[e], q, tab);
-                        if (e & 1)
-                            s1 += t;
-                        else
-                            s0 += t;
-                    }
-                    continue;
+                for (int e = 0; e < 4; ++e) {
+                    const float t = (px[e] == 0.f && l2[e] > -INFINITY) ? klrev_logp_term(pt[e], lt[e], et[e], l2[e])
+                                                                       : fterm<FAM>(px[e], pt[e], lt[e], et[e], q, tab);
+                    if (e & 1)
+                        s1 += t;
+                    else
+                        s0 += t;
                 }
-                s0 += fterm<FAM>(v[u].x, p4.x, l4.x, e4.x, q, tab);
-                s1 += fterm<FAM>(v[u].y, p4.y, l4.y, e4.y, q, tab);
-                s0 += fterm<FAM>(v[u].z, p4.z, l4.z, e4.z, q, tab);
-                s1 += fterm<FAM>(v[u].w, p4.w, l4.w, e4.w, q, tab);
+                continue;
             }
+            s0 += fterm<FAM>(v[u].x, p4.x, l4.x, e4.x, q, tab);
+            s1 += fterm<FAM>(v[u].y, p4.y, l4.y, e4.y, q, tab);
+            s0 += fterm<FAM>(v[u].z, p4.z, l4.z, e4.z, q, tab);
+            s1 += fterm<FAM>(v[u].w, p4.w, l4.w, e4.w, q, tab);
         }
-        float s = s0 + s1;
+    };
+    auto done = [&](int64_t x) {
+        float sum = s0 + s1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) out[(int64_t)a * n_v + x] = s;
-    }
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) out[(int64_t)a * n_v + x] = sum;
+        s0 = s1 = 0.0f;
+    };
+    stream_rows<4>(P, n_v, k_pad, warp, nwarps, lane, chunk, done);
 }
 
-// The reverse KL (the target-weighted KL of dd_distance's DD_F_KLT) in two
-// passes, as the streaming KL kernel: a first pass per element
-//   P_t ((lg2 m_t - lg2 m_x) + (E_t - E_x))      (times ln2 at the end)
-// with exact exponents and hardware mantissa logs, within ln2 *
-// DD_FAST_LOG_SPREAD * sum_b P[t,b] = 3.5e-7 of the exact form (the constant
-// part of the mantissa log's error cancels between the two sides), then every
-// row whose first-pass value is below DD_EXACT_BELOW -- the rows around the
-// target, x = t among them -- recomputed by its warp with the table
-// logarithm (fterm), so every value keeps 1e-5 relative accuracy.  A row
-// entry P[x,b] = 0 is taken at FLT_MIN on both passes.  Shared memory: the
-// target's P, table mantissa log, biased exponent and hardware mantissa log2.
-__global__ void __launch_bounds__(256) klrev_two_pass_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
-                                                            const float *__restrict__ sP, const float *__restrict__ sL,
-                                                            const float *__restrict__ sE, const float *__restrict__ sF,
-                                                            float *__restrict__ out) {
+// The reverse KL (the target-weighted KL of dd_distance's DD_F_KLT) and the
+// alpha family in two passes, as the streaming KL kernel.  A first pass per
+// element with exact exponents and hardware mantissa logs:
+//   reverse KL: P_t ((lg2 m_t - lg2 m_x) + (E_t - E_x))   (times ln2 at the end),
+//     within ln2 DD_FAST_LOG_SPREAD sum_b P[t,b] = 3.5e-7 of the exact form
+//     (the constant part of the mantissa log's error cancels between the two
+//     sides);
+//   alpha: alpha_fast_term, within a few 1e-6 of the exact term relatively;
+// then every row whose first-pass value is below DD_EXACT_BELOW -- the rows
+// around the target, x = t among them -- recomputed by its warp with the
+// table logarithm (fterm), so every value keeps 1e-5 relative accuracy.  A
+// row entry P[x,b] = 0 is taken at FLT_MIN on both passes (reverse KL).
+// Shared memory: the target's P, table mantissa log, biased exponent and
+// hardware mantissa log2.
+template <int FAM>
+__global__ void __launch_bounds__(256) two_pass_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
+                                                       const float *__restrict__ sP, const float *__restrict__ sL,
+                                                       const float *__restrict__ sE, const float *__restrict__ sF,
+                                                       FdParams q, float *__restrict__ out) {
     extern __shared__ __align__(16) float fsm[];
     __shared__ float tab[2 * kLogTab];
     float *tP = fsm, *tL = fsm + k_pad, *tE = fsm + 2 * k_pad, *tF = fsm + 3 * k_pad;
@@ -226,61 +315,73 @@ __global__ void __launch_bounds__(256) klrev_two_pass_kernel(const float *__rest
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nvec = (int)(k_pad >> 2);
-    const FdParams q{};
-    for (int64_t x = warp; x < n_v; x += nwarps) {
-        const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
-        float s0 = 0.0f, s1 = 0.0f;
-        for (int c0 = 0; c0 < nvec; c0 += 128) {
-            float4 v[4];
+    float s0 = 0.0f, s1 = 0.0f;
+    auto chunk = [&](const float4(&v)[4], int64_t, int c0) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = c0 + u * 32 + lane;
-                v[u] = c < nvec ? __ldcs(row + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = c0 + u * 32 + lane;
-                if (c >= nvec) break;
-                const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
-                const float4 f4 = reinterpret_cast<const float4 *>(tF)[c];
-                const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * 32 + lane;
+            if (FAM == kAlpha) {
+                // every lane takes part (the first pass votes per group of four entries)
+                const bool in = c < nvec;
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 p4 = in ? reinterpret_cast<const float4 *>(tP)[c] : z;
+                const float4 f4 = in ? reinterpret_cast<const float4 *>(tF)[c] : z;
+                const float4 e4 = in ? reinterpret_cast<const float4 *>(tE)[c] : z;
                 const float px[4] = {v[u].x, v[u].y, v[u].z, v[u].w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
                 const float ft[4] = {f4.x, f4.y, f4.z, f4.w}, et[4] = {e4.x, e4.y, e4.z, e4.w};
+                float t[4];
+                alpha_fast4(px, pt, ft, et, q, t);
+                s0 += t[0];
+                s1 += t[1];
+                s0 += t[2];
+                s1 += t[3];
+                continue;
+            }
+            if (c >= nvec) break;
+            const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
+            const float4 f4 = reinterpret_cast<const float4 *>(tF)[c];
+            const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
+            const float px[4] = {v[u].x, v[u].y, v[u].z, v[u].w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
+            const float ft[4] = {f4.x, f4.y, f4.z, f4.w}, et[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int bits = __float_as_int(fmaxf(px[e], FLT_MIN));
-                    const float lf = lg2_mant(bits);
-                    const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
-                    const float t = pt[e] * __fadd_rn(__fadd_rn(ft[e], -lf), __fadd_rn(et[e], -eb));
-                    if (e & 1)
-                        s1 += t;
-                    else
-                        s0 += t;
-                }
+            for (int e = 0; e < 4; ++e) {
+                const int bits = __float_as_int(fmaxf(px[e], FLT_MIN));
+                const float lf = lg2_mant(bits);
+                const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
+                const float t = pt[e] * __fadd_rn(__fadd_rn(ft[e], -lf), __fadd_rn(et[e], -eb));
+                if (e & 1)
+                    s1 += t;
+                else
+                    s0 += t;
             }
         }
-        float s = s0 + s1;
+    };
+    auto done = [&](int64_t x) {
+        float sum = s0 + s1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        s *= kLn2f;
-        if (s < (float)DD_EXACT_BELOW) {        // warp-uniform: the exact (table) form
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (FAM == kKlRev) sum *= kLn2f;
+        if (sum < q.below) {                    // warp-uniform: the exact (table) form
+            const float4 *row = reinterpret_cast<const float4 *>(P + x * k_pad);
             float r0 = 0.0f, r1 = 0.0f;
             for (int c = lane; c < nvec; c += 32) {
                 const float4 vx = __ldcg(row + c);
                 const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
                 const float4 l4 = reinterpret_cast<const float4 *>(tL)[c];
                 const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
-                r0 += fterm<kKlRev>(vx.x, p4.x, l4.x, e4.x, q, tab);
-                r1 += fterm<kKlRev>(vx.y, p4.y, l4.y, e4.y, q, tab);
-                r0 += fterm<kKlRev>(vx.z, p4.z, l4.z, e4.z, q, tab);
-                r1 += fterm<kKlRev>(vx.w, p4.w, l4.w, e4.w, q, tab);
+                r0 += fterm<FAM>(vx.x, p4.x, l4.x, e4.x, q, tab);
+                r1 += fterm<FAM>(vx.y, p4.y, l4.y, e4.y, q, tab);
+                r0 += fterm<FAM>(vx.z, p4.z, l4.z, e4.z, q, tab);
+                r1 += fterm<FAM>(vx.w, p4.w, l4.w, e4.w, q, tab);
             }
-            s = r0 + r1;
+            sum = r0 + r1;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         }
-        if (lane == 0) out[(int64_t)a * n_v + x] = s;
-    }
+        if (lane == 0) out[(int64_t)a * n_v + x] = sum;
+        s0 = s1 = 0.0f;
+    };
+    stream_rows<4>(P, n_v, k_pad, warp, nwarps, lane, chunk, done);
 }
 
 }  // namespace
@@ -295,14 +396,26 @@ dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *
         err = "divergence fields: k_pad too large for the staged target row";
         return DD_EINVAL;
     }
-    FdParams q;
+    FdParams q{};
     q.p = (float)param;
     q.lin = 0.0f;
     q.alpha_gt1 = 0;
+    q.below = (float)DD_EXACT_BELOW;
+    bool alpha_fast = false;
     if (family == DD_DIV_ALPHA) {
-        q.p = (float)((1.0 + param) / 2.0);
-        q.lin = (float)(2.0 / (1.0 - param));
+        const double e = (1.0 + param) / 2.0, lin = 2.0 / (1.0 - param);
+        q.p = (float)e;
+        q.lin = (float)lin;
         q.alpha_gt1 = param > 1.0;
+        q.inv_e = (float)(1.0 / e);
+        double en = e, fact = 1.0;                         // e^(n-1), n!
+        for (int n = 2; n <= 7; ++n) {
+            fact *= n;
+            q.c[n - 2] = (float)((1.0 - en) / fact);
+            en *= e;
+        }
+        q.below = (float)std::max((double)DD_EXACT_BELOW, 2e5 * std::fabs(lin / e) * std::ldexp(1.0, -22));
+        alpha_fast = std::fabs(e) >= 0.1 && std::fabs(e) <= 2.0 && std::fabs(1.0 - e) >= 0.1;
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -322,12 +435,12 @@ dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *
                                                                    family == DD_DIV_KL_REVERSE ? LP : nullptr);
         }
     };
-    if (family == DD_DIV_KL_REVERSE && !LP) {
+    if ((family == DD_DIV_KL_REVERSE && !LP) || alpha_fast) {
         // two passes (hardware mantissa logs, then the table form near the target)
         const float *sF = sE + (int64_t)T * k_pad;
         const size_t smem4 = 4 * (size_t)k_pad * sizeof(float);
         if (smem4 <= 200 * 1024) {
-            auto kern = klrev_two_pass_kernel;
+            auto kern = family == DD_DIV_ALPHA ? two_pass_kernel<kAlpha> : two_pass_kernel<kKlRev>;
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem4);
@@ -336,8 +449,8 @@ dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *
             const int64_t rows_blocks = (n_v + 7) / 8;
             if (gx < 1) gx = 1;
             if (gx > rows_blocks) gx = rows_blocks;
-            KMark km_("klrev_two_pass_kernel", s);
-            kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem4, s>>>(P, n_v, k_pad, sP, sL, sE, sF, out);
+            KMark km_("two_pass_kernel", s);
+            kern<<<dim3((unsigned)gx, (unsigned)T), 256, smem4, s>>>(P, n_v, k_pad, sP, sL, sE, sF, q, out);
             return DD_OK;
         }
     }

@@ -374,7 +374,8 @@ __device__ __forceinline__ void lds_vec(float (&dst)[N], const float *src) {
 // logarithm (log2 P from dd_log_poisson_kernel) that logarithm instead of
 // the clamp -- else from the staged entry itself (the multi-domain launch).
 // Data movement (the arithmetic and its order are those of a plain loop over
-// 32-column chunks).  Each chunk of the row tile and of the target tile is
+// the columns in 64-column partial sums).  Each 32-column chunk of the row
+// tile and of the target tile is
 // fetched by cp.async into a raw buffer (rows of 32 floats at a pitch of 36,
 // so that the transposing reads below hit different banks) while the
 // previous chunk is being summed; after a barrier every thread transposes
@@ -441,14 +442,20 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
         cp_async_commit();
     };
 
-    // two-level summation: 32-term chunk sums, added into the totals with a
-    // compensated (Kahan) sum for KL, whose terms partly cancel
+    // two-level summation: 64-term sums (two chunks), added into the totals
+    // with a compensated (Kahan) sum for KL, whose terms partly cancel
     float kl[RM][CN], tv[RM][CN], klc[RM][CN];
 #pragma unroll
     for (int r = 0; r < RM; ++r)
 #pragma unroll
         for (int c = 0; c < CN; ++c) kl[r][c] = tv[r][c] = klc[r][c] = 0.0f;
 
+    // partial sums over two chunks (64 columns) between merges
+    float ckl[RM][CN], ctv[RM][CN];
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int c = 0; c < CN; ++c) ckl[r][c] = ctv[r][c] = 0.0f;
     fetch(0);
     for (int64_t b0 = 0; b0 < k_pad; b0 += kTileB) {
         cp_async_wait_all();
@@ -501,11 +508,6 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
         }
         __syncthreads();        // the chunk is transposed; the raw buffer is free
         if (b0 + kTileB < k_pad) fetch(b0 + kTileB);
-        float ckl[RM][CN], ctv[RM][CN];
-#pragma unroll
-        for (int r = 0; r < RM; ++r)
-#pragma unroll
-            for (int c = 0; c < CN; ++c) ckl[r][c] = ctv[r][c] = 0.0f;
         // columns in groups of G, inside which both swizzles are constant: the
         // swizzled offsets are formed once per group, the columns' addresses
         // are then fixed offsets from them
@@ -573,16 +575,19 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
                     }
             }
         }
+        if (((b0 / kTileB) & 1) || b0 + kTileB >= k_pad) {
 #pragma unroll
-        for (int r = 0; r < RM; ++r)
+            for (int r = 0; r < RM; ++r)
 #pragma unroll
-            for (int c = 0; c < CN; ++c) {
-                const float y = __fsub_rn(ckl[r][c], klc[r][c]);
-                const float t = __fadd_rn(kl[r][c], y);
-                klc[r][c] = __fsub_rn(__fsub_rn(t, kl[r][c]), y);
-                kl[r][c] = t;
-                tv[r][c] = __fadd_rn(tv[r][c], ctv[r][c]);
-            }
+                for (int c = 0; c < CN; ++c) {
+                    const float y = __fsub_rn(ckl[r][c], klc[r][c]);
+                    const float t = __fadd_rn(kl[r][c], y);
+                    klc[r][c] = __fsub_rn(__fsub_rn(t, kl[r][c]), y);
+                    kl[r][c] = t;
+                    tv[r][c] = __fadd_rn(tv[r][c], ctv[r][c]);
+                    ckl[r][c] = ctv[r][c] = 0.0f;
+                }
+        }
     }
     __syncthreads();            // the transposed arrays may be refilled by the next tile of this CTA
 #pragma unroll
@@ -640,15 +645,70 @@ __global__ void __launch_bounds__(256) fix_kl_kernel(BatchProblem q) {
     fix_problem(q, wid, nw, base, tab, threadIdx.x & 31);
 }
 
-__global__ void __launch_bounds__(256) fix_kl_batch_kernel(const BatchProblem *__restrict__ probs, int32_t n_probs) {
+// The multi-domain recompute, per target: blockIdx.y is a target of the
+// batch (tprob / tloc: its problem and its index there), blockIdx.x one of
+// its `parts` CTAs.  The CTA stages the target's P, table mantissa log and
+// exponent rows in shared memory, scans the first-pass KL of its share of
+// the rows (blocks of 32 consecutive rows dealt round-robin over the parts,
+// so that the rows around the target spread over all of them) and queues
+// those below kTileExactBelow; its warps then take the queued rows in turn
+// (kl_row_exact, the row from L2 or DRAM, the target's arrays from shared
+// memory).  On many domains with small k this beats the grid-wide scan of
+// fix_kl_kernel (batch64: 13.0 against 18.0 ms), whose warps read the
+// target arrays from L2 per flagged row; on one large domain it does not.
+constexpr int kFixWindow = 1024;      // rows scanned per queue round: 8 warps x 4 blocks of 32
+
+__global__ void __launch_bounds__(256) fix_kl_batch_kernel(const BatchProblem *__restrict__ probs,
+                                                           const int32_t *__restrict__ tprob,
+                                                           const int32_t *__restrict__ tloc, int parts, int g0) {
+    extern __shared__ __align__(16) float fsm[];
     __shared__ float tab[2 * kLogTab];
+    __shared__ int queue[kFixWindow];
+    __shared__ int qn;
     build_log_table(tab);
+    const int g = g0 + (int)blockIdx.y;
+    const BatchProblem q = probs[tprob[g]];
+    if (!q.out_kl) return;
+    const int a = tloc[g], part = (int)blockIdx.x;
+    const int64_t k_pad = q.k_pad, n_v = q.n_v;
+    float *tP = fsm, *tL = fsm + k_pad, *tE = fsm + 2 * k_pad;
+    const int64_t o = (int64_t)a * k_pad;
+    for (int64_t b = threadIdx.x; b < k_pad; b += blockDim.x) {
+        tP[b] = q.sP[o + b];
+        tL[b] = q.sL[o + b];
+        tE[b] = q.sE[o + b];
+    }
+    if (threadIdx.x == 0) qn = 0;
     __syncthreads();
-    const int64_t wid = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x, nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    int64_t base = 0;
-    for (int p = 0; p < n_probs; ++p) {
-        const BatchProblem q = probs[p];
-        fix_problem(q, wid, nw, base, tab, threadIdx.x & 31);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nvec = (int)(k_pad >> 2);
+    float *row = q.out_kl + (int64_t)a * n_v;
+    const int64_t nblk = (n_v + 31) / 32;
+    const int64_t mine = nblk > part ? (nblk - part + parts - 1) / parts : 0;      // blocks of this part
+    for (int64_t w0 = 0; w0 < mine; w0 += kFixWindow / 32) {
+#pragma unroll
+        for (int j = 0; j < kFixWindow / 256; ++j) {
+            const int64_t i = w0 + warp * (kFixWindow / 256) + j;
+            const int64_t x = (part + i * parts) * 32 + lane;
+            const bool low = i < mine && x < n_v && row[x] < kTileExactBelow;
+            const unsigned m = __ballot_sync(0xffffffffu, low);
+            if (m) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&qn, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (low) queue[base + __popc(m & ((1u << lane) - 1u))] = (int)x;
+            }
+        }
+        __syncthreads();
+        const int n = qn;
+        for (int i = warp; i < n; i += 8) {
+            const int x = queue[i];
+            const float v = kl_row_exact(q.P, x, k_pad, nvec, tP, tL, tE, tab, lane);
+            if (lane == 0) row[x] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) qn = 0;
+        __syncthreads();
     }
 }
 
@@ -907,7 +967,8 @@ void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, con
 }
 
 void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const BatchItem *d_items, int32_t n_items,
-                         int32_t *d_counter, cudaStream_t s) {
+                         int32_t *d_counter, cudaStream_t s, const int32_t *d_tprob, const int32_t *d_tloc,
+                         int32_t n_targets, int64_t k_max, int64_t n_max) {
     if (n_items <= 0) return;
     const size_t smem = (size_t)(2 * kTileB + kTileB + 4) * (256 + 16) * sizeof(float);
     cudaFuncSetAttribute(batch_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -921,10 +982,19 @@ void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const Bat
         KMark km_("batch_tile_kernel", s);
         batch_tile_kernel<<<(unsigned)grid, 256, smem, s>>>(d_probs, d_items, n_items, d_counter);
     }
-    {
+    if (n_targets > 0) {
+        // about four CTAs per SM over all targets, each with at least 64 blocks of 32 rows to scan
+        const size_t fsm = 3 * (size_t)k_max * sizeof(float);
+        cudaFuncSetAttribute(fix_kl_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+        const int64_t want = (4 * (int64_t)num_sms() + n_targets - 1) / n_targets;
+        const int64_t cap = std::max<int64_t>(1, (n_max + 32 * 64 - 1) / (32 * 64));
+        const int parts = (int)std::max<int64_t>(1, std::min(want, cap));
         KMark km_("fix_kl_batch_kernel", s);
-        fix_kl_batch_kernel<<<(unsigned)(num_sms() * 4), 256, 0, s>>>(d_probs, n_probs);
+        for (int32_t g0 = 0; g0 < n_targets; g0 += 65535)        // grid rows: at most 65,535 targets per launch
+            fix_kl_batch_kernel<<<dim3((unsigned)parts, (unsigned)std::min<int32_t>(65535, n_targets - g0)), 256, fsm,
+                                  s>>>(d_probs, d_tprob, d_tloc, parts, g0);
     }
+    (void)n_probs;
 }
 
 std::string tuning_table() {

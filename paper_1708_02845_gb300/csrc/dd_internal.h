@@ -132,8 +132,12 @@ int tile_rows(int variant);
 int tile_targets(int variant);
 void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, const int32_t *d_tlocal,
                         const int32_t *d_targets, int32_t n_targets, int64_t k_max, cudaStream_t s);
+// tile pass over every item, then the exact recompute per target (d_tprob /
+// d_tloc: each of the n_targets targets' problem and index there; k_max,
+// n_max: the largest k_pad and n_v of the problems)
 void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const BatchItem *d_items, int32_t n_items,
-                         int32_t *d_counter, cudaStream_t s);
+                         int32_t *d_counter, cudaStream_t s, const int32_t *d_tprob, const int32_t *d_tloc,
+                         int32_t n_targets, int64_t k_max, int64_t n_max);
 std::string tuning_table();
 // spurious local minima of T fields [T][n_v] (counts host [T], flags optional [T][n_v])
 void launch_local_minima(const DevMesh &m, const float *fields, const int32_t *targets, int32_t T, int32_t *counts,

@@ -217,7 +217,9 @@ bool launch_batch(dd_server *sv, Slot &sl) {
                            nT, max_k, s);
         launch_batch_fields(reinterpret_cast<const BatchProblem *>(d + o_probs), (int32_t)n_items,
                             reinterpret_cast<const BatchItem *>(d + o_items), (int32_t)n_tiles,
-                            reinterpret_cast<int32_t *>(d + o_counter), s);
+                            reinterpret_cast<int32_t *>(d + o_counter), s,
+                            reinterpret_cast<const int32_t *>(d + o_tprob), reinterpret_cast<const int32_t *>(d + o_tloc),
+                            nT, max_k, max_nv);
         launch_batch_trace(d + o_doms, reinterpret_cast<const int32_t *>(d + o_tprob),
                            reinterpret_cast<const int32_t *>(d + o_tloc), reinterpret_cast<const int32_t *>(d + o_targets),
                            reinterpret_cast<const int32_t *>(d + o_sources), nT, 0, max_nt, max_nv, sv->max_pts,

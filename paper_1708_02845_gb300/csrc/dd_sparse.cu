@@ -14,9 +14,10 @@
 // Layouts.  dd_sparsify stores the sparsified P as CSR (each row's kept
 // entries in column order: FP32 values, 16-bit columns, 64-bit row offsets),
 // about a sixth of the dense P at 84 % sparsity.  KL~ and TV~ read only that
-// (csr_field_kernel: one warp per row, the target row's thresholded values
-// and logarithms staged in shared memory by bulk async copies and gathered
-// by column).  KLT~ needs the field row at the target's kept columns, which
+// (csr_stream_kernel: one warp per row, the row's entries streamed into
+// shared memory by bulk async copies with several chunks in flight per warp;
+// the target row's thresholded values and logarithms staged in shared
+// memory the same way and gathered by column).  KLT~ needs the field row at the target's kept columns, which
 // the CSR row may not hold (an entry below the field row's own threshold is
 // still non-zero), so it reads the dense P at the 4-column blocks holding
 // S_t (sparse_field_kernel, the list built once per target by
@@ -470,10 +471,11 @@ __global__ void __launch_bounds__(256, 3) sparse_field_kernel(
 }
 
 // exact (table) KL~ of one CSR row for one warp: sum over the row's entries
-// of P[x,b] log(P[x,b] / P[t,b]), the target's logs from the staged arrays
+// of P[x,b] log(P[x,b] / P[t,b]), the target's table mantissa logs from its
+// staged row in global memory, its biased exponents every es floats of tE
 __device__ __forceinline__ float csr_kl_exact(const float *__restrict__ val, const uint16_t *__restrict__ col,
-                                              int64_t o0, int64_t o1, const float *tL, const float *tE,
-                                              const float *tab, int lane) {
+                                              int64_t o0, int64_t o1, const float *__restrict__ gL,
+                                              const float *tE, int es, const float *tab, int lane) {
     float k0 = 0.0f, k1 = 0.0f;
     int q = 0;
     for (int64_t i = o0 + lane; i < o1; i += 32, ++q) {
@@ -481,7 +483,7 @@ __device__ __forceinline__ float csr_kl_exact(const float *__restrict__ val, con
         const int c = col[i];
         float lm, Eb;
         split_log<false>(v, tab, lm, Eb);
-        const float lr = __fmaf_rn(__fadd_rn(Eb, -tE[c]), kLn2s, __fadd_rn(lm, -tL[c]));
+        const float lr = __fmaf_rn(__fadd_rn(Eb, -tE[es * c]), kLn2s, __fadd_rn(lm, -__ldg(gL + c)));
         if (q & 1)
             k1 = __fmaf_rn(v, lr, k1);
         else
@@ -493,169 +495,225 @@ __device__ __forceinline__ float csr_kl_exact(const float *__restrict__ val, con
     return s;
 }
 
-// the staged target mass over one CSR row's columns, sum_{b in S_x} P~[t,b]:
-// lane l adds the row's entries l, l + 32, ... in order, then the fixed
-// shuffle tree -- the same additions the field kernel makes, so that on row
-// x = t it reproduces the target's total bit for bit
+// the staged target mass over one CSR row's columns, sum_{b in S_x} P~[t,b],
+// in the order csr_stream_kernel adds a row: lane l takes the pairs of
+// entries i, i + 1 with i = a + 2 l (mod 64), a the row's first entry rounded
+// down to a multiple of 8 (where its first chunk starts), in increasing
+// order, then the fixed shuffle tree -- on row x = t it reproduces the
+// target's total bit for bit
 __device__ __forceinline__ float csr_target_mass(const uint16_t *__restrict__ col, int64_t o0, int64_t o1,
                                                  const float *tP, int lane) {
     float a = 0.0f;
-    for (int64_t i = o0 + lane; i < o1; i += 32) a = __fadd_rn(a, tP[col[i]]);
+    for (int64_t i = (o0 & ~(int64_t)7) + 2 * lane; i < o1; i += 64) {
+        if (i >= o0) a = __fadd_rn(a, tP[col[i]]);
+        if (i + 1 >= o0 && i + 1 < o1) a = __fadd_rn(a, tP[col[i + 1]]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a = __fadd_rn(a, __shfl_xor_sync(0xffffffffu, a, o));
     return a;
 }
 
+// csr_stream_kernel's configurations: W warps, NS chunk buffers of C entries per warp
+constexpr int kCsrW = 16, kCsrC = 512, kCsrNS = 3;
+
 // KL~ and TV~ from the CSR rows, one target per grid row (blockIdx.y).
-// Dynamic smem: the target's thresholded row P~[t,:], its table mantissa log,
-// biased exponent and hardware mantissa log2 (the logs of the dense row),
-// one bulk copy each.  One warp per row; items are (row, chunk of 32 U
-// entries), each lane loading U values and columns of the next item while the
-// current one is summed.  Per entry v = P[x,b] at column c:
+// Dynamic smem: the target's thresholded row P~[t,:] and its (hardware
+// mantissa log2, biased exponent) pairs, staged by bulk copies; then, per
+// warp, NS chunk buffers of C values and C columns.  One warp per row (rows
+// strided by the grid's warp count).  A row is cut into chunks of at most C
+// entries, from its first entry rounded down to a multiple of 8 to its last
+// rounded up (so that both arrays start and end on 16-byte boundaries); each
+// chunk is one pair of bulk copies completing on the warp's own mbarrier,
+// NS chunks in flight per warp.  Lane 0 issues; the row offsets are read one
+// row ahead.  Each lane takes two neighbouring entries per step (one 8-byte
+// and one 4-byte shared load).  Per entry v = P[x,b] at column c (the
+// rounded ends' entries of other rows skipped):
 //   KL: v ((lg2 m_v - lg2 m_t[c]) + (E_v - E_t[c])), times ln2 at the end
 //   TV: |v - P~[t,c]|, and the target mass the row covers, P~[t,c]
 // so that TV~ = sum |v - P~[t,c]| + (M~_t - covered), M~_t the target's own
-// total by the same additions (csr_target_mass on row t).
-template <int U, bool KL, bool TV>
-__global__ void __launch_bounds__(256, 2) csr_field_kernel(
+// total by the same additions (csr_target_mass on row t).  Rows with
+// KL~ < DD_EXACT_BELOW are recomputed with the table logarithm, the target's
+// table mantissa logs read from the staged array in global memory.
+template <int W, int C, int NS, bool KL, bool TV>
+__global__ void __launch_bounds__(W * 32, 1) csr_stream_kernel(
     const float *__restrict__ val, const uint16_t *__restrict__ col, const int64_t *__restrict__ off, int64_t n_v,
     int64_t k_pad, const float *__restrict__ sP, const float *__restrict__ sL, const float *__restrict__ sE,
     const float *__restrict__ sF, const int32_t *__restrict__ targets, float *__restrict__ out_kl,
     float *__restrict__ out_tv, int *__restrict__ err_flag) {
+    static_assert(C % 64 == 0 && NS >= 2, "chunks of whole warp steps, at least double buffered");
     extern __shared__ __align__(16) float smem[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t wbar[W][NS];
+    __shared__ int64_t wdesc[W][NS][4];        // per chunk buffer: row (n_v: none), o0, o1, chunk start
     __shared__ float tab[2 * kLogTab];
     __shared__ float mt_sh;
     float *tP = smem;
-    float *tL = tP + k_pad;
-    float *tE = tL + k_pad;
-    float *tF = tE + k_pad;
-    const int a = blockIdx.y;
+    float2 *tEF = reinterpret_cast<float2 *>(smem + k_pad);              // (lg2 m_t, E_t) per column
+    float *region = smem + 3 * k_pad;                                    // chunk buffers (first: E_t, lg2 m_t)
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *bv = region + (int64_t)wid * NS * C;
+    uint16_t *bc = reinterpret_cast<uint16_t *>(region + (int64_t)W * NS * C) + (int64_t)wid * NS * C;
+    uint64_t *wb = wbar[wid];
+    int64_t(*wd)[4] = wdesc[wid];
+    const int a_t = blockIdx.y;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
+        for (int w = 0; w < W; ++w)
+            for (int s = 0; s < NS; ++s) mbar_init(&wbar[w][s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t row_bytes = (uint32_t)(k_pad * sizeof(float));
-        mbar_expect_tx(&bar, 4u * row_bytes);
-        bulk_g2s(tP, sP + (int64_t)a * k_pad, row_bytes, &bar);
-        bulk_g2s(tL, sL + (int64_t)a * k_pad, row_bytes, &bar);
-        bulk_g2s(tE, sE + (int64_t)a * k_pad, row_bytes, &bar);
-        bulk_g2s(tF, sF + (int64_t)a * k_pad, row_bytes, &bar);
+        mbar_expect_tx(&bar, 3u * row_bytes);
+        bulk_g2s(tP, sP + (int64_t)a_t * k_pad, row_bytes, &bar);
+        bulk_g2s(region, sE + (int64_t)a_t * k_pad, row_bytes, &bar);
+        bulk_g2s(region + k_pad, sF + (int64_t)a_t * k_pad, row_bytes, &bar);
     }
     build_log_table(tab);
-    __syncthreads();
     // every thread waits (bounded); a CTA whose wait gave up waits once more
     // (also bounded) so that it does not exit while its copies may still land
     const bool ok = mbar_wait(&bar, 0, err_flag);
     if (!ok) mbar_wait(&bar, 0, err_flag);
-    const int lane = threadIdx.x & 31;
+    if (ok)
+        for (int64_t c = threadIdx.x; c < k_pad; c += blockDim.x) tEF[c] = make_float2(region[k_pad + c], region[c]);
+    __syncthreads();
     if (TV && threadIdx.x < 32) {
-        const int64_t t = targets[a];
+        const int64_t t = targets[a_t];
         const float m = ok ? csr_target_mass(col, off[t], off[t + 1], tP, lane) : 0.0f;
         if (lane == 0) mt_sh = m;
     }
     __syncthreads();
     if (!ok) return;
     const float Mt = TV ? mt_sh : 0.0f;
+    const float *gL = sL + (int64_t)a_t * k_pad;
+    float *okl = KL ? out_kl + (int64_t)a_t * n_v : nullptr;
+    float *otv = TV ? out_tv + (int64_t)a_t * n_v : nullptr;
+    const int64_t nw = (int64_t)gridDim.x * W;
 
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    float *okl = KL ? out_kl + (int64_t)a * n_v : nullptr;
-    float *otv = TV ? out_tv + (int64_t)a * n_v : nullptr;
+    // issue state (meaningful in lane 0): row ix with entries [io0, io1),
+    // next chunk start ia; the offsets of row ix + nw already requested
+    int64_t ix = (int64_t)blockIdx.x * W + wid, io0 = 0, io1 = 0, ia = 0, po0 = 0, po1 = 0;
+    if (lane == 0 && ix < n_v) {
+        io0 = __ldg(off + ix);
+        io1 = __ldg(off + ix + 1);
+        ia = io0 & ~(int64_t)7;
+        if (ix + nw < n_v) {
+            po0 = __ldg(off + ix + nw);
+            po1 = __ldg(off + ix + nw + 1);
+        }
+    }
+    auto issue = [&](int s) {                  // lane 0: the next chunk into buffer s
+        if (ix >= n_v) {
+            wd[s][0] = n_v;
+            return;
+        }
+        const int64_t end8 = (io1 + 7) & ~(int64_t)7;
+        const int64_t e = ia + C < end8 ? ia + C : end8;
+        const uint32_t ne = (uint32_t)(e - ia);
+        wd[s][0] = ix;
+        wd[s][1] = io0;
+        wd[s][2] = io1;
+        wd[s][3] = ia;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&wb[s], ne * 6u);       // 0 for an empty row: the phase completes at once
+        if (ne) {
+            bulk_g2s(bv + s * C, val + ia, ne * 4u, &wb[s]);
+            bulk_g2s(bc + s * C, col + ia, ne * 2u, &wb[s]);
+        }
+        if (e < end8) {
+            ia = e;
+        } else {
+            ix += nw;
+            io0 = po0;
+            io1 = po1;
+            ia = io0 & ~(int64_t)7;
+            if (ix + nw < n_v) {
+                po0 = __ldg(off + ix + nw);
+                po1 = __ldg(off + ix + nw + 1);
+            }
+        }
+    };
+    if (lane == 0)
+        for (int s = 0; s < NS; ++s) issue(s);
+    __syncwarp();
 
-    float vb[2][U];
-    int cb[2][U];
     float kl = 0.0f, tv = 0.0f, cov = 0.0f;
-
-    // an item: row x, its entries [o0, o1), chunk start i0
-    struct Item {
-        int64_t x, o0, o1, i0;
-    };
-    auto first = [&](int64_t x) {
-        Item it{x, 0, 0, 0};
-        if (x < n_v) {
-            it.o0 = off[x];
-            it.o1 = off[x + 1];
-            it.i0 = it.o0;
-        }
-        return it;
-    };
-    auto next = [&](const Item &it) {
-        if (it.i0 + 32 * U < it.o1) return Item{it.x, it.o0, it.o1, it.i0 + 32 * U};
-        return first(it.x + nwarps);
-    };
-    auto fetch = [&](auto S_, const Item &it) {
-        constexpr int s = decltype(S_)::value;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = it.i0 + u * 32 + lane;
-            const bool in = i < it.o1;
-            vb[s][u] = in ? __ldcs(val + i) : 0.0f;
-            cb[s][u] = in ? (int)__ldcs(col + i) : -1;
-        }
-    };
-    auto compute = [&](auto S_) {
-        constexpr int s = decltype(S_)::value;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int c = cb[s][u];
-            if (c < 0) break;
-            const float v = vb[s][u];
-            if (KL) {
-                const int bits = __float_as_int(v);
-                const float lf = lg2_mant(bits);
-                const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
-                const float d = __fadd_rn(__fadd_rn(lf, -tF[c]), __fadd_rn(eb, -tE[c]));
-                kl = __fmaf_rn(v, d, kl);
-            }
-            if (TV) {
-                const float pt = tP[c];
-                tv = __fadd_rn(tv, fabsf(__fadd_rn(v, -pt)));
-                cov = __fadd_rn(cov, pt);
-            }
-        }
-    };
-    auto finish = [&](const Item &it) {
-        float skl = kl, stv = tv, sc = cov;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            if (KL) skl += __shfl_xor_sync(0xffffffffu, skl, o);
-            if (TV) {
-                stv += __shfl_xor_sync(0xffffffffu, stv, o);
-                sc = __fadd_rn(sc, __shfl_xor_sync(0xffffffffu, sc, o));
-            }
-        }
+    auto entry = [&](float v, int c) {
         if (KL) {
-            skl *= kLn2s;
-            if (skl < kExactBelowS)                  // warp-uniform
-                skl = csr_kl_exact(val, col, it.o0, it.o1, tL, tE, tab, lane);
+            const int bits = __float_as_int(v);
+            const float lf = lg2_mant(bits);
+            const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
+            const float2 fe = tEF[c];
+            kl = __fmaf_rn(v, __fadd_rn(__fadd_rn(lf, -fe.x), __fadd_rn(eb, -fe.y)), kl);
         }
-        if (lane == 0) {
-            if (KL) okl[it.x] = skl;
-            if (TV) otv[it.x] = __fadd_rn(stv, __fadd_rn(Mt, -sc));
+        if (TV) {
+            const float pt = tP[c];
+            tv = __fadd_rn(tv, fabsf(__fadd_rn(v, -pt)));
+            cov = __fadd_rn(cov, pt);
         }
-        kl = tv = cov = 0.0f;
     };
-    using B0 = std::integral_constant<int, 0>;
-    using B1 = std::integral_constant<int, 1>;
-    Item cur = first(warp);
-    if (cur.x >= n_v) return;
-    fetch(B0{}, cur);
+    int s = 0;
+    uint32_t ph = 0;
     for (;;) {
-        Item nx = next(cur);
-        if (nx.x < n_v) fetch(B1{}, nx);
-        compute(B0{});
-        if (nx.x != cur.x) finish(cur);
-        if (nx.x >= n_v) break;
-        cur = nx;
-        nx = next(cur);
-        if (nx.x < n_v) fetch(B0{}, nx);
-        compute(B1{});
-        if (nx.x != cur.x) finish(cur);
-        if (nx.x >= n_v) break;
-        cur = nx;
+        const int64_t x = wd[s][0];
+        if (x >= n_v) break;
+        const int64_t o0 = wd[s][1], o1 = wd[s][2], a = wd[s][3];
+        if (!mbar_wait_suspend(&wb[s], ph, err_flag)) {
+            // give up: wait (bounded) for this warp's other copies in flight, then leave
+            for (int j = 1; j < NS; ++j) {
+                const int sj = (s + j) % NS;
+                if (wd[sj][0] < n_v) mbar_wait_suspend(&wb[sj], sj > s ? ph : ph ^ 1u, err_flag);
+            }
+            return;
+        }
+        const int64_t end8 = (o1 + 7) & ~(int64_t)7;
+        const int ne = (int)((a + C < end8 ? a + C : end8) - a);
+        const int lo = (int)(o0 > a ? o0 - a : 0);
+        const int hi = (int)(o1 - a < ne ? o1 - a : ne);
+        const float *cv = bv + s * C;
+        const uint16_t *cc = bc + s * C;
+#pragma unroll 2
+        for (int q = 2 * lane; q < ne; q += 64) {
+            const float2 v2 = *reinterpret_cast<const float2 *>(cv + q);
+            const uint32_t c2 = *reinterpret_cast<const uint32_t *>(cc + q);
+            if (q >= lo && q + 1 < hi) {       // both entries the row's (all but a row's two ends)
+                entry(v2.x, (int)(c2 & 0xFFFFu));
+                entry(v2.y, (int)(c2 >> 16));
+            } else {
+                if (q >= lo && q < hi) entry(v2.x, (int)(c2 & 0xFFFFu));
+                if (q + 1 >= lo && q + 1 < hi) entry(v2.y, (int)(c2 >> 16));
+            }
+        }
+        __syncwarp();                          // buffer s read by every lane
+        if (lane == 0) issue(s);
+        __syncwarp();                          // its descriptor visible
+        if (a + C >= end8) {                   // the row's last chunk: reduce and store
+            float skl = kl, stv = tv, sc = cov;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                if (KL) skl += __shfl_xor_sync(0xffffffffu, skl, o);
+                if (TV) {
+                    stv += __shfl_xor_sync(0xffffffffu, stv, o);
+                    sc = __fadd_rn(sc, __shfl_xor_sync(0xffffffffu, sc, o));
+                }
+            }
+            if (KL) {
+                skl *= kLn2s;
+                if (skl < kExactBelowS)              // warp-uniform
+                    skl = csr_kl_exact(val, col, o0, o1, gL, reinterpret_cast<const float *>(tEF) + 1, 2, tab,
+                                       lane);
+            }
+            if (lane == 0) {
+                if (KL) okl[x] = skl;
+                if (TV) otv[x] = __fadd_rn(stv, __fadd_rn(Mt, -sc));
+            }
+            kl = tv = cov = 0.0f;
+        }
+        if (++s == NS) {
+            s = 0;
+            ph ^= 1u;
+        }
     }
 }
 
@@ -676,6 +734,17 @@ size_t sparse_field_smem(int64_t k_pad) {
 
 size_t sparse_count_bytes(int32_t T) { return ((size_t)T * sizeof(int32_t) + 15) / 16 * 16; }
 
+// dynamic shared memory of csr_stream_kernel: the target's P~ row and
+// (lg2 m, E) pairs, then W warps x NS chunk buffers of C FP32 values and C
+// 16-bit columns (at least the two staged rows the pairs are built from); at
+// most the 227 KB a CTA may hold less 4 KB for its static arrays
+constexpr size_t kCsrSmemMax = 232448 - 4096;
+
+size_t csr_stream_smem(int64_t k_pad, int W, int C, int NS) {
+    const size_t bufs = (size_t)W * NS * C * (sizeof(float) + sizeof(uint16_t));
+    return 3 * (size_t)k_pad * sizeof(float) + std::max(bufs, 2 * (size_t)k_pad * sizeof(float));
+}
+
 size_t sparse_stage_bytes(int64_t k_pad, int32_t T) {
     return 4 * (size_t)T * k_pad * sizeof(float) + (size_t)T * sparse_list_pitch(k_pad) * sizeof(uint16_t) +
            sparse_count_bytes(T) + (size_t)T * sizeof(double);
@@ -685,6 +754,10 @@ dd_status build_sparse_rows(DevMesh &m, double theta, cudaStream_t s, int64_t *k
                             std::string &err) {
     if (m.k > 65536) {
         err = "sparse fields: more than 65,536 boundary columns (16-bit column ids)";
+        return DD_EINVAL;
+    }
+    if (csr_stream_smem(m.k_pad, 8, 128, 2) > kCsrSmemMax || sparse_field_smem(m.k_pad) > kCsrSmemMax) {
+        err = "sparse fields: the target's staged row does not fit in shared memory (k above about 13,500)";
         return DD_EINVAL;
     }
     long long *rowsum = nullptr;
@@ -726,8 +799,13 @@ dd_status build_sparse_rows(DevMesh &m, double theta, cudaStream_t s, int64_t *k
     for (int64_t x = 0; x < n; ++x) ho[x + 1] = ho[x] + hk[x];
     const int64_t nnz = ho[n];
     e = cudaMemcpyAsync(off, ho.data(), (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&val, (size_t)std::max<int64_t>(nnz, 1) * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&col, (size_t)std::max<int64_t>(nnz, 1) * sizeof(uint16_t));
+    // both arrays padded (with zeros) to a multiple of 8 entries: the row
+    // stream copies whole 16-byte pieces, up to the last row's end rounded up
+    const int64_t nnz8 = (std::max<int64_t>(nnz, 1) + 7) / 8 * 8;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&val, (size_t)nnz8 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&col, (size_t)nnz8 * sizeof(uint16_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(val + nnz, 0, (size_t)(nnz8 - nnz) * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(col + nnz, 0, (size_t)(nnz8 - nnz) * sizeof(uint16_t), s);
     if (e == cudaSuccess) {
         csr_fill_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(m.P, n, m.k_pad, row_thr, off, val, col);
         e = cudaGetLastError();
@@ -785,13 +863,31 @@ void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *st
         kern<<<dim3(gx, (unsigned)T), 256, smem, s>>>(m.P, m.n_v, m.k_pad, sP, sL, sE, sF, sList, lp, sCount, sMt,
                                                        m.sp_rowsum, out_kl, out_tv, out_klt, err_flag);
     };
-    // the CSR rows: KL~ and TV~
-    auto go_csr = [&](auto kern) {
-        const size_t smem = 4 * (size_t)m.k_pad * sizeof(float);
-        const unsigned gx = grid_x(kern, smem);
-        KMark km_("csr_field_kernel", s);
-        kern<<<dim3(gx, (unsigned)T), 256, smem, s>>>(m.sp_val, m.sp_col, m.sp_off, m.n_v, m.k_pad, sP, sL, sE, sF,
-                                                       d_targets, out_kl, out_tv, err_flag);
+    // the CSR rows: KL~ and TV~.  The deepest pipeline whose buffers fit next
+    // to the staged target row: 16 warps x 3 chunks of 512 entries (one CTA
+    // per SM, 144 KB of chunk buffers), else fewer or shorter chunks.
+    auto go_csr = [&](auto kern, int W, int C, int NS) {
+        const size_t smem = csr_stream_smem(m.k_pad, W, C, NS);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, smem);
+        if (per_sm < 1) per_sm = 1;
+        int64_t gx = (int64_t)sms_now() * per_sm / T;
+        const int64_t row_groups = (m.n_v + W - 1) / W;
+        if (gx < 1) gx = 1;
+        if (gx > row_groups) gx = row_groups;
+        KMark km_("csr_stream_kernel", s);
+        kern<<<dim3((unsigned)gx, (unsigned)T), W * 32, smem, s>>>(m.sp_val, m.sp_col, m.sp_off, m.n_v, m.k_pad, sP,
+                                                                    sL, sE, sF, d_targets, out_kl, out_tv, err_flag);
+    };
+    auto csr = [&](auto kl_, auto tv_) {
+        constexpr bool KL = decltype(kl_)::value, TV = decltype(tv_)::value;
+        if (csr_stream_smem(m.k_pad, kCsrW, kCsrC, kCsrNS) <= kCsrSmemMax)
+            go_csr(csr_stream_kernel<kCsrW, kCsrC, kCsrNS, KL, TV>, kCsrW, kCsrC, kCsrNS);
+        else if (csr_stream_smem(m.k_pad, 8, 512, 2) <= kCsrSmemMax)
+            go_csr(csr_stream_kernel<8, 512, 2, KL, TV>, 8, 512, 2);
+        else
+            go_csr(csr_stream_kernel<8, 128, 2, KL, TV>, 8, 128, 2);
     };
     if (merged) {
         // two blocks per lane and item, three CTAs per SM (measured: U = 4 or 8 with
@@ -808,11 +904,13 @@ void launch_sparse_fields(const DevMesh &m, const int32_t *d_targets, float4 *st
         }
         return;
     }
+    using Yes = std::true_type;
+    using No = std::false_type;
     if (out_kl && out_tv)
-        go_csr(csr_field_kernel<8, true, true>);
+        csr(Yes{}, Yes{});
     else if (out_kl)
-        go_csr(csr_field_kernel<8, true, false>);
+        csr(Yes{}, No{});
     else if (out_tv)
-        go_csr(csr_field_kernel<8, false, true>);
+        csr(No{}, Yes{});
     if (out_klt) go(sparse_field_kernel<2, false, false, true, false>);
 }

@@ -47,7 +47,10 @@ def env():
 
 FAMILIES = [("chi2", "DD_DIV_CHI2", 0.0), ("hellinger", "DD_DIV_HELLINGER", 0.0), ("power", "DD_DIV_POWER", 1.0),
             ("power", "DD_DIV_POWER", 2.5), ("alpha", "DD_DIV_ALPHA", 0.5), ("alpha", "DD_DIV_ALPHA", -0.7),
-            ("alpha", "DD_DIV_ALPHA", 3.0), ("kl_reverse", "DD_DIV_KL_REVERSE", 0.0)]
+            ("alpha", "DD_DIV_ALPHA", 3.0), ("alpha", "DD_DIV_ALPHA", 0.8), ("alpha", "DD_DIV_ALPHA", -5.0),
+            ("alpha", "DD_DIV_ALPHA", 0.95), ("alpha", "DD_DIV_ALPHA", 4.5), ("kl_reverse", "DD_DIV_KL_REVERSE", 0.0)]
+# alpha: 0.5, -0.7, 3.0, 0.8 and -5.0 take the two-pass form (first pass with
+# hardware logarithms and exp2), 0.95 and 4.5 the exact form throughout
 
 
 @pytest.mark.parametrize("name", list(CASES))
