@@ -239,9 +239,12 @@ std::vector<int32_t> morton_order(const DevMesh &m, const int32_t *targets, int3
 
 // fields of T targets into dst [nf][T][n_v] (device), targets already in scratch
 // (h_targets: the same ids on the host, or null)
+// The fields of T targets into dst ([fields][T][n_v] by default; stride: the
+// distance between two fields' blocks when dst is a block of rows inside a
+// larger output)
 dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t T, uint32_t f_mask, int32_t prec,
-                      float *dst, const int32_t *h_targets = nullptr) {
-    const int64_t stride = (int64_t)T * m.n_v;
+                      float *dst, const int32_t *h_targets = nullptr, int64_t stride = -1) {
+    if (stride < 0) stride = (int64_t)T * m.n_v;
     float *kl = field_slot(dst, f_mask, DD_F_KL, stride);
     float *tv = field_slot(dst, f_mask, DD_F_TV, stride);
     float *klt = field_slot(dst, f_mask, DD_F_KLT, stride);
@@ -1013,18 +1016,37 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
             if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
             dst = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
         }
-        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst,
-                         targets);
-        if (st != DD_OK) return st;
-        const float *trace_field = field_slot(dst, f_mask, trace_f, (int64_t)T * m->n_v);
+        const int64_t stride = (int64_t)T * m->n_v;
+        const int32_t *d_targets = reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]);
         if (sf == 0) {
-            // the fields go back on a side stream while the paths are traced
+            // Host fields: computed in chunks of targets, each chunk's rows going
+            // back on a side stream while the next chunk is computed (and the
+            // last one while the paths are traced); FP32 many-target path only,
+            // one chunk otherwise
             if ((st = ensure_side(ctx)) != DD_OK) return st;
-            CK(cudaEventRecord(ctx->side_ev[0], ctx->stream), "fields ready");
-            CK(cudaStreamWaitEvent(ctx->side, ctx->side_ev[0], 0), "side wait");
-            CK(cudaMemcpyAsync(out_fields, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->side), "copy fields");
+            const int nf = popcount2(f_mask);
+            const int32_t nch = (prec == DD_PREC_FP32 && T >= 256) ? std::min<int32_t>(8, T / 128) : 1;
+            const int32_t per = (T + nch - 1) / nch;
+            for (int32_t a0 = 0; a0 < T; a0 += per) {
+                const int32_t Tc = std::min(per, T - a0);
+                st = fields_into(ctx, *m, d_targets + a0, Tc, f_mask, prec, dst + (int64_t)a0 * m->n_v, targets + a0,
+                                 stride);
+                if (st != DD_OK) return st;
+                CK(cudaEventRecord(ctx->side_ev[0], ctx->stream), "fields ready");
+                CK(cudaStreamWaitEvent(ctx->side, ctx->side_ev[0], 0), "side wait");
+                for (int f = 0; f < nf; ++f) {
+                    const int64_t o = f * stride + (int64_t)a0 * m->n_v;
+                    CK(cudaMemcpyAsync(out_fields + o, dst + o, (size_t)Tc * m->n_v * sizeof(float),
+                                       cudaMemcpyDeviceToHost, ctx->side),
+                       "copy fields");
+                }
+            }
             CK(cudaEventRecord(ctx->side_ev[1], ctx->side), "fields copied");
+        } else {
+            st = fields_into(ctx, *m, d_targets, T, f_mask, prec, dst, targets);
+            if (st != DD_OK) return st;
         }
+        const float *trace_field = field_slot(dst, f_mask, trace_f, stride);
         st = trace_into(ctx, *m, trace_field, targets, T, sources, S, max_pts, out_xy, out_len, out_status, true);
         if (sf == 0) {
             // the next call may reuse the field scratch: the copy must be done

@@ -212,6 +212,43 @@ def test_query_host_equals_device(env):
     dd.dd_unload_mesh(ctx, mid)
 
 
+def test_query_host_chunks_equal_device(env):
+    """With host field buffers and many targets the fields are computed in
+    chunks of targets, each chunk copied back while the next is computed:
+    fields (pinned and pageable buffers), lengths, statuses and paths equal
+    the device-buffer call's bit for bit."""
+    dd, ctx = env
+    wl = workloads.grid140(T=1, S=1)
+    mesh = wl.mesh
+    mid = load(dd, ctx, mesh)
+    dd.dd_poisson_kernel(ctx, mid, 1e-15, 20000)
+    interior = np.nonzero(~mesh.boundary_flags())[0]
+    rng = np.random.default_rng(140300)
+    T, S, mp = 300, 2, 1024
+    targets = rng.choice(interior, T, replace=False).astype(np.int32)
+    src = rng.choice(interior, (T, S)).astype(np.int32)
+    df = torch.zeros((2, T, mesh.n_v), dtype=torch.float32, device="cuda")
+    dxy = torch.zeros((T * S, mp, 2), dtype=torch.float32, device="cuda")
+    dl = torch.zeros(T * S, dtype=torch.int32, device="cuda")
+    ds = torch.zeros(T * S, dtype=torch.int32, device="cuda")
+    dd.dd_query(ctx, mid, targets, src, 3, 0, dd.DD_F_KL, mp, df, dxy, dl, ds)
+    dd.dd_sync(ctx)
+    ref = df.cpu().numpy()
+    for pinned in (True, False):
+        hf = torch.zeros((2, T, mesh.n_v), dtype=torch.float32)
+        if pinned:
+            hf = hf.pin_memory()
+        hxy = np.zeros((T * S, mp, 2), np.float32)
+        hl = np.zeros(T * S, np.int32)
+        hs = np.zeros(T * S, np.int32)
+        dd.dd_query(ctx, mid, targets, src, 3, 0, dd.DD_F_KL, mp, hf.numpy(), hxy, hl, hs)
+        assert np.array_equal(hf.numpy(), ref), pinned
+        assert np.array_equal(hl, dl.cpu().numpy()) and np.array_equal(hs, ds.cpu().numpy())
+        for i in range(0, T * S, 7):
+            assert np.array_equal(hxy[i, :hl[i]], dxy[i, :hl[i]].cpu().numpy())
+    dd.dd_unload_mesh(ctx, mid)
+
+
 def test_errors(env):
     dd, ctx = env
     wl, po, P = case("grid24")
