@@ -316,9 +316,10 @@ __global__ void __launch_bounds__(256) two_pass_kernel(const float *__restrict__
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nvec = (int)(k_pad >> 2);
     float s0 = 0.0f, s1 = 0.0f;
-    auto chunk = [&](const float4(&v)[4], int64_t, int c0) {
+    constexpr int U = 8;       // float4 per lane and buffer: 2 x 4 KB per warp in flight
+    auto chunk = [&](const float4(&v)[U], int64_t, int c0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int c = c0 + u * 32 + lane;
             if (FAM == kAlpha) {
                 // every lane takes part (the first pass votes per group of four entries)
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(256) two_pass_kernel(const float *__restrict__
         if (lane == 0) out[(int64_t)a * n_v + x] = sum;
         s0 = s1 = 0.0f;
     };
-    stream_rows<4>(P, n_v, k_pad, warp, nwarps, lane, chunk, done);
+    stream_rows<U>(P, n_v, k_pad, warp, nwarps, lane, chunk, done);
 }
 
 }  // namespace
