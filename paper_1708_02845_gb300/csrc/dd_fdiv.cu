@@ -34,6 +34,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "dd_f32x2.cuh"
 #include "dd_internal.h"
 #include "dd_splitlog.cuh"
 
@@ -144,16 +145,27 @@ __device__ __forceinline__ float klrev_logp_term(float pt, float lmt, float Ebt,
 // P_x = P_t = 0 and give 0).
 __device__ __forceinline__ void alpha_fast4(const float (&px)[4], const float (&pt)[4], const float (&ft)[4],
                                             const float (&et)[4], const FdParams &q, float (&t)[4]) {
+    // the adds and multiplies two entries at a time in packed FP32x2 (each half
+    // rounds exactly as the scalar operation: a product is fma(a, b, 0))
+    const f2_t mone = pk(-1.0f, -1.0f), zero = pk(0.0f, 0.0f);
+    const f2_t e2 = pk(q.p, q.p), nie2 = pk(-q.inv_e, -q.inv_e), lin2 = pk(q.lin, q.lin);
     bool special = false;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int bits = __float_as_int(fmaxf(px[j], FLT_MIN));
-        const float lf = lg2_mant(bits);
-        const float eb = __int_as_float((int)__funnelshift_r((unsigned)bits, (unsigned)kMagicHi, 23));
-        const float L2 = __fadd_rn(__fadd_rn(ft[j], -lf), __fadd_rn(et[j], -eb));
-        const float ue = ex2_hw(q.p * L2);
-        t[j] = q.lin * __fmaf_rn(-px[j] * q.inv_e, ue - 1.0f, pt[j] - px[j]);
-        special |= px[j] == 0.0f || pt[j] == 0.0f;
+    for (int h = 0; h < 2; ++h) {
+        const int j0 = 2 * h, j1 = 2 * h + 1;
+        const int b0 = __float_as_int(fmaxf(px[j0], FLT_MIN)), b1 = __float_as_int(fmaxf(px[j1], FLT_MIN));
+        const f2_t lf = pk(lg2_mant(b0), lg2_mant(b1));
+        const f2_t eb = pk(__int_as_float((int)__funnelshift_r((unsigned)b0, (unsigned)kMagicHi, 23)),
+                           __int_as_float((int)__funnelshift_r((unsigned)b1, (unsigned)kMagicHi, 23)));
+        const f2_t px2 = pk(px[j0], px[j1]), pt2 = pk(pt[j0], pt[j1]);
+        // L2 = (lg2 m_t - lg2 m_x) + (E_t - E_x)
+        const f2_t L2 = add2(fma2(lf, mone, pk(ft[j0], ft[j1])), fma2(eb, mone, pk(et[j0], et[j1])));
+        float y0, y1;
+        upk(fma2(L2, e2, zero), y0, y1);
+        const f2_t um1 = add2(pk(ex2_hw(y0), ex2_hw(y1)), mone);                    // 2^(e L2) - 1
+        const f2_t r = fma2(fma2(px2, nie2, zero), um1, fma2(px2, mone, pt2));      // (P_t - P_x) - P_x um1 / e
+        upk(fma2(r, lin2, zero), t[j0], t[j1]);
+        special |= px[j0] == 0.0f || pt[j0] == 0.0f || px[j1] == 0.0f || pt[j1] == 0.0f;
     }
     if (__any_sync(0xffffffffu, special)) {
         const float at_px0 = q.alpha_gt1 ? INFINITY : q.lin;
