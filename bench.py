@@ -66,7 +66,7 @@ STEP_LAUNCHES = 6
 # 64-target column of tiles: 16 x 3.03 GB.
 TRAFFIC = {
     "grid140": {},
-    "grid450": {"T": 1024, "S": 16, "field_tile_kernel": 50092987319, "trace_kernel": 307350638},
+    "grid450": {"T": 1024, "S": 16, "field_tile_kernel": 50085696804, "trace_kernel": 307603236},
 }
 # the same for one field_stream_kernel launch of the grid450 single-target pass
 STREAM_TRAFFIC_BYTES = 3035740160    # 3,032,217,088 read + 3,523,072 written (4 n k_pad = 3.03 GB of P)
@@ -805,8 +805,9 @@ def mid_section(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 8):
     """A mid-size grid for full ncu captures (a few GB on the device): N = 300
     with 12 obstacles (n = 86,449, k = 2,122, P = 0.73 GB, larger than L2).
     The single-target dense stream (KL+TV), the sparse pass (KL+TV, Section V),
-    the split-BF16 KL GEMM and the FP32 KL+TV pass for 512 targets, each timed
-    with CUDA events (L2 flushed before every launch)."""
+    the split-BF16 KL GEMM, the FP32 KL+TV pass for 512 targets and the
+    alpha (0.5) and reverse-KL fields of one target, each timed with CUDA
+    events (L2 flushed before every launch)."""
     import torch
     from synthetic import workloads
     T = 512
@@ -843,6 +844,13 @@ def mid_section(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 8):
     out2 = torch.empty((2, T, n_v), dtype=torch.float32, device=dev)
     dd.dd_distance(ctx, mid, tl, 3, dd.DD_PREC_FP32, out2)      # the first call runs the tile autotuner
     tile_ms = timed(lambda i: dd.dd_distance(ctx, mid, tl, 3, dd.DD_PREC_FP32, out2), 4)
+    # two f-divergence families of the two-pass kernel, one target per call
+    outd = torch.empty((1, n_v), dtype=torch.float32, device=dev)
+    fdiv = {}
+    for name, fam, prm in (("alpha0.5", dd.DD_DIV_ALPHA, 0.5), ("kl_reverse", dd.DD_DIV_KL_REVERSE, 0.0)):
+        dd.dd_divergence(ctx, mid, [tl[0]], fam, prm, outd)
+        f_ms = timed(lambda i: dd.dd_divergence(ctx, mid, [tl[i]], fam, prm, outd), reps)
+        fdiv[name] = {"ms": round(f_ms, 4), "gbs": round(4.0 * n_v * k_pad / (f_ms / 1e3) / 1e9, 1)}
     dd.dd_unload_mesh(ctx, mid)
     issued = 3 * 2.0 * n_v * k * T / (gemm_ms / 1e3) / 1e12
     return {"workload": "grid300: n=%d, k=%d, P=%.2f GB FP32" % (n_v, k, 4.0 * n_v * k_pad / 1e9),
@@ -850,6 +858,7 @@ def mid_section(dd, ctx, dev, stream, flush, pk, pk_kind, reps: int = 8):
             "dense_stream_gbs": round(4.0 * n_v * k_pad / (dense_ms / 1e3) / 1e9, 1),
             "sparse_ms": round(sparse_ms, 4), "gemm_T": T, "gemm_ms": round(gemm_ms, 4),
             "fp32_fields_ms": round(tile_ms, 4), "tile_shapes": dd.dd_tuning_table().strip().splitlines(),
+            "f_divergences": fdiv,
             "gemm_tflops_issued": round(issued, 1), "peak_bf16": pk.get("bf16_tflops"), "peak_source": pk_kind}
 
 

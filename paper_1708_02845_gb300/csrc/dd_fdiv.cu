@@ -153,7 +153,8 @@ __device__ __forceinline__ void alpha_fast4(const float (&px)[4], const float (&
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int j0 = 2 * h, j1 = 2 * h + 1;
-        const int b0 = __float_as_int(fmaxf(px[j0], FLT_MIN)), b1 = __float_as_int(fmaxf(px[j1], FLT_MIN));
+        // no clamp: P holds no subnormals, and a zero entry takes its limit below
+        const int b0 = __float_as_int(px[j0]), b1 = __float_as_int(px[j1]);
         const f2_t lf = pk(lg2_mant(b0), lg2_mant(b1));
         const f2_t eb = pk(__int_as_float((int)__funnelshift_r((unsigned)b0, (unsigned)kMagicHi, 23)),
                            __int_as_float((int)__funnelshift_r((unsigned)b1, (unsigned)kMagicHi, 23)));
@@ -165,7 +166,11 @@ __device__ __forceinline__ void alpha_fast4(const float (&px)[4], const float (&
         const f2_t um1 = add2(pk(ex2_hw(y0), ex2_hw(y1)), mone);                    // 2^(e L2) - 1
         const f2_t r = fma2(fma2(px2, nie2, zero), um1, fma2(px2, mone, pt2));      // (P_t - P_x) - P_x um1 / e
         upk(fma2(r, lin2, zero), t[j0], t[j1]);
-        special |= px[j0] == 0.0f || pt[j0] == 0.0f || px[j1] == 0.0f || pt[j1] == 0.0f;
+        // a zero factor among P_x, P_t (a product that underflows only sends the
+        // warp through the selection, which leaves every other entry as it is)
+        float z0, z1;
+        upk(fma2(px2, pt2, zero), z0, z1);
+        special |= (z0 == 0.0f) | (z1 == 0.0f);
     }
     if (__any_sync(0xffffffffu, special)) {
         const float at_px0 = q.alpha_gt1 ? INFINITY : q.lin;
@@ -226,6 +231,10 @@ __device__ __forceinline__ void stream_rows(const float *__restrict__ P, int64_t
         ch = cn;
     }
 }
+
+// floats per staged row of two_pass_kernel: k_pad rounded up to whole
+// chunks of 32 lanes x 8 float4
+__host__ __device__ constexpr int64_t two_pass_pitch(int64_t k_pad) { return (k_pad + 1023) / 1024 * 1024; }
 
 // LP (reverse KL only, may be null): log2 P; an entry whose FP32 value is 0
 // takes log P[x,b] from it instead of the clamp at FLT_MIN
@@ -311,15 +320,20 @@ __global__ void __launch_bounds__(256) two_pass_kernel(const float *__restrict__
                                                        const float *__restrict__ sP, const float *__restrict__ sL,
                                                        const float *__restrict__ sE, const float *__restrict__ sF,
                                                        FdParams q, float *__restrict__ out) {
+    constexpr int U = 8;       // float4 per lane and buffer: 2 x 4 KB per warp in flight
     extern __shared__ __align__(16) float fsm[];
     __shared__ float tab[2 * kLogTab];
-    float *tP = fsm, *tL = fsm + k_pad, *tE = fsm + 2 * k_pad, *tF = fsm + 3 * k_pad;
+    // alpha: the staged rows zero-padded to whole chunks (two_pass_pitch), so
+    // that every lane of a chunk reads its target entries without a test
+    const int64_t kp = FAM == kAlpha ? two_pass_pitch(k_pad) : k_pad;
+    float *tP = fsm, *tL = fsm + kp, *tE = fsm + 2 * kp, *tF = fsm + 3 * kp;
     const int a = blockIdx.y;
-    for (int64_t b = threadIdx.x; b < k_pad; b += blockDim.x) {
-        tP[b] = sP[(int64_t)a * k_pad + b];
-        tL[b] = sL[(int64_t)a * k_pad + b];
-        tE[b] = sE[(int64_t)a * k_pad + b];
-        tF[b] = sF[(int64_t)a * k_pad + b];
+    for (int64_t b = threadIdx.x; b < kp; b += blockDim.x) {
+        const bool in = b < k_pad;
+        tP[b] = in ? sP[(int64_t)a * k_pad + b] : 0.0f;
+        tL[b] = in ? sL[(int64_t)a * k_pad + b] : 0.0f;
+        tE[b] = in ? sE[(int64_t)a * k_pad + b] : 0.0f;
+        tF[b] = in ? sF[(int64_t)a * k_pad + b] : 0.0f;
     }
     build_log_table(tab);
     __syncthreads();
@@ -328,18 +342,16 @@ __global__ void __launch_bounds__(256) two_pass_kernel(const float *__restrict__
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int nvec = (int)(k_pad >> 2);
     float s0 = 0.0f, s1 = 0.0f;
-    constexpr int U = 8;       // float4 per lane and buffer: 2 x 4 KB per warp in flight
     auto chunk = [&](const float4(&v)[U], int64_t, int c0) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int c = c0 + u * 32 + lane;
             if (FAM == kAlpha) {
-                // every lane takes part (the first pass votes per group of four entries)
-                const bool in = c < nvec;
-                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 p4 = in ? reinterpret_cast<const float4 *>(tP)[c] : z;
-                const float4 f4 = in ? reinterpret_cast<const float4 *>(tF)[c] : z;
-                const float4 e4 = in ? reinterpret_cast<const float4 *>(tE)[c] : z;
+                // every lane takes part (the first pass votes per group of four
+                // entries); past the row's end P and the padded target row are 0
+                const float4 p4 = reinterpret_cast<const float4 *>(tP)[c];
+                const float4 f4 = reinterpret_cast<const float4 *>(tF)[c];
+                const float4 e4 = reinterpret_cast<const float4 *>(tE)[c];
                 const float px[4] = {v[u].x, v[u].y, v[u].z, v[u].w}, pt[4] = {p4.x, p4.y, p4.z, p4.w};
                 const float ft[4] = {f4.x, f4.y, f4.z, f4.w}, et[4] = {e4.x, e4.y, e4.z, e4.w};
                 float t[4];
@@ -451,7 +463,8 @@ dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *
     if ((family == DD_DIV_KL_REVERSE && !LP) || alpha_fast) {
         // two passes (hardware mantissa logs, then the table form near the target)
         const float *sF = sE + (int64_t)T * k_pad;
-        const size_t smem4 = 4 * (size_t)k_pad * sizeof(float);
+        const size_t smem4 =
+            4 * (size_t)(family == DD_DIV_ALPHA ? two_pass_pitch(k_pad) : k_pad) * sizeof(float);
         if (smem4 <= 200 * 1024) {
             auto kern = family == DD_DIV_ALPHA ? two_pass_kernel<kAlpha> : two_pass_kernel<kKlRev>;
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
