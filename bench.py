@@ -55,18 +55,20 @@ WORKLOADS = {
                         "+ %dx%d KL paths per step"},
 }
 HEADLINE = "grid450"
-# kernels one dd_query step launches at most: target staging, field tile,
-# exact KL recompute near the targets, triangle rates and vertex decisions
-# (only when 128 or more paths share a field), path walk
-STEP_LAUNCHES = 6
+# kernels one dd_query step launches at most: target staging, the targets in
+# the tiled layout, field tile, exact KL recompute near the targets, triangle
+# rates and vertex decisions (only when 128 or more paths share a field),
+# path walk
+STEP_LAUNCHES = 7
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from
 # ncu captures of the step's kernels (means over the captured query steps);
 # absent where no capture of the current kernel exists; used only when the
-# step runs the captured (T, S).  grid450's tile launch reads P once per
-# 64-target column of tiles: 16 x 3.03 GB.
+# step runs the captured (T, S).  grid450's tile launch (the pipelined tile
+# on the tiled copy of P) reads each pair of row tiles from DRAM about once:
+# the 16 CTAs of one pair run together and share it through L2.
 TRAFFIC = {
     "grid140": {},
-    "grid450": {"T": 1024, "S": 16, "field_tile_kernel": 50085696804, "trace_kernel": 307603236},
+    "grid450": {"T": 1024, "S": 16, "field_tile_kernel": 10150322124, "trace_kernel": 308048085},
 }
 # the same for one field_stream_kernel launch of the grid450 single-target pass
 STREAM_TRAFFIC_BYTES = 3035740160    # 3,032,217,088 read + 3,523,072 written (4 n k_pad = 3.03 GB of P)

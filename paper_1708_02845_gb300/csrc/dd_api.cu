@@ -150,6 +150,14 @@ void release(DevMesh &m, T *&p, int64_t bytes) {
     p = nullptr;
 }
 
+// the tiled copy of P and of its log2 (the pipelined many-target field pass)
+void drop_tiled(DevMesh &m) {
+    const int64_t bytes = ((m.n_v + 127) / 128) * 128 * m.pt_kt * (int64_t)sizeof(float);
+    release(m, m.pt_p, bytes);
+    release(m, m.pt_l, bytes);
+    m.pt_kt = 0;
+}
+
 void drop_sparse(DevMesh &m) {
     release(m, m.sp_rowsum, m.n_v * (int64_t)sizeof(long long));
     release(m, m.sp_off, (m.n_v + 1) * (int64_t)sizeof(int64_t));
@@ -163,6 +171,7 @@ void drop_sparse(DevMesh &m) {
 // sparse rows) goes when P is recomputed or replaced
 void drop_derived(DevMesh &m) {
     release(m, m.LP, m.n_v * m.k_pad * (int64_t)sizeof(float));
+    drop_tiled(m);
     release(m, m.p_hi, m.n_v * m.kb * 2);
     release(m, m.p_lo, m.n_v * m.kb * 2);
     release(m, m.ex, m.n_v * (int64_t)sizeof(float));
@@ -282,9 +291,22 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
         if ((st = upload(ctx, S_ORDER, o.data(), o.size() * sizeof(int32_t))) != DD_OK) return st;
         order = reinterpret_cast<const int32_t *>(ctx->scratch[S_ORDER]);
     }
-    if (kl || tv)
+    if (kl || tv) {
+        // more than two targets: the tiled copy of P (built once per mesh) and the
+        // targets staged in the same layout make the pipelined tile available
+        TiledArgs ta{};
+        const TiledArgs *tiled = nullptr;
+        if (T > 2) {
+            std::string err;
+            if ((st = prepare_tiled(m, ctx->stream, err)) != DD_OK) return set_err(ctx, st, err);
+            if ((st = ensure_scratch(ctx, S_TSTAGE, tiled_target_bytes(m.k_pad, T))) != DD_OK) return st;
+            float *ts = reinterpret_cast<float *>(ctx->scratch[S_TSTAGE]);
+            ta = TiledArgs{m.pt_p, m.pt_l, ts, ts + tiled_target_bytes(m.k_pad, T) / (2 * sizeof(float)), m.pt_kt};
+            tiled = &ta;
+        }
         launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream, -1, m.LP != nullptr,
-                           order);
+                           order, tiled);
+    }
     if (klt) {
         // the target-weighted KL is the reverse-KL member of the f-divergence kernels
         std::string err;
@@ -645,6 +667,7 @@ dd_status dd_log_poisson_kernel(dd_ctx *ctx, int32_t mesh, double tol, int32_t m
         release(*m, m->p_hi, m->n_v * m->kb * 2);
         release(*m, m->p_lo, m->n_v * m->kb * 2);
         release(*m, m->ex, m->n_v * (int64_t)sizeof(float));
+        drop_tiled(*m);
         m->kb = 0;
         drop_sparse(*m);
         std::string err;

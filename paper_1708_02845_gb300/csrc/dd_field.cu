@@ -604,6 +604,229 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
     }
 }
 
+// ------------------------------------------------------------------ pipelined tile (tiled layout)
+// The tile above spends a fifth of its time staging: every 32-column chunk is
+// transposed through shared memory and its logarithms formed, between two
+// barriers, while the FMA pipe waits.  The pipelined tile takes both out of
+// the loop.  The mesh keeps a second copy of P in a tiled layout, [row tile
+// of 64][column][row in tile], with the one-number log2 of every entry beside
+// it in the same layout (formed once per mesh, by the same fast_l2); each
+// call stages its targets the same way ([target tile of 64][column][target],
+// P and log2).  A stage -- 64 columns of the CTA's two row tiles and of its
+// target tile -- is then six contiguous 16 KB blocks, brought into shared
+// memory by bulk async copies that complete on an mbarrier; two stages
+// alternate, the CTA's warps release a stage on a second mbarrier and one
+// thread refills it.  Every wait is bounded (error flag, no output).  The
+// sums are those of tile_body<64, 64, 4, 4> -- the same operations on the
+// same operands in the same order, partial sums merged after the same
+// columns -- so the two kernels give bit-identical fields.
+constexpr int kTiledRows = 64;      // rows (and targets) per tile of the tiled layout
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// P and fast_l2(P) of one row tile x 32 columns into the tiled layout (zero
+// past n_v and k_pad; fast_l2(0) = -127 is finite)
+__global__ void tiled_layout_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad, int64_t k32,
+                                    float *__restrict__ PT, float *__restrict__ LT) {
+    __shared__ float t[kTiledRows][33];
+    const int64_t xt = blockIdx.x, b0 = (int64_t)blockIdx.y * 32;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int r = threadIdx.x / 8 + 32 * h, c4 = threadIdx.x % 8;
+        const int64_t x = xt * kTiledRows + r, b = b0 + 4 * c4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (x < n_v && b < k_pad) v = *reinterpret_cast<const float4 *>(P + x * k_pad + b);
+        t[r][4 * c4] = v.x;
+        t[r][4 * c4 + 1] = v.y;
+        t[r][4 * c4 + 2] = v.z;
+        t[r][4 * c4 + 3] = v.w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int idx = threadIdx.x + 256 * i;
+        const int c = idx / kTiledRows, r = idx % kTiledRows;
+        const float v = t[r][c];
+        const int64_t o = (xt * k32 + b0 + c) * kTiledRows + r;
+        PT[o] = v;
+        LT[o] = fast_l2(v);
+    }
+}
+
+// the staged targets (sP, and sE / sF when the staging holds logarithms of
+// entries below FLT_MIN) into the tiled layout: -P[t,b] and -log2 P[t,b],
+// the target-side log2 formed exactly as tile_body forms it
+__global__ void tiled_targets_kernel(const float *__restrict__ sP, const float *__restrict__ sE,
+                                     const float *__restrict__ sF, int32_t T, int64_t k_pad, int64_t k32,
+                                     float *__restrict__ TQ, float *__restrict__ TL) {
+    const int at = blockIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.y * 32;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int idx = threadIdx.x + 256 * i;
+        const int c = idx / kTiledRows, al = idx % kTiledRows;
+        const int a = at * kTiledRows + al;
+        const int64_t b = b0 + c;
+        const bool ok = a < T && b < k_pad;
+        const float q = ok ? sP[(int64_t)a * k_pad + b] : 0.0f;
+        float lt;
+        if (sF) {
+            const float ev = ok ? sE[(int64_t)a * k_pad + b] : 12583039.0f;
+            const float fv = ok ? sF[(int64_t)a * k_pad + b] : 0.0f;
+            lt = __fadd_rn(__fsub_rn(ev, 12583039.0f), fv);
+        } else {
+            lt = fast_l2(fmaxf(q, FLT_MIN));
+        }
+        const int64_t o = ((int64_t)at * k32 + b) * kTiledRows + al;
+        TQ[o] = q;
+        TL[o] = lt;
+    }
+}
+
+template <bool KL, bool TV, int H, int PB, int PS, int UNR>
+__global__ void __launch_bounds__(256 * H, 2 / H) field_tile_pipe_kernel(const float *__restrict__ PT,
+                                                                      const float *__restrict__ LT, int64_t n_v,
+                                                                      int64_t kt, const float *__restrict__ TQ,
+                                                                      const float *__restrict__ TL, int32_t T,
+                                                                      float *__restrict__ out_kl,
+                                                                      float *__restrict__ out_tv,
+                                                                      int *__restrict__ err) {
+    constexpr int RM = 4, CN = 4, NW = 8 * H;
+    constexpr int TCH = PB * kTiledRows;            // floats per array, stage and 64-row (or target) tile
+    constexpr int RCH = H * TCH;
+    constexpr int SST = 2 * RCH + 2 * TCH;          // floats per stage
+    extern __shared__ __align__(128) float psm[];   // [stage][P rows, log2 rows, P targets, log2 targets]
+    __shared__ __align__(8) uint64_t full[PS], empty[PS];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tx = tid % (kTiledRows / CN), ty = tid / (kTiledRows / CN);
+    // target tiles vary fastest over the grid: the CTAs that read one pair of
+    // row tiles run together and share it through L2
+    const int64_t x0 = (int64_t)blockIdx.y * H * kTiledRows;
+    const int a0 = blockIdx.x * kTiledRows;
+    const float *gP = PT + (int64_t)blockIdx.y * H * kt * kTiledRows;
+    const float *gL = LT + (int64_t)blockIdx.y * H * kt * kTiledRows;
+    const float *gQ = TQ + (int64_t)blockIdx.x * kt * kTiledRows;
+    const float *gT = TL + (int64_t)blockIdx.x * kt * kTiledRows;
+    const int nch = (int)(kt / PB);
+    constexpr uint32_t kArr = TCH * sizeof(float);
+    constexpr uint32_t kStageBytes = kArr * (H * (KL ? 2 : 1) + (KL ? 1 : 0) + (TV ? 1 : 0));
+    auto issue = [&](int c) {
+        const int s = c % PS;
+        float *st = psm + s * SST;
+        const int64_t go = (int64_t)c * TCH;
+        mbar_expect_tx(&full[s], kStageBytes);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            bulk_g2s(st + h * TCH, gP + (int64_t)h * kt * kTiledRows + go, kArr, &full[s]);
+            if (KL) bulk_g2s(st + RCH + h * TCH, gL + (int64_t)h * kt * kTiledRows + go, kArr, &full[s]);
+        }
+        if (TV) bulk_g2s(st + 2 * RCH, gQ + go, kArr, &full[s]);
+        if (KL) bulk_g2s(st + 2 * RCH + TCH, gT + go, kArr, &full[s]);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < PS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int issued = 0;
+    if (tid == 0)
+        for (; issued < PS && issued < nch; ++issued) issue(issued);
+
+    float kl[RM][CN], tv[RM][CN], klc[RM][CN], ckl[RM][CN], ctv[RM][CN];
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int c = 0; c < CN; ++c) kl[r][c] = tv[r][c] = klc[r][c] = ckl[r][c] = ctv[r][c] = 0.0f;
+    // this thread's rows within the stage: 64-row half ty / 16, rows (ty % 16) * 4 ..
+    const int roff = (ty / 16) * TCH + (ty % 16) * RM;
+    bool ok = true;
+    int c = 0;
+    for (; c < nch; ++c) {
+        const int s = c % PS;
+        // refill the stage every warp released last with the chunk PS after it
+        if (tid == 0 && c >= 1 && issued < nch) {
+            const int cf = c - 1;
+            if (!mbar_wait_suspend(&empty[cf % PS], (uint32_t)(cf / PS) & 1u, err)) {
+                ok = false;
+                break;
+            }
+            issue(issued++);
+        }
+        if (!mbar_wait_suspend(&full[s], (uint32_t)(c / PS) & 1u, err)) {
+            ok = false;
+            break;
+        }
+        const float *cP = psm + s * SST + roff, *cL = cP + RCH;
+        const float *cQ = psm + s * SST + 2 * RCH + tx * CN, *cT = cQ + TCH;
+#pragma unroll UNR
+        for (int j = 0; j < PB; ++j) {
+            float rP[RM], rL[RM], tQ[CN], tL[CN];
+            {
+                const float4 p4 = *reinterpret_cast<const float4 *>(cP + j * kTiledRows);
+                rP[0] = p4.x, rP[1] = p4.y, rP[2] = p4.z, rP[3] = p4.w;
+                if (KL) {
+                    const float4 l4 = *reinterpret_cast<const float4 *>(cL + j * kTiledRows);
+                    rL[0] = l4.x, rL[1] = l4.y, rL[2] = l4.z, rL[3] = l4.w;
+                    const float4 t4 = *reinterpret_cast<const float4 *>(cT + j * kTiledRows);
+                    tL[0] = t4.x, tL[1] = t4.y, tL[2] = t4.z, tL[3] = t4.w;
+                }
+                if (TV) {
+                    const float4 q4 = *reinterpret_cast<const float4 *>(cQ + j * kTiledRows);
+                    tQ[0] = q4.x, tQ[1] = q4.y, tQ[2] = q4.z, tQ[3] = q4.w;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int q = 0; q < CN; ++q) {
+                    if (KL) ckl[r][q] = __fmaf_rn(rP[r], __fadd_rn(rL[r], -tL[q]), ckl[r][q]);
+                    if (TV) ctv[r][q] = __fadd_rn(ctv[r][q], fabsf(__fadd_rn(rP[r], -tQ[q])));
+                }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        // 64-column partial sums, merged at the end of every 64 columns
+        if (((c + 1) * PB) % 64 == 0 || c == nch - 1) {
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int q = 0; q < CN; ++q) {
+                    const float y = __fsub_rn(ckl[r][q], klc[r][q]);
+                    const float t = __fadd_rn(kl[r][q], y);
+                    klc[r][q] = __fsub_rn(__fsub_rn(t, kl[r][q]), y);
+                    kl[r][q] = t;
+                    tv[r][q] = __fadd_rn(tv[r][q], ctv[r][q]);
+                    ckl[r][q] = ctv[r][q] = 0.0f;
+                }
+        }
+    }
+    if (!ok) {
+        // a wait gave up (the error flag is set): let this CTA's copies in flight land, waiting
+        // again with a limit, and write nothing
+        if (tid == 0)
+            for (int cf = c; cf < issued; ++cf)
+                if (!mbar_wait_suspend(&full[cf % PS], (uint32_t)(cf / PS) & 1u, err)) break;
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        const int64_t x = x0 + ty * RM + r;
+        if (x >= n_v) continue;
+#pragma unroll
+        for (int q = 0; q < CN; ++q) {
+            const int a = a0 + tx * CN + q;
+            if (a >= T) continue;
+            if (KL && out_kl) out_kl[(int64_t)a * n_v + x] = __fmul_rn(kl[r][q], kLn2);
+            if (TV && out_tv) out_tv[(int64_t)a * n_v + x] = tv[r][q];
+        }
+    }
+}
+
 // Exact recompute after the tile pass: one warp reads the first-pass KL of 32
 // rows of one target, rows g, g + G, g + 2G, ... (G = ceil(n_v / 32) groups
 // per target), and every row below kTileExactBelow among them is recomputed
@@ -823,11 +1046,41 @@ __global__ void batch_stage_kernel(const BatchProblem *__restrict__ probs, const
 // that no operand needs a broadcast, was measured at 0.41 ms against 0.36 ms
 // for shape 1 on 64 grid140 targets, and dropped: the inner loop is bound by
 // shared-memory latency, not by FP32 issue)
-constexpr int kNumShapes = 3;
-const int kShapeRows[kNumShapes] = {64, 128, 256}, kShapeTargets[kNumShapes] = {64, 32, 16};
+constexpr int kNumShapes = 4;
+const int kShapeRows[kNumShapes] = {64, 128, 256, 128}, kShapeTargets[kNumShapes] = {64, 32, 16, 64};
+constexpr int kPipeShape = 3;      // the pipelined tile on the tiled layout (single-problem launches only)
+
+// the pipelined tile: 128 rows x 64 targets per CTA of 512 threads (one CTA per
+// SM), two stages of 64 columns (192 KB of shared memory); the column loop is
+// unrolled 16 deep for KL+TV (a longer body measured slower) and 32 deep for
+// one field
+void launch_pipe(const TiledArgs &ta, int64_t n_v, int32_t T, float *out_kl, float *out_tv, int *err,
+                 cudaStream_t s) {
+    constexpr int H = 2, PB = 64, PS = 2;
+    const dim3 g((unsigned)((T + kTiledRows - 1) / kTiledRows),
+                 (unsigned)((n_v + H * kTiledRows - 1) / (H * kTiledRows)));
+    auto go = [&](auto kern) {
+        const size_t smem = (size_t)PS * (2 * H + 2) * PB * kTiledRows * sizeof(float);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        KMark km_("field_tile_kernel", s);
+        kern<<<g, 256 * H, smem, s>>>(ta.PT, ta.LT, n_v, ta.kt, ta.TQ, ta.TL, T, out_kl, out_tv, err);
+    };
+    if (out_kl && out_tv)
+        go(field_tile_pipe_kernel<true, true, H, PB, PS, 16>);
+    else if (out_kl)
+        go(field_tile_pipe_kernel<true, false, H, PB, PS, 32>);
+    else
+        go(field_tile_pipe_kernel<false, true, H, PB, PS, 32>);
+}
 
 void launch_variant(int v, const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL,
-                    const float *sE, const float *sF, int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
+                    const float *sE, const float *sF, int32_t T, float *out_kl, float *out_tv, cudaStream_t s,
+                    const TiledArgs *tiled = nullptr, int *err = nullptr) {
+    if (v == kPipeShape && tiled && err) {
+        launch_pipe(*tiled, n_v, T, out_kl, out_tv, err, s);
+        return;
+    }
+    if (v == kPipeShape) v = 0;
     if (v == 0)
         launch_tile<TileA, 64, 64, 4, 4>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s);
     else if (v == 1)
@@ -855,13 +1108,17 @@ std::tuple<int, int, int> tune_key(int64_t n_v, int64_t k_pad, int32_t T) {
 }
 
 int tune_variant(const float *P, int64_t n_v, int64_t k_pad, const float *sP, const float *sL, const float *sE,
-                 const float *sF, int32_t T, float *out_kl, float *out_tv, cudaStream_t s) {
-    // DD_TILE_SHAPE=0..2 pins the shape (tests run every shape through it)
+                 const float *sF, int32_t T, float *out_kl, float *out_tv, cudaStream_t s,
+                 const TiledArgs *tiled = nullptr, int *err = nullptr) {
+    const bool pipe = tiled && err;
+    // DD_TILE_SHAPE=0..3 pins the shape (tests run every shape through it)
     if (const char *pin = std::getenv("DD_TILE_SHAPE")) {
         const int v = std::atoi(pin);
-        if (v >= 0 && v < kNumShapes) return v;
+        if (v >= 0 && v < kNumShapes && (v != kPipeShape || pipe)) return v;
     }
-    const auto key = tune_key(n_v, k_pad, T);
+    // the classes of launches with and without the tiled layout are kept apart
+    auto key = tune_key(n_v, k_pad, T);
+    if (pipe) std::get<2>(key) += 100;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune.find(key);
@@ -873,9 +1130,11 @@ int tune_variant(const float *P, int64_t n_v, int64_t k_pad, const float *sP, co
     int best = 0;
     float best_ms = 1e30f;
     for (int v = 0; v < kNumShapes; ++v) {
-        launch_variant(v, P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s);   // warm-up
+        if (v == kPipeShape && !pipe) continue;
+        launch_variant(v, P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s, tiled, err);   // warm-up
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; ++r) launch_variant(v, P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s);
+        for (int r = 0; r < 3; ++r)
+            launch_variant(v, P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv, s, tiled, err);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -907,9 +1166,49 @@ void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int3
     }
 }
 
+int64_t tiled_k32(int64_t k_pad) { return (k_pad + 63) / 64 * 64; }
+
+size_t tiled_target_bytes(int64_t k_pad, int32_t T) {
+    return 2 * (size_t)((T + kTiledRows - 1) / kTiledRows) * (size_t)tiled_k32(k_pad) * kTiledRows * sizeof(float);
+}
+
+dd_status prepare_tiled(DevMesh &m, cudaStream_t s, std::string &err) {
+    if (m.pt_p) return DD_OK;
+    // row tiles in pairs (a CTA of the wide shape takes two), columns to a multiple of 64
+    const int64_t k32 = tiled_k32(m.k_pad), nt = (m.n_v + 2 * kTiledRows - 1) / (2 * kTiledRows) * 2;
+    const size_t ne = (size_t)nt * k32 * kTiledRows;
+    void *pp = nullptr, *pl = nullptr;
+    if (cudaMalloc(&pp, ne * sizeof(float)) != cudaSuccess || cudaMalloc(&pl, ne * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        if (pp) cudaFree(pp);
+        if (pl) cudaFree(pl);
+        err = "allocation of the tiled copy of P failed";
+        return DD_ENOMEM;
+    }
+    {
+        KMark km_("tiled_layout_kernel", s);
+        tiled_layout_kernel<<<dim3((unsigned)nt, (unsigned)(k32 / 32)), 256, 0, s>>>(m.P, m.n_v, m.k_pad, k32,
+                                                                                    (float *)pp, (float *)pl);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFree(pp);
+        cudaFree(pl);
+        err = std::string("tiled layout launch failed: ") + cudaGetErrorString(e);
+        return DD_ECUDA;
+    }
+    m.pt_p = (float *)pp;
+    m.pt_l = (float *)pl;
+    m.pt_kt = k32;
+    m.owned.push_back(pp);
+    m.owned.push_back(pl);
+    m.bytes += (int64_t)(2 * ne * sizeof(float));
+    return DD_OK;
+}
+
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, float *out_kl,
                         float *out_tv, int *err_flag, cudaStream_t s, int variant, bool staged_logs,
-                        const int32_t *order) {
+                        const int32_t *order, const TiledArgs *tiled) {
     const float *sP = reinterpret_cast<const float *>(stage);
     const float *sL = sP + (int64_t)T * k_pad;
     const float *sE = sL + (int64_t)T * k_pad;
@@ -936,10 +1235,16 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
         }
         return;
     }
+    if (tiled) {
+        // the staged targets in the tiled layout (P and the target-side log2)
+        KMark km_("tiled_targets_kernel", s);
+        tiled_targets_kernel<<<dim3((unsigned)((T + kTiledRows - 1) / kTiledRows), (unsigned)(tiled->kt / 32)), 256,
+                               0, s>>>(sP, sE, tF, T, k_pad, tiled->kt, tiled->TQ, tiled->TL);
+    }
     const int v = (variant >= 0 && variant < kNumShapes)
                       ? variant
-                      : tune_variant(P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s);
-    launch_variant(v, P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s);
+                      : tune_variant(P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s, tiled, err_flag);
+    launch_variant(v, P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s, tiled, err_flag);
     if (out_kl) {
         const BatchProblem q{P, n_v, k_pad, sP, sL, sE, T, v, out_kl, nullptr, order};
         KMark km_("fix_kl_kernel", s);
@@ -1000,11 +1305,12 @@ void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const Bat
 std::string tuning_table() {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     std::string out;
-    const char *names[kNumShapes] = {"64x64", "128x32", "256x16"};
+    const char *names[kNumShapes] = {"64x64", "128x32", "256x16", "128x64 pipelined"};
     for (auto &kv : g_tune) {
-        char buf[128];
-        std::snprintf(buf, sizeof buf, "rows<=2^%d k_pad<=2^%d T<=2^%d: %s\n", std::get<0>(kv.first),
-                      std::get<1>(kv.first), std::get<2>(kv.first), names[kv.second]);
+        char buf[160];
+        const int tk = std::get<2>(kv.first);
+        std::snprintf(buf, sizeof buf, "rows<=2^%d k_pad<=2^%d T<=2^%d%s: %s\n", std::get<0>(kv.first),
+                      std::get<1>(kv.first), tk % 100, tk >= 100 ? " (tiled copy of P)" : "", names[kv.second]);
         out += buf;
     }
     return out;

@@ -65,6 +65,13 @@ struct DevMesh {
     void *p_hi = nullptr, *p_lo = nullptr;   // BF16 split of P, [n_v][kb] (built on first BF16 request)
     float *ex = nullptr;                     // [n_v] sum_b P log P (FP64-accumulated)
     int64_t kb = 0;                          // BF16 row pitch: k rounded up to 64
+    // tiled copy of P for the pipelined many-target field pass (built on the
+    // first FP32 request for more than two targets): [row tile of 64][column]
+    // [row in tile] over an even number of row tiles and k_pad rounded up to
+    // 64 columns (pt_kt), zero past n_v and k_pad; pt_l holds the one-number
+    // log2 of every entry
+    float *pt_p = nullptr, *pt_l = nullptr;
+    int64_t pt_kt = 0;
     // sparse fields (dd_sparsify): the threshold relative to the row maximum,
     // the sparsified P as CSR (each row's kept entries in column order), and
     // the exact total of every stored row (for the merged-bin extension)
@@ -103,16 +110,27 @@ dd_status refine_log_poisson(DevMesh &m, double tol, int32_t max_sweeps, cudaStr
 void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int32_t *targets, int32_t T,
                           float4 *stage, cudaStream_t s, int *bad_id = nullptr, const float *LP = nullptr);
 // FP32 fields.  out_kl / out_tv: [T][n_v] (either may be null).  variant: the
-// tile shape for T > 2 (0, 1, 2), or -1 for the autotuner's choice (which may
+// tile shape for T > 2 (0 .. 5), or -1 for the autotuner's choice (which may
 // run timed launches the first time a size class is seen).  staged_logs: the
 // staging took logarithms from log2 P (launch_stage_targets with LP), which
 // the tile kernel then reads instead of forming them from the staged entries.
 // order: null, or device [T], the order in which the exact recompute after the
 // tile pass visits the targets (spatially close targets one after the other
 // share the rows they recompute through L2).
+// tiled: null, or the tiled copies of P and log2 P (DevMesh::pt_p / pt_l)
+// with room for the staged targets in the same layout, which make the
+// pipelined tile shape (variant 5) available to the autotuner.
+struct TiledArgs {
+    const float *PT, *LT;        // [row tiles][kt][64]
+    float *TQ, *TL;              // [ceil(T / 64)][kt][64], filled by launch_fields_fp32
+    int64_t kt;
+};
+int64_t tiled_k32(int64_t k_pad);
+size_t tiled_target_bytes(int64_t k_pad, int32_t T);
+dd_status prepare_tiled(DevMesh &m, cudaStream_t s, std::string &err);
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T,
                         float *out_kl, float *out_tv, int *err_flag, cudaStream_t s, int variant = -1,
-                        bool staged_logs = false, const int32_t *order = nullptr);
+                        bool staged_logs = false, const int32_t *order = nullptr, const TiledArgs *tiled = nullptr);
 // One problem of a multi-domain field launch, and one output tile of it.
 struct BatchProblem {
     const float *P;
@@ -206,7 +224,7 @@ void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t
 
 // ---------------------------------------------------------------- context
 enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_META, S_ORDER,
-                 S_COUNT };
+                 S_TSTAGE, S_COUNT };
 
 struct MeshSlot {
     bool live = false;

@@ -275,28 +275,45 @@ def test_errors(env):
 
 
 def test_every_tile_shape_bit_identical(env, monkeypatch):
-    """The three tile shapes sum every (row, target) in the same order (32-term
-    chunks, compensated across chunks), so their fields are bit-identical; they
-    match the oracle."""
+    """The tile shapes sum every (row, target) in the same order (32-term
+    chunks, compensated across 64-column partial sums), so their fields are
+    bit-identical -- the three staged shapes and the pipelined shape on the
+    tiled copy of P, for KL+TV, KL alone and TV alone, on 70 targets (a
+    ragged second target tile) of a mesh whose row and column counts are not
+    multiples of the tiles; they match the oracle.  Replacing P replaces the
+    tiled copy: the pipelined shape then matches the oracle on the new P."""
     dd, ctx = env
     wl, po, P = case("grid37")
     mid = load(dd, ctx, wl.mesh)
     dd.dd_set_poisson_kernel(ctx, mid, P)
     targets = [int(t) for t in wl.targets]
-    outs = []
-    for shape in range(3):
+    assert len(targets) > 64 and len(targets) % 64 and wl.mesh.n_v % 128
+
+    def fields(shape, f_mask):
         monkeypatch.setenv("DD_TILE_SHAPE", str(shape))
-        out = torch.empty((2, len(targets), wl.mesh.n_v), dtype=torch.float32, device="cuda")
-        dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, out)
+        nf = 2 if f_mask == (dd.DD_F_KL | dd.DD_F_TV) else 1
+        out = torch.empty((nf, len(targets), wl.mesh.n_v), dtype=torch.float32, device="cuda")
+        dd.dd_distance(ctx, mid, targets, f_mask, dd.DD_PREC_FP32, out)
         dd.dd_sync(ctx)
-        outs.append(out.cpu().numpy())
+        return out.cpu().numpy()
+
+    for f_mask in (dd.DD_F_KL | dd.DD_F_TV, dd.DD_F_KL, dd.DD_F_TV):
+        outs = [fields(shape, f_mask) for shape in range(4)]
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+        if f_mask == (dd.DD_F_KL | dd.DD_F_TV):
+            for a, t in enumerate(targets):
+                assert field_error(outs[3][0, a], kl_field_fast(P, P[t])) <= TOL_FP32
+                assert field_error(outs[3][1, a], tv_field(P, P[t])) <= TOL_FP32
+                assert outs[3][0, a, t] == 0.0 and outs[3][1, a, t] == 0.0
+    # a new P (rows still distributions): the tiled copy follows it
+    P2 = 0.5 * (P + P[:, ::-1])
+    dd.dd_set_poisson_kernel(ctx, mid, np.ascontiguousarray(P2))
+    o = fields(3, dd.DD_F_KL | dd.DD_F_TV)
     monkeypatch.delenv("DD_TILE_SHAPE")
-    for o in outs[1:]:
-        assert np.array_equal(o, outs[0])
-    for a, t in enumerate(targets):
-        assert field_error(outs[2][0, a], kl_field_fast(P, P[t])) <= TOL_FP32
-        assert field_error(outs[2][1, a], tv_field(P, P[t])) <= TOL_FP32
-        assert outs[2][0, a, t] == 0.0 and outs[2][1, a, t] == 0.0
+    for a, t in enumerate(targets[:8]):
+        assert field_error(o[0, a], kl_field_fast(P2, P2[t])) <= TOL_FP32
+        assert field_error(o[1, a], tv_field(P2, P2[t])) <= TOL_FP32
     dd.dd_unload_mesh(ctx, mid)
 
 
