@@ -288,6 +288,12 @@ dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, in
  * but P[x,b] > 0 (a boundary row x of a column with no interior support) the
  * exact KL is +inf and the result is finite and at least 87; KLT is +inf on
  * every boundary row and the result there is at least 50.
+ * Memory: the first DD_PREC_FP32 call with T > 2 on a mesh stores a tiled
+ * copy of P and of its log2 beside P (2 x 4 n_v k_pad bytes, rounded up to
+ * whole tiles; kept until P is recomputed, refined or replaced or the mesh
+ * unloaded), and every such call stages its targets in the same layout
+ * (context scratch, 8 T k_pad bytes rounded up): the pipelined tile pass
+ * reads them.  DD_ENOMEM when the copy does not fit.
  * Errors: DD_EINVAL, DD_ESTATE (no Poisson kernel), DD_ENOMEM, DD_ECUDA. */
 dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
                       uint32_t f_mask, int32_t prec, float *out);
