@@ -616,10 +616,16 @@ __device__ __forceinline__ void tile_body(const float *__restrict__ P, int64_t n
 // target tile -- is then six contiguous 16 KB blocks, brought into shared
 // memory by bulk async copies that complete on an mbarrier; two stages
 // alternate, the CTA's warps release a stage on a second mbarrier and one
-// thread refills it.  Every wait is bounded (error flag, no output).  The
-// sums are those of tile_body<64, 64, 4, 4> -- the same operations on the
-// same operands in the same order, partial sums merged after the same
-// columns -- so the two kernels give bit-identical fields.
+// thread refills it.  Every wait is bounded (error flag, no output).  With
+// no staging phase left, the arithmetic is packed in FP32x2 over pairs of
+// targets (the targets are staged negated, so each difference is one packed
+// addition; the row operand is duplicated into both halves): a packed
+// instruction occupies the FMA pipe as long as its two halves but takes one
+// issue slot, and the slots it frees carry the shared-memory loads and the
+// loop while the pipe is busy.  The sums are those of tile_body<64, 64, 4, 4>
+// -- each half the same IEEE operation on the same operands, in the same
+// order, partial sums merged after the same columns -- so the two kernels
+// give bit-identical fields.
 constexpr int kTiledRows = 64;      // rows (and targets) per tile of the tiled layout
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -680,8 +686,8 @@ __global__ void tiled_targets_kernel(const float *__restrict__ sP, const float *
             lt = fast_l2(fmaxf(q, FLT_MIN));
         }
         const int64_t o = ((int64_t)at * k32 + b) * kTiledRows + al;
-        TQ[o] = q;
-        TL[o] = lt;
+        TQ[o] = -q;
+        TL[o] = -lt;
     }
 }
 
@@ -780,13 +786,29 @@ __global__ void __launch_bounds__(256 * H, 2 / H) field_tile_pipe_kernel(const f
                     tQ[0] = q4.x, tQ[1] = q4.y, tQ[2] = q4.z, tQ[3] = q4.w;
                 }
             }
+            // packed over pairs of targets: the row operands duplicated into both
+            // halves, the (negated) target values of a pair side by side
+            const f2_t nl[2] = {pk(tL[0], tL[1]), pk(tL[2], tL[3])};
+            const f2_t nq[2] = {pk(tQ[0], tQ[1]), pk(tQ[2], tQ[3])};
 #pragma unroll
-            for (int r = 0; r < RM; ++r)
+            for (int r = 0; r < RM; ++r) {
+                const f2_t p2 = pk(rP[r], rP[r]);
+                const f2_t l2 = pk(rL[r], rL[r]);
 #pragma unroll
-                for (int q = 0; q < CN; ++q) {
-                    if (KL) ckl[r][q] = __fmaf_rn(rP[r], __fadd_rn(rL[r], -tL[q]), ckl[r][q]);
-                    if (TV) ctv[r][q] = __fadd_rn(ctv[r][q], fabsf(__fadd_rn(rP[r], -tQ[q])));
+                for (int h = 0; h < 2; ++h) {
+                    if (KL) {
+                        f2_t acc = pk(ckl[r][2 * h], ckl[r][2 * h + 1]);
+                        acc = fma2(p2, add2(l2, nl[h]), acc);
+                        upk(acc, ckl[r][2 * h], ckl[r][2 * h + 1]);
+                    }
+                    if (TV) {
+                        float d0, d1;
+                        upk(add2(p2, nq[h]), d0, d1);
+                        ctv[r][2 * h] = __fadd_rn(ctv[r][2 * h], fabsf(d0));
+                        ctv[r][2 * h + 1] = __fadd_rn(ctv[r][2 * h + 1], fabsf(d1));
+                    }
                 }
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -1052,8 +1074,7 @@ constexpr int kPipeShape = 3;      // the pipelined tile on the tiled layout (si
 
 // the pipelined tile: 128 rows x 64 targets per CTA of 512 threads (one CTA per
 // SM), two stages of 64 columns (192 KB of shared memory); the column loop is
-// unrolled 16 deep for KL+TV (a longer body measured slower) and 32 deep for
-// one field
+// unrolled 16 deep for KL+TV and 32 deep for one field
 void launch_pipe(const TiledArgs &ta, int64_t n_v, int32_t T, float *out_kl, float *out_tv, int *err,
                  cudaStream_t s) {
     constexpr int H = 2, PB = 64, PS = 2;
