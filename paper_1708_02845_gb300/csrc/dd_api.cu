@@ -213,46 +213,11 @@ float *field_slot(float *dst, uint32_t f_mask, uint32_t bit, int64_t stride) {
     return dst + slot * stride;
 }
 
-// The order in which the exact KL recompute visits the targets: along a
-// Morton (Z-order) curve of their positions, 16 bits per axis over the
-// targets' bounding box, ties by index.
-std::vector<int32_t> morton_order(const DevMesh &m, const int32_t *targets, int32_t T) {
-    float x0 = 3.4e38f, y0 = 3.4e38f, x1 = -3.4e38f, y1 = -3.4e38f;
-    for (int32_t a = 0; a < T; ++a) {
-        const float x = m.xy_h[2 * (size_t)targets[a]], y = m.xy_h[2 * (size_t)targets[a] + 1];
-        x0 = std::min(x0, x);
-        x1 = std::max(x1, x);
-        y0 = std::min(y0, y);
-        y1 = std::max(y1, y);
-    }
-    const float sx = x1 > x0 ? 65535.0f / (x1 - x0) : 0.0f, sy = y1 > y0 ? 65535.0f / (y1 - y0) : 0.0f;
-    auto spread = [](uint32_t v) {   // bits of v at the even positions
-        v &= 0xFFFFu;
-        v = (v | (v << 8)) & 0x00FF00FFu;
-        v = (v | (v << 4)) & 0x0F0F0F0Fu;
-        v = (v | (v << 2)) & 0x33333333u;
-        v = (v | (v << 1)) & 0x55555555u;
-        return v;
-    };
-    std::vector<std::pair<uint32_t, int32_t>> key((size_t)T);
-    for (int32_t a = 0; a < T; ++a) {
-        const uint32_t qx = (uint32_t)((m.xy_h[2 * (size_t)targets[a]] - x0) * sx);
-        const uint32_t qy = (uint32_t)((m.xy_h[2 * (size_t)targets[a] + 1] - y0) * sy);
-        key[a] = {spread(qx) | (spread(qy) << 1), a};
-    }
-    std::sort(key.begin(), key.end());
-    std::vector<int32_t> order((size_t)T);
-    for (int32_t a = 0; a < T; ++a) order[a] = key[a].second;
-    return order;
-}
-
-// fields of T targets into dst [nf][T][n_v] (device), targets already in scratch
-// (h_targets: the same ids on the host, or null)
-// The fields of T targets into dst ([fields][T][n_v] by default; stride: the
-// distance between two fields' blocks when dst is a block of rows inside a
-// larger output)
+// The fields of T targets (ids already in device scratch) into dst
+// ([fields][T][n_v] by default; stride: the distance between two fields'
+// blocks when dst is a block of rows inside a larger output)
 dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t T, uint32_t f_mask, int32_t prec,
-                      float *dst, const int32_t *h_targets = nullptr, int64_t stride = -1) {
+                      float *dst, int64_t stride = -1) {
     if (stride < 0) stride = (int64_t)T * m.n_v;
     float *kl = field_slot(dst, f_mask, DD_F_KL, stride);
     float *tv = field_slot(dst, f_mask, DD_F_TV, stride);
@@ -285,12 +250,6 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
     if (st != DD_OK) return st;
     float4 *stage = reinterpret_cast<float4 *>(ctx->scratch[S_STAGE]);
     launch_stage_targets(m.P, m.n_v, m.k_pad, d_targets, T, stage, ctx->stream, nullptr, m.LP);
-    const int32_t *order = nullptr;
-    if (kl && h_targets && T > 2 && !m.xy_h.empty()) {
-        const std::vector<int32_t> o = morton_order(m, h_targets, T);
-        if ((st = upload(ctx, S_ORDER, o.data(), o.size() * sizeof(int32_t))) != DD_OK) return st;
-        order = reinterpret_cast<const int32_t *>(ctx->scratch[S_ORDER]);
-    }
     if (kl || tv) {
         // more than two targets: the tiled copy of P (built once per mesh) and the
         // targets staged in the same layout make the pipelined tile available
@@ -305,7 +264,7 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
             tiled = &ta;
         }
         launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream, -1, m.LP != nullptr,
-                           order, tiled);
+                           tiled);
     }
     if (klt) {
         // the target-weighted KL is the reverse-KL member of the f-divergence kernels
@@ -738,8 +697,7 @@ dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t
             if ((st = ensure_scratch(ctx, S_FIELDS, out_bytes)) != DD_OK) return st;
             dst = reinterpret_cast<float *>(ctx->scratch[S_FIELDS]);
         }
-        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst,
-                         targets);
+        st = fields_into(ctx, *m, reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]), T, f_mask, prec, dst);
         if (st != DD_OK) return st;
         if (sp == 0) {
             CK(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, ctx->stream), "copy fields to host");
@@ -1052,8 +1010,7 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
             const int32_t per = (T + nch - 1) / nch;
             for (int32_t a0 = 0; a0 < T; a0 += per) {
                 const int32_t Tc = std::min(per, T - a0);
-                st = fields_into(ctx, *m, d_targets + a0, Tc, f_mask, prec, dst + (int64_t)a0 * m->n_v, targets + a0,
-                                 stride);
+                st = fields_into(ctx, *m, d_targets + a0, Tc, f_mask, prec, dst + (int64_t)a0 * m->n_v, stride);
                 if (st != DD_OK) return st;
                 CK(cudaEventRecord(ctx->side_ev[0], ctx->stream), "fields ready");
                 CK(cudaStreamWaitEvent(ctx->side, ctx->side_ev[0], 0), "side wait");
@@ -1066,7 +1023,7 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
             }
             CK(cudaEventRecord(ctx->side_ev[1], ctx->side), "fields copied");
         } else {
-            st = fields_into(ctx, *m, d_targets, T, f_mask, prec, dst, targets);
+            st = fields_into(ctx, *m, d_targets, T, f_mask, prec, dst);
             if (st != DD_OK) return st;
         }
         const float *trace_field = field_slot(dst, f_mask, trace_f, stride);
@@ -1223,11 +1180,12 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
             std::memcpy(meta.data() + o_items + j * sizeof(BatchItem), &order[j].second, sizeof(BatchItem));
         if ((st = upload(ctx, S_META, meta.data(), meta.size())) != DD_OK) return st;
         dmeta = reinterpret_cast<uint8_t *>(ctx->scratch[S_META]);
+        int64_t fix_blocks = 0;
+        for (int i = 0; i < n_items; ++i)
+            if (probs[i].out_kl) fix_blocks += fix_row_blocks(probs[i].n_v);
         launch_batch_fields(reinterpret_cast<const BatchProblem *>(dmeta + o_probs), (int32_t)n_items,
                             reinterpret_cast<const BatchItem *>(dmeta + o_items), (int32_t)order.size(),
-                            reinterpret_cast<int32_t *>(dmeta + o_counter), ctx->stream,
-                            reinterpret_cast<const int32_t *>(dmeta + o_tprob),
-                            reinterpret_cast<const int32_t *>(dmeta + o_tloc), nT, max_k, max_nv);
+                            reinterpret_cast<int32_t *>(dmeta + o_counter), ctx->stream, fix_blocks);
         CK(cudaGetLastError(), "batch field launch");
         bool host = false;
         if (sf == 0) {

@@ -110,16 +110,13 @@ dd_status refine_log_poisson(DevMesh &m, double tol, int32_t max_sweeps, cudaStr
 void launch_stage_targets(const float *P, int64_t n_v, int64_t k_pad, const int32_t *targets, int32_t T,
                           float4 *stage, cudaStream_t s, int *bad_id = nullptr, const float *LP = nullptr);
 // FP32 fields.  out_kl / out_tv: [T][n_v] (either may be null).  variant: the
-// tile shape for T > 2 (0 .. 5), or -1 for the autotuner's choice (which may
+// tile shape for T > 2 (0 .. 3), or -1 for the autotuner's choice (which may
 // run timed launches the first time a size class is seen).  staged_logs: the
 // staging took logarithms from log2 P (launch_stage_targets with LP), which
 // the tile kernel then reads instead of forming them from the staged entries.
-// order: null, or device [T], the order in which the exact recompute after the
-// tile pass visits the targets (spatially close targets one after the other
-// share the rows they recompute through L2).
 // tiled: null, or the tiled copies of P and log2 P (DevMesh::pt_p / pt_l)
 // with room for the staged targets in the same layout, which make the
-// pipelined tile shape (variant 5) available to the autotuner.
+// pipelined tile shape (variant 3) available to the autotuner.
 struct TiledArgs {
     const float *PT, *LT;        // [row tiles][kt][64]
     float *TQ, *TL;              // [ceil(T / 64)][kt][64], filled by launch_fields_fp32
@@ -130,7 +127,7 @@ size_t tiled_target_bytes(int64_t k_pad, int32_t T);
 dd_status prepare_tiled(DevMesh &m, cudaStream_t s, std::string &err);
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T,
                         float *out_kl, float *out_tv, int *err_flag, cudaStream_t s, int variant = -1,
-                        bool staged_logs = false, const int32_t *order = nullptr, const TiledArgs *tiled = nullptr);
+                        bool staged_logs = false, const TiledArgs *tiled = nullptr);
 // One problem of a multi-domain field launch, and one output tile of it.
 struct BatchProblem {
     const float *P;
@@ -138,7 +135,6 @@ struct BatchProblem {
     const float *sP, *sL, *sE;   // staged targets [T][k_pad] each
     int32_t T, variant;          // targets; tile shape (0: 64x64, 1: 128x32, 2: 256x16)
     float *out_kl, *out_tv;      // [T][n_v] each (either may be null)
-    const int32_t *order;        // null, or [T]: the order in which the exact recompute visits the targets
 };
 struct BatchItem {
     int32_t prob, x_tile, a_tile, pad;
@@ -150,12 +146,11 @@ int tile_rows(int variant);
 int tile_targets(int variant);
 void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, const int32_t *d_tlocal,
                         const int32_t *d_targets, int32_t n_targets, int64_t k_max, cudaStream_t s);
-// tile pass over every item, then the exact recompute per target (d_tprob /
-// d_tloc: each of the n_targets targets' problem and index there; k_max,
-// n_max: the largest k_pad and n_v of the problems)
+// tile pass over every item, then the exact recompute by row blocks of every
+// problem with KL output (fix_blocks: the sum of their fix_row_blocks(n_v))
 void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const BatchItem *d_items, int32_t n_items,
-                         int32_t *d_counter, cudaStream_t s, const int32_t *d_tprob, const int32_t *d_tloc,
-                         int32_t n_targets, int64_t k_max, int64_t n_max);
+                         int32_t *d_counter, cudaStream_t s, int64_t fix_blocks);
+int64_t fix_row_blocks(int64_t n_v);
 std::string tuning_table();
 // spurious local minima of T fields [T][n_v] (counts host [T], flags optional [T][n_v])
 void launch_local_minima(const DevMesh &m, const float *fields, const int32_t *targets, int32_t T, int32_t *counts,
@@ -223,7 +218,7 @@ void launch_batch_trace(const void *d_doms, const int32_t *d_tdom, const int32_t
                         const int32_t *d_path_target = nullptr, int64_t n_paths = 0);
 
 // ---------------------------------------------------------------- context
-enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_META, S_ORDER,
+enum ScratchId { S_TARGETS, S_SOURCES, S_STAGE, S_FIELDS, S_XY, S_LEN, S_STATUS, S_GRAD, S_GEMM, S_META,
                  S_TSTAGE, S_COUNT };
 
 struct MeshSlot {

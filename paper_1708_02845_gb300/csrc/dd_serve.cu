@@ -215,11 +215,11 @@ bool launch_batch(dd_server *sv, Slot &sl) {
         launch_batch_stage(reinterpret_cast<const BatchProblem *>(d + o_probs), reinterpret_cast<const int32_t *>(d + o_tprob),
                            reinterpret_cast<const int32_t *>(d + o_tloc), reinterpret_cast<const int32_t *>(d + o_targets),
                            nT, max_k, s);
+        int64_t fix_blocks = 0;
+        for (int i = 0; i < n_items; ++i) fix_blocks += fix_row_blocks(ms[i]->n_v);
         launch_batch_fields(reinterpret_cast<const BatchProblem *>(d + o_probs), (int32_t)n_items,
                             reinterpret_cast<const BatchItem *>(d + o_items), (int32_t)n_tiles,
-                            reinterpret_cast<int32_t *>(d + o_counter), s,
-                            reinterpret_cast<const int32_t *>(d + o_tprob), reinterpret_cast<const int32_t *>(d + o_tloc),
-                            nT, max_k, max_nv);
+                            reinterpret_cast<int32_t *>(d + o_counter), s, fix_blocks);
         launch_batch_trace(d + o_doms, reinterpret_cast<const int32_t *>(d + o_tprob),
                            reinterpret_cast<const int32_t *>(d + o_tloc), reinterpret_cast<const int32_t *>(d + o_targets),
                            reinterpret_cast<const int32_t *>(d + o_sources), nT, 0, max_nt, max_nv, sv->max_pts,
