@@ -1164,7 +1164,45 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
                          [](const std::pair<int64_t, BatchItem> &x, const std::pair<int64_t, BatchItem> &y) {
                              return x.first > y.first;
                          });
-        meta.resize(o_items + order.size() * sizeof(BatchItem));
+        // the pipelined launch: every mesh's tiled copy of P (built once per
+        // mesh; without room for it the batch stays staged), every problem's
+        // targets in the tiled layout, items of 128 rows x 64 targets
+        bool pipe_ok = true;
+        int64_t tstage_bytes = 0, max_tiles = 0;
+        for (int i = 0; i < n_items && pipe_ok; ++i) {
+            std::string err;
+            if (prepare_tiled(*ms[i], ctx->stream, err) != DD_OK) pipe_ok = false;
+            tstage_bytes += (int64_t)tiled_target_bytes(ms[i]->k_pad, T_per[i]);
+            max_tiles = std::max<int64_t>(max_tiles, (T_per[i] + 63) / 64 * (tiled_k32(ms[i]->k_pad) / 32));
+        }
+        if (pipe_ok && ensure_scratch(ctx, S_TSTAGE, (size_t)tstage_bytes) != DD_OK) {
+            cudaGetLastError();
+            pipe_ok = false;
+        }
+        std::vector<std::pair<int64_t, BatchItem>> order_pipe;
+        if (pipe_ok) {
+            float *ts = reinterpret_cast<float *>(ctx->scratch[S_TSTAGE]);
+            for (int i = 0; i < n_items; ++i) {
+                BatchProblem &q = probs[i];
+                const DevMesh &m = *ms[i];
+                const int64_t half = (int64_t)tiled_target_bytes(m.k_pad, T_per[i]) / (2 * sizeof(float));
+                q.PT = m.pt_p;
+                q.LT = m.pt_l;
+                q.kt = m.pt_kt;
+                q.TQ = ts;
+                q.TL = ts + half;
+                ts += 2 * half;
+                for (int64_t xt = 0; xt * 128 < m.n_v; ++xt)
+                    for (int at = 0; at * 64 < T_per[i]; ++at)
+                        order_pipe.push_back({m.pt_kt, BatchItem{i, (int32_t)xt, at, 0}});
+            }
+            std::stable_sort(order_pipe.begin(), order_pipe.end(),
+                             [](const std::pair<int64_t, BatchItem> &x, const std::pair<int64_t, BatchItem> &y) {
+                                 return x.first > y.first;
+                             });
+        }
+        const size_t o_items_pipe = o_items + align256(order.size() * sizeof(BatchItem));
+        meta.resize(o_items_pipe + order_pipe.size() * sizeof(BatchItem));
         std::memcpy(meta.data() + o_probs, probs.data(), n_items * sizeof(BatchProblem));
         // trace domains; gradients per item in consecutive blocks [T_i][n_t_i]
         {
@@ -1178,14 +1216,30 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
         }
         for (size_t j = 0; j < order.size(); ++j)
             std::memcpy(meta.data() + o_items + j * sizeof(BatchItem), &order[j].second, sizeof(BatchItem));
+        for (size_t j = 0; j < order_pipe.size(); ++j)
+            std::memcpy(meta.data() + o_items_pipe + j * sizeof(BatchItem), &order_pipe[j].second, sizeof(BatchItem));
         if ((st = upload(ctx, S_META, meta.data(), meta.size())) != DD_OK) return st;
         dmeta = reinterpret_cast<uint8_t *>(ctx->scratch[S_META]);
-        int64_t fix_blocks = 0;
-        for (int i = 0; i < n_items; ++i)
+        int64_t fix_blocks = 0, work = 0;
+        for (int i = 0; i < n_items; ++i) {
             if (probs[i].out_kl) fix_blocks += fix_row_blocks(probs[i].n_v);
-        launch_batch_fields(reinterpret_cast<const BatchProblem *>(dmeta + o_probs), (int32_t)n_items,
-                            reinterpret_cast<const BatchItem *>(dmeta + o_items), (int32_t)order.size(),
-                            reinterpret_cast<int32_t *>(dmeta + o_counter), ctx->stream, fix_blocks);
+            work += ms[i]->n_v * ms[i]->k_pad * (int64_t)T_per[i];
+        }
+        const BatchProblem *dprobs = reinterpret_cast<const BatchProblem *>(dmeta + o_probs);
+        int32_t *dcounter = reinterpret_cast<int32_t *>(dmeta + o_counter);
+        auto staged = [&]() {
+            launch_batch_fields(dprobs, (int32_t)n_items, reinterpret_cast<const BatchItem *>(dmeta + o_items),
+                                (int32_t)order.size(), dcounter, ctx->stream, fix_blocks);
+        };
+        auto pipelined = [&]() {
+            launch_batch_fields_pipe(dprobs, (int32_t)n_items, reinterpret_cast<const BatchItem *>(dmeta + o_items_pipe),
+                                     (int32_t)order_pipe.size(), dcounter, ctx->d_err, ctx->stream, fix_blocks,
+                                     max_tiles, (f_mask & DD_F_KL) != 0, (f_mask & DD_F_TV) != 0);
+        };
+        if (pipe_ok && batch_launch_choice(n_items, work, staged, pipelined, ctx->stream) == 1)
+            pipelined();
+        else
+            staged();
         CK(cudaGetLastError(), "batch field launch");
         bool host = false;
         if (sf == 0) {

@@ -664,11 +664,10 @@ __global__ void tiled_layout_kernel(const float *__restrict__ P, int64_t n_v, in
 // the staged targets (sP, and sE / sF when the staging holds logarithms of
 // entries below FLT_MIN) into the tiled layout: -P[t,b] and -log2 P[t,b],
 // the target-side log2 formed exactly as tile_body forms it
-__global__ void tiled_targets_kernel(const float *__restrict__ sP, const float *__restrict__ sE,
-                                     const float *__restrict__ sF, int32_t T, int64_t k_pad, int64_t k32,
-                                     float *__restrict__ TQ, float *__restrict__ TL) {
-    const int at = blockIdx.x;
-    const int64_t b0 = (int64_t)blockIdx.y * 32;
+__device__ __forceinline__ void tiled_targets_block(const float *__restrict__ sP, const float *__restrict__ sE,
+                                                    const float *__restrict__ sF, int32_t T, int64_t k_pad,
+                                                    int64_t kt, float *__restrict__ TQ, float *__restrict__ TL,
+                                                    int at, int64_t b0) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int idx = threadIdx.x + 256 * i;
@@ -685,9 +684,99 @@ __global__ void tiled_targets_kernel(const float *__restrict__ sP, const float *
         } else {
             lt = fast_l2(fmaxf(q, FLT_MIN));
         }
-        const int64_t o = ((int64_t)at * k32 + b) * kTiledRows + al;
+        const int64_t o = ((int64_t)at * kt + b) * kTiledRows + al;
         TQ[o] = -q;
         TL[o] = -lt;
+    }
+}
+
+__global__ void tiled_targets_kernel(const float *__restrict__ sP, const float *__restrict__ sE,
+                                     const float *__restrict__ sF, int32_t T, int64_t k_pad, int64_t kt,
+                                     float *__restrict__ TQ, float *__restrict__ TL) {
+    tiled_targets_block(sP, sE, sF, T, k_pad, kt, TQ, TL, blockIdx.x, (int64_t)blockIdx.y * 32);
+}
+
+// One stage of the pipelined tile: PB columns of the CTA's rows and targets
+// (cP / cL: this thread's 4 rows, cQ / cT: its 4 targets, column j at
+// j * 64) summed into the 64-column partial sums.
+template <bool KL, bool TV, int PB, int UNR>
+__device__ __forceinline__ void pipe_stage(const float *cP, const float *cL, const float *cQ, const float *cT,
+                                           float (&ckl)[4][4], float (&ctv)[4][4]) {
+    constexpr int RM = 4;
+#pragma unroll UNR
+    for (int j = 0; j < PB; ++j) {
+        float rP[RM], rL[RM], tQ[4], tL[4];
+        {
+            const float4 p4 = *reinterpret_cast<const float4 *>(cP + j * kTiledRows);
+            rP[0] = p4.x, rP[1] = p4.y, rP[2] = p4.z, rP[3] = p4.w;
+            if (KL) {
+                const float4 l4 = *reinterpret_cast<const float4 *>(cL + j * kTiledRows);
+                rL[0] = l4.x, rL[1] = l4.y, rL[2] = l4.z, rL[3] = l4.w;
+                const float4 t4 = *reinterpret_cast<const float4 *>(cT + j * kTiledRows);
+                tL[0] = t4.x, tL[1] = t4.y, tL[2] = t4.z, tL[3] = t4.w;
+            }
+            if (TV) {
+                const float4 q4 = *reinterpret_cast<const float4 *>(cQ + j * kTiledRows);
+                tQ[0] = q4.x, tQ[1] = q4.y, tQ[2] = q4.z, tQ[3] = q4.w;
+            }
+        }
+        // packed over pairs of targets: the row operands duplicated into both
+        // halves, the (negated) target values of a pair side by side
+        const f2_t nl[2] = {pk(tL[0], tL[1]), pk(tL[2], tL[3])};
+        const f2_t nq[2] = {pk(tQ[0], tQ[1]), pk(tQ[2], tQ[3])};
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            const f2_t p2 = pk(rP[r], rP[r]);
+            const f2_t l2 = pk(rL[r], rL[r]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (KL) {
+                    f2_t acc = pk(ckl[r][2 * h], ckl[r][2 * h + 1]);
+                    acc = fma2(p2, add2(l2, nl[h]), acc);
+                    upk(acc, ckl[r][2 * h], ckl[r][2 * h + 1]);
+                }
+                if (TV) {
+                    float d0, d1;
+                    upk(add2(p2, nq[h]), d0, d1);
+                    ctv[r][2 * h] = __fadd_rn(ctv[r][2 * h], fabsf(d0));
+                    ctv[r][2 * h + 1] = __fadd_rn(ctv[r][2 * h + 1], fabsf(d1));
+                }
+            }
+        }
+    }
+}
+
+// the 64-column partial sums into the totals (compensated for KL)
+__device__ __forceinline__ void pipe_merge(float (&kl)[4][4], float (&klc)[4][4], float (&tv)[4][4],
+                                           float (&ckl)[4][4], float (&ctv)[4][4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float y = __fsub_rn(ckl[r][q], klc[r][q]);
+            const float t = __fadd_rn(kl[r][q], y);
+            klc[r][q] = __fsub_rn(__fsub_rn(t, kl[r][q]), y);
+            kl[r][q] = t;
+            tv[r][q] = __fadd_rn(tv[r][q], ctv[r][q]);
+            ckl[r][q] = ctv[r][q] = 0.0f;
+        }
+}
+
+template <bool KL, bool TV>
+__device__ __forceinline__ void pipe_store(const float (&kl)[4][4], const float (&tv)[4][4], int64_t xr, int ar,
+                                           int64_t n_v, int32_t T, float *__restrict__ out_kl,
+                                           float *__restrict__ out_tv) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t x = xr + r;
+        if (x >= n_v) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int a = ar + q;
+            if (a >= T) continue;
+            if (KL && out_kl) out_kl[(int64_t)a * n_v + x] = __fmul_rn(kl[r][q], kLn2);
+            if (TV && out_tv) out_tv[(int64_t)a * n_v + x] = tv[r][q];
+        }
     }
 }
 
@@ -767,65 +856,13 @@ __global__ void __launch_bounds__(256 * H, 2 / H) field_tile_pipe_kernel(const f
             ok = false;
             break;
         }
-        const float *cP = psm + s * SST + roff, *cL = cP + RCH;
-        const float *cQ = psm + s * SST + 2 * RCH + tx * CN, *cT = cQ + TCH;
-#pragma unroll UNR
-        for (int j = 0; j < PB; ++j) {
-            float rP[RM], rL[RM], tQ[CN], tL[CN];
-            {
-                const float4 p4 = *reinterpret_cast<const float4 *>(cP + j * kTiledRows);
-                rP[0] = p4.x, rP[1] = p4.y, rP[2] = p4.z, rP[3] = p4.w;
-                if (KL) {
-                    const float4 l4 = *reinterpret_cast<const float4 *>(cL + j * kTiledRows);
-                    rL[0] = l4.x, rL[1] = l4.y, rL[2] = l4.z, rL[3] = l4.w;
-                    const float4 t4 = *reinterpret_cast<const float4 *>(cT + j * kTiledRows);
-                    tL[0] = t4.x, tL[1] = t4.y, tL[2] = t4.z, tL[3] = t4.w;
-                }
-                if (TV) {
-                    const float4 q4 = *reinterpret_cast<const float4 *>(cQ + j * kTiledRows);
-                    tQ[0] = q4.x, tQ[1] = q4.y, tQ[2] = q4.z, tQ[3] = q4.w;
-                }
-            }
-            // packed over pairs of targets: the row operands duplicated into both
-            // halves, the (negated) target values of a pair side by side
-            const f2_t nl[2] = {pk(tL[0], tL[1]), pk(tL[2], tL[3])};
-            const f2_t nq[2] = {pk(tQ[0], tQ[1]), pk(tQ[2], tQ[3])};
-#pragma unroll
-            for (int r = 0; r < RM; ++r) {
-                const f2_t p2 = pk(rP[r], rP[r]);
-                const f2_t l2 = pk(rL[r], rL[r]);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (KL) {
-                        f2_t acc = pk(ckl[r][2 * h], ckl[r][2 * h + 1]);
-                        acc = fma2(p2, add2(l2, nl[h]), acc);
-                        upk(acc, ckl[r][2 * h], ckl[r][2 * h + 1]);
-                    }
-                    if (TV) {
-                        float d0, d1;
-                        upk(add2(p2, nq[h]), d0, d1);
-                        ctv[r][2 * h] = __fadd_rn(ctv[r][2 * h], fabsf(d0));
-                        ctv[r][2 * h + 1] = __fadd_rn(ctv[r][2 * h + 1], fabsf(d1));
-                    }
-                }
-            }
-        }
+        const float *cP = psm + s * SST + roff;
+        const float *cQ = psm + s * SST + 2 * RCH + tx * CN;
+        pipe_stage<KL, TV, PB, UNR>(cP, cP + RCH, cQ, cQ + TCH, ckl, ctv);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         // 64-column partial sums, merged at the end of every 64 columns
-        if (((c + 1) * PB) % 64 == 0 || c == nch - 1) {
-#pragma unroll
-            for (int r = 0; r < RM; ++r)
-#pragma unroll
-                for (int q = 0; q < CN; ++q) {
-                    const float y = __fsub_rn(ckl[r][q], klc[r][q]);
-                    const float t = __fadd_rn(kl[r][q], y);
-                    klc[r][q] = __fsub_rn(__fsub_rn(t, kl[r][q]), y);
-                    kl[r][q] = t;
-                    tv[r][q] = __fadd_rn(tv[r][q], ctv[r][q]);
-                    ckl[r][q] = ctv[r][q] = 0.0f;
-                }
-        }
+        if (((c + 1) * PB) % 64 == 0 || c == nch - 1) pipe_merge(kl, klc, tv, ckl, ctv);
     }
     if (!ok) {
         // a wait gave up (the error flag is set): let this CTA's copies in flight land, waiting
@@ -835,18 +872,148 @@ __global__ void __launch_bounds__(256 * H, 2 / H) field_tile_pipe_kernel(const f
                 if (!mbar_wait_suspend(&full[cf % PS], (uint32_t)(cf / PS) & 1u, err)) break;
         return;
     }
-#pragma unroll
-    for (int r = 0; r < RM; ++r) {
-        const int64_t x = x0 + ty * RM + r;
-        if (x >= n_v) continue;
-#pragma unroll
-        for (int q = 0; q < CN; ++q) {
-            const int a = a0 + tx * CN + q;
-            if (a >= T) continue;
-            if (KL && out_kl) out_kl[(int64_t)a * n_v + x] = __fmul_rn(kl[r][q], kLn2);
-            if (TV && out_tv) out_tv[(int64_t)a * n_v + x] = tv[r][q];
+    pipe_store<KL, TV>(kl, tv, x0 + ty * RM, a0 + tx * CN, n_v, T, out_kl, out_tv);
+}
+
+// Many problems in one persistent launch, on the tiled layouts: one CTA of
+// 512 threads per SM takes (problem, pair of row tiles, target tile) items
+// from an atomic counter, largest first.  One thread streams the chunks of
+// the items it takes, item after item, through the two stages, and records
+// with each stage the item and chunk it holds; the CTA's warps start an item
+// at its first chunk (the problem's sizes and outputs, zero sums) and write
+// it out after its last, so the copies of one item's first chunks overlap
+// the sums of the previous item's last.  The stage that follows the last item
+// carries no copy and the item -1: the CTA ends there.  Every wait is bounded
+// (error flag, no output from the CTA that gave up).
+template <bool KL, bool TV>
+__global__ void __launch_bounds__(512, 1) batch_pipe_kernel(const BatchProblem *__restrict__ probs,
+                                                         const BatchItem *__restrict__ items, int32_t n_items,
+                                                         int32_t *__restrict__ counter, int *__restrict__ err) {
+    constexpr int H = 2, PB = 64, PS = 2, RM = 4, CN = 4, NW = 16;
+    constexpr int TCH = PB * kTiledRows, RCH = H * TCH, SST = 2 * RCH + 2 * TCH;
+    constexpr uint32_t kArr = TCH * sizeof(float);
+    constexpr uint32_t kStageBytes = kArr * (H * (KL ? 2 : 1) + (KL ? 1 : 0) + (TV ? 1 : 0));
+    extern __shared__ __align__(128) float psm[];
+    __shared__ __align__(8) uint64_t full[PS], empty[PS];
+    __shared__ int slot_item[PS], slot_chunk[PS];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tx = tid % (kTiledRows / CN), ty = tid / (kTiledRows / CN);
+
+    // producer state (thread 0)
+    int p_item = -1, p_ch = 0, p_nch = 0, produced = 0;
+    bool p_done = false;
+    int64_t p_kt = 0;
+    const float *gP = nullptr, *gL = nullptr, *gQ = nullptr, *gT = nullptr;
+    auto produce = [&](int s) {
+        if (p_ch >= p_nch) {
+            const int it = atomicAdd(counter, 1);
+            if (it >= n_items) {
+                p_done = true;
+                slot_item[s] = -1;
+                slot_chunk[s] = 0;
+                mbar_arrive(&full[s]);
+                return;
+            }
+            const BatchItem w = items[it];
+            const BatchProblem &q = probs[w.prob];
+            p_item = it;
+            p_ch = 0;
+            p_kt = q.kt;
+            p_nch = (int)(q.kt / PB);
+            gP = q.PT + (int64_t)w.x_tile * H * q.kt * kTiledRows;
+            gL = q.LT + (int64_t)w.x_tile * H * q.kt * kTiledRows;
+            gQ = q.TQ + (int64_t)w.a_tile * q.kt * kTiledRows;
+            gT = q.TL + (int64_t)w.a_tile * q.kt * kTiledRows;
         }
+        slot_item[s] = p_item;
+        slot_chunk[s] = p_ch;
+        float *st = psm + s * SST;
+        const int64_t go = (int64_t)p_ch * TCH;
+        mbar_expect_tx(&full[s], kStageBytes);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            bulk_g2s(st + h * TCH, gP + (int64_t)h * p_kt * kTiledRows + go, kArr, &full[s]);
+            if (KL) bulk_g2s(st + RCH + h * TCH, gL + (int64_t)h * p_kt * kTiledRows + go, kArr, &full[s]);
+        }
+        if (TV) bulk_g2s(st + 2 * RCH, gQ + go, kArr, &full[s]);
+        if (KL) bulk_g2s(st + 2 * RCH + TCH, gT + go, kArr, &full[s]);
+        ++p_ch;
+        ++produced;
+    };
+    if (tid == 0) {
+        for (int s = 0; s < PS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < PS && !p_done; ++s) produce(s);
+
+    float kl[RM][CN], tv[RM][CN], klc[RM][CN], ckl[RM][CN], ctv[RM][CN];
+    int64_t n_v = 0, xr = 0;
+    int32_t T = 0;
+    int ar = 0, nch = 0;
+    float *okl = nullptr, *otv = nullptr;
+    const int roff = (ty / 16) * TCH + (ty % 16) * RM;
+    bool ok = true;
+    int c = 0;
+    for (;; ++c) {
+        const int s = c % PS;
+        // refill the stage every warp released last with the next chunk of the stream
+        if (tid == 0 && c >= 1 && !p_done) {
+            const int cf = c - 1;
+            if (!mbar_wait_suspend(&empty[cf % PS], (uint32_t)(cf / PS) & 1u, err)) {
+                ok = false;
+                break;
+            }
+            produce(cf % PS);
+        }
+        if (!mbar_wait_suspend(&full[s], (uint32_t)(c / PS) & 1u, err)) {
+            ok = false;
+            break;
+        }
+        const int it = slot_item[s], ch = slot_chunk[s];
+        if (it < 0) break;
+        if (ch == 0) {
+            const BatchItem w = items[it];
+            const BatchProblem &q = probs[w.prob];
+            n_v = q.n_v;
+            T = q.T;
+            okl = q.out_kl;
+            otv = q.out_tv;
+            nch = (int)(q.kt / PB);
+            xr = (int64_t)w.x_tile * H * kTiledRows + ty * RM;
+            ar = w.a_tile * kTiledRows + tx * CN;
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int q2 = 0; q2 < CN; ++q2) kl[r][q2] = tv[r][q2] = klc[r][q2] = ckl[r][q2] = ctv[r][q2] = 0.0f;
+        }
+        const float *cP = psm + s * SST + roff;
+        const float *cQ = psm + s * SST + 2 * RCH + tx * CN;
+        pipe_stage<KL, TV, PB, 16>(cP, cP + RCH, cQ, cQ + TCH, ckl, ctv);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        pipe_merge(kl, klc, tv, ckl, ctv);           // every stage is one 64-column block
+        if (ch == nch - 1) pipe_store<KL, TV>(kl, tv, xr, ar, n_v, T, okl, otv);
+    }
+    if (!ok && tid == 0) {
+        // a wait gave up (the error flag is set): let the copies in flight land, waiting again with a limit
+        for (int cf = c; cf < produced; ++cf)
+            if (!mbar_wait_suspend(&full[cf % PS], (uint32_t)(cf / PS) & 1u, err)) break;
+    }
+}
+
+// the targets of every problem into the tiled layout: blockIdx.y a problem,
+// blockIdx.x one (target tile, 32 columns) block of it
+__global__ void batch_tiled_targets_kernel(const BatchProblem *__restrict__ probs) {
+    const BatchProblem &q = probs[blockIdx.y];
+    const int64_t cb = q.kt / 32, nt = (q.T + kTiledRows - 1) / kTiledRows;
+    const int64_t i = blockIdx.x;
+    if (i >= nt * cb) return;
+    tiled_targets_block(q.sP, q.sE, nullptr, q.T, q.k_pad, q.kt, q.TQ, q.TL, (int)(i / cb), (i % cb) * 32);
 }
 
 // Exact recompute by row blocks (one domain).  One CTA takes 32 consecutive
@@ -1378,7 +1545,76 @@ void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const Bat
     }
 }
 
+void launch_batch_fields_pipe(const BatchProblem *d_probs, int32_t n_probs, const BatchItem *d_items,
+                              int32_t n_items, int32_t *d_counter, int *err, cudaStream_t s, int64_t fix_blocks,
+                              int64_t max_tiles, bool f_kl, bool f_tv) {
+    if (n_items <= 0) return;
+    {
+        KMark km_("tiled_targets_kernel", s);
+        batch_tiled_targets_kernel<<<dim3((unsigned)max_tiles, (unsigned)n_probs), 256, 0, s>>>(d_probs);
+    }
+    constexpr size_t smem = (size_t)2 * 6 * 64 * kTiledRows * sizeof(float);
+    cudaMemsetAsync(d_counter, 0, sizeof(int32_t), s);
+    const unsigned grid = (unsigned)std::min<int64_t>(num_sms(), n_items);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        KMark km_("batch_tile_kernel", s);
+        kern<<<grid, 512, smem, s>>>(d_probs, d_items, n_items, d_counter, err);
+    };
+    if (f_kl && f_tv)
+        go(batch_pipe_kernel<true, true>);
+    else if (f_kl)
+        go(batch_pipe_kernel<true, false>);
+    else
+        go(batch_pipe_kernel<false, true>);
+    if (fix_blocks > 0) {
+        KMark km_("fix_kl_batch_kernel", s);
+        fix_kl_rows_batch_kernel<<<(unsigned)fix_blocks, 256, 0, s>>>(d_probs, n_probs);
+    }
+}
+
 int64_t fix_row_blocks(int64_t n_v) { return (n_v + kFixRB - 1) / kFixRB; }
+
+std::map<std::pair<int, int>, int> g_batch_tune;      // (log2 problems, log2 work) -> 0 staged / 1 pipelined
+
+int batch_launch_choice(int32_t n_probs, int64_t work, const std::function<void()> &staged,
+                        const std::function<void()> &pipelined, cudaStream_t s) {
+    if (const char *pin = std::getenv("DD_BATCH_PIPE")) {
+        if (pin[0] == '0') return 0;
+        if (pin[0] == '1') return 1;
+    }
+    const auto key = std::make_pair(ilog2_ceil(n_probs), ilog2_ceil(work));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_batch_tune.find(key);
+        if (it != g_batch_tune.end()) return it->second;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best = 0;
+    for (int v = 0; v < 2; ++v) {
+        const std::function<void()> &f = v ? pipelined : staged;
+        f();                                 // warm-up
+        cudaEventRecord(e0, s);
+        f();
+        f();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_batch_tune[key] = best;
+    return best;
+}
 
 std::string tuning_table() {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -1389,6 +1625,12 @@ std::string tuning_table() {
         const int tk = std::get<2>(kv.first);
         std::snprintf(buf, sizeof buf, "rows<=2^%d k_pad<=2^%d T<=2^%d%s: %s\n", std::get<0>(kv.first),
                       std::get<1>(kv.first), tk % 100, tk >= 100 ? " (tiled copy of P)" : "", names[kv.second]);
+        out += buf;
+    }
+    for (auto &kv : g_batch_tune) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "batch of problems<=2^%d n*k*T<=2^%d: %s\n", kv.first.first, kv.first.second,
+                      kv.second ? "pipelined persistent launch" : "staged persistent launch");
         out += buf;
     }
     return out;

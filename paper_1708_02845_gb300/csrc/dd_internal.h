@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <memory>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -133,8 +134,13 @@ struct BatchProblem {
     const float *P;
     int64_t n_v, k_pad;
     const float *sP, *sL, *sE;   // staged targets [T][k_pad] each
-    int32_t T, variant;          // targets; tile shape (0: 64x64, 1: 128x32, 2: 256x16)
+    int32_t T, variant;          // targets; tile shape (0: 64x64, 1: 128x32, 2: 256x16, 3: pipelined)
     float *out_kl, *out_tv;      // [T][n_v] each (either may be null)
+    // the pipelined launch: the mesh's tiled copies of P and log2 P and this
+    // problem's targets in the same layout (null when the launch is staged)
+    const float *PT, *LT;
+    float *TQ, *TL;
+    int64_t kt;
 };
 struct BatchItem {
     int32_t prob, x_tile, a_tile, pad;
@@ -150,7 +156,23 @@ void launch_batch_stage(const BatchProblem *d_probs, const int32_t *d_tprob, con
 // problem with KL output (fix_blocks: the sum of their fix_row_blocks(n_v))
 void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const BatchItem *d_items, int32_t n_items,
                          int32_t *d_counter, cudaStream_t s, int64_t fix_blocks);
+// The pipelined multi-domain launch: every problem carries its tiled arrays
+// (PT, LT, TQ, TL, kt) and the items are 128-row x 64-target tiles (BatchItem
+// x_tile counts pairs of 64-row tiles); the targets are first put into the
+// tiled layout (max_tiles: the largest ceil(T / 64) * kt / 32 of the problems),
+// then one persistent launch computes every tile (f_kl / f_tv: which fields
+// all problems ask for), then the exact recompute.
+void launch_batch_fields_pipe(const BatchProblem *d_probs, int32_t n_probs, const BatchItem *d_items,
+                              int32_t n_items, int32_t *d_counter, int *err, cudaStream_t s, int64_t fix_blocks,
+                              int64_t max_tiles, bool f_kl, bool f_tv);
 int64_t fix_row_blocks(int64_t n_v);
+// The autotuner's choice between the staged (0) and the pipelined (1)
+// multi-domain launch: the first time a class of batches is seen (problems
+// and n k T work in powers of two) both run (a warm-up and two timed launches
+// each, on the caller's stream) and the faster is kept for the class.
+// DD_BATCH_PIPE=0 or 1 pins the choice.
+int batch_launch_choice(int32_t n_probs, int64_t work, const std::function<void()> &staged,
+                        const std::function<void()> &pipelined, cudaStream_t s);
 std::string tuning_table();
 // spurious local minima of T fields [T][n_v] (counts host [T], flags optional [T][n_v])
 void launch_local_minima(const DevMesh &m, const float *fields, const int32_t *targets, int32_t T, int32_t *counts,

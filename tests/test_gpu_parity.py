@@ -317,6 +317,34 @@ def test_every_tile_shape_bit_identical(env, monkeypatch):
     dd.dd_unload_mesh(ctx, mid)
 
 
+def test_more_targets_than_one_recompute_window(env):
+    """1,100 targets (repeats included) on grid37: the exact recompute scans
+    its row blocks' first-pass values in windows of 1,024 targets and stages
+    the flagging targets in groups of 16, so this crosses a window and runs
+    many groups; every field (KL and TV) matches the oracle's, and a repeated
+    target gives identical rows."""
+    dd, ctx = env
+    wl, po, P = case("grid37")
+    mid = load(dd, ctx, wl.mesh)
+    dd.dd_set_poisson_kernel(ctx, mid, P)
+    rng = np.random.default_rng(1100)
+    pool = [int(t) for t in wl.targets]
+    targets = [pool[i] for i in rng.integers(0, len(pool), 1100)]
+    out = torch.empty((2, len(targets), wl.mesh.n_v), dtype=torch.float32, device="cuda")
+    dd.dd_distance(ctx, mid, targets, dd.DD_F_KL | dd.DD_F_TV, dd.DD_PREC_FP32, out)
+    dd.dd_sync(ctx)
+    o = out.cpu().numpy()
+    refs = {}
+    for a, t in enumerate(targets):
+        if t not in refs:
+            refs[t] = (kl_field_fast(P, P[t]), tv_field(P, P[t]), a)
+        kl, tv, first = refs[t]
+        assert field_error(o[0, a], kl) <= TOL_FP32
+        assert field_error(o[1, a], tv) <= TOL_FP32
+        assert np.array_equal(o[:, a], o[:, first])
+    dd.dd_unload_mesh(ctx, mid)
+
+
 def test_kernel_timing_hook(env):
     """dd_kernel_timing: per-kernel CUDA-event totals of the launches on the
     context's stream, one entry per kernel of a dd_query, none once disabled."""
