@@ -1046,7 +1046,11 @@ struct FixSmem {
     float acc[kFixRB][kFixG];
 };
 
-// rows x0 .. x0 + 31 of one problem (sh.tab built; called by all 256 threads)
+// rows x0 .. x0 + 31 of one problem (sh.tab built; called by all 256 threads).
+// PF: each warp issues the loads of all its flagged rows of a chunk before
+// it uses any (for launches of one wave, where nothing else hides their
+// latency; the registers it takes cost occupancy on larger ones)
+template <bool PF>
 __device__ __forceinline__ void fix_rows(const float *__restrict__ P, int64_t n_v, int64_t k_pad, int32_t T,
                                          const float *__restrict__ sL, const float *__restrict__ sE,
                                          float *__restrict__ out_kl, int64_t x0, FixSmem &sh) {
@@ -1095,20 +1099,39 @@ __device__ __forceinline__ void fix_rows(const float *__restrict__ P, int64_t n_
                     *reinterpret_cast<float4 *>(&sh.ge[u][4 * c4]) = e;
                 }
                 __syncthreads();
-                for (int r = warp; r < kFixRB; r += 8) {
-                    // the group's targets that flag row r, one bit per target
-                    const bool f = lane < ng && ((sh.rmask[sh.ulist[g0 + min(lane, ng - 1)]] >> r) & 1u);
-                    unsigned gm = __ballot_sync(0xffffffffu, f);
-                    if (!gm) continue;
-                    const int64_t x = x0 + r;
-                    float px[8], lm[8], eb[8];
+                // this warp's rows warp, warp + 8, ..: the group's targets that flag
+                // each (one bit per target), and the flagged rows' entries of the
+                // chunk, all loads issued before any is used
+                constexpr int RW = kFixRB / 8;
+                constexpr int NB = PF ? RW : 1;       // rows whose entries are held at once
+                unsigned gms[RW];
+                float pxs[NB][8];
+                auto load_row = [&](int i, float(&px)[8]) {
+                    const int r = warp + 8 * i;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int64_t col = c0 + h * 128 + 4 * lane;
                         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (col < k_pad) v = __ldcg(reinterpret_cast<const float4 *>(P + x * k_pad + col));
+                        if (gms[i] && col < k_pad)
+                            v = __ldcg(reinterpret_cast<const float4 *>(P + (x0 + r) * k_pad + col));
                         px[4 * h] = v.x, px[4 * h + 1] = v.y, px[4 * h + 2] = v.z, px[4 * h + 3] = v.w;
                     }
+                };
+#pragma unroll
+                for (int i = 0; i < RW; ++i) {
+                    const int r = warp + 8 * i;
+                    const bool f = lane < ng && ((sh.rmask[sh.ulist[g0 + min(lane, ng - 1)]] >> r) & 1u);
+                    gms[i] = __ballot_sync(0xffffffffu, f);
+                    if (PF) load_row(i, pxs[PF ? i : 0]);
+                }
+#pragma unroll
+                for (int i = 0; i < RW; ++i) {
+                    const int r = warp + 8 * i;
+                    unsigned gm = gms[i];
+                    if (!gm) continue;
+                    if (!PF) load_row(i, pxs[0]);
+                    const float(&px)[8] = pxs[PF ? i : 0];
+                    float lm[8], eb[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) split_log<false>(px[q], sh.tab, lm[q], eb[q]);
                     while (gm) {
@@ -1141,19 +1164,23 @@ __device__ __forceinline__ void fix_rows(const float *__restrict__ P, int64_t n_
     }
 }
 
-__global__ void __launch_bounds__(256) fix_kl_rows_kernel(const float *__restrict__ P, int64_t n_v, int64_t k_pad,
-                                                        int32_t T, const float *__restrict__ sL,
-                                                        const float *__restrict__ sE, float *__restrict__ out_kl) {
+template <bool PF>
+__global__ void __launch_bounds__(256, PF ? 3 : 4) fix_kl_rows_kernel(const float *__restrict__ P, int64_t n_v,
+                                                                     int64_t k_pad, int32_t T,
+                                                                     const float *__restrict__ sL,
+                                                                     const float *__restrict__ sE,
+                                                                     float *__restrict__ out_kl) {
     __shared__ FixSmem sh;
     build_log_table(sh.tab);
-    fix_rows(P, n_v, k_pad, T, sL, sE, out_kl, (int64_t)blockIdx.x * kFixRB, sh);
+    fix_rows<PF>(P, n_v, k_pad, T, sL, sE, out_kl, (int64_t)blockIdx.x * kFixRB, sh);
 }
 
 // Many problems: CTA g takes row block g of the problems' row blocks in
 // order (problems without KL output have none); the CTA finds its problem by
 // a block-wide prefix sum over the problems' row-block counts.
-__global__ void __launch_bounds__(256) fix_kl_rows_batch_kernel(const BatchProblem *__restrict__ probs,
-                                                              int32_t n_probs) {
+template <bool PF>
+__global__ void __launch_bounds__(256, PF ? 3 : 4) fix_kl_rows_batch_kernel(const BatchProblem *__restrict__ probs,
+                                                                           int32_t n_probs) {
     __shared__ FixSmem sh;
     __shared__ int64_t wsum[8];
     __shared__ int found_prob;
@@ -1187,7 +1214,7 @@ __global__ void __launch_bounds__(256) fix_kl_rows_batch_kernel(const BatchProbl
     }
     if (found_prob < 0) return;
     const BatchProblem &q = probs[found_prob];
-    fix_rows(q.P, q.n_v, q.k_pad, q.T, q.sL, q.sE, q.out_kl, found_x0, sh);
+    fix_rows<PF>(q.P, q.n_v, q.k_pad, q.T, q.sL, q.sE, q.out_kl, found_x0, sh);
 }
 
 // the three shapes the autotuner chooses from
@@ -1237,6 +1264,9 @@ int num_sms() {
     }
     return g_num_sms;
 }
+// the prefetching recompute when every row block is resident at once (three
+// CTAs per SM at its register count), the other one beyond
+bool fix_prefetch(int64_t blocks) { return blocks <= 3 * (int64_t)num_sms(); }
 
 
 // ------------------------------------------------------------------ multi-problem persistent launch
@@ -1501,7 +1531,11 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
     launch_variant(v, P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s, tiled, err_flag);
     if (out_kl) {
         KMark km_("fix_kl_kernel", s);        // the timing hook's name of the exact recompute
-        fix_kl_rows_kernel<<<(unsigned)((n_v + kFixRB - 1) / kFixRB), 256, 0, s>>>(P, n_v, k_pad, T, sL, sE, out_kl);
+        const int64_t blocks = (n_v + kFixRB - 1) / kFixRB;
+        if (fix_prefetch(blocks))
+            fix_kl_rows_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(P, n_v, k_pad, T, sL, sE, out_kl);
+        else
+            fix_kl_rows_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(P, n_v, k_pad, T, sL, sE, out_kl);
     }
 }
 
@@ -1541,7 +1575,10 @@ void launch_batch_fields(const BatchProblem *d_probs, int32_t n_probs, const Bat
     }
     if (fix_blocks > 0) {
         KMark km_("fix_kl_batch_kernel", s);      // the timing hook's name of the exact recompute
-        fix_kl_rows_batch_kernel<<<(unsigned)fix_blocks, 256, 0, s>>>(d_probs, n_probs);
+        if (fix_prefetch(fix_blocks))
+            fix_kl_rows_batch_kernel<true><<<(unsigned)fix_blocks, 256, 0, s>>>(d_probs, n_probs);
+        else
+            fix_kl_rows_batch_kernel<false><<<(unsigned)fix_blocks, 256, 0, s>>>(d_probs, n_probs);
     }
 }
 
@@ -1569,11 +1606,15 @@ void launch_batch_fields_pipe(const BatchProblem *d_probs, int32_t n_probs, cons
         go(batch_pipe_kernel<false, true>);
     if (fix_blocks > 0) {
         KMark km_("fix_kl_batch_kernel", s);
-        fix_kl_rows_batch_kernel<<<(unsigned)fix_blocks, 256, 0, s>>>(d_probs, n_probs);
+        if (fix_prefetch(fix_blocks))
+            fix_kl_rows_batch_kernel<true><<<(unsigned)fix_blocks, 256, 0, s>>>(d_probs, n_probs);
+        else
+            fix_kl_rows_batch_kernel<false><<<(unsigned)fix_blocks, 256, 0, s>>>(d_probs, n_probs);
     }
 }
 
 int64_t fix_row_blocks(int64_t n_v) { return (n_v + kFixRB - 1) / kFixRB; }
+
 
 std::map<std::pair<int, int>, int> g_batch_tune;      // (log2 problems, log2 work) -> 0 staged / 1 pipelined
 
