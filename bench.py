@@ -68,7 +68,7 @@ STEP_LAUNCHES = 7
 # the 16 CTAs of one pair run together and share it through L2.
 TRAFFIC = {
     "grid140": {},
-    "grid450": {"T": 1024, "S": 16, "field_tile_kernel": 9284659660, "trace_kernel": 307725013},
+    "grid450": {"T": 1024, "S": 16, "field_tile_kernel": 9287471001, "trace_kernel": 307644416},
 }
 # the same for one field_stream_kernel launch of the grid450 single-target pass
 STREAM_TRAFFIC_BYTES = 3035740160    # 3,032,217,088 read + 3,523,072 written (4 n k_pad = 3.03 GB of P)
