@@ -1000,13 +1000,17 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
         const int64_t stride = (int64_t)T * m->n_v;
         const int32_t *d_targets = reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]);
         if (sf == 0) {
-            // Host fields: computed in chunks of targets, each chunk's rows going
-            // back on a side stream while the next chunk is computed (and the
-            // last one while the paths are traced); FP32 many-target path only,
-            // one chunk otherwise
+            // Host fields: computed in two halves of the targets, the first
+            // half's rows going back on a side stream while the second is
+            // computed, the second's while the paths are traced; FP32
+            // many-target path only, one part otherwise.  (grid450, 1,024
+            // targets, end to end: 19.7k fields/s with two parts, 19.6k with
+            // four, 19.5k with eight, 19.2k with one or sixteen: each part
+            // adds its own last partial wave of the tile pass and its own
+            // recompute launch)
             if ((st = ensure_side(ctx)) != DD_OK) return st;
             const int nf = popcount2(f_mask);
-            const int32_t nch = (prec == DD_PREC_FP32 && T >= 256) ? std::min<int32_t>(8, T / 128) : 1;
+            const int32_t nch = (prec == DD_PREC_FP32 && T >= 256) ? 2 : 1;
             const int32_t per = (T + nch - 1) / nch;
             for (int32_t a0 = 0; a0 < T; a0 += per) {
                 const int32_t Tc = std::min(per, T - a0);
