@@ -195,14 +195,38 @@ def roof_tile(n_v, k, T, tile_ms, sms, sm_mhz, traffic):
                               "no ncu capture of this kernel on this workload"}
 
 
-def roof_walk(walk_ms, walk_points, max_points, traffic):
+_LOAD_NS = {}
+
+
+def load_latency(dd, ctx):
+    """ns per dependent global load (L1 bypassed), measured once per run by
+    dd_load_latency: a 32 MB cycle (L2 hits after a warm-up pass) and a 1 GB
+    one (DRAM)."""
+    if not _LOAD_NS:
+        try:
+            _LOAD_NS["l2"] = round(dd.dd_load_latency(ctx, 32 << 20, 200000), 1)
+            _LOAD_NS["dram"] = round(dd.dd_load_latency(ctx, 1 << 30, 100000), 1)
+        except Exception as e:     # a measurement, not a result: report why it is missing
+            _LOAD_NS["error"] = str(e)
+    return _LOAD_NS
+
+
+def roof_walk(walk_ms, walk_points, max_points, traffic, lat=None):
     """The walk: a chain of dependent gathers per path (one triangle record and
     one rate vector per crossing), bounded by the longest path's chain of
-    dependent L2 round trips, not by a bandwidth."""
-    return {"kernel": "trace_kernel", "bound": "latency", "ms_per_launch": round(walk_ms, 4),
-            "points_per_s": round(walk_points / (walk_ms / 1e3), 1), "longest_path_points": int(max_points),
-            "us_per_point_of_longest_path": round(walk_ms * 1e3 / max(max_points, 1), 4), "traffic": traffic,
-            "note": "one dependent record + rate gather per crossing; the launch lasts as long as its longest path"}
+    dependent L2 round trips, not by a bandwidth.  With the measured latency
+    of one dependent L2 load: the floor of one such load per point of the
+    longest path, and the step's time in those loads."""
+    us_pt = walk_ms * 1e3 / max(max_points, 1)
+    out = {"kernel": "trace_kernel", "bound": "latency", "ms_per_launch": round(walk_ms, 4),
+           "points_per_s": round(walk_points / (walk_ms / 1e3), 1), "longest_path_points": int(max_points),
+           "us_per_point_of_longest_path": round(us_pt, 4), "traffic": traffic,
+           "note": "one dependent record + rate gather per crossing; the launch lasts as long as its longest path"}
+    if lat and "l2" in lat:
+        out["dependent_load_ns"] = {"l2": lat["l2"], "dram": lat["dram"], "source": "dd_load_latency, CUDA events"}
+        out["floor_ms_one_l2_load_per_point"] = round(max_points * lat["l2"] / 1e6, 4)
+        out["l2_loads_per_point"] = round(us_pt * 1e3 / lat["l2"], 2)
+    return out
 
 
 def query_step(dd, ctx, dev, stream, flush, args, rank, world, local_rank, name, pk, pk_kind):
@@ -336,7 +360,8 @@ def query_step(dd, ctx, dev, stream, flush, args, rank, world, local_rank, name,
     roof_t = roof_tile(n_v, k, T, tile_ms, sms, sm_mhz, traffic.get("field_tile_kernel"))
     walk_ms = per_launch.get("trace_kernel")
     walk_points = int(np.clip(lens, 0, None).sum())
-    roof_w = roof_walk(walk_ms, walk_points, int(lens.max()), traffic.get("trace_kernel")) if walk_ms else None
+    roof_w = (roof_walk(walk_ms, walk_points, int(lens.max()), traffic.get("trace_kernel"), load_latency(dd, ctx))
+              if walk_ms else None)
     dom = max(kernel_ms, key=lambda kn: kernel_ms[kn][1]) if kernel_ms else "field_tile_kernel"
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,

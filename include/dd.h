@@ -420,6 +420,20 @@ int32_t dd_tuning_table(char *buf, int32_t len);
  * context had when timing was enabled. */
 int32_t dd_kernel_timing(dd_ctx *ctx, int32_t mode, char *buf, int32_t len);
 
+/* Latency of one dependent global load (a measurement hook for the floor of
+ * the path walk, a chain of dependent gathers; the paper has no counterpart).
+ * One thread follows a seeded random cycle through `bytes` of device memory,
+ * one 4-byte index at the head of every 128-byte line, each load's address
+ * the value the previous one returned, with L1 bypassed: after a warm-up a
+ * buffer that fits L2 times an L2 hit, a much larger one a DRAM access.
+ * Allocates its buffer (and the host copy of the cycle) and frees both.
+ *   bytes        4096 .. 2^32, a multiple of 128
+ *   steps        timed loads (>= 1)
+ *   ns_per_load  out: CUDA-event time of the timed loads / steps
+ * Runs on the context's stream and synchronizes with it.
+ * Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA. */
+dd_status dd_load_latency(dd_ctx *ctx, int64_t bytes, int32_t steps, double *ns_per_load);
+
 /* ---- query server: continuous batching of path queries ------------------
  * A query asks for the paths from S sources to one interior target of a
  * loaded mesh, traced on the target's KL field (Section IV).  A server runs a

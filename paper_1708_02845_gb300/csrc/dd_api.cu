@@ -1373,6 +1373,22 @@ int32_t dd_kernel_timing(dd_ctx *ctx, int32_t mode, char *buf, int32_t len) {
     return (int32_t)out.size() + 1;
 }
 
+dd_status dd_load_latency(dd_ctx *ctx, int64_t bytes, int32_t steps, double *ns_per_load) {
+    if (!ctx || !ns_per_load || bytes < 4096 || bytes > (int64_t(1) << 32) || bytes % 128 || steps < 1)
+        return ctx ? set_err(ctx, DD_EINVAL, "dd_load_latency: bytes in [4096, 2^32], a multiple of 128; steps >= 1")
+                   : DD_EINVAL;
+    try {
+        dd_status st = select_device(ctx);
+        if (st != DD_OK) return st;
+        std::string err;
+        if ((st = measure_load_latency(bytes, steps, ctx->stream, ns_per_load, err)) != DD_OK)
+            return set_err(ctx, st, err);
+        return DD_OK;
+    } catch (...) {
+        return set_err(ctx, DD_ENOMEM, "host allocation failed");
+    }
+}
+
 int32_t dd_tuning_table(char *buf, int32_t len) {
     try {
         const std::string t = tuning_table();

@@ -189,6 +189,9 @@ dd_status launch_fdiv(const float *P, int64_t n_v, int64_t k_pad, const float4 *
 // Copy the defined prefix of every path (len[i] points of row i, pitch max_pts)
 // from device memory to another buffer (e.g. pinned host memory seen through its
 // device address), one warp per path, 16-byte stores (dd_trace.cu).
+// ns per dependent 4-byte load (L1 bypassed) along a random cycle of 128-byte
+// lines through `bytes` of device memory (allocated and freed here)
+dd_status measure_load_latency(int64_t bytes, int32_t steps, cudaStream_t s, double *ns, std::string &err);
 void launch_copy_paths(const float2 *src, const int32_t *len, int64_t n, int32_t max_pts, float2 *dst,
                        cudaStream_t s);
 

@@ -36,6 +36,8 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cmath>
+#include <random>
+#include <vector>
 
 #include "dd_internal.h"
 
@@ -680,4 +682,66 @@ void launch_copy_paths(const float2 *src, const int32_t *len, int64_t n, int32_t
         copy_paths_kernel<1><<<grid, 256, 0, s>>>(src, len, n, max_pts, dst);
     else
         copy_paths_kernel<0><<<grid, 256, 0, s>>>(src, len, n, max_pts, dst);
+}
+
+// ------------------------------------------------------------------ dependent-load latency
+// The walk's floor is a chain of dependent gathers.  This measures the
+// latency of one such gather: one thread follows a random cycle through a
+// buffer, one 4-byte index at the head of every 128-byte line, each load's
+// address the value of the one before (loads at L2, bypassing L1).
+namespace {
+// steps loads from the position *pos, which is left where the chase ended
+__global__ void load_chase_kernel(const int32_t *__restrict__ a, int64_t steps, int32_t *__restrict__ pos) {
+    int32_t j = *pos;
+    for (int64_t i = 0; i < steps; ++i) j = __ldcg(a + j);
+    *pos = j;
+}
+}  // namespace
+
+dd_status measure_load_latency(int64_t bytes, int32_t steps, cudaStream_t s, double *ns, std::string &err) {
+    const int64_t n = bytes / 128;            // lines
+    // a single cycle over all lines in a seeded random order
+    std::vector<int64_t> perm((size_t)n);
+    for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = i;
+    std::mt19937_64 rng(0x5eedULL);
+    for (int64_t i = n - 1; i > 0; --i) {
+        const int64_t j = (int64_t)(rng() % (uint64_t)(i + 1));
+        std::swap(perm[(size_t)i], perm[(size_t)j]);
+    }
+    std::vector<int32_t> next((size_t)n);
+    for (int64_t i = 0; i < n; ++i) next[(size_t)perm[(size_t)i]] = (int32_t)(perm[(size_t)((i + 1) % n)] * 32);
+    int32_t *d = nullptr, *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    dd_status st = DD_OK;
+    auto fail = [&](dd_status code, const char *what) {
+        cudaGetLastError();
+        err = what;
+        st = code;
+    };
+    if (cudaMalloc(&d, (size_t)n * 128) != cudaSuccess || cudaMalloc(&sink, sizeof(int32_t)) != cudaSuccess) {
+        fail(DD_ENOMEM, "allocation of the latency buffer failed");
+    } else if (cudaMemcpy2DAsync(d, 128, next.data(), sizeof(int32_t), sizeof(int32_t), (size_t)n,
+                                 cudaMemcpyHostToDevice, s) != cudaSuccess ||
+               cudaMemsetAsync(sink, 0, sizeof(int32_t), s) != cudaSuccess ||
+               cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        fail(DD_ECUDA, "latency buffer set-up failed");
+    } else {
+        // warm-up: the whole cycle when it is short (the timed loads then hit
+        // L2), else its first 2^18 lines (the timed loads go on to lines not
+        // yet visited)
+        load_chase_kernel<<<1, 1, 0, s>>>(d, std::min<int64_t>(n, 1 << 18), sink);
+        cudaEventRecord(e0, s);
+        load_chase_kernel<<<1, 1, 0, s>>>(d, steps, sink);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            fail(DD_ECUDA, "latency kernel failed");
+        else
+            *ns = (double)ms * 1e6 / steps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (d) cudaFree(d);
+    if (sink) cudaFree(sink);
+    return st;
 }

@@ -63,6 +63,7 @@ _SIGS = {
     "dd_query_batch": (_i32, [_p, _i32, _p, _p, _p, _p, _i32, _u32, _u32, _i32, _p, _p, _p, _p]),
     "dd_tuning_table": (_i32, [ctypes.c_char_p, _i32]),
     "dd_kernel_timing": (_i32, [_p, _i32, ctypes.c_char_p, _i32]),
+    "dd_load_latency": (_i32, [_p, _i64, _i32, ctypes.POINTER(ctypes.c_double)]),
     "dd_check_fast_log": (_i32, [ctypes.POINTER(ctypes.c_double)]),
     "dd_multigrid_check": (_i32, [_p, _p, _p, _i64, _p, _p, _f64, _i32, _p, _p]),
     "dd_server_create": (_i32, [_p, _i64, _i32, _i32, _i32, ctypes.POINTER(_p)]),
@@ -364,6 +365,13 @@ def dd_server_wait_idle(sv, timeout_s: float = 60.0):
 
 def dd_server_destroy(sv):
     lib.dd_server_destroy(sv)
+
+
+def dd_load_latency(ctx, nbytes: int, steps: int) -> float:
+    """ns per dependent global load along a random cycle through nbytes."""
+    ns = ctypes.c_double(0.0)
+    _check(ctx, lib.dd_load_latency(ctx, int(nbytes), int(steps), ctypes.byref(ns)))
+    return ns.value
 
 
 def dd_kernel_timing(ctx, mode: int) -> dict:
