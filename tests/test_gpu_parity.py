@@ -345,6 +345,20 @@ def test_more_targets_than_one_recompute_window(env):
     dd.dd_unload_mesh(ctx, mid)
 
 
+def test_load_latency_hook(env):
+    """dd_load_latency: a dependent-load chase through a buffer that fits L2
+    is faster than one through a buffer far larger than L2 (DRAM), both
+    positive; sizes outside [4096, 2^32] or not a multiple of 128 are refused."""
+    dd, ctx = env
+    l2 = dd.dd_load_latency(ctx, 16 << 20, 20000)
+    dram = dd.dd_load_latency(ctx, 1 << 30, 20000)
+    assert 0.0 < l2 < dram
+    for nbytes, steps in ((1000, 10), (4096 + 64, 10), ((1 << 32) + 128, 10), (4096, 0)):
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_load_latency(ctx, nbytes, steps)
+        assert e.value.status == dd.DD_EINVAL
+
+
 def test_kernel_timing_hook(env):
     """dd_kernel_timing: per-kernel CUDA-event totals of the launches on the
     context's stream, one entry per kernel of a dd_query, none once disabled."""
