@@ -293,7 +293,8 @@ dd_status dd_sparsify(dd_ctx *ctx, int32_t mesh, double theta, int64_t *kept, in
  * whole tiles; kept until P is recomputed, refined or replaced or the mesh
  * unloaded), and every such call stages its targets in the same layout
  * (context scratch, 8 T k_pad bytes rounded up): the pipelined tile pass
- * reads them.  DD_ENOMEM when the copy does not fit.
+ * reads them.  When either does not fit, the call runs the staged tile
+ * shapes instead, which need neither (same fields, bit for bit).
  * Errors: DD_EINVAL, DD_ESTATE (no Poisson kernel), DD_ENOMEM, DD_ECUDA. */
 dd_status dd_distance(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
                       uint32_t f_mask, int32_t prec, float *out);

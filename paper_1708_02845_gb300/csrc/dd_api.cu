@@ -255,13 +255,19 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
         // targets staged in the same layout make the pipelined tile available
         TiledArgs ta{};
         const TiledArgs *tiled = nullptr;
+        // (without room for them the staged tile shapes, which need none, run instead)
         if (T > 2) {
             std::string err;
-            if ((st = prepare_tiled(m, ctx->stream, err)) != DD_OK) return set_err(ctx, st, err);
-            if ((st = ensure_scratch(ctx, S_TSTAGE, tiled_target_bytes(m.k_pad, T))) != DD_OK) return st;
-            float *ts = reinterpret_cast<float *>(ctx->scratch[S_TSTAGE]);
-            ta = TiledArgs{m.pt_p, m.pt_l, ts, ts + tiled_target_bytes(m.k_pad, T) / (2 * sizeof(float)), m.pt_kt};
-            tiled = &ta;
+            if (prepare_tiled(m, ctx->stream, err) == DD_OK &&
+                ensure_scratch(ctx, S_TSTAGE, tiled_target_bytes(m.k_pad, T)) == DD_OK) {
+                float *ts = reinterpret_cast<float *>(ctx->scratch[S_TSTAGE]);
+                ta = TiledArgs{m.pt_p, m.pt_l, ts, ts + tiled_target_bytes(m.k_pad, T) / (2 * sizeof(float)),
+                               m.pt_kt};
+                tiled = &ta;
+            } else {
+                cudaGetLastError();
+                ctx->err.clear();
+            }
         }
         launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream, -1, m.LP != nullptr,
                            tiled);
