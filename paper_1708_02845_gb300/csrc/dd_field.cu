@@ -19,7 +19,7 @@
 // bit-identical values.  Target-side arguments below FLT_MIN are evaluated
 // at FLT_MIN; row-side terms with P[x,b] = 0 contribute 0 (the 0 log 0 rule).
 //
-// Two kernels:
+// The kernels:
 //  * field_stream (few targets): one warp per group of R rows, lanes along b,
 //    16-byte loads of P software-pipelined U float4 per lane and row ahead
 //    of the arithmetic, the target row and its logs staged in shared memory
@@ -28,9 +28,13 @@
 //  * field_tile (many targets): TM rows x TN targets per CTA, b in chunks of
 //    32 staged through shared memory, register micro-tiles.  Each P element's
 //    base-2 logarithm is formed once per CTA as one FP32 number and reused for
-//    TN targets (one subtraction and one multiply-add per KL term); the
-//    (row, target) pairs whose KL lands below DD_TILE_EXACT_BELOW are then
-//    recomputed in the exact split form by a second kernel (fix_kl_rows_kernel).
+//    TN targets (one subtraction and one multiply-add per KL term).
+//  * field_tile_pipe (many targets, one domain) and batch_pipe (many
+//    domains): the same sums on a tiled copy of P and of its log2, streamed
+//    through shared memory by bulk copies in stages of 64 columns, no
+//    staging arithmetic in the loop, FP32x2 over target pairs.
+//  * fix_kl_rows: the (row, target) pairs whose first-pass KL lands below
+//    DD_TILE_EXACT_BELOW recomputed in the exact split form, by row blocks.
 #include <algorithm>
 #include <vector>
 #include <type_traits>
