@@ -383,9 +383,14 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
 
 /* Fields and paths for targets on several loaded meshes in one pass (a batch
  * of uneven domains).  Item i is mesh mesh_ids[i] with T_per[i] targets; the
- * fields of all items are computed by one persistent launch whose tile shape
- * per item is chosen by the autotuner (dd_tuning_table), then the paths of
- * all items by one tracer launch.  Same arithmetic as dd_query with FP32.
+ * fields of all items are computed by one persistent launch, then the paths
+ * of all items by one tracer launch.  The launch is staged (each item in the
+ * tile shape the autotuner picks for it) or pipelined (every item in 128 x 64
+ * tiles on the meshes' tiled copies of P, as dd_distance builds them: 2 x 4
+ * n_v k_pad bytes per mesh, kept with the mesh; without room for them the
+ * launch stays staged), whichever the autotuner measured faster for the
+ * class of the batch (dd_tuning_table).  Same arithmetic as dd_query with
+ * FP32: both launches give the same fields, bit for bit.
  *   n_items   number of items (>= 1)
  *   mesh_ids  host [n_items] loaded meshes with a Poisson kernel
  *   T_per     host [n_items] targets per item (>= 1)
@@ -398,8 +403,10 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
  *   out_xy, out_len, out_status  as dd_trace_fields over sum T x S paths in
  *             target order (may be NULL when S = 0)
  * The first call that meets a new (size, k, T) class runs timed launches of
- * each tile shape before the batch.  Errors: DD_EINVAL, DD_ESTATE, DD_ENOMEM,
- * DD_ECUDA, DD_ETIMEOUT. */
+ * each tile shape before the batch, and the first that meets a new class of
+ * batches (items and sum n k T in powers of two) a warm-up and two timed
+ * runs of each of the two launches, on the context's stream, synchronizing
+ * with it.  Errors: DD_EINVAL, DD_ESTATE, DD_ENOMEM, DD_ECUDA, DD_ETIMEOUT. */
 dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, const int32_t *T_per,
                          const int32_t *targets, const int32_t *sources, int32_t S, uint32_t f_mask,
                          uint32_t trace_f, int32_t max_pts, float *out_fields, float *out_xy,
