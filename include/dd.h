@@ -413,8 +413,11 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
                          int32_t *out_len, int32_t *out_status);
 
 /* The autotuner's decisions so far as text, one line per size class
- * ("rows<=2^r k_pad<=2^c T<=2^t: 64x64").  Writes at most len bytes (NUL
- * terminated) into buf (may be NULL) and returns the full length. */
+ * ("rows<=2^r k_pad<=2^c T<=2^t: 64x64"; "... (tiled copy of P): 128x64
+ * pipelined" for single-domain calls that had the tiled copy) and one per
+ * class of batches ("batch of problems<=2^p n*k*T<=2^w: pipelined
+ * persistent launch").  Writes at most len bytes (NUL terminated) into buf
+ * (may be NULL) and returns the full length. */
 int32_t dd_tuning_table(char *buf, int32_t len);
 
 /* Per-kernel device time on the context's stream (an observability hook; the
