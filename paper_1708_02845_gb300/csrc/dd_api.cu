@@ -106,7 +106,8 @@ dd_status ensure_side(dd_ctx *ctx) {
     if (ctx->side) return DD_OK;
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->side_ev[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->side_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->side_ev[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->side_ev[2], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         return set_err(ctx, DD_ECUDA, "side stream creation failed");
     }
@@ -216,8 +217,10 @@ float *field_slot(float *dst, uint32_t f_mask, uint32_t bit, int64_t stride) {
 // The fields of T targets (ids already in device scratch) into dst
 // ([fields][T][n_v] by default; stride: the distance between two fields'
 // blocks when dst is a block of rows inside a larger output)
+// (tile_done: null, or an event recorded once TV is final -- after the FP32
+// many-target tile pass, else at the end)
 dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t T, uint32_t f_mask, int32_t prec,
-                      float *dst, int64_t stride = -1) {
+                      float *dst, int64_t stride = -1, cudaEvent_t tile_done = nullptr) {
     if (stride < 0) stride = (int64_t)T * m.n_v;
     float *kl = field_slot(dst, f_mask, DD_F_KL, stride);
     float *tv = field_slot(dst, f_mask, DD_F_TV, stride);
@@ -270,7 +273,9 @@ dd_status fields_into(dd_ctx *ctx, DevMesh &m, const int32_t *d_targets, int32_t
             }
         }
         launch_fields_fp32(m.P, m.n_v, m.k_pad, stage, T, kl, tv, ctx->d_err, ctx->stream, -1, m.LP != nullptr,
-                           tiled);
+                           tiled, tile_done);
+    } else if (tile_done) {
+        CK(cudaEventRecord(tile_done, ctx->stream), "fields event");
     }
     if (klt) {
         // the target-weighted KL is the reverse-KL member of the f-divergence kernels
@@ -1006,30 +1011,41 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
         const int64_t stride = (int64_t)T * m->n_v;
         const int32_t *d_targets = reinterpret_cast<const int32_t *>(ctx->scratch[S_TARGETS]);
         if (sf == 0) {
-            // Host fields: computed in two halves of the targets, the first
-            // half's rows going back on a side stream while the second is
-            // computed, the second's while the paths are traced; FP32
-            // many-target path only, one part otherwise.  (grid450, 1,024
-            // targets, end to end: 19.7k fields/s with two parts, 19.6k with
-            // four, 19.5k with eight, 19.2k with one or sixteen: each part
-            // adds its own last partial wave of the tile pass and its own
-            // recompute launch)
+            // Host fields: computed in up to four parts of the targets (at
+            // least 128 each), each part's rows going back on a side stream
+            // while the next is computed, the last one's while the paths are
+            // traced; FP32 many-target path only, one part otherwise.  Each
+            // part adds its own last partial wave of the tile pass and its own
+            // recompute launch, while fewer parts leave more of the copy
+            // exposed.  (grid450, 1,024 targets, end to end on one box, two
+            // runs each: two parts 20.1k / 18.8k fields/s, four 19.3k / 19.4k,
+            // eight 19.5k / 19.3k)
             if ((st = ensure_side(ctx)) != DD_OK) return st;
             const int nf = popcount2(f_mask);
-            const int32_t nch = (prec == DD_PREC_FP32 && T >= 256) ? 2 : 1;
+            const int32_t nch = (prec == DD_PREC_FP32 && T >= 256) ? std::min<int32_t>(4, T / 128) : 1;
             const int32_t per = (T + nch - 1) / nch;
+            // (TV is final once the tile pass has ended: its copy starts then,
+            // while the exact KL recompute runs)
+            const int tv_slot = (f_mask & DD_F_TV) ? ((f_mask & DD_F_KL) ? 1 : 0) : -1;
+            const bool early_tv = prec == DD_PREC_FP32 && tv_slot >= 0;
             for (int32_t a0 = 0; a0 < T; a0 += per) {
                 const int32_t Tc = std::min(per, T - a0);
-                st = fields_into(ctx, *m, d_targets + a0, Tc, f_mask, prec, dst + (int64_t)a0 * m->n_v, stride);
+                st = fields_into(ctx, *m, d_targets + a0, Tc, f_mask, prec, dst + (int64_t)a0 * m->n_v, stride,
+                                 early_tv ? ctx->side_ev[2] : nullptr);
                 if (st != DD_OK) return st;
+                auto copy = [&](int f) {
+                    const int64_t o = f * stride + (int64_t)a0 * m->n_v;
+                    return cudaMemcpyAsync(out_fields + o, dst + o, (size_t)Tc * m->n_v * sizeof(float),
+                                           cudaMemcpyDeviceToHost, ctx->side);
+                };
+                if (early_tv) {
+                    CK(cudaStreamWaitEvent(ctx->side, ctx->side_ev[2], 0), "side wait");
+                    CK(copy(tv_slot), "copy fields");
+                }
                 CK(cudaEventRecord(ctx->side_ev[0], ctx->stream), "fields ready");
                 CK(cudaStreamWaitEvent(ctx->side, ctx->side_ev[0], 0), "side wait");
-                for (int f = 0; f < nf; ++f) {
-                    const int64_t o = f * stride + (int64_t)a0 * m->n_v;
-                    CK(cudaMemcpyAsync(out_fields + o, dst + o, (size_t)Tc * m->n_v * sizeof(float),
-                                       cudaMemcpyDeviceToHost, ctx->side),
-                       "copy fields");
-                }
+                for (int f = 0; f < nf; ++f)
+                    if (!early_tv || f != tv_slot) CK(copy(f), "copy fields");
             }
             CK(cudaEventRecord(ctx->side_ev[1], ctx->side), "fields copied");
         } else {

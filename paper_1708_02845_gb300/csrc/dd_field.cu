@@ -1496,7 +1496,7 @@ dd_status prepare_tiled(DevMesh &m, cudaStream_t s, std::string &err) {
 
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T, float *out_kl,
                         float *out_tv, int *err_flag, cudaStream_t s, int variant, bool staged_logs,
-                        const TiledArgs *tiled) {
+                        const TiledArgs *tiled, cudaEvent_t tile_done) {
     const float *sP = reinterpret_cast<const float *>(stage);
     const float *sL = sP + (int64_t)T * k_pad;
     const float *sE = sL + (int64_t)T * k_pad;
@@ -1521,6 +1521,7 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
             kern<<<dim3((unsigned)grid_x, (unsigned)T), 256, smem, s>>>(P, n_v, k_pad, sP, sL, sE, sF, T, out_kl, out_tv,
                                                                        err_flag);
         }
+        if (tile_done) cudaEventRecord(tile_done, s);
         return;
     }
     if (tiled) {
@@ -1533,6 +1534,7 @@ void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4
                       ? variant
                       : tune_variant(P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s, tiled, err_flag);
     launch_variant(v, P, n_v, k_pad, sP, sL, sE, tF, T, out_kl, out_tv, s, tiled, err_flag);
+    if (tile_done) cudaEventRecord(tile_done, s);
     if (out_kl) {
         KMark km_("fix_kl_kernel", s);        // the timing hook's name of the exact recompute
         const int64_t blocks = (n_v + kFixRB - 1) / kFixRB;

@@ -126,9 +126,12 @@ struct TiledArgs {
 int64_t tiled_k32(int64_t k_pad);
 size_t tiled_target_bytes(int64_t k_pad, int32_t T);
 dd_status prepare_tiled(DevMesh &m, cudaStream_t s, std::string &err);
+// tile_done: null, or an event recorded on s when the many-target tile pass
+// has ended (TV final; KL still to be recomputed near the targets).
 void launch_fields_fp32(const float *P, int64_t n_v, int64_t k_pad, const float4 *stage, int32_t T,
                         float *out_kl, float *out_tv, int *err_flag, cudaStream_t s, int variant = -1,
-                        bool staged_logs = false, const TiledArgs *tiled = nullptr);
+                        bool staged_logs = false, const TiledArgs *tiled = nullptr,
+                        cudaEvent_t tile_done = nullptr);
 // One problem of a multi-domain field launch, and one output tile of it.
 struct BatchProblem {
     const float *P;
@@ -263,7 +266,7 @@ struct dd_ctx {
     size_t pinned_cap[S_COUNT] = {};
     cudaEvent_t pinned_free[S_COUNT] = {};    // recorded after the last upload from pinned[id]
     cudaStream_t side = nullptr;              // copies that overlap the main stream's kernels
-    cudaEvent_t side_ev[2] = {};
+    cudaEvent_t side_ev[3] = {};             // fields ready, fields copied, tile pass done
 };
 
 // Per-kernel device time (dd_kernel_timing): while timing is enabled for a
