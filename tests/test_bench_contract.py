@@ -64,6 +64,7 @@ def _fake_dd(n_v, k, kernel_ms):
     m.dd_trace_fields = lambda ctx, mid, f, tg, sr, max_pts, xy, ln, st: None
     m.dd_kernel_timing = kernel_timing
     m.dd_tuning_table = lambda: "rows<=2^18 k_pad<=2^12 T<=2^8: 64x64\n"
+    m.dd_load_latency = lambda ctx, nbytes, steps: 150.0 if nbytes < (64 << 20) else 410.0
     return m
 
 
@@ -93,6 +94,7 @@ def stand_ins(monkeypatch):
                             {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3})
         monkeypatch.setitem(bench.WORKLOADS, bench.HEADLINE, dict(bench.WORKLOADS[bench.HEADLINE], **SMALL))
         monkeypatch.setattr(bench, "sm_count", lambda dev: 148)
+        monkeypatch.setattr(bench, "_LOAD_NS", {})
         return fake
     return install
 
@@ -133,6 +135,10 @@ def test_step_line_keeps_the_contract(stand_ins):
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
     w = line["roofline_walk"]
     assert w["kernel"] == "trace_kernel" and w["bound"] == "latency" and w["longest_path_points"] == 12
+    # against one dependent L2 load per point of the longest path (150 ns from the latency hook)
+    assert w["dependent_load_ns"]["l2"] == 150.0 and w["dependent_load_ns"]["dram"] == 410.0
+    assert abs(w["floor_ms_one_l2_load_per_point"] - 12 * 150.0 / 1e6) < 1e-6
+    assert abs(w["l2_loads_per_point"] - w["us_per_point_of_longest_path"] * 1e3 / 150.0) < 0.01
     assert line["roofline_fields"] is None and line["gpu_launches"] == 18
     assert abs(line["recompute_over_tile"] - 0.6 / 6.7) < 1e-3
     e = line["e2e"]
