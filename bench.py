@@ -181,16 +181,19 @@ def clocks_rejected(clocks) -> bool:
 
 
 def roof_tile(n_v, k, T, tile_ms, sms, sm_mhz, traffic):
-    """The field tile kernel against the FP32 instruction issue rate: per
-    (row, column, target) KL one FADD (log2 ratio) + one FFMA, TV two FADD."""
+    """The field tile kernel against the FP32 pipe's rate: per (row, column,
+    target) 4 FP32 operations -- KL one addition (the log2 ratio) and one
+    multiply-add, TV two additions -- against 128 FP32 lanes x clock per SM
+    (one operation per lane per clock; a packed FP32x2 instruction does two
+    and holds the pipe twice as long)."""
     ops = 4.0 * n_v * k * T
     peak_alu = sms * 128 * sm_mhz * 1e6 / 1e12
     achieved = ops / (tile_ms / 1e3) / 1e12
     return {"kernel": "field_tile_kernel", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_alu, 3),
-            "unit": "T FP32 instructions/s", "frac": round(achieved / peak_alu, 4), "traffic": traffic,
+            "unit": "T FP32 operations/s", "frac": round(achieved / peak_alu, 4), "traffic": traffic,
             "algorithmic_fp32_ops": ops, "ms_per_launch": round(tile_ms, 4),
             "peak_source": f"{sms} SMs (read from the device) x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock "
-                           "sampled in the timed region), one FP32 instruction per lane per clock",
+                           "sampled in the timed region), one FP32 operation per lane per clock",
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch" if traffic else
                               "no ncu capture of this kernel on this workload"}
 
