@@ -404,7 +404,7 @@ dd_status dd_query(dd_ctx *ctx, int32_t mesh, const int32_t *targets, int32_t T,
  *             target order (may be NULL when S = 0)
  * The first call that meets a new (size, k, T) class runs timed launches of
  * each tile shape before the batch, and the first that meets a new class of
- * batches (items and sum n k T in powers of two) a warm-up and two timed
+ * batches (f_mask, items and sum n k T in powers of two) a warm-up and two timed
  * runs of each of the two launches, on the context's stream, synchronizing
  * with it.  Errors: DD_EINVAL, DD_ESTATE, DD_ENOMEM, DD_ECUDA, DD_ETIMEOUT. */
 dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, const int32_t *T_per,
@@ -415,7 +415,7 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
 /* The autotuner's decisions so far as text, one line per size class
  * ("rows<=2^r k_pad<=2^c T<=2^t: 64x64"; "... (tiled copy of P): 128x64
  * pipelined" for single-domain calls that had the tiled copy) and one per
- * class of batches ("batch of problems<=2^p n*k*T<=2^w: pipelined
+ * class of batches ("batch of problems<=2^p n*k*T<=2^w (KL+TV): pipelined
  * persistent launch").  Writes at most len bytes (NUL terminated) into buf
  * (may be NULL) and returns the full length. */
 int32_t dd_tuning_table(char *buf, int32_t len);

@@ -1262,7 +1262,7 @@ dd_status dd_query_batch(dd_ctx *ctx, int32_t n_items, const int32_t *mesh_ids, 
                                      (int32_t)order_pipe.size(), dcounter, ctx->d_err, ctx->stream, fix_blocks,
                                      max_tiles, (f_mask & DD_F_KL) != 0, (f_mask & DD_F_TV) != 0);
         };
-        if (pipe_ok && batch_launch_choice(n_items, work, staged, pipelined, ctx->stream) == 1)
+        if (pipe_ok && batch_launch_choice(n_items, work, f_mask, staged, pipelined, ctx->stream) == 1)
             pipelined();
         else
             staged();

@@ -1622,15 +1622,16 @@ void launch_batch_fields_pipe(const BatchProblem *d_probs, int32_t n_probs, cons
 int64_t fix_row_blocks(int64_t n_v) { return (n_v + kFixRB - 1) / kFixRB; }
 
 
-std::map<std::pair<int, int>, int> g_batch_tune;      // (log2 problems, log2 work) -> 0 staged / 1 pipelined
+// (fields asked for, log2 problems, log2 work) -> 0 staged / 1 pipelined
+std::map<std::tuple<int, int, int>, int> g_batch_tune;
 
-int batch_launch_choice(int32_t n_probs, int64_t work, const std::function<void()> &staged,
+int batch_launch_choice(int32_t n_probs, int64_t work, uint32_t f_mask, const std::function<void()> &staged,
                         const std::function<void()> &pipelined, cudaStream_t s) {
     if (const char *pin = std::getenv("DD_BATCH_PIPE")) {
         if (pin[0] == '0') return 0;
         if (pin[0] == '1') return 1;
     }
-    const auto key = std::make_pair(ilog2_ceil(n_probs), ilog2_ceil(work));
+    const auto key = std::make_tuple((int)f_mask, ilog2_ceil(n_probs), ilog2_ceil(work));
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_batch_tune.find(key);
@@ -1676,7 +1677,9 @@ std::string tuning_table() {
     }
     for (auto &kv : g_batch_tune) {
         char buf[160];
-        std::snprintf(buf, sizeof buf, "batch of problems<=2^%d n*k*T<=2^%d: %s\n", kv.first.first, kv.first.second,
+        const int fm = std::get<0>(kv.first);
+        std::snprintf(buf, sizeof buf, "batch of problems<=2^%d n*k*T<=2^%d (%s): %s\n", std::get<1>(kv.first),
+                      std::get<2>(kv.first), fm == 3 ? "KL+TV" : (fm == 1 ? "KL" : "TV"),
                       kv.second ? "pipelined persistent launch" : "staged persistent launch");
         out += buf;
     }

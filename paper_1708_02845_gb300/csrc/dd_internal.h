@@ -170,11 +170,11 @@ void launch_batch_fields_pipe(const BatchProblem *d_probs, int32_t n_probs, cons
                               int64_t max_tiles, bool f_kl, bool f_tv);
 int64_t fix_row_blocks(int64_t n_v);
 // The autotuner's choice between the staged (0) and the pipelined (1)
-// multi-domain launch: the first time a class of batches is seen (problems
-// and n k T work in powers of two) both run (a warm-up and two timed launches
-// each, on the caller's stream) and the faster is kept for the class.
-// DD_BATCH_PIPE=0 or 1 pins the choice.
-int batch_launch_choice(int32_t n_probs, int64_t work, const std::function<void()> &staged,
+// multi-domain launch: the first time a class of batches is seen (the fields
+// asked for, problems and n k T work in powers of two) both run (a warm-up
+// and two timed launches each, on the caller's stream) and the faster is kept
+// for the class.  DD_BATCH_PIPE=0 or 1 pins the choice.
+int batch_launch_choice(int32_t n_probs, int64_t work, uint32_t f_mask, const std::function<void()> &staged,
                         const std::function<void()> &pipelined, cudaStream_t s);
 std::string tuning_table();
 // spurious local minima of T fields [T][n_v] (counts host [T], flags optional [T][n_v])
